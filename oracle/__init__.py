@@ -1,0 +1,244 @@
+"""ctypes wrapper of the FP64 brute-force CPU oracle (``oracle.c``).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is what the CUDA path is checked
+against; only the test suite, the smoke check and the benchmark's CPU
+baseline may import it.  It shares no code with the CUDA library: both only
+consume the seeded arrays of the ``scenes`` package.
+
+Path records on this side are AoS: ``photons[n, B, 8]`` float32 with
+(x, y, z, prim-as-int32-bits, E_r, E_g, E_b, path-length) per photon (the
+32-byte record of Sec. 4), ``info[n]`` uint32 (Sec. 4 bit fields) and
+``origin[n, 3]`` float32.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "liboracle.so")
+
+MODE_NAIVE_AABB = 0
+MODE_NAIVE_EXACT = 1
+MODE_ERROR = 2
+FLAG_TEST_OLD_TRIS = 1
+FLAG_ERROR_EXACT = 2
+
+AMB_TRACE = 1
+AMB_VERIFY = 2
+AMB_CONT = 4
+AMB_ENERGY = 8
+AMB_LIGHT = 16
+
+INFO_REPLACE = 1 << 30
+INFO_REUSE_LIGHT = 1 << 31
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, no floating-point contraction)."""
+    src = os.path.join(_HERE, "oracle.c")
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
+            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp",
+                               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, src, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class _Light(C.Structure):
+    _fields_ = [("type", C.c_int32), ("pos", C.c_float * 3), ("normal", C.c_float * 3),
+                ("tangent", C.c_float * 3), ("size", C.c_float * 2), ("power", C.c_float * 3),
+                ("n_paths", C.c_uint32)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in (
+        "paths", "segments_tested", "segments_amb", "vis_rays", "cont_rays", "trace_rays",
+        "energy_tests", "energy_amb", "n_reemit", "n_tail", "n_updated", "n_truncated")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_SO)
+        P = C.c_void_p
+        L.or_scene_create.restype = P
+        L.or_scene_create.argtypes = [P, C.c_uint32, P, C.c_uint32, P, P, C.c_double, C.c_uint32]
+        L.or_scene_destroy.argtypes = [P]
+        L.or_scene_set_poses.argtypes = [P, P, P, P, P, C.c_uint32]
+        L.or_philox4x32_10.argtypes = [P, P, P]
+        L.or_trace.argtypes = [P, P, C.c_uint32, C.c_uint64, C.c_uint32, P, P, P, P, P]
+        L.or_verify.argtypes = [P, P, C.c_uint32, C.c_int32, C.c_double, C.c_uint32, P, P, P, P, P, P]
+        L.or_compact.restype = C.c_uint32
+        L.or_compact.argtypes = [P, C.c_uint32, P]
+        L.or_retrace.argtypes = [P, P, C.c_uint32, C.c_uint64, C.c_uint32, P, P, P, P, P]
+        L.or_deposit.argtypes = [P, C.c_uint32, P, C.c_uint32, C.c_uint32, C.c_uint32,
+                                 C.c_float, C.c_float, C.c_float, C.c_float, P]
+        L.or_closest_hit.restype = C.c_int32
+        L.or_closest_hit.argtypes = [P, P, P, C.c_double, C.c_int32, P, P]
+        L.or_num_threads.restype = C.c_int32
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    o = np.zeros(4, np.uint32)
+    lib().or_philox4x32_10(_p(c), _p(k), _p(o))
+    return o
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())
+
+
+def _lights(ls):
+    arr = (_Light * len(ls))()
+    for i, l in enumerate(ls):
+        arr[i].type = l.type
+        arr[i].pos[:] = list(l.pos)
+        arr[i].normal[:] = list(l.normal)
+        arr[i].tangent[:] = list(l.tangent)
+        arr[i].size[:] = list(l.size)
+        arr[i].power[:] = list(l.power)
+        arr[i].n_paths = l.n_paths
+    return arr
+
+
+@dataclass
+class Paths:
+    """Oracle-side path records for a subset of path ids."""
+    ids: np.ndarray                 # uint32 [n]
+    info: np.ndarray                # uint32 [n]
+    origin: np.ndarray              # float32 [n,3]
+    photons: np.ndarray             # float32 [n,B,8]
+    amb: np.ndarray                 # uint32 [n] ambiguity bits (accumulated)
+    stats: dict = field(default_factory=dict)
+
+    @property
+    def nseg(self) -> np.ndarray:
+        return (self.info >> 22) & 15
+
+    @property
+    def start(self) -> np.ndarray:
+        return (self.info >> 26) & 15
+
+    @property
+    def prim(self) -> np.ndarray:
+        return self.photons[..., 3].view(np.int32)
+
+    def copy(self) -> "Paths":
+        return Paths(self.ids.copy(), self.info.copy(), self.origin.copy(), self.photons.copy(),
+                     self.amb.copy(), dict(self.stats))
+
+
+class OracleScene:
+    """Oracle view of a ``scenes.Scene`` at a pair of (old, new) frames."""
+
+    def __init__(self, scene):
+        self.scene = scene
+        self.B = int(scene.max_bounces)
+        L = lib()
+        self._keep = (np.ascontiguousarray(scene.verts, np.float32),
+                      np.ascontiguousarray(scene.tri_object, np.uint32),
+                      np.ascontiguousarray(scene.object_dynamic, np.uint8),
+                      np.ascontiguousarray(scene.object_albedo, np.float32))
+        v, to, dy, al = self._keep
+        self._h = L.or_scene_create(_p(v), scene.n_tris, _p(to), scene.n_objects, _p(dy), _p(al),
+                                    float(scene.diag), self.B)
+        self.frames = None
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().or_scene_destroy(self._h)
+            self._h = None
+
+    def set_frames(self, frame_old: int, frame_new: int) -> None:
+        self.set_poses(self.scene.xforms(frame_old), self.scene.xforms(frame_new),
+                       self.scene.lights(frame_old), self.scene.lights(frame_new))
+        self.frames = (frame_old, frame_new)
+
+    def set_poses(self, xf_old, xf_new, lights_old, lights_new) -> None:
+        xo = np.ascontiguousarray(xf_old, np.float32)
+        xn = np.ascontiguousarray(xf_new, np.float32)
+        lo, ln = _lights(lights_old), _lights(lights_new)
+        lib().or_scene_set_poses(self._h, _p(xo), _p(xn), C.cast(lo, C.c_void_p),
+                                 C.cast(ln, C.c_void_p), len(lights_new))
+        self.frames = None
+
+    def trace(self, ids, seed: int, frame: int) -> Paths:
+        ids = np.ascontiguousarray(ids, np.uint32)
+        n = ids.shape[0]
+        p = Paths(ids, np.zeros(n, np.uint32), np.zeros((n, 3), np.float32),
+                  np.zeros((n, self.B, 8), np.float32), np.zeros(n, np.uint32))
+        st = _Stats()
+        lib().or_trace(self._h, _p(ids), n, seed, frame, _p(p.info), _p(p.origin), _p(p.photons),
+                       _p(p.amb), C.byref(st))
+        p.stats = st.as_dict()
+        return p
+
+    def verify(self, paths: Paths, mode: int, tau: float, flags: int = 0):
+        """In place; returns (segment mask [n], stats).  Ambiguity bits are
+        OR-ed into ``paths.amb``."""
+        n = paths.ids.shape[0]
+        mask = np.zeros(n, np.uint32)
+        amb = np.zeros(n, np.uint32)
+        st = _Stats()
+        lib().or_verify(self._h, _p(paths.ids), n, mode, float(tau), flags, _p(paths.info),
+                        _p(paths.origin), _p(paths.photons), _p(mask), _p(amb), C.byref(st))
+        paths.amb |= amb
+        return mask, st.as_dict()
+
+    def retrace(self, paths: Paths, seed: int, frame: int) -> dict:
+        n = paths.ids.shape[0]
+        amb = np.zeros(n, np.uint32)
+        st = _Stats()
+        lib().or_retrace(self._h, _p(paths.ids), n, seed, frame, _p(paths.info), _p(paths.origin),
+                         _p(paths.photons), _p(amb), C.byref(st))
+        paths.amb |= amb
+        return st.as_dict()
+
+    def closest_hit(self, o, d, tlo: float, exclude: int = -1):
+        o = np.ascontiguousarray(o, np.float64)
+        d = np.ascontiguousarray(d, np.float64)
+        t = C.c_double()
+        a = C.c_int32()
+        prim = lib().or_closest_hit(self._h, _p(o), _p(d), tlo, exclude, C.byref(t), C.byref(a))
+        return int(prim), float(t.value), bool(a.value)
+
+
+def compact(info: np.ndarray) -> np.ndarray:
+    """Ascending positions whose replace bit is set (the oracle's definition)."""
+    info = np.ascontiguousarray(info, np.uint32)
+    out = np.zeros(info.shape[0], np.uint32)
+    c = lib().or_compact(_p(info), info.shape[0], _p(out))
+    return out[:c]
+
+
+def deposit(paths: Paths, width: int, height: int, rect) -> np.ndarray:
+    """float64 [height, width, 3] atlas of incident photon energy."""
+    atlas = np.zeros((height, width, 3), np.float64)
+    B = paths.photons.shape[1]
+    x0, z0, x1, z1 = (float(np.float32(v)) for v in rect)
+    lib().or_deposit(_p(np.ascontiguousarray(paths.info)), paths.ids.shape[0],
+                     _p(np.ascontiguousarray(paths.photons)), B, width, height, x0, z0, x1, z1,
+                     _p(atlas))
+    return atlas

@@ -1,0 +1,968 @@
+/*
+ * FP64 brute-force oracle for per-frame photon-path verification.
+ * TEST INFRASTRUCTURE ONLY: see oracle.h for who may use it and why.
+ *
+ * Paper: Moreau, Doggett, Sintorn, "Path Verification for Dynamic Indirect
+ * Illumination" (arXiv 2111.06906).  Each function names the passage it
+ * follows.  Geometry is tested against every triangle, in double precision;
+ * path records are FP32 and every step restarts from the stored record.
+ *
+ * Readings of the paper taken here (the paper is silent or ambiguous):
+ *  - a photon record stores the hit position where Sec. 4 lists the incoming
+ *    direction; directions are differences of consecutive positions;
+ *  - "BRDF(Segment, NextSeg)" (Alg. 1) is the stored sample re-weighted for
+ *    the new vertex:  E_N = E_i * rho' * max(0, n'_s . w') / (q_i * (n_s . w)),
+ *    which equals E_O when nothing changed (Lambertian surfaces only, Sec. 6);
+ *  - Eq. 2 is applied per RGB channel and all channels must pass;
+ *  - AreClose (Alg. 1) = same primitive and |dx|_inf <= 1e-5 x diagonal; when
+ *    it holds E_N := E_O;
+ *  - after the skip branch of Alg. 1 the next segment is known valid and the
+ *    check resumes with the segment after it;
+ *  - a re-traced ray that misses everything truncates the path there;
+ *  - area-light origins keep the stored direction and re-intersect the new
+ *    light plane (Sec. 3.1); a path is invalid if the new origin leaves the
+ *    rectangle, lies behind x1, or the direction leaves the emitting
+ *    hemisphere; a tilted light re-weights the primary energy by
+ *    (n'.d)/(n.d) and applies Eq. 2;
+ *  - the point light's shadow-map check (Sec. 3.1) is an exact visibility ray.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+#define MAXL 4
+
+struct or_scene {
+  uint32_t n_tris, n_objects, B;
+  double diag, eps, tmin, close_tol;
+  float* verts;          /* [n_tris][9] as given */
+  uint32_t* tri_object;  /* [n_tris] */
+  uint8_t* dyn;          /* [n_objects] */
+  float* albedo;         /* [n_objects][3] */
+  double* world[2];      /* [n_tris][12] = v0,v1,v2,n (unnormalised) for pose 0=old, 1=new */
+  uint32_t* obj_first;   /* CSR of triangles per object: [n_objects+1] */
+  uint32_t* obj_tris;    /* [n_tris] */
+  uint8_t* moved;        /* [n_objects] */
+  uint32_t* moved_list;  /* [n_objects] */
+  uint32_t n_moved;
+  double* box;           /* [n_objects][2][6] lo/hi of old (0) and new (1) pose */
+  or_light light[2][MAXL];
+  uint32_t n_lights;
+  uint32_t light_first[MAXL + 1];
+  uint8_t light_moved[MAXL];
+  uint8_t light_tilted[MAXL];
+};
+
+/* ------------------------------------------------------------------------ */
+/* small vector helpers                                                       */
+/* ------------------------------------------------------------------------ */
+static inline double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static inline void sub3(const double* a, const double* b, double* r) {
+  r[0] = a[0] - b[0]; r[1] = a[1] - b[1]; r[2] = a[2] - b[2];
+}
+static inline void cross3(const double* a, const double* b, double* r) {
+  r[0] = a[1] * b[2] - a[2] * b[1];
+  r[1] = a[2] * b[0] - a[0] * b[2];
+  r[2] = a[0] * b[1] - a[1] * b[0];
+}
+static inline double norm3(const double* a) { return sqrt(dot3(a, a)); }
+static inline void normalize3(double* a) {
+  double l = norm3(a);
+  a[0] /= l; a[1] /= l; a[2] /= l;
+}
+static inline void f2d(const float* f, double* d) { d[0] = f[0]; d[1] = f[1]; d[2] = f[2]; }
+static inline double max3(const float* a) {
+  double m = a[0];
+  if (a[1] > m) m = a[1];
+  if (a[2] > m) m = a[2];
+  return m;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): ten rounds of two     */
+/* 32x32->64 multiplies; between rounds the key advances by the Weyl constants */
+/* (golden ratio and sqrt(3)-1 in 32-bit fixed point).                         */
+/* ------------------------------------------------------------------------ */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    uint32_t n1 = (uint32_t)p1;
+    uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    uint32_t n3 = (uint32_t)p0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Four uniforms in [0,1) with 24 significant bits (exact in FP32 and FP64)
+ * keyed by (path, vertex, frame).  Vertex 0: origin (u0,u1) and direction
+ * (u2,u3) of an emission; vertex k>=1: direction (u0,u1) and Russian-roulette
+ * draw (u2) of the bounce at photon k. */
+static void rng4(uint64_t seed, uint32_t path, uint32_t vertex, uint32_t frame, double u[4]) {
+  uint32_t ctr[4] = {path, vertex, frame, 0u};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t o[4];
+  or_philox4x32_10(ctr, key, o);
+  for (int j = 0; j < 4; ++j) u[j] = (double)(o[j] >> 8) * (1.0 / 16777216.0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* scene                                                                      */
+/* ------------------------------------------------------------------------ */
+or_scene* or_scene_create(const float* verts, uint32_t n_tris, const uint32_t* tri_object,
+                          uint32_t n_objects, const uint8_t* object_dynamic, const float* albedo,
+                          double diag, uint32_t max_bounces) {
+  or_scene* s = (or_scene*)calloc(1, sizeof(or_scene));
+  s->n_tris = n_tris;
+  s->n_objects = n_objects;
+  s->B = max_bounces;
+  s->diag = diag;
+  s->eps = 1e-6 * diag;
+  s->tmin = 1e-5 * diag;
+  s->close_tol = 1e-5 * diag;
+  s->verts = (float*)malloc(sizeof(float) * 9 * (size_t)n_tris);
+  memcpy(s->verts, verts, sizeof(float) * 9 * (size_t)n_tris);
+  s->tri_object = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)n_tris);
+  memcpy(s->tri_object, tri_object, sizeof(uint32_t) * (size_t)n_tris);
+  s->dyn = (uint8_t*)malloc(n_objects ? n_objects : 1);
+  memcpy(s->dyn, object_dynamic, n_objects);
+  s->albedo = (float*)malloc(sizeof(float) * 3 * (size_t)(n_objects ? n_objects : 1));
+  memcpy(s->albedo, albedo, sizeof(float) * 3 * (size_t)n_objects);
+  for (int p = 0; p < 2; ++p) s->world[p] = (double*)malloc(sizeof(double) * 12 * (size_t)(n_tris ? n_tris : 1));
+  s->obj_first = (uint32_t*)calloc((size_t)n_objects + 1, sizeof(uint32_t));
+  s->obj_tris = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n_tris ? n_tris : 1));
+  for (uint32_t t = 0; t < n_tris; ++t) s->obj_first[tri_object[t] + 1]++;
+  for (uint32_t o = 0; o < n_objects; ++o) s->obj_first[o + 1] += s->obj_first[o];
+  uint32_t* fill = (uint32_t*)calloc((size_t)n_objects + 1, sizeof(uint32_t));
+  for (uint32_t t = 0; t < n_tris; ++t) {
+    uint32_t o = tri_object[t];
+    s->obj_tris[s->obj_first[o] + fill[o]++] = t;
+  }
+  free(fill);
+  s->moved = (uint8_t*)calloc(n_objects ? n_objects : 1, 1);
+  s->moved_list = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n_objects ? n_objects : 1));
+  s->box = (double*)malloc(sizeof(double) * 12 * (size_t)(n_objects ? n_objects : 1));
+  return s;
+}
+
+void or_scene_destroy(or_scene* s) {
+  if (!s) return;
+  free(s->verts); free(s->tri_object); free(s->dyn); free(s->albedo);
+  free(s->world[0]); free(s->world[1]);
+  free(s->obj_first); free(s->obj_tris); free(s->moved); free(s->moved_list); free(s->box);
+  free(s);
+}
+
+/* World triangles at a pose: static objects as given, dynamic ones through
+ * their 3x4 transform [R|t] (row-major), in double precision. */
+static void pose_world(or_scene* s, const float* xf, double* W) {
+  for (uint32_t t = 0; t < s->n_tris; ++t) {
+    uint32_t o = s->tri_object[t];
+    const float* v = s->verts + 9 * (size_t)t;
+    double* w = W + 12 * (size_t)t;
+    for (int k = 0; k < 3; ++k) {
+      if (s->dyn[o]) {
+        const float* m = xf + 12 * (size_t)o;
+        for (int r = 0; r < 3; ++r)
+          w[3 * k + r] = (double)m[4 * r + 0] * v[3 * k + 0] + (double)m[4 * r + 1] * v[3 * k + 1] +
+                         (double)m[4 * r + 2] * v[3 * k + 2] + (double)m[4 * r + 3];
+      } else {
+        w[3 * k + 0] = v[3 * k + 0];
+        w[3 * k + 1] = v[3 * k + 1];
+        w[3 * k + 2] = v[3 * k + 2];
+      }
+    }
+    double e1[3], e2[3];
+    sub3(w + 3, w, e1);
+    sub3(w + 6, w, e2);
+    cross3(e1, e2, w + 9);
+  }
+}
+
+void or_scene_set_poses(or_scene* s, const float* xform_old, const float* xform_new,
+                        const or_light* lights_old, const or_light* lights_new, uint32_t n_lights) {
+  pose_world(s, xform_old, s->world[0]);
+  pose_world(s, xform_new, s->world[1]);
+  s->n_moved = 0;
+  for (uint32_t o = 0; o < s->n_objects; ++o) {
+    s->moved[o] = s->dyn[o] && memcmp(xform_old + 12 * (size_t)o, xform_new + 12 * (size_t)o, 12 * sizeof(float)) != 0;
+    if (s->moved[o]) s->moved_list[s->n_moved++] = o;
+    for (int p = 0; p < 2; ++p) {
+      double* b = s->box + 12 * (size_t)o + 6 * p;
+      b[0] = b[1] = b[2] = INFINITY;
+      b[3] = b[4] = b[5] = -INFINITY;
+      for (uint32_t k = s->obj_first[o]; k < s->obj_first[o + 1]; ++k) {
+        const double* w = s->world[p] + 12 * (size_t)s->obj_tris[k];
+        for (int v = 0; v < 3; ++v)
+          for (int a = 0; a < 3; ++a) {
+            if (w[3 * v + a] < b[a]) b[a] = w[3 * v + a];
+            if (w[3 * v + a] > b[3 + a]) b[3 + a] = w[3 * v + a];
+          }
+      }
+    }
+  }
+  s->n_lights = n_lights > MAXL ? MAXL : n_lights;
+  s->light_first[0] = 0;
+  for (uint32_t l = 0; l < s->n_lights; ++l) {
+    s->light[0][l] = lights_old[l];
+    s->light[1][l] = lights_new[l];
+    s->light_first[l + 1] = s->light_first[l] + lights_new[l].n_paths;
+    const or_light *a = &lights_old[l], *b = &lights_new[l];
+    s->light_moved[l] = memcmp(a->pos, b->pos, sizeof a->pos) != 0 || memcmp(a->normal, b->normal, sizeof a->normal) != 0 ||
+                        memcmp(a->tangent, b->tangent, sizeof a->tangent) != 0 || memcmp(a->size, b->size, sizeof a->size) != 0;
+    s->light_tilted[l] = memcmp(a->normal, b->normal, sizeof a->normal) != 0;
+  }
+}
+
+static uint32_t light_of(const or_scene* s, uint32_t pid) {
+  for (uint32_t l = 0; l + 1 < s->n_lights; ++l)
+    if (pid < s->light_first[l + 1]) return l;
+  return s->n_lights ? s->n_lights - 1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* ray / triangle with ambiguity                                             */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  double t, epst;
+  int32_t prim;
+  int hit, amb;
+} cand_t;
+
+/* Classify triangle T (v0,v1,v2,n) against the ray o + t d (|d| = 1) for
+ * t in (tlo, thi).  Hit: the ray meets the closed triangle inside the open
+ * range.  Ambiguous: the ray line passes within eps of an edge line
+ * (distance measured between the two lines), or the plane crossing lies
+ * within eps/|cos| of a range end, or the ray runs parallel to the plane
+ * within eps of it.  Returns 0 for a robust miss. */
+static int tri_classify(const double* T, const double* o, const double* d, double tlo, double thi,
+                        double eps, cand_t* c) {
+  const double* n = T + 9;
+  double nn = norm3(n);
+  if (nn == 0.0) return 0;
+  double nd = dot3(n, d);
+  double cosang = nd / nn;
+  double v0o[3];
+  sub3(T, o, v0o);
+  double pd = dot3(n, v0o) / nn;
+  if (fabs(cosang) < 1e-12) {
+    if (fabs(pd) < eps) {
+      c->t = tlo; c->epst = INFINITY; c->hit = 0; c->amb = 1;
+      return 1;
+    }
+    return 0;
+  }
+  double t = pd / cosang;
+  double epst = eps / fabs(cosang);
+  if (t <= tlo - epst || t >= thi + epst) return 0;
+  double sgn = nd > 0.0 ? 1.0 : -1.0;
+  double m = INFINITY;
+  for (int e = 0; e < 3; ++e) {
+    const double* a = T + 3 * e;
+    const double* b = T + 3 * ((e + 1) % 3);
+    double ab[3], cr[3], ao[3];
+    sub3(b, a, ab);
+    cross3(ab, d, cr);
+    double cl = norm3(cr);
+    sub3(a, o, ao);
+    double dist = sgn * dot3(ao, cr) / cl;
+    if (dist < m) m = dist;
+  }
+  if (m <= -eps) return 0;
+  c->t = t;
+  c->epst = epst;
+  c->hit = (m >= 0.0) && t > tlo && t < thi;
+  c->amb = (m < eps) || fabs(t - tlo) < epst || (isfinite(thi) && fabs(t - thi) < epst);
+  return 1;
+}
+
+typedef struct {
+  cand_t* c;
+  size_t n, cap;
+} candvec;
+
+static void cv_push(candvec* v, const cand_t* c) {
+  if (v->n == v->cap) {
+    v->cap = v->cap ? 2 * v->cap : 64;
+    v->c = (cand_t*)realloc(v->c, v->cap * sizeof(cand_t));
+  }
+  v->c[v->n++] = *c;
+}
+
+/* Closest hit over every triangle at pose p, t in (tlo, inf), skipping
+ * primitive ``exclude``.  Ambiguous if the nearest result could change under
+ * the eps perturbation: the nearest hit is itself ambiguous, an ambiguous
+ * triangle lies in front of (or level with) it, or another hit lies within
+ * the combined t tolerance. */
+static int32_t closest_hit(const or_scene* s, int p, const double* o, const double* d, double tlo,
+                           int32_t exclude, double* t_out, int* amb_out) {
+  candvec cv = {0, 0, 0};
+  int32_t best = -1;
+  double best_t = INFINITY;
+  const double* W = s->world[p];
+  for (uint32_t t = 0; t < s->n_tris; ++t) {
+    if ((int32_t)t == exclude) continue;
+    cand_t c;
+    if (!tri_classify(W + 12 * (size_t)t, o, d, tlo, INFINITY, s->eps, &c)) continue;
+    c.prim = (int32_t)t;
+    cv_push(&cv, &c);
+    if (c.hit && c.t < best_t) {
+      best_t = c.t;
+      best = (int32_t)t;
+    }
+  }
+  int amb = 0;
+  double best_eps = 0.0;
+  for (size_t i = 0; i < cv.n; ++i)
+    if (cv.c[i].prim == best) {
+      best_eps = cv.c[i].epst;
+      if (cv.c[i].amb) amb = 1;
+    }
+  for (size_t i = 0; i < cv.n; ++i) {
+    const cand_t* c = &cv.c[i];
+    if (c->prim == best) continue;
+    if (best < 0) {
+      if (c->amb) amb = 1;
+      continue;
+    }
+    if (c->amb && c->t - c->epst < best_t + best_eps) amb = 1;
+    if (c->hit && fabs(c->t - best_t) < c->epst + best_eps) amb = 1;
+  }
+  free(cv.c);
+  *t_out = best_t;
+  *amb_out = amb;
+  return best;
+}
+
+int32_t or_closest_hit(const or_scene* s, const double o[3], const double d[3], double tlo,
+                       int32_t exclude, double* t_out, int32_t* amb) {
+  int a = 0;
+  int32_t r = closest_hit(s, 1, o, d, tlo, exclude, t_out, &a);
+  *amb = a;
+  return r;
+}
+
+/* Any hit of the segment a->b, interior (tmin, len - tmin), against a set of
+ * triangles (all triangles if list == NULL) at pose p.  *amb is set when no
+ * robust hit exists but some triangle is ambiguous. */
+static int any_hit(const or_scene* s, int p, const uint32_t* list, uint32_t count, const double* a,
+                   const double* b, int32_t exclude, int* amb) {
+  double d[3];
+  sub3(b, a, d);
+  double len = norm3(d);
+  *amb = 0;
+  if (!(len > 0.0)) return 0;
+  d[0] /= len; d[1] /= len; d[2] /= len;
+  double thi = len - s->tmin;
+  int any_amb = 0, any = 0;
+  const double* W = s->world[p];
+  uint32_t n = list ? count : s->n_tris;
+  for (uint32_t k = 0; k < n; ++k) {
+    uint32_t t = list ? list[k] : k;
+    if ((int32_t)t == exclude) continue;
+    cand_t c;
+    if (!tri_classify(W + 12 * (size_t)t, a, d, s->tmin, thi, s->eps, &c)) continue;
+    if (c.hit) any = 1;
+    if (c.hit && !c.amb) {
+      *amb = 0;
+      return 1;
+    }
+    if (c.amb) any_amb = 1;
+  }
+  *amb = any_amb;
+  return any;
+}
+
+/* Closed segment a->b against the closed box [lo,hi] (slab test); the result
+ * is ambiguous when the box grown by eps and the box shrunk by eps (never
+ * below zero thickness) disagree. */
+static int seg_box_one(const double* a, const double* b, const double* lo, const double* hi) {
+  double t0 = 0.0, t1 = 1.0;
+  for (int k = 0; k < 3; ++k) {
+    if (lo[k] > hi[k]) return 0;
+    double dk = b[k] - a[k];
+    if (dk == 0.0) {
+      if (a[k] < lo[k] || a[k] > hi[k]) return 0;
+      continue;
+    }
+    double u0 = (lo[k] - a[k]) / dk, u1 = (hi[k] - a[k]) / dk;
+    if (u0 > u1) { double tt = u0; u0 = u1; u1 = tt; }
+    if (u0 > t0) t0 = u0;
+    if (u1 < t1) t1 = u1;
+    if (t0 > t1) return 0;
+  }
+  return 1;
+}
+
+static int seg_box(const double* a, const double* b, const double* box /* lo[3],hi[3] */, double eps, int* amb) {
+  double glo[3], ghi[3], slo[3], shi[3];
+  for (int k = 0; k < 3; ++k) {
+    /* shrinking stops at zero thickness: a flat box stays a flat box */
+    double e = fmin(eps, 0.5 * (box[3 + k] - box[k]));
+    glo[k] = box[k] - eps; ghi[k] = box[3 + k] + eps;
+    slo[k] = box[k] + e; shi[k] = box[3 + k] - e;
+  }
+  int g = seg_box_one(a, b, glo, ghi);
+  int sh = seg_box_one(a, b, slo, shi);
+  int exact = seg_box_one(a, b, box, box + 3);
+  *amb = g != sh;
+  return exact;
+}
+
+/* ------------------------------------------------------------------------ */
+/* sampling (Sec. 3, "generate rays")                                         */
+/* ------------------------------------------------------------------------ */
+static void unit_normal(const or_scene* s, int p, int32_t prim, double n[3]) {
+  const double* w = s->world[p] + 12 * (size_t)prim;
+  n[0] = w[9]; n[1] = w[10]; n[2] = w[11];
+  normalize3(n);
+}
+
+/* Orthonormal basis around unit n (Duff, Burgess, Christensen, Hery, Kensler,
+ * Liani, Villemin, JCGT 2017), with the branch taken on n.z >= 0. */
+static void onb(const double* n, double* b1, double* b2) {
+  double sg = n[2] >= 0.0 ? 1.0 : -1.0;
+  double a = -1.0 / (sg + n[2]);
+  double b = n[0] * n[1] * a;
+  b1[0] = 1.0 + sg * n[0] * n[0] * a; b1[1] = sg * b; b1[2] = -sg * n[0];
+  b2[0] = b; b2[1] = sg + n[1] * n[1] * a; b2[2] = -n[1];
+}
+
+/* Cosine-weighted direction about unit n (Malley's method: uniform disk point
+ * lifted to the hemisphere). */
+static void cosine_dir(const double* n, const double* b1, const double* b2, double u0, double u1, double* d) {
+  double r = sqrt(u0);
+  double ph = 2.0 * M_PI * u1;
+  double x = r * cos(ph), y = r * sin(ph), z = sqrt(fmax(0.0, 1.0 - u0));
+  for (int k = 0; k < 3; ++k) d[k] = x * b1[k] + y * b2[k] + z * n[k];
+  normalize3(d);
+}
+
+/* Emission from light L with uniforms u: point = uniform sphere, rectangle =
+ * uniform position and cosine-weighted direction about its normal. */
+static void emit(const or_light* L, const double* u, double* o, double* d) {
+  if (L->type == 0) {
+    f2d(L->pos, o);
+    double z = 1.0 - 2.0 * u[2];
+    double r = sqrt(fmax(0.0, 1.0 - z * z));
+    double ph = 2.0 * M_PI * u[3];
+    d[0] = r * cos(ph); d[1] = r * sin(ph); d[2] = z;
+    normalize3(d);
+  } else {
+    double c[3], n[3], t[3], b[3];
+    f2d(L->pos, c); f2d(L->normal, n); f2d(L->tangent, t);
+    cross3(n, t, b);
+    double su = (u[0] - 0.5) * L->size[0], sv = (u[1] - 0.5) * L->size[1];
+    for (int k = 0; k < 3; ++k) o[k] = c[k] + su * t[k] + sv * b[k];
+    cosine_dir(n, t, b, u[2], u[3], d);
+  }
+}
+
+/* Facing normal: the geometric normal flipped against the incoming ray. */
+static void facing(const or_scene* s, int p, int32_t prim, const double* d_in, double* ns, int* amb) {
+  double n[3];
+  unit_normal(s, p, prim, n);
+  double c = dot3(n, d_in);
+  if (fabs(c) < 1e-6) *amb = 1;
+  double sg = c < 0.0 ? 1.0 : -1.0;
+  ns[0] = sg * n[0]; ns[1] = sg * n[1]; ns[2] = sg * n[2];
+  if (ns[2] != 0.0 && fabs(ns[2]) < 1e-6) *amb = 1;   /* basis branch near n.z = 0 */
+}
+
+static inline uint32_t info_nseg(uint32_t w) { return (w >> OR_INFO_NSEG_SHIFT) & 15u; }
+static inline uint32_t info_start(uint32_t w) { return (w >> OR_INFO_START_SHIFT) & 15u; }
+static inline uint32_t info_make(uint32_t cell, uint32_t nseg, uint32_t start, int replace, int reuse) {
+  return (cell & OR_INFO_CELL_MASK) | (nseg << OR_INFO_NSEG_SHIFT) | (start << OR_INFO_START_SHIFT) |
+         (replace ? OR_INFO_REPLACE : 0u) | (reuse ? OR_INFO_REUSE_LIGHT : 0u);
+}
+
+/* Extend a path (Fig. 2 "generate rays" / "trace rays" loop): k photons are
+ * stored already.  For k == 0 the first ray (o, d) carrying E is given;
+ * for k >= 1 the path first scatters at photon k (Russian roulette with
+ * q = max albedo, cosine-weighted direction about the facing normal,
+ * E_{k+1} = E_k * albedo / q).  Returns the new photon count. */
+static uint32_t extend_path(const or_scene* s, uint32_t pid, uint64_t seed, uint32_t frame, uint32_t k,
+                            double* o, double* d, double* E, double radius, const float* origin,
+                            or_photon* ph, uint32_t* amb, uint64_t* rays) {
+  int32_t excl = -1;
+  for (;;) {
+    if (k >= 1) {
+      if (k >= s->B) break;
+      or_photon* v = &ph[k - 1];
+      double u[4];
+      rng4(seed, pid, k, frame, u);
+      const float* alb = s->albedo + 3 * (size_t)s->tri_object[v->prim];
+      double q = max3(alb);
+      if (!(u[2] < q)) break;
+      double xin[3], xk[3], din[3];
+      if (k == 1) f2d(origin, xin); else f2d(ph[k - 2].pos, xin);
+      f2d(v->pos, xk);
+      sub3(xk, xin, din);
+      normalize3(din);
+      double ns[3], b1[3], b2[3];
+      int a = 0;
+      facing(s, 1, v->prim, din, ns, &a);
+      if (a) *amb |= OR_AMB_TRACE;
+      onb(ns, b1, b2);
+      cosine_dir(ns, b1, b2, u[0], u[1], d);
+      for (int c = 0; c < 3; ++c) E[c] = (double)v->E[c] * (double)alb[c] / q;
+      f2d(v->pos, o);
+      excl = v->prim;
+      radius = v->radius;
+    }
+    double t;
+    int a = 0;
+    int32_t prim = closest_hit(s, 1, o, d, s->tmin, excl, &t, &a);
+    (*rays)++;
+    if (a) *amb |= OR_AMB_TRACE;
+    if (prim < 0) break;
+    or_photon* v = &ph[k];
+    for (int c = 0; c < 3; ++c) {
+      v->pos[c] = (float)(o[c] + t * d[c]);
+      v->E[c] = (float)E[c];
+    }
+    v->prim = prim;
+    v->radius = (float)(radius + t);
+    ++k;
+  }
+  return k;
+}
+
+void or_trace(const or_scene* s, const uint32_t* ids, uint32_t n, uint64_t seed, uint32_t frame,
+              uint32_t* info, float* origin, or_photon* photons, uint32_t* amb, or_stats* st) {
+  uint64_t rays = 0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : rays)
+  for (uint32_t i = 0; i < n; ++i) {
+    uint32_t pid = ids[i];
+    uint32_t l = light_of(s, pid);
+    const or_light* L = &s->light[1][l];
+    double u[4], o[3], d[3], E[3];
+    rng4(seed, pid, 0, frame, u);
+    emit(L, u, o, d);
+    for (int c = 0; c < 3; ++c) E[c] = (double)L->power[c] / (double)L->n_paths;
+    float* org = origin + 3 * (size_t)i;
+    for (int c = 0; c < 3; ++c) org[c] = (float)o[c];
+    f2d(org, o);
+    amb[i] = 0;
+    uint64_t r = 0;
+    uint32_t k = extend_path(s, pid, seed, frame, 0, o, d, E, 0.0, org, photons + (size_t)i * s->B, &amb[i], &r);
+    rays += r;
+    info[i] = info_make(l << 20, k, 0, 0, 0);
+  }
+  if (st) {
+    st->paths += n;
+    st->trace_rays += rays;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* verification                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. 2 per channel: -T*E_O <= E_N - E_O <= T*E_O.  *near is set on a
+ * near-tie (| |E_N - E_O| - T*E_O | <= 1e-6 E_O). */
+static int energy_close(const double* EN, const float* EOf, double tau, int* near) {
+  int ok = 1;
+  for (int c = 0; c < 3; ++c) {
+    double EO = EOf[c];
+    double diff = EN[c] - EO;
+    if (EO == 0.0) {
+      if (EN[c] != 0.0) ok = 0;
+      continue;
+    }
+    double lim = tau * EO;
+    if (!(-lim <= diff && diff <= lim)) ok = 0;
+    if (fabs(fabs(diff) - lim) <= 1e-6 * EO) *near = 1;
+  }
+  return ok;
+}
+
+static int obj_moved(const or_scene* s, int32_t prim) { return prim >= 0 && s->moved[s->tri_object[prim]]; }
+
+/* Segment a->b against the moved objects (Sec. 3.2): the bounding-box test
+ * (naive mode, and the error-based mode of Sec. 3.3 whose skip case exists
+ * because of it) uses the union of the old and new bounding boxes of each
+ * moved object; the exact test (naive-exact mode, or error mode with
+ * OR_FLAG_ERROR_EXACT) tests the open segment against the moved objects'
+ * triangles at the new pose (and the old pose with OR_FLAG_TEST_OLD_TRIS). */
+static int seg_vs_moved(const or_scene* s, int mode, uint32_t flags, const double* a, const double* b, int* amb) {
+  int any = 0, any_amb = 0;
+  for (uint32_t m = 0; m < s->n_moved; ++m) {
+    uint32_t o = s->moved_list[m];
+    int am = 0, hit;
+    if (mode == OR_MODE_NAIVE_AABB || (mode == OR_MODE_ERROR && !(flags & OR_FLAG_ERROR_EXACT))) {
+      const double* bo = s->box + 12 * (size_t)o;
+      double u[6];
+      for (int k = 0; k < 3; ++k) {
+        u[k] = fmin(bo[k], bo[6 + k]);
+        u[3 + k] = fmax(bo[3 + k], bo[9 + k]);
+      }
+      hit = seg_box(a, b, u, s->eps, &am);
+    } else {
+      const uint32_t* lst = s->obj_tris + s->obj_first[o];
+      uint32_t cnt = s->obj_first[o + 1] - s->obj_first[o];
+      hit = any_hit(s, 1, lst, cnt, a, b, -1, &am);
+      if (!(hit && !am) && (flags & OR_FLAG_TEST_OLD_TRIS)) {
+        int am2 = 0;
+        int h2 = any_hit(s, 0, lst, cnt, a, b, -1, &am2);
+        if (h2 && !am2) {
+          hit = 1;
+          am = 0;
+        } else {
+          hit = hit || h2;
+          am = am || am2;
+        }
+      }
+    }
+    if (hit && !am) {
+      *amb = 0;
+      return 1;
+    }
+    if (hit) any = 1;
+    if (am) any_amb = 1;
+  }
+  *amb = any_amb;
+  return any;
+}
+
+void or_verify(const or_scene* s, const uint32_t* ids, uint32_t n, int32_t mode, double tau,
+               uint32_t flags, uint32_t* info, float* origin, or_photon* photons, uint32_t* seg_mask,
+               uint32_t* ambv, or_stats* st) {
+  uint64_t seg_t = 0, seg_a = 0, vis = 0, cont = 0, et = 0, ea = 0, nre = 0, ntail = 0, nupd = 0, ntr = 0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : seg_t, seg_a, vis, cont, et, ea, nre, ntail, nupd, ntr)
+  for (uint32_t i = 0; i < n; ++i) {
+    uint32_t pid = ids[i];
+    uint32_t w = info[i];
+    uint32_t cell = w & OR_INFO_CELL_MASK;
+    uint32_t L = info_nseg(w);
+    uint32_t l = light_of(s, pid);
+    or_photon* ph = photons + (size_t)i * s->B;
+    float* org = origin + 3 * (size_t)i;
+    uint32_t amb = 0;
+    int seg1_blocked = 0;
+    seg_mask[i] = 0;
+
+    /* ---- Sec. 3.1 "update path origins" ---- */
+    if (s->light_moved[l]) {
+      const or_light* Ln = &s->light[1][l];
+      const or_light* Lo = &s->light[0][l];
+      int invalid = 0;
+      if (L == 0) {
+        invalid = 1;          /* an escaped path has no vertex to re-aim at */
+      } else if (Ln->type == 0) {
+        for (int c = 0; c < 3; ++c) org[c] = Ln->pos[c];
+        double a[3], b[3];
+        f2d(org, a);
+        f2d(ph[0].pos, b);
+        int am = 0;
+        seg1_blocked = any_hit(s, 1, NULL, 0, a, b, ph[0].prim, &am);
+        vis++;
+        if (am) amb |= OR_AMB_VERIFY;
+      } else {
+        double x1[3], o0[3], d[3], c[3], nn[3], tt[3], bb[3], no[3];
+        f2d(ph[0].pos, x1);
+        f2d(org, o0);
+        sub3(x1, o0, d);
+        normalize3(d);
+        f2d(Ln->pos, c); f2d(Ln->normal, nn); f2d(Ln->tangent, tt);
+        cross3(nn, tt, bb);
+        double ndv = dot3(nn, d);
+        if (fabs(ndv) < 1e-6) amb |= OR_AMB_LIGHT;
+        if (!(ndv > 0.0)) {
+          invalid = 1;
+        } else {
+          double x1c[3];
+          sub3(x1, c, x1c);
+          double tp = dot3(nn, x1c) / ndv;
+          if (fabs(tp) < s->eps) amb |= OR_AMB_LIGHT;
+          if (!(tp > 0.0)) {
+            invalid = 1;
+          } else {
+            double op[3], rel[3];
+            for (int k = 0; k < 3; ++k) op[k] = x1[k] - tp * d[k];
+            sub3(op, c, rel);
+            double su = dot3(tt, rel), sv = dot3(bb, rel);
+            double hw = 0.5 * Ln->size[0], hh = 0.5 * Ln->size[1];
+            if (fabs(fabs(su) - hw) < s->eps || fabs(fabs(sv) - hh) < s->eps) amb |= OR_AMB_LIGHT;
+            if (fabs(su) > hw || fabs(sv) > hh) invalid = 1;
+            if (!invalid && s->light_tilted[l]) {
+              f2d(Lo->normal, no);
+              double ratio = ndv / dot3(no, d);
+              double EN[3];
+              for (int k = 0; k < 3; ++k) EN[k] = (double)ph[0].E[k] * ratio;
+              int near = 0;
+              et++;
+              if (!energy_close(EN, ph[0].E, tau, &near)) invalid = 1;
+              if (near) { ea++; amb |= OR_AMB_ENERGY; }
+            }
+            for (int k = 0; k < 3; ++k) org[k] = (float)op[k];
+          }
+        }
+      }
+      if (invalid) {
+        info[i] = info_make(cell, 0, 0, 1, 0);
+        nre++;
+        ambv[i] = amb;
+        continue;
+      }
+    }
+
+    /* ---- Sec. 3.2 "dynamic occlusions": segments in order from the light ---- */
+    uint32_t mask = 0;
+    for (uint32_t k = 1; k <= L; ++k) {
+      double a[3], b[3];
+      if (k == 1) f2d(org, a); else f2d(ph[k - 2].pos, a);
+      f2d(ph[k - 1].pos, b);
+      int hit = obj_moved(s, ph[k - 1].prim) || (k >= 2 && obj_moved(s, ph[k - 2].prim)) || (k == 1 && seg1_blocked);
+      if (!hit) {
+        int am = 0;
+        hit = seg_vs_moved(s, mode, flags, a, b, &am);
+        seg_t++;
+        if (am) { seg_a++; amb |= OR_AMB_VERIFY; }
+      }
+      if (hit) {
+        mask |= 1u << k;
+        if (mode != OR_MODE_ERROR) break;
+      }
+    }
+    seg_mask[i] = mask;
+    if (!mask) {
+      ambv[i] = amb;
+      continue;
+    }
+    uint32_t first = 0;
+    while (!((mask >> first) & 1u)) ++first;
+
+    if (mode != OR_MODE_ERROR) {
+      if (first == 1) {
+        info[i] = info_make(cell, 0, 0, 1, 1);   /* keep light position and direction */
+        nre++;
+      } else {
+        info[i] = info_make(cell, first - 1, first - 1, 1, 0);
+        ntail++;
+      }
+      ambv[i] = amb;
+      continue;
+    }
+
+    /* ---- Sec. 3.3, Alg. 1: error-based threshold continuation ---- */
+    double xo[16][3];      /* original vertex positions, 0 = origin */
+    int32_t po[16];
+    f2d(org, xo[0]);
+    po[0] = -1;
+    for (uint32_t k = 1; k <= L; ++k) { f2d(ph[k - 1].pos, xo[k]); po[k] = ph[k - 1].prim; }
+    uint32_t moved_origin = 0;
+    int updated = 0, done = 0;
+    uint32_t seg = first;
+    while (seg <= L && !done) {
+      if (!((mask >> seg) & 1u) && !((moved_origin >> seg) & 1u)) { ++seg; continue; }
+      double a[3], b[3], d[3];
+      if (seg == 1) f2d(org, a); else f2d(ph[seg - 2].pos, a);
+      f2d(ph[seg - 1].pos, b);
+      sub3(b, a, d);
+      normalize3(d);
+      int32_t excl = seg == 1 ? -1 : ph[seg - 2].prim;
+      double t;
+      int am = 0;
+      int32_t pn = closest_hit(s, 1, a, d, s->tmin, excl, &t, &am);
+      cont++;
+      if (am) amb |= OR_AMB_CONT;
+      if (pn < 0) {                       /* nothing hit: the path ends here */
+        L = seg - 1;
+        ntr++;
+        done = 1;
+        break;
+      }
+      float xn[3];
+      double xnd[3];
+      for (int c = 0; c < 3; ++c) { xn[c] = (float)(a[c] + t * d[c]); xnd[c] = xn[c]; }
+      double dx = 0.0;
+      for (int c = 0; c < 3; ++c) dx = fmax(dx, fabs(xnd[c] - b[c]));
+      int close = pn == ph[seg - 1].prim && dx <= s->close_tol;
+      if (pn == ph[seg - 1].prim && fabs(dx - s->close_tol) < s->eps) amb |= OR_AMB_CONT;
+      if (seg == L) {                     /* last photon: move it, nothing follows */
+        for (int c = 0; c < 3; ++c) ph[seg - 1].pos[c] = xn[c];
+        ph[seg - 1].prim = pn;
+        updated = 1;
+        done = 1;
+        break;
+      }
+      double EN[3];
+      const float* EO = ph[seg].E;
+      if (close) {
+        for (int c = 0; c < 3; ++c) EN[c] = EO[c];
+      } else {
+        /* new vertex: albedo, facing normal, direction to the stored next photon */
+        const float* albn = s->albedo + 3 * (size_t)s->tri_object[pn];
+        double nsn[3], w[3], xnext[3];
+        int af = 0;
+        facing(s, 1, pn, d, nsn, &af);
+        f2d(ph[seg].pos, xnext);
+        sub3(xnext, xnd, w);
+        double wl = norm3(w);
+        double cosn = 0.0;
+        if (wl > 0.0) {
+          w[0] /= wl; w[1] /= wl; w[2] /= wl;
+          cosn = fmax(0.0, dot3(nsn, w));
+        }
+        /* old vertex (old pose): RR probability, facing normal, sampled direction */
+        const float* albo = s->albedo + 3 * (size_t)s->tri_object[po[seg]];
+        double q = max3(albo);
+        double dino[3], nso[3], wo[3];
+        sub3(xo[seg], xo[seg - 1], dino);
+        normalize3(dino);
+        int af2 = 0;
+        facing(s, 0, po[seg], dino, nso, &af2);
+        if (af || af2) amb |= OR_AMB_CONT;
+        sub3(xo[seg + 1], xo[seg], wo);
+        normalize3(wo);
+        double coso = dot3(nso, wo);
+        for (int c = 0; c < 3; ++c)
+          EN[c] = coso > 0.0 ? (double)ph[seg - 1].E[c] * (double)albn[c] * cosn / (q * coso) : 0.0;
+      }
+      int near = 0;
+      et++;
+      int pass = energy_close(EN, EO, tau, &near);
+      if (near && !close) { ea++; amb |= OR_AMB_ENERGY; }
+      if (!pass) {                        /* re-trace from the new vertex */
+        for (int c = 0; c < 3; ++c) ph[seg - 1].pos[c] = xn[c];
+        ph[seg - 1].prim = pn;
+        info[i] = info_make(cell, seg, seg, 1, 0);
+        ntail++;
+        done = 2;
+        break;
+      }
+      if (close && !((mask >> (seg + 1)) & 1u) && !obj_moved(s, pn) && !obj_moved(s, ph[seg].prim)) {
+        seg += 2;                         /* next segment known valid: skip its check */
+        continue;
+      }
+      for (int c = 0; c < 3; ++c) ph[seg - 1].pos[c] = xn[c];
+      ph[seg - 1].prim = pn;
+      updated = 1;
+      moved_origin |= 1u << (seg + 1);
+      ++seg;
+    }
+    if (done != 2) {
+      info[i] = info_make(cell, L, 0, 0, 0);
+      if (updated) nupd++;
+    }
+    ambv[i] = amb;
+  }
+  if (st) {
+    st->paths += n;
+    st->segments_tested += seg_t;
+    st->segments_amb += seg_a;
+    st->vis_rays += vis;
+    st->cont_rays += cont;
+    st->energy_tests += et;
+    st->energy_amb += ea;
+    st->n_reemit += nre;
+    st->n_tail += ntail;
+    st->n_updated += nupd;
+    st->n_truncated += ntr;
+  }
+}
+
+uint32_t or_compact(const uint32_t* info, uint32_t n, uint32_t* list) {
+  uint32_t c = 0;
+  for (uint32_t i = 0; i < n; ++i)
+    if (info[i] & OR_INFO_REPLACE) list[c++] = i;
+  return c;
+}
+
+void or_retrace(const or_scene* s, const uint32_t* ids, uint32_t n, uint64_t seed, uint32_t frame,
+                uint32_t* info, float* origin, or_photon* photons, uint32_t* ambv, or_stats* st) {
+  uint64_t rays = 0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : rays)
+  for (uint32_t i = 0; i < n; ++i) {
+    uint32_t w = info[i];
+    if (!(w & OR_INFO_REPLACE)) continue;
+    uint32_t pid = ids[i];
+    uint32_t l = light_of(s, pid);
+    const or_light* L = &s->light[1][l];
+    uint32_t start = info_start(w);
+    or_photon* ph = photons + (size_t)i * s->B;
+    float* org = origin + 3 * (size_t)i;
+    double o[3], d[3], E[3];
+    uint32_t k;
+    uint64_t r = 0;
+    if (start == 0) {
+      if (w & OR_INFO_REUSE_LIGHT) {
+        double x1[3];
+        f2d(org, o);
+        f2d(ph[0].pos, x1);
+        sub3(x1, o, d);
+        normalize3(d);
+        for (int c = 0; c < 3; ++c) E[c] = ph[0].E[c];
+      } else {
+        double u[4];
+        rng4(seed, pid, 0, frame, u);
+        emit(L, u, o, d);
+        for (int c = 0; c < 3; ++c) org[c] = (float)o[c];
+        f2d(org, o);
+        for (int c = 0; c < 3; ++c) E[c] = (double)L->power[c] / (double)L->n_paths;
+      }
+      k = extend_path(s, pid, seed, frame, 0, o, d, E, 0.0, org, ph, &ambv[i], &r);
+    } else {
+      k = extend_path(s, pid, seed, frame, start, o, d, E, 0.0, org, ph, &ambv[i], &r);
+    }
+    rays += r;
+    info[i] = info_make(w & OR_INFO_CELL_MASK, k, 0, 0, 0);
+  }
+  if (st) st->trace_rays += rays;
+}
+
+/* ------------------------------------------------------------------------ */
+/* deposit                                                                   */
+/* ------------------------------------------------------------------------ */
+/* Texel of a position in the top-down XZ atlas, decided in float32 with no
+ * fused operations (the oracle is compiled with -ffp-contract=off). */
+static inline int texel(float p, float lo, float hi, uint32_t res) {
+  float scale = (float)res / (hi - lo);
+  float u = (p - lo) * scale;
+  float f = floorf(u);
+  int i;
+  if (!(f >= 0.0f)) i = 0;
+  else if (f >= (float)res) i = (int)res - 1;
+  else i = (int)f;
+  return i;
+}
+
+void or_deposit(const uint32_t* info, uint32_t n, const or_photon* photons, uint32_t max_bounces,
+                uint32_t width, uint32_t height, float x0, float z0, float x1, float z1, double* atlas) {
+  for (uint32_t i = 0; i < n; ++i) {
+    uint32_t L = info_nseg(info[i]);
+    for (uint32_t k = 0; k < L; ++k) {
+      const or_photon* v = &photons[(size_t)i * max_bounces + k];
+      int tx = texel(v->pos[0], x0, x1, width);
+      int tz = texel(v->pos[2], z0, z1, height);
+      double* a = atlas + 3 * ((size_t)tz * width + tx);
+      a[0] += v->E[0];
+      a[1] += v->E[1];
+      a[2] += v->E[2];
+    }
+  }
+}
+
+int32_t or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

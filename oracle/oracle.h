@@ -1,0 +1,155 @@
+/*
+ * FP64 brute-force CPU oracle for per-frame photon-path verification
+ * (Moreau, Doggett, Sintorn, "Path Verification for Dynamic Indirect
+ * Illumination", arXiv 2111.06906).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or constant with the CUDA library; both sides receive the
+ * same seeded scene arrays and each implements the Philox-4x32-10 counter
+ * generator (Salmon et al., SC 2011) from its published definition.
+ *
+ * Every geometric query tests every triangle (no acceleration structure) in
+ * double precision.  Path records are stored as FP32 (the method's storage
+ * format, Sec. 4) and every step continues from the stored FP32 record.
+ *
+ * Alongside each result the oracle reports whether the result is ambiguous:
+ * whether a perturbation of 1e-6 x scene diagonal (edge/plane proximity), a
+ * near-tie in Eq. 2 or in the AreClose test of Alg. 1 could flip a decision.
+ * Such paths are excluded from bit-exact comparison and counted.
+ */
+#ifndef PV_ORACLE_H
+#define PV_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A light pose (64 bytes): type 0 = isotropic point, 1 = rectangle emitting
+ * on the side of ``normal``; ``size[0]`` runs along ``tangent`` and
+ * ``size[1]`` along normal x tangent.  Paths are assigned to lights in order:
+ * light 0 owns path ids [0, n0), light 1 the next n1 ids, ... */
+typedef struct {
+  int32_t type;
+  float pos[3], normal[3], tangent[3], size[2], power[3];
+  uint32_t n_paths;
+} or_light;
+
+/* One stored photon (32 bytes, Sec. 4): hit position (see the reading of the
+ * record in the design notes), hit primitive id, incident RGB energy, and the
+ * path length travelled from the light ("radius" slot). */
+typedef struct {
+  float pos[3];
+  int32_t prim;
+  float E[3];
+  float radius;
+} or_photon;
+
+/* Info word bit fields (Sec. 4): DM cell (22 bits; light index << 20),
+ * number of segments (4), retrace start vertex (4), replace (1), reuse light
+ * position and direction (1). */
+#define OR_INFO_CELL_MASK 0x003FFFFFu
+#define OR_INFO_NSEG_SHIFT 22
+#define OR_INFO_START_SHIFT 26
+#define OR_INFO_REPLACE (1u << 30)
+#define OR_INFO_REUSE_LIGHT (1u << 31)
+
+/* verification modes */
+#define OR_MODE_NAIVE_AABB 0
+#define OR_MODE_NAIVE_EXACT 1
+#define OR_MODE_ERROR 2
+#define OR_FLAG_TEST_OLD_TRIS 1u
+#define OR_FLAG_ERROR_EXACT 2u   /* error mode: exact triangle test instead of boxes */
+
+/* ambiguity bits reported per path */
+#define OR_AMB_TRACE 1u
+#define OR_AMB_VERIFY 2u
+#define OR_AMB_CONT 4u
+#define OR_AMB_ENERGY 8u
+#define OR_AMB_LIGHT 16u
+
+typedef struct or_scene or_scene;
+
+/* per-call counters (summed over the paths processed) */
+typedef struct {
+  uint64_t paths;            /* paths processed */
+  uint64_t segments_tested;  /* segment-vs-object tests made */
+  uint64_t segments_amb;     /* of which ambiguous */
+  uint64_t vis_rays;         /* point-light visibility rays (Sec. 3.1) */
+  uint64_t cont_rays;        /* closest-hit rays of Alg. 1 */
+  uint64_t trace_rays;       /* closest-hit rays of tracing / re-tracing */
+  uint64_t energy_tests;     /* Eq. 2 evaluations */
+  uint64_t energy_amb;       /* Eq. 2 near-ties */
+  uint64_t n_reemit;         /* paths to re-emit from the light (start 0) */
+  uint64_t n_tail;           /* paths to re-trace from a vertex > 0 */
+  uint64_t n_updated;        /* paths reused with moved vertices (Alg. 1) */
+  uint64_t n_truncated;      /* paths shortened because a re-traced ray missed */
+} or_stats;
+
+/* Scene: verts [n_tris][3][3] (object-local for dynamic objects),
+ * tri_object [n_tris], object_dynamic [n_objects], albedo [n_objects][3].
+ * diag is the scene diagonal; eps = 1e-6 diag and t_min = 1e-5 diag. */
+or_scene* or_scene_create(const float* verts, uint32_t n_tris, const uint32_t* tri_object,
+                          uint32_t n_objects, const uint8_t* object_dynamic,
+                          const float* albedo, double diag, uint32_t max_bounces);
+void or_scene_destroy(or_scene* s);
+
+/* Set the previous (old) and current (new) poses: xforms [n_objects][12]
+ * row-major 3x4, lights [n_lights].  An object or light "moved" iff any of
+ * its float32 pose values differ bit for bit. */
+void or_scene_set_poses(or_scene* s, const float* xform_old, const float* xform_new,
+                        const or_light* lights_old, const or_light* lights_new,
+                        uint32_t n_lights);
+
+/* Philox-4x32-10 block: out[4] = philox(ctr[4], key[2]). */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Paths are processed for a subset of ids; every per-path array below is
+ * indexed by position in ``ids`` (n entries): info[n], origin[n][3],
+ * photons[n][B], amb[n].  */
+
+/* Trace every listed path from scratch at the current pose (emission +
+ * bounces, Sec. 3 / Fig. 2 "generate rays" and "trace rays"). */
+void or_trace(const or_scene* s, const uint32_t* ids, uint32_t n, uint64_t seed,
+              uint32_t frame, uint32_t* info, float* origin, or_photon* photons,
+              uint32_t* amb, or_stats* st);
+
+/* Verify the listed paths against the pose change: update origins
+ * (Sec. 3.1), dynamic occlusions (Sec. 3.2) and, in OR_MODE_ERROR, the
+ * error-based threshold continuation (Sec. 3.3, Alg. 1, Eq. 2).  Sets the
+ * replace / start / reuse-light bits, updates origins and moved vertices in
+ * place, and returns the intersected-segment mask (bit i = segment i). */
+void or_verify(const or_scene* s, const uint32_t* ids, uint32_t n, int32_t mode, double tau,
+               uint32_t flags, uint32_t* info, float* origin, or_photon* photons,
+               uint32_t* seg_mask, uint32_t* amb, or_stats* st);
+
+/* Ascending list of the positions (into ids) whose replace bit is set;
+ * returns the count (Sec. 5.2, pruned-paths array pattern). */
+uint32_t or_compact(const uint32_t* info, uint32_t n, uint32_t* list);
+
+/* Re-trace every listed path whose replace bit is set, from its start
+ * vertex, at the current pose with the frame's random numbers. */
+void or_retrace(const or_scene* s, const uint32_t* ids, uint32_t n, uint64_t seed,
+                uint32_t frame, uint32_t* info, float* origin, or_photon* photons,
+                uint32_t* amb, or_stats* st);
+
+/* Deposit every stored photon's incident energy into a width x height
+ * top-down XZ atlas over [x0,x1] x [z0,z1]; atlas is [height][width][3]
+ * (accumulated, not cleared).  The texel index is computed in float32. */
+void or_deposit(const uint32_t* info, uint32_t n, const or_photon* photons, uint32_t max_bounces,
+                uint32_t width, uint32_t height, float x0, float z0, float x1, float z1,
+                double* atlas);
+
+/* Closest hit of one ray against the current pose (test helper): returns the
+ * prim id or -1, writes the distance, ambiguity flag. */
+int32_t or_closest_hit(const or_scene* s, const double o[3], const double d[3], double tlo,
+                       int32_t exclude, double* t_out, int32_t* amb);
+
+/* Number of OpenMP threads the oracle uses. */
+int32_t or_num_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
