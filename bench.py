@@ -1,0 +1,430 @@
+#!/usr/bin/env python
+"""Benchmark of the per-frame path-verification hot path on one GB300.
+
+One step = one frame of the reuse pipeline on the seeded city workload
+(200k static triangles, 4 moving tori, a 1x1 m area light translating
+0.1 m/frame, 1M photon paths of up to 7 bounces, error-based mode with
+tau = 1 %):  pv_update_dynamic -> pv_verify_paths (origin update, dynamic
+occlusions, Alg. 1 continuation, compaction) -> pv_retrace_invalid ->
+pv_deposit.  The same library's trace-all frame (pv_update_dynamic ->
+pv_trace_all -> pv_deposit) is timed beside it.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "photon paths verified+reused+retraced/s and frame ms vs trace-all on 1 GB300"
+MODES = {"naive_aabb": 0, "naive_exact": 1, "error": 2}
+WORKLOADS = {
+    "city": "procedural city: 100x100 m floor, 16666 random boxes (200k static tris), 4 tori of 2048 tris on "
+            "sinusoidal paths (2 m amplitude), 1x1 m area light translating 0.1 m/frame; 1M paths, <=7 bounces",
+    "villa": "villa-shaped interior: 4x3 rooms, 2M static tris (30% clutter), 10 yawing tori of 5000 tris, "
+             "point light + static area light + moving tilting torch; 3M paths, <=7 bounces",
+    "tiny_box": "open 2x2x2 box (10 tris) + moving unit cube (12 tris), point light; 10k paths, <=3 bounces",
+}
+OPS_PER_NODE = 38     # FP32-pipe ops per BVH node visit (two slab tests), counted from the source
+OPS_PER_TRI = 40      # FP32-pipe ops per Moller-Trumbore test, counted from the source
+SM_COUNT, FP32_LANES = 152, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="city", choices=list(WORKLOADS))
+    ap.add_argument("--mode", default="error", choices=list(MODES))
+    ap.add_argument("--tau", type=float, default=None)
+    ap.add_argument("--atlas", type=int, default=1024)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling (every 200 ms) during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def scene_for(name, rank=0):
+    import scenes
+    return scenes.by_name(name)
+
+
+# ----------------------------------------------------------------------------- ours
+def run_ours(args, ws, rank, local):
+    import torch
+
+    import paper_2111_06906_gb300 as pv
+    from paper_2111_06906_gb300 import build as pvbuild
+    pvbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc = scene_for(args.workload)
+    mode = MODES[args.mode]
+    tau = sc.tau if args.tau is None else args.tau
+    seed = sc.seed + 7919 * rank
+    N, B = sc.n_paths, sc.max_bounces
+    frames_needed = 2 * (args.warmup + args.steps) + 3
+    xfs = {f: sc.xforms(f) for f in range(1, frames_needed + 1)}
+    lts = {f: sc.lights(f) for f in range(1, frames_needed + 1)}
+
+    t0 = time.time()
+    h = pv.pv_build_scene(sc.verts, sc.tri_object, sc.object_dynamic, sc.object_albedo, lts[1], B, sc.diag,
+                          object_xform=xfs[1])
+    build_s = time.time() - t0
+    P = pv.Paths.allocate(N, B, dev)
+    A = args.atlas
+    atlas = torch.zeros(A, A, 3, dtype=torch.int64, device=dev)
+    scale = 40 if args.workload != "tiny_box" else 31
+    lst = torch.zeros(N, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    K, W = args.steps, args.warmup
+    stats = torch.zeros(4 * K + 2, pv.STATS_WORDS, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    pv.pv_trace_all(h, P, seed, 1)
+    frame = 1
+
+    def reuse_frame(f, st):
+        pv.pv_update_dynamic(h, xfs[f], lts[f])
+        pv.pv_verify_paths(h, P, mode, tau, 0, lst, cnt, st)
+        pv.pv_retrace_invalid(h, P, lst, cnt, seed, f, st)
+        pv.pv_deposit(h, P, atlas, sc.atlas_rect, scale)
+
+    def timed_loop(fn, first_frame, rows_a, rows_b):
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+        for i in range(K):
+            f = first_frame + i
+            e = ev[i]
+            e[0].record(stream)
+            pv.pv_update_dynamic(h, xfs[f], lts[f])
+            e[1].record(stream)
+            fn(f, rows_a[i], rows_b[i], e)
+            e[4].record(stream)
+        return ev
+
+    def reuse_body(f, st_v, st_r, e):
+        pv.pv_verify_paths(h, P, mode, tau, 0, lst, cnt, st_v)
+        e[2].record(stream)
+        pv.pv_retrace_invalid(h, P, lst, cnt, seed, f, st_r)
+        e[3].record(stream)
+        pv.pv_deposit(h, P, atlas, sc.atlas_rect, scale)
+
+    def trace_body(f, st_v, st_r, e):
+        e[2].record(stream)
+        pv.pv_trace_all(h, P, seed, f, st_r)
+        e[3].record(stream)
+        pv.pv_deposit(h, P, atlas, sc.atlas_rect, scale)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- reuse pipeline
+    for i in range(W):
+        frame += 1
+        reuse_frame(frame, stats[-1])
+    barrier()
+    clocks = Clocks(local)
+    with clocks:
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        ev = timed_loop(reuse_body, frame + 1, stats[:K], stats[K:2 * K])
+        stop.record(stream)
+        barrier()
+    frame += K
+    reuse_ms = start.elapsed_time(stop) / K
+    parts = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in ev])
+    reuse_parts = parts.mean(axis=0)
+    st_verify = [pv.stats_dict(stats[i]) for i in range(K)]
+    st_retrace = [pv.stats_dict(stats[K + i]) for i in range(K)]
+    st_reuse = [{k: a[k] + b[k] for k in a} for a, b in zip(st_verify, st_retrace)]
+    info_np = P.info.cpu().numpy().view(np.uint32)
+    mean_L = float(((info_np >> 22) & 15).mean())
+    status = pv.pv_read_device_status(h)
+
+    # ---- trace-all baseline (same library, same GPU)
+    for i in range(W):
+        frame += 1
+        pv.pv_update_dynamic(h, xfs[frame], lts[frame])
+        pv.pv_trace_all(h, P, seed, frame, stats[-1])
+        pv.pv_deposit(h, P, atlas, sc.atlas_rect, scale)
+    barrier()
+    start2 = torch.cuda.Event(enable_timing=True)
+    stop2 = torch.cuda.Event(enable_timing=True)
+    start2.record(stream)
+    ev2 = timed_loop(trace_body, frame + 1, stats[2 * K:3 * K], stats[3 * K:4 * K])
+    stop2.record(stream)
+    barrier()
+    frame += K
+    trace_ms = start2.elapsed_time(stop2) / K
+    parts2 = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in ev2]).mean(axis=0)
+    st_trace = [pv.stats_dict(stats[3 * K + i]) for i in range(K)]
+
+    # ---- end to end through the API: host poses in, atlas and stats out (pinned), every frame
+    e2e = None
+    if not args.no_e2e:
+        host_atlas = torch.empty(A, A, 3, dtype=torch.int64, pin_memory=True)
+        host_stats = torch.empty(pv.STATS_WORDS, dtype=torch.int32, pin_memory=True)
+        # continue the reuse pipeline from a fresh bootstrap
+        pv.pv_trace_all(h, P, seed, frame)
+        for i in range(W):
+            frame += 1
+            reuse_frame(frame, stats[-2])
+            host_atlas.copy_(atlas, non_blocking=True)
+            host_stats.copy_(stats[-2], non_blocking=True)
+            stream.synchronize()
+        barrier()
+        t = time.perf_counter()
+        for i in range(K):
+            frame += 1
+            reuse_frame(frame, stats[-2])
+            host_atlas.copy_(atlas, non_blocking=True)
+            host_stats.copy_(stats[-2], non_blocking=True)
+            stream.synchronize()
+        e2e_s = (time.perf_counter() - t) / K
+        h2d = 12 * 4 * int(sc.object_dynamic.sum()) + 64 * len(lts[1])
+        e2e = {"value": None, "unit": "paths/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": int(host_atlas.numel() * 8 + host_stats.numel() * 4), "_s": e2e_s}
+    status2 = pv.pv_read_device_status(h)
+    pv.pv_destroy_scene(h)
+
+    # ---- max over ranks
+    vals = torch.tensor([reuse_ms, trace_ms, e2e["_s"] if e2e else 0.0], dtype=torch.float64, device=dev)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    reuse_ms, trace_ms, e2e_s = vals.tolist()
+    if rank != 0:
+        return
+
+    pk, pk_kind = peaks()
+    names = ["update", "verify", "retrace", "deposit"]
+    dom = int(np.argmax(reuse_parts))
+    agg = lambda key, rows: float(np.mean([r[key] for r in rows]))
+    roof = None
+    if names[dom] == "retrace":
+        ops = OPS_PER_NODE * agg("node_visits", st_retrace) + OPS_PER_TRI * agg("tri_tests", st_retrace)
+        ops_peak = SM_COUNT * FP32_LANES * pk.get("sm_max_mhz", 2070.0) * 1e6
+        achieved = ops / (reuse_parts[2] * 1e-3)
+        roof = {"kernel": "k_trace (pv_retrace_invalid)", "bound": "alu", "achieved": achieved / 1e12,
+                "peak": ops_peak / 1e12, "unit": "Top/s", "frac": achieved / ops_peak, "traffic": None,
+                "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x max SM clock"}
+    elif names[dom] == "verify":
+        listed = agg("n_listed", st_reuse)
+        byts = N * (4 + 12 + 16 * mean_L) + 4 * N + 4 * listed
+        achieved = byts / (reuse_parts[1] * 1e-3) / 1e9
+        roof = {"kernel": "k_verify+k_continue+k_compact (pv_verify_paths)", "bound": "hbm", "achieved": achieved,
+                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                "peak_kind": pk_kind}
+    else:
+        byts = N * 4 + N * mean_L * 32
+        achieved = byts / (reuse_parts[dom] * 1e-3) / 1e9
+        roof = {"kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_kind": pk_kind}
+    rays_reuse = agg("vis_rays", st_reuse) + agg("cont_rays", st_reuse) + agg("trace_rays", st_reuse)
+    rays_trace = agg("trace_rays", st_trace)
+    value = ws * N / (reuse_ms * 1e-3)
+    cfg = {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "paths": N, "max_bounces": B,
+           "mode": args.mode, "tau": tau, "frames_timed": K,
+           "l2": "inputs larger than L2 (path buffers %.0f MB)" % (N * (4 + 12 + 32 * B) / 1e6),
+           "reuse_ms_per_frame": reuse_ms, "trace_all_ms_per_frame": trace_ms,
+           "speedup_vs_trace_all": trace_ms / reuse_ms,
+           "reuse_ms_parts": dict(zip(names, [float(x) for x in reuse_parts])),
+           "trace_all_ms_parts": dict(zip(names, [float(x) for x in parts2])),
+           "rays_per_frame_reuse": rays_reuse, "rays_per_frame_trace_all": rays_trace,
+           "listed_per_frame": agg("n_listed", st_reuse), "mean_photons_per_path": mean_L,
+           "scene_build_s": build_s, "device_status": [status, status2]}
+    launches_per_frame = 2 + (3 if mode == 2 else 2) + 1 + 1
+    out = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws, "steps": K, "warmup": W,
+           "ms_per_step": reuse_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roof,
+           "gpu_launches": launches_per_frame * K, "clocks": clocks.summary()}
+    if e2e:
+        e2e["value"] = ws * N / e2e_s
+        e2e.pop("_s")
+        out["e2e"] = e2e
+    if not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(args.workload, mode, tau, args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------- oracle
+def _oracle_sample(workload, n_sample, seed_off=0):
+    import oracle
+    sc = scene_for(workload)
+    ids = np.sort(np.random.default_rng(1234 + seed_off).choice(sc.n_paths, n_sample, replace=False)).astype(np.uint32)
+    o = oracle.OracleScene(sc)
+    o.set_frames(1, 1)
+    p = o.trace(ids, sc.seed, 1)
+    return sc, o, p
+
+
+def _oracle_frame(o, sc, p, mode, tau, f):
+    import oracle
+    o.set_frames(f - 1, f)
+    o.verify(p, mode, tau)
+    o.retrace(p, sc.seed, f)
+    oracle.deposit(p, 1024, 1024, sc.atlas_rect)
+
+
+def cpu_baseline(workload, mode, tau, seconds):
+    """The oracle as it stands, on this host's cores, on a bounded sample."""
+    import oracle
+    n_sample = {"city": 4000, "villa": 600, "tiny_box": 10000}[workload]
+    sc, o, p = _oracle_sample(workload, n_sample)
+    t = time.perf_counter()
+    frames = 0
+    f = 1
+    while time.perf_counter() - t < seconds and frames < 60:
+        f += 1
+        _oracle_frame(o, sc, p, mode, tau, f)
+        frames += 1
+    dt = time.perf_counter() - t
+    return {"value": n_sample * frames / dt, "unit": "paths/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n_sample} seeded paths of the {workload} workload, frames 2..{f} "
+                      f"(verify + retrace + deposit, FP64 brute force over all {sc.n_tris} triangles)"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    sc0 = scene_for(args.workload)
+    mode = MODES[args.mode]
+    tau = sc0.tau if args.tau is None else args.tau
+    n_sample = {"city": 2000, "villa": 300, "tiny_box": 10000}[args.workload]
+    sc, o, p = _oracle_sample(args.workload, n_sample)
+    f = 1
+    for _ in range(args.warmup):
+        f += 1
+        _oracle_frame(o, sc, p, mode, tau, f)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        f += 1
+        _oracle_frame(o, sc, p, mode, tau, f)
+    dt = (time.perf_counter() - t) / args.steps
+    val = n_sample / dt
+    sample = (f"{n_sample} seeded paths of the {args.workload} workload per step "
+              f"(verify + retrace + deposit, FP64 brute force)")
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "paths/s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "mode": args.mode, "tau": tau,
+                      "sample_paths": n_sample},
+           "cpu_baseline": {"value": val, "unit": "paths/s", "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": val, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, ws, rank)
+        else:
+            run_ours(args, ws, rank, local)
+    finally:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

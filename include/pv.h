@@ -1,0 +1,225 @@
+/*
+ * pv.h -- C ABI of the GB300 (sm_103a) path-verification library.
+ *
+ * The library implements the per-frame hot path of Moreau, Doggett, Sintorn,
+ * "Path Verification for Dynamic Indirect Illumination" (arXiv 2111.06906):
+ * photon paths traced in earlier frames are checked against the lights and
+ * objects that moved (Sec. 3.1 "update path origins", Sec. 3.2 "dynamic
+ * occlusions", Sec. 3.3 / Alg. 1 / Eq. 2 "error-based threshold"), the paths
+ * that fail are compacted into a list (Sec. 5.2, pruned-paths array) and only
+ * those are re-traced (Fig. 2 "generate rays" / "trace rays", Sec. 4).
+ *
+ * Conventions
+ *  - Every call is asynchronous on the given CUDA stream (``stream`` is a
+ *    cudaStream_t passed as void*; NULL = legacy default stream) and no call
+ *    after pv_build_scene allocates device memory.
+ *  - Host-detectable errors return a negative pv_status immediately and
+ *    enqueue nothing.  Errors found on the device (traversal stack overflow,
+ *    iteration caps) are recorded in a sticky status word read by
+ *    pv_read_device_status; kernels never trap.
+ *  - The scene (acceleration structures, poses, workspace) is owned by the
+ *    library.  Path buffers, lists, counters, statistics and atlases are
+ *    device memory owned by the caller.  One scene must not be used by two
+ *    streams at once.
+ *  - Coordinates are metres, y up; all path data are FP32.
+ */
+#ifndef PV_H
+#define PV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pv_scene pv_scene;
+
+typedef enum {
+  PV_OK = 0,
+  PV_ERR_ARG = -1,        /* bad argument (null pointer, size mismatch, unknown mode) */
+  PV_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+  PV_ERR_OOM = -3,        /* device allocation failed (pv_build_scene only) */
+  PV_ERR_STACK = -4,      /* device: BVH traversal stack overflow */
+  PV_ERR_ITER_CAP = -5,   /* device: a bounded loop or wait hit its cap */
+  PV_ERR_LIMIT = -6,      /* a format limit: bounces > 15, lights > 4, dynamic objects > 64 */
+  PV_ERR_STATE = -7       /* call out of order (e.g. paths larger than the scene's workspace) */
+} pv_status;
+
+enum { PV_LIGHT_POINT = 0, PV_LIGHT_RECT = 1 };
+
+/* Verification modes.  NAIVE_AABB: Sec. 3.2, each segment is tested in order
+ * against the union of the old and new bounding boxes of every moved object;
+ * the first hit schedules that segment and all later ones for re-tracing.
+ * NAIVE_EXACT: same, with the moved objects' triangles at their new pose.
+ * ERROR: Sec. 3.3 / Alg. 1 -- boxes flag segments, a ray re-finds the end of
+ * each flagged segment and the path is kept while the reflected energy stays
+ * within tau of the stored one (Eq. 2). */
+enum { PV_MODE_NAIVE_AABB = 0, PV_MODE_NAIVE_EXACT = 1, PV_MODE_ERROR = 2 };
+enum {
+  PV_FLAG_TEST_OLD_TRIS = 1u,   /* exact tests also test the old pose's triangles */
+  PV_FLAG_ERROR_EXACT = 2u      /* ERROR mode flags segments with triangles, not boxes */
+};
+enum { PV_BUILD_DYN_REBUILD = 1u };  /* rebuild dynamic BVHs every frame instead of refitting */
+
+#define PV_MAX_LIGHTS 4
+#define PV_MAX_DYN_OBJECTS 64
+#define PV_MAX_BOUNCES 15
+
+/* Info word (Sec. 4): DM cell (22 bits, here light index << 20), number of
+ * segments (4), re-trace start vertex (4), replace (1), reuse the light's
+ * position and direction (1). */
+#define PV_INFO_CELL_MASK 0x003FFFFFu
+#define PV_INFO_NSEG_SHIFT 22
+#define PV_INFO_START_SHIFT 26
+#define PV_INFO_REPLACE (1u << 30)
+#define PV_INFO_REUSE_LIGHT (1u << 31)
+
+/* A light pose (64 bytes).  POINT: isotropic, ``pos``.  RECT: a w x h
+ * rectangle centred at ``pos`` emitting on the side of unit ``normal``;
+ * ``size[0]`` runs along unit ``tangent``, ``size[1]`` along normal x tangent.
+ * ``power`` is the RGB flux carried by the light's ``n_paths`` paths.  Paths
+ * belong to lights in order: light 0 owns path ids [0, n0), light 1 the next
+ * n1 ids, and so on. */
+typedef struct {
+  int32_t type;
+  float pos[3], normal[3], tangent[3], size[2], power[3];
+  uint32_t n_paths;
+} pv_light;
+
+/* Scene description; all arrays are HOST memory and are copied.
+ *  verts          [n_tris][3][3]  triangle corners; object-local for dynamic objects
+ *  tri_object     [n_tris]        object of each triangle (primitive id = index)
+ *  object_dynamic [n_objects]     1 = rigid dynamic object (at most 64), 0 = static
+ *  object_albedo  [n_objects][3]  Lambertian albedo (> 0 in some channel)
+ *  object_xform   [n_objects][12] initial 3x4 row-major [R|t] pose, NULL = identity
+ *  scene_diag     length unit of the tolerances: t_min = 1e-5 diag for rays
+ *                 leaving a surface, AreClose = 1e-5 diag (Alg. 1)           */
+typedef struct {
+  const float* verts;
+  uint32_t n_tris;
+  const uint32_t* tri_object;
+  uint32_t n_objects;
+  const uint8_t* object_dynamic;
+  const float* object_albedo;
+  const float* object_xform;
+  uint32_t n_lights;
+  const pv_light* lights;
+  uint32_t max_bounces;
+  float scene_diag;
+  uint32_t flags;
+} pv_scene_desc;
+
+/* Path buffers (device memory, caller-owned), the 2-D photon array of Sec. 4
+ * with row k holding the k-th photon of every path, split in two coalesced
+ * 16-byte planes:
+ *  info   [n]         info word (above)
+ *  origin [3][n]      emission point, x plane then y then z
+ *  pa     [B][n][4]   photon hit position x,y,z and primitive id (int32 bits)
+ *  pb     [B][n][4]   incident RGB energy and path length from the light     */
+typedef struct {
+  uint32_t n;
+  uint32_t max_bounces;
+  uint32_t* info;
+  float* origin;
+  float* pa;
+  float* pb;
+} pv_paths;
+
+typedef struct {
+  int32_t mode;     /* PV_MODE_* */
+  float tau;        /* Eq. 2 threshold T (relative); INFINITY accepts every energy */
+  uint32_t flags;   /* PV_FLAG_* */
+} pv_verify_params;
+
+/* Top-down XZ atlas (device, caller-owned): data[height][width][3] unsigned
+ * fixed point with 2^scale_log2 units per energy unit over [x0,x1] x [z0,z1];
+ * a photon lands in texel floor((x-x0) * width/(x1-x0)), clamped, computed in
+ * FP32 without fused operations. */
+typedef struct {
+  uint64_t* data;
+  uint32_t width, height;
+  float x0, z0, x1, z1;
+  int32_t scale_log2;
+} pv_atlas;
+
+/* Per-frame counters (device, caller-owned, accumulated; zero them first). */
+typedef struct {
+  uint32_t n_paths;          /* paths verified */
+  uint32_t n_listed;         /* paths in the re-trace list */
+  uint32_t n_reemit;         /* re-traced from the light (start 0) */
+  uint32_t n_tail;           /* re-traced from a vertex > 0 */
+  uint32_t n_updated;        /* kept with moved vertices (Alg. 1) */
+  uint32_t n_truncated;      /* shortened because a re-found segment escaped */
+  uint32_t n_cont;           /* paths that entered Alg. 1 */
+  uint32_t vis_rays;         /* point-light visibility rays (Sec. 3.1) */
+  uint32_t cont_rays;        /* rays traced by Alg. 1 */
+  uint32_t trace_rays;       /* rays traced by re-tracing / trace-all */
+  uint32_t segments_tested;  /* segment-vs-moved-object tests */
+  uint32_t photons_written;  /* photons stored by re-tracing / trace-all */
+  uint64_t node_visits;      /* BVH nodes visited by every ray query of the call */
+  uint64_t tri_tests;        /* ray-triangle tests of every ray query of the call */
+} pv_frame_stats;
+
+/* Build the static BVH and the dynamic objects' BVHs (Morton-code LBVH),
+ * upload per-primitive data and size the per-frame workspace for the lights'
+ * total path count.  Sets the initial pose as both old and new pose.
+ * Returns PV_ERR_LIMIT for more than 4 lights, 64 dynamic objects or 15
+ * bounces, PV_ERR_OOM if device memory runs out.  Synchronous. */
+int pv_build_scene(const pv_scene_desc* desc, void* stream, pv_scene** out);
+
+/* Advance one frame (no paper counterpart beyond the moving scene of Sec. 3):
+ * the current pose becomes the old pose; ``xforms`` (host [n_objects][12],
+ * only dynamic objects read; NULL = unchanged) and ``lights`` (host
+ * [n_lights], NULL = unchanged) become the new pose.  Moved objects are
+ * transformed and their BVHs refitted (or rebuilt) on the device.  An object
+ * or light moved iff one of its float values changed bit for bit. */
+int pv_update_dynamic(pv_scene* s, const float* xforms, const pv_light* lights, void* stream);
+
+/* Verify every path against the change from the old to the new pose:
+ * update origins (Sec. 3.1; point light: exact visibility ray replacing the
+ * shadow map; area light: stored direction re-intersected with the new
+ * light plane, with Eq. 2 on the primary energy for a tilted light), dynamic
+ * occlusions (Sec. 3.2), and in PV_MODE_ERROR the threshold continuation
+ * (Alg. 1, Eq. 2) which may move vertices in place.  Paths to re-trace get
+ * the replace bit and a start vertex; their ids are written in ascending
+ * order to d_list[0..*d_count) (d_list holds n entries).  d_stats may be
+ * NULL.  Returns PV_ERR_ARG if paths->n differs from the lights' total. */
+int pv_verify_paths(pv_scene* s, const pv_paths* paths, const pv_verify_params* params,
+                    uint32_t* d_list, uint32_t* d_count, pv_frame_stats* d_stats, void* stream);
+
+/* Re-trace the listed paths at the new pose from their start vertex with a
+ * persistent kernel: start 0 without reuse = fresh emission; start 0 with
+ * reuse = same origin and primary direction; start k > 0 = Russian roulette
+ * and a cosine-weighted bounce at photon k.  Random numbers are
+ * Philox-4x32-10 keyed by (path, vertex, frame) with key ``seed``.  The
+ * count is read on the device (no host synchronisation). */
+int pv_retrace_invalid(pv_scene* s, const pv_paths* paths, const uint32_t* d_list,
+                       const uint32_t* d_count, uint64_t seed, uint32_t frame,
+                       pv_frame_stats* d_stats, void* stream);
+
+/* Baseline of Sec. 5: re-trace every path from the light (no reuse). */
+int pv_trace_all(pv_scene* s, const pv_paths* paths, uint64_t seed, uint32_t frame,
+                 pv_frame_stats* d_stats, void* stream);
+
+/* Ascending ids of the paths whose replace bit is set (Sec. 5.2 pattern:
+ * the marked paths packed so that as few blocks as possible process them);
+ * single-pass decoupled look-back scan using the scene's workspace. */
+int pv_compact_replace(pv_scene* s, const pv_paths* paths, uint32_t* d_list, uint32_t* d_count,
+                       void* stream);
+
+/* Clear the atlas and add every stored photon's incident energy to the
+ * texel under it (stand-in for the renderer's splatting, Fig. 2). */
+int pv_deposit(pv_scene* s, const pv_paths* paths, const pv_atlas* atlas, void* stream);
+
+/* Synchronise the scene's last stream and return the first device-side error
+ * recorded since the last call (then clear it), or PV_OK. */
+int pv_read_device_status(pv_scene* s);
+
+void pv_destroy_scene(pv_scene* s);
+const char* pv_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PV_H */

@@ -710,7 +710,8 @@ void or_verify(const or_scene* s, const uint32_t* ids, uint32_t n, int32_t mode,
               if (!energy_close(EN, ph[0].E, tau, &near)) invalid = 1;
               if (near) { ea++; amb |= OR_AMB_ENERGY; }
             }
-            for (int k = 0; k < 3; ++k) org[k] = (float)op[k];
+            if (!invalid)
+              for (int k = 0; k < 3; ++k) org[k] = (float)op[k];
           }
         }
       }

@@ -1,0 +1,249 @@
+"""Python binding of the GB300 path-verification library (``include/pv.h``).
+
+Argument marshalling only: every step of the path runs in the CUDA kernels of
+``_build/libpv.so``.  PyTorch supplies device memory (``data_ptr()``) and
+streams; nothing here computes on the data.  Importing works without a GPU;
+every call that reaches the library fails loudly if the library was not built.
+
+Path buffers follow ``pv_paths`` (Sec. 4 of the paper, row k = photon k of
+every path): ``info`` int32 [N] (uint32 bits), ``origin`` float32 [3, N],
+``pa`` float32 [B, N, 4] (hit position, primitive id bits), ``pb`` float32
+[B, N, 4] (incident RGB energy, path length).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpv.so")
+
+PV_OK = 0
+PV_LIGHT_POINT, PV_LIGHT_RECT = 0, 1
+PV_MODE_NAIVE_AABB, PV_MODE_NAIVE_EXACT, PV_MODE_ERROR = 0, 1, 2
+PV_FLAG_TEST_OLD_TRIS, PV_FLAG_ERROR_EXACT = 1, 2
+PV_BUILD_DYN_REBUILD = 1
+PV_INFO_NSEG_SHIFT, PV_INFO_START_SHIFT = 22, 26
+PV_INFO_REPLACE, PV_INFO_REUSE_LIGHT = 1 << 30, 1 << 31
+
+EXPORTS = ["pv_build_scene", "pv_update_dynamic", "pv_verify_paths", "pv_retrace_invalid", "pv_trace_all",
+           "pv_compact_replace", "pv_deposit", "pv_read_device_status", "pv_destroy_scene", "pv_status_string"]
+
+
+class PvError(RuntimeError):
+    pass
+
+
+class PvLight(C.Structure):
+    _fields_ = [("type", C.c_int32), ("pos", C.c_float * 3), ("normal", C.c_float * 3), ("tangent", C.c_float * 3),
+                ("size", C.c_float * 2), ("power", C.c_float * 3), ("n_paths", C.c_uint32)]
+
+
+class PvSceneDesc(C.Structure):
+    _fields_ = [("verts", C.c_void_p), ("n_tris", C.c_uint32), ("tri_object", C.c_void_p), ("n_objects", C.c_uint32),
+                ("object_dynamic", C.c_void_p), ("object_albedo", C.c_void_p), ("object_xform", C.c_void_p),
+                ("n_lights", C.c_uint32), ("lights", C.c_void_p), ("max_bounces", C.c_uint32),
+                ("scene_diag", C.c_float), ("flags", C.c_uint32)]
+
+
+class PvPaths(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("max_bounces", C.c_uint32), ("info", C.c_void_p), ("origin", C.c_void_p),
+                ("pa", C.c_void_p), ("pb", C.c_void_p)]
+
+
+class PvVerifyParams(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("tau", C.c_float), ("flags", C.c_uint32)]
+
+
+class PvAtlas(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("width", C.c_uint32), ("height", C.c_uint32), ("x0", C.c_float),
+                ("z0", C.c_float), ("x1", C.c_float), ("z1", C.c_float), ("scale_log2", C.c_int32)]
+
+
+STATS_FIELDS = ["n_paths", "n_listed", "n_reemit", "n_tail", "n_updated", "n_truncated", "n_cont", "vis_rays",
+                "cont_rays", "trace_rays", "segments_tested", "photons_written"]
+STATS_FIELDS64 = ["node_visits", "tri_tests"]
+STATS_WORDS = len(STATS_FIELDS) + 2 * len(STATS_FIELDS64)
+
+_lib = None
+
+
+def load():
+    """Load ``libpv.so``; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise PvError(f"CUDA library missing at {LIB_PATH}: run paper_2111_06906_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        L.pv_build_scene.argtypes = [C.POINTER(PvSceneDesc), P, C.POINTER(C.c_void_p)]
+        L.pv_update_dynamic.argtypes = [P, P, P, P]
+        L.pv_verify_paths.argtypes = [P, C.POINTER(PvPaths), C.POINTER(PvVerifyParams), P, P, P, P]
+        L.pv_retrace_invalid.argtypes = [P, C.POINTER(PvPaths), P, P, C.c_uint64, C.c_uint32, P, P]
+        L.pv_trace_all.argtypes = [P, C.POINTER(PvPaths), C.c_uint64, C.c_uint32, P, P]
+        L.pv_compact_replace.argtypes = [P, C.POINTER(PvPaths), P, P, P]
+        L.pv_deposit.argtypes = [P, C.POINTER(PvPaths), C.POINTER(PvAtlas), P]
+        L.pv_read_device_status.argtypes = [P]
+        L.pv_destroy_scene.argtypes = [P]
+        L.pv_destroy_scene.restype = None
+        L.pv_status_string.argtypes = [C.c_int]
+        L.pv_status_string.restype = C.c_char_p
+        for name in EXPORTS:
+            if name not in ("pv_destroy_scene", "pv_status_string"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def pv_status_string(rc: int) -> str:
+    return load().pv_status_string(int(rc)).decode()
+
+
+def _check(name: str, rc: int) -> None:
+    if rc != PV_OK:
+        raise PvError(f"{name}: {pv_status_string(rc)} ({rc})")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def make_lights(lights) -> C.Array:
+    """Pack objects with type/pos/normal/tangent/size/power/n_paths into pv_light[]."""
+    arr = (PvLight * len(lights))()
+    for i, l in enumerate(lights):
+        arr[i].type = int(l.type)
+        arr[i].pos[:] = [float(v) for v in l.pos]
+        arr[i].normal[:] = [float(v) for v in l.normal]
+        arr[i].tangent[:] = [float(v) for v in l.tangent]
+        arr[i].size[:] = [float(v) for v in l.size]
+        arr[i].power[:] = [float(v) for v in l.power]
+        arr[i].n_paths = int(l.n_paths)
+    return arr
+
+
+@dataclass
+class Paths:
+    """Caller-owned device path buffers (torch tensors)."""
+    info: "object"
+    origin: "object"
+    pa: "object"
+    pb: "object"
+
+    @classmethod
+    def allocate(cls, n: int, max_bounces: int, device="cuda"):
+        import torch
+        return cls(torch.zeros(n, dtype=torch.int32, device=device),
+                   torch.zeros(3, n, dtype=torch.float32, device=device),
+                   torch.zeros(max_bounces, n, 4, dtype=torch.float32, device=device),
+                   torch.zeros(max_bounces, n, 4, dtype=torch.float32, device=device))
+
+    @property
+    def n(self) -> int:
+        return int(self.info.shape[0])
+
+    @property
+    def max_bounces(self) -> int:
+        return int(self.pa.shape[0])
+
+    def struct(self) -> PvPaths:
+        for t in (self.info, self.origin, self.pa, self.pb):
+            if not t.is_contiguous():
+                raise PvError("path buffers must be contiguous")
+        return PvPaths(self.n, self.max_bounces, self.info.data_ptr(), self.origin.data_ptr(), self.pa.data_ptr(),
+                       self.pb.data_ptr())
+
+
+def pv_build_scene(verts, tri_object, object_dynamic, object_albedo, lights, max_bounces: int, scene_diag: float,
+                   object_xform=None, flags: int = 0, stream=None) -> C.c_void_p:
+    """Build a scene from host arrays (copied); returns the opaque handle."""
+    L = load()
+    keep = [np.ascontiguousarray(verts, np.float32), np.ascontiguousarray(tri_object, np.uint32),
+            np.ascontiguousarray(object_dynamic, np.uint8), np.ascontiguousarray(object_albedo, np.float32)]
+    xf = None if object_xform is None else np.ascontiguousarray(object_xform, np.float32)
+    la = make_lights(lights)
+    d = PvSceneDesc(keep[0].ctypes.data, keep[0].shape[0], keep[1].ctypes.data, keep[2].shape[0], keep[2].ctypes.data,
+                    keep[3].ctypes.data, 0 if xf is None else xf.ctypes.data, len(lights), C.cast(la, C.c_void_p),
+                    int(max_bounces), float(scene_diag), int(flags))
+    h = C.c_void_p()
+    _check("pv_build_scene", L.pv_build_scene(C.byref(d), _stream(stream), C.byref(h)))
+    return h
+
+
+def pv_update_dynamic(scene, xforms=None, lights=None, stream=None) -> None:
+    xf = None if xforms is None else np.ascontiguousarray(xforms, np.float32)
+    la = None if lights is None else make_lights(lights)
+    _check("pv_update_dynamic", load().pv_update_dynamic(
+        scene, None if xf is None else xf.ctypes.data_as(C.c_void_p), None if la is None else C.cast(la, C.c_void_p),
+        _stream(stream)))
+
+
+def pv_verify_paths(scene, paths: Paths, mode: int, tau: float, flags: int, d_list, d_count, d_stats=None,
+                    stream=None) -> None:
+    ps = paths.struct()
+    prm = PvVerifyParams(int(mode), float(tau), int(flags))
+    _check("pv_verify_paths", load().pv_verify_paths(scene, C.byref(ps), C.byref(prm), _ptr(d_list), _ptr(d_count),
+                                                      _ptr(d_stats), _stream(stream)))
+
+
+def pv_retrace_invalid(scene, paths: Paths, d_list, d_count, seed: int, frame: int, d_stats=None, stream=None) -> None:
+    ps = paths.struct()
+    _check("pv_retrace_invalid", load().pv_retrace_invalid(scene, C.byref(ps), _ptr(d_list), _ptr(d_count),
+                                                            int(seed), int(frame), _ptr(d_stats), _stream(stream)))
+
+
+def pv_trace_all(scene, paths: Paths, seed: int, frame: int, d_stats=None, stream=None) -> None:
+    ps = paths.struct()
+    _check("pv_trace_all", load().pv_trace_all(scene, C.byref(ps), int(seed), int(frame), _ptr(d_stats),
+                                                _stream(stream)))
+
+
+def pv_compact_replace(scene, paths: Paths, d_list, d_count, stream=None) -> None:
+    ps = paths.struct()
+    _check("pv_compact_replace", load().pv_compact_replace(scene, C.byref(ps), _ptr(d_list), _ptr(d_count),
+                                                            _stream(stream)))
+
+
+def pv_deposit(scene, paths: Paths, atlas, rect, scale_log2: int, stream=None) -> None:
+    """``atlas``: int64 tensor [H, W, 3] (uint64 fixed point, cleared here)."""
+    ps = paths.struct()
+    H, W = int(atlas.shape[0]), int(atlas.shape[1])
+    a = PvAtlas(atlas.data_ptr(), W, H, float(rect[0]), float(rect[1]), float(rect[2]), float(rect[3]),
+                int(scale_log2))
+    _check("pv_deposit", load().pv_deposit(scene, C.byref(ps), C.byref(a), _stream(stream)))
+
+
+def pv_read_device_status(scene) -> int:
+    return int(load().pv_read_device_status(scene))
+
+
+def pv_destroy_scene(scene) -> None:
+    if scene:
+        load().pv_destroy_scene(scene)
+
+
+def stats_dict(d_stats) -> dict:
+    """Decode a ``pv_frame_stats`` device buffer (int32 tensor)."""
+    v = d_stats.cpu().numpy().view(np.uint32)
+    out = {k: int(v[i]) for i, k in enumerate(STATS_FIELDS)}
+    w = v[len(STATS_FIELDS):].copy().view(np.uint64)
+    out.update({k: int(w[i]) for i, k in enumerate(STATS_FIELDS64)})
+    return out
+
+
+def new_stats(device="cuda"):
+    """Zeroed ``pv_frame_stats`` (8-byte aligned int32 tensor)."""
+    import torch
+    return torch.zeros(STATS_WORDS, dtype=torch.int32, device=device)

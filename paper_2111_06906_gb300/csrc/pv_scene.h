@@ -1,0 +1,112 @@
+// Host-side scene object and launch helpers shared by the library's
+// translation units (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "pv.h"
+#include "pv_device.cuh"
+
+struct pv_scene {
+  int device = 0;
+  int num_sms = 0;
+  uint32_t n_tris = 0, n_objects = 0, n_static = 0, n_dyn_tris = 0, n_dyn = 0;
+  uint32_t B = 0;
+  float diag = 0.f, tmin = 0.f, close_tol = 0.f;
+  uint32_t flags = 0;
+
+  // static BVH
+  pvk::Node* s_nodes = nullptr;
+  pvk::Tri* s_tris = nullptr;
+  int32_t s_root = INT32_MIN;
+
+  // dynamic objects (one LBVH over all dynamic triangles, keyed by slot first)
+  pvk::Node* d_nodes = nullptr;
+  pvk::Tri* d_tris = nullptr;
+  float* d_local = nullptr;          // [n_dyn_tris][9] object-local corners, BVH order
+  uint32_t* d_tri_prim = nullptr;    // [n_dyn_tris] primitive id, BVH order
+  uint32_t* d_leaf_parent = nullptr; // [n_dyn_tris] parent << 1 | side
+  uint32_t* d_node_parent = nullptr; // [n_dyn_tris] parent << 1 | side of internal nodes
+  uint32_t* d_fit_flags = nullptr;   // [n_dyn_tris] arrival counters for the bottom-up pass
+  uint8_t* d_tri_slot = nullptr;     // [n_dyn_tris] slot per dynamic triangle
+  pvk::DynObj* objs = nullptr;       // [n_dyn]
+  std::vector<pvk::DynObj> h_objs;
+  std::vector<std::vector<uint32_t>> dyn_tris_of;   // slot -> primitive ids (build only)
+  // rebuild scratch (PV_BUILD_DYN_REBUILD)
+  uint64_t* r_keys[2] = {nullptr, nullptr};
+  uint32_t* r_vals[2] = {nullptr, nullptr};
+  uint32_t* r_hist = nullptr;
+  pvk::Tri* r_tris = nullptr;
+  float* r_local = nullptr;
+  uint32_t* r_prim = nullptr;
+  int32_t* d_obj_root = nullptr;     // [n_dyn] roots found by the hierarchy pass
+
+  // per primitive
+  uint8_t* prim_slot = nullptr;
+  uint32_t* prim_dyn = nullptr;
+  float4* prim_alb = nullptr;
+  float4* prim_nrm = nullptr;        // [n_tris] e1 x e2 of the given corners (object-local for dynamic)
+
+  // poses: host copies of the object table's dynamic transforms and lights
+  std::vector<uint32_t> dyn_object;          // slot -> user object id
+  std::vector<float> h_xf_old, h_xf_new;     // [n_dyn][12]
+  float* xf_old = nullptr;                   // device [kMaxDyn][12]
+  float* xf_new = nullptr;
+  uint64_t moved = 0;
+  uint32_t n_lights = 0;
+  pv_light lights_old[PV_MAX_LIGHTS], lights_new[PV_MAX_LIGHTS];
+  uint32_t n_paths_total = 0;
+
+  // per-frame workspace
+  uint32_t* ws_mask = nullptr;       // [n_paths] intersected-segment masks (error mode)
+  uint32_t* ws_cont = nullptr;       // [n_paths] continuation list
+  uint64_t* ws_tiles = nullptr;      // [n_tiles + 1] decoupled look-back tile states
+  uint32_t n_tiles = 0;
+  uint32_t* ws_ctr = nullptr;        // [16] work counters
+  int* status = nullptr;             // sticky device status
+  cudaStream_t last_stream = nullptr;
+
+  int verify_blocks = 0, trace_blocks = 0, cont_blocks = 0;
+};
+
+namespace pvh {
+
+constexpr int kTraceThreads = 128;
+constexpr int kVerifyThreads = 256;
+constexpr int kCompactThreads = 256;
+constexpr int kCompactItems = 16;    // paths per thread in the compaction tile
+constexpr uint32_t kTile = kCompactThreads * kCompactItems;
+
+// work counter slots in ws_ctr
+enum { CTR_CONT = 0, CTR_TRACE = 1, CTR_TILE = 2, CTR_ALL = 3 };
+
+pvk::SceneView view(const pv_scene* s);
+pvk::FrameLights frame_lights(const pv_scene* s);
+
+// bvh.cu
+int build_static_bvh(pv_scene* s, const float* h_verts, const std::vector<uint32_t>& static_prims, cudaStream_t st);
+int build_dynamic_bvh(pv_scene* s, const float* h_verts, cudaStream_t st);
+void launch_update_dynamic(pv_scene* s, cudaStream_t st);
+
+// compact.cu
+void launch_compact(pv_scene* s, const uint32_t* info, uint32_t n, uint32_t* list, uint32_t* count,
+                    uint32_t* stats_listed, cudaStream_t st);
+
+// trace.cu
+void launch_trace(pv_scene* s, const pv_paths* p, const uint32_t* list, const uint32_t* count, uint64_t seed,
+                  uint32_t frame, pv_frame_stats* stats, cudaStream_t st);
+
+// verify.cu: argument checks shared by the entry points
+int check_paths(const pv_scene* s, const pv_paths* p);
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? PV_OK : PV_ERR_CUDA; }
+
+}  // namespace pvh
+
+#define PV_CHECK(call)                         \
+  do {                                         \
+    cudaError_t _e = (call);                   \
+    if (_e != cudaSuccess) return PV_ERR_CUDA; \
+  } while (0)

@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bit-exact: info words (segment counts, start vertices, replace and
+reuse-light bits), primitive ids and the re-trace lists.  Within tolerance:
+positions (1e-5 x scene diagonal, FP32 storage), energies and path lengths
+(1e-5 relative).  Paths the oracle flags as ambiguous (a decision within
+1e-6 x diagonal of an edge or plane, or an Eq. 2 / AreClose near-tie) are
+excluded and counted.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+import paper_2111_06906_gb300 as pv
+from tests import gpu_util as gu
+from tests import scene_kit as kit
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2111_06906_gb300 import build
+    build.build()
+    pv.load()
+
+
+def _t():
+    import torch
+    return torch
+
+
+def _buffers(n):
+    torch = _t()
+    return (torch.zeros(max(n, 1), dtype=torch.int32, device="cuda"), torch.zeros(1, dtype=torch.int32, device="cuda"),
+            pv.new_stats())
+
+
+def _list(lst, cnt):
+    return lst[: int(cnt.item())].cpu().numpy().view(np.uint32)
+
+
+def test_trace_all_parity_tiny_box():
+    sc = scenes.tiny_box()
+    h = gu.lib_scene(sc)
+    P = pv.Paths.allocate(sc.n_paths, sc.max_bounces)
+    st = pv.new_stats()
+    pv.pv_trace_all(h, P, 1, 1, st)
+    assert pv.pv_read_device_status(h) == 0
+    o = oracle.OracleScene(sc)
+    o.set_frames(1, 1)
+    op = o.trace(np.arange(sc.n_paths, dtype=np.uint32), 1, 1)
+    r = gu.compare(gu.download(P), op, sc.diag)
+    print(r)
+    gu.assert_parity(r)
+    assert r["ambiguous"] <= 0.01 * r["n"]
+    s = pv.stats_dict(st)
+    assert abs(s["trace_rays"] - op.stats["trace_rays"]) <= 2 * r["ambiguous"]
+    pv.pv_destroy_scene(h)
+
+
+def _verify_case(sc, mode, tau, flags=0, seed=1, f_old=1, f_new=2, check_retrace=True):
+    ids = np.arange(sc.n_paths, dtype=np.uint32)
+    o = oracle.OracleScene(sc)
+    o.set_frames(f_old, f_old)
+    op = o.trace(ids, seed, f_old)
+    h = gu.lib_scene(sc, frame=f_old)
+    P = pv.Paths.allocate(sc.n_paths, sc.max_bounces)
+    gu.upload(P, op)
+    gu.advance(h, sc, f_new)
+    lst, cnt, st = _buffers(sc.n_paths)
+    pv.pv_verify_paths(h, P, mode, tau, flags, lst, cnt, st)
+    o.set_frames(f_old, f_new)
+    q = op.copy()
+    _, ost = o.verify(q, mode, tau, flags)
+    gv = gu.download(P)
+    r = gu.compare(gv, q, sc.diag)
+    gl = _list(lst, cnt)
+    ol = oracle.compact(q.info)
+    amb = set(np.nonzero(q.amb)[0].tolist())
+    assert np.all(np.diff(gl.astype(np.int64)) > 0)
+    assert set(gl.tolist()) - amb == set(ol.tolist()) - amb
+    print(mode, tau, flags, r, "listed", len(gl), "oracle", len(ol), ost)
+    gu.assert_parity(r)
+    if check_retrace:
+        pv.pv_retrace_invalid(h, P, lst, cnt, seed, f_new, st)
+        o.retrace(q, seed, f_new)
+        r2 = gu.compare(gu.download(P), q, sc.diag)
+        print("retrace", r2)
+        gu.assert_parity(r2)
+    assert pv.pv_read_device_status(h) == 0
+    stats = pv.stats_dict(st)
+    pv.pv_destroy_scene(h)
+    return r, len(ol), stats, ost
+
+
+@pytest.mark.parametrize("mode,flags", [(0, 0), (1, 0), (2, 0), (2, pv.PV_FLAG_ERROR_EXACT)])
+def test_verify_parity_tiny_box(mode, flags):
+    r, n_list, stats, ost = _verify_case(scenes.tiny_box(), mode, 0.01, flags)
+    assert n_list > 50
+    assert stats["n_paths"] == 10_000
+
+
+@pytest.mark.parametrize("mode,tau,flags", [(0, 0.01, 0), (1, 0.01, 0), (1, 0.01, pv.PV_FLAG_TEST_OLD_TRIS),
+                                            (2, 0.0, 0), (2, 0.01, 0), (2, 0.05, pv.PV_FLAG_ERROR_EXACT),
+                                            (2, math.inf, 0)])
+def test_verify_parity_moving_torus(mode, tau, flags):
+    _verify_case(kit.box_with_torus(8000, B=4), mode, tau, flags)
+
+
+def test_verify_parity_area_light_moves_and_tilts():
+    a = math.radians(4.0)
+    sc = kit.rect_light_over_floor(20_000, shift=lambda f: (0.07 * (f - 1), 0.0, 0.02 * (f - 1)),
+                                   normal=lambda f: (0.0, -1.0, 0.0) if f == 1 else (0.0, -math.cos(a), math.sin(a)),
+                                   B=2)
+    for tau in (0.0, 0.02, math.inf):
+        _verify_case(sc, 2, tau)
+
+
+def test_verify_parity_point_light_moves():
+    R = 2.0
+    floor = kit.quad((-R, 0, -R), (0, 0, 2 * R), (2 * R, 0, 0))
+    wall = kit.quad((0.5, 0, -R), (0, 0, 2 * R), (0, 1.0, 0))
+    lights = lambda f: [scenes.Light(scenes.LIGHT_POINT, (0.3 * (f - 1), 0.5, 0.3), power=(1.0,) * 3, n_paths=6000)]
+    sc = kit.build([(floor, (0.5,) * 3, False), (wall, (0.6, 0.5, 0.4), False)], lights, B=3, diag=6.0)
+    for mode in (0, 2):
+        _verify_case(sc, mode, 0.01, f_old=1, f_new=3)
+
+
+def test_deposit_parity_tiny_box():
+    torch = _t()
+    sc = scenes.tiny_box()
+    o = oracle.OracleScene(sc)
+    o.set_frames(1, 1)
+    op = o.trace(np.arange(sc.n_paths, dtype=np.uint32), 1, 1)
+    h = gu.lib_scene(sc)
+    P = pv.Paths.allocate(sc.n_paths, sc.max_bounces)
+    gu.upload(P, op)
+    W = H = 256
+    S = 31
+    atlas = torch.zeros(H, W, 3, dtype=torch.int64, device="cuda")
+    pv.pv_deposit(h, P, atlas, sc.atlas_rect, S)
+    got = atlas.cpu().numpy().astype(np.float64) / 2.0 ** S
+    want = oracle.deposit(op, W, H, sc.atlas_rect)
+    cnt = oracle.deposit(oracle.Paths(op.ids, op.info, op.origin,
+                                      np.concatenate([op.photons[..., :4], np.ones_like(op.photons[..., 4:])], -1),
+                                      op.amb), W, H, sc.atlas_rect)[..., 0]
+    tol = 1e-5 * np.abs(want) + cnt[..., None] * 2.0 ** -S
+    assert np.all(np.abs(got - want) <= tol)
+    assert (want > 0).sum() > 1000
+    pv.pv_destroy_scene(h)
+
+
+@pytest.mark.parametrize("n", [1, 31, 4095, 4096, 4097, 3 * 4096 + 5, 100_003])
+def test_compaction_sizes(n):
+    torch = _t()
+    lights = lambda f: [scenes.Light(scenes.LIGHT_POINT, (0.0, 1.0, 0.0), n_paths=n)]
+    sc = kit.build([(kit.quad((-1, 0, -1), (0, 0, 2), (2, 0, 0)), (0.5,) * 3, False)], lights, B=1, diag=3.0)
+    h = gu.lib_scene(sc)
+    P = pv.Paths.allocate(n, 1)
+    rng = np.random.default_rng(n)
+    for density in (0.0, 0.003, 0.5, 1.0):
+        bits = rng.random(n) < density
+        info = np.where(bits, pv.PV_INFO_REPLACE, 0).astype(np.uint32) | (1 << 22)
+        P.info.copy_(torch.as_tensor(info.view(np.int32), device="cuda"))
+        lst, cnt, _ = _buffers(n)
+        pv.pv_compact_replace(h, P, lst, cnt)
+        assert np.array_equal(_list(lst, cnt), np.nonzero(bits)[0].astype(np.uint32))
+    assert pv.pv_read_device_status(h) == 0
+    pv.pv_destroy_scene(h)
+
+
+def test_static_frame_reuses_everything_city():
+    torch = _t()
+    sc = scenes.city()
+    h = gu.lib_scene(sc)
+    P = pv.Paths.allocate(sc.n_paths, sc.max_bounces)
+    pv.pv_trace_all(h, P, sc.seed, 1)
+    before = [t.clone() for t in (P.info, P.origin, P.pa, P.pb)]
+    gu.advance(h, sc, 1)                       # same pose again: nothing moved
+    for mode in (0, 1, 2):
+        lst, cnt, st = _buffers(sc.n_paths)
+        pv.pv_verify_paths(h, P, mode, 0.0, 0, lst, cnt, st)
+        assert int(cnt.item()) == 0
+        assert all(torch.equal(a, b) for a, b in zip(before, (P.info, P.origin, P.pa, P.pb)))
+    assert pv.pv_read_device_status(h) == 0
+    pv.pv_destroy_scene(h)
+
+
+def _sampled_full_size(sc, n_sample, mode=2, tau=0.01, frames=(1, 2)):
+    torch = _t()
+    h = gu.lib_scene(sc)
+    P = pv.Paths.allocate(sc.n_paths, sc.max_bounces)
+    pv.pv_trace_all(h, P, sc.seed, frames[0])
+    ids = np.sort(np.random.default_rng(42).choice(sc.n_paths, n_sample, replace=False)).astype(np.uint32)
+    o = oracle.OracleScene(sc)
+    o.set_frames(frames[0], frames[0])
+    op = o.trace(ids, sc.seed, frames[0])
+    r = gu.compare(gu.download(P, ids), op, sc.diag)
+    print("trace", r)
+    gu.assert_parity(r)
+    gu.advance(h, sc, frames[1])
+    lst, cnt, st = _buffers(sc.n_paths)
+    pv.pv_verify_paths(h, P, mode, tau, 0, lst, cnt, st)
+    o.set_frames(*frames)
+    q = op.copy()
+    o.verify(q, mode, tau)
+    r = gu.compare(gu.download(P, ids), q, sc.diag)
+    print("verify", r)
+    gu.assert_parity(r)
+    gl = set(_list(lst, cnt).tolist()) & set(ids.tolist())
+    ol = set(ids[oracle.compact(q.info)].tolist())
+    amb = set(ids[q.amb != 0].tolist())
+    assert gl - amb == ol - amb
+    pv.pv_retrace_invalid(h, P, lst, cnt, sc.seed, frames[1], st)
+    o.retrace(q, sc.seed, frames[1])
+    r = gu.compare(gu.download(P, ids), q, sc.diag)
+    print("retrace", r, pv.stats_dict(st))
+    gu.assert_parity(r)
+    assert pv.pv_read_device_status(h) == 0
+    pv.pv_destroy_scene(h)
+
+
+def test_city_full_size_sampled():
+    _sampled_full_size(scenes.city(), 1500)
+
+
+def test_villa_full_size_sampled():
+    _sampled_full_size(scenes.villa(), 240, frames=(1, 2))
