@@ -19,10 +19,10 @@ __device__ __forceinline__ int texel(float p, float lo, float hi, uint32_t res) 
   return (int)f;
 }
 
-__global__ void __launch_bounds__(256) k_deposit(uint32_t n, const uint32_t* info, const float4* pa, const float4* pb,
-                                                 pv_atlas at) {
+__global__ void __launch_bounds__(256) k_deposit(uint32_t n, uint32_t B, const uint32_t* info, const float4* pa,
+                                                 const float4* pb, pv_atlas at) {
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const uint32_t L = info_nseg(info[p]);
+    const uint32_t L = min(info_nseg(info[p]), B);
     for (uint32_t k = 0; k < L; ++k) {
       const float4 x = pa[(size_t)k * n + p];
       const float4 e = pb[(size_t)k * n + p];
@@ -51,7 +51,7 @@ extern "C" int pv_deposit(pv_scene* s, const pv_paths* paths, const pv_atlas* at
   const uint32_t n = paths->n;
   if (n) {
     const uint32_t blocks = (uint32_t)s->num_sms * 8u;
-    k_deposit<<<blocks, 256, 0, st>>>(n, paths->info, reinterpret_cast<const float4*>(paths->pa),
+    k_deposit<<<blocks, 256, 0, st>>>(n, s->B, paths->info, reinterpret_cast<const float4*>(paths->pa),
                                       reinterpret_cast<const float4*>(paths->pb), *atlas);
   }
   return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;

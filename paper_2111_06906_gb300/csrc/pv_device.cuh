@@ -316,7 +316,7 @@ __device__ __forceinline__ bool closest_hit(const SceneView& sv, const float* bo
   if (sv.s_root != INT32_MIN) traverse<false>(sv.s_nodes, sv.s_tris, sv.s_root, r, tb, best, exclude, sv.max_visits, sv.status, wk);
   for (uint32_t s = 0; s < sv.n_dyn; ++s) {
     float te;
-    if (!box1(r, tb, boxes + 6 * s, te)) continue;
+    if (sv.objs[s].root == INT32_MIN || !box1(r, tb, boxes + 6 * s, te)) continue;
     int b2 = -1;
     traverse<false>(sv.d_nodes, sv.d_tris, sv.objs[s].root, r, tb, b2, exclude, sv.max_visits, sv.status, wk);
     if (b2 >= 0) {
@@ -342,7 +342,7 @@ __device__ __forceinline__ bool any_hit_all(const SceneView& sv, const float* bo
   }
   for (uint32_t s = 0; s < sv.n_dyn; ++s) {
     float te;
-    if (!box1(r, tb, boxes + 6 * s, te)) continue;
+    if (sv.objs[s].root == INT32_MIN || !box1(r, tb, boxes + 6 * s, te)) continue;
     traverse<true>(sv.d_nodes, sv.d_tris, sv.objs[s].root, r, tb, best, exclude, sv.max_visits, sv.status, wk);
     if (best >= 0) return true;
   }

@@ -34,6 +34,7 @@ __device__ __forceinline__ bool seg_box(float3 a, float3 dv, float3 inv, const f
   const float av[3] = {a.x, a.y, a.z}, dd[3] = {dv.x, dv.y, dv.z}, iv[3] = {inv.x, inv.y, inv.z};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
+    if (bx[k] > bx[3 + k]) return false;            // empty box
     if (dd[k] == 0.0f) {
       if (av[k] < bx[k] || av[k] > bx[3 + k]) return false;
       continue;
@@ -77,7 +78,7 @@ __device__ bool seg_vs_moved(const SceneView& sv, const float* cull, const float
     const int s = __ffsll((long long)m) - 1;
     m &= m - 1;
     float te;
-    if (box1(r, tmax, cull + 6 * s, te)) {
+    if (sv.objs[s].root != INT32_MIN && box1(r, tmax, cull + 6 * s, te)) {
       float tb = tmax;
       int best = -1;
       traverse<true>(sv.d_nodes, sv.d_tris, sv.objs[s].root, r, tb, best, -1, sv.max_visits, sv.status, wk);
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(pvh::kVerifyThreads) k_verify(SceneView sv, Fr
   bool want_cont = false;
   if (p < n) {
     const uint32_t w = A.info[p];
-    const uint32_t nseg = info_nseg(w), l = info_light(w), cell = w & PV_INFO_CELL_MASK;
+    const uint32_t nseg = min(info_nseg(w), sv.B), l = info_light(w), cell = w & PV_INFO_CELL_MASK;
     float3 o = make_float3(A.origin[p], A.origin[n + p], A.origin[2 * (size_t)n + p]);
     bool blocked1 = false, invalid = false;
     if ((L.moved_mask >> l) & 1u) {
@@ -256,7 +257,7 @@ __device__ void continue_path(const SceneView& sv, const float* cull, const Cont
   const uint32_t n = A.n;
   const uint32_t w = A.info[p];
   const uint32_t cell = w & PV_INFO_CELL_MASK;
-  uint32_t nseg = info_nseg(w);
+  uint32_t nseg = min(info_nseg(w), sv.B);
   const uint32_t mask = A.mask[p];
   float3 xo[PV_MAX_BOUNCES + 1], xc[PV_MAX_BOUNCES + 1];
   int po[PV_MAX_BOUNCES + 1], pc[PV_MAX_BOUNCES + 1];

@@ -480,7 +480,7 @@ def villa(n_paths_per_light: int = 1_000_000, seed: int = 3, n_static: int = 2_0
         f = frame - 1
         ang = 0.05 * f / 1.0            # 0.05 m/frame along a 1 m radius loop
         cxk, czk = 3 * RS + 2.5, 2 * RS + 2.5
-        pos = (cxk + math.cos(ang), 1.6, czk + math.sin(ang))
+        pos = (cxk + math.cos(ang), 2.5, czk + math.sin(ang))    # above the furniture (<= 2.2 m)
         tilt = math.radians(10.0) * math.sin(2.0 * math.pi * f / 60.0)
         # torch points down, tilted about x by +-10 degrees
         nrm = (0.0, -math.cos(tilt), math.sin(tilt))
