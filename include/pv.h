@@ -208,6 +208,24 @@ int pv_trace_all(pv_scene* s, const pv_paths* paths, uint64_t seed, uint32_t fra
 int pv_compact_replace(pv_scene* s, const pv_paths* paths, uint32_t* d_list, uint32_t* d_count,
                        void* stream);
 
+/* Same result as pv_compact_replace over info[0..n), without a scene and
+ * without allocating device memory (the paper has no counterpart; this serves
+ * callers that must not allocate once running, e.g. a renderer that reserves
+ * its memory budget at start-up or whose device memory belongs to another
+ * allocator, and frame loops that cannot take the device-wide synchronisation
+ * an allocation may cause).  d_info[n], d_list[n] and d_count are device
+ * memory owned by the caller.  The scratch is one fixed array inside the
+ * library, sized for at most PV_STATIC_COMPACT_MAX_PATHS paths (128 KiB,
+ * kept on every GPU that loads the library until the process exits); larger
+ * n returns PV_ERR_LIMIT.  The first call on a device looks up the array's
+ * device address (make that first call before any stream capture).  All calls
+ * share the array, so calls that overlap on the GPU race; serialise them (one
+ * stream, or events).  Returns PV_ERR_ARG for null pointers.  Device-side
+ * errors of this call are not recorded. */
+#define PV_STATIC_COMPACT_MAX_PATHS (1u << 26)
+int pv_compact_replace_static(const uint32_t* d_info, uint32_t n, uint32_t* d_list, uint32_t* d_count,
+                              void* stream);
+
 /* Clear the atlas and add every stored photon's incident energy to the
  * texel under it (stand-in for the renderer's splatting, Fig. 2). */
 int pv_deposit(pv_scene* s, const pv_paths* paths, const pv_atlas* atlas, void* stream);

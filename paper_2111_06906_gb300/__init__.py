@@ -30,7 +30,9 @@ PV_INFO_NSEG_SHIFT, PV_INFO_START_SHIFT = 22, 26
 PV_INFO_REPLACE, PV_INFO_REUSE_LIGHT = 1 << 30, 1 << 31
 
 EXPORTS = ["pv_build_scene", "pv_update_dynamic", "pv_verify_paths", "pv_retrace_invalid", "pv_trace_all",
-           "pv_compact_replace", "pv_deposit", "pv_read_device_status", "pv_destroy_scene", "pv_status_string"]
+           "pv_compact_replace", "pv_compact_replace_static", "pv_deposit", "pv_read_device_status",
+           "pv_destroy_scene", "pv_status_string"]
+PV_STATIC_COMPACT_MAX_PATHS = 1 << 26
 
 
 class PvError(RuntimeError):
@@ -85,6 +87,7 @@ def load():
         L.pv_retrace_invalid.argtypes = [P, C.POINTER(PvPaths), P, P, C.c_uint64, C.c_uint32, P, P]
         L.pv_trace_all.argtypes = [P, C.POINTER(PvPaths), C.c_uint64, C.c_uint32, P, P]
         L.pv_compact_replace.argtypes = [P, C.POINTER(PvPaths), P, P, P]
+        L.pv_compact_replace_static.argtypes = [P, C.c_uint32, P, P, P]
         L.pv_deposit.argtypes = [P, C.POINTER(PvPaths), C.POINTER(PvAtlas), P]
         L.pv_read_device_status.argtypes = [P]
         L.pv_destroy_scene.argtypes = [P]
@@ -214,6 +217,13 @@ def pv_compact_replace(scene, paths: Paths, d_list, d_count, stream=None) -> Non
     ps = paths.struct()
     _check("pv_compact_replace", load().pv_compact_replace(scene, C.byref(ps), _ptr(d_list), _ptr(d_count),
                                                             _stream(stream)))
+
+
+def pv_compact_replace_static(d_info, n: int, d_list, d_count, stream=None) -> None:
+    """Allocation-free compaction for callers that must not allocate device
+    memory while running (no scene needed; at most 2^26 paths)."""
+    _check("pv_compact_replace_static", load().pv_compact_replace_static(_ptr(d_info), int(n), _ptr(d_list),
+                                                                          _ptr(d_count), _stream(stream)))
 
 
 def pv_deposit(scene, paths: Paths, atlas, rect, scale_log2: int, stream=None) -> None:
