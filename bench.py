@@ -37,7 +37,7 @@ WORKLOADS = {
              "point light + static area light + moving tilting torch; 3M paths, <=7 bounces",
     "tiny_box": "open 2x2x2 box (10 tris) + moving unit cube (12 tris), point light; 10k paths, <=3 bounces",
 }
-OPS_PER_NODE = 38     # FP32-pipe ops per BVH node visit (two slab tests), counted from the source
+OPS_PER_NODE = 107    # FP32-pipe ops per wide-node visit (four slab tests + ordering network), from the source
 OPS_PER_TRI = 40      # FP32-pipe ops per Moller-Trumbore test, counted from the source
 SM_COUNT, FP32_LANES = 152, 128
 
@@ -321,6 +321,8 @@ def run_ours(args, ws, rank, local):
            "trace_all_ms_parts": dict(zip(names, [float(x) for x in parts2])),
            "rays_per_frame_reuse": rays_reuse, "rays_per_frame_trace_all": rays_trace,
            "listed_per_frame": agg("n_listed", st_reuse), "mean_photons_per_path": mean_L,
+           "retrace_node_visits_per_ray": agg("node_visits", st_retrace) / max(agg("trace_rays", st_retrace), 1),
+           "retrace_tri_tests_per_ray": agg("tri_tests", st_retrace) / max(agg("trace_rays", st_retrace), 1),
            "scene_build_s": build_s, "device_status": [status, status2]}
     launches_per_frame = 2 + (3 if mode == 2 else 2) + 1 + 1
     out = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws, "steps": K, "warmup": W,

@@ -22,8 +22,9 @@ NVCC = os.environ.get("NVCC", "nvcc")
 
 
 def _flags(extra=()):
+    user = os.environ.get("PV_NVCC_FLAGS", "").split()      # extra definitions for tuning builds
     return ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-            "-I", CSRC, *ARCH, *extra]
+            "-I", CSRC, *ARCH, *user, *extra]
 
 
 def _stale(target, deps):

@@ -1,13 +1,28 @@
-// Morton-code LBVH construction, refit and per-frame rebuild.
+// Morton-code LBVH construction, refit, per-frame rebuild and top level.
 //
-// Build: 63-bit Morton keys of triangle centroids (21 bits per axis), a
-// stable LSD radix sort (8-bit digits, per-warp stable ranks), the binary
-// radix tree of Karras ("Maximizing parallelism in the construction of BVHs,
-// octrees and k-d trees", HPG 2012) with index tie-break for equal keys, and
-// a bottom-up box pass where the second child to arrive at a node builds the
-// union.  The dynamic objects share one tree keyed by (slot, 57-bit Morton of
-// the object-local centroid): slots occupy the top key bits, so every
-// object's triangles form one subtree whose root is recorded per slot.
+// All triangles and nodes live in two arrays shared by every tree:
+//   triangles: [static references | dynamic triangles]
+//   nodes:     [static tree | dynamic tree | top level]
+// Child indices are global (>= 0 internal node, ~i leaf = triangle i), so a
+// query walks the top level, the static tree and the dynamic objects' trees
+// in one traversal.
+//
+// Static build: oversized triangles are first split into references, each
+// bounded by the part of the triangle inside one cell of a grid over the
+// triangle's box (polygon clipping), so a few huge triangles (a floor) cannot
+// inflate the boxes of their ancestors.  Then: 63-bit Morton keys of the
+// reference centroids, a stable LSD radix sort (8-bit digits, per-warp stable
+// ranks), the binary radix tree of Karras ("Maximizing parallelism in the
+// construction of BVHs, octrees and k-d trees", HPG 2012) with index
+// tie-break for equal keys, and a bottom-up box pass in which the second child
+// to arrive at a node builds the union.
+//
+// Dynamic objects share one tree keyed by (slot, 57-bit Morton code of the
+// object-local centroid): slots occupy the top key bits, so each object's
+// triangles form one subtree whose root is recorded per slot.  Every frame the
+// moved objects are transformed and the tree is refitted (or rebuilt from
+// world-space keys), then the top level over the static root and the object
+// roots is rebuilt by a median split.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -43,13 +58,12 @@ struct Frame6 {
   float lo[3], ext[3];
 };
 
-// keys for the static triangles: centroid Morton code over the scene frame
-__global__ void k_morton_static(const float* verts, uint32_t n, Frame6 f, uint64_t* keys, uint32_t* vals) {
+// keys for the static references: centroid of the reference box
+__global__ void k_morton_static(const float* ref_box, uint32_t n, Frame6 f, uint64_t* keys, uint32_t* vals) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const float* v = verts + 9 * (size_t)i;
-  const float3 c = make_float3((v[0] + v[3] + v[6]) * (1.f / 3.f), (v[1] + v[4] + v[7]) * (1.f / 3.f),
-                               (v[2] + v[5] + v[8]) * (1.f / 3.f));
+  const float* b = ref_box + 6 * (size_t)i;
+  const float3 c = make_float3(0.5f * (b[0] + b[3]), 0.5f * (b[1] + b[4]), 0.5f * (b[2] + b[5]));
   keys[i] = morton(c, f.lo, f.ext, 21);
   vals[i] = i;
 }
@@ -181,9 +195,10 @@ __device__ __forceinline__ int lcp(const uint64_t* keys, int n, int i, int j) {
 }
 
 // Internal node i of the radix tree over n sorted keys: its key range, split
-// and children; parent links for the bottom-up pass; per-object roots.
-__global__ void k_karras(const uint64_t* keys, int n, Node* nodes, uint32_t* node_parent, uint32_t* leaf_parent,
-                         const uint8_t* tri_slot, DynObj* objs) {
+// and children (global indices: nodes at node_off, leaves at tri_off), the
+// parent links of the bottom-up pass (local indices) and per-object roots.
+__global__ void k_karras(const uint64_t* keys, int n, Node* nodes, int node_off, int tri_off, uint32_t* node_parent,
+                         uint32_t* leaf_parent, const uint8_t* tri_slot, DynObj* objs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
   const int d = (lcp(keys, n, i, i + 1) - lcp(keys, n, i, i - 1)) >= 0 ? 1 : -1;
@@ -202,28 +217,33 @@ __global__ void k_karras(const uint64_t* keys, int n, Node* nodes, uint32_t* nod
   } while (t > 1);
   const int gamma = i + s * d + min(d, 0);
   const int first = min(i, j), last = max(i, j);
-  const int left = first == gamma ? ~gamma : gamma;
-  const int right = last == gamma + 1 ? ~(gamma + 1) : gamma + 1;
-  nodes[i].d = make_int4(left, right, first, last);
-  if (left < 0) leaf_parent[gamma] = ((uint32_t)i << 1); else node_parent[gamma] = ((uint32_t)i << 1);
-  if (right < 0) leaf_parent[gamma + 1] = ((uint32_t)i << 1) | 1u; else node_parent[gamma + 1] = ((uint32_t)i << 1) | 1u;
+  const bool lleaf = first == gamma, rleaf = last == gamma + 1;
+  const int left = lleaf ? ~(tri_off + gamma) : node_off + gamma;
+  const int right = rleaf ? ~(tri_off + gamma + 1) : node_off + gamma + 1;
+  nodes[node_off + i].d = make_int4(left, right, first, last);
+  if (lleaf) leaf_parent[gamma] = ((uint32_t)i << 1); else node_parent[gamma] = ((uint32_t)i << 1);
+  if (rleaf) leaf_parent[gamma + 1] = ((uint32_t)i << 1) | 1u; else node_parent[gamma + 1] = ((uint32_t)i << 1) | 1u;
   if (tri_slot) {
     const uint32_t sl = tri_slot[first];
     if (objs[sl].tri_begin == (uint32_t)first && objs[sl].tri_begin + objs[sl].tri_count - 1 == (uint32_t)last)
-      objs[sl].root = i;
+      objs[sl].root = node_off + i;
   }
 }
 
-__global__ void k_gather_static(const float* verts, const uint32_t* order, const uint32_t* prim_of, uint32_t n, Tri* out) {
+// sorted references -> triangle records and leaf boxes
+__global__ void k_gather_static(const float* verts, const uint32_t* ref_tri, const float* ref_box, const uint32_t* order,
+                                const uint32_t* prim_of, uint32_t n, Tri* out, float* leaf_box) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const uint32_t src = order[i];
+  const uint32_t r = order[i];
+  const uint32_t src = ref_tri[r];
   const float* v = verts + 9 * (size_t)src;
   Tri T;
   T.v0 = make_float4(v[0], v[1], v[2], __int_as_float((int)prim_of[src]));
   T.e1 = make_float4(v[3] - v[0], v[4] - v[1], v[5] - v[2], 0.f);
   T.e2 = make_float4(v[6] - v[0], v[7] - v[1], v[8] - v[2], 0.f);
   out[i] = T;
+  for (int k = 0; k < 6; ++k) leaf_box[6 * (size_t)i + k] = ref_box[6 * (size_t)r + k];
 }
 
 // permute the dynamic arrays into the sorted order
@@ -248,20 +268,35 @@ __device__ __forceinline__ void store_slot(Node* nd, int side, float3 lo, float3
   }
 }
 
-// Bottom-up boxes: leaves from triangles (padded by a relative 2^-22 so the
-// FP32 slab test never rejects a box that holds a hit), then each internal
-// node's box is completed by the second child to arrive.
-__global__ void k_fit(Node* nodes, const uint32_t* node_parent, const uint32_t* leaf_parent, uint32_t* flags,
-                      const Tri* tris, int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || n < 2) return;
-  const Tri T = tris[i];
+__device__ __forceinline__ void tri_box(const Tri& T, float3& lo, float3& hi) {
   const float3 v0 = f3(T.v0), v1 = v0 + f3(T.e1), v2 = v0 + f3(T.e2);
-  float3 lo = make_float3(fminf(v0.x, fminf(v1.x, v2.x)), fminf(v0.y, fminf(v1.y, v2.y)), fminf(v0.z, fminf(v1.z, v2.z)));
-  float3 hi = make_float3(fmaxf(v0.x, fmaxf(v1.x, v2.x)), fmaxf(v0.y, fmaxf(v1.y, v2.y)), fmaxf(v0.z, fmaxf(v1.z, v2.z)));
+  lo = make_float3(fminf(v0.x, fminf(v1.x, v2.x)), fminf(v0.y, fminf(v1.y, v2.y)), fminf(v0.z, fminf(v1.z, v2.z)));
+  hi = make_float3(fmaxf(v0.x, fmaxf(v1.x, v2.x)), fmaxf(v0.y, fmaxf(v1.y, v2.y)), fmaxf(v0.z, fmaxf(v1.z, v2.z)));
+}
+
+__device__ __forceinline__ void pad_box(float3& lo, float3& hi) {
   const float pad = 2.384185791015625e-07f * fmaxf(maxabs3(lo), maxabs3(hi)) + 1e-30f;
   lo = lo - make_float3(pad, pad, pad);
   hi = hi + make_float3(pad, pad, pad);
+}
+
+// Bottom-up boxes of one tree (``nodes`` = its first node, local indices):
+// leaves from the triangle (or the given leaf box), padded by a relative
+// 2^-22 so the FP32 slab test never rejects a box that holds a hit; each
+// internal node's box is completed by the second child to arrive.
+__global__ void k_fit(Node* nodes, const uint32_t* node_parent, const uint32_t* leaf_parent, uint32_t* flags,
+                      const Tri* tris, const float* leaf_box, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || n < 2) return;
+  float3 lo, hi;
+  if (leaf_box) {
+    const float* b = leaf_box + 6 * (size_t)i;
+    lo = make_float3(b[0], b[1], b[2]);
+    hi = make_float3(b[3], b[4], b[5]);
+  } else {
+    tri_box(tris[i], lo, hi);
+  }
+  pad_box(lo, hi);
   uint32_t p = leaf_parent[i];
   for (int guard = 0; guard < 200; ++guard) {
     const int node = (int)(p >> 1);
@@ -338,6 +373,292 @@ __global__ void __launch_bounds__(256) k_update_objects(XformParams P, const flo
   if (threadIdx.x < 6) o->box_new[threadIdx.x] = red[threadIdx.x][0];
 }
 
+// ------------------------------------------------------------------ wide (4-child) nodes
+__device__ __forceinline__ int range_size(const Node* bnodes, int b) {
+  const int4 d = bnodes[b].d;
+  return d.w - d.z + 1;
+}
+
+__device__ __forceinline__ void slot_box(const Node* bnodes, int b, int side, float* box) {
+  const float* a = reinterpret_cast<const float*>(bnodes + b) + 4 * side;
+  const float* z = reinterpret_cast<const float*>(bnodes + b) + 8 + 2 * side;
+  box[0] = __ldcg(a + 0);
+  box[3] = __ldcg(a + 1);
+  box[1] = __ldcg(a + 2);
+  box[4] = __ldcg(a + 3);
+  box[2] = __ldcg(z + 0);
+  box[5] = __ldcg(z + 1);
+}
+
+__device__ __forceinline__ void write_wide(WNode* w, const float (*box)[6], const int* ref, int m) {
+  float b[4][6];
+  int c[4];
+  for (int i = 0; i < 4; ++i) {
+    for (int k = 0; k < 3; ++k) {
+      b[i][k] = i < m ? box[i][k] : 3.0e38f;
+      b[i][3 + k] = i < m ? box[i][3 + k] : -3.0e38f;
+    }
+    c[i] = i < m ? ref[i] : INT32_MIN;
+  }
+  w->lox = make_float4(b[0][0], b[1][0], b[2][0], b[3][0]);
+  w->hix = make_float4(b[0][3], b[1][3], b[2][3], b[3][3]);
+  w->loy = make_float4(b[0][1], b[1][1], b[2][1], b[3][1]);
+  w->hiy = make_float4(b[0][4], b[1][4], b[2][4], b[3][4]);
+  w->loz = make_float4(b[0][2], b[1][2], b[2][2], b[3][2]);
+  w->hiz = make_float4(b[0][5], b[1][5], b[2][5], b[3][5]);
+  w->child = make_int4(c[0], c[1], c[2], c[3]);
+  w->pad = make_int4(0, 0, 0, 0);
+}
+
+// Collapse a binary tree into wide nodes, one block, level by level.  Each
+// wide node starts from its binary node's two children and repeatedly opens
+// the child of largest surface area until it has four children; a child whose
+// subtree holds at most kLeafMax triangles becomes a leaf range (subtrees of a
+// radix tree cover consecutive sorted triangles).  ``wsrc`` records, for every
+// wide child, the binary slot its box comes from (binary node << 1 | side), so
+// a refit of the binary tree can refresh the wide boxes.
+//   static tree: one seed, binary root ``seed_root``, wide index ``wbase``;
+//   dynamic objects: one seed per object with more than kLeafMax triangles.
+__global__ void __launch_bounds__(1024) k_collapse(const Node* bnodes, int tri_off, int seed_root, DynObj* objs, int n_dyn,
+                                                   int* qa, int* qb, uint32_t q_cap, WNode* wnodes, int* wsrc,
+                                                   int wbase, uint32_t* wcount, int* status) {
+  __shared__ uint32_t s_in, s_out, s_next;
+  if (threadIdx.x == 0) {
+    uint32_t cnt = 0, next = 0;
+    if (objs) {
+      for (int s = 0; s < n_dyn; ++s) {
+        const DynObj& o = objs[s];
+        if (o.tri_count == 0) {
+          objs[s].wroot = INT32_MIN;
+        } else if (o.tri_count <= (uint32_t)kLeafMax) {
+          objs[s].wroot = leaf_ref(tri_off + o.tri_begin, o.tri_count);
+        } else {
+          objs[s].wroot = wbase + (int)next;
+          qa[2 * cnt] = o.root;
+          qa[2 * cnt + 1] = wbase + (int)next;
+          ++cnt;
+          ++next;
+        }
+      }
+    } else {
+      qa[0] = seed_root;
+      qa[1] = wbase;
+      cnt = 1;
+      next = 1;
+    }
+    s_in = cnt;
+    s_next = next;
+  }
+  __syncthreads();
+  for (int level = 0; level < 128; ++level) {
+    const uint32_t n_in = s_in;
+    if (n_in == 0) break;
+    if (threadIdx.x == 0) s_out = 0;
+    __syncthreads();
+    for (uint32_t it = threadIdx.x; it < n_in; it += blockDim.x) {
+      const int b = qa[2 * it], w = qa[2 * it + 1];
+      float box[4][6];
+      int ref[4], src[4];
+      int m = 2;
+      const int4 d = bnodes[b].d;
+      ref[0] = d.x;
+      ref[1] = d.y;
+      slot_box(bnodes, b, 0, box[0]);
+      slot_box(bnodes, b, 1, box[1]);
+      src[0] = b << 1;
+      src[1] = (b << 1) | 1;
+      while (m < 4) {
+        int pick = -1;
+        float best = -1.f;
+        for (int i = 0; i < m; ++i) {
+          if (ref[i] < 0 || range_size(bnodes, ref[i]) <= kLeafMax) continue;
+          const float ex = box[i][3] - box[i][0], ey = box[i][4] - box[i][1], ez = box[i][5] - box[i][2];
+          const float area = ex * ey + ey * ez + ez * ex;
+          if (area > best) {
+            best = area;
+            pick = i;
+          }
+        }
+        if (pick < 0) break;
+        const int c = ref[pick];
+        const int4 dc = bnodes[c].d;
+        ref[pick] = dc.x;
+        slot_box(bnodes, c, 0, box[pick]);
+        src[pick] = c << 1;
+        ref[m] = dc.y;
+        slot_box(bnodes, c, 1, box[m]);
+        src[m] = (c << 1) | 1;
+        ++m;
+      }
+      int wref[4];
+      for (int i = 0; i < m; ++i) {
+        const int c = ref[i];
+        if (c < 0) {
+          wref[i] = leaf_ref((uint32_t)(~c), 1);
+        } else {
+          const int4 dc = bnodes[c].d;
+          const int size = dc.w - dc.z + 1;
+          if (size <= kLeafMax) {
+            wref[i] = leaf_ref((uint32_t)(tri_off + dc.z), (uint32_t)size);
+          } else {
+            const uint32_t slot = atomicAdd(&s_out, 1u);
+            const int nw = wbase + (int)atomicAdd(&s_next, 1u);
+            if (slot < q_cap) {
+              qb[2 * slot] = c;
+              qb[2 * slot + 1] = nw;
+            } else {
+              record_error(status, PV_ERR_ITER_CAP);
+            }
+            wref[i] = nw;
+          }
+        }
+      }
+      write_wide(wnodes + w, box, wref, m);
+      for (int i = 0; i < 4; ++i) wsrc[4 * (w - wbase) + i] = i < m ? src[i] : -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_in = min(s_out, q_cap);
+    int* t = qa;
+    qa = qb;
+    qb = t;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *wcount = s_next;
+}
+
+// Refresh the boxes of wide nodes [0, n) of one tree from the refitted
+// binary slots recorded by k_collapse.
+__global__ void k_wide_refit(const Node* bnodes, const int* wsrc, const uint32_t* n_wide, WNode* wnodes) {
+  const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= *n_wide) return;
+  float* lo[3] = {&wnodes[w].lox.x, &wnodes[w].loy.x, &wnodes[w].loz.x};
+  float* hi[3] = {&wnodes[w].hix.x, &wnodes[w].hiy.x, &wnodes[w].hiz.x};
+  for (int i = 0; i < 4; ++i) {
+    const int src = wsrc[4 * w + i];
+    if (src < 0) continue;
+    float box[6];
+    slot_box(bnodes, src >> 1, src & 1, box);
+    for (int k = 0; k < 3; ++k) {
+      lo[k][i] = box[k];
+      hi[k][i] = box[3 + k];
+    }
+  }
+}
+
+// box of a wide reference (node: union of its children; leaf: its triangles)
+__device__ void ref_box(const WNode* wnodes, const Tri* tris, int r, float* b) {
+  for (int k = 0; k < 3; ++k) {
+    b[k] = 3.0e38f;
+    b[3 + k] = -3.0e38f;
+  }
+  if (r >= 0) {
+    const WNode& n = wnodes[r];
+    const float lx[4] = {n.lox.x, n.lox.y, n.lox.z, n.lox.w}, hx[4] = {n.hix.x, n.hix.y, n.hix.z, n.hix.w};
+    const float ly[4] = {n.loy.x, n.loy.y, n.loy.z, n.loy.w}, hy[4] = {n.hiy.x, n.hiy.y, n.hiy.z, n.hiy.w};
+    const float lz[4] = {n.loz.x, n.loz.y, n.loz.z, n.loz.w}, hz[4] = {n.hiz.x, n.hiz.y, n.hiz.z, n.hiz.w};
+    for (int c = 0; c < 4; ++c) {
+      b[0] = fminf(b[0], lx[c]); b[1] = fminf(b[1], ly[c]); b[2] = fminf(b[2], lz[c]);
+      b[3] = fmaxf(b[3], hx[c]); b[4] = fmaxf(b[4], hy[c]); b[5] = fmaxf(b[5], hz[c]);
+    }
+  } else {
+    const uint32_t f = leaf_first(r), c = leaf_count(r);
+    for (uint32_t i = 0; i < c; ++i) {
+      float3 lo, hi;
+      tri_box(tris[f + i], lo, hi);
+      pad_box(lo, hi);
+      b[0] = fminf(b[0], lo.x); b[1] = fminf(b[1], lo.y); b[2] = fminf(b[2], lo.z);
+      b[3] = fmaxf(b[3], hi.x); b[4] = fmaxf(b[4], hi.y); b[5] = fmaxf(b[5], hi.z);
+    }
+  }
+}
+
+// Top level over the static root and the dynamic objects' roots, rebuilt
+// every frame by one thread: entries sorted along the axis of largest
+// centroid spread and cut into four consecutive groups, recursively.
+__global__ void k_build_top(WNode* wnodes, const Tri* tris, int top_off, int static_root, const DynObj* objs, int n_dyn,
+                            int* root_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  float box[kMaxDyn + 1][6];
+  int ref[kMaxDyn + 1];
+  int n = 0;
+  if (static_root != INT32_MIN) {
+    ref_box(wnodes, tris, static_root, box[n]);
+    ref[n++] = static_root;
+  }
+  for (int s = 0; s < n_dyn; ++s) {
+    const int r = objs[s].wroot;
+    if (r == INT32_MIN) continue;
+    ref_box(wnodes, tris, r, box[n]);
+    ref[n++] = r;
+  }
+  if (n == 0) {
+    *root_out = INT32_MIN;
+    return;
+  }
+  if (n == 1) {
+    *root_out = ref[0];
+    return;
+  }
+  float clo[3] = {3e38f, 3e38f, 3e38f}, chi[3] = {-3e38f, -3e38f, -3e38f};
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < 3; ++k) {
+      const float c = 0.5f * (box[i][k] + box[i][3 + k]);
+      clo[k] = fminf(clo[k], c);
+      chi[k] = fmaxf(chi[k], c);
+    }
+  int ax = 0;
+  for (int k = 1; k < 3; ++k)
+    if (chi[k] - clo[k] > chi[ax] - clo[ax]) ax = k;
+  int order[kMaxDyn + 1];
+  for (int i = 0; i < n; ++i) order[i] = i;
+  for (int i = 1; i < n; ++i) {
+    const int v = order[i];
+    const float cv = box[v][ax] + box[v][3 + ax];
+    int j = i - 1;
+    while (j >= 0 && box[order[j]][ax] + box[order[j]][3 + ax] > cv) {
+      order[j + 1] = order[j];
+      --j;
+    }
+    order[j + 1] = v;
+  }
+  int st_b[kMaxDyn + 2], st_e[kMaxDyn + 2], st_node[kMaxDyn + 2];
+  int sp = 1, next = 1;
+  st_b[0] = 0;
+  st_e[0] = n;
+  st_node[0] = top_off;
+  while (sp > 0) {
+    --sp;
+    const int b = st_b[sp], e = st_e[sp], node = st_node[sp];
+    const int size = e - b;
+    const int groups = size < 4 ? size : 4;
+    float cb[4][6];
+    int child[4];
+    for (int g = 0; g < groups; ++g) {
+      const int gb = b + (size * g) / groups, ge = b + (size * (g + 1)) / groups;
+      for (int k = 0; k < 3; ++k) {
+        cb[g][k] = 3e38f;
+        cb[g][3 + k] = -3e38f;
+      }
+      for (int i = gb; i < ge; ++i)
+        for (int k = 0; k < 3; ++k) {
+          cb[g][k] = fminf(cb[g][k], box[order[i]][k]);
+          cb[g][3 + k] = fmaxf(cb[g][3 + k], box[order[i]][3 + k]);
+        }
+      if (ge - gb == 1) {
+        child[g] = ref[order[gb]];
+      } else {
+        child[g] = top_off + next++;
+        st_b[sp] = gb;
+        st_e[sp] = ge;
+        st_node[sp] = child[g];
+        ++sp;
+      }
+    }
+    write_wide(wnodes + node, cb, child, groups);
+  }
+  *root_out = top_off;
+}
+
 }  // namespace pvk
 
 using namespace pvk;
@@ -358,79 +679,201 @@ static void radix_sort(uint64_t*& k0, uint32_t*& v0, uint64_t*& k1, uint32_t*& v
 
 static inline uint32_t blocks(uint32_t n, uint32_t t) { return (n + t - 1) / t; }
 
-int build_static_bvh(pv_scene* s, const float* h_verts, const std::vector<uint32_t>& static_prims, cudaStream_t st) {
-  const uint32_t n = (uint32_t)static_prims.size();
-  s->n_static = n;
-  if (n == 0) {
-    s->s_root = INT32_MIN;
-    return PV_OK;
-  }
-  std::vector<float> sv(9 * (size_t)n);
-  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (uint32_t i = 0; i < n; ++i) {
-    const float* v = h_verts + 9 * (size_t)static_prims[i];
-    std::memcpy(&sv[9 * (size_t)i], v, 9 * sizeof(float));
-    for (int k = 0; k < 3; ++k) {
-      const float c = (v[k] + v[3 + k] + v[6 + k]) * (1.f / 3.f);
-      lo[k] = std::min(lo[k], c);
-      hi[k] = std::max(hi[k], c);
+// ---- oversized-triangle references (host)
+
+// Clip the convex polygon P (n vertices) against the half-space s*x[axis] <= s*v.
+static int clip_plane(const double (*P)[3], int n, int axis, double v, double s, double (*Q)[3]) {
+  int m = 0;
+  for (int i = 0; i < n; ++i) {
+    const double* a = P[i];
+    const double* b = P[(i + 1) % n];
+    const double da = s * (a[axis] - v), db = s * (b[axis] - v);
+    if (da <= 0.0) {
+      std::memcpy(Q[m++], a, sizeof(double) * 3);
+    }
+    if ((da < 0.0 && db > 0.0) || (da > 0.0 && db < 0.0)) {
+      const double t = da / (da - db);
+      for (int k = 0; k < 3; ++k) Q[m][k] = a[k] + t * (b[k] - a[k]);
+      ++m;
     }
   }
-  Frame6 f;
-  for (int k = 0; k < 3; ++k) {
-    f.lo[k] = lo[k];
-    f.ext[k] = hi[k] - lo[k];
-  }
-  float* d_v = nullptr;
-  uint32_t* d_prim = nullptr;
-  uint64_t *k0 = nullptr, *k1 = nullptr;
-  uint32_t *v0 = nullptr, *v1 = nullptr, *hist = nullptr, *np = nullptr, *lp = nullptr, *flags = nullptr;
-  const uint32_t n_tiles = blocks(n, kRsTile);
-  int rc = PV_OK;
-  auto fail = [&](cudaError_t e) { if (e != cudaSuccess && rc == PV_OK) rc = e == cudaErrorMemoryAllocation ? PV_ERR_OOM : PV_ERR_CUDA; };
-  fail(cudaMalloc(&d_v, sv.size() * sizeof(float)));
-  fail(cudaMalloc(&d_prim, n * sizeof(uint32_t)));
-  fail(cudaMalloc(&k0, n * sizeof(uint64_t)));
-  fail(cudaMalloc(&k1, n * sizeof(uint64_t)));
-  fail(cudaMalloc(&v0, n * sizeof(uint32_t)));
-  fail(cudaMalloc(&v1, n * sizeof(uint32_t)));
-  fail(cudaMalloc(&hist, 256 * (size_t)n_tiles * sizeof(uint32_t)));
-  fail(cudaMalloc(&np, n * sizeof(uint32_t)));
-  fail(cudaMalloc(&lp, n * sizeof(uint32_t)));
-  fail(cudaMalloc(&flags, n * sizeof(uint32_t)));
-  fail(cudaMalloc(&s->s_tris, n * sizeof(Tri)));
-  fail(cudaMalloc(&s->s_nodes, std::max<uint32_t>(n - 1, 1) * sizeof(Node)));
-  if (rc == PV_OK) {
-    fail(cudaMemcpyAsync(d_v, sv.data(), sv.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-    fail(cudaMemcpyAsync(d_prim, static_prims.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    k_morton_static<<<blocks(n, 256), 256, 0, st>>>(d_v, n, f, k0, v0);
-    radix_sort(k0, v0, k1, v1, n, hist, 0, 64, st);
-    k_gather_static<<<blocks(n, 256), 256, 0, st>>>(d_v, v0, d_prim, n, s->s_tris);
-    if (n >= 2) {
-      k_karras<<<blocks(n - 1, 256), 256, 0, st>>>(k0, (int)n, s->s_nodes, np, lp, nullptr, nullptr);
-      fail(cudaMemsetAsync(flags, 0, n * sizeof(uint32_t), st));
-      k_fit<<<blocks(n, 256), 256, 0, st>>>(s->s_nodes, np, lp, flags, s->s_tris, (int)n);
-      s->s_root = 0;
-    } else {
-      s->s_root = ~0;
-    }
-    fail(cudaGetLastError());
-    fail(cudaStreamSynchronize(st));
-  }
-  cudaFree(d_v); cudaFree(d_prim); cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1);
-  cudaFree(hist); cudaFree(np); cudaFree(lp); cudaFree(flags);
-  return rc;
+  return m;
 }
 
-// Dynamic objects: one tree over all dynamic triangles; keeps the parent
-// links and the sort scratch for refits and rebuilds.
-int build_dynamic_bvh(pv_scene* s, const float* h_verts, cudaStream_t st) {
-  const uint32_t n = s->n_dyn_tris;
-  if (n == 0) return PV_OK;
-  // group the dynamic triangles by slot (object order), local corners
-  std::vector<float> loc(9 * (size_t)n);
-  std::vector<uint32_t> prim(n);
-  std::vector<uint8_t> slot(n);
+// References of the static triangles: one per triangle, except that a
+// triangle whose box diagonal exceeds 8x the median is split over a grid of
+// cells of that size, one reference per non-empty clipped part (at most 4096).
+static void make_refs(const float* verts, const std::vector<uint32_t>& prims, std::vector<uint32_t>& ref_tri,
+                      std::vector<float>& ref_box) {
+  const size_t n = prims.size();
+  std::vector<float> diag(n);
+  for (size_t i = 0; i < n; ++i) {
+    const float* v = verts + 9 * (size_t)prims[i];
+    float d2 = 0.f;
+    for (int k = 0; k < 3; ++k) {
+      const float lo = std::min(v[k], std::min(v[3 + k], v[6 + k]));
+      const float hi = std::max(v[k], std::max(v[3 + k], v[6 + k]));
+      d2 += (hi - lo) * (hi - lo);
+    }
+    diag[i] = std::sqrt(d2);
+  }
+  std::vector<float> tmp(diag);
+  std::nth_element(tmp.begin(), tmp.begin() + n / 2, tmp.end());
+  const double cell = std::max(8.0 * tmp[n / 2], 1e-6);
+  ref_tri.reserve(n);
+  ref_box.reserve(6 * n);
+  for (size_t i = 0; i < n; ++i) {
+    const float* v = verts + 9 * (size_t)prims[i];
+    float lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(v[k], std::min(v[3 + k], v[6 + k]));
+      hi[k] = std::max(v[k], std::max(v[3 + k], v[6 + k]));
+    }
+    if (diag[i] <= cell) {
+      ref_tri.push_back((uint32_t)i);
+      ref_box.insert(ref_box.end(), {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]});
+      continue;
+    }
+    int m[3];
+    for (int k = 0; k < 3; ++k) m[k] = std::max(1, std::min(64, (int)std::ceil((hi[k] - lo[k]) / cell)));
+    while ((long)m[0] * m[1] * m[2] > 4096)
+      for (int k = 0; k < 3; ++k) m[k] = std::max(1, m[k] / 2);
+    for (int a = 0; a < m[0]; ++a)
+      for (int b = 0; b < m[1]; ++b)
+        for (int c = 0; c < m[2]; ++c) {
+          const int idx[3] = {a, b, c};
+          double P[16][3], Q[16][3];
+          for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) P[j][k] = v[3 * j + k];
+          int cnt = 3;
+          for (int k = 0; k < 3 && cnt; ++k) {
+            const double c0 = lo[k] + (double)(hi[k] - lo[k]) * idx[k] / m[k];
+            const double c1 = idx[k] + 1 == m[k] ? (double)hi[k] : lo[k] + (double)(hi[k] - lo[k]) * (idx[k] + 1) / m[k];
+            cnt = clip_plane(P, cnt, k, c1, 1.0, Q);
+            cnt = clip_plane(Q, cnt, k, c0, -1.0, P);
+          }
+          if (cnt == 0) continue;
+          double blo[3] = {1e300, 1e300, 1e300}, bhi[3] = {-1e300, -1e300, -1e300};
+          for (int j = 0; j < cnt; ++j)
+            for (int k = 0; k < 3; ++k) {
+              blo[k] = std::min(blo[k], P[j][k]);
+              bhi[k] = std::max(bhi[k], P[j][k]);
+            }
+          ref_tri.push_back((uint32_t)i);
+          float fb[6];
+          for (int k = 0; k < 3; ++k) {   // round outward, never past the triangle's own box
+            fb[k] = std::max(lo[k], std::nextafter((float)blo[k], -INFINITY));
+            fb[3 + k] = std::min(hi[k], std::nextafter((float)bhi[k], INFINITY));
+          }
+          ref_box.insert(ref_box.end(), fb, fb + 6);
+        }
+  }
+}
+
+int build_bvh(pv_scene* s, const float* h_verts, const std::vector<uint32_t>& static_prims, cudaStream_t st) {
+  int rc = PV_OK;
+  auto fail = [&](cudaError_t e) {
+    if (e != cudaSuccess && rc == PV_OK) rc = e == cudaErrorMemoryAllocation ? PV_ERR_OOM : PV_ERR_CUDA;
+  };
+  // ---- sizes and the shared arrays
+  std::vector<uint32_t> ref_tri;
+  std::vector<float> ref_box;
+  if (!static_prims.empty()) make_refs(h_verts, static_prims, ref_tri, ref_box);
+  const uint32_t ns = (uint32_t)ref_tri.size();
+  const uint32_t nd = s->n_dyn_tris;
+  s->n_static_refs = ns;
+  s->d_tri_off = ns;
+  s->d_node_off = ns > 1 ? ns - 1 : 0;
+  const uint32_t n_nodes = s->d_node_off + (nd > 1 ? nd - 1 : 0) + 1;
+  s->w_dyn_off = ns > 1 ? ns - 1 : 0;
+  s->w_top_off = s->w_dyn_off + (nd > 1 ? nd - 1 : 0);
+  s->n_wide = s->w_top_off + kMaxDyn + 1;
+  s->q_cap = std::max<uint32_t>(ns, nd) + 64;
+  fail(cudaMalloc(&s->tris, std::max<uint32_t>(ns + nd, 1) * sizeof(Tri)));
+  fail(cudaMalloc(&s->nodes, n_nodes * sizeof(Node)));
+  fail(cudaMalloc(&s->wnodes, s->n_wide * sizeof(WNode)));
+  fail(cudaMalloc(&s->wsrc, 4 * (size_t)s->n_wide * sizeof(int)));
+  fail(cudaMalloc(&s->wcount, 2 * sizeof(uint32_t)));
+  fail(cudaMalloc(&s->cq, 4 * (size_t)s->q_cap * sizeof(int)));
+  fail(cudaMalloc(&s->root, sizeof(int)));
+  if (rc != PV_OK) return rc;
+  fail(cudaMemsetAsync(s->nodes, 0, n_nodes * sizeof(Node), st));
+  fail(cudaMemsetAsync(s->wnodes, 0, s->n_wide * sizeof(WNode), st));
+  fail(cudaMemsetAsync(s->wcount, 0, 2 * sizeof(uint32_t), st));
+
+  // ---- static tree
+  s->s_root = INT32_MIN;
+  if (ns) {
+    Frame6 f;
+    float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (uint32_t i = 0; i < ns; ++i)
+      for (int k = 0; k < 3; ++k) {
+        const float c = 0.5f * (ref_box[6 * i + k] + ref_box[6 * i + 3 + k]);
+        clo[k] = std::min(clo[k], c);
+        chi[k] = std::max(chi[k], c);
+      }
+    for (int k = 0; k < 3; ++k) {
+      f.lo[k] = clo[k];
+      f.ext[k] = chi[k] - clo[k];
+    }
+    std::vector<float> sv(9 * static_prims.size());
+    for (size_t i = 0; i < static_prims.size(); ++i)
+      std::memcpy(&sv[9 * i], h_verts + 9 * (size_t)static_prims[i], 9 * sizeof(float));
+    float *d_v = nullptr, *d_rbox = nullptr, *d_lbox = nullptr;
+    uint32_t *d_prim = nullptr, *d_rtri = nullptr;
+    uint64_t *k0 = nullptr, *k1 = nullptr;
+    uint32_t *v0 = nullptr, *v1 = nullptr, *hist = nullptr, *np = nullptr, *lp = nullptr, *flags = nullptr;
+    const uint32_t n_tiles = blocks(ns, kRsTile);
+    fail(cudaMalloc(&d_v, sv.size() * sizeof(float)));
+    fail(cudaMalloc(&d_prim, static_prims.size() * sizeof(uint32_t)));
+    fail(cudaMalloc(&d_rtri, ns * sizeof(uint32_t)));
+    fail(cudaMalloc(&d_rbox, 6 * (size_t)ns * sizeof(float)));
+    fail(cudaMalloc(&d_lbox, 6 * (size_t)ns * sizeof(float)));
+    fail(cudaMalloc(&k0, ns * sizeof(uint64_t)));
+    fail(cudaMalloc(&k1, ns * sizeof(uint64_t)));
+    fail(cudaMalloc(&v0, ns * sizeof(uint32_t)));
+    fail(cudaMalloc(&v1, ns * sizeof(uint32_t)));
+    fail(cudaMalloc(&hist, 256 * (size_t)n_tiles * sizeof(uint32_t)));
+    fail(cudaMalloc(&np, ns * sizeof(uint32_t)));
+    fail(cudaMalloc(&lp, ns * sizeof(uint32_t)));
+    fail(cudaMalloc(&flags, ns * sizeof(uint32_t)));
+    if (rc == PV_OK) {
+      fail(cudaMemcpyAsync(d_v, sv.data(), sv.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+      fail(cudaMemcpyAsync(d_prim, static_prims.data(), static_prims.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+      fail(cudaMemcpyAsync(d_rtri, ref_tri.data(), ns * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+      fail(cudaMemcpyAsync(d_rbox, ref_box.data(), 6 * (size_t)ns * sizeof(float), cudaMemcpyHostToDevice, st));
+      k_morton_static<<<blocks(ns, 256), 256, 0, st>>>(d_rbox, ns, f, k0, v0);
+      radix_sort(k0, v0, k1, v1, ns, hist, 0, 64, st);
+      k_gather_static<<<blocks(ns, 256), 256, 0, st>>>(d_v, d_rtri, d_rbox, v0, d_prim, ns, s->tris, d_lbox);
+      if (ns >= 2) {
+        k_karras<<<blocks(ns - 1, 256), 256, 0, st>>>(k0, (int)ns, s->nodes, 0, 0, np, lp, nullptr, nullptr);
+        fail(cudaMemsetAsync(flags, 0, ns * sizeof(uint32_t), st));
+        k_fit<<<blocks(ns, 256), 256, 0, st>>>(s->nodes, np, lp, flags, s->tris, d_lbox, (int)ns);
+        s->s_root = 0;
+        if (ns <= (uint32_t)kLeafMax) {
+          s->s_wroot = leaf_ref(0, ns);
+        } else {
+          k_collapse<<<1, 1024, 0, st>>>(s->nodes, 0, 0, nullptr, 0, s->cq, s->cq + 2 * s->q_cap, s->q_cap, s->wnodes,
+                                         s->wsrc, 0, s->wcount, s->status);
+          s->s_wroot = 0;
+        }
+      } else {
+        s->s_root = ~0;
+        s->s_wroot = leaf_ref(0, 1);
+      }
+      fail(cudaGetLastError());
+      fail(cudaStreamSynchronize(st));
+    }
+    cudaFree(d_v); cudaFree(d_prim); cudaFree(d_rtri); cudaFree(d_rbox); cudaFree(d_lbox);
+    cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1); cudaFree(hist); cudaFree(np); cudaFree(lp); cudaFree(flags);
+    if (rc != PV_OK) return rc;
+  }
+
+  // ---- dynamic tree
+  if (nd == 0) return PV_OK;
+  std::vector<float> loc(9 * (size_t)nd);
+  std::vector<uint32_t> prim(nd);
+  std::vector<uint8_t> slot(nd);
   std::vector<Frame6> frames(s->n_dyn);
   {
     uint32_t w = 0;
@@ -450,86 +893,109 @@ int build_dynamic_bvh(pv_scene* s, const float* h_verts, cudaStream_t st) {
         ++w;
       }
       o.tri_count = w - o.tri_begin;
-      o.root = o.tri_count == 1 ? ~(int32_t)o.tri_begin : INT32_MIN;
+      o.root = o.tri_count == 1 ? ~(int32_t)(s->d_tri_off + o.tri_begin) : INT32_MIN;
+      o.wroot = INT32_MIN;
       for (int k = 0; k < 3; ++k) {
         frames[sl].lo[k] = lo[k];
         frames[sl].ext[k] = hi[k] - lo[k];
       }
     }
   }
-  int rc = PV_OK;
-  auto fail = [&](cudaError_t e) { if (e != cudaSuccess && rc == PV_OK) rc = e == cudaErrorMemoryAllocation ? PV_ERR_OOM : PV_ERR_CUDA; };
-  const uint32_t n_tiles = blocks(n, kRsTile);
+  const uint32_t n_tiles = blocks(nd, kRsTile);
   Frame6* d_frames = nullptr;
   float* tmp_local = nullptr;
   uint32_t* tmp_prim = nullptr;
   fail(cudaMalloc(&d_frames, s->n_dyn * sizeof(Frame6)));
-  fail(cudaMalloc(&tmp_local, 9 * (size_t)n * sizeof(float)));
-  fail(cudaMalloc(&tmp_prim, n * sizeof(uint32_t)));
-  fail(cudaMalloc(&s->d_local, 9 * (size_t)n * sizeof(float)));
-  fail(cudaMalloc(&s->d_tri_prim, n * sizeof(uint32_t)));
-  fail(cudaMalloc(&s->d_tri_slot, n * sizeof(uint8_t)));
-  fail(cudaMalloc(&s->d_tris, n * sizeof(Tri)));
-  fail(cudaMalloc(&s->d_nodes, std::max<uint32_t>(n - 1, 1) * sizeof(Node)));
-  fail(cudaMalloc(&s->d_leaf_parent, n * sizeof(uint32_t)));
-  fail(cudaMalloc(&s->d_node_parent, n * sizeof(uint32_t)));
-  fail(cudaMalloc(&s->d_fit_flags, n * sizeof(uint32_t)));
+  fail(cudaMalloc(&tmp_local, 9 * (size_t)nd * sizeof(float)));
+  fail(cudaMalloc(&tmp_prim, nd * sizeof(uint32_t)));
+  fail(cudaMalloc(&s->d_local, 9 * (size_t)nd * sizeof(float)));
+  fail(cudaMalloc(&s->d_tri_prim, nd * sizeof(uint32_t)));
+  fail(cudaMalloc(&s->d_tri_slot, nd * sizeof(uint8_t)));
+  fail(cudaMalloc(&s->d_leaf_parent, nd * sizeof(uint32_t)));
+  fail(cudaMalloc(&s->d_node_parent, nd * sizeof(uint32_t)));
+  fail(cudaMalloc(&s->d_fit_flags, nd * sizeof(uint32_t)));
   fail(cudaMalloc(&s->objs, s->n_dyn * sizeof(DynObj)));
   for (int b = 0; b < 2; ++b) {
-    fail(cudaMalloc(&s->r_keys[b], n * sizeof(uint64_t)));
-    fail(cudaMalloc(&s->r_vals[b], n * sizeof(uint32_t)));
+    fail(cudaMalloc(&s->r_keys[b], nd * sizeof(uint64_t)));
+    fail(cudaMalloc(&s->r_vals[b], nd * sizeof(uint32_t)));
   }
   fail(cudaMalloc(&s->r_hist, 256 * (size_t)n_tiles * sizeof(uint32_t)));
-  fail(cudaMalloc(&s->r_tris, n * sizeof(Tri)));
-  fail(cudaMalloc(&s->r_local, 9 * (size_t)n * sizeof(float)));
-  fail(cudaMalloc(&s->r_prim, n * sizeof(uint32_t)));
+  fail(cudaMalloc(&s->r_tris, nd * sizeof(Tri)));
+  fail(cudaMalloc(&s->r_local, 9 * (size_t)nd * sizeof(float)));
+  fail(cudaMalloc(&s->r_prim, nd * sizeof(uint32_t)));
   if (rc != PV_OK) {
     cudaFree(d_frames); cudaFree(tmp_local); cudaFree(tmp_prim);
     return rc;
   }
   fail(cudaMemcpyAsync(d_frames, frames.data(), s->n_dyn * sizeof(Frame6), cudaMemcpyHostToDevice, st));
   fail(cudaMemcpyAsync(tmp_local, loc.data(), loc.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-  fail(cudaMemcpyAsync(tmp_prim, prim.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-  fail(cudaMemcpyAsync(s->d_tri_slot, slot.data(), n * sizeof(uint8_t), cudaMemcpyHostToDevice, st));
+  fail(cudaMemcpyAsync(tmp_prim, prim.data(), nd * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+  fail(cudaMemcpyAsync(s->d_tri_slot, slot.data(), nd * sizeof(uint8_t), cudaMemcpyHostToDevice, st));
   fail(cudaMemcpyAsync(s->objs, s->h_objs.data(), s->n_dyn * sizeof(DynObj), cudaMemcpyHostToDevice, st));
   uint64_t *k0 = s->r_keys[0], *k1 = s->r_keys[1];
   uint32_t *v0 = s->r_vals[0], *v1 = s->r_vals[1];
-  k_morton_dyn<<<blocks(n, 256), 256, 0, st>>>(tmp_local, nullptr, s->d_tri_slot, n, d_frames, s->objs, 0, k0, v0);
-  radix_sort(k0, v0, k1, v1, n, s->r_hist, 0, 64, st);
-  k_gather_dyn<<<blocks(n, 256), 256, 0, st>>>(v0, n, tmp_local, tmp_prim, nullptr, s->d_local, s->d_tri_prim, nullptr);
-  if (n >= 2) k_karras<<<blocks(n - 1, 256), 256, 0, st>>>(k0, (int)n, s->d_nodes, s->d_node_parent, s->d_leaf_parent, s->d_tri_slot, s->objs);
+  k_morton_dyn<<<blocks(nd, 256), 256, 0, st>>>(tmp_local, nullptr, s->d_tri_slot, nd, d_frames, s->objs, 0, k0, v0);
+  radix_sort(k0, v0, k1, v1, nd, s->r_hist, 0, 64, st);
+  k_gather_dyn<<<blocks(nd, 256), 256, 0, st>>>(v0, nd, tmp_local, tmp_prim, nullptr, s->d_local, s->d_tri_prim, nullptr);
+  if (nd >= 2)
+    k_karras<<<blocks(nd - 1, 256), 256, 0, st>>>(k0, (int)nd, s->nodes, (int)s->d_node_off, (int)s->d_tri_off,
+                                                  s->d_node_parent, s->d_leaf_parent, s->d_tri_slot, s->objs);
   fail(cudaGetLastError());
   fail(cudaStreamSynchronize(st));
   cudaFree(d_frames); cudaFree(tmp_local); cudaFree(tmp_prim);
   return rc;
 }
 
-// Per frame: previous pose kept, moved objects transformed; the tree is
-// refitted, or rebuilt from world-space Morton codes (PV_BUILD_DYN_REBUILD).
+// Per frame: previous pose kept, moved objects transformed; the dynamic tree
+// is refitted, or rebuilt from world-space Morton codes
+// (PV_BUILD_DYN_REBUILD); then the top level is rebuilt.
 void launch_update_dynamic(pv_scene* s, cudaStream_t st) {
   const uint32_t n = s->n_dyn_tris;
-  if (n == 0) return;
-  XformParams P;
-  std::memset(&P, 0, sizeof P);
-  for (uint32_t sl = 0; sl < s->n_dyn; ++sl) std::memcpy(P.xf[sl], &s->h_xf_new[12 * sl], 12 * sizeof(float));
-  P.moved = s->moved;
-  P.n_dyn = s->n_dyn;
-  k_update_objects<<<s->n_dyn, 256, 0, st>>>(P, s->d_local, s->d_tri_prim, s->d_tris, s->objs, s->xf_old, s->xf_new);
-  if (!s->moved) return;
-  if (s->flags & PV_BUILD_DYN_REBUILD) {
-    uint64_t *k0 = s->r_keys[0], *k1 = s->r_keys[1];
-    uint32_t *v0 = s->r_vals[0], *v1 = s->r_vals[1];
-    k_morton_dyn<<<blocks(n, 256), 256, 0, st>>>(nullptr, s->d_tris, s->d_tri_slot, n, nullptr, s->objs, 1, k0, v0);
-    radix_sort(k0, v0, k1, v1, n, s->r_hist, 0, 64, st);
-    k_gather_dyn<<<blocks(n, 256), 256, 0, st>>>(v0, n, s->d_local, s->d_tri_prim, s->d_tris, s->r_local, s->r_prim, s->r_tris);
-    std::swap(s->d_local, s->r_local);
-    std::swap(s->d_tri_prim, s->r_prim);
-    std::swap(s->d_tris, s->r_tris);
-    if (n >= 2) k_karras<<<blocks(n - 1, 256), 256, 0, st>>>(k0, (int)n, s->d_nodes, s->d_node_parent, s->d_leaf_parent, s->d_tri_slot, s->objs);
+  Tri* dtris = s->tris + s->d_tri_off;
+  Node* dnodes = s->nodes + s->d_node_off;
+  const bool collapse = s->moved && (!s->top_built || (s->flags & PV_BUILD_DYN_REBUILD));
+  if (n) {
+    XformParams P;
+    std::memset(&P, 0, sizeof P);
+    for (uint32_t sl = 0; sl < s->n_dyn; ++sl) std::memcpy(P.xf[sl], &s->h_xf_new[12 * sl], 12 * sizeof(float));
+    P.moved = s->moved;
+    P.n_dyn = s->n_dyn;
+    k_update_objects<<<s->n_dyn, 256, 0, st>>>(P, s->d_local, s->d_tri_prim, dtris, s->objs, s->xf_old, s->xf_new);
+    if (s->moved) {
+      if (s->flags & PV_BUILD_DYN_REBUILD) {
+        uint64_t *k0 = s->r_keys[0], *k1 = s->r_keys[1];
+        uint32_t *v0 = s->r_vals[0], *v1 = s->r_vals[1];
+        k_morton_dyn<<<blocks(n, 256), 256, 0, st>>>(nullptr, dtris, s->d_tri_slot, n, nullptr, s->objs, 1, k0, v0);
+        radix_sort(k0, v0, k1, v1, n, s->r_hist, 0, 64, st);
+        k_gather_dyn<<<blocks(n, 256), 256, 0, st>>>(v0, n, s->d_local, s->d_tri_prim, dtris, s->r_local, s->r_prim, s->r_tris);
+        std::swap(s->d_local, s->r_local);
+        std::swap(s->d_tri_prim, s->r_prim);
+        cudaMemcpyAsync(dtris, s->r_tris, n * sizeof(Tri), cudaMemcpyDeviceToDevice, st);
+        if (n >= 2)
+          k_karras<<<blocks(n - 1, 256), 256, 0, st>>>(k0, (int)n, s->nodes, (int)s->d_node_off, (int)s->d_tri_off,
+                                                       s->d_node_parent, s->d_leaf_parent, s->d_tri_slot, s->objs);
+      }
+      if (n >= 2) {
+        cudaMemsetAsync(s->d_fit_flags, 0, n * sizeof(uint32_t), st);
+        k_fit<<<blocks(n, 256), 256, 0, st>>>(dnodes, s->d_node_parent, s->d_leaf_parent, s->d_fit_flags, dtris, nullptr,
+                                              (int)n);
+      }
+      if (collapse) {
+        // wide nodes of the dynamic objects (topology from the binary tree)
+        k_collapse<<<1, 1024, 0, st>>>(s->nodes, (int)s->d_tri_off, 0, s->objs, (int)s->n_dyn, s->cq,
+                                       s->cq + 2 * s->q_cap, s->q_cap, s->wnodes, s->wsrc + 4 * (size_t)s->w_dyn_off,
+                                       (int)s->w_dyn_off, s->wcount + 1, s->status);
+      } else if (n > (uint32_t)kLeafMax) {
+        // refit: refresh the wide boxes from the binary slots
+        const uint32_t cap = s->w_top_off - s->w_dyn_off;
+        k_wide_refit<<<blocks(std::max<uint32_t>(cap, 1), 256), 256, 0, st>>>(s->nodes, s->wsrc + 4 * (size_t)s->w_dyn_off,
+                                                                             s->wcount + 1, s->wnodes + s->w_dyn_off);
+      }
+    }
   }
-  if (n >= 2) {
-    cudaMemsetAsync(s->d_fit_flags, 0, n * sizeof(uint32_t), st);
-    k_fit<<<blocks(n, 256), 256, 0, st>>>(s->d_nodes, s->d_node_parent, s->d_leaf_parent, s->d_fit_flags, s->d_tris, (int)n);
+  if (s->moved || !s->top_built) {
+    k_build_top<<<1, 32, 0, st>>>(s->wnodes, s->tris, (int)s->w_top_off, s->s_wroot, s->objs, (int)s->n_dyn, s->root);
+    s->top_built = true;
   }
 }
 

@@ -22,10 +22,11 @@ __device__ __forceinline__ int texel(float p, float lo, float hi, uint32_t res) 
 __global__ void __launch_bounds__(256) k_deposit(uint32_t n, uint32_t B, const uint32_t* info, const float4* pa,
                                                  const float4* pb, pv_atlas at) {
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const uint32_t L = min(info_nseg(info[p]), B);
+    const uint32_t L = min(info_nseg(__ldcs(info + p)), B);
     for (uint32_t k = 0; k < L; ++k) {
-      const float4 x = pa[(size_t)k * n + p];
-      const float4 e = pb[(size_t)k * n + p];
+      // streaming loads: the path buffers must not evict the atlas from L2
+      const float4 x = __ldcs(pa + (size_t)k * n + p);
+      const float4 e = __ldcs(pb + (size_t)k * n + p);
       const int tx = texel(x.x, at.x0, at.x1, at.width);
       const int tz = texel(x.z, at.z0, at.z1, at.height);
       unsigned long long* t = reinterpret_cast<unsigned long long*>(at.data) + 3 * ((size_t)tz * at.width + tx);

@@ -32,11 +32,33 @@ struct __align__(16) Tri {
   float4 e2;
 };
 
+// Wide (4-child) traversal node, 128 B = one cache line: the four child
+// boxes stored per coordinate, then the four child references.  A reference
+// >= 0 is a wide node; < 0 is a leaf range ~(first | (count - 1) << 29) of
+// 1..4 consecutive triangles.  Unused slots carry an empty box.
+struct __align__(128) WNode {
+  float4 lox, hix, loy, hiy, loz, hiz;
+  int4 child;
+  int4 pad;
+};
+
+#ifndef PV_LEAF_MAX
+#define PV_LEAF_MAX 1
+#endif
+constexpr int kLeafMax = PV_LEAF_MAX;   // triangles per wide leaf range
+
+__host__ __device__ __forceinline__ int leaf_ref(uint32_t first, uint32_t count) {
+  return ~(int)(first | ((count - 1u) << 29));
+}
+__host__ __device__ __forceinline__ uint32_t leaf_first(int ref) { return (uint32_t)(~ref) & 0x1FFFFFFFu; }
+__host__ __device__ __forceinline__ uint32_t leaf_count(int ref) { return ((uint32_t)(~ref) >> 29) + 1u; }
+
 // per dynamic object ("slot"), resident on the device
 struct DynObj {
   uint32_t user_object;
   uint32_t tri_begin, tri_count;
-  int32_t root;              // child-index encoding into the dynamic node array
+  int32_t root;              // binary subtree root (child-index encoding), INT32_MIN if none
+  int32_t wroot;             // wide subtree root reference, INT32_MIN if none
   float box_new[6];          // tight world box of the current pose (lo xyz, hi xyz)
   float box_old[6];          // tight world box of the previous pose
 };
@@ -61,11 +83,9 @@ struct FrameLights {
 
 // read-only scene view passed by value to the kernels
 struct SceneView {
-  const Node* s_nodes;
-  const Tri* s_tris;
-  int32_t s_root;            // child-index encoding; INT32_MIN = empty
-  const Node* d_nodes;
-  const Tri* d_tris;
+  const WNode* nodes;        // wide nodes [static tree | dynamic objects | top level]
+  const Tri* tris;           // [static references | dynamic triangles]
+  const int* root;           // device word: root child index of the whole scene (INT32_MIN = empty)
   const DynObj* objs;
   uint32_t n_dyn;
   const uint8_t* prim_slot;  // [n_tris] 255 = static, else dynamic slot
@@ -182,20 +202,24 @@ __device__ __forceinline__ Ray make_ray(float3 o, float3 d, float tmin) {
   return r;
 }
 
-// Both child boxes of a node against the ray within [tmin, tmax].
-__device__ __forceinline__ void box2(const Ray& r, float tmax, const Node& n, bool& h0, bool& h1, float& t0, float& t1) {
-  const float ax0 = fmaf(n.a.x, r.inv.x, r.ooi.x), ax1 = fmaf(n.a.y, r.inv.x, r.ooi.x);
-  const float ay0 = fmaf(n.a.z, r.inv.y, r.ooi.y), ay1 = fmaf(n.a.w, r.inv.y, r.ooi.y);
-  const float az0 = fmaf(n.c.x, r.inv.z, r.ooi.z), az1 = fmaf(n.c.y, r.inv.z, r.ooi.z);
-  const float bx0 = fmaf(n.b.x, r.inv.x, r.ooi.x), bx1 = fmaf(n.b.y, r.inv.x, r.ooi.x);
-  const float by0 = fmaf(n.b.z, r.inv.y, r.ooi.y), by1 = fmaf(n.b.w, r.inv.y, r.ooi.y);
-  const float bz0 = fmaf(n.c.z, r.inv.z, r.ooi.z), bz1 = fmaf(n.c.w, r.inv.z, r.ooi.z);
-  t0 = fmaxf(fmaxf(fminf(ax0, ax1), fminf(ay0, ay1)), fmaxf(fminf(az0, az1), r.tmin));
-  const float e0 = fminf(fminf(fmaxf(ax0, ax1), fmaxf(ay0, ay1)), fminf(fmaxf(az0, az1), tmax));
-  t1 = fmaxf(fmaxf(fminf(bx0, bx1), fminf(by0, by1)), fmaxf(fminf(bz0, bz1), r.tmin));
-  const float e1 = fminf(fminf(fmaxf(bx0, bx1), fmaxf(by0, by1)), fminf(fmaxf(bz0, bz1), tmax));
-  h0 = t0 <= e0;
-  h1 = t1 <= e1;
+// The four child boxes of a wide node against the ray within [tmin, tmax]:
+// entry distances, hit mask (bit c = child c).
+__device__ __forceinline__ uint32_t box4(const Ray& r, float tmax, const WNode& n, float t[4]) {
+  const float lx[4] = {n.lox.x, n.lox.y, n.lox.z, n.lox.w}, hx[4] = {n.hix.x, n.hix.y, n.hix.z, n.hix.w};
+  const float ly[4] = {n.loy.x, n.loy.y, n.loy.z, n.loy.w}, hy[4] = {n.hiy.x, n.hiy.y, n.hiy.z, n.hiy.w};
+  const float lz[4] = {n.loz.x, n.loz.y, n.loz.z, n.loz.w}, hz[4] = {n.hiz.x, n.hiz.y, n.hiz.z, n.hiz.w};
+  uint32_t mask = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float x0 = fmaf(lx[c], r.inv.x, r.ooi.x), x1 = fmaf(hx[c], r.inv.x, r.ooi.x);
+    const float y0 = fmaf(ly[c], r.inv.y, r.ooi.y), y1 = fmaf(hy[c], r.inv.y, r.ooi.y);
+    const float z0 = fmaf(lz[c], r.inv.z, r.ooi.z), z1 = fmaf(hz[c], r.inv.z, r.ooi.z);
+    const float tn = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), r.tmin));
+    const float tf = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tmax));
+    t[c] = tn;
+    mask |= (tn <= tf ? 1u : 0u) << c;
+  }
+  return mask;
 }
 
 // One box (lo xyz, hi xyz) against the ray within [tmin, tmax]; entry distance.
@@ -225,13 +249,16 @@ __device__ __forceinline__ bool tri_hit(const Ray& r, const Tri& T, float tmax, 
   return t > r.tmin && t < tmax;
 }
 
-__device__ __forceinline__ Node load_node(const Node* nodes, int i) {
+__device__ __forceinline__ WNode load_wnode(const WNode* nodes, int i) {
   const float4* p = reinterpret_cast<const float4*>(nodes + i);
-  Node n;
-  n.a = __ldg(p);
-  n.b = __ldg(p + 1);
-  n.c = __ldg(p + 2);
-  n.d = __ldg(reinterpret_cast<const int4*>(p + 3));
+  WNode n;
+  n.lox = __ldg(p);
+  n.hix = __ldg(p + 1);
+  n.loy = __ldg(p + 2);
+  n.hiy = __ldg(p + 3);
+  n.loz = __ldg(p + 4);
+  n.hiz = __ldg(p + 5);
+  n.child = __ldg(reinterpret_cast<const int4*>(p + 6));
   return n;
 }
 
@@ -249,48 +276,94 @@ struct Work {
   uint32_t nodes = 0, tris = 0;
 };
 
-// Traverse one BVH from ``root``; ANY: stop at the first hit.  ``tbest`` is
-// the current closest distance (in/out), ``best`` the hit triangle index.
-// Returns false and records an error on stack overflow or visit cap.
+// Visit a wide node: push the hit children far-to-near, return the nearest
+// in ``next`` (INT32_MIN if none was hit).  False on stack overflow.  The
+// four (distance, child) pairs are ordered by a five-comparator sorting
+// network on registers, misses carrying an infinite distance.
+__device__ __forceinline__ void cswap(float& ka, int& va, float& kb, int& vb) {
+  const bool s = kb < ka;
+  const float k = s ? kb : ka;
+  const int v = s ? vb : va;
+  kb = s ? ka : kb;
+  vb = s ? va : vb;
+  ka = k;
+  va = v;
+}
+
+__device__ __forceinline__ bool visit_wide(const WNode& n, const Ray& r, float tbest, int* stk, int& sp, int& next) {
+  float t[4];
+  const uint32_t mask = box4(r, tbest, n, t);
+  const int m = __popc(mask);
+  if (m == 0) {
+    next = INT32_MIN;
+    return true;
+  }
+  const float inf = __int_as_float(0x7f800000);
+  float k0 = (mask & 1u) ? t[0] : inf, k1 = (mask & 2u) ? t[1] : inf;
+  float k2 = (mask & 4u) ? t[2] : inf, k3 = (mask & 8u) ? t[3] : inf;
+  int v0 = n.child.x, v1 = n.child.y, v2 = n.child.z, v3 = n.child.w;
+  cswap(k0, v0, k1, v1);
+  cswap(k2, v2, k3, v3);
+  cswap(k0, v0, k2, v2);
+  cswap(k1, v1, k3, v3);
+  cswap(k1, v1, k2, v2);
+  if (sp + m - 1 > kStack) return false;
+  if (m >= 4) stk[sp++] = v3;
+  if (m >= 3) stk[sp++] = v2;
+  if (m >= 2) stk[sp++] = v1;
+  next = v0;
+  return true;
+}
+
+// Test the triangles of a leaf range; true if the closest hit improved.
+__device__ __forceinline__ bool visit_leaf(const Tri* tris, int ref, const Ray& r, float& tbest, int& best, int exclude,
+                                           Work& wk) {
+  const uint32_t first = leaf_first(ref), cnt = leaf_count(ref);
+  bool any = false;
+  for (uint32_t i = 0; i < cnt; ++i) {
+    ++wk.tris;
+    const Tri T = load_tri(tris, (int)(first + i));
+    float t;
+    if (__float_as_int(T.v0.w) != exclude && tri_hit(r, T, tbest, t)) {
+      tbest = t;
+      best = (int)(first + i);
+      any = true;
+    }
+  }
+  return any;
+}
+
+// Traverse the wide tree from ``root``; ANY: stop at the first hit.
+// ``tbest`` is the current closest distance (in/out), ``best`` the hit
+// triangle index.  Returns false and records an error on stack overflow or
+// visit cap.
 template <bool ANY>
-__device__ __forceinline__ bool traverse(const Node* nodes, const Tri* tris, int root, const Ray& r, float& tbest,
+__device__ __forceinline__ bool traverse(const WNode* nodes, const Tri* tris, int root, const Ray& r, float& tbest,
                                          int& best, int exclude, uint32_t max_visits, int* status, Work& wk) {
   int stack[kStack];
   int sp = 0;
   int node = root;
   uint32_t visits = 0;
   for (;;) {
-    if (++visits > max_visits) {
-      record_error(status, PV_ERR_ITER_CAP);
-      return false;
-    }
-    if (node >= 0) {
-      ++wk.nodes;
-      const Node n = load_node(nodes, node);
-      bool h0, h1;
-      float t0, t1;
-      box2(r, tbest, n, h0, h1, t0, t1);
-      if (h0 && h1) {
-        const bool first0 = t0 <= t1;
-        if (sp == kStack) {
+    if (node != INT32_MIN) {
+      if (++visits > max_visits) {
+        record_error(status, PV_ERR_ITER_CAP);
+        return false;
+      }
+      if (node >= 0) {
+        ++wk.nodes;
+        const WNode n = load_wnode(nodes, node);
+        int next;
+        if (!visit_wide(n, r, tbest, stack, sp, next)) {
           record_error(status, PV_ERR_STACK);
           return false;
         }
-        stack[sp++] = first0 ? n.d.y : n.d.x;
-        node = first0 ? n.d.x : n.d.y;
-        continue;
-      }
-      if (h0) { node = n.d.x; continue; }
-      if (h1) { node = n.d.y; continue; }
-    } else {
-      const int ti = ~node;
-      ++wk.tris;
-      const Tri T = load_tri(tris, ti);
-      float t;
-      if (__float_as_int(T.v0.w) != exclude && tri_hit(r, T, tbest, t)) {
-        tbest = t;
-        best = ti;
-        if (ANY) return true;
+        if (next != INT32_MIN) {
+          node = next;
+          continue;
+        }
+      } else {
+        if (visit_leaf(tris, node, r, tbest, best, exclude, wk) && ANY) return true;
       }
     }
     if (sp == 0) return true;
@@ -298,54 +371,71 @@ __device__ __forceinline__ bool traverse(const Node* nodes, const Tri* tris, int
   }
 }
 
-// Hit record of the two-level query: which array, which triangle.
+// Hit record of a scene query: distance and triangle index (in sv.tris).
 struct Hit {
   float t;
-  int tri;        // index in the static (dyn == false) or dynamic triangle array
-  bool dyn;
+  int tri;
 };
 
-// Closest hit over the static BVH and every dynamic object's BVH at the
-// current pose.  ``boxes`` = the dynamic objects' current tight boxes (in
-// shared memory), 6 floats each.
-__device__ __forceinline__ bool closest_hit(const SceneView& sv, const float* boxes, const Ray& r, int exclude,
-                                            Hit& h, Work& wk) {
+// Closest hit over the whole scene (top level, static tree, dynamic objects).
+__device__ __forceinline__ bool closest_hit(const SceneView& sv, int root, const Ray& r, int exclude, Hit& h, Work& wk) {
   float tb = 3.0e38f;
   int best = -1;
-  bool dyn = false;
-  if (sv.s_root != INT32_MIN) traverse<false>(sv.s_nodes, sv.s_tris, sv.s_root, r, tb, best, exclude, sv.max_visits, sv.status, wk);
-  for (uint32_t s = 0; s < sv.n_dyn; ++s) {
-    float te;
-    if (sv.objs[s].root == INT32_MIN || !box1(r, tb, boxes + 6 * s, te)) continue;
-    int b2 = -1;
-    traverse<false>(sv.d_nodes, sv.d_tris, sv.objs[s].root, r, tb, b2, exclude, sv.max_visits, sv.status, wk);
-    if (b2 >= 0) {
-      best = b2;
-      dyn = true;
-    }
-  }
+  if (root != INT32_MIN) traverse<false>(sv.nodes, sv.tris, root, r, tb, best, exclude, sv.max_visits, sv.status, wk);
   h.t = tb;
   h.tri = best;
-  h.dyn = dyn;
   return best >= 0;
 }
 
-// Any hit of the open segment (tmin, tmax) over the static BVH and all
-// dynamic objects at the current pose.
-__device__ __forceinline__ bool any_hit_all(const SceneView& sv, const float* boxes, const Ray& r, float tmax, int exclude,
+// Any hit of the open segment (tmin, tmax) over the whole scene.
+__device__ __forceinline__ bool any_hit_all(const SceneView& sv, int root, const Ray& r, float tmax, int exclude,
                                             Work& wk) {
   float tb = tmax;
   int best = -1;
-  if (sv.s_root != INT32_MIN) {
-    traverse<true>(sv.s_nodes, sv.s_tris, sv.s_root, r, tb, best, exclude, sv.max_visits, sv.status, wk);
-    if (best >= 0) return true;
+  if (root != INT32_MIN) traverse<true>(sv.nodes, sv.tris, root, r, tb, best, exclude, sv.max_visits, sv.status, wk);
+  return best >= 0;
+}
+
+// Resumable traversal state of one ray (used by the persistent kernels).
+struct Trav {
+  int node, sp, best;
+  float tbest;
+  uint32_t visits;
+};
+
+__device__ __forceinline__ void trav_begin(Trav& t, int root) {
+  t.node = root;
+  t.sp = 0;
+  t.best = -1;
+  t.tbest = 3.0e38f;
+  t.visits = 0;
+}
+
+// One traversal step (one wide node or one leaf range); true once the ray is done.
+__device__ __forceinline__ bool trav_step(const SceneView& sv, const Ray& r, Trav& t, int* stk, int exclude, Work& wk) {
+  if (t.node != INT32_MIN) {
+    if (++t.visits > sv.max_visits) {
+      record_error(sv.status, PV_ERR_ITER_CAP);
+      return true;
+    }
+    if (t.node >= 0) {
+      ++wk.nodes;
+      const WNode n = load_wnode(sv.nodes, t.node);
+      int next;
+      if (!visit_wide(n, r, t.tbest, stk, t.sp, next)) {
+        record_error(sv.status, PV_ERR_STACK);
+        return true;
+      }
+      if (next != INT32_MIN) {
+        t.node = next;
+        return false;
+      }
+    } else {
+      visit_leaf(sv.tris, t.node, r, t.tbest, t.best, exclude, wk);
+    }
   }
-  for (uint32_t s = 0; s < sv.n_dyn; ++s) {
-    float te;
-    if (sv.objs[s].root == INT32_MIN || !box1(r, tb, boxes + 6 * s, te)) continue;
-    traverse<true>(sv.d_nodes, sv.d_tris, sv.objs[s].root, r, tb, best, exclude, sv.max_visits, sv.status, wk);
-    if (best >= 0) return true;
-  }
+  if (t.sp == 0) return true;
+  t.node = stk[--t.sp];
   return false;
 }
 
@@ -363,6 +453,29 @@ __device__ __forceinline__ void warp_add(uint32_t* ctr, uint32_t v) {
   const unsigned m = __activemask();
   const uint32_t s = __reduce_add_sync(m, v);
   if ((int)(threadIdx.x & 31) == __ffs(m) - 1 && s) atomicAdd(ctr, s);
+}
+
+// Block-wide sums of K per-thread counters with one pair of barriers, then one
+// atomic per non-zero counter per block (``sh`` = 32*K words of shared memory).
+template <int K>
+__device__ __forceinline__ void block_add_n(uint32_t* const (&ctr)[K], const uint32_t (&v)[K], uint32_t* sh) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  uint32_t s[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) s[k] = __reduce_add_sync(0xffffffffu, v[k]);
+  __syncthreads();
+  if (l == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[32 * k + w] = s[k];
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const uint32_t t = __reduce_add_sync(0xffffffffu, l < nw ? sh[32 * k + l] : 0u);
+      if (l == 0 && t && ctr[k]) atomicAdd(ctr[k], t);
+    }
+  }
 }
 
 // Block-wide 64-bit sum of per-thread counters, one atomic per block.

@@ -17,14 +17,23 @@ struct pv_scene {
   float diag = 0.f, tmin = 0.f, close_tol = 0.f;
   uint32_t flags = 0;
 
-  // static BVH
-  pvk::Node* s_nodes = nullptr;
-  pvk::Tri* s_tris = nullptr;
-  int32_t s_root = INT32_MIN;
+  // shared BVH arrays: triangles [static references | dynamic]; binary nodes
+  // [static | dynamic] (build and refit); wide nodes [static | dynamic | top] (traversal)
+  pvk::Node* nodes = nullptr;
+  pvk::WNode* wnodes = nullptr;
+  pvk::Tri* tris = nullptr;
+  int* root = nullptr;               // device word: wide root of the whole scene
+  int32_t s_root = INT32_MIN;        // static binary root (child index)
+  int32_t s_wroot = INT32_MIN;       // static wide root (reference)
+  uint32_t n_static_refs = 0, d_tri_off = 0, d_node_off = 0;
+  uint32_t w_dyn_off = 0, w_top_off = 0, n_wide = 0;
+  int* wsrc = nullptr;               // [n_wide][4] binary slot of each wide child (refit source)
+  uint32_t* wcount = nullptr;        // device: [0] static wide count, [1] dynamic wide count
+  int* cq = nullptr;                 // collapse queues, 2 x [q_cap][2]
+  uint32_t q_cap = 0;
+  bool top_built = false;
 
   // dynamic objects (one LBVH over all dynamic triangles, keyed by slot first)
-  pvk::Node* d_nodes = nullptr;
-  pvk::Tri* d_tris = nullptr;
   float* d_local = nullptr;          // [n_dyn_tris][9] object-local corners, BVH order
   uint32_t* d_tri_prim = nullptr;    // [n_dyn_tris] primitive id, BVH order
   uint32_t* d_leaf_parent = nullptr; // [n_dyn_tris] parent << 1 | side
@@ -41,7 +50,6 @@ struct pv_scene {
   pvk::Tri* r_tris = nullptr;
   float* r_local = nullptr;
   uint32_t* r_prim = nullptr;
-  int32_t* d_obj_root = nullptr;     // [n_dyn] roots found by the hierarchy pass
 
   // per primitive
   uint8_t* prim_slot = nullptr;
@@ -86,8 +94,7 @@ pvk::SceneView view(const pv_scene* s);
 pvk::FrameLights frame_lights(const pv_scene* s);
 
 // bvh.cu
-int build_static_bvh(pv_scene* s, const float* h_verts, const std::vector<uint32_t>& static_prims, cudaStream_t st);
-int build_dynamic_bvh(pv_scene* s, const float* h_verts, cudaStream_t st);
+int build_bvh(pv_scene* s, const float* h_verts, const std::vector<uint32_t>& static_prims, cudaStream_t st);
 void launch_update_dynamic(pv_scene* s, cudaStream_t st);
 
 // compact.cu

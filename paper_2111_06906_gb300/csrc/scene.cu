@@ -44,11 +44,10 @@ int check_lights(const pv_light* l, uint32_t n) {
 
 void free_scene(pv_scene* s) {
   if (!s) return;
-  void* ptrs[] = {s->s_nodes, s->s_tris, s->d_nodes, s->d_tris, s->d_local, s->d_tri_prim, s->d_leaf_parent,
-                  s->d_node_parent, s->d_fit_flags, s->d_tri_slot, s->objs, s->r_keys[0], s->r_keys[1], s->r_vals[0],
-                  s->r_vals[1], s->r_hist, s->r_tris, s->r_local, s->r_prim, s->d_obj_root, s->prim_slot,
-                  s->prim_dyn, s->prim_alb, s->prim_nrm, s->xf_old, s->xf_new, s->ws_mask, s->ws_cont, s->ws_tiles,
-                  s->ws_ctr, s->status};
+  void* ptrs[] = {s->nodes, s->wnodes, s->wsrc, s->wcount, s->cq, s->tris, s->root, s->d_local, s->d_tri_prim, s->d_leaf_parent, s->d_node_parent,
+                  s->d_fit_flags, s->d_tri_slot, s->objs, s->r_keys[0], s->r_keys[1], s->r_vals[0], s->r_vals[1],
+                  s->r_hist, s->r_tris, s->r_local, s->r_prim, s->prim_slot, s->prim_dyn, s->prim_alb, s->prim_nrm,
+                  s->xf_old, s->xf_new, s->ws_mask, s->ws_cont, s->ws_tiles, s->ws_ctr, s->status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete s;
@@ -60,11 +59,9 @@ namespace pvh {
 
 SceneView view(const pv_scene* s) {
   SceneView v;
-  v.s_nodes = s->s_nodes;
-  v.s_tris = s->s_tris;
-  v.s_root = s->s_root;
-  v.d_nodes = s->d_nodes;
-  v.d_tris = s->d_tris;
+  v.nodes = s->wnodes;
+  v.tris = s->tris;
+  v.root = s->root;
   v.objs = s->objs;
   v.n_dyn = s->n_dyn;
   v.prim_slot = s->prim_slot;
@@ -78,7 +75,7 @@ SceneView view(const pv_scene* s) {
   v.tmin = s->tmin;
   v.close_tol = s->close_tol;
   v.moved = s->moved;
-  v.max_visits = 2u * (s->n_static > s->n_dyn_tris ? s->n_static : s->n_dyn_tris) + 64u;
+  v.max_visits = 2u * (s->n_static_refs + s->n_dyn_tris) + 256u;
   v.status = s->status;
   return v;
 }
@@ -206,15 +203,16 @@ extern "C" int pv_build_scene(const pv_scene_desc* d, void* stream, pv_scene** o
   fail(cudaMemsetAsync(s->xf_new, 0, kMaxDyn * 12 * sizeof(float), st));
   fail(cudaMemsetAsync(s->status, 0, sizeof(int), st));
   fail(cudaMemsetAsync(s->ws_ctr, 0, 16 * sizeof(uint32_t), st));
-  if (rc == PV_OK) rc = pvh::build_static_bvh(s, d->verts, static_prims, st);
-  if (rc == PV_OK) rc = pvh::build_dynamic_bvh(s, d->verts, st);
-  if (rc == PV_OK && s->n_dyn_tris) {
-    // world triangles and boxes of the initial pose, then make it the old pose too
+  s->n_static = (uint32_t)static_prims.size();
+  if (rc == PV_OK) rc = pvh::build_bvh(s, d->verts, static_prims, st);
+  if (rc == PV_OK) {
+    // world triangles, boxes and top level of the initial pose, then make it the old pose too
     s->moved = s->n_dyn == 64 ? ~0ull : ((1ull << s->n_dyn) - 1ull);
     pvh::launch_update_dynamic(s, st);
     s->moved = 0;
     pvh::launch_update_dynamic(s, st);
-    k_invert<<<(s->n_dyn_tris + 255) / 256, 256, 0, st>>>(s->d_tri_prim, s->n_dyn_tris, s->prim_dyn);
+    if (s->n_dyn_tris)
+      k_invert<<<(s->n_dyn_tris + 255) / 256, 256, 0, st>>>(s->d_tri_prim, s->n_dyn_tris, s->prim_dyn);
     fail(cudaGetLastError());
   }
   if (rc == PV_OK) fail(cudaStreamSynchronize(st));

@@ -27,27 +27,17 @@ struct VerifyArgs {
   pv_frame_stats* stats;
 };
 
-// closed segment a + s (b - a), s in [0,1], against a closed box (slab test;
-// an axis the segment does not move along must contain the segment)
-__device__ __forceinline__ bool seg_box(float3 a, float3 dv, float3 inv, const float* bx) {
-  float t0 = 0.0f, t1 = 1.0f;
-  const float av[3] = {a.x, a.y, a.z}, dd[3] = {dv.x, dv.y, dv.z}, iv[3] = {inv.x, inv.y, inv.z};
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    if (bx[k] > bx[3 + k]) return false;            // empty box
-    if (dd[k] == 0.0f) {
-      if (av[k] < bx[k] || av[k] > bx[3 + k]) return false;
-      continue;
-    }
-    float u0 = (bx[k] - av[k]) * iv[k], u1 = (bx[3 + k] - av[k]) * iv[k];
-    if (u0 > u1) {
-      const float t = u0;
-      u0 = u1;
-      u1 = t;
-    }
-    t0 = fmaxf(t0, u0);
-    t1 = fminf(t1, u1);
-  }
+// Closed segment a + s (b - a), s in [0,1], against a closed box: slab test
+// with the reciprocal direction precomputed (a component below 1e-20 gets the
+// reciprocal 1e20 of its sign, which keeps the axis' interval around [0,1]
+// when a lies inside the slab and away from it when a lies outside; only a
+// segment lying exactly in a face plane can be decided differently).
+__device__ __forceinline__ bool seg_box(float3 inv, float3 aoi, const float* bx) {
+  const float x0 = fmaf(bx[0], inv.x, aoi.x), x1 = fmaf(bx[3], inv.x, aoi.x);
+  const float y0 = fmaf(bx[1], inv.y, aoi.y), y1 = fmaf(bx[4], inv.y, aoi.y);
+  const float z0 = fmaf(bx[2], inv.z, aoi.z), z1 = fmaf(bx[5], inv.z, aoi.z);
+  const float t0 = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.0f));
+  const float t1 = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), 1.0f));
   return t0 <= t1;
 }
 
@@ -59,12 +49,16 @@ __device__ bool seg_vs_moved(const SceneView& sv, const float* cull, const float
   const float3 dv = b - a;
   uint64_t m = sv.moved;
   if (boxes) {
-    const float3 inv = make_float3(dv.x != 0.f ? 1.0f / dv.x : 0.f, dv.y != 0.f ? 1.0f / dv.y : 0.f,
-                                   dv.z != 0.f ? 1.0f / dv.z : 0.f);
+    const float e = 1e-20f;                 // |1/d| <= 1e20 keeps a * inv finite for any scene size
+    const float3 inv = make_float3(__frcp_rn(fabsf(dv.x) > e ? dv.x : copysignf(e, dv.x)),
+                                   __frcp_rn(fabsf(dv.y) > e ? dv.y : copysignf(e, dv.y)),
+                                   __frcp_rn(fabsf(dv.z) > e ? dv.z : copysignf(e, dv.z)));
+    const float3 aoi = make_float3(-a.x * inv.x, -a.y * inv.y, -a.z * inv.z);
+    if (!seg_box(inv, aoi, uni + 6 * kMaxDyn)) return false;     // union of all moved boxes
     while (m) {
       const int s = __ffsll((long long)m) - 1;
       m &= m - 1;
-      if (seg_box(a, dv, inv, uni + 6 * s)) return true;
+      if (seg_box(inv, aoi, uni + 6 * s)) return true;
     }
     return false;
   }
@@ -78,10 +72,10 @@ __device__ bool seg_vs_moved(const SceneView& sv, const float* cull, const float
     const int s = __ffsll((long long)m) - 1;
     m &= m - 1;
     float te;
-    if (sv.objs[s].root != INT32_MIN && box1(r, tmax, cull + 6 * s, te)) {
+    if (sv.objs[s].wroot != INT32_MIN && box1(r, tmax, cull + 6 * s, te)) {
       float tb = tmax;
       int best = -1;
-      traverse<true>(sv.d_nodes, sv.d_tris, sv.objs[s].root, r, tb, best, -1, sv.max_visits, sv.status, wk);
+      traverse<true>(sv.nodes, sv.tris, sv.objs[s].wroot, r, tb, best, -1, sv.max_visits, sv.status, wk);
       if (best >= 0) return true;
     }
     if (test_old) {
@@ -111,18 +105,32 @@ __device__ __forceinline__ uint32_t* field(pv_frame_stats* s, size_t off) {
   return s ? reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(s) + off) : nullptr;
 }
 
+// kPointVis: a moved point light needs visibility rays; kExact: segments are
+// tested against triangles (not only boxes).  Specialised so the common case
+// carries no traversal code.
+template <bool kPointVis, bool kExact>
 __global__ void __launch_bounds__(pvh::kVerifyThreads) k_verify(SceneView sv, FrameLights L, VerifyArgs A) {
   __shared__ float s_cull[kMaxDyn * 6];
-  __shared__ float s_uni[kMaxDyn * 6];
-  __shared__ uint32_t s_red[32];
+  __shared__ float s_uni[(kMaxDyn + 1) * 6];
+  __shared__ uint32_t s_red[32 * 6];
   __shared__ unsigned long long s_red64[32];
   load_boxes(sv, s_cull, s_uni);
   __syncthreads();
+  if (threadIdx.x < 6) {                 // union of the moved objects' old u new boxes
+    const int k = threadIdx.x;
+    float v = k < 3 ? 3.0e38f : -3.0e38f;
+    for (uint64_t m = sv.moved; m; m &= m - 1) {
+      const float x = s_uni[6 * (__ffsll((long long)m) - 1) + k];
+      v = k < 3 ? fminf(v, x) : fmaxf(v, x);
+    }
+    s_uni[6 * kMaxDyn + k] = v;
+  }
+  __syncthreads();
   Work wk;
+  const int root = *sv.root;
   const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t n = A.n;
-  const bool boxes = A.mode == PV_MODE_NAIVE_AABB || (A.mode == PV_MODE_ERROR && !(A.flags & PV_FLAG_ERROR_EXACT));
-  const bool test_old = (A.flags & PV_FLAG_TEST_OLD_TRIS) != 0;
+  const bool test_old = kExact && (A.flags & PV_FLAG_TEST_OLD_TRIS) != 0;
   uint32_t c_tested = 0, c_vis = 0, c_reemit = 0, c_tail = 0;
   bool want_cont = false;
   if (p < n) {
@@ -140,13 +148,15 @@ __global__ void __launch_bounds__(pvh::kVerifyThreads) k_verify(SceneView sv, Fr
         const LightPose& Ln = L.cur[l];
         if (Ln.type == PV_LIGHT_POINT) {
           o = Ln.pos;
-          const float3 dv = x1 - o;
-          const float len = sqrtf(dot(dv, dv));
-          if (len > 0.0f) {
-            const Ray r = make_ray(o, make_float3(dv.x / len, dv.y / len, dv.z / len), sv.tmin);
-            blocked1 = any_hit_all(sv, s_cull, r, len - sv.tmin, __float_as_int(x1v.w), wk);
+          if (kPointVis) {
+            const float3 dv = x1 - o;
+            const float len = sqrtf(dot(dv, dv));
+            if (len > 0.0f) {
+              const Ray r = make_ray(o, make_float3(dv.x / len, dv.y / len, dv.z / len), sv.tmin);
+              blocked1 = any_hit_all(sv, root, r, len - sv.tmin, __float_as_int(x1v.w), wk);
+            }
+            ++c_vis;
           }
-          ++c_vis;
         } else {
           const float3 d = normalize_exact(x1 - o);
           const float nd = dot(Ln.n, d);
@@ -192,7 +202,8 @@ __global__ void __launch_bounds__(pvh::kVerifyThreads) k_verify(SceneView sv, Fr
         bool hit = slot_moved(sv, prim_b) || (k >= 2 && slot_moved(sv, prim_a)) || (k == 1 && blocked1);
         if (!hit && sv.moved) {
           ++c_tested;
-          hit = seg_vs_moved(sv, s_cull, s_uni, boxes, test_old, a, b, wk);
+          hit = kExact ? seg_vs_moved(sv, s_cull, s_uni, false, test_old, a, b, wk)
+                       : seg_vs_moved(sv, s_cull, s_uni, true, false, a, b, wk);
         }
         if (hit) {
           mask |= 1u << k;
@@ -227,14 +238,18 @@ __global__ void __launch_bounds__(pvh::kVerifyThreads) k_verify(SceneView sv, Fr
     base = __shfl_sync(0xffffffffu, base, leader);
     if (want_cont) A.cont_list[base + __popc(wm & ((1u << lane) - 1u))] = p;
   }
-  block_add(field(A.stats, offsetof(pv_frame_stats, n_paths)), p < n ? 1u : 0u, s_red);
-  block_add(field(A.stats, offsetof(pv_frame_stats, segments_tested)), c_tested, s_red);
-  block_add(field(A.stats, offsetof(pv_frame_stats, vis_rays)), c_vis, s_red);
-  block_add(field(A.stats, offsetof(pv_frame_stats, n_reemit)), c_reemit, s_red);
-  block_add(field(A.stats, offsetof(pv_frame_stats, n_tail)), c_tail, s_red);
-  block_add(field(A.stats, offsetof(pv_frame_stats, n_cont)), want_cont ? 1u : 0u, s_red);
-  block_add64(A.stats ? (unsigned long long*)&A.stats->node_visits : nullptr, wk.nodes, s_red64);
-  block_add64(A.stats ? (unsigned long long*)&A.stats->tri_tests : nullptr, wk.tris, s_red64);
+  uint32_t* const ctr[6] = {field(A.stats, offsetof(pv_frame_stats, n_paths)),
+                            field(A.stats, offsetof(pv_frame_stats, segments_tested)),
+                            field(A.stats, offsetof(pv_frame_stats, vis_rays)),
+                            field(A.stats, offsetof(pv_frame_stats, n_reemit)),
+                            field(A.stats, offsetof(pv_frame_stats, n_tail)),
+                            field(A.stats, offsetof(pv_frame_stats, n_cont))};
+  const uint32_t val[6] = {p < n ? 1u : 0u, c_tested, c_vis, c_reemit, c_tail, want_cont ? 1u : 0u};
+  block_add_n<6>(ctr, val, s_red);
+  if (kPointVis || kExact) {
+    block_add64(A.stats ? (unsigned long long*)&A.stats->node_visits : nullptr, wk.nodes, s_red64);
+    block_add64(A.stats ? (unsigned long long*)&A.stats->tri_tests : nullptr, wk.tris, s_red64);
+  }
 }
 
 struct ContArgs {
@@ -251,71 +266,77 @@ struct ContArgs {
   pv_frame_stats* stats;
 };
 
-// Alg. 1 for one path whose intersected segments are ``mask``.
-__device__ void continue_path(const SceneView& sv, const float* cull, const ContArgs& A, uint32_t p, uint32_t& c_rays,
+// Alg. 1 for one path whose intersected segments are ``mask``.  Vertices are
+// read from and updated in the path buffer as the loop advances; only the
+// origin of the current segment (current and original position) is carried
+// in registers.
+__device__ void continue_path(const SceneView& sv, int root, const ContArgs& A, uint32_t p, uint32_t& c_rays,
                               uint32_t& c_tail, uint32_t& c_upd, uint32_t& c_trunc, Work& wk) {
   const uint32_t n = A.n;
   const uint32_t w = A.info[p];
   const uint32_t cell = w & PV_INFO_CELL_MASK;
   uint32_t nseg = min(info_nseg(w), sv.B);
   const uint32_t mask = A.mask[p];
-  float3 xo[PV_MAX_BOUNCES + 1], xc[PV_MAX_BOUNCES + 1];
-  int po[PV_MAX_BOUNCES + 1], pc[PV_MAX_BOUNCES + 1];
-  xo[0] = make_float3(A.origin[p], A.origin[n + p], A.origin[2 * (size_t)n + p]);
-  po[0] = -1;
-  for (uint32_t k = 1; k <= nseg; ++k) {
-    const float4 v = A.pa[(size_t)(k - 1) * n + p];
-    xo[k] = f3(v);
-    po[k] = __float_as_int(v.w);
-  }
-  for (uint32_t k = 0; k <= nseg; ++k) {
-    xc[k] = xo[k];
-    pc[k] = po[k];
-  }
+  const float3 org = make_float3(A.origin[p], A.origin[n + p], A.origin[2 * (size_t)n + p]);
+  auto vertex = [&](uint32_t k) -> float4 {        // stored vertex k (0 = origin)
+    return k == 0 ? make_float4(org.x, org.y, org.z, __int_as_float(-1)) : A.pa[(size_t)(k - 1) * n + p];
+  };
   uint32_t moved_origin = 0;
-  bool updated = false;
+  bool updated = false, a_valid = false;
   int done = 0;
+  float3 a_cur = org, a_orig = org;
+  int a_prim = -1;
   uint32_t seg = __ffs(mask) - 1;
   while (seg <= nseg) {
     if (!((mask >> seg) & 1u) && !((moved_origin >> seg) & 1u)) {
       ++seg;
+      a_valid = false;
       continue;
     }
-    const float3 a = xc[seg - 1], b = xc[seg];
-    const float3 d = normalize_exact(b - a);
-    const Ray r = make_ray(a, d, sv.tmin);
+    if (!a_valid) {
+      const float4 v = vertex(seg - 1);
+      a_cur = a_orig = f3(v);
+      a_prim = __float_as_int(v.w);
+    }
+    const float4 bv = vertex(seg);
+    const float3 b = f3(bv);
+    const int b_prim = __float_as_int(bv.w);
+    const float3 d = normalize_exact(b - a_cur);
+    const Ray r = make_ray(a_cur, d, sv.tmin);
     Hit h;
     ++c_rays;
-    if (!closest_hit(sv, cull, r, seg == 1 ? -1 : pc[seg - 1], h, wk)) {   // escaped: the path ends here
+    if (!closest_hit(sv, root, r, seg == 1 ? -1 : a_prim, h, wk)) {   // escaped: the path ends here
       nseg = seg - 1;
       ++c_trunc;
       done = 1;
       break;
     }
-    const Tri T = load_tri(h.dyn ? sv.d_tris : sv.s_tris, h.tri);
+    const Tri T = load_tri(sv.tris, h.tri);
     const int pn = __float_as_int(T.v0.w);
-    const float3 xn = make_float3(fmaf(h.t, d.x, a.x), fmaf(h.t, d.y, a.y), fmaf(h.t, d.z, a.z));
-    const bool close = pn == pc[seg] && maxabs3(xn - b) <= sv.close_tol;
+    const float3 xn = make_float3(fmaf(h.t, d.x, a_cur.x), fmaf(h.t, d.y, a_cur.y), fmaf(h.t, d.z, a_cur.z));
+    const bool close = pn == b_prim && maxabs3(xn - b) <= sv.close_tol;
     if (seg == nseg) {                                                  // last photon: move it
       A.pa[(size_t)(seg - 1) * n + p] = make_float4(xn.x, xn.y, xn.z, __int_as_float(pn));
       updated = true;
       done = 1;
       break;
     }
+    const float4 cv = vertex(seg + 1);                                  // stored next photon
+    const float3 c = f3(cv);
     const float3 EO = f3(A.pb[(size_t)seg * n + p]);
     float3 EN = EO;
     if (!close) {
       const float4 albn = __ldg(sv.prim_alb + pn);
       const float3 nn = normalize(cross(f3(T.e1), f3(T.e2)));
       const float3 nsn = dot(nn, d) < 0.0f ? nn : -1.0f * nn;
-      const float3 wv = xc[seg + 1] - xn;
+      const float3 wv = c - xn;
       const float wl = sqrtf(dot(wv, wv));
       const float cosn = wl > 0.0f ? fmaxf(0.0f, dot(nsn, (1.0f / wl) * wv)) : 0.0f;
-      const float4 albo = __ldg(sv.prim_alb + po[seg]);
-      const float3 no = normalize(prim_normal(sv, po[seg], true));
-      const float3 dino = normalize_exact(xo[seg] - xo[seg - 1]);
+      const float4 albo = __ldg(sv.prim_alb + b_prim);
+      const float3 no = normalize(prim_normal(sv, b_prim, true));
+      const float3 dino = normalize_exact(b - a_orig);
       const float3 nso = dot(no, dino) < 0.0f ? no : -1.0f * no;
-      const float coso = dot(nso, normalize_exact(xo[seg + 1] - xo[seg]));
+      const float coso = dot(nso, normalize_exact(c - b));
       const float3 Ei = f3(A.pb[(size_t)(seg - 1) * n + p]);
       const float f = coso > 0.0f ? cosn / (albo.w * coso) : 0.0f;
       EN = make_float3(Ei.x * albn.x * f, Ei.y * albn.y * f, Ei.z * albn.z * f);
@@ -327,13 +348,16 @@ __device__ void continue_path(const SceneView& sv, const float* cull, const Cont
       done = 2;
       break;
     }
-    if (close && !((mask >> (seg + 1)) & 1u) && !slot_moved(sv, pn) && !slot_moved(sv, pc[seg + 1])) {
+    if (close && !((mask >> (seg + 1)) & 1u) && !slot_moved(sv, pn) && !slot_moved(sv, __float_as_int(cv.w))) {
       seg += 2;                                                         // next segment known valid
+      a_valid = false;
       continue;
     }
     A.pa[(size_t)(seg - 1) * n + p] = make_float4(xn.x, xn.y, xn.z, __int_as_float(pn));
-    xc[seg] = xn;
-    pc[seg] = pn;
+    a_cur = xn;                                                         // origin of the next segment moved
+    a_orig = b;
+    a_prim = pn;
+    a_valid = true;
     updated = true;
     moved_origin |= 1u << (seg + 1);
     ++seg;
@@ -345,11 +369,9 @@ __device__ void continue_path(const SceneView& sv, const float* cull, const Cont
 }
 
 __global__ void __launch_bounds__(128) k_continue(SceneView sv, ContArgs A) {
-  __shared__ float s_cull[kMaxDyn * 6];
-  __shared__ uint32_t s_red[32];
+  __shared__ uint32_t s_red[32 * 4];
   __shared__ unsigned long long s_red64[32];
-  load_boxes(sv, s_cull, nullptr);
-  __syncthreads();
+  const int root = *sv.root;
   const uint32_t total = *A.count;
   const int lane = threadIdx.x & 31;
   uint32_t c_rays = 0, c_tail = 0, c_upd = 0, c_trunc = 0;
@@ -360,13 +382,13 @@ __global__ void __launch_bounds__(128) k_continue(SceneView sv, ContArgs A) {
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= total) break;
     const uint32_t i = base + lane;
-    if (i < total) continue_path(sv, s_cull, A, A.list[i], c_rays, c_tail, c_upd, c_trunc, wk);
+    if (i < total) continue_path(sv, root, A, A.list[i], c_rays, c_tail, c_upd, c_trunc, wk);
     __syncwarp();
   }
-  block_add(A.stats ? &A.stats->cont_rays : nullptr, c_rays, s_red);
-  block_add(A.stats ? &A.stats->n_tail : nullptr, c_tail, s_red);
-  block_add(A.stats ? &A.stats->n_updated : nullptr, c_upd, s_red);
-  block_add(A.stats ? &A.stats->n_truncated : nullptr, c_trunc, s_red);
+  uint32_t* const ctr[4] = {A.stats ? &A.stats->cont_rays : nullptr, A.stats ? &A.stats->n_tail : nullptr,
+                            A.stats ? &A.stats->n_updated : nullptr, A.stats ? &A.stats->n_truncated : nullptr};
+  const uint32_t val[4] = {c_rays, c_tail, c_upd, c_trunc};
+  block_add_n<4>(ctr, val, s_red);
   block_add64(A.stats ? (unsigned long long*)&A.stats->node_visits : nullptr, wk.nodes, s_red64);
   block_add64(A.stats ? (unsigned long long*)&A.stats->tri_tests : nullptr, wk.tris, s_red64);
 }
@@ -407,7 +429,18 @@ extern "C" int pv_verify_paths(pv_scene* s, const pv_paths* paths, const pv_veri
   A.cont_list = s->ws_cont;
   A.cont_count = s->ws_ctr + pvh::CTR_ALL;
   A.stats = d_stats;
-  if (n) k_verify<<<(n + pvh::kVerifyThreads - 1) / pvh::kVerifyThreads, pvh::kVerifyThreads, 0, st>>>(sv, L, A);
+  if (n) {
+    bool point_vis = false;
+    for (uint32_t l = 0; l < s->n_lights; ++l)
+      if (((L.moved_mask >> l) & 1u) && s->lights_new[l].type == PV_LIGHT_POINT) point_vis = true;
+    const bool exact = params->mode == PV_MODE_NAIVE_EXACT ||
+                       (params->mode == PV_MODE_ERROR && (params->flags & PV_FLAG_ERROR_EXACT));
+    const dim3 grid((n + pvh::kVerifyThreads - 1) / pvh::kVerifyThreads);
+    if (point_vis && exact) k_verify<true, true><<<grid, pvh::kVerifyThreads, 0, st>>>(sv, L, A);
+    else if (point_vis) k_verify<true, false><<<grid, pvh::kVerifyThreads, 0, st>>>(sv, L, A);
+    else if (exact) k_verify<false, true><<<grid, pvh::kVerifyThreads, 0, st>>>(sv, L, A);
+    else k_verify<false, false><<<grid, pvh::kVerifyThreads, 0, st>>>(sv, L, A);
+  }
   if (n && params->mode == PV_MODE_ERROR && (s->moved || L.moved_mask)) {
     if (!s->cont_blocks) {
       int per = 0;
