@@ -230,6 +230,13 @@ int pv_compact_replace_static(const uint32_t* d_info, uint32_t n, uint32_t* d_li
  * texel under it (stand-in for the renderer's splatting, Fig. 2). */
 int pv_deposit(pv_scene* s, const pv_paths* paths, const pv_atlas* atlas, void* stream);
 
+/* Cap the BVH node visits of every ray query (0 restores the default, which
+ * no query on a valid tree reaches).  A query that reaches the cap stops,
+ * counts as a miss and records PV_ERR_ITER_CAP in the device status: the way
+ * to exercise device-side error reporting without faulting the GPU.
+ * Returns PV_ERR_ARG for a null scene. */
+int pv_set_traversal_limit(pv_scene* s, uint32_t max_visits);
+
 /* Synchronise the scene's last stream and return the first device-side error
  * recorded since the last call (then clear it), or PV_OK. */
 int pv_read_device_status(pv_scene* s);

@@ -30,8 +30,8 @@ PV_INFO_NSEG_SHIFT, PV_INFO_START_SHIFT = 22, 26
 PV_INFO_REPLACE, PV_INFO_REUSE_LIGHT = 1 << 30, 1 << 31
 
 EXPORTS = ["pv_build_scene", "pv_update_dynamic", "pv_verify_paths", "pv_retrace_invalid", "pv_trace_all",
-           "pv_compact_replace", "pv_compact_replace_static", "pv_deposit", "pv_read_device_status",
-           "pv_destroy_scene", "pv_status_string"]
+           "pv_compact_replace", "pv_compact_replace_static", "pv_deposit", "pv_set_traversal_limit",
+           "pv_read_device_status", "pv_destroy_scene", "pv_status_string"]
 PV_STATIC_COMPACT_MAX_PATHS = 1 << 26
 
 
@@ -89,6 +89,7 @@ def load():
         L.pv_compact_replace.argtypes = [P, C.POINTER(PvPaths), P, P, P]
         L.pv_compact_replace_static.argtypes = [P, C.c_uint32, P, P, P]
         L.pv_deposit.argtypes = [P, C.POINTER(PvPaths), C.POINTER(PvAtlas), P]
+        L.pv_set_traversal_limit.argtypes = [P, C.c_uint32]
         L.pv_read_device_status.argtypes = [P]
         L.pv_destroy_scene.argtypes = [P]
         L.pv_destroy_scene.restype = None
@@ -233,6 +234,10 @@ def pv_deposit(scene, paths: Paths, atlas, rect, scale_log2: int, stream=None) -
     a = PvAtlas(atlas.data_ptr(), W, H, float(rect[0]), float(rect[1]), float(rect[2]), float(rect[3]),
                 int(scale_log2))
     _check("pv_deposit", load().pv_deposit(scene, C.byref(ps), C.byref(a), _stream(stream)))
+
+
+def pv_set_traversal_limit(scene, max_visits: int) -> None:
+    _check("pv_set_traversal_limit", load().pv_set_traversal_limit(scene, int(max_visits)))
 
 
 def pv_read_device_status(scene) -> int:

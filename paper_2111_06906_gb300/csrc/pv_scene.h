@@ -77,6 +77,7 @@ struct pv_scene {
   cudaStream_t last_stream = nullptr;
 
   int verify_blocks = 0, trace_blocks = 0, cont_blocks = 0;
+  uint32_t visit_limit = 0;          // 0 = default cap (see view())
 };
 
 namespace pvh {

@@ -75,7 +75,7 @@ SceneView view(const pv_scene* s) {
   v.tmin = s->tmin;
   v.close_tol = s->close_tol;
   v.moved = s->moved;
-  v.max_visits = 2u * (s->n_static_refs + s->n_dyn_tris) + 256u;
+  v.max_visits = s->visit_limit ? s->visit_limit : 2u * (s->n_static_refs + s->n_dyn_tris) + 256u;
   v.status = s->status;
   return v;
 }
@@ -253,6 +253,12 @@ extern "C" int pv_update_dynamic(pv_scene* s, const float* xforms, const pv_ligh
     k_invert<<<(s->n_dyn_tris + 255) / 256, 256, 0, st>>>(s->d_tri_prim, s->n_dyn_tris, s->prim_dyn);
   s->last_stream = st;
   return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
+}
+
+extern "C" int pv_set_traversal_limit(pv_scene* s, uint32_t max_visits) {
+  if (!s) return PV_ERR_ARG;
+  s->visit_limit = max_visits;
+  return PV_OK;
 }
 
 extern "C" int pv_read_device_status(pv_scene* s) {

@@ -115,6 +115,7 @@ def test_host_argument_errors_need_no_gpu(lib):
     assert lib.pv_compact_replace(None, None, None, None, None) == -1
     assert lib.pv_deposit(None, None, None, None) == -1
     assert lib.pv_read_device_status(None) == -1
+    assert lib.pv_set_traversal_limit(None, 1) == -1
     lib.pv_destroy_scene(None)
 
 

@@ -230,3 +230,76 @@ def test_city_full_size_sampled():
 
 def test_villa_full_size_sampled():
     _sampled_full_size(scenes.villa(), 240, frames=(1, 2))
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_verify_parity_rebuild_mode(mode):
+    """Dynamic BVHs rebuilt from world-space Morton codes every frame."""
+    sc = kit.box_with_torus(6000, B=4)
+    ids = np.arange(sc.n_paths, dtype=np.uint32)
+    o = oracle.OracleScene(sc)
+    o.set_frames(1, 1)
+    op = o.trace(ids, 1, 1)
+    h = gu.lib_scene(sc, flags=pv.PV_BUILD_DYN_REBUILD)
+    P = pv.Paths.allocate(sc.n_paths, sc.max_bounces)
+    gu.upload(P, op)
+    gu.advance(h, sc, 2)
+    lst, cnt, st = _buffers(sc.n_paths)
+    pv.pv_verify_paths(h, P, mode, 0.01, 0, lst, cnt, st)
+    o.set_frames(1, 2)
+    q = op.copy()
+    o.verify(q, mode, 0.01)
+    gu.assert_parity(gu.compare(gu.download(P), q, sc.diag))
+    pv.pv_retrace_invalid(h, P, lst, cnt, 1, 2, st)
+    o.retrace(q, 1, 2)
+    gu.assert_parity(gu.compare(gu.download(P), q, sc.diag))
+    assert pv.pv_read_device_status(h) == 0
+    pv.pv_destroy_scene(h)
+
+
+def test_multi_frame_chain_tiny_box_and_torus():
+    """Five consecutive frames of update -> verify -> re-trace -> deposit on
+    both sides; paths that were ever ambiguous are excluded from then on."""
+    for sc, mode in ((scenes.tiny_box(), 2), (kit.box_with_torus(6000, B=4), 0)):
+        ids = np.arange(sc.n_paths, dtype=np.uint32)
+        o = oracle.OracleScene(sc)
+        o.set_frames(1, 1)
+        q = o.trace(ids, 5, 1)
+        h = gu.lib_scene(sc)
+        P = pv.Paths.allocate(sc.n_paths, sc.max_bounces)
+        pv.pv_trace_all(h, P, 5, 1)
+        gu.assert_parity(gu.compare(gu.download(P), q, sc.diag))
+        for f in range(2, 7):
+            gu.advance(h, sc, f)
+            lst, cnt, st = _buffers(sc.n_paths)
+            pv.pv_verify_paths(h, P, mode, 0.01, 0, lst, cnt, st)
+            pv.pv_retrace_invalid(h, P, lst, cnt, 5, f, st)
+            o.set_frames(f - 1, f)
+            o.verify(q, mode, 0.01)
+            o.retrace(q, 5, f)
+            r = gu.compare(gu.download(P), q, sc.diag)
+            print(sc.name, f, r)
+            gu.assert_parity(r)
+            assert r["ambiguous"] <= 0.02 * r["n"]
+        assert pv.pv_read_device_status(h) == 0
+        pv.pv_destroy_scene(h)
+
+
+def test_device_error_reporting_without_fault():
+    """A traversal cap of one visit makes every query stop early: the kernels
+    return normally, the status word reports PV_ERR_ITER_CAP, reading it
+    clears it, and lifting the cap restores exact results."""
+    sc = scenes.tiny_box()
+    h = gu.lib_scene(sc)
+    P = pv.Paths.allocate(sc.n_paths, sc.max_bounces)
+    pv.pv_set_traversal_limit(h, 1)
+    pv.pv_trace_all(h, P, 1, 1)
+    assert pv.pv_read_device_status(h) == -5
+    assert pv.pv_read_device_status(h) == 0
+    pv.pv_set_traversal_limit(h, 0)
+    pv.pv_trace_all(h, P, 1, 1)
+    assert pv.pv_read_device_status(h) == 0
+    o = oracle.OracleScene(sc)
+    o.set_frames(1, 1)
+    gu.assert_parity(gu.compare(gu.download(P), o.trace(np.arange(sc.n_paths, dtype=np.uint32), 1, 1), sc.diag))
+    pv.pv_destroy_scene(h)
