@@ -90,6 +90,13 @@ def lib():
         L.or_closest_hit.restype = C.c_int32
         L.or_closest_hit.argtypes = [P, P, P, C.c_double, C.c_int32, P, P]
         L.or_num_threads.restype = C.c_int32
+        L.or_theta_size.restype = C.c_uint32
+        L.or_theta_size.argtypes = [P]
+        L.or_theta_current.argtypes = [P, P]
+        L.or_model_deposit.argtypes = [P, P, C.c_uint32, P, P, P, P, C.c_uint32, C.c_uint32, C.c_float, C.c_float,
+                                       C.c_float, C.c_float, P]
+        L.or_adjoint.argtypes = [P, P, C.c_uint32, P, P, P, P, C.c_uint32, C.c_uint32, C.c_float, C.c_float,
+                                 C.c_float, C.c_float, P, P, P]
         _lib = L
     return _lib
 
@@ -215,6 +222,32 @@ class OracleScene:
                          _p(paths.photons), _p(amb), C.byref(st))
         paths.amb |= amb
         return st.as_dict()
+
+    # ---- differentiable deposit model (frozen triangles and directions)
+    def theta_current(self) -> np.ndarray:
+        th = np.zeros(lib().or_theta_size(self._h), np.float64)
+        lib().or_theta_current(self._h, _p(th))
+        return th
+
+    def model_deposit(self, paths: Paths, theta, width: int, height: int, rect) -> np.ndarray:
+        th = np.ascontiguousarray(theta, np.float64)
+        atlas = np.zeros((height, width, 3), np.float64)
+        x0, z0, x1, z1 = (float(np.float32(v)) for v in rect)
+        lib().or_model_deposit(self._h, _p(paths.ids), paths.ids.shape[0], _p(paths.info), _p(paths.origin),
+                               _p(paths.photons), _p(th), width, height, x0, z0, x1, z1, _p(atlas))
+        return atlas
+
+    def adjoint(self, paths: Paths, theta, G, rect):
+        """(dL/dtheta, per-path scores) for G = dL/datlas [h, w, 3]."""
+        th = np.ascontiguousarray(theta, np.float64)
+        G = np.ascontiguousarray(G, np.float64)
+        height, width = G.shape[:2]
+        dth = np.zeros_like(th)
+        score = np.zeros(paths.ids.shape[0], np.float64)
+        x0, z0, x1, z1 = (float(np.float32(v)) for v in rect)
+        lib().or_adjoint(self._h, _p(paths.ids), paths.ids.shape[0], _p(paths.info), _p(paths.origin),
+                         _p(paths.photons), _p(th), width, height, x0, z0, x1, z1, _p(G), _p(dth), _p(score))
+        return dth, score
 
     def closest_hit(self, o, d, tlo: float, exclude: int = -1):
         o = np.ascontiguousarray(o, np.float64)

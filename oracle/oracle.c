@@ -55,6 +55,9 @@ struct or_scene {
   uint32_t* moved_list;  /* [n_objects] */
   uint32_t n_moved;
   double* box;           /* [n_objects][2][6] lo/hi of old (0) and new (1) pose */
+  float* xf_new;         /* [n_objects][12] current pose */
+  int32_t* dyn_index;    /* [n_objects] position among the dynamic objects, -1 if static */
+  uint32_t n_dynamic;
   or_light light[2][MAXL];
   uint32_t n_lights;
   uint32_t light_first[MAXL + 1];
@@ -157,6 +160,10 @@ or_scene* or_scene_create(const float* verts, uint32_t n_tris, const uint32_t* t
   s->moved = (uint8_t*)calloc(n_objects ? n_objects : 1, 1);
   s->moved_list = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n_objects ? n_objects : 1));
   s->box = (double*)malloc(sizeof(double) * 12 * (size_t)(n_objects ? n_objects : 1));
+  s->xf_new = (float*)calloc(12 * (size_t)(n_objects ? n_objects : 1), sizeof(float));
+  s->dyn_index = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_objects ? n_objects : 1));
+  s->n_dynamic = 0;
+  for (uint32_t o = 0; o < n_objects; ++o) s->dyn_index[o] = object_dynamic[o] ? (int32_t)s->n_dynamic++ : -1;
   return s;
 }
 
@@ -165,6 +172,7 @@ void or_scene_destroy(or_scene* s) {
   free(s->verts); free(s->tri_object); free(s->dyn); free(s->albedo);
   free(s->world[0]); free(s->world[1]);
   free(s->obj_first); free(s->obj_tris); free(s->moved); free(s->moved_list); free(s->box);
+  free(s->xf_new); free(s->dyn_index);
   free(s);
 }
 
@@ -198,6 +206,7 @@ void or_scene_set_poses(or_scene* s, const float* xform_old, const float* xform_
                         const or_light* lights_old, const or_light* lights_new, uint32_t n_lights) {
   pose_world(s, xform_old, s->world[0]);
   pose_world(s, xform_new, s->world[1]);
+  memcpy(s->xf_new, xform_new, sizeof(float) * 12 * (size_t)s->n_objects);
   s->n_moved = 0;
   for (uint32_t o = 0; o < s->n_objects; ++o) {
     s->moved[o] = s->dyn[o] && memcmp(xform_old + 12 * (size_t)o, xform_new + 12 * (size_t)o, 12 * sizeof(float)) != 0;
@@ -966,4 +975,207 @@ int32_t or_num_threads(void) {
 #else
   return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* differentiable deposit model and its adjoint                               */
+/* ------------------------------------------------------------------------ */
+uint32_t or_theta_size(const or_scene* s) { return 7u * s->n_lights + 3u * s->n_dynamic; }
+
+void or_theta_current(const or_scene* s, double* th) {
+  for (uint32_t l = 0; l < s->n_lights; ++l) {
+    const or_light* L = &s->light[1][l];
+    for (int k = 0; k < 3; ++k) {
+      th[7 * l + k] = L->pos[k];
+      th[7 * l + 3 + k] = L->normal[k];
+    }
+    th[7 * l + 6] = 1.0;
+  }
+  for (uint32_t o = 0; o < s->n_objects; ++o)
+    if (s->dyn_index[o] >= 0)
+      for (int k = 0; k < 3; ++k) th[7 * s->n_lights + 3 * s->dyn_index[o] + k] = s->xf_new[12 * o + 4 * k + 3];
+}
+
+/* Forward chain of one path: emission point o, direction d0, and photon
+ * positions x[1..L] under theta (plane of photon k: unit normal nu[k] through
+ * the stored photon moved by its object's translation). */
+typedef struct {
+  uint32_t L, l;
+  double o[3], d0[3], x[16][3], nu[16][3], d[16][3], tau1;
+  double alpha, beta, ell[3], t[3];
+  int32_t dyn[16];
+} model_path;
+
+static void model_forward(const or_scene* s, uint32_t w, const float* org, const or_photon* ph, const double* th,
+                          model_path* m) {
+  m->L = (w >> OR_INFO_NSEG_SHIFT) & 15u;
+  if (m->L > s->B) m->L = s->B;
+  m->l = (w >> 20) & 3u;
+  const or_light* L0 = &s->light[1][m->l];
+  const double* tl = th + 7 * m->l;
+  double o0[3], p0[3], n0[3], x10[3], d00[3];
+  f2d(org, o0);
+  f2d(L0->pos, p0);
+  f2d(L0->normal, n0);
+  f2d(L0->tangent, m->t);
+  if (m->L == 0) return;
+  f2d(ph[0].pos, x10);
+  sub3(x10, o0, d00);
+  if (L0->type == 0) {
+    for (int k = 0; k < 3; ++k) { m->o[k] = tl[k]; m->d0[k] = d00[k]; }
+  } else {
+    double b0[3], rel[3], nl[3], bl[3];
+    cross3(n0, m->t, b0);
+    sub3(o0, p0, rel);
+    m->alpha = dot3(m->t, rel);
+    m->beta = dot3(b0, rel);
+    m->ell[0] = dot3(m->t, d00);
+    m->ell[1] = dot3(b0, d00);
+    m->ell[2] = dot3(n0, d00);
+    for (int k = 0; k < 3; ++k) nl[k] = tl[3 + k];
+    cross3(nl, m->t, bl);
+    for (int k = 0; k < 3; ++k) {
+      m->o[k] = tl[k] + m->alpha * m->t[k] + m->beta * bl[k];
+      m->d0[k] = m->ell[0] * m->t[k] + m->ell[1] * bl[k] + m->ell[2] * nl[k];
+    }
+  }
+  const double* prev = m->o;
+  const double* dir = m->d0;
+  for (uint32_t k = 1; k <= m->L; ++k) {
+    const or_photon* v = &ph[k - 1];
+    unit_normal(s, 1, v->prim, m->nu[k]);
+    double q[3];
+    f2d(v->pos, q);
+    const int32_t di = s->dyn_index[s->tri_object[v->prim]];
+    m->dyn[k] = di;
+    if (di >= 0) {
+      const uint32_t obj = s->tri_object[v->prim];
+      for (int c = 0; c < 3; ++c) q[c] += th[7 * s->n_lights + 3 * di + c] - (double)s->xf_new[12 * obj + 4 * c + 3];
+    }
+    double qp[3];
+    sub3(q, prev, qp);
+    const double tau = dot3(m->nu[k], qp) / dot3(m->nu[k], dir);
+    if (k == 1) m->tau1 = tau;
+    for (int c = 0; c < 3; ++c) m->x[k][c] = prev[c] + tau * dir[c];
+    if (k < m->L) {
+      double xa[3], xb[3];
+      f2d(ph[k - 1].pos, xa);
+      f2d(ph[k].pos, xb);
+      sub3(xb, xa, m->d[k]);           /* stored direction of segment k+1 (fixed) */
+    }
+    prev = m->x[k];
+    dir = m->d[k];
+  }
+}
+
+/* Bilinear weights of (x, z): four texels (i+a, j+b), weight and gradient. */
+static void bilinear(double x, double z, uint32_t W, uint32_t H, float x0, float z0, float x1, float z1, int* ti,
+                     int* tj, double* wt, double* gx, double* gz) {
+  const double sx = (double)W / ((double)x1 - (double)x0), sz = (double)H / ((double)z1 - (double)z0);
+  const double u = (x - x0) * sx - 0.5, v = (z - z0) * sz - 0.5;
+  const double fi = floor(u), fj = floor(v);
+  const double fu = u - fi, fv = v - fj;
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const int k = 2 * b + a;
+      ti[k] = (int)fi + a;
+      tj[k] = (int)fj + b;
+      const double wu = a ? fu : 1.0 - fu, wv = b ? fv : 1.0 - fv;
+      wt[k] = wu * wv;
+      gx[k] = (a ? 1.0 : -1.0) * sx * wv;
+      gz[k] = (b ? 1.0 : -1.0) * sz * wu;
+    }
+}
+
+void or_model_deposit(const or_scene* s, const uint32_t* ids, uint32_t n, const uint32_t* info, const float* origin,
+                      const or_photon* photons, const double* theta, uint32_t W, uint32_t H, float x0, float z0,
+                      float x1, float z1, double* atlas) {
+  (void)ids;
+  for (uint32_t i = 0; i < n; ++i) {
+    model_path m;
+    model_forward(s, info[i], origin + 3 * (size_t)i, photons + (size_t)i * s->B, theta, &m);
+    const double sc = theta[7 * m.l + 6];
+    for (uint32_t k = 1; k <= m.L; ++k) {
+      const or_photon* v = &photons[(size_t)i * s->B + k - 1];
+      int ti[4], tj[4];
+      double wt[4], gx[4], gz[4];
+      bilinear(m.x[k][0], m.x[k][2], W, H, x0, z0, x1, z1, ti, tj, wt, gx, gz);
+      for (int q = 0; q < 4; ++q) {
+        if (ti[q] < 0 || tj[q] < 0 || ti[q] >= (int)W || tj[q] >= (int)H) continue;
+        double* a = atlas + 3 * ((size_t)tj[q] * W + ti[q]);
+        for (int c = 0; c < 3; ++c) a[c] += sc * v->E[c] * wt[q];
+      }
+    }
+  }
+}
+
+/* Reverse mode over one path: gradient of each photon's deposit with respect
+ * to its position (g), carried back through the plane intersections
+ * x_{k+1} = x_k + d_k nu.(q - x_k)/(nu.d_k):  dx_{k+1}/dx_k = I - d nu^T/(nu.d),
+ * dx_{k+1}/dq = d nu^T/(nu.d); at the light x_1 = o + d0 tau with
+ * dx_1/do = I - d0 nu^T/(nu.d0), dx_1/dd0 = tau (I - d0 nu^T/(nu.d0)). */
+void or_adjoint(const or_scene* s, const uint32_t* ids, uint32_t n, const uint32_t* info, const float* origin,
+                const or_photon* photons, const double* theta, uint32_t W, uint32_t H, float x0, float z0, float x1,
+                float z1, const double* G, double* dtheta, double* score) {
+  (void)ids;
+  const uint32_t nt = or_theta_size(s);
+  double* acc = (double*)calloc(nt, sizeof(double));
+  for (uint32_t i = 0; i < n; ++i) {
+    model_path m;
+    model_forward(s, info[i], origin + 3 * (size_t)i, photons + (size_t)i * s->B, theta, &m);
+    const double sc = theta[7 * m.l + 6];
+    double gpos[16][3];
+    double sgE = 0.0, gscale = 0.0;
+    for (uint32_t k = 1; k <= m.L; ++k) {
+      const or_photon* v = &photons[(size_t)i * s->B + k - 1];
+      int ti[4], tj[4];
+      double wt[4], gx[4], gz[4];
+      bilinear(m.x[k][0], m.x[k][2], W, H, x0, z0, x1, z1, ti, tj, wt, gx, gz);
+      gpos[k][0] = gpos[k][1] = gpos[k][2] = 0.0;
+      for (int q = 0; q < 4; ++q) {
+        if (ti[q] < 0 || tj[q] < 0 || ti[q] >= (int)W || tj[q] >= (int)H) continue;
+        const double* g = G + 3 * ((size_t)tj[q] * W + ti[q]);
+        for (int c = 0; c < 3; ++c) {
+          const double e = sc * v->E[c];
+          gpos[k][0] += g[c] * e * gx[q];
+          gpos[k][2] += g[c] * e * gz[q];
+          sgE += g[c] * e * wt[q];
+          gscale += g[c] * v->E[c] * wt[q];
+        }
+      }
+    }
+    if (score) score[i] = fabs(sgE);
+    if (m.L == 0) continue;
+    acc[7 * m.l + 6] += gscale;
+    /* backward along the path */
+    double g[3] = {0, 0, 0};
+    for (uint32_t k = m.L; k >= 1; --k) {
+      for (int c = 0; c < 3; ++c) g[c] += gpos[k][c];
+      const double* dir = k == 1 ? m.d0 : m.d[k - 1];
+      const double* nu = m.nu[k];
+      const double dg = dot3(dir, g), nd = dot3(nu, dir);
+      if (m.dyn[k] >= 0)   /* dx_k/dq_k = d nu^T / (nu.d): q moves with the translation */
+        for (int c = 0; c < 3; ++c) acc[7 * s->n_lights + 3 * m.dyn[k] + c] += nu[c] * dg / nd;
+      double gp[3];        /* g (I - d nu^T/(nu.d)) = g - nu (d.g)/(nu.d) */
+      for (int c = 0; c < 3; ++c) gp[c] = g[c] - nu[c] * dg / nd;
+      if (k == 1) {
+        /* light: o and d0 */
+        double go[3], gd[3];
+        for (int c = 0; c < 3; ++c) { go[c] = gp[c]; gd[c] = m.tau1 * gp[c]; }
+        const or_light* L0 = &s->light[1][m.l];
+        for (int c = 0; c < 3; ++c) acc[7 * m.l + c] += go[c];
+        if (L0->type != 0) {
+          double tg[3], tgd[3];
+          cross3(m.t, go, tg);      /* d/dn of beta (n x t) . go = beta (t x go) */
+          cross3(m.t, gd, tgd);
+          for (int c = 0; c < 3; ++c)
+            acc[7 * m.l + 3 + c] += m.beta * tg[c] + m.ell[1] * tgd[c] + m.ell[2] * gd[c];
+        }
+      } else {
+        for (int c = 0; c < 3; ++c) g[c] = gp[c];
+      }
+    }
+  }
+  for (uint32_t j = 0; j < nt; ++j) dtheta[j] += acc[j];
+  free(acc);
 }

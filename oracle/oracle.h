@@ -141,6 +141,28 @@ void or_deposit(const uint32_t* info, uint32_t n, const or_photon* photons, uint
                 uint32_t width, uint32_t height, float x0, float z0, float x1, float z1,
                 double* atlas);
 
+/* Differentiable deposit model (no counterpart in the paper; used to rank the
+ * paths to re-trace).  Every stored path keeps its triangles and sampled
+ * directions; with parameters theta the emission point and direction follow
+ * the light, each photon is re-found on its triangle's plane (translated with
+ * its dynamic object) along its stored incoming direction, energies scale with
+ * the light's intensity, and photons are deposited bilinearly (texel centres
+ * at half-integers, texels outside the atlas dropped).  theta layout: for
+ * every light pos[3], normal[3], intensity scale[1]; then for every dynamic
+ * object (object order) its translation[3].  At theta = the current pose
+ * (scale 1) the model reproduces the stored photons.
+ * or_model_deposit adds the model atlas [h][w][3]; or_adjoint adds
+ * dL/dtheta given G = dL/datlas and writes per-path scores
+ * |sum_k,c dL/dE_kc E_kc| (may be NULL). */
+uint32_t or_theta_size(const or_scene* s);
+void or_theta_current(const or_scene* s, double* theta);
+void or_model_deposit(const or_scene* s, const uint32_t* ids, uint32_t n, const uint32_t* info, const float* origin,
+                      const or_photon* photons, const double* theta, uint32_t width, uint32_t height, float x0,
+                      float z0, float x1, float z1, double* atlas);
+void or_adjoint(const or_scene* s, const uint32_t* ids, uint32_t n, const uint32_t* info, const float* origin,
+                const or_photon* photons, const double* theta, uint32_t width, uint32_t height, float x0, float z0,
+                float x1, float z1, const double* G, double* dtheta, double* score);
+
 /* Closest hit of one ray against the current pose (test helper): returns the
  * prim id or -1, writes the distance, ambiguity flag. */
 int32_t or_closest_hit(const or_scene* s, const double o[3], const double d[3], double tlo,
