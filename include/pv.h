@@ -230,6 +230,61 @@ int pv_compact_replace_static(const uint32_t* d_info, uint32_t n, uint32_t* d_li
  * texel under it (stand-in for the renderer's splatting, Fig. 2). */
 int pv_deposit(pv_scene* s, const pv_paths* paths, const pv_atlas* atlas, void* stream);
 
+/* ---- differentiable deposit model (the paper has no counterpart) ----------
+ * Serves to rank the paths invalidated by the Eq. 2 test when a ray budget
+ * cannot re-trace them all.  Every stored path keeps its triangles and its
+ * sampled directions; the light and the dynamic objects move by parameters
+ * theta (float32, device memory, pv_theta_size floats):
+ *   per light l:           theta[7l+0..2] position, theta[7l+3..5] normal
+ *                          (rectangles; the tangent stays fixed),
+ *                          theta[7l+6] intensity factor (1 = as traced);
+ *   per dynamic object j   theta[7L+3j+0..2] translation (world space),
+ *   (slot order = ascending object id among the dynamic objects).
+ * Photon k is re-found on its triangle's plane (through the stored photon,
+ * moved with its object's translation) along the stored incoming direction;
+ * a point light re-aims from its position through the first stored photon, a
+ * rectangle keeps the stored sample point and direction in its frame.  The
+ * photon's energy times the intensity factor is splatted bilinearly into an
+ * RGB float32 atlas of height x width texels over rect = {x0, z0, x1, z1}
+ * (texel centres at half-integers, texels outside dropped).  At theta equal
+ * to the current poses (positions, normals, factor 1, translations) the
+ * model reproduces the stored photons.  Rotations are held at their current
+ * value. */
+
+/* Number of floats in theta, or PV_ERR_ARG for a null scene. */
+int pv_theta_size(const pv_scene* s);
+
+/* Write theta at the current poses into h_theta (host float[pv_theta_size]).
+ * PV_ERR_ARG for null pointers. */
+int pv_theta_current(const pv_scene* s, float* h_theta);
+
+/* Add the model's splat of every path in paths to d_atlas (float32
+ * [height][width][3], caller-owned device memory, NOT cleared here) with
+ * float atomics.  rect: host float[4].  PV_ERR_ARG for null pointers, an
+ * empty or inverted rect, or a side above 2^20 texels. */
+int pv_model_deposit(pv_scene* s, const pv_paths* paths, const float* d_theta, float* d_atlas,
+                     uint32_t width, uint32_t height, const float* rect, void* stream);
+
+/* Reverse mode of pv_model_deposit for the loss gradient d_grad_atlas
+ * (float32 [height][width][3], device): ADDS dL/dtheta into d_dtheta
+ * (float32 [pv_theta_size], device, caller clears it) and writes, when
+ * d_score is not null, each path's score |dL/d(intensity of that path)| =
+ * |sum over its photons of G . E w| into d_score (float32 [n], device).
+ * Same argument rules as pv_model_deposit. */
+int pv_adjoint_deposit(pv_scene* s, const pv_paths* paths, const float* d_theta, const float* d_grad_atlas,
+                       uint32_t width, uint32_t height, const float* rect, float* d_dtheta, float* d_score,
+                       void* stream);
+
+/* Ray budget: of the d_count listed paths (d_list, ascending ids, as
+ * pv_verify_paths writes it), keep the min(budget, count) with the largest
+ * d_score (ties and non-positive scores: smaller id first) and write them in
+ * ascending id order to d_out, their number to d_out_count (device memory,
+ * caller-owned, d_out sized for the scene's path count).  Uses the scene's
+ * workspace (it overwrites the intersected-segment masks, which only live
+ * inside pv_verify_paths).  PV_ERR_ARG for null pointers. */
+int pv_budget_list(pv_scene* s, const uint32_t* d_list, const uint32_t* d_count, const float* d_score,
+                   uint32_t budget, uint32_t* d_out, uint32_t* d_out_count, void* stream);
+
 /* Cap the BVH node visits of every ray query (0 restores the default, which
  * no query on a valid tree reaches).  A query that reaches the cap stops,
  * counts as a miss and records PV_ERR_ITER_CAP in the device status: the way

@@ -31,7 +31,8 @@ PV_INFO_REPLACE, PV_INFO_REUSE_LIGHT = 1 << 30, 1 << 31
 
 EXPORTS = ["pv_build_scene", "pv_update_dynamic", "pv_verify_paths", "pv_retrace_invalid", "pv_trace_all",
            "pv_compact_replace", "pv_compact_replace_static", "pv_deposit", "pv_set_traversal_limit",
-           "pv_read_device_status", "pv_destroy_scene", "pv_status_string"]
+           "pv_read_device_status", "pv_destroy_scene", "pv_status_string", "pv_theta_size", "pv_theta_current",
+           "pv_model_deposit", "pv_adjoint_deposit", "pv_budget_list"]
 PV_STATIC_COMPACT_MAX_PATHS = 1 << 26
 
 
@@ -93,6 +94,11 @@ def load():
         L.pv_read_device_status.argtypes = [P]
         L.pv_destroy_scene.argtypes = [P]
         L.pv_destroy_scene.restype = None
+        L.pv_theta_size.argtypes = [P]
+        L.pv_theta_current.argtypes = [P, P]
+        L.pv_model_deposit.argtypes = [P, C.POINTER(PvPaths), P, P, C.c_uint32, C.c_uint32, P, P]
+        L.pv_adjoint_deposit.argtypes = [P, C.POINTER(PvPaths), P, P, C.c_uint32, C.c_uint32, P, P, P, P]
+        L.pv_budget_list.argtypes = [P, P, P, P, C.c_uint32, P, P, P]
         L.pv_status_string.argtypes = [C.c_int]
         L.pv_status_string.restype = C.c_char_p
         for name in EXPORTS:
@@ -234,6 +240,90 @@ def pv_deposit(scene, paths: Paths, atlas, rect, scale_log2: int, stream=None) -
     a = PvAtlas(atlas.data_ptr(), W, H, float(rect[0]), float(rect[1]), float(rect[2]), float(rect[3]),
                 int(scale_log2))
     _check("pv_deposit", load().pv_deposit(scene, C.byref(ps), C.byref(a), _stream(stream)))
+
+
+def _rect(rect):
+    r = (C.c_float * 4)(*[float(v) for v in rect])
+    return r, C.cast(r, C.c_void_p)
+
+
+def pv_theta_size(scene) -> int:
+    n = int(load().pv_theta_size(scene))
+    if n < 0:
+        _check("pv_theta_size", n)
+    return n
+
+
+def pv_theta_current(scene) -> np.ndarray:
+    """Parameters of the differentiable deposit model at the current poses:
+    per light [pos 3, normal 3, intensity factor 1], per dynamic object
+    [translation 3] (float32, host)."""
+    th = np.zeros(pv_theta_size(scene), np.float32)
+    _check("pv_theta_current", load().pv_theta_current(scene, th.ctypes.data_as(C.c_void_p)))
+    return th
+
+
+def pv_model_deposit(scene, paths: Paths, theta, atlas, rect, stream=None) -> None:
+    """Add the model's bilinear splat under ``theta`` (float32 device tensor)
+    to ``atlas`` (float32 device tensor [H, W, 3], not cleared)."""
+    ps = paths.struct()
+    keep, r = _rect(rect)
+    H, W = int(atlas.shape[0]), int(atlas.shape[1])
+    _check("pv_model_deposit", load().pv_model_deposit(scene, C.byref(ps), _ptr(theta), _ptr(atlas), W, H, r,
+                                                        _stream(stream)))
+
+
+def pv_adjoint_deposit(scene, paths: Paths, theta, grad_atlas, rect, dtheta, score=None, stream=None) -> None:
+    """Add dL/dtheta for the atlas gradient ``grad_atlas`` ([H, W, 3]) into
+    ``dtheta``; per-path scores into ``score`` (float32 [N]) when given."""
+    ps = paths.struct()
+    keep, r = _rect(rect)
+    H, W = int(grad_atlas.shape[0]), int(grad_atlas.shape[1])
+    _check("pv_adjoint_deposit", load().pv_adjoint_deposit(scene, C.byref(ps), _ptr(theta), _ptr(grad_atlas), W, H,
+                                                            r, _ptr(dtheta), _ptr(score), _stream(stream)))
+
+
+def pv_budget_list(scene, d_list, d_count, score, budget: int, d_out, d_out_count, stream=None) -> None:
+    """The ``budget`` listed paths of largest score, in ascending id order."""
+    _check("pv_budget_list", load().pv_budget_list(scene, _ptr(d_list), _ptr(d_count), _ptr(score), int(budget),
+                                                    _ptr(d_out), _ptr(d_out_count), _stream(stream)))
+
+
+_model_fn = None
+
+
+def _model_function():
+    """torch.autograd.Function over pv_model_deposit / pv_adjoint_deposit
+    (built on first use so that importing needs no torch)."""
+    global _model_fn
+    if _model_fn is None:
+        import torch
+
+        class ModelDeposit(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, theta, scene, paths, height, width, rect):
+                th = theta.detach().to(torch.float32).contiguous()
+                atlas = torch.zeros(height, width, 3, dtype=torch.float32, device=th.device)
+                pv_model_deposit(scene, paths, th, atlas, rect)
+                ctx.save_for_backward(th)
+                ctx.scene, ctx.paths, ctx.rect = scene, paths, rect
+                return atlas
+
+            @staticmethod
+            def backward(ctx, grad):
+                (th,) = ctx.saved_tensors
+                d = torch.zeros_like(th)
+                pv_adjoint_deposit(ctx.scene, ctx.paths, th, grad.to(torch.float32).contiguous(), ctx.rect, d)
+                return d, None, None, None, None, None
+
+        _model_fn = ModelDeposit
+    return _model_fn
+
+
+def model_deposit(scene, paths: Paths, theta, height: int, width: int, rect):
+    """Differentiable atlas (float32 [height, width, 3]) of the stored paths
+    under ``theta``; ``backward`` runs the CUDA adjoint."""
+    return _model_function().apply(theta, scene, paths, int(height), int(width), tuple(float(v) for v in rect))
 
 
 def pv_set_traversal_limit(scene, max_visits: int) -> None:

@@ -665,7 +665,7 @@ using namespace pvk;
 
 namespace pvh {
 
-static void radix_sort(uint64_t*& k0, uint32_t*& v0, uint64_t*& k1, uint32_t*& v1, uint32_t n, uint32_t* hist,
+void radix_sort(uint64_t*& k0, uint32_t*& v0, uint64_t*& k1, uint32_t*& v1, uint32_t n, uint32_t* hist,
                        int lo_bit, int hi_bit, cudaStream_t st) {
   const uint32_t n_tiles = (n + kRsTile - 1) / kRsTile;
   for (int shift = lo_bit; shift < hi_bit; shift += 8) {
@@ -676,6 +676,8 @@ static void radix_sort(uint64_t*& k0, uint32_t*& v0, uint64_t*& k1, uint32_t*& v
     std::swap(v0, v1);
   }
 }
+
+uint32_t radix_tiles(uint32_t n) { return (n + kRsTile - 1) / kRsTile; }
 
 static inline uint32_t blocks(uint32_t n, uint32_t t) { return (n + t - 1) / t; }
 

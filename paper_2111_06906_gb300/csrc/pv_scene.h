@@ -73,6 +73,9 @@ struct pv_scene {
   uint64_t* ws_tiles = nullptr;      // [n_tiles + 1] decoupled look-back tile states
   uint32_t n_tiles = 0;
   uint32_t* ws_ctr = nullptr;        // [16] work counters
+  uint64_t* b_keys[2] = {nullptr, nullptr};   // [n_paths] budget ranking sort keys (ping-pong)
+  uint32_t* b_vals[2] = {nullptr, nullptr};
+  uint32_t* b_hist = nullptr;                 // [256][radix tiles of n_paths]
   int* status = nullptr;             // sticky device status
   cudaStream_t last_stream = nullptr;
 
@@ -95,6 +98,11 @@ pvk::SceneView view(const pv_scene* s);
 pvk::FrameLights frame_lights(const pv_scene* s);
 
 // bvh.cu
+// stable LSD radix sort of (key, value) pairs on key bits [lo_bit, hi_bit);
+// the buffers swap so that k0/v0 hold the result; hist holds 256 * radix_tiles(n)
+void radix_sort(uint64_t*& k0, uint32_t*& v0, uint64_t*& k1, uint32_t*& v1, uint32_t n, uint32_t* hist, int lo_bit,
+                int hi_bit, cudaStream_t st);
+uint32_t radix_tiles(uint32_t n);
 int build_bvh(pv_scene* s, const float* h_verts, const std::vector<uint32_t>& static_prims, cudaStream_t st);
 void launch_update_dynamic(pv_scene* s, cudaStream_t st);
 
