@@ -244,7 +244,8 @@ int pv_deposit(pv_scene* s, const pv_paths* paths, const pv_atlas* atlas, void* 
  * moved with its object's translation) along the stored incoming direction;
  * a point light re-aims from its position through the first stored photon, a
  * rectangle keeps the stored sample point and direction in its frame.  The
- * photon's energy times the intensity factor is splatted bilinearly into an
+ * photon's energy times the intensity factor is splatted with the uniform
+ * cubic B-spline (4 x 4 texels, twice continuously differentiable) into an
  * RGB float32 atlas of height x width texels over rect = {x0, z0, x1, z1}
  * (texel centres at half-integers, texels outside dropped).  At theta equal
  * to the current poses (positions, normals, factor 1, translations) the

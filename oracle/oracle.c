@@ -1068,22 +1068,42 @@ static void model_forward(const or_scene* s, uint32_t w, const float* org, const
   }
 }
 
-/* Bilinear weights of (x, z): four texels (i+a, j+b), weight and gradient. */
-static void bilinear(double x, double z, uint32_t W, uint32_t H, float x0, float z0, float x1, float z1, int* ti,
-                     int* tj, double* wt, double* gx, double* gz) {
+/* Uniform cubic B-spline splat of (x, z) (C2, so the model loss is twice
+ * continuously differentiable in theta): with u = (x - x0) W/(x1 - x0) - 1/2
+ * the texel-centre coordinate, i = floor(u) and f = u - i, the four texels
+ * i-1 .. i+2 get the cardinal cubic B-spline weights
+ *   b0 = (1-f)^3/6, b1 = (3f^3 - 6f^2 + 4)/6, b2 = (-3f^3 + 3f^2 + 3f + 1)/6,
+ *   b3 = f^3/6      (sum 1), and the 2-D weight is the product over x and z.
+ * Entry 4b+a is texel (i-1+a, j-1+b) with weight wx[a] wz[b] and gradient
+ * (sx wx'[a] wz[b], sz wx[a] wz'[b]). */
+static void bspline1(double f, double* w, double* dw) {
+  const double g = 1.0 - f;
+  w[0] = g * g * g / 6.0;
+  w[1] = (3.0 * f * f * f - 6.0 * f * f + 4.0) / 6.0;
+  w[2] = (-3.0 * f * f * f + 3.0 * f * f + 3.0 * f + 1.0) / 6.0;
+  w[3] = f * f * f / 6.0;
+  dw[0] = -g * g / 2.0;
+  dw[1] = (3.0 * f * f - 4.0 * f) / 2.0;
+  dw[2] = (-3.0 * f * f + 2.0 * f + 1.0) / 2.0;
+  dw[3] = f * f / 2.0;
+}
+
+static void splat_weights(double x, double z, uint32_t W, uint32_t H, float x0, float z0, float x1, float z1,
+                          int* ti, int* tj, double* wt, double* gx, double* gz) {
   const double sx = (double)W / ((double)x1 - (double)x0), sz = (double)H / ((double)z1 - (double)z0);
   const double u = (x - x0) * sx - 0.5, v = (z - z0) * sz - 0.5;
   const double fi = floor(u), fj = floor(v);
-  const double fu = u - fi, fv = v - fj;
-  for (int a = 0; a < 2; ++a)
-    for (int b = 0; b < 2; ++b) {
-      const int k = 2 * b + a;
-      ti[k] = (int)fi + a;
-      tj[k] = (int)fj + b;
-      const double wu = a ? fu : 1.0 - fu, wv = b ? fv : 1.0 - fv;
-      wt[k] = wu * wv;
-      gx[k] = (a ? 1.0 : -1.0) * sx * wv;
-      gz[k] = (b ? 1.0 : -1.0) * sz * wu;
+  double wx[4], dwx[4], wz[4], dwz[4];
+  bspline1(u - fi, wx, dwx);
+  bspline1(v - fj, wz, dwz);
+  for (int b = 0; b < 4; ++b)
+    for (int a = 0; a < 4; ++a) {
+      const int k = 4 * b + a;
+      ti[k] = (int)fi - 1 + a;
+      tj[k] = (int)fj - 1 + b;
+      wt[k] = wx[a] * wz[b];
+      gx[k] = sx * dwx[a] * wz[b];
+      gz[k] = sz * wx[a] * dwz[b];
     }
 }
 
@@ -1097,10 +1117,10 @@ void or_model_deposit(const or_scene* s, const uint32_t* ids, uint32_t n, const 
     const double sc = theta[7 * m.l + 6];
     for (uint32_t k = 1; k <= m.L; ++k) {
       const or_photon* v = &photons[(size_t)i * s->B + k - 1];
-      int ti[4], tj[4];
-      double wt[4], gx[4], gz[4];
-      bilinear(m.x[k][0], m.x[k][2], W, H, x0, z0, x1, z1, ti, tj, wt, gx, gz);
-      for (int q = 0; q < 4; ++q) {
+      int ti[16], tj[16];
+      double wt[16], gx[16], gz[16];
+      splat_weights(m.x[k][0], m.x[k][2], W, H, x0, z0, x1, z1, ti, tj, wt, gx, gz);
+      for (int q = 0; q < 16; ++q) {
         if (ti[q] < 0 || tj[q] < 0 || ti[q] >= (int)W || tj[q] >= (int)H) continue;
         double* a = atlas + 3 * ((size_t)tj[q] * W + ti[q]);
         for (int c = 0; c < 3; ++c) a[c] += sc * v->E[c] * wt[q];
@@ -1128,11 +1148,11 @@ void or_adjoint(const or_scene* s, const uint32_t* ids, uint32_t n, const uint32
     double sgE = 0.0, gscale = 0.0;
     for (uint32_t k = 1; k <= m.L; ++k) {
       const or_photon* v = &photons[(size_t)i * s->B + k - 1];
-      int ti[4], tj[4];
-      double wt[4], gx[4], gz[4];
-      bilinear(m.x[k][0], m.x[k][2], W, H, x0, z0, x1, z1, ti, tj, wt, gx, gz);
+      int ti[16], tj[16];
+      double wt[16], gx[16], gz[16];
+      splat_weights(m.x[k][0], m.x[k][2], W, H, x0, z0, x1, z1, ti, tj, wt, gx, gz);
       gpos[k][0] = gpos[k][1] = gpos[k][2] = 0.0;
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < 16; ++q) {
         if (ti[q] < 0 || tj[q] < 0 || ti[q] >= (int)W || tj[q] >= (int)H) continue;
         const double* g = G + 3 * ((size_t)tj[q] * W + ti[q]);
         for (int c = 0; c < 3; ++c) {

@@ -146,8 +146,9 @@ void or_deposit(const uint32_t* info, uint32_t n, const or_photon* photons, uint
  * directions; with parameters theta the emission point and direction follow
  * the light, each photon is re-found on its triangle's plane (translated with
  * its dynamic object) along its stored incoming direction, energies scale with
- * the light's intensity, and photons are deposited bilinearly (texel centres
- * at half-integers, texels outside the atlas dropped).  theta layout: for
+ * the light's intensity, and photons are splatted with the uniform cubic
+ * B-spline over 4 x 4 texels (texel centres at half-integers, texels outside
+ * the atlas dropped).  theta layout: for
  * every light pos[3], normal[3], intensity scale[1]; then for every dynamic
  * object (object order) its translation[3].  At theta = the current pose
  * (scale 1) the model reproduces the stored photons.

@@ -264,7 +264,7 @@ def pv_theta_current(scene) -> np.ndarray:
 
 
 def pv_model_deposit(scene, paths: Paths, theta, atlas, rect, stream=None) -> None:
-    """Add the model's bilinear splat under ``theta`` (float32 device tensor)
+    """Add the model's cubic B-spline splat under ``theta`` (float32 device tensor)
     to ``atlas`` (float32 device tensor [H, W, 3], not cleared)."""
     ps = paths.struct()
     keep, r = _rect(rect)

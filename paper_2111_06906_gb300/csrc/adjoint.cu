@@ -12,8 +12,8 @@
 //     the stored photon, translated with its dynamic object) along the stored
 //     incoming direction: x_k = x_{k-1} + d nu.(q_k - x_{k-1}) / (nu.d);
 //   - energies scale with the light's intensity factor;
-//   - photons splat bilinearly (texel centres at half-integers; texels
-//     outside the atlas are dropped).
+//   - photons splat with the uniform cubic B-spline over 4 x 4 texels
+//     (C2, texel centres at half-integers, texels outside dropped).
 // theta = per light [pos 3, normal 3, scale 1], then per dynamic object in
 // slot order [translation 3].  At the current pose the model reproduces the
 // stored photons.  The adjoint runs the chain backwards per path:
@@ -93,35 +93,41 @@ __device__ __forceinline__ float3 photon_point(const ModelArgs& A, const float* 
   return q;
 }
 
-// Bilinear footprint of (x, z): texel (i0 + (c & 1), j0 + (c >> 1)) for c < 4.
-struct Bilinear {
-  int i0, j0;
-  float fu, fv, sx, sz;
-  __device__ __forceinline__ int ti(int c) const { return i0 + (c & 1); }
-  __device__ __forceinline__ int tj(int c) const { return j0 + (c >> 1); }
-  __device__ __forceinline__ float wu(int c) const { return (c & 1) ? fu : 1.f - fu; }
-  __device__ __forceinline__ float wv(int c) const { return (c >> 1) ? fv : 1.f - fv; }
-  __device__ __forceinline__ float w(int c) const { return wu(c) * wv(c); }
-  __device__ __forceinline__ float gx(int c) const { return ((c & 1) ? sx : -sx) * wv(c); }
-  __device__ __forceinline__ float gz(int c) const { return ((c >> 1) ? sz : -sz) * wu(c); }
+// Uniform cubic B-spline footprint of (x, z): with u = (x - x0) W/(x1 - x0) - 1/2
+// (texel-centre coordinate), i0 = floor(u) and f = u - i0, texels i0-1 .. i0+2
+// get the cardinal weights (1-f)^3/6, (3f^3 - 6f^2 + 4)/6,
+// (-3f^3 + 3f^2 + 3f + 1)/6, f^3/6 (derivatives -(1-f)^2/2, (3f^2 - 4f)/2,
+// (-3f^2 + 2f + 1)/2, f^2/2); the 2-D weight is the product over x and z.
+struct Spline {
+  int i0, j0;                 // texel of tap 0 in x and z
+  float wx[4], dx[4], wz[4], dz[4];
+  float sx, sz;
 };
 
-__device__ __forceinline__ Bilinear bilinear(const ModelArgs& A, float x, float z) {
-  Bilinear b;
+__device__ __forceinline__ void bspline1(float f, float* w, float* d) {
+  const float g = 1.f - f, f2 = f * f, f3 = f2 * f;
+  w[0] = g * g * g * (1.f / 6.f);
+  w[1] = (3.f * f3 - 6.f * f2 + 4.f) * (1.f / 6.f);
+  w[2] = (-3.f * f3 + 3.f * f2 + 3.f * f + 1.f) * (1.f / 6.f);
+  w[3] = f3 * (1.f / 6.f);
+  d[0] = -0.5f * g * g;
+  d[1] = 0.5f * (3.f * f2 - 4.f * f);
+  d[2] = 0.5f * (-3.f * f2 + 2.f * f + 1.f);
+  d[3] = 0.5f * f2;
+}
+
+__device__ __forceinline__ Spline spline(const ModelArgs& A, float x, float z) {
+  Spline b;
   b.sx = (float)A.W / (A.x1 - A.x0);
   b.sz = (float)A.H / (A.z1 - A.z0);
   const float u = (x - A.x0) * b.sx - 0.5f, v = (z - A.z0) * b.sz - 0.5f;
   const float fi = floorf(u), fj = floorf(v);
-  b.fu = u - fi;
-  b.fv = v - fj;
-  // far outside: keep the indices representable (every corner is dropped)
-  b.i0 = (int)fmaxf(fminf(fi, 1e9f), -1e9f);
-  b.j0 = (int)fmaxf(fminf(fj, 1e9f), -1e9f);
+  bspline1(u - fi, b.wx, b.dx);
+  bspline1(v - fj, b.wz, b.dz);
+  // far outside: keep the indices representable (every tap is dropped)
+  b.i0 = (int)fmaxf(fminf(fi, 1e9f), -1e9f) - 1;
+  b.j0 = (int)fmaxf(fminf(fj, 1e9f), -1e9f) - 1;
   return b;
-}
-
-__device__ __forceinline__ bool inside(const ModelArgs& A, int i, int j) {
-  return i >= 0 && j >= 0 && i < (int)A.W && j < (int)A.H;
 }
 
 __device__ __forceinline__ void stage_theta(const ModelArgs& A, float* s_th) {
@@ -147,15 +153,21 @@ __global__ void __launch_bounds__(256) k_model_deposit(SceneView sv, FrameLights
     const float3 q = photon_point(A, s_th, v, slot);
     const float3 x = prev + (dot(nu, q - prev) / dot(nu, dir)) * dir;
     const float3 E = sc * f3(A.pb[(size_t)(k - 1) * A.n + p]);
-    const Bilinear b = bilinear(A, x.x, x.z);
+    const Spline b = spline(A, x.x, x.z);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      if (!inside(A, b.ti(c), b.tj(c))) continue;
-      float* t = atlas + 3 * ((size_t)b.tj(c) * A.W + b.ti(c));
-      const float wc = b.w(c);
-      atomicAdd(t + 0, E.x * wc);
-      atomicAdd(t + 1, E.y * wc);
-      atomicAdd(t + 2, E.z * wc);
+    for (int r = 0; r < 4; ++r) {
+      const int tj = b.j0 + r;
+      if (tj < 0 || tj >= (int)A.H) continue;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int ti = b.i0 + c;
+        if (ti < 0 || ti >= (int)A.W) continue;
+        float* t = atlas + 3 * ((size_t)tj * A.W + ti);
+        const float wc = b.wx[c] * b.wz[r];
+        atomicAdd(t + 0, E.x * wc);
+        atomicAdd(t + 1, E.y * wc);
+        atomicAdd(t + 2, E.z * wc);
+      }
     }
     if (k < nseg) {
       const float4 vn = A.pa[(size_t)k * A.n + p];
@@ -166,7 +178,7 @@ __global__ void __launch_bounds__(256) k_model_deposit(SceneView sv, FrameLights
   }
 }
 
-// Reverse mode, one path per thread: the forward pass keeps the deposit
+// Reverse mode, one path per thread: the forward pass keeps the splat
 // gradient of each photon position (only x and z are nonzero); the backward
 // pass reloads the planes and directions.  dtheta is reduced per block in
 // shared memory, then added to the global vector.
@@ -198,17 +210,29 @@ __global__ void __launch_bounds__(128) k_adjoint(SceneView sv, FrameLights L, Mo
         if (k == 1) tau1 = tau;
         const float3 x = prev + tau * dir;
         const float3 E0 = f3(A.pb[(size_t)(k - 1) * A.n + p]);
-        const Bilinear b = bilinear(A, x.x, x.z);
+        const Spline b = spline(A, x.x, x.z);
         float2 g = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          if (!inside(A, b.ti(c), b.tj(c))) continue;
-          const float* gg = G + 3 * ((size_t)b.tj(c) * A.W + b.ti(c));
-          const float ge = __ldg(gg) * E0.x + __ldg(gg + 1) * E0.y + __ldg(gg + 2) * E0.z;
-          g.x += sc * ge * b.gx(c);
-          g.y += sc * ge * b.gz(c);
-          gscale += ge * b.w(c);
+        for (int r = 0; r < 4; ++r) {
+          const int tj = b.j0 + r;
+          if (tj < 0 || tj >= (int)A.H) continue;
+          float gr = 0.f, gdx = 0.f, gdz = 0.f;       // row sums of ge weighted by wx, dx
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int ti = b.i0 + c;
+            if (ti < 0 || ti >= (int)A.W) continue;
+            const float* gg = G + 3 * ((size_t)tj * A.W + ti);
+            const float ge = __ldg(gg) * E0.x + __ldg(gg + 1) * E0.y + __ldg(gg + 2) * E0.z;
+            gr = fmaf(ge, b.wx[c], gr);
+            gdx = fmaf(ge, b.dx[c], gdx);
+          }
+          gdz = gr * b.dz[r];
+          g.x = fmaf(gdx, b.wz[r], g.x);
+          g.y += gdz;
+          gscale = fmaf(gr, b.wz[r], gscale);
         }
+        g.x *= sc * b.sx;
+        g.y *= sc * b.sz;
         gpos[k] = g;
         if (k < nseg) {
           const float4 vn = A.pa[(size_t)k * A.n + p];

@@ -500,3 +500,19 @@ def villa(n_paths_per_light: int = 1_000_000, seed: int = 3, n_static: int = 2_0
 
 def by_name(name: str, **kw) -> Scene:
     return {"tiny_box": tiny_box, "city": city, "villa": villa}[name](**kw)
+
+
+def perturbed_theta(theta, n_lights: int, seed: int = 2111) -> np.ndarray:
+    """Seeded target pose of the adjoint workload: every light's position
+    moved by N(0, 5 cm) per axis, its normal by N(0, 0.02) per component,
+    its intensity factor times 1.1, and every dynamic object's translation
+    moved by N(0, 5 cm) per axis (theta layout: per light pos 3, normal 3,
+    intensity 1; then per dynamic object translation 3)."""
+    rng = np.random.default_rng(seed)
+    th = np.array(theta, np.float64, copy=True)
+    for l in range(n_lights):
+        th[7 * l:7 * l + 3] += rng.normal(0.0, 0.05, 3)
+        th[7 * l + 3:7 * l + 6] += rng.normal(0.0, 0.02, 3)
+        th[7 * l + 6] *= 1.1
+    th[7 * n_lights:] += rng.normal(0.0, 0.05, th.shape[0] - 7 * n_lights)
+    return th

@@ -3,7 +3,9 @@
 The model freezes every stored path's triangles and sampled directions and
 re-finds each photon on its (translated) triangle plane; the adjoint is
 checked against central differences of the model itself, closed forms and an
-independent bilinear splat of the stored photons."""
+independent cubic B-spline splat of the stored photons (written from the
+distance form of the kernel, not the per-fraction polynomials the oracle
+uses)."""
 import numpy as np
 import pytest
 
@@ -22,8 +24,19 @@ def _setup(sc, frame=1, n=None, seed=3):
     return o, p
 
 
-def _bilinear_numpy(p, rect):
-    """Independent splat of the stored photons (texel centres at half-integers)."""
+def _bspline(t):
+    """Cardinal cubic B-spline as a function of the distance |t| in texels."""
+    a = abs(t)
+    if a < 1.0:
+        return 2.0 / 3.0 - a * a + a ** 3 / 2.0
+    if a < 2.0:
+        return (2.0 - a) ** 3 / 6.0
+    return 0.0
+
+
+def _bspline_numpy(p, rect):
+    """Independent splat of the stored photons: texel (i, j) with centre
+    coordinate (i, j) gets B(u - i) B(v - j)."""
     x0, z0, x1, z1 = rect
     A = np.zeros((H, W, 3))
     for i in range(p.ids.shape[0]):
@@ -31,13 +44,10 @@ def _bilinear_numpy(p, rect):
             x, z = float(p.photons[i, k, 0]), float(p.photons[i, k, 2])
             u = (x - x0) * W / (x1 - x0) - 0.5
             v = (z - z0) * H / (z1 - z0) - 0.5
-            iu, iv = int(np.floor(u)), int(np.floor(v))
-            fu, fv = u - iu, v - iv
-            for a in (0, 1):
-                for b in (0, 1):
-                    ti, tj = iu + a, iv + b
+            for ti in range(int(np.floor(u)) - 2, int(np.floor(u)) + 4):
+                for tj in range(int(np.floor(v)) - 2, int(np.floor(v)) + 4):
                     if 0 <= ti < W and 0 <= tj < H:
-                        w = (fu if a else 1 - fu) * (fv if b else 1 - fv)
+                        w = _bspline(u - ti) * _bspline(v - tj)
                         A[tj, ti] += w * p.photons[i, k, 4:7].astype(np.float64)
     return A
 
@@ -46,7 +56,7 @@ def test_model_reproduces_stored_photons():
     sc = kit.box_with_torus(1500, B=4)
     o, p = _setup(sc)
     A = o.model_deposit(p, o.theta_current(), W, H, sc.atlas_rect)
-    B = _bilinear_numpy(p, sc.atlas_rect)
+    B = _bspline_numpy(p, sc.atlas_rect)
     assert np.allclose(A, B, rtol=1e-9, atol=1e-12)
 
 
