@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -74,20 +75,58 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling (every 200 ms) during the timed region."""
+    """SM clock and clock-event reasons sampled during the timed region: every
+    5 ms through NVML (the driver's libnvidia-ml, read-only queries), else
+    nvidia-smi every 50 ms."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.samples = []             # (sm_mhz, max_mhz, reasons bitmask or names)
+        self.stop = threading.Event()
+        self.source = None
+
+    def _nvml(self):
+        import ctypes as C
+        lib = C.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None
+        dev = C.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(self.index), C.byref(dev)) != 0:
+            return None
+        fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        return lib, dev, fn
+
+    def _poll_nvml(self, lib, dev, fn):
+        import ctypes as C
+        sm, mx, rs = C.c_uint(), C.c_uint(), C.c_ulonglong()
+        while not self.stop.is_set():
+            if (lib.nvmlDeviceGetClockInfo(dev, 1, C.byref(sm)) == 0 and
+                    lib.nvmlDeviceGetMaxClockInfo(dev, 1, C.byref(mx)) == 0 and fn(dev, C.byref(rs)) == 0):
+                self.samples.append((float(sm.value), float(mx.value),
+                                     {n for bit, n in self.REASONS.items() if rs.value & bit}))
+            time.sleep(0.005)
 
     def __enter__(self):
         try:
+            h = self._nvml()
+        except (OSError, AttributeError):
+            h = None
+        if h:
+            self.source = "nvml 5 ms"
+            self.t = threading.Thread(target=self._poll_nvml, args=h, daemon=True)
+            self.t.start()
+            return self
+        try:
+            self.source = "nvidia-smi 50 ms"
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
                 text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -96,36 +135,35 @@ class Clocks:
         return self
 
     def _read(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            f = [x.strip() for x in line.strip().split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                self.samples.append((float(f[0]), float(f[1]),
+                                     {n for n, v in zip(names, f[3:7]) if v.lower().startswith("active")}))
+            except ValueError:
+                continue
 
     def __exit__(self, *a):
+        self.stop.set()
         if self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+        if getattr(self, "t", None):
+            self.t.join(timeout=5)
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in self.lines:
-            f = [x.strip() for x in l.split(",")]
-            if len(f) < 7:
-                continue
-            try:
-                sm.append(float(f[0]))
-                mx.append(float(f[1]))
-            except ValueError:
-                continue
-            for n, v in zip(names, f[3:7]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        if not sm:
+        if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        sm = [x[0] for x in self.samples]
+        reasons = set().union(*[x[2] for x in self.samples])
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(x[1] for x in self.samples)),
+                "reasons": sorted(reasons), "samples": len(sm), "source": self.source}
 
 
 def scene_for(name, rank=0):
@@ -273,6 +311,8 @@ def run_ours(args, ws, rank, local):
         h2d = 12 * 4 * int(sc.object_dynamic.sum()) + 64 * len(lts[1])
         e2e = {"value": None, "unit": "paths/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": int(host_atlas.numel() * 8 + host_stats.numel() * 4), "_s": e2e_s}
+    # ---- differentiable model: forward splat and adjoint of an L2 atlas loss
+    adjoint = None if args.no_adjoint else time_adjoint(pv, h, P, sc, N, A, K, W, stream, dev)
     status2 = pv.pv_read_device_status(h)
     pv.pv_destroy_scene(h)
 
@@ -329,6 +369,8 @@ def run_ours(args, ws, rank, local):
            "ms_per_step": reuse_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roof,
            "gpu_launches": launches_per_frame * K, "clocks": clocks.summary()}
+    if adjoint:
+        cfg["adjoint"] = adjoint
     if e2e:
         e2e["value"] = ws * N / e2e_s
         e2e.pop("_s")
@@ -336,6 +378,62 @@ def run_ours(args, ws, rank, local):
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(args.workload, mode, tau, args.cpu_seconds)
     print(json.dumps(out), flush=True)
+
+
+def time_adjoint(pv, h, P, sc, N, A, K, W, stream, dev):
+    """Forward model splat and adjoint on the current path records, L2 loss
+    against the atlas at the seeded perturbed pose (G = 2 (A - T) formed once,
+    outside the timed calls); each call timed alone with CUDA events, L2
+    flushed before each by writing a 256 MB buffer."""
+    import torch
+
+    import scenes
+    rect = sc.atlas_rect
+    th0 = torch.as_tensor(pv.pv_theta_current(h), device=dev)
+    ths = torch.as_tensor(scenes.perturbed_theta(th0.cpu().numpy(), len(sc.lights(1))), dtype=torch.float32,
+                          device=dev)
+    T = torch.zeros(A, A, 3, dtype=torch.float32, device=dev)
+    pv.pv_model_deposit(h, P, ths, T, rect)
+    At = torch.zeros_like(T)
+    pv.pv_model_deposit(h, P, th0, At, rect)
+    G = 2 * (At - T)
+    dth = torch.zeros_like(th0)
+    score = torch.zeros(N, dtype=torch.float32, device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    fwd, bwd = [], []
+    for i in range(W + K):
+        flush.zero_()
+        At.zero_()
+        dth.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        pv.pv_model_deposit(h, P, th0, At, rect)
+        e[1].record(stream)
+        flush.zero_()
+        e[2].record(stream)
+        pv.pv_adjoint_deposit(h, P, th0, G, rect, dth, score)
+        e[3].record(stream)
+        if i >= W:
+            fwd.append(e)
+    torch.cuda.synchronize()
+    f_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in fwd]))
+    b_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in fwd]))
+    info = P.info.cpu().numpy().view(np.uint32)
+    photons = float(np.minimum((info >> 22) & 15, sc.max_bounces).sum())
+    # algorithmic bytes: per path info + origin + score, per photon PA + PB rows;
+    # the atlas (read-modify-write forward, G read backward) once
+    b_fwd = 16.0 * N + 32.0 * photons + 2 * 12.0 * A * A
+    b_bwd = 20.0 * N + 32.0 * photons + 12.0 * A * A
+    pk, pk_kind = peaks()
+    return {"atlas": f"{A}x{A} RGB f32, uniform cubic B-spline splat", "loss": "L2 against the seeded perturbed pose",
+            "forward_ms": f_ms, "adjoint_ms": b_ms, "paths_per_s_fwd_bwd": N / ((f_ms + b_ms) * 1e-3),
+            "photons": photons, "theta": int(th0.numel()),
+            "roofline_adjoint": {"kernel": "k_adjoint", "bound": "hbm", "achieved": b_bwd / (b_ms * 1e-3) / 1e9,
+                                 "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                 "frac": b_bwd / (b_ms * 1e-3) / 1e9 / pk["hbm_gbs"], "peak_kind": pk_kind},
+            "roofline_forward": {"kernel": "k_model_deposit", "bound": "hbm",
+                                 "achieved": b_fwd / (f_ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                 "frac": b_fwd / (f_ms * 1e-3) / 1e9 / pk["hbm_gbs"], "peak_kind": pk_kind}}
 
 
 # ----------------------------------------------------------------------------- oracle

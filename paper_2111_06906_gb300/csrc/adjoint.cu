@@ -130,12 +130,54 @@ __device__ __forceinline__ Spline spline(const ModelArgs& A, float x, float z) {
   return b;
 }
 
+// Add 12 consecutive floats (one row of four RGB taps) with the widest
+// aligned vector atomics (sm_90+ global float2/float4 atomicAdd).  O = floats
+// by which p lies past a 16-byte boundary; every index is a constant so v
+// stays in registers.
+template <int O>
+__device__ __forceinline__ void add_row12_at(float* p, const float* v) {
+  int i = 0;
+  if (O == 1) {
+    atomicAdd(p, v[0]);
+    atomicAdd(reinterpret_cast<float2*>(p + 1), make_float2(v[1], v[2]));
+    i = 3;
+  } else if (O == 2) {
+    atomicAdd(reinterpret_cast<float2*>(p), make_float2(v[0], v[1]));
+    i = 2;
+  } else if (O == 3) {
+    atomicAdd(p, v[0]);
+    i = 1;
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    if (i + 4 <= 12) {
+      atomicAdd(reinterpret_cast<float4*>(p + i), make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]));
+      i += 4;
+    }
+  if (i + 2 <= 12) {
+    atomicAdd(reinterpret_cast<float2*>(p + i), make_float2(v[i], v[i + 1]));
+    i += 2;
+  }
+  if (i < 12) atomicAdd(p + i, v[i]);
+}
+
+// p must be 4-byte aligned inside a 16-byte aligned array.
+__device__ __forceinline__ void add_row12(float* p, const float* v) {
+  switch ((reinterpret_cast<uintptr_t>(p) >> 2) & 3u) {
+    case 0: add_row12_at<0>(p, v); break;
+    case 1: add_row12_at<1>(p, v); break;
+    case 2: add_row12_at<2>(p, v); break;
+    default: add_row12_at<3>(p, v); break;
+  }
+}
+
 __device__ __forceinline__ void stage_theta(const ModelArgs& A, float* s_th) {
   for (uint32_t j = threadIdx.x; j < A.n_theta; j += blockDim.x) s_th[j] = A.theta[j];
 }
 
 __global__ void __launch_bounds__(256) k_model_deposit(SceneView sv, FrameLights L, ModelArgs A, float* atlas) {
   __shared__ float s_th[kMaxTheta];
+  const bool vec_ok = (reinterpret_cast<uintptr_t>(atlas) & 15u) == 0;
   stage_theta(A, s_th);
   __syncthreads();
   const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -154,10 +196,23 @@ __global__ void __launch_bounds__(256) k_model_deposit(SceneView sv, FrameLights
     const float3 x = prev + (dot(nu, q - prev) / dot(nu, dir)) * dir;
     const float3 E = sc * f3(A.pb[(size_t)(k - 1) * A.n + p]);
     const Spline b = spline(A, x.x, x.z);
+    const bool row_inside = b.i0 >= 0 && b.i0 + 3 < (int)A.W;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int tj = b.j0 + r;
       if (tj < 0 || tj >= (int)A.H) continue;
+      if (row_inside && vec_ok) {
+        float rv[12];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float wc = b.wx[c] * b.wz[r];
+          rv[3 * c] = E.x * wc;
+          rv[3 * c + 1] = E.y * wc;
+          rv[3 * c + 2] = E.z * wc;
+        }
+        add_row12(atlas + 3 * ((size_t)tj * A.W + b.i0), rv);
+        continue;
+      }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int ti = b.i0 + c;
@@ -190,11 +245,14 @@ __global__ void __launch_bounds__(128) k_adjoint(SceneView sv, FrameLights L, Mo
   for (uint32_t j = threadIdx.x; j < A.n_theta; j += blockDim.x) s_acc[j] = 0.f;
   __syncthreads();
   const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  float lc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // this path's light gradient
+  int my_l = -1;
   if (p < A.n) {
     const uint32_t w = A.info[p];
     const uint32_t nseg = min(info_nseg(w), sv.B), l = info_light(w);
     float sgE = 0.f;
     if (nseg > 0) {
+      my_l = (int)l;
       float2 gpos[PV_MAX_BOUNCES + 1];
       const float4 v1 = A.pa[p];
       const Emission e = model_emission(L.cur[l], s_th + 7 * l, A, p, f3(v1));
@@ -242,7 +300,7 @@ __global__ void __launch_bounds__(128) k_adjoint(SceneView sv, FrameLights L, Mo
         prev = x;
       }
       sgE = sc * gscale;
-      atomicAdd(&s_acc[7 * l + 6], gscale);
+      lc[6] = gscale;
       float3 g = make_float3(0.f, 0.f, 0.f);
       for (uint32_t k = nseg; k >= 1; --k) {
         g.x += gpos[k].x;
@@ -261,19 +319,31 @@ __global__ void __launch_bounds__(128) k_adjoint(SceneView sv, FrameLights L, Mo
         g = g - r * nu;
       }
       // light: g is now the gradient with respect to o; d0 receives tau_1 g
-      float* a = s_acc + 7 * l;
-      atomicAdd(a + 0, g.x);
-      atomicAdd(a + 1, g.y);
-      atomicAdd(a + 2, g.z);
+      lc[0] = g.x;
+      lc[1] = g.y;
+      lc[2] = g.z;
       if (e.rect) {
         const float3 gd = tau1 * g;
         const float3 gn = e.beta * cross(e.t, g) + e.ell.y * cross(e.t, gd) + e.ell.z * gd;
-        atomicAdd(a + 3, gn.x);
-        atomicAdd(a + 4, gn.y);
-        atomicAdd(a + 5, gn.z);
+        lc[3] = gn.x;
+        lc[4] = gn.y;
+        lc[5] = gn.z;
       }
     }
     if (score) score[p] = fabsf(sgE);
+  }
+  // light entries: summed over the warp per light, one shared atomic per entry
+  const int lane = threadIdx.x & 31;
+  for (uint32_t ll = 0; ll < A.n_lights; ++ll) {
+    const bool mine = my_l == (int)ll;
+    if (!__any_sync(0xffffffffu, mine)) continue;
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+      float v = mine ? lc[c] : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && v != 0.f) atomicAdd(&s_acc[7 * ll + c], v);
+    }
   }
   __syncthreads();
   for (uint32_t j = threadIdx.x; j < A.n_theta; j += blockDim.x)
