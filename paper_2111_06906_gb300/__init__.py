@@ -32,7 +32,10 @@ PV_INFO_REPLACE, PV_INFO_REUSE_LIGHT = 1 << 30, 1 << 31
 EXPORTS = ["pv_build_scene", "pv_update_dynamic", "pv_verify_paths", "pv_retrace_invalid", "pv_trace_all",
            "pv_compact_replace", "pv_compact_replace_static", "pv_deposit", "pv_set_traversal_limit",
            "pv_read_device_status", "pv_destroy_scene", "pv_status_string", "pv_theta_size", "pv_theta_current",
-           "pv_model_deposit", "pv_adjoint_deposit", "pv_budget_list"]
+           "pv_model_deposit", "pv_adjoint_deposit", "pv_budget_list", "pv_batch_create", "pv_batch_frame",
+           "pv_batch_autotune", "pv_batch_tuning", "pv_batch_set_config", "pv_batch_get_config", "pv_batch_step_times",
+           "pv_batch_destroy"]
+PV_BATCH_MAX_SCENES = 32
 PV_STATIC_COMPACT_MAX_PATHS = 1 << 26
 
 
@@ -64,6 +67,16 @@ class PvVerifyParams(C.Structure):
 class PvAtlas(C.Structure):
     _fields_ = [("data", C.c_void_p), ("width", C.c_uint32), ("height", C.c_uint32), ("x0", C.c_float),
                 ("z0", C.c_float), ("x1", C.c_float), ("z1", C.c_float), ("scale_log2", C.c_int32)]
+
+
+class PvBatchScene(C.Structure):
+    _fields_ = [("scene", C.c_void_p), ("paths", PvPaths), ("d_list", C.c_void_p), ("d_count", C.c_void_p),
+                ("d_stats", C.c_void_p), ("seed", C.c_uint64)]
+
+
+class PvBatchConfig(C.Structure):
+    _fields_ = [("verify_mapping", C.c_int32), ("verify_threads", C.c_int32), ("trace_steps", C.c_int32),
+                ("trace_blocks", C.c_int32), ("stack", C.c_int32)]
 
 
 STATS_FIELDS = ["n_paths", "n_listed", "n_reemit", "n_tail", "n_updated", "n_truncated", "n_cont", "vis_rays",
@@ -99,10 +112,20 @@ def load():
         L.pv_model_deposit.argtypes = [P, C.POINTER(PvPaths), P, P, C.c_uint32, C.c_uint32, P, P]
         L.pv_adjoint_deposit.argtypes = [P, C.POINTER(PvPaths), P, P, C.c_uint32, C.c_uint32, P, P, P, P]
         L.pv_budget_list.argtypes = [P, P, P, P, C.c_uint32, P, P, P]
+        L.pv_batch_create.argtypes = [C.POINTER(PvBatchScene), C.c_uint32, C.POINTER(PvVerifyParams), P,
+                                      C.POINTER(C.c_void_p)]
+        L.pv_batch_frame.argtypes = [P, P, P, C.c_uint32, P]
+        L.pv_batch_autotune.argtypes = [P, C.c_uint32]
+        L.pv_batch_tuning.argtypes = [P]
+        L.pv_batch_set_config.argtypes = [P, C.POINTER(PvBatchConfig)]
+        L.pv_batch_get_config.argtypes = [P, C.POINTER(PvBatchConfig)]
+        L.pv_batch_step_times.argtypes = [P, P]
+        L.pv_batch_destroy.argtypes = [P]
+        L.pv_batch_destroy.restype = None
         L.pv_status_string.argtypes = [C.c_int]
         L.pv_status_string.restype = C.c_char_p
         for name in EXPORTS:
-            if name not in ("pv_destroy_scene", "pv_status_string"):
+            if name not in ("pv_destroy_scene", "pv_status_string", "pv_batch_destroy"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -324,6 +347,97 @@ def model_deposit(scene, paths: Paths, theta, height: int, width: int, rect):
     """Differentiable atlas (float32 [height, width, 3]) of the stored paths
     under ``theta``; ``backward`` runs the CUDA adjoint."""
     return _model_function().apply(theta, scene, paths, int(height), int(width), tuple(float(v) for v in rect))
+
+
+class Batch:
+    """Handle of a pv_batch plus the host objects its calls must keep alive."""
+
+    def __init__(self, handle, n):
+        self.handle = handle
+        self.n = n
+
+    def __bool__(self):
+        return bool(self.handle)
+
+
+def pv_batch_create(items, mode: int, tau: float, flags: int = 0, stream=None) -> Batch:
+    """items: sequence of (scene, Paths, d_list, d_count, d_stats or None, seed)."""
+    arr = (PvBatchScene * len(items))()
+    for i, (scene, paths, d_list, d_count, d_stats, seed) in enumerate(items):
+        arr[i].scene = scene.value if isinstance(scene, C.c_void_p) else scene
+        arr[i].paths = paths.struct()
+        arr[i].d_list = d_list.data_ptr()
+        arr[i].d_count = d_count.data_ptr()
+        arr[i].d_stats = d_stats.data_ptr() if d_stats is not None else None
+        arr[i].seed = int(seed)
+    prm = PvVerifyParams(int(mode), float(tau), int(flags))
+    h = C.c_void_p()
+    _check("pv_batch_create", load().pv_batch_create(arr, len(items), C.byref(prm), _stream(stream), C.byref(h)))
+    return Batch(h, len(items))
+
+
+def pv_batch_frame(batch: Batch, xforms, lights, frame: int, stream=None) -> None:
+    """xforms / lights: per scene a float32 [n_objects, 12] array / list of
+    lights, or None (whole argument or per entry)."""
+    n = batch.n
+    keep = []
+    xf = None
+    if xforms is not None:
+        xf = (C.c_void_p * n)()
+        for i, x in enumerate(xforms):
+            if x is not None:
+                a = np.ascontiguousarray(x, np.float32)
+                keep.append(a)
+                xf[i] = a.ctypes.data
+    lt = None
+    if lights is not None:
+        lt = (C.c_void_p * n)()
+        for i, l in enumerate(lights):
+            if l is not None:
+                a = make_lights(l)
+                keep.append(a)
+                lt[i] = C.cast(a, C.c_void_p).value
+    _check("pv_batch_frame", load().pv_batch_frame(batch.handle, None if xf is None else C.cast(xf, C.c_void_p),
+                                                    None if lt is None else C.cast(lt, C.c_void_p), int(frame),
+                                                    _stream(stream)))
+
+
+def pv_batch_autotune(batch: Batch, frames_per_candidate: int = 1) -> None:
+    _check("pv_batch_autotune", load().pv_batch_autotune(batch.handle, int(frames_per_candidate)))
+
+
+def pv_batch_tuning(batch: Batch) -> bool:
+    rc = int(load().pv_batch_tuning(batch.handle))
+    if rc < 0:
+        _check("pv_batch_tuning", rc)
+    return rc == 1
+
+
+def pv_batch_set_config(batch: Batch, **cfg) -> None:
+    c = PvBatchConfig()
+    _check("pv_batch_get_config", load().pv_batch_get_config(batch.handle, C.byref(c)))
+    for k, v in cfg.items():
+        setattr(c, k, int(v))
+    _check("pv_batch_set_config", load().pv_batch_set_config(batch.handle, C.byref(c)))
+
+
+def pv_batch_get_config(batch: Batch) -> dict:
+    c = PvBatchConfig()
+    _check("pv_batch_get_config", load().pv_batch_get_config(batch.handle, C.byref(c)))
+    return {k: int(getattr(c, k)) for k, _ in PvBatchConfig._fields_}
+
+
+def pv_batch_step_times(batch: Batch):
+    """[pose update, verify, continuation, compaction, re-trace] in ms."""
+    a = (C.c_float * 5)()
+    _check("pv_batch_step_times", load().pv_batch_step_times(batch.handle, C.cast(a, C.c_void_p)))
+    return [float(x) for x in a]
+
+
+def pv_batch_destroy(batch: Batch) -> None:
+    if batch and batch.handle:
+        load().pv_batch_destroy(batch.handle)
+        batch.handle = None
 
 
 def pv_set_traversal_limit(scene, max_visits: int) -> None:

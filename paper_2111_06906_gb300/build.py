@@ -15,8 +15,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpv.so")
-SOURCES = ["scene.cu", "bvh.cu", "verify.cu", "compact.cu", "trace.cu", "deposit.cu", "adjoint.cu"]
-HEADERS = ["pv_device.cuh", "pv_scene.h"]
+SOURCES = ["scene.cu", "bvh.cu", "verify.cu", "compact.cu", "trace.cu", "deposit.cu", "adjoint.cu", "batch.cu"]
+HEADERS = ["pv_device.cuh", "pv_scene.h", "verify_core.cuh", "trace_core.cuh", "compact_core.cuh",
+           "update_core.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
@@ -36,7 +37,7 @@ def _stale(target, deps):
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "pv.h")]
+    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", h) for h in ("pv.h", "pv_batch.h")]
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

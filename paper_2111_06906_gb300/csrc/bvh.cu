@@ -27,7 +27,7 @@
 #include <cmath>
 #include <cstring>
 
-#include "pv_scene.h"
+#include "update_core.cuh"
 
 namespace pvk {
 
@@ -257,157 +257,24 @@ __global__ void k_gather_dyn(const uint32_t* order, uint32_t n, const float* loc
   if (tri_in) tri_out[i] = tri_in[src];
 }
 
-__device__ __forceinline__ void store_slot(Node* nd, int side, float3 lo, float3 hi) {
-  float* a = reinterpret_cast<float*>(nd);
-  if (side == 0) {
-    *reinterpret_cast<float4*>(a + 0) = make_float4(lo.x, hi.x, lo.y, hi.y);
-    *reinterpret_cast<float2*>(a + 8) = make_float2(lo.z, hi.z);
-  } else {
-    *reinterpret_cast<float4*>(a + 4) = make_float4(lo.x, hi.x, lo.y, hi.y);
-    *reinterpret_cast<float2*>(a + 10) = make_float2(lo.z, hi.z);
-  }
-}
-
-__device__ __forceinline__ void tri_box(const Tri& T, float3& lo, float3& hi) {
-  const float3 v0 = f3(T.v0), v1 = v0 + f3(T.e1), v2 = v0 + f3(T.e2);
-  lo = make_float3(fminf(v0.x, fminf(v1.x, v2.x)), fminf(v0.y, fminf(v1.y, v2.y)), fminf(v0.z, fminf(v1.z, v2.z)));
-  hi = make_float3(fmaxf(v0.x, fmaxf(v1.x, v2.x)), fmaxf(v0.y, fmaxf(v1.y, v2.y)), fmaxf(v0.z, fmaxf(v1.z, v2.z)));
-}
-
-__device__ __forceinline__ void pad_box(float3& lo, float3& hi) {
-  const float pad = 2.384185791015625e-07f * fmaxf(maxabs3(lo), maxabs3(hi)) + 1e-30f;
-  lo = lo - make_float3(pad, pad, pad);
-  hi = hi + make_float3(pad, pad, pad);
-}
-
-// Bottom-up boxes of one tree (``nodes`` = its first node, local indices):
-// leaves from the triangle (or the given leaf box), padded by a relative
-// 2^-22 so the FP32 slab test never rejects a box that holds a hit; each
-// internal node's box is completed by the second child to arrive.
 __global__ void k_fit(Node* nodes, const uint32_t* node_parent, const uint32_t* leaf_parent, uint32_t* flags,
                       const Tri* tris, const float* leaf_box, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || n < 2) return;
-  float3 lo, hi;
-  if (leaf_box) {
-    const float* b = leaf_box + 6 * (size_t)i;
-    lo = make_float3(b[0], b[1], b[2]);
-    hi = make_float3(b[3], b[4], b[5]);
-  } else {
-    tri_box(tris[i], lo, hi);
-  }
-  pad_box(lo, hi);
-  uint32_t p = leaf_parent[i];
-  for (int guard = 0; guard < 200; ++guard) {
-    const int node = (int)(p >> 1);
-    store_slot(nodes + node, (int)(p & 1u), lo, hi);
-    __threadfence();
-    if (atomicAdd(&flags[node], 1u) == 0u) return;
-    const float* a = reinterpret_cast<const float*>(nodes + node);
-    const float4 s0 = __ldcg(reinterpret_cast<const float4*>(a));
-    const float4 s1 = __ldcg(reinterpret_cast<const float4*>(a + 4));
-    const float4 sz = __ldcg(reinterpret_cast<const float4*>(a + 8));
-    lo = make_float3(fminf(s0.x, s1.x), fminf(s0.z, s1.z), fminf(sz.x, sz.z));
-    hi = make_float3(fmaxf(s0.y, s1.y), fmaxf(s0.w, s1.w), fmaxf(sz.y, sz.w));
-    if (node == 0) return;
-    p = node_parent[node];
-  }
+  fit_leaf(nodes, node_parent, leaf_parent, flags, tris, leaf_box, i);
 }
 
 // ------------------------------------------------------------------ per-frame update
-struct XformParams {
-  float xf[kMaxDyn][12];
-  uint64_t moved;
-  uint32_t n_dyn;
-};
-
-// One block per dynamic slot: keep the previous pose (transform and tight
-// box), and for a moved object transform its object-local corners to the new
-// pose and reduce the new tight box.
 __global__ void __launch_bounds__(256) k_update_objects(XformParams P, const float* local, const uint32_t* prim,
                                                           Tri* tris, DynObj* objs, float* xf_old, float* xf_new) {
   const uint32_t s = blockIdx.x;
-  __shared__ float red[6][256];
-  __shared__ float m[12];
-  DynObj* o = objs + s;
-  if (threadIdx.x < 12) {
-    xf_old[12 * s + threadIdx.x] = xf_new[12 * s + threadIdx.x];
-    m[threadIdx.x] = P.xf[s][threadIdx.x];
-  }
-  if (threadIdx.x < 6) o->box_old[threadIdx.x] = o->box_new[threadIdx.x];
-  __syncthreads();
-  if (threadIdx.x < 12) xf_new[12 * s + threadIdx.x] = m[threadIdx.x];
-  if (!((P.moved >> s) & 1ull)) return;
-  float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
-  const uint32_t b = o->tri_begin, e = b + o->tri_count;
-  for (uint32_t i = b + threadIdx.x; i < e; i += blockDim.x) {
-    const float* v = local + 9 * (size_t)i;
-    float w[9];
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        w[3 * k + r] = fmaf(m[4 * r + 0], v[3 * k + 0], fmaf(m[4 * r + 1], v[3 * k + 1], fmaf(m[4 * r + 2], v[3 * k + 2], m[4 * r + 3])));
-        lo[r] = fminf(lo[r], w[3 * k + r]);
-        hi[r] = fmaxf(hi[r], w[3 * k + r]);
-      }
-    Tri T;
-    T.v0 = make_float4(w[0], w[1], w[2], __int_as_float((int)prim[i]));
-    T.e1 = make_float4(w[3] - w[0], w[4] - w[1], w[5] - w[2], 0.f);
-    T.e2 = make_float4(w[6] - w[0], w[7] - w[1], w[8] - w[2], 0.f);
-    tris[i] = T;
-  }
-  for (int k = 0; k < 3; ++k) {
-    red[k][threadIdx.x] = lo[k];
-    red[3 + k][threadIdx.x] = hi[k];
-  }
-  __syncthreads();
-  for (int off = blockDim.x >> 1; off > 0; off >>= 1) {
-    if (threadIdx.x < off)
-      for (int k = 0; k < 3; ++k) {
-        red[k][threadIdx.x] = fminf(red[k][threadIdx.x], red[k][threadIdx.x + off]);
-        red[3 + k][threadIdx.x] = fmaxf(red[3 + k][threadIdx.x], red[3 + k][threadIdx.x + off]);
-      }
-    __syncthreads();
-  }
-  if (threadIdx.x < 6) o->box_new[threadIdx.x] = red[threadIdx.x][0];
+  update_object(P.xf[s], ((P.moved >> s) & 1ull) != 0, local, prim, tris, objs, xf_old, xf_new, s);
 }
 
 // ------------------------------------------------------------------ wide (4-child) nodes
 __device__ __forceinline__ int range_size(const Node* bnodes, int b) {
   const int4 d = bnodes[b].d;
   return d.w - d.z + 1;
-}
-
-__device__ __forceinline__ void slot_box(const Node* bnodes, int b, int side, float* box) {
-  const float* a = reinterpret_cast<const float*>(bnodes + b) + 4 * side;
-  const float* z = reinterpret_cast<const float*>(bnodes + b) + 8 + 2 * side;
-  box[0] = __ldcg(a + 0);
-  box[3] = __ldcg(a + 1);
-  box[1] = __ldcg(a + 2);
-  box[4] = __ldcg(a + 3);
-  box[2] = __ldcg(z + 0);
-  box[5] = __ldcg(z + 1);
-}
-
-__device__ __forceinline__ void write_wide(WNode* w, const float (*box)[6], const int* ref, int m) {
-  float b[4][6];
-  int c[4];
-  for (int i = 0; i < 4; ++i) {
-    for (int k = 0; k < 3; ++k) {
-      b[i][k] = i < m ? box[i][k] : 3.0e38f;
-      b[i][3 + k] = i < m ? box[i][3 + k] : -3.0e38f;
-    }
-    c[i] = i < m ? ref[i] : INT32_MIN;
-  }
-  w->lox = make_float4(b[0][0], b[1][0], b[2][0], b[3][0]);
-  w->hix = make_float4(b[0][3], b[1][3], b[2][3], b[3][3]);
-  w->loy = make_float4(b[0][1], b[1][1], b[2][1], b[3][1]);
-  w->hiy = make_float4(b[0][4], b[1][4], b[2][4], b[3][4]);
-  w->loz = make_float4(b[0][2], b[1][2], b[2][2], b[3][2]);
-  w->hiz = make_float4(b[0][5], b[1][5], b[2][5], b[3][5]);
-  w->child = make_int4(c[0], c[1], c[2], c[3]);
-  w->pad = make_int4(0, 0, 0, 0);
 }
 
 // Collapse a binary tree into wide nodes, one block, level by level.  Each
@@ -531,133 +398,15 @@ __global__ void __launch_bounds__(1024) k_collapse(const Node* bnodes, int tri_o
 __global__ void k_wide_refit(const Node* bnodes, const int* wsrc, const uint32_t* n_wide, WNode* wnodes) {
   const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= *n_wide) return;
-  float* lo[3] = {&wnodes[w].lox.x, &wnodes[w].loy.x, &wnodes[w].loz.x};
-  float* hi[3] = {&wnodes[w].hix.x, &wnodes[w].hiy.x, &wnodes[w].hiz.x};
-  for (int i = 0; i < 4; ++i) {
-    const int src = wsrc[4 * w + i];
-    if (src < 0) continue;
-    float box[6];
-    slot_box(bnodes, src >> 1, src & 1, box);
-    for (int k = 0; k < 3; ++k) {
-      lo[k][i] = box[k];
-      hi[k][i] = box[3 + k];
-    }
-  }
+  wide_refit_node(bnodes, wsrc, wnodes, w);
 }
 
-// box of a wide reference (node: union of its children; leaf: its triangles)
-__device__ void ref_box(const WNode* wnodes, const Tri* tris, int r, float* b) {
-  for (int k = 0; k < 3; ++k) {
-    b[k] = 3.0e38f;
-    b[3 + k] = -3.0e38f;
-  }
-  if (r >= 0) {
-    const WNode& n = wnodes[r];
-    const float lx[4] = {n.lox.x, n.lox.y, n.lox.z, n.lox.w}, hx[4] = {n.hix.x, n.hix.y, n.hix.z, n.hix.w};
-    const float ly[4] = {n.loy.x, n.loy.y, n.loy.z, n.loy.w}, hy[4] = {n.hiy.x, n.hiy.y, n.hiy.z, n.hiy.w};
-    const float lz[4] = {n.loz.x, n.loz.y, n.loz.z, n.loz.w}, hz[4] = {n.hiz.x, n.hiz.y, n.hiz.z, n.hiz.w};
-    for (int c = 0; c < 4; ++c) {
-      b[0] = fminf(b[0], lx[c]); b[1] = fminf(b[1], ly[c]); b[2] = fminf(b[2], lz[c]);
-      b[3] = fmaxf(b[3], hx[c]); b[4] = fmaxf(b[4], hy[c]); b[5] = fmaxf(b[5], hz[c]);
-    }
-  } else {
-    const uint32_t f = leaf_first(r), c = leaf_count(r);
-    for (uint32_t i = 0; i < c; ++i) {
-      float3 lo, hi;
-      tri_box(tris[f + i], lo, hi);
-      pad_box(lo, hi);
-      b[0] = fminf(b[0], lo.x); b[1] = fminf(b[1], lo.y); b[2] = fminf(b[2], lo.z);
-      b[3] = fmaxf(b[3], hi.x); b[4] = fmaxf(b[4], hi.y); b[5] = fmaxf(b[5], hi.z);
-    }
-  }
-}
-
-// Top level over the static root and the dynamic objects' roots, rebuilt
-// every frame by one thread: entries sorted along the axis of largest
-// centroid spread and cut into four consecutive groups, recursively.
 __global__ void k_build_top(WNode* wnodes, const Tri* tris, int top_off, int static_root, const DynObj* objs, int n_dyn,
                             int* root_out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  float box[kMaxDyn + 1][6];
-  int ref[kMaxDyn + 1];
-  int n = 0;
-  if (static_root != INT32_MIN) {
-    ref_box(wnodes, tris, static_root, box[n]);
-    ref[n++] = static_root;
-  }
-  for (int s = 0; s < n_dyn; ++s) {
-    const int r = objs[s].wroot;
-    if (r == INT32_MIN) continue;
-    ref_box(wnodes, tris, r, box[n]);
-    ref[n++] = r;
-  }
-  if (n == 0) {
-    *root_out = INT32_MIN;
-    return;
-  }
-  if (n == 1) {
-    *root_out = ref[0];
-    return;
-  }
-  float clo[3] = {3e38f, 3e38f, 3e38f}, chi[3] = {-3e38f, -3e38f, -3e38f};
-  for (int i = 0; i < n; ++i)
-    for (int k = 0; k < 3; ++k) {
-      const float c = 0.5f * (box[i][k] + box[i][3 + k]);
-      clo[k] = fminf(clo[k], c);
-      chi[k] = fmaxf(chi[k], c);
-    }
-  int ax = 0;
-  for (int k = 1; k < 3; ++k)
-    if (chi[k] - clo[k] > chi[ax] - clo[ax]) ax = k;
-  int order[kMaxDyn + 1];
-  for (int i = 0; i < n; ++i) order[i] = i;
-  for (int i = 1; i < n; ++i) {
-    const int v = order[i];
-    const float cv = box[v][ax] + box[v][3 + ax];
-    int j = i - 1;
-    while (j >= 0 && box[order[j]][ax] + box[order[j]][3 + ax] > cv) {
-      order[j + 1] = order[j];
-      --j;
-    }
-    order[j + 1] = v;
-  }
-  int st_b[kMaxDyn + 2], st_e[kMaxDyn + 2], st_node[kMaxDyn + 2];
-  int sp = 1, next = 1;
-  st_b[0] = 0;
-  st_e[0] = n;
-  st_node[0] = top_off;
-  while (sp > 0) {
-    --sp;
-    const int b = st_b[sp], e = st_e[sp], node = st_node[sp];
-    const int size = e - b;
-    const int groups = size < 4 ? size : 4;
-    float cb[4][6];
-    int child[4];
-    for (int g = 0; g < groups; ++g) {
-      const int gb = b + (size * g) / groups, ge = b + (size * (g + 1)) / groups;
-      for (int k = 0; k < 3; ++k) {
-        cb[g][k] = 3e38f;
-        cb[g][3 + k] = -3e38f;
-      }
-      for (int i = gb; i < ge; ++i)
-        for (int k = 0; k < 3; ++k) {
-          cb[g][k] = fminf(cb[g][k], box[order[i]][k]);
-          cb[g][3 + k] = fmaxf(cb[g][3 + k], box[order[i]][3 + k]);
-        }
-      if (ge - gb == 1) {
-        child[g] = ref[order[gb]];
-      } else {
-        child[g] = top_off + next++;
-        st_b[sp] = gb;
-        st_e[sp] = ge;
-        st_node[sp] = child[g];
-        ++sp;
-      }
-    }
-    write_wide(wnodes + node, cb, child, groups);
-  }
-  *root_out = top_off;
+  build_top(wnodes, tris, top_off, static_root, objs, n_dyn, root_out);
 }
+
 
 }  // namespace pvk
 

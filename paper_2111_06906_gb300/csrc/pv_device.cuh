@@ -290,6 +290,7 @@ __device__ __forceinline__ void cswap(float& ka, int& va, float& kb, int& vb) {
   va = v;
 }
 
+template <int S = kStack>
 __device__ __forceinline__ bool visit_wide(const WNode& n, const Ray& r, float tbest, int* stk, int& sp, int& next) {
   float t[4];
   const uint32_t mask = box4(r, tbest, n, t);
@@ -307,7 +308,7 @@ __device__ __forceinline__ bool visit_wide(const WNode& n, const Ray& r, float t
   cswap(k0, v0, k2, v2);
   cswap(k1, v1, k3, v3);
   cswap(k1, v1, k2, v2);
-  if (sp + m - 1 > kStack) return false;
+  if (sp + m - 1 > S) return false;
   if (m >= 4) stk[sp++] = v3;
   if (m >= 3) stk[sp++] = v2;
   if (m >= 2) stk[sp++] = v1;
@@ -337,10 +338,10 @@ __device__ __forceinline__ bool visit_leaf(const Tri* tris, int ref, const Ray& 
 // ``tbest`` is the current closest distance (in/out), ``best`` the hit
 // triangle index.  Returns false and records an error on stack overflow or
 // visit cap.
-template <bool ANY>
+template <bool ANY, int S = kStack>
 __device__ __forceinline__ bool traverse(const WNode* nodes, const Tri* tris, int root, const Ray& r, float& tbest,
                                          int& best, int exclude, uint32_t max_visits, int* status, Work& wk) {
-  int stack[kStack];
+  int stack[S];
   int sp = 0;
   int node = root;
   uint32_t visits = 0;
@@ -354,7 +355,7 @@ __device__ __forceinline__ bool traverse(const WNode* nodes, const Tri* tris, in
         ++wk.nodes;
         const WNode n = load_wnode(nodes, node);
         int next;
-        if (!visit_wide(n, r, tbest, stack, sp, next)) {
+        if (!visit_wide<S>(n, r, tbest, stack, sp, next)) {
           record_error(status, PV_ERR_STACK);
           return false;
         }
@@ -378,21 +379,23 @@ struct Hit {
 };
 
 // Closest hit over the whole scene (top level, static tree, dynamic objects).
+template <int S = kStack>
 __device__ __forceinline__ bool closest_hit(const SceneView& sv, int root, const Ray& r, int exclude, Hit& h, Work& wk) {
   float tb = 3.0e38f;
   int best = -1;
-  if (root != INT32_MIN) traverse<false>(sv.nodes, sv.tris, root, r, tb, best, exclude, sv.max_visits, sv.status, wk);
+  if (root != INT32_MIN) traverse<false, S>(sv.nodes, sv.tris, root, r, tb, best, exclude, sv.max_visits, sv.status, wk);
   h.t = tb;
   h.tri = best;
   return best >= 0;
 }
 
 // Any hit of the open segment (tmin, tmax) over the whole scene.
+template <int S = kStack>
 __device__ __forceinline__ bool any_hit_all(const SceneView& sv, int root, const Ray& r, float tmax, int exclude,
                                             Work& wk) {
   float tb = tmax;
   int best = -1;
-  if (root != INT32_MIN) traverse<true>(sv.nodes, sv.tris, root, r, tb, best, exclude, sv.max_visits, sv.status, wk);
+  if (root != INT32_MIN) traverse<true, S>(sv.nodes, sv.tris, root, r, tb, best, exclude, sv.max_visits, sv.status, wk);
   return best >= 0;
 }
 
@@ -412,6 +415,8 @@ __device__ __forceinline__ void trav_begin(Trav& t, int root) {
 }
 
 // One traversal step (one wide node or one leaf range); true once the ray is done.
+// ``stk`` holds S entries.
+template <int S = kStack>
 __device__ __forceinline__ bool trav_step(const SceneView& sv, const Ray& r, Trav& t, int* stk, int exclude, Work& wk) {
   if (t.node != INT32_MIN) {
     if (++t.visits > sv.max_visits) {
@@ -422,7 +427,7 @@ __device__ __forceinline__ bool trav_step(const SceneView& sv, const Ray& r, Tra
       ++wk.nodes;
       const WNode n = load_wnode(sv.nodes, t.node);
       int next;
-      if (!visit_wide(n, r, t.tbest, stk, t.sp, next)) {
+      if (!visit_wide<S>(n, r, t.tbest, stk, t.sp, next)) {
         record_error(sv.status, PV_ERR_STACK);
         return true;
       }

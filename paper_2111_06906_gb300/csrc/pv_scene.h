@@ -81,6 +81,7 @@ struct pv_scene {
 
   int verify_blocks = 0, trace_blocks = 0, cont_blocks = 0;
   uint32_t visit_limit = 0;          // 0 = default cap (see view())
+  uint32_t stack_need = 0;           // traversal stack entries the wide tree can need (0 = not yet measured)
 };
 
 namespace pvh {
@@ -96,6 +97,11 @@ enum { CTR_CONT = 0, CTR_TRACE = 1, CTR_TILE = 2, CTR_ALL = 3 };
 
 pvk::SceneView view(const pv_scene* s);
 pvk::FrameLights frame_lights(const pv_scene* s);
+// scene.cu: host half of pv_update_dynamic (validation, pose bookkeeping, moved bits)
+int stage_poses(pv_scene* s, const float* xforms, const pv_light* lights);
+// scene.cu: traversal stack entries the scene's wide tree can need (three per
+// wide node on its deepest root-to-leaf path), measured once (synchronous)
+int stack_need(pv_scene* s, uint32_t* out);
 
 // bvh.cu
 // stable LSD radix sort of (key, value) pairs on key bits [lo_bit, hi_bit);

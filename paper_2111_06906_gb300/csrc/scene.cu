@@ -1,6 +1,9 @@
 // Scene construction, per-frame pose update and status handling (C ABI).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <utility>
+#include <vector>
 
 #include "pv_scene.h"
 
@@ -233,14 +236,17 @@ extern "C" int pv_build_scene(const pv_scene_desc* d, void* stream, pv_scene** o
   return PV_OK;
 }
 
-extern "C" int pv_update_dynamic(pv_scene* s, const float* xforms, const pv_light* lights, void* stream) {
+namespace pvh {
+
+// Host half of a pose update: the new poses become current, the previous
+// ones old, and the moved bits are found by bitwise comparison.
+int stage_poses(pv_scene* s, const float* xforms, const pv_light* lights) {
   if (!s) return PV_ERR_ARG;
   if (lights) {
     if (check_lights(lights, s->n_lights) != PV_OK) return PV_ERR_ARG;
     for (uint32_t l = 0; l < s->n_lights; ++l)
       if (lights[l].n_paths != s->lights_new[l].n_paths) return PV_ERR_ARG;
   }
-  cudaStream_t st = (cudaStream_t)stream;
   s->h_xf_old = s->h_xf_new;
   uint64_t moved = 0;
   if (xforms)
@@ -254,6 +260,45 @@ extern "C" int pv_update_dynamic(pv_scene* s, const float* xforms, const pv_ligh
     if (lights) s->lights_new[l] = lights[l];
   }
   s->moved = moved;
+  return PV_OK;
+}
+
+int stack_need(pv_scene* s, uint32_t* out) {
+  if (!s || !out) return PV_ERR_ARG;
+  if (!s->stack_need) {
+    if (cudaStreamSynchronize(s->last_stream) != cudaSuccess) return PV_ERR_CUDA;
+    int root = INT32_MIN;
+    if (cudaMemcpy(&root, s->root, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return PV_ERR_CUDA;
+    std::vector<int4> ch(s->n_wide);
+    if (s->n_wide && cudaMemcpy2D(ch.data(), sizeof(int4), &s->wnodes[0].child, sizeof(WNode), sizeof(int4), s->n_wide,
+                                  cudaMemcpyDeviceToHost) != cudaSuccess)
+      return PV_ERR_CUDA;
+    // deepest root-to-leaf path, counted in wide nodes (iterative, bounded)
+    uint32_t height = 0;
+    std::vector<std::pair<int, uint32_t>> todo;
+    if (root >= 0) todo.push_back({root, 1u});
+    for (size_t guard = 0; !todo.empty() && guard < 4 * (size_t)s->n_wide + 16; ++guard) {
+      const auto [node, depth] = todo.back();
+      todo.pop_back();
+      if (node < 0 || (uint32_t)node >= s->n_wide) continue;
+      height = std::max(height, depth);
+      const int c[4] = {ch[node].x, ch[node].y, ch[node].z, ch[node].w};
+      for (int k = 0; k < 4; ++k)
+        if (c[k] >= 0) todo.push_back({c[k], depth + 1});
+    }
+    s->stack_need = std::max<uint32_t>(3 * height, 1);
+  }
+  *out = s->stack_need;
+  return PV_OK;
+}
+
+}  // namespace pvh
+
+extern "C" int pv_update_dynamic(pv_scene* s, const float* xforms, const pv_light* lights, void* stream) {
+  const int rc = pvh::stage_poses(s, xforms, lights);
+  if (rc != PV_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint64_t moved = s->moved;
   pvh::launch_update_dynamic(s, st);
   if (moved && (s->flags & PV_BUILD_DYN_REBUILD))
     k_invert<<<(s->n_dyn_tris + 255) / 256, 256, 0, st>>>(s->d_tri_prim, s->n_dyn_tris, s->prim_dyn);

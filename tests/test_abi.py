@@ -1,4 +1,4 @@
-"""The C-ABI library builds, loads and exports what include/pv.h declares;
+"""The C-ABI library builds, loads and exports what include/*.h declare;
 the Python structs match the C layout; host-side argument errors are
 reported without touching a GPU (CPU only)."""
 import ctypes as C
@@ -13,7 +13,8 @@ import paper_2111_06906_gb300 as pv
 from paper_2111_06906_gb300 import build as pvbuild
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "pv.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if h.endswith(".h")]
 
 
 @pytest.fixture(scope="module")
@@ -23,9 +24,11 @@ def lib():
 
 
 def _declared():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(pv_[a-z_]+)\s*\(", src)))
+    names = set()
+    for h in HEADERS:
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(pv_[a-z_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_exports_every_declared_symbol(lib):
@@ -43,12 +46,14 @@ def test_struct_layout_matches_header():
 #include <stdio.h>
 #include <stddef.h>
 #include "pv.h"
+#include "pv_batch.h"
 #define S(t) printf(#t " %zu\n", sizeof(t));
 #define O(t, f) printf(#t "." #f " %zu\n", offsetof(t, f));
 int main(void) {
   S(pv_light) S(pv_scene_desc) S(pv_paths) S(pv_verify_params) S(pv_atlas) S(pv_frame_stats)
   O(pv_scene_desc, scene_diag) O(pv_scene_desc, flags) O(pv_paths, pb) O(pv_atlas, scale_log2)
   O(pv_light, n_paths) O(pv_frame_stats, photons_written)
+  S(pv_batch_scene) S(pv_batch_config) O(pv_batch_scene, paths) O(pv_batch_scene, seed) O(pv_batch_config, stack)
   return 0;
 }
 """
@@ -71,6 +76,11 @@ int main(void) {
     assert got["pv_atlas.scale_log2"] == pv.PvAtlas.scale_log2.offset
     assert got["pv_light.n_paths"] == pv.PvLight.n_paths.offset
     assert got["pv_frame_stats.photons_written"] == 4 * pv.STATS_FIELDS.index("photons_written")
+    assert got["pv_batch_scene"] == C.sizeof(pv.PvBatchScene)
+    assert got["pv_batch_config"] == C.sizeof(pv.PvBatchConfig)
+    assert got["pv_batch_scene.paths"] == pv.PvBatchScene.paths.offset
+    assert got["pv_batch_scene.seed"] == pv.PvBatchScene.seed.offset
+    assert got["pv_batch_config.stack"] == pv.PvBatchConfig.stack.offset
 
 
 def test_status_strings(lib):
@@ -117,6 +127,18 @@ def test_host_argument_errors_need_no_gpu(lib):
     assert lib.pv_read_device_status(None) == -1
     assert lib.pv_set_traversal_limit(None, 1) == -1
     lib.pv_destroy_scene(None)
+    b = C.c_void_p()
+    prm = pv.PvVerifyParams(2, 0.01, 0)
+    assert lib.pv_batch_create(None, 1, C.byref(prm), None, C.byref(b)) == -1
+    items = (pv.PvBatchScene * 40)()
+    assert lib.pv_batch_create(items, 40, C.byref(prm), None, C.byref(b)) == -6
+    assert lib.pv_batch_create(items, 0, C.byref(prm), None, C.byref(b)) == -1
+    assert lib.pv_batch_frame(None, None, None, 0, None) == -1
+    assert lib.pv_batch_autotune(None, 1) == -1
+    assert lib.pv_batch_tuning(None) == -1
+    assert lib.pv_batch_set_config(None, None) == -1
+    assert lib.pv_batch_get_config(None, None) == -1
+    lib.pv_batch_destroy(None)
 
 
 def test_product_path_has_no_oracle_dependency():
