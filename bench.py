@@ -36,6 +36,8 @@ WORKLOADS = {
     "villa": "villa-shaped interior: 4x3 rooms, 2M static tris (30% clutter), 10 yawing tori of 5000 tris, "
              "point light + static area light + moving tilting torch; 3M paths, <=7 bounces",
     "tiny_box": "open 2x2x2 box (10 tris) + moving unit cube (12 tris), point light; 10k paths, <=3 bounces",
+    "batch16": "16 independent districts: 10k to 2M tris, 50k to 3M paths (12.4M in all), 1 to 3 lights, "
+               "bounce caps 1 to 7, 1 to 4 moving tori; one batched graph-captured frame per step, tuned",
 }
 OPS_PER_NODE = 107    # FP32-pipe ops per wide-node visit (four slab tests + ordering network), from the source
 OPS_PER_TRI = 40      # FP32-pipe ops per Moller-Trumbore test, counted from the source
@@ -56,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--tune-frames", type=int, default=1, help="batch16: frames per tuner candidate")
     return ap.parse_args()
 
 
@@ -436,6 +439,148 @@ def time_adjoint(pv, h, P, sc, N, A, K, W, stream, dev):
                                  "frac": b_fwd / (f_ms * 1e-3) / 1e9 / pk["hbm_gbs"], "peak_kind": pk_kind}}
 
 
+# ----------------------------------------------------------------------------- batch of 16 scenes
+def run_batch(args, ws, rank, local):
+    """Sixteen uneven scenes per frame: the batched, tuned, graph-replayed
+    frame against the same scenes driven one after another through the
+    single-scene calls (same frames, bit-identical results) and against
+    trace-all of every scene."""
+    import torch
+
+    import paper_2111_06906_gb300 as pv
+    import scenes
+    from paper_2111_06906_gb300 import build as pvbuild
+    pvbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scs = scenes.batch16()
+    mode = MODES[args.mode]
+    tau = 0.01 if args.tau is None else args.tau
+    K, W = args.steps, args.warmup
+    stream = torch.cuda.Stream(device=dev)
+    n_total = sum(sc.n_paths for sc in scs)
+
+    def make(copy):
+        out = []
+        for i, sc in enumerate(scs):
+            h = pv.pv_build_scene(sc.verts, sc.tri_object, sc.object_dynamic, sc.object_albedo, sc.lights(1),
+                                  sc.max_bounces, sc.diag, object_xform=sc.xforms(1), stream=stream)
+            P = pv.Paths.allocate(sc.n_paths, sc.max_bounces, dev)
+            lst = torch.zeros(sc.n_paths, dtype=torch.int32, device=dev)
+            cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+            st = pv.new_stats(dev)
+            seed = sc.seed + 7919 * rank
+            pv.pv_trace_all(h, P, seed, 1, None, stream)
+            out.append((h, P, lst, cnt, st, seed))
+        return out
+
+    t0 = time.time()
+    with torch.cuda.stream(stream):
+        B = make(1)
+    build_s = time.time() - t0
+    batch = pv.pv_batch_create(B, mode, tau, 0, stream)
+    frame = 1
+
+    def batch_frame(f):
+        pv.pv_batch_frame(batch, [sc.xforms(f) for sc in scs], [sc.lights(f) for sc in scs], f, stream)
+
+    pv.pv_batch_autotune(batch, max(1, args.tune_frames))
+    tune_frames = 0
+    while pv.pv_batch_tuning(batch):
+        frame += 1
+        tune_frames += 1
+        batch_frame(frame)
+    for _ in range(W):
+        frame += 1
+        batch_frame(frame)
+    with torch.cuda.stream(stream):
+        for x in B:
+            x[4].zero_()                      # counters of the timed frames only
+    stream.synchronize()
+    first = frame + 1
+    clocks = Clocks(local)
+    with clocks:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t = time.perf_counter()
+        e0.record(stream)
+        for _ in range(K):
+            frame += 1
+            batch_frame(frame)
+        e1.record(stream)
+        stream.synchronize()
+        wall = (time.perf_counter() - t) / K
+    batch_ms = e0.elapsed_time(e1) / K
+    cfg = pv.pv_batch_get_config(batch)
+    step_ms = pv.pv_batch_step_times(batch)
+    stats_b = [pv.stats_dict(x[4]) for x in B]
+    pv.pv_batch_destroy(batch)
+    status_b = [pv.pv_read_device_status(x[0]) for x in B]
+    for x in B:
+        pv.pv_destroy_scene(x[0])
+    del B
+    torch.cuda.empty_cache()
+
+    # the same frames, scene after scene through the single-scene calls
+    with torch.cuda.stream(stream):
+        A = make(0)
+    for f in range(2, first):
+        for sc, (h, P, lst, cnt, st, seed) in zip(scs, A):
+            pv.pv_update_dynamic(h, sc.xforms(f), sc.lights(f), stream)
+            pv.pv_verify_paths(h, P, mode, tau, 0, lst, cnt, None, stream)
+            pv.pv_retrace_invalid(h, P, lst, cnt, seed, f, None, stream)
+    stream.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for f in range(first, first + K):
+        for sc, (h, P, lst, cnt, st, seed) in zip(scs, A):
+            pv.pv_update_dynamic(h, sc.xforms(f), sc.lights(f), stream)
+            pv.pv_verify_paths(h, P, mode, tau, 0, lst, cnt, st, stream)
+            pv.pv_retrace_invalid(h, P, lst, cnt, seed, f, st, stream)
+    e3.record(stream)
+    stream.synchronize()
+    seq_ms = e2.elapsed_time(e3) / K
+    # trace-all of every scene, same frames
+    e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e4.record(stream)
+    for f in range(first + K, first + 2 * K):
+        for sc, (h, P, lst, cnt, st, seed) in zip(scs, A):
+            pv.pv_update_dynamic(h, sc.xforms(f), sc.lights(f), stream)
+            pv.pv_trace_all(h, P, seed, f, None, stream)
+    e5.record(stream)
+    stream.synchronize()
+    trace_ms = e4.elapsed_time(e5) / K
+    status_a = [pv.pv_read_device_status(x[0]) for x in A]
+    for x in A:
+        pv.pv_destroy_scene(x[0])
+    if rank != 0:
+        return
+    agg = lambda key, rows: float(sum(r[key] for r in rows)) / K
+    pk, pk_kind = peaks()
+    ops = OPS_PER_NODE * agg("node_visits", stats_b) + OPS_PER_TRI * agg("tri_tests", stats_b)
+    ops_peak = SM_COUNT * FP32_LANES * pk.get("sm_max_mhz", 2070.0) * 1e6
+    achieved = ops / (batch_ms * 1e-3)
+    out = {"metric": METRIC, "value": ws * n_total / (batch_ms * 1e-3), "unit": "paths/s", "n_gpus": ws, "steps": K,
+           "warmup": W, "ms_per_step": batch_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"batch16: {WORKLOADS['batch16']}", "paths": n_total, "mode": args.mode, "tau": tau,
+                      "frames_timed": K, "l2": "inputs larger than L2", "batch_frame_ms": batch_ms,
+                      "batch_frame_wall_ms": wall * 1e3, "sequential_single_scene_ms": seq_ms,
+                      "speedup_vs_sequential": seq_ms / batch_ms, "trace_all_ms": trace_ms,
+                      "speedup_vs_trace_all": trace_ms / batch_ms, "tuned_config": cfg, "tune_frames": tune_frames,
+                      "tuned_step_ms": dict(zip(["update", "verify", "continue", "compact", "retrace"], step_ms)),
+                      "listed_per_frame": agg("n_listed", stats_b), "rays_per_frame": agg("trace_rays", stats_b)
+                      + agg("cont_rays", stats_b) + agg("vis_rays", stats_b),
+                      "scene_build_s": build_s, "device_status": status_b + status_a},
+           "roofline": {"kernel": "whole batched frame (traversal-bound)", "bound": "alu",
+                        "achieved": achieved / 1e12, "peak": ops_peak / 1e12, "unit": "Top/s",
+                        "frac": achieved / ops_peak, "traffic": None,
+                        "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x max SM clock"},
+           # graph nodes per frame: prologue, object update, leaf refit, wide refit, top level, verify,
+           # continuation, compaction, re-trace
+           "gpu_launches": 9 * K, "clocks": clocks.summary()}
+    print(json.dumps(out), flush=True)
+
+
 # ----------------------------------------------------------------------------- oracle
 def _oracle_sample(workload, n_sample, seed_off=0):
     import oracle
@@ -518,6 +663,8 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, ws, rank)
+        elif args.workload == "batch16":
+            run_batch(args, ws, rank, local)
         else:
             run_ours(args, ws, rank, local)
     finally:

@@ -516,3 +516,84 @@ def perturbed_theta(theta, n_lights: int, seed: int = 2111) -> np.ndarray:
         th[7 * l + 6] *= 1.1
     th[7 * n_lights:] += rng.normal(0.0, 0.05, th.shape[0] - 7 * n_lights)
     return th
+
+
+def district(n_tris: int, n_paths: int, n_lights: int = 1, max_bounces: int = 7, n_tori: int = 4,
+             seed: int = 5) -> Scene:
+    """City-like district of about ``n_tris`` triangles: a square floor with
+    random boxes at the city's density (0.77 m grid cells, sides U[0.3, 0.7] m,
+    heights U[0.5, 5] m), ``n_tori`` (1..4) tori of 2048 triangles on x or z
+    sinusoids (amplitude 2 m, period 30 frames) and 1..3 lights sharing
+    ``n_paths``: a 1x1 m area light at 12 m translating 0.1 m/frame, a static
+    point light at 8 m, a static 0.5x0.5 m area light at 10 m."""
+    st = Stream(seed, 1)
+    b = _Builder()
+    cell = 100.0 / 130.0
+    n_boxes = max(1, (n_tris - 2 - 2048 * n_tori) // 12)
+    G = int(math.ceil(math.sqrt(n_boxes / 0.9))) + 4
+    L = G * cell
+    h = 0.5 * L
+    b.add(_quad_grid((-h, 0, -h), (0, 0, L), (L, 0, 0), 1, 1), st.uniform(3, 0.3, 0.8))
+    q = max(L / 6.0, 6.0)
+    centres = [(q, 2.5, q), (-q, 2.5, q), (-q, 2.5, -q), (q, 2.5, -q)][:n_tori]
+    axes = [0, 2, 0, 2][:n_tori]
+    R, r, amp = 1.0, 0.35, 2.0
+    gi, gj = np.meshgrid(np.arange(G), np.arange(G), indexing="ij")
+    cx = -h + (gi.reshape(-1) + 0.5) * cell
+    cz = -h + (gj.reshape(-1) + 0.5) * cell
+    keep = np.ones(cx.shape[0], bool)
+    for (x0, _, z0), ax in zip(centres, axes):
+        hx = (amp if ax == 0 else 0.0) + R + r + 0.6
+        hz = (amp if ax == 2 else 0.0) + R + r + 0.6
+        keep &= ~((np.abs(cx - x0) < hx) & (np.abs(cz - z0) < hz))
+    idx = np.nonzero(keep)[0]
+    idx = np.sort(idx[Stream(seed, 2).permutation(idx.shape[0])][:n_boxes])
+    nb = idx.shape[0]
+    sx = st.uniform(nb, 0.3, 0.7)
+    sz = st.uniform(nb, 0.3, 0.7)
+    hh = st.uniform(nb, 0.5, 5.0)
+    jx = (st.uniform(nb) - 0.5) * (cell - sx)
+    jz = (st.uniform(nb) - 0.5) * (cell - sz)
+    lo = np.stack([cx[idx] + jx - 0.5 * sx, np.zeros(nb), cz[idx] + jz - 0.5 * sz], axis=1)
+    hi = np.stack([cx[idx] + jx + 0.5 * sx, hh, cz[idx] + jz + 0.5 * sz], axis=1)
+    b.add_many(_boxes(lo, hi), st.uniform(3 * nb, 0.3, 0.8).reshape(nb, 3))
+    torus = _torus(32, 32, R, r, vertical=False)
+    tids = [b.add(torus, st.uniform(3, 0.3, 0.8), dynamic=True) for _ in range(n_tori)]
+    verts, obj, dyn, alb = b.arrays()
+    n_obj = dyn.shape[0]
+    n_lights = max(1, min(3, n_lights))
+    per = [n_paths // n_lights + (1 if l < n_paths % n_lights else 0) for l in range(n_lights)]
+
+    def xf(frame: int) -> np.ndarray:
+        x = _identity_xforms(n_obj)
+        for j, (oid, (x0, y0, z0), ax) in enumerate(zip(tids, centres, axes)):
+            off = amp * math.sin(2.0 * math.pi * (frame - 1) / 30.0 + j * math.pi / 2.0)
+            p = [x0, y0, z0]
+            p[ax] += off
+            x[oid, 3], x[oid, 7], x[oid, 11] = p
+        return x
+
+    def lf(frame: int) -> List[Light]:
+        ls = [Light(LIGHT_RECT, (0.1 * (frame - 1), 12.0, 0.0), (0.0, -1.0, 0.0), (1.0, 0.0, 0.0), (1.0, 1.0),
+                    (1000.0, 1000.0, 1000.0), per[0])]
+        if n_lights >= 2:
+            ls.append(Light(LIGHT_POINT, (0.25 * h, 8.0, -0.25 * h), power=(500.0, 500.0, 500.0), n_paths=per[1]))
+        if n_lights >= 3:
+            ls.append(Light(LIGHT_RECT, (-0.25 * h, 10.0, 0.25 * h), (0.0, -1.0, 0.0), (1.0, 0.0, 0.0), (0.5, 0.5),
+                            (500.0, 500.0, 500.0), per[2]))
+        return ls
+
+    diag = math.sqrt(2.0 * L * L + 12.0 ** 2)
+    return Scene(f"district{n_tris}", verts, obj, dyn, alb, max_bounces=max_bounces, diag=diag,
+                 atlas_rect=(-h, -h, h, h), seed=seed, frames=60, tau=0.01, _xform_fn=xf, _light_fn=lf)
+
+
+def batch16(seed: int = 4) -> List[Scene]:
+    """Sixteen independent districts of uneven size: triangles log-spaced from
+    10k to 2M, paths log-spaced from 50k to 3M (paired by a seeded
+    permutation), 1 to 3 lights, bounce caps cycling 1..7, 1 to 4 tori."""
+    tris = np.geomspace(10_000, 2_000_000, 16)
+    paths = np.geomspace(50_000, 3_000_000, 16)
+    perm = Stream(seed, 9).permutation(16)
+    return [district(int(tris[i]), int(paths[perm[i]]), n_lights=1 + i % 3, max_bounces=1 + (3 * i) % 7,
+                     n_tori=1 + i % 4, seed=100 * seed + i) for i in range(16)]
