@@ -60,7 +60,7 @@ class _Light(C.Structure):
 class _Stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "paths", "segments_tested", "segments_amb", "vis_rays", "cont_rays", "trace_rays",
-        "energy_tests", "energy_amb", "n_reemit", "n_tail", "n_updated", "n_truncated")]
+        "energy_tests", "energy_amb", "n_reemit", "n_tail", "n_updated", "n_truncated", "n_pruned", "n_filled")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -81,7 +81,21 @@ def lib():
         L.or_scene_set_poses.argtypes = [P, P, P, P, P, C.c_uint32]
         L.or_philox4x32_10.argtypes = [P, P, P]
         L.or_trace.argtypes = [P, P, C.c_uint32, C.c_uint64, C.c_uint32, P, P, P, P, P]
-        L.or_verify.argtypes = [P, P, C.c_uint32, C.c_int32, C.c_double, C.c_uint32, P, P, P, P, P, P]
+        L.or_verify.argtypes = [P, P, C.c_uint32, C.c_int32, C.c_double, C.c_uint32, C.c_uint64, C.c_uint32, P, P,
+                                P, P, P, P]
+        L.or_scene_set_dm.restype = C.c_int32
+        L.or_scene_set_dm.argtypes = [P, P, P]
+        L.or_dm_reset.argtypes = [P]
+        L.or_dm_cells.restype = C.c_uint32
+        L.or_dm_cells.argtypes = [P, C.c_uint32]
+        L.or_dm_target.restype = C.c_uint32
+        L.or_dm_target.argtypes = [P, C.c_uint32, C.c_uint32]
+        L.or_dm_counts.argtypes = [P, C.c_uint32, P]
+        L.or_dm_set_counts.argtypes = [P, C.c_uint32, P]
+        L.or_dm_cell_of.restype = C.c_int32
+        L.or_dm_cell_of.argtypes = [P, C.c_uint32, P, P]
+        L.or_dm_turn.restype = C.c_float
+        L.or_dm_turn.argtypes = [C.c_float, C.c_float]
         L.or_compact.restype = C.c_uint32
         L.or_compact.argtypes = [P, C.c_uint32, P]
         L.or_retrace.argtypes = [P, P, C.c_uint32, C.c_uint64, C.c_uint32, P, P, P, P, P]
@@ -202,14 +216,15 @@ class OracleScene:
         p.stats = st.as_dict()
         return p
 
-    def verify(self, paths: Paths, mode: int, tau: float, flags: int = 0):
+    def verify(self, paths: Paths, mode: int, tau: float, flags: int = 0, seed: int = 0, frame: int = 0):
         """In place; returns (segment mask [n], stats).  Ambiguity bits are
-        OR-ed into ``paths.amb``."""
+        OR-ed into ``paths.amb``.  seed and frame key the prune draws of the
+        distribution maps."""
         n = paths.ids.shape[0]
         mask = np.zeros(n, np.uint32)
         amb = np.zeros(n, np.uint32)
         st = _Stats()
-        lib().or_verify(self._h, _p(paths.ids), n, mode, float(tau), flags, _p(paths.info),
+        lib().or_verify(self._h, _p(paths.ids), n, mode, float(tau), flags, int(seed), int(frame), _p(paths.info),
                         _p(paths.origin), _p(paths.photons), _p(mask), _p(amb), C.byref(st))
         paths.amb |= amb
         return mask, st.as_dict()
@@ -222,6 +237,40 @@ class OracleScene:
                          _p(paths.photons), _p(amb), C.byref(st))
         paths.amb |= amb
         return st.as_dict()
+
+    # ---- distribution maps (Sec. 3.1)
+    def set_dm(self, rect=(0, 0, 0, 0), point=(0, 0)) -> None:
+        """Give every rectangle light a rect[0..3] map over (x, y, sin^2 theta,
+        phi/2pi) and every point light a point[0..1] map over ((1-z)/2,
+        phi/2pi); call after set_frames.  Zeros: no map."""
+        r = np.ascontiguousarray(rect, np.uint32)
+        q = np.ascontiguousarray(point, np.uint32)
+        if lib().or_scene_set_dm(self._h, _p(r), _p(q)) != 0:
+            raise ValueError("distribution map larger than 2^20 cells")
+
+    def dm_reset(self) -> None:
+        lib().or_dm_reset(self._h)
+
+    def dm_cells(self, light: int) -> int:
+        return int(lib().or_dm_cells(self._h, light))
+
+    def dm_counts(self, light: int) -> np.ndarray:
+        out = np.zeros(self.dm_cells(light), np.uint32)
+        lib().or_dm_counts(self._h, light, _p(out))
+        return out
+
+    def dm_set_counts(self, light: int, counts) -> None:
+        c = np.ascontiguousarray(counts, np.uint32)
+        assert c.shape[0] == self.dm_cells(light)
+        lib().or_dm_set_counts(self._h, light, _p(c))
+
+    def dm_targets(self, light: int) -> np.ndarray:
+        return np.array([lib().or_dm_target(self._h, light, c) for c in range(self.dm_cells(light))], np.uint32)
+
+    def dm_cell_of(self, light: int, x1, o) -> int:
+        a = np.ascontiguousarray(x1, np.float32)
+        b = np.ascontiguousarray(o, np.float32)
+        return int(lib().or_dm_cell_of(self._h, light, _p(a), _p(b)))
 
     # ---- differentiable deposit model (frozen triangles and directions)
     def theta_current(self) -> np.ndarray:
@@ -256,6 +305,11 @@ class OracleScene:
         a = C.c_int32()
         prim = lib().or_closest_hit(self._h, _p(o), _p(d), tlo, exclude, C.byref(t), C.byref(a))
         return int(prim), float(t.value), bool(a.value)
+
+
+def dm_turn(x: float, y: float) -> float:
+    """Fraction of a turn of the angle of (x, y) as the map's parametrisation computes it."""
+    return float(lib().or_dm_turn(float(x), float(y)))
 
 
 def compact(info: np.ndarray) -> np.ndarray:

@@ -63,6 +63,13 @@ struct or_scene {
   uint32_t light_first[MAXL + 1];
   uint8_t light_moved[MAXL];
   uint8_t light_tilted[MAXL];
+  /* distribution maps (Sec. 3.1): per light its resolution over the sample
+   * dimensions (rectangle: x, y, theta, phi; point: theta, phi), cell count
+   * and current counts DM_C (DM_T is computed as needed) */
+  uint32_t dm_res[MAXL][4];
+  uint32_t dm_dims[MAXL];
+  uint32_t dm_cells[MAXL];
+  uint32_t* dm_c[MAXL];
 };
 
 /* ------------------------------------------------------------------------ */
@@ -173,6 +180,7 @@ void or_scene_destroy(or_scene* s) {
   free(s->world[0]); free(s->world[1]);
   free(s->obj_first); free(s->obj_tris); free(s->moved); free(s->moved_list); free(s->box);
   free(s->xf_new); free(s->dyn_index);
+  for (int l = 0; l < MAXL; ++l) free(s->dm_c[l]);
   free(s);
 }
 
@@ -500,6 +508,174 @@ static inline uint32_t info_make(uint32_t cell, uint32_t nseg, uint32_t start, i
          (replace ? OR_INFO_REPLACE : 0u) | (reuse ? OR_INFO_REUSE_LIGHT : 0u);
 }
 
+/* ------------------------------------------------------------------------ */
+/* distribution maps (Sec. 3.1)                                              */
+/* ------------------------------------------------------------------------ */
+/* A cell is a box of the emission's sample space: a rectangle's uniforms
+ * (u0, u1) pick the point and (u2, u3) = (sin^2 theta, phi / 2 pi) the
+ * cosine-weighted direction; a point light's (u2, u3) = ((1 - z) / 2,
+ * phi / 2 pi) pick the direction.  Every cell therefore has the same
+ * emission probability, and sampling restricted to a cell is a uniform draw
+ * inside its box.  The cell of a path is decided in float32 with correctly
+ * rounded +, -, *, / and sqrt only (compiled without contraction), from the
+ * stored float32 photon and origin and the float32 light pose. */
+static const int dm_u_rect[4] = {0, 1, 2, 3};
+static const int dm_u_point[2] = {2, 3};
+
+/* Fraction of a full turn of the angle of (x, y), in [0, 1): the angle to the
+ * nearer axis from two half-angle steps atan t = 2 atan(t / (1 + sqrt(1 + t^2)))
+ * and the Gregory series to t^9 (|t| <= tan(pi/16), truncation < 2e-9). */
+float or_dm_turn(float x, float y) {
+  const float ax = fabsf(x), ay = fabsf(y);
+  const float mx = ax > ay ? ax : ay, mn = ax > ay ? ay : ax;
+  if (!(mx > 0.0f)) return 0.0f;
+  float t = mn / mx;
+  t = t / (1.0f + sqrtf(1.0f + t * t));
+  t = t / (1.0f + sqrtf(1.0f + t * t));
+  const float q = t * t;
+  float a = 1.0f / 9.0f;
+  a = 1.0f / 7.0f - q * a;
+  a = 1.0f / 5.0f - q * a;
+  a = 1.0f / 3.0f - q * a;
+  a = 1.0f - q * a;
+  a = 4.0f * (t * a);
+  if (ay > ax) a = 1.57079632679489662f - a;
+  if (x < 0.0f) a = 3.14159265358979324f - a;
+  if (y < 0.0f) a = 6.28318530717958648f - a;
+  const float f = a / 6.28318530717958648f;
+  return f < 1.0f ? f : 0.0f;
+}
+
+static inline float dotf(const float* a, const float* b) { return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2]; }
+
+/* The light's bitangent n x t: products exact in double, one rounding each
+ * way (as the pose is prepared for the GPU). */
+static void bitangent_f(const or_light* L, float* b) {
+  const double n0 = L->normal[0], n1 = L->normal[1], n2 = L->normal[2];
+  const double t0 = L->tangent[0], t1 = L->tangent[1], t2 = L->tangent[2];
+  b[0] = (float)(n1 * t2 - n2 * t1);
+  b[1] = (float)(n2 * t0 - n0 * t2);
+  b[2] = (float)(n0 * t1 - n1 * t0);
+}
+
+/* Sample-space coordinates of a path under pose L (the parametrisation
+ * function of Sec. 3.1); 0 when the path does not come from the light. */
+static int dm_param(const or_light* L, const float* x1, const float* o, float* u) {
+  if (L->type == 0) {
+    const float dx[3] = {x1[0] - L->pos[0], x1[1] - L->pos[1], x1[2] - L->pos[2]};
+    const float len = sqrtf(dotf(dx, dx));
+    if (!(len > 0.0f)) return 0;
+    const float d[3] = {dx[0] / len, dx[1] / len, dx[2] / len};
+    u[2] = (1.0f - d[2]) * 0.5f;
+    u[3] = or_dm_turn(d[0], d[1]);
+    return u[2] >= 0.0f && u[2] < 1.0f;
+  }
+  const float dv[3] = {x1[0] - o[0], x1[1] - o[1], x1[2] - o[2]};
+  const float len = sqrtf(dotf(dv, dv));
+  if (!(len > 0.0f)) return 0;
+  const float d[3] = {dv[0] / len, dv[1] / len, dv[2] / len};
+  float b[3];
+  bitangent_f(L, b);
+  const float nd = dotf(L->normal, d);
+  if (!(nd > 0.0f)) return 0;
+  const float x1c[3] = {x1[0] - L->pos[0], x1[1] - L->pos[1], x1[2] - L->pos[2]};
+  const float tp = dotf(L->normal, x1c) / nd;
+  if (!(tp > 0.0f)) return 0;
+  const float rel[3] = {x1c[0] - tp * d[0], x1c[1] - tp * d[1], x1c[2] - tp * d[2]};
+  u[0] = dotf(L->tangent, rel) / L->size[0] + 0.5f;
+  u[1] = dotf(b, rel) / L->size[1] + 0.5f;
+  const float dx = dotf(d, L->tangent), dy = dotf(d, b);
+  u[2] = dx * dx + dy * dy;
+  u[3] = or_dm_turn(dx, dy);
+  for (int k = 0; k < 4; ++k)
+    if (!(u[k] >= 0.0f && u[k] < 1.0f)) return 0;
+  return 1;
+}
+
+/* Cell of sample-space coordinates u (row-major over the light's dimensions). */
+static uint32_t dm_cell_of_u(const or_scene* s, uint32_t l, const float* u) {
+  const int* ux = s->dm_dims[l] == 4 ? dm_u_rect : dm_u_point;
+  uint32_t c = 0;
+  for (uint32_t k = 0; k < s->dm_dims[l]; ++k) {
+    const uint32_t n = s->dm_res[l][k];
+    uint32_t i = (uint32_t)floorf(u[ux[k]] * (float)n);
+    if (i >= n) i = n - 1;
+    c = c * n + i;
+  }
+  return c;
+}
+
+int32_t or_dm_cell_of(const or_scene* s, uint32_t light, const float x1[3], const float o[3]) {
+  if (light >= s->n_lights || !s->dm_c[light]) return -1;
+  float u[4];
+  if (!dm_param(&s->light[1][light], x1, o, u)) return -1;
+  return (int32_t)dm_cell_of_u(s, light, u);
+}
+
+/* DM_T: N paths spread over the cells as evenly as integers allow. */
+uint32_t or_dm_target(const or_scene* s, uint32_t l, uint32_t c) {
+  const uint64_t N = s->light[1][l].n_paths, n = s->dm_cells[l];
+  return (uint32_t)(((uint64_t)(c + 1) * N) / n - ((uint64_t)c * N) / n);
+}
+
+/* Cell of the j-th path of a light in a full trace: path j lies in cell c
+ * when floor(N c / n) <= j < floor(N (c + 1) / n), so DM_C = DM_T exactly. */
+static uint32_t dm_stratified(const or_scene* s, uint32_t l, uint32_t j) {
+  const uint64_t N = s->light[1][l].n_paths, n = s->dm_cells[l];
+  return (uint32_t)((((uint64_t)j + 1) * n - 1) / N);
+}
+
+/* Restrict the uniforms of an emission to cell c: u_k' = (i_k + u_k) / n_k,
+ * rounded in float32 (each u_k has 24 bits and is exact in float32). */
+static void dm_restrict(const or_scene* s, uint32_t l, uint32_t c, double* u) {
+  const int* ux = s->dm_dims[l] == 4 ? dm_u_rect : dm_u_point;
+  for (int k = (int)s->dm_dims[l] - 1; k >= 0; --k) {
+    const uint32_t n = s->dm_res[l][k];
+    const uint32_t i = c % n;
+    c /= n;
+    const float v = ((float)i + (float)u[ux[k]]) / (float)n;
+    u[ux[k]] = (double)v;
+  }
+}
+
+int32_t or_scene_set_dm(or_scene* s, const uint32_t rect[4], const uint32_t point[2]) {
+  for (uint32_t l = 0; l < s->n_lights; ++l) {
+    free(s->dm_c[l]);
+    s->dm_c[l] = NULL;
+    const int rectl = s->light[1][l].type != 0;
+    const uint32_t dims = rectl ? 4u : 2u;
+    uint64_t cells = 1;
+    for (uint32_t k = 0; k < dims; ++k) {
+      const uint32_t r = rectl ? rect[k] : point[k];
+      if (r == 0) { cells = 0; break; }
+      s->dm_res[l][k] = r;
+      cells *= r;
+    }
+    if (cells == 0) continue;                 /* no map for this light */
+    if (cells > (1u << 20)) return -1;        /* the info word holds light << 20 | cell */
+    s->dm_dims[l] = dims;
+    s->dm_cells[l] = (uint32_t)cells;
+    s->dm_c[l] = (uint32_t*)calloc(cells, sizeof(uint32_t));
+  }
+  return 0;
+}
+
+void or_dm_reset(or_scene* s) {
+  for (uint32_t l = 0; l < s->n_lights; ++l)
+    if (s->dm_c[l])
+      for (uint32_t c = 0; c < s->dm_cells[l]; ++c) s->dm_c[l][c] = or_dm_target(s, l, c);
+}
+
+uint32_t or_dm_cells(const or_scene* s, uint32_t light) { return light < s->n_lights && s->dm_c[light] ? s->dm_cells[light] : 0; }
+
+void or_dm_counts(const or_scene* s, uint32_t light, uint32_t* out) {
+  if (light < s->n_lights && s->dm_c[light]) memcpy(out, s->dm_c[light], sizeof(uint32_t) * s->dm_cells[light]);
+}
+
+void or_dm_set_counts(or_scene* s, uint32_t light, const uint32_t* in) {
+  if (light < s->n_lights && s->dm_c[light]) memcpy(s->dm_c[light], in, sizeof(uint32_t) * s->dm_cells[light]);
+}
+
 /* Extend a path (Fig. 2 "generate rays" / "trace rays" loop): k photons are
  * stored already.  For k == 0 the first ray (o, d) carrying E is given;
  * for k >= 1 the path first scatters at photon k (Russian roulette with
@@ -562,6 +738,11 @@ void or_trace(const or_scene* s, const uint32_t* ids, uint32_t n, uint64_t seed,
     const or_light* L = &s->light[1][l];
     double u[4], o[3], d[3], E[3];
     rng4(seed, pid, 0, frame, u);
+    uint32_t cell = 0;
+    if (s->dm_c[l]) {                          /* stratified over the distribution map */
+      cell = dm_stratified(s, l, pid - s->light_first[l]);
+      dm_restrict(s, l, cell, u);
+    }
     emit(L, u, o, d);
     for (int c = 0; c < 3; ++c) E[c] = (double)L->power[c] / (double)L->n_paths;
     float* org = origin + 3 * (size_t)i;
@@ -571,7 +752,7 @@ void or_trace(const or_scene* s, const uint32_t* ids, uint32_t n, uint64_t seed,
     uint64_t r = 0;
     uint32_t k = extend_path(s, pid, seed, frame, 0, o, d, E, 0.0, org, photons + (size_t)i * s->B, &amb[i], &r);
     rays += r;
-    info[i] = info_make(l << 20, k, 0, 0, 0);
+    info[i] = info_make((l << 20) | cell, k, 0, 0, 0);
   }
   if (st) {
     st->paths += n;
@@ -650,9 +831,11 @@ static int seg_vs_moved(const or_scene* s, int mode, uint32_t flags, const doubl
 }
 
 void or_verify(const or_scene* s, const uint32_t* ids, uint32_t n, int32_t mode, double tau,
-               uint32_t flags, uint32_t* info, float* origin, or_photon* photons, uint32_t* seg_mask,
-               uint32_t* ambv, or_stats* st) {
+               uint32_t flags, uint64_t seed, uint32_t frame, uint32_t* info, float* origin, or_photon* photons,
+               uint32_t* seg_mask, uint32_t* ambv, or_stats* st) {
   uint64_t seg_t = 0, seg_a = 0, vis = 0, cont = 0, et = 0, ea = 0, nre = 0, ntail = 0, nupd = 0, ntr = 0;
+  /* paths of a moved light with a distribution map that keep their origin (counted in DM_C) */
+  uint8_t* counted = (uint8_t*)calloc(n ? n : 1, 1);
 #pragma omp parallel for schedule(dynamic, 8) reduction(+ : seg_t, seg_a, vis, cont, et, ea, nre, ntail, nupd, ntr)
   for (uint32_t i = 0; i < n; ++i) {
     uint32_t pid = ids[i];
@@ -671,8 +854,13 @@ void or_verify(const or_scene* s, const uint32_t* ids, uint32_t n, int32_t mode,
       const or_light* Ln = &s->light[1][l];
       const or_light* Lo = &s->light[0][l];
       int invalid = 0;
-      if (L == 0) {
-        invalid = 1;          /* an escaped path has no vertex to re-aim at */
+      int dm_cell = -1;
+      if (L > 0 && s->dm_c[l]) {               /* Compute DM_C: the parametrisation decides */
+        float u[4];
+        if (dm_param(Ln, ph[0].pos, org, u)) dm_cell = (int)dm_cell_of_u(s, l, u);
+      }
+      if (L == 0 || (s->dm_c[l] && dm_cell < 0)) {
+        invalid = 1;          /* an escaped path has no vertex to re-aim at; or off the map */
       } else if (Ln->type == 0) {
         for (int c = 0; c < 3; ++c) org[c] = Ln->pos[c];
         double a[3], b[3];
@@ -690,16 +878,19 @@ void or_verify(const or_scene* s, const uint32_t* ids, uint32_t n, int32_t mode,
         normalize3(d);
         f2d(Ln->pos, c); f2d(Ln->normal, nn); f2d(Ln->tangent, tt);
         cross3(nn, tt, bb);
+        /* with a distribution map the float32 parametrisation has decided
+         * validity; the double-precision tests below decide it otherwise */
+        const int by_map = s->dm_c[l] != NULL;
         double ndv = dot3(nn, d);
-        if (fabs(ndv) < 1e-6) amb |= OR_AMB_LIGHT;
-        if (!(ndv > 0.0)) {
+        if (!by_map && fabs(ndv) < 1e-6) amb |= OR_AMB_LIGHT;
+        if (!by_map && !(ndv > 0.0)) {
           invalid = 1;
         } else {
           double x1c[3];
           sub3(x1, c, x1c);
           double tp = dot3(nn, x1c) / ndv;
-          if (fabs(tp) < s->eps) amb |= OR_AMB_LIGHT;
-          if (!(tp > 0.0)) {
+          if (!by_map && fabs(tp) < s->eps) amb |= OR_AMB_LIGHT;
+          if (!by_map && !(tp > 0.0)) {
             invalid = 1;
           } else {
             double op[3], rel[3];
@@ -707,8 +898,10 @@ void or_verify(const or_scene* s, const uint32_t* ids, uint32_t n, int32_t mode,
             sub3(op, c, rel);
             double su = dot3(tt, rel), sv = dot3(bb, rel);
             double hw = 0.5 * Ln->size[0], hh = 0.5 * Ln->size[1];
-            if (fabs(fabs(su) - hw) < s->eps || fabs(fabs(sv) - hh) < s->eps) amb |= OR_AMB_LIGHT;
-            if (fabs(su) > hw || fabs(sv) > hh) invalid = 1;
+            if (!by_map) {
+              if (fabs(fabs(su) - hw) < s->eps || fabs(fabs(sv) - hh) < s->eps) amb |= OR_AMB_LIGHT;
+              if (fabs(su) > hw || fabs(sv) > hh) invalid = 1;
+            }
             if (!invalid && s->light_tilted[l]) {
               f2d(Lo->normal, no);
               double ratio = ndv / dot3(no, d);
@@ -729,6 +922,11 @@ void or_verify(const or_scene* s, const uint32_t* ids, uint32_t n, int32_t mode,
         nre++;
         ambv[i] = amb;
         continue;
+      }
+      if (dm_cell >= 0) {
+        cell = (l << 20) | (uint32_t)dm_cell;
+        info[i] = (w & ~OR_INFO_CELL_MASK) | cell;
+        counted[i] = 1;
       }
     }
 
@@ -873,7 +1071,80 @@ void or_verify(const or_scene* s, const uint32_t* ids, uint32_t n, int32_t mode,
     }
     ambv[i] = amb;
   }
+  /* ---- Compute DM_C, prune paths (Eq. 1, mark then edit), fill DM_C (Sec. 3.1) ---- */
+  uint64_t npr = 0, nfi = 0;
+  for (uint32_t l = 0; l < s->n_lights; ++l) {
+    if (!s->dm_c[l] || !s->light_moved[l]) continue;
+    uint32_t* dmc = s->dm_c[l];
+    const uint32_t ncell = s->dm_cells[l];
+    memset(dmc, 0, sizeof(uint32_t) * ncell);
+    for (uint32_t i = 0; i < n; ++i)
+      if (counted[i] && light_of(s, ids[i]) == l) dmc[info[i] & 0xFFFFFu]++;
+    /* pass 1: mark, with the counts before any pruning */
+    uint8_t* pruned = (uint8_t*)calloc(n ? n : 1, 1);
+    for (uint32_t i = 0; i < n; ++i) {
+      if (!counted[i] || light_of(s, ids[i]) != l) continue;
+      const uint32_t c = info[i] & 0xFFFFFu;
+      const uint32_t dc = dmc[c], dt = or_dm_target(s, l, c);
+      if (dc <= dt) continue;
+      uint32_t ctr[4] = {ids[i], 16u, frame, 0u};
+      uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+      uint32_t r[4];
+      or_philox4x32_10(ctr, key, r);
+      /* prune with probability (DM_C - DM_T) / DM_C, decided exactly on the 24-bit draw */
+      if ((uint64_t)(r[0] >> 8) * dc < ((uint64_t)(dc - dt) << 24)) {
+        pruned[i] = 1;
+        info[i] = info_make((l << 20) | c, 0, 0, 1, 0);
+        npr++;
+      }
+    }
+    /* pass 2: edit the counts */
+    for (uint32_t i = 0; i < n; ++i)
+      if (pruned[i]) dmc[info[i] & 0xFFFFFu]--;
+    free(pruned);
+    /* fill: free paths (fresh emissions of this light) in ascending id order
+     * take the cells' deficits in cell order; any further ones spread evenly */
+    uint64_t D = 0;
+    for (uint32_t c = 0; c < ncell; ++c) {
+      const uint32_t dt = or_dm_target(s, l, c);
+      if (dmc[c] < dt) D += dt - dmc[c];
+    }
+    uint64_t F = 0;
+    for (uint32_t i = 0; i < n; ++i)
+      if (light_of(s, ids[i]) == l && (info[i] & (OR_INFO_REPLACE | OR_INFO_REUSE_LIGHT | (15u << OR_INFO_START_SHIFT))) == OR_INFO_REPLACE) F++;
+    uint64_t j = 0;
+    uint32_t c = 0;
+    uint64_t used = 0;                         /* deficit slots of cells before c already taken */
+    for (uint32_t i = 0; i < n; ++i) {
+      if (light_of(s, ids[i]) != l) continue;
+      if ((info[i] & (OR_INFO_REPLACE | OR_INFO_REUSE_LIGHT | (15u << OR_INFO_START_SHIFT))) != OR_INFO_REPLACE) continue;
+      uint32_t cell;
+      if (j < D) {
+        for (;;) {                              /* the cell whose deficit range holds j */
+          const uint32_t dt = or_dm_target(s, l, c);
+          const uint64_t def = dmc[c] < dt ? dt - dmc[c] : 0;
+          if (j < used + def) break;
+          used += def;
+          ++c;
+        }
+        cell = c;
+      } else {
+        cell = (uint32_t)(((j - D) * ncell) / (F - D));
+      }
+      info[i] = info_make((l << 20) | cell, 0, 0, 1, 0);
+      ++j;
+      nfi++;
+    }
+    /* the filled cells now hold their new paths */
+    for (uint32_t i = 0; i < n; ++i)
+      if (light_of(s, ids[i]) == l &&
+          (info[i] & (OR_INFO_REPLACE | OR_INFO_REUSE_LIGHT | (15u << OR_INFO_START_SHIFT))) == OR_INFO_REPLACE)
+        dmc[info[i] & 0xFFFFFu]++;
+  }
+  free(counted);
   if (st) {
+    st->n_pruned += npr;
+    st->n_filled += nfi;
     st->paths += n;
     st->segments_tested += seg_t;
     st->segments_amb += seg_a;
@@ -922,6 +1193,7 @@ void or_retrace(const or_scene* s, const uint32_t* ids, uint32_t n, uint64_t see
       } else {
         double u[4];
         rng4(seed, pid, 0, frame, u);
+        if (s->dm_c[l]) dm_restrict(s, l, w & 0xFFFFFu, u);   /* within the path's cell */
         emit(L, u, o, d);
         for (int c = 0; c < 3; ++c) org[c] = (float)o[c];
         f2d(org, o);

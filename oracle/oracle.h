@@ -85,6 +85,8 @@ typedef struct {
   uint64_t n_tail;           /* paths to re-trace from a vertex > 0 */
   uint64_t n_updated;        /* paths reused with moved vertices (Alg. 1) */
   uint64_t n_truncated;      /* paths shortened because a re-traced ray missed */
+  uint64_t n_pruned;         /* paths pruned by Eq. 1 (distribution maps) */
+  uint64_t n_filled;         /* free paths given a distribution-map cell to fill */
 } or_stats;
 
 /* Scene: verts [n_tris][3][3] (object-local for dynamic objects),
@@ -121,8 +123,34 @@ void or_trace(const or_scene* s, const uint32_t* ids, uint32_t n, uint64_t seed,
  * replace / start / reuse-light bits, updates origins and moved vertices in
  * place, and returns the intersected-segment mask (bit i = segment i). */
 void or_verify(const or_scene* s, const uint32_t* ids, uint32_t n, int32_t mode, double tau,
-               uint32_t flags, uint32_t* info, float* origin, or_photon* photons,
-               uint32_t* seg_mask, uint32_t* amb, or_stats* st);
+               uint32_t flags, uint64_t seed, uint32_t frame, uint32_t* info, float* origin,
+               or_photon* photons, uint32_t* seg_mask, uint32_t* amb, or_stats* st);
+
+/* Distribution maps (Sec. 3.1).  or_scene_set_dm (after the poses are set)
+ * gives every rectangle light a map of rect[0] x rect[1] x rect[2] x rect[3]
+ * cells over its sample space (x, y, sin^2 theta, phi / 2 pi) and every point
+ * light one of point[0] x point[1] cells over ((1 - z) / 2, phi / 2 pi); a zero
+ * resolution leaves that kind of light without a map; -1 if a map has more
+ * than 2^20 cells.  With a map, a full trace puts path j of a light in cell
+ * floor(((j + 1) n - 1) / N) (so DM_C = DM_T), fresh emissions sample inside
+ * their cell, and or_verify, when the light moved, recomputes each kept
+ * path's cell with the float32 parametrisation (a path it does not map is
+ * invalid), counts DM_C, prunes with probability (DM_C - DM_T) / DM_C (Eq. 1;
+ * Philox counter (path, 16, frame), exact on the 24-bit draw) marking first
+ * and then editing the counts, and fills: the free paths in ascending order
+ * take the cells' deficits in cell order and spread any rest evenly.  DM_T(c)
+ * = floor(N (c + 1) / n) - floor(N c / n).  or_dm_reset sets DM_C = DM_T
+ * (after a full trace). */
+int32_t or_scene_set_dm(or_scene* s, const uint32_t rect[4], const uint32_t point[2]);
+void or_dm_reset(or_scene* s);
+uint32_t or_dm_cells(const or_scene* s, uint32_t light);
+uint32_t or_dm_target(const or_scene* s, uint32_t light, uint32_t cell);
+void or_dm_counts(const or_scene* s, uint32_t light, uint32_t* out);
+void or_dm_set_counts(or_scene* s, uint32_t light, const uint32_t* in);
+/* cell of a path (first photon x1, stored origin o) under the current pose, or -1 */
+int32_t or_dm_cell_of(const or_scene* s, uint32_t light, const float x1[3], const float o[3]);
+/* fraction of a turn of the angle of (x, y), as the parametrisation computes it */
+float or_dm_turn(float x, float y);
 
 /* Ascending list of the positions (into ids) whose replace bit is set;
  * returns the count (Sec. 5.2, pruned-paths array pattern). */
