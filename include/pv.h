@@ -94,7 +94,16 @@ typedef struct {
  *  object_albedo  [n_objects][3]  Lambertian albedo (> 0 in some channel)
  *  object_xform   [n_objects][12] initial 3x4 row-major [R|t] pose, NULL = identity
  *  scene_diag     length unit of the tolerances: t_min = 1e-5 diag for rays
- *                 leaving a surface, AreClose = 1e-5 diag (Alg. 1)           */
+ *                 leaving a surface, AreClose = 1e-5 diag (Alg. 1)
+ *  dm_rect        distribution map of every rectangle light (Sec. 3.1): cells
+ *                 along its sample dimensions x, y, sin^2 theta, phi / 2 pi
+ *                 (all zero: none), e.g. 8 x 8 x 64 x 64
+ *  dm_point       distribution map of every point light over (1 - z) / 2 and
+ *                 phi / 2 pi (all zero: none); a map holds at most 2^20 cells
+ * With a map, pv_trace_all spreads each light's paths evenly over its cells
+ * (DM_C = DM_T), fresh emissions sample inside the cell in the path's info
+ * word, and pv_verify_paths computes DM_C, prunes (Eq. 1) and fills for every
+ * light that moved (see pv_verify_paths). */
 typedef struct {
   const float* verts;
   uint32_t n_tris;
@@ -108,6 +117,8 @@ typedef struct {
   uint32_t max_bounces;
   float scene_diag;
   uint32_t flags;
+  uint32_t dm_rect[4];
+  uint32_t dm_point[2];
 } pv_scene_desc;
 
 /* Path buffers (device memory, caller-owned), the 2-D photon array of Sec. 4
@@ -130,6 +141,8 @@ typedef struct {
   int32_t mode;     /* PV_MODE_* */
   float tau;        /* Eq. 2 threshold T (relative); INFINITY accepts every energy */
   uint32_t flags;   /* PV_FLAG_* */
+  uint32_t frame;   /* frame number and seed of the prune draws (Philox counter */
+  uint64_t seed;    /* (path, 16, frame), key seed); used only with distribution maps */
 } pv_verify_params;
 
 /* Top-down XZ atlas (device, caller-owned): data[height][width][3] unsigned
@@ -157,6 +170,8 @@ typedef struct {
   uint32_t trace_rays;       /* rays traced by re-tracing / trace-all */
   uint32_t segments_tested;  /* segment-vs-moved-object tests */
   uint32_t photons_written;  /* photons stored by re-tracing / trace-all */
+  uint32_t n_pruned;         /* paths pruned by Eq. 1 (distribution maps) */
+  uint32_t n_filled;         /* free paths given a cell to fill (distribution maps) */
   uint64_t node_visits;      /* BVH nodes visited by every ray query of the call */
   uint64_t tri_tests;        /* ray-triangle tests of every ray query of the call */
 } pv_frame_stats;
@@ -184,7 +199,21 @@ int pv_update_dynamic(pv_scene* s, const float* xforms, const pv_light* lights, 
  * (Alg. 1, Eq. 2) which may move vertices in place.  Paths to re-trace get
  * the replace bit and a start vertex; their ids are written in ascending
  * order to d_list[0..*d_count) (d_list holds n entries).  d_stats may be
- * NULL.  Returns PV_ERR_ARG if paths->n differs from the lights' total. */
+ * NULL.  Returns PV_ERR_ARG if paths->n differs from the lights' total.
+ *
+ * Distribution maps (Sec. 3.1), for a light with a map that moved: the
+ * parametrisation (float32, correctly rounded basic operations; the angle
+ * from half-angle steps and the Gregory series) decides each kept path's
+ * cell and whether it still comes from the light (the rectangle's extent
+ * test is replaced by it) -- "compute DM_C", fused with the origin update as
+ * in Sec. 4; then paths of cells with DM_C > DM_T are pruned with
+ * probability (DM_C - DM_T) / DM_C (Eq. 1), decided exactly on the 24-bit
+ * draw of Philox counter (path, 16, frame), marking first and editing the
+ * counts in a second pass (Sec. 4); then the free paths (pruned, or no
+ * longer from the light) in ascending id order take the cells' deficits
+ * DM_T - DM_C in cell order and spread any further ones evenly ("fill
+ * DM_C").  DM_T(c) = floor(N (c + 1) / n) - floor(N c / n) for N paths and
+ * n cells. */
 int pv_verify_paths(pv_scene* s, const pv_paths* paths, const pv_verify_params* params,
                     uint32_t* d_list, uint32_t* d_count, pv_frame_stats* d_stats, void* stream);
 
@@ -296,6 +325,12 @@ int pv_set_traversal_limit(pv_scene* s, uint32_t max_visits);
 /* Synchronise the scene's last stream and return the first device-side error
  * recorded since the last call (then clear it), or PV_OK. */
 int pv_read_device_status(pv_scene* s);
+
+/* Number of cells of light ``light``'s distribution map (0: none), or
+ * PV_ERR_ARG.  pv_read_distribution_map synchronises the scene's last stream
+ * and copies its current counts DM_C to h_counts (host, that many entries). */
+int pv_distribution_map_cells(const pv_scene* s, uint32_t light);
+int pv_read_distribution_map(pv_scene* s, uint32_t light, uint32_t* h_counts);
 
 void pv_destroy_scene(pv_scene* s);
 const char* pv_status_string(int status);

@@ -73,7 +73,7 @@ typedef struct {
  * only through pv_batch_frame.  Allocates the batch's device tables and
  * pinned staging (synchronous).  PV_ERR_ARG for bad arguments,
  * PV_ERR_LIMIT for too many scenes, PV_ERR_STATE for a scene built with
- * PV_BUILD_DYN_REBUILD. */
+ * PV_BUILD_DYN_REBUILD or with distribution maps. */
 int pv_batch_create(const pv_batch_scene* scenes, uint32_t n, const pv_verify_params* params, void* stream,
                     pv_batch** out);
 

@@ -533,16 +533,17 @@ float or_dm_turn(float x, float y) {
   t = t / (1.0f + sqrtf(1.0f + t * t));
   t = t / (1.0f + sqrtf(1.0f + t * t));
   const float q = t * t;
-  float a = 1.0f / 9.0f;
-  a = 1.0f / 7.0f - q * a;
-  a = 1.0f / 5.0f - q * a;
-  a = 1.0f / 3.0f - q * a;
+  /* 1/9, 1/7, 1/5, 1/3, pi/2, pi, 2 pi rounded to float32 */
+  float a = 0x1.c71c72p-4f;
+  a = 0x1.24924ap-3f - q * a;
+  a = 0x1.99999ap-3f - q * a;
+  a = 0x1.555556p-2f - q * a;
   a = 1.0f - q * a;
   a = 4.0f * (t * a);
-  if (ay > ax) a = 1.57079632679489662f - a;
-  if (x < 0.0f) a = 3.14159265358979324f - a;
-  if (y < 0.0f) a = 6.28318530717958648f - a;
-  const float f = a / 6.28318530717958648f;
+  if (ay > ax) a = 0x1.921fb6p+0f - a;
+  if (x < 0.0f) a = 0x1.921fb6p+1f - a;
+  if (y < 0.0f) a = 0x1.921fb6p+2f - a;
+  const float f = a / 0x1.921fb6p+2f;
   return f < 1.0f ? f : 0.0f;
 }
 

@@ -34,7 +34,7 @@ EXPORTS = ["pv_build_scene", "pv_update_dynamic", "pv_verify_paths", "pv_retrace
            "pv_read_device_status", "pv_destroy_scene", "pv_status_string", "pv_theta_size", "pv_theta_current",
            "pv_model_deposit", "pv_adjoint_deposit", "pv_budget_list", "pv_batch_create", "pv_batch_frame",
            "pv_batch_autotune", "pv_batch_tuning", "pv_batch_set_config", "pv_batch_get_config", "pv_batch_step_times",
-           "pv_batch_destroy"]
+           "pv_batch_destroy", "pv_distribution_map_cells", "pv_read_distribution_map"]
 PV_BATCH_MAX_SCENES = 32
 PV_STATIC_COMPACT_MAX_PATHS = 1 << 26
 
@@ -52,7 +52,8 @@ class PvSceneDesc(C.Structure):
     _fields_ = [("verts", C.c_void_p), ("n_tris", C.c_uint32), ("tri_object", C.c_void_p), ("n_objects", C.c_uint32),
                 ("object_dynamic", C.c_void_p), ("object_albedo", C.c_void_p), ("object_xform", C.c_void_p),
                 ("n_lights", C.c_uint32), ("lights", C.c_void_p), ("max_bounces", C.c_uint32),
-                ("scene_diag", C.c_float), ("flags", C.c_uint32)]
+                ("scene_diag", C.c_float), ("flags", C.c_uint32), ("dm_rect", C.c_uint32 * 4),
+                ("dm_point", C.c_uint32 * 2)]
 
 
 class PvPaths(C.Structure):
@@ -61,7 +62,8 @@ class PvPaths(C.Structure):
 
 
 class PvVerifyParams(C.Structure):
-    _fields_ = [("mode", C.c_int32), ("tau", C.c_float), ("flags", C.c_uint32)]
+    _fields_ = [("mode", C.c_int32), ("tau", C.c_float), ("flags", C.c_uint32), ("frame", C.c_uint32),
+                ("seed", C.c_uint64)]
 
 
 class PvAtlas(C.Structure):
@@ -80,7 +82,7 @@ class PvBatchConfig(C.Structure):
 
 
 STATS_FIELDS = ["n_paths", "n_listed", "n_reemit", "n_tail", "n_updated", "n_truncated", "n_cont", "vis_rays",
-                "cont_rays", "trace_rays", "segments_tested", "photons_written"]
+                "cont_rays", "trace_rays", "segments_tested", "photons_written", "n_pruned", "n_filled"]
 STATS_FIELDS64 = ["node_visits", "tri_tests"]
 STATS_WORDS = len(STATS_FIELDS) + 2 * len(STATS_FIELDS64)
 
@@ -121,6 +123,8 @@ def load():
         L.pv_batch_get_config.argtypes = [P, C.POINTER(PvBatchConfig)]
         L.pv_batch_step_times.argtypes = [P, P]
         L.pv_batch_destroy.argtypes = [P]
+        L.pv_distribution_map_cells.argtypes = [P, C.c_uint32]
+        L.pv_read_distribution_map.argtypes = [P, C.c_uint32, P]
         L.pv_batch_destroy.restype = None
         L.pv_status_string.argtypes = [C.c_int]
         L.pv_status_string.restype = C.c_char_p
@@ -200,8 +204,11 @@ class Paths:
 
 
 def pv_build_scene(verts, tri_object, object_dynamic, object_albedo, lights, max_bounces: int, scene_diag: float,
-                   object_xform=None, flags: int = 0, stream=None) -> C.c_void_p:
-    """Build a scene from host arrays (copied); returns the opaque handle."""
+                   object_xform=None, flags: int = 0, stream=None, dm_rect=(0, 0, 0, 0),
+                   dm_point=(0, 0)) -> C.c_void_p:
+    """Build a scene from host arrays (copied); returns the opaque handle.
+    dm_rect / dm_point: distribution-map resolutions of the rectangle and
+    point lights (zeros: no map)."""
     L = load()
     keep = [np.ascontiguousarray(verts, np.float32), np.ascontiguousarray(tri_object, np.uint32),
             np.ascontiguousarray(object_dynamic, np.uint8), np.ascontiguousarray(object_albedo, np.float32)]
@@ -209,7 +216,8 @@ def pv_build_scene(verts, tri_object, object_dynamic, object_albedo, lights, max
     la = make_lights(lights)
     d = PvSceneDesc(keep[0].ctypes.data, keep[0].shape[0], keep[1].ctypes.data, keep[2].shape[0], keep[2].ctypes.data,
                     keep[3].ctypes.data, 0 if xf is None else xf.ctypes.data, len(lights), C.cast(la, C.c_void_p),
-                    int(max_bounces), float(scene_diag), int(flags))
+                    int(max_bounces), float(scene_diag), int(flags), (C.c_uint32 * 4)(*[int(v) for v in dm_rect]),
+                    (C.c_uint32 * 2)(*[int(v) for v in dm_point]))
     h = C.c_void_p()
     _check("pv_build_scene", L.pv_build_scene(C.byref(d), _stream(stream), C.byref(h)))
     return h
@@ -224,9 +232,10 @@ def pv_update_dynamic(scene, xforms=None, lights=None, stream=None) -> None:
 
 
 def pv_verify_paths(scene, paths: Paths, mode: int, tau: float, flags: int, d_list, d_count, d_stats=None,
-                    stream=None) -> None:
+                    stream=None, seed: int = 0, frame: int = 0) -> None:
+    """seed / frame key the distribution maps' prune draws."""
     ps = paths.struct()
-    prm = PvVerifyParams(int(mode), float(tau), int(flags))
+    prm = PvVerifyParams(int(mode), float(tau), int(flags), int(frame), int(seed))
     _check("pv_verify_paths", load().pv_verify_paths(scene, C.byref(ps), C.byref(prm), _ptr(d_list), _ptr(d_count),
                                                       _ptr(d_stats), _stream(stream)))
 
@@ -370,7 +379,7 @@ def pv_batch_create(items, mode: int, tau: float, flags: int = 0, stream=None) -
         arr[i].d_count = d_count.data_ptr()
         arr[i].d_stats = d_stats.data_ptr() if d_stats is not None else None
         arr[i].seed = int(seed)
-    prm = PvVerifyParams(int(mode), float(tau), int(flags))
+    prm = PvVerifyParams(int(mode), float(tau), int(flags), 0, 0)
     h = C.c_void_p()
     _check("pv_batch_create", load().pv_batch_create(arr, len(items), C.byref(prm), _stream(stream), C.byref(h)))
     return Batch(h, len(items))
@@ -438,6 +447,21 @@ def pv_batch_destroy(batch: Batch) -> None:
     if batch and batch.handle:
         load().pv_batch_destroy(batch.handle)
         batch.handle = None
+
+
+def pv_distribution_map_cells(scene, light: int) -> int:
+    n = int(load().pv_distribution_map_cells(scene, int(light)))
+    if n < 0:
+        _check("pv_distribution_map_cells", n)
+    return n
+
+
+def pv_read_distribution_map(scene, light: int) -> np.ndarray:
+    """Current counts DM_C of a light's distribution map (synchronises)."""
+    out = np.zeros(pv_distribution_map_cells(scene, light), np.uint32)
+    _check("pv_read_distribution_map", load().pv_read_distribution_map(scene, int(light),
+                                                                        out.ctypes.data_as(C.c_void_p)))
+    return out
 
 
 def pv_set_traversal_limit(scene, max_visits: int) -> None:

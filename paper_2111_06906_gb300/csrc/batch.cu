@@ -636,7 +636,7 @@ extern "C" int pv_batch_create(const pv_batch_scene* scenes, uint32_t n, const p
   for (uint32_t i = 0; i < n; ++i) {
     const pv_batch_scene& it = scenes[i];
     if (pvh::check_paths(it.scene, &it.paths) != PV_OK || !it.d_list || !it.d_count) return PV_ERR_ARG;
-    if (it.scene->flags & PV_BUILD_DYN_REBUILD) return PV_ERR_STATE;
+    if ((it.scene->flags & PV_BUILD_DYN_REBUILD) || it.scene->has_dm) return PV_ERR_STATE;
     for (uint32_t j = 0; j < i; ++j)
       if (scenes[j].scene == it.scene) return PV_ERR_ARG;
   }

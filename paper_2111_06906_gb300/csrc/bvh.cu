@@ -428,6 +428,8 @@ void radix_sort(uint64_t*& k0, uint32_t*& v0, uint64_t*& k1, uint32_t*& v1, uint
 
 uint32_t radix_tiles(uint32_t n) { return (n + kRsTile - 1) / kRsTile; }
 
+void exclusive_scan(uint32_t* data, uint32_t m, cudaStream_t st) { k_rs_scan<<<1, 1024, 0, st>>>(data, m); }
+
 static inline uint32_t blocks(uint32_t n, uint32_t t) { return (n + t - 1) / t; }
 
 // ---- oversized-triangle references (host)

@@ -71,6 +71,16 @@ struct LightPose {
   uint32_t n_paths;
 };
 
+// Distribution map of one light (Sec. 3.1): cells over its emission sample
+// space (see dm_core.cuh) and its device counts DM_C.
+struct DmLight {
+  uint32_t res[4];           // cells per dimension: rectangle x, y, theta, phi; point theta, phi
+  uint32_t dims;             // 4 rectangle, 2 point, 0 no map
+  uint32_t cells;
+  uint32_t n_paths;          // N: DM_T spreads N paths over the cells
+  uint32_t* dmc;             // DM_C [cells]
+};
+
 // light state passed by value to the kernels
 struct FrameLights {
   LightPose cur[PV_MAX_LIGHTS];
@@ -79,6 +89,7 @@ struct FrameLights {
   uint32_t n;
   uint32_t moved_mask;       // bit l: light l moved (position, frame or size)
   uint32_t tilted_mask;      // bit l: its normal changed
+  DmLight dm[PV_MAX_LIGHTS];
 };
 
 // read-only scene view passed by value to the kernels

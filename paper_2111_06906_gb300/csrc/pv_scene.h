@@ -73,6 +73,15 @@ struct pv_scene {
   uint64_t* ws_tiles = nullptr;      // [n_tiles + 1] decoupled look-back tile states
   uint32_t n_tiles = 0;
   uint32_t* ws_ctr = nullptr;        // [16] work counters
+  // distribution maps (Sec. 3.1), per light; workspace shared by the lights
+  uint32_t dm_res[PV_MAX_LIGHTS][4] = {};
+  uint32_t dm_dims[PV_MAX_LIGHTS] = {}, dm_cells[PV_MAX_LIGHTS] = {};
+  uint32_t* dm_c[PV_MAX_LIGHTS] = {};         // DM_C [cells]
+  uint32_t* dm_flag = nullptr;                // [n_paths] pruned mark, then free-path flags
+  uint32_t* dm_free = nullptr;                // [n_paths] free paths, ascending
+  uint32_t* dm_scan = nullptr;                // [max cells + 1] deficits, then their exclusive prefix
+  uint32_t* dm_ctr = nullptr;                 // [8] free paths per light, free-list length
+  bool has_dm = false;
   uint64_t* b_keys[2] = {nullptr, nullptr};   // [n_paths] budget ranking sort keys (ping-pong)
   uint32_t* b_vals[2] = {nullptr, nullptr};
   uint32_t* b_hist = nullptr;                 // [256][radix tiles of n_paths]
@@ -103,7 +112,16 @@ int stage_poses(pv_scene* s, const float* xforms, const pv_light* lights);
 // wide node on its deepest root-to-leaf path), measured once (synchronous)
 int stack_need(pv_scene* s, uint32_t* out);
 
+// dm.cu: distribution maps.  dm_reset sets DM_C = DM_T for every light with a
+// map; dm_frame runs count-independent steps after verification of a frame in
+// which lights with maps moved (prune, edit, free list, fill).
+void dm_reset(pv_scene* s, cudaStream_t st);
+int dm_frame(pv_scene* s, const pv_paths* p, const pvk::FrameLights& L, const pv_verify_params* prm,
+             pv_frame_stats* stats, cudaStream_t st);
+
 // bvh.cu
+// exclusive prefix sum of m counters in place (one block)
+void exclusive_scan(uint32_t* data, uint32_t m, cudaStream_t st);
 // stable LSD radix sort of (key, value) pairs on key bits [lo_bit, hi_bit);
 // the buffers swap so that k0/v0 hold the result; hist holds 256 * radix_tiles(n)
 void radix_sort(uint64_t*& k0, uint32_t*& v0, uint64_t*& k1, uint32_t*& v1, uint32_t n, uint32_t* hist, int lo_bit,

@@ -51,7 +51,8 @@ void free_scene(pv_scene* s) {
                   s->d_fit_flags, s->d_tri_slot, s->objs, s->r_keys[0], s->r_keys[1], s->r_vals[0], s->r_vals[1],
                   s->r_hist, s->r_tris, s->r_local, s->r_prim, s->prim_slot, s->prim_dyn, s->prim_alb, s->prim_nrm,
                   s->xf_old, s->xf_new, s->ws_mask, s->ws_cont, s->ws_tiles, s->ws_ctr, s->status, s->b_keys[0], s->b_keys[1],
-                  s->b_vals[0], s->b_vals[1], s->b_hist};
+                  s->b_vals[0], s->b_vals[1], s->b_hist, s->dm_c[0], s->dm_c[1], s->dm_c[2], s->dm_c[3],
+                  s->dm_flag, s->dm_free, s->dm_scan, s->dm_ctr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete s;
@@ -97,6 +98,14 @@ FrameLights frame_lights(const pv_scene* s) {
     if (std::memcmp(s->lights_old[l].normal, s->lights_new[l].normal, sizeof(float) * 3) != 0) L.tilted_mask |= 1u << l;
   }
   for (uint32_t l = s->n_lights; l < PV_MAX_LIGHTS; ++l) L.first[l + 1] = L.first[l];
+  for (uint32_t l = 0; l < s->n_lights; ++l) {
+    DmLight& D = L.dm[l];
+    D.dims = s->dm_dims[l];
+    D.cells = s->dm_cells[l];
+    D.n_paths = s->lights_new[l].n_paths;
+    D.dmc = s->dm_c[l];
+    for (int k = 0; k < 4; ++k) D.res[k] = s->dm_res[l][k];
+  }
   return L;
 }
 
@@ -117,9 +126,32 @@ extern "C" int pv_build_scene(const pv_scene_desc* d, void* stream, pv_scene** o
     if (d->tri_object[t] >= d->n_objects) return PV_ERR_ARG;
   if (d->n_tris >= (1u << 31)) return PV_ERR_LIMIT;
 
+  uint32_t dm_res[PV_MAX_LIGHTS][4] = {}, dm_dims[PV_MAX_LIGHTS] = {}, dm_cells[PV_MAX_LIGHTS] = {};
+  for (uint32_t l = 0; l < d->n_lights; ++l) {
+    const bool rect = d->lights[l].type == PV_LIGHT_RECT;
+    const uint32_t dims = rect ? 4u : 2u;
+    uint64_t cells = 1;
+    for (uint32_t k = 0; k < dims; ++k) {
+      const uint32_t r = rect ? d->dm_rect[k] : d->dm_point[k];
+      dm_res[l][k] = r;
+      cells *= r;
+    }
+    if (cells == 0) continue;                  // no map for this light
+    if (cells > (1u << 20)) return PV_ERR_LIMIT;
+    dm_dims[l] = dims;
+    dm_cells[l] = (uint32_t)cells;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   pv_scene* s = new pv_scene;
   s->flags = d->flags;
+  uint32_t dm_max = 0;
+  for (uint32_t l = 0; l < PV_MAX_LIGHTS; ++l) {
+    for (int k = 0; k < 4; ++k) s->dm_res[l][k] = dm_res[l][k];
+    s->dm_dims[l] = dm_dims[l];
+    s->dm_cells[l] = dm_cells[l];
+    if (dm_cells[l]) s->has_dm = true;
+    dm_max = std::max(dm_max, dm_cells[l]);
+  }
   s->n_tris = d->n_tris;
   s->n_objects = d->n_objects;
   s->B = d->max_bounces;
@@ -195,6 +227,17 @@ extern "C" int pv_build_scene(const pv_scene_desc* d, void* stream, pv_scene** o
   fail(cudaMalloc(&s->ws_mask, (size_t)s->n_paths_total * sizeof(uint32_t)));
   fail(cudaMalloc(&s->ws_cont, (size_t)s->n_paths_total * sizeof(uint32_t)));
   fail(cudaMalloc(&s->ws_tiles, (size_t)(s->n_tiles + 1) * sizeof(uint64_t)));
+  for (uint32_t l = 0; l < PV_MAX_LIGHTS; ++l)
+    if (s->dm_cells[l]) {
+      fail(cudaMalloc(&s->dm_c[l], (size_t)s->dm_cells[l] * sizeof(uint32_t)));
+      if (s->dm_c[l]) fail(cudaMemsetAsync(s->dm_c[l], 0, (size_t)s->dm_cells[l] * sizeof(uint32_t), st));
+    }
+  if (s->has_dm) {
+    fail(cudaMalloc(&s->dm_flag, (size_t)s->n_paths_total * sizeof(uint32_t)));
+    fail(cudaMalloc(&s->dm_free, (size_t)s->n_paths_total * sizeof(uint32_t)));
+    fail(cudaMalloc(&s->dm_scan, ((size_t)dm_max + 1) * sizeof(uint32_t)));
+    fail(cudaMalloc(&s->dm_ctr, 8 * sizeof(uint32_t)));
+  }
   for (int b = 0; b < 2; ++b) {
     fail(cudaMalloc(&s->b_keys[b], (size_t)s->n_paths_total * sizeof(uint64_t)));
     fail(cudaMalloc(&s->b_vals[b], (size_t)s->n_paths_total * sizeof(uint32_t)));
@@ -310,6 +353,19 @@ extern "C" int pv_set_traversal_limit(pv_scene* s, uint32_t max_visits) {
   if (!s) return PV_ERR_ARG;
   s->visit_limit = max_visits;
   return PV_OK;
+}
+
+extern "C" int pv_distribution_map_cells(const pv_scene* s, uint32_t light) {
+  if (!s || light >= s->n_lights) return PV_ERR_ARG;
+  return (int)s->dm_cells[light];
+}
+
+extern "C" int pv_read_distribution_map(pv_scene* s, uint32_t light, uint32_t* h_counts) {
+  if (!s || light >= s->n_lights || !h_counts) return PV_ERR_ARG;
+  if (!s->dm_cells[light]) return PV_OK;
+  if (cudaStreamSynchronize(s->last_stream) != cudaSuccess) return PV_ERR_CUDA;
+  return pvh::cuda_status(cudaMemcpy(h_counts, s->dm_c[light], (size_t)s->dm_cells[light] * sizeof(uint32_t),
+                                     cudaMemcpyDeviceToHost));
 }
 
 extern "C" int pv_read_device_status(pv_scene* s) {

@@ -146,5 +146,6 @@ extern "C" int pv_trace_all(pv_scene* s, const pv_paths* paths, uint64_t seed, u
   cudaStream_t st = (cudaStream_t)stream;
   s->last_stream = st;
   pvh::launch_trace(s, paths, nullptr, nullptr, seed, frame, d_stats, st);
+  if (s->has_dm) pvh::dm_reset(s, st);            // a full trace is stratified: DM_C = DM_T
   return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
 }

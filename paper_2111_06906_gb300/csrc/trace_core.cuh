@@ -3,6 +3,7 @@
 // paper generates rays (Sec. 4), from the light (start 0) or by Russian
 // roulette and a cosine-weighted bounce at the first photon to re-trace.
 #pragma once
+#include "dm_core.cuh"
 #include "pv_scene.h"
 
 namespace pvk {
@@ -65,7 +66,8 @@ __device__ __forceinline__ bool init_path(const SceneView& sv, const FrameLights
   uint32_t l = 0;
   if (all) {
     while (l + 1 < L.n && pid >= L.first[l + 1]) ++l;
-    s.cell = l << 20;
+    // a full trace is stratified over the light's distribution map (DM_C = DM_T)
+    s.cell = (l << 20) | (L.dm[l].dims ? dm_stratified(L.dm[l], pid - L.first[l]) : 0u);
   } else {
     l = info_light(w);
     s.cell = w & PV_INFO_CELL_MASK;
@@ -79,10 +81,12 @@ __device__ __forceinline__ bool init_path(const SceneView& sv, const FrameLights
       const float3 o = load_origin(A, pid);
       r = make_ray(o, normalize_exact(f3(A.pa[pid]) - o), sv.tmin);
       s.E = f3(A.pb[pid]);
-    } else {                                     // fresh emission
+    } else {                                     // fresh emission, inside the path's cell if the light has a map
       const LightPose& Lp = L.cur[l];
       float3 o, d;
-      emit(Lp, rng4(A.seed, pid, 0, A.frame), o, d);
+      float4 u = rng4(A.seed, pid, 0, A.frame);
+      if (L.dm[l].dims) dm_restrict(L.dm[l], s.cell & 0xFFFFFu, u);
+      emit(Lp, u, o, d);
       A.origin[pid] = o.x;
       A.origin[n + pid] = o.y;
       A.origin[2 * (size_t)n + pid] = o.z;

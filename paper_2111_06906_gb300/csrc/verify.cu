@@ -66,6 +66,10 @@ extern "C" int pv_verify_paths(pv_scene* s, const pv_paths* paths, const pv_veri
   const SceneView sv = pvh::view(s);
   const FrameLights L = pvh::frame_lights(s);
   if (cudaMemsetAsync(s->ws_ctr, 0, 16 * sizeof(uint32_t), st) != cudaSuccess) return PV_ERR_CUDA;
+  for (uint32_t l = 0; l < s->n_lights; ++l)       // DM_C of moved lights with a map is counted afresh
+    if (L.dm[l].dims && ((L.moved_mask >> l) & 1u))
+      if (cudaMemsetAsync(L.dm[l].dmc, 0, (size_t)L.dm[l].cells * sizeof(uint32_t), st) != cudaSuccess)
+        return PV_ERR_CUDA;
   VerifyArgs A;
   A.n = n;
   A.info = paths->info;
@@ -111,6 +115,7 @@ extern "C" int pv_verify_paths(pv_scene* s, const pv_paths* paths, const pv_veri
     C.stats = d_stats;
     k_continue<<<s->cont_blocks, 128, 0, st>>>(sv, C);
   }
+  if (s->has_dm && (rc = pvh::dm_frame(s, paths, L, params, d_stats, st)) != PV_OK) return rc;
   pvh::launch_compact(s, paths->info, n, d_list, d_count, d_stats ? &d_stats->n_listed : nullptr, st);
   return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
 }

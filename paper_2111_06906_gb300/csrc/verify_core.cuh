@@ -7,6 +7,7 @@
 // continue_path: the error-based threshold continuation of Sec. 3.3, Alg. 1
 //   and Eq. 2, for one path flagged by verify_block in error mode.
 #pragma once
+#include "dm_core.cuh"
 #include "pv_scene.h"
 
 namespace pvk {
@@ -158,9 +159,16 @@ __device__ __forceinline__ PathCheck origin_stage(const SceneView& sv, const Fra
   v.blocked1 = false;
   bool invalid = false;
   if ((L.moved_mask >> l) & 1u) {
-    if (v.nseg == 0) {
-      invalid = true;                        // an escaped path has no vertex to re-aim at
+    const DmLight& D = L.dm[l];
+    int dm_cell = -1;
+    if (D.dims && v.nseg > 0) {              // Compute DM_C: the parametrisation decides (Sec. 3.1)
+      float u[4];
+      if (dm_param(L.cur[l], f3(A.pa[p]), v.o, u)) dm_cell = (int)dm_cell_of_u(D, u);
+    }
+    if (v.nseg == 0 || (D.dims && dm_cell < 0)) {
+      invalid = true;                        // an escaped path has no vertex to re-aim at; or off the map
     } else {
+      const bool by_map = D.dims != 0;       // the map has decided validity
       const float4 x1v = A.pa[p];
       const float3 x1 = f3(x1v);
       const LightPose& Ln = L.cur[l];
@@ -179,16 +187,17 @@ __device__ __forceinline__ PathCheck origin_stage(const SceneView& sv, const Fra
       } else {
         const float3 d = normalize_exact(x1 - o);
         const float nd = dot(Ln.n, d);
-        if (!(nd > 0.0f)) {
+        if (!by_map && !(nd > 0.0f)) {
           invalid = true;
         } else {
           const float tp = dot(Ln.n, x1 - Ln.pos) / nd;
-          if (!(tp > 0.0f)) {
+          if (!by_map && !(tp > 0.0f)) {
             invalid = true;
           } else {
             const float3 op = make_float3(fmaf(-tp, d.x, x1.x), fmaf(-tp, d.y, x1.y), fmaf(-tp, d.z, x1.z));
             const float3 rel = op - Ln.pos;
-            if (fabsf(dot(Ln.t, rel)) > 0.5f * Ln.size.x || fabsf(dot(Ln.b, rel)) > 0.5f * Ln.size.y) invalid = true;
+            if (!by_map && (fabsf(dot(Ln.t, rel)) > 0.5f * Ln.size.x || fabsf(dot(Ln.b, rel)) > 0.5f * Ln.size.y))
+              invalid = true;
             if (!invalid && ((L.tilted_mask >> l) & 1u)) {
               const float ratio = nd / dot(L.old[l].n, d);
               const float4 e = A.pb[p];
@@ -208,6 +217,10 @@ __device__ __forceinline__ PathCheck origin_stage(const SceneView& sv, const Fra
     if (invalid) {
       A.info[p] = info_make(v.cell, 0, 0, true, false);
       ++c_reemit;
+    } else if (dm_cell >= 0) {
+      atomicAdd(D.dmc + dm_cell, 1u);
+      v.cell = (l << 20) | (uint32_t)dm_cell;
+      if (v.cell != (w & PV_INFO_CELL_MASK)) A.info[p] = (w & ~PV_INFO_CELL_MASK) | v.cell;
     }
   }
   v.test = !invalid && (sv.moved || v.blocked1);

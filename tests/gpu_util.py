@@ -9,9 +9,10 @@ import oracle
 import paper_2111_06906_gb300 as pv
 
 
-def lib_scene(sc, flags: int = 0, frame: int = 1):
+def lib_scene(sc, flags: int = 0, frame: int = 1, dm_rect=(0, 0, 0, 0), dm_point=(0, 0)):
     return pv.pv_build_scene(sc.verts, sc.tri_object, sc.object_dynamic, sc.object_albedo, sc.lights(frame),
-                             sc.max_bounces, sc.diag, object_xform=sc.xforms(frame), flags=flags)
+                             sc.max_bounces, sc.diag, object_xform=sc.xforms(frame), flags=flags, dm_rect=dm_rect,
+                             dm_point=dm_point)
 
 
 def advance(h, sc, frame: int) -> None:
