@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-dm", action="store_true", help="skip the distribution-map frame measurement")
     ap.add_argument("--tune-frames", type=int, default=1, help="batch16: frames per tuner candidate")
     return ap.parse_args()
 
@@ -316,6 +317,9 @@ def run_ours(args, ws, rank, local):
                "d2h_bytes_per_step": int(host_atlas.numel() * 8 + host_stats.numel() * 4), "_s": e2e_s}
     # ---- differentiable model: forward splat and adjoint of an L2 atlas loss
     adjoint = None if args.no_adjoint else time_adjoint(pv, h, P, sc, N, A, K, W, stream, dev)
+    # ---- the same reuse frames with distribution maps on the lights (Sec. 3.1)
+    dm = None if args.no_dm or args.workload == "tiny_box" else time_dm(pv, sc, mode, tau, seed, K, W, xfs, lts,
+                                                                          stream, dev)
     status2 = pv.pv_read_device_status(h)
     pv.pv_destroy_scene(h)
 
@@ -374,6 +378,8 @@ def run_ours(args, ws, rank, local):
            "gpu_launches": launches_per_frame * K, "clocks": clocks.summary()}
     if adjoint:
         cfg["adjoint"] = adjoint
+    if dm:
+        cfg["distribution_maps"] = dm
     if e2e:
         e2e["value"] = ws * N / e2e_s
         e2e.pop("_s")
@@ -381,6 +387,48 @@ def run_ours(args, ws, rank, local):
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(args.workload, mode, tau, args.cpu_seconds)
     print(json.dumps(out), flush=True)
+
+
+def time_dm(pv, sc, mode, tau, seed, K, W, xfs, lts, stream, dev):
+    """Reuse frames (update, verify with compute DM_C / prune / fill, re-trace)
+    of a second copy of the scene whose lights carry distribution maps:
+    8 x 8 x 64 x 64 for rectangles, 64 x 64 for point lights."""
+    import torch
+    rect, point = (8, 8, 64, 64), (64, 64)
+    h = pv.pv_build_scene(sc.verts, sc.tri_object, sc.object_dynamic, sc.object_albedo, lts[1], sc.max_bounces,
+                          sc.diag, object_xform=xfs[1], dm_rect=rect, dm_point=point)
+    N = sc.n_paths
+    P = pv.Paths.allocate(N, sc.max_bounces, dev)
+    lst = torch.zeros(N, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    stats = torch.zeros(K, pv.STATS_WORDS, dtype=torch.int32, device=dev)
+    scratch = pv.new_stats(dev)
+    pv.pv_trace_all(h, P, seed, 1)
+    ev = []
+    for i in range(W + K):
+        f = 2 + i
+        st = scratch if i < W else stats[i - W]
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        pv.pv_update_dynamic(h, xfs[f], lts[f])
+        pv.pv_verify_paths(h, P, mode, tau, 0, lst, cnt, st, seed=seed, frame=f)
+        e[1].record(stream)
+        pv.pv_retrace_invalid(h, P, lst, cnt, seed, f, st)
+        e[2].record(stream)
+        if i >= W:
+            ev.append(e)
+    torch.cuda.synchronize()
+    rows = [pv.stats_dict(stats[i]) for i in range(K)]
+    status = pv.pv_read_device_status(h)
+    cells = [pv.pv_distribution_map_cells(h, l) for l in range(len(lts[1]))]
+    pv.pv_destroy_scene(h)
+    verify_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    retrace_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    mean = lambda k: float(np.mean([r[k] for r in rows]))
+    return {"maps": {"rect": list(rect), "point": list(point)}, "cells_per_light": cells,
+            "frame_ms": verify_ms + retrace_ms, "update_verify_dm_ms": verify_ms, "retrace_ms": retrace_ms,
+            "pruned_per_frame": mean("n_pruned"), "filled_per_frame": mean("n_filled"),
+            "listed_per_frame": mean("n_listed"), "device_status": status}
 
 
 def time_adjoint(pv, h, P, sc, N, A, K, W, stream, dev):
