@@ -57,6 +57,22 @@ class _Light(C.Structure):
                 ("n_paths", C.c_uint32)]
 
 
+class Camera(C.Structure):
+    """Pinhole camera: pos, target, up, vertical field of view (radians), pixels."""
+    _fields_ = [("pos", C.c_float * 3), ("target", C.c_float * 3), ("up", C.c_float * 3), ("fov_y", C.c_float),
+                ("width", C.c_uint32), ("height", C.c_uint32)]
+
+    @classmethod
+    def make(cls, pos, target, up, fov_y, width, height):
+        c = cls()
+        c.pos[:] = [float(v) for v in pos]
+        c.target[:] = [float(v) for v in target]
+        c.up[:] = [float(v) for v in up]
+        c.fov_y = float(fov_y)
+        c.width, c.height = int(width), int(height)
+        return c
+
+
 class _Stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "paths", "segments_tested", "segments_amb", "vis_rays", "cont_rays", "trace_rays",
@@ -94,6 +110,7 @@ def lib():
         L.or_dm_set_counts.argtypes = [P, C.c_uint32, P]
         L.or_dm_cell_of.restype = C.c_int32
         L.or_dm_cell_of.argtypes = [P, C.c_uint32, P, P]
+        L.or_splat.argtypes = [P, P, C.c_uint32, P, P, P, P, C.c_double, P, P]
         L.or_dm_turn.restype = C.c_float
         L.or_dm_turn.argtypes = [C.c_float, C.c_float]
         L.or_compact.restype = C.c_uint32
@@ -237,6 +254,15 @@ class OracleScene:
                          _p(paths.photons), _p(amb), C.byref(st))
         paths.amb |= amb
         return st.as_dict()
+
+    # ---- screen-space splat (Fig. 2 splat/gather, radius kernel)
+    def splat(self, paths: Paths, cam: "Camera", radius: float):
+        """(image [h, w, 3] float64, ambiguous pixels [h, w] bool) at the current pose."""
+        img = np.zeros((cam.height, cam.width, 3), np.float64)
+        amb = np.zeros((cam.height, cam.width), np.uint8)
+        lib().or_splat(self._h, _p(paths.ids), paths.ids.shape[0], _p(paths.info), _p(paths.origin),
+                       _p(paths.photons), C.byref(cam), float(radius), _p(img), _p(amb))
+        return img, amb.astype(bool)
 
     # ---- distribution maps (Sec. 3.1)
     def set_dm(self, rect=(0, 0, 0, 0), point=(0, 0)) -> None:

@@ -1251,6 +1251,130 @@ int32_t or_num_threads(void) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* screen-space photon splat (Fig. 2 "splat/gather")                         */
+/* ------------------------------------------------------------------------ */
+/* Pinhole camera basis: forward f, right r = f x up, true up u = r x f. */
+static void cam_basis(const or_camera* c, double* pos, double* f, double* r, double* u, double* th) {
+  double tg[3], up[3];
+  f2d(c->pos, pos);
+  f2d(c->target, tg);
+  f2d(c->up, up);
+  sub3(tg, pos, f);
+  normalize3(f);
+  cross3(f, up, r);
+  normalize3(r);
+  cross3(r, f, u);
+  *th = tan(0.5 * (double)c->fov_y);
+}
+
+/* View depth of q. */
+static double cam_depth(const double* pos, const double* f, const double* q) {
+  double v[3];
+  sub3(q, pos, v);
+  return dot3(v, f);
+}
+
+/* G-buffer from primary rays through pixel centres, then for every pixel
+ * with a visible surface point p (normal n facing the camera, albedo rho)
+ * and every photon x with incident direction d_in (from the previous vertex,
+ * the origin for the first) arriving on the visible side (n . d_in < 0):
+ *   L += rho / pi * E * 2 (1 - s^2) / (pi r^2),   s = |p - x| / r < 1,
+ * a radius kernel normalised over the disk (integral over the plane = 1).
+ * A photon is skipped when any corner of its kernel cube lies less than
+ * 1e-3 diag in front of the camera (no screen-space footprint).  amb[pixel]
+ * is set when its hit, a side test or a near-plane decision is within the
+ * tolerances. */
+void or_splat(const or_scene* s, const uint32_t* ids, uint32_t n, const uint32_t* info, const float* origin,
+              const or_photon* photons, const or_camera* cam, double radius, double* image, uint8_t* amb) {
+  (void)ids;
+  const uint32_t W = cam->width, H = cam->height;
+  double pos[3], f[3], r[3], u[3], th;
+  cam_basis(cam, pos, f, r, u, &th);
+  const double aspect = (double)W / (double)H;
+  const size_t npx = (size_t)W * H;
+  double* gp = (double*)malloc(sizeof(double) * 3 * (npx ? npx : 1));
+  double* gn = (double*)malloc(sizeof(double) * 3 * (npx ? npx : 1));
+  int32_t* gprim = (int32_t*)malloc(sizeof(int32_t) * (npx ? npx : 1));
+#pragma omp parallel for schedule(dynamic, 16)
+  for (size_t px = 0; px < npx; ++px) {
+    const uint32_t i = (uint32_t)(px % W), j = (uint32_t)(px / W);
+    const double x = (2.0 * (i + 0.5) / W - 1.0) * th * aspect;
+    const double y = (1.0 - 2.0 * (j + 0.5) / H) * th;
+    double d[3];
+    for (int k = 0; k < 3; ++k) d[k] = f[k] + x * r[k] + y * u[k];
+    normalize3(d);
+    double t;
+    int a = 0;
+    const int32_t prim = closest_hit(s, 1, pos, d, 0.0, -1, &t, &a);
+    amb[px] = (uint8_t)(a != 0);
+    gprim[px] = prim;
+    if (prim >= 0) {
+      for (int k = 0; k < 3; ++k) gp[3 * px + k] = pos[k] + t * d[k];
+      double nn[3];
+      unit_normal(s, 1, prim, nn);
+      const double sg = dot3(nn, d) > 0.0 ? -1.0 : 1.0;
+      for (int k = 0; k < 3; ++k) gn[3 * px + k] = sg * nn[k];
+    }
+  }
+  /* photons: position, incident direction, energy, near-plane status */
+  size_t np = 0;
+  for (uint32_t i = 0; i < n; ++i) np += (info[i] >> OR_INFO_NSEG_SHIFT) & 15u;
+  double* ph = (double*)malloc(sizeof(double) * 9 * (np ? np : 1));
+  int8_t* ok = (int8_t*)malloc(np ? np : 1);   /* 1 splat, 0 skip, -1 skip but ambiguous */
+  size_t q = 0;
+  const double znear = 1e-3 * s->diag;
+  for (uint32_t i = 0; i < n; ++i) {
+    const uint32_t L = (info[i] >> OR_INFO_NSEG_SHIFT) & 15u;
+    const or_photon* pp = photons + (size_t)i * s->B;
+    for (uint32_t k = 0; k < L && k < s->B; ++k, ++q) {
+      double x[3], prev[3];
+      f2d(pp[k].pos, x);
+      if (k == 0) f2d(origin + 3 * (size_t)i, prev); else f2d(pp[k - 1].pos, prev);
+      double* e = ph + 9 * q;
+      for (int c = 0; c < 3; ++c) { e[c] = x[c]; e[3 + c] = x[c] - prev[c]; e[6 + c] = pp[k].E[c]; }
+      int8_t st = 1;
+      for (int cx = -1; cx <= 1; cx += 2)
+        for (int cy = -1; cy <= 1; cy += 2)
+          for (int cz = -1; cz <= 1; cz += 2) {
+            const double cor[3] = {x[0] + cx * radius, x[1] + cy * radius, x[2] + cz * radius};
+            const double z = cam_depth(pos, f, cor);
+            if (!(z > znear)) st = 0;
+            else if (fabs(z - znear) < s->eps && st == 1) st = -1;
+          }
+      ok[q] = st;
+    }
+  }
+  const double r2 = radius * radius;
+  const double norm = 2.0 / (M_PI * r2);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (size_t px = 0; px < npx; ++px) {
+    double* L = image + 3 * px;
+    L[0] = L[1] = L[2] = 0.0;
+    if (gprim[px] < 0) continue;
+    const double* p = gp + 3 * px;
+    const double* nv = gn + 3 * px;
+    const float* rho = s->albedo + 3 * (size_t)s->tri_object[gprim[px]];
+    for (size_t k = 0; k < np; ++k) {
+      const double* e = ph + 9 * k;
+      double dx[3];
+      sub3(p, e, dx);
+      const double s2 = dot3(dx, dx) / r2;
+      if (!(s2 < 1.0)) continue;
+      if (ok[k] <= 0) {
+        if (ok[k] < 0) amb[px] = 1;
+        continue;
+      }
+      const double side = dot3(nv, e + 3);
+      if (fabs(side) < 1e-6 * norm3(e + 3)) amb[px] = 1;
+      if (!(side < 0.0)) continue;
+      const double w = norm * (1.0 - s2) / M_PI;
+      for (int c = 0; c < 3; ++c) L[c] += (double)rho[c] * e[6 + c] * w;
+    }
+  }
+  free(gp); free(gn); free(gprim); free(ph); free(ok);
+}
+
+/* ------------------------------------------------------------------------ */
 /* differentiable deposit model and its adjoint                               */
 /* ------------------------------------------------------------------------ */
 uint32_t or_theta_size(const or_scene* s) { return 7u * s->n_lights + 3u * s->n_dynamic; }

@@ -169,6 +169,23 @@ void or_deposit(const uint32_t* info, uint32_t n, const or_photon* photons, uint
                 uint32_t width, uint32_t height, float x0, float z0, float x1, float z1,
                 double* atlas);
 
+/* Screen-space photon splat (the renderer's "splat/gather" step of Fig. 2;
+ * its splatting method is only cited, so a plain radius kernel): pinhole
+ * camera at pos looking at target (up vector, vertical field of view fov_y in
+ * radians, width x height pixels, pixel centres).  Every pixel's primary ray
+ * finds its visible point p (normal facing the camera, albedo rho); every
+ * photon x with energy E arriving on the visible side adds
+ * rho/pi * E * 2 (1 - s^2) / (pi r^2), s = |p - x| / r < 1.  A photon whose
+ * kernel cube reaches within 1e-3 diag of the camera plane is skipped.
+ * image [height][width][3] (written), amb [height][width] (written). */
+typedef struct {
+  float pos[3], target[3], up[3];
+  float fov_y;
+  uint32_t width, height;
+} or_camera;
+void or_splat(const or_scene* s, const uint32_t* ids, uint32_t n, const uint32_t* info, const float* origin,
+              const or_photon* photons, const or_camera* cam, double radius, double* image, uint8_t* amb);
+
 /* Differentiable deposit model (no counterpart in the paper; used to rank the
  * paths to re-trace).  Every stored path keeps its triangles and sampled
  * directions; with parameters theta the emission point and direction follow
