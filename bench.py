@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-dm", action="store_true", help="skip the distribution-map frame measurement")
+    ap.add_argument("--no-splat", action="store_true", help="skip the 1920x1080 screen-space splat measurement")
     ap.add_argument("--tune-frames", type=int, default=1, help="batch16: frames per tuner candidate")
     return ap.parse_args()
 
@@ -317,6 +318,8 @@ def run_ours(args, ws, rank, local):
                "d2h_bytes_per_step": int(host_atlas.numel() * 8 + host_stats.numel() * 4), "_s": e2e_s}
     # ---- differentiable model: forward splat and adjoint of an L2 atlas loss
     adjoint = None if args.no_adjoint else time_adjoint(pv, h, P, sc, N, A, K, W, stream, dev)
+    # ---- screen-space splat of the current records at 1920 x 1080
+    splat = None if args.no_splat or args.workload == "tiny_box" else time_splat(pv, h, P, sc, K, W, stream, dev)
     # ---- the same reuse frames with distribution maps on the lights (Sec. 3.1)
     dm = None if args.no_dm or args.workload == "tiny_box" else time_dm(pv, sc, mode, tau, seed, K, W, xfs, lts,
                                                                           stream, dev)
@@ -380,6 +383,8 @@ def run_ours(args, ws, rank, local):
         cfg["adjoint"] = adjoint
     if dm:
         cfg["distribution_maps"] = dm
+    if splat:
+        cfg["splat"] = splat
     if e2e:
         e2e["value"] = ws * N / e2e_s
         e2e.pop("_s")
@@ -387,6 +392,34 @@ def run_ours(args, ws, rank, local):
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(args.workload, mode, tau, args.cpu_seconds)
     print(json.dumps(out), flush=True)
+
+
+SPLAT_CAMERAS = {"city": ((0.0, 45.0, 35.0), (0.0, 0.0, 0.0), 0.3), "villa": ((10.0, 2.5, 2.0), (14.0, 0.5, 6.0), 0.08)}
+
+
+def time_splat(pv, h, P, sc, K, W, stream, dev):
+    """Screen-space splat (primary-ray G-buffer + radius kernel) of the current
+    records at 1920 x 1080, 60 degree vertical field of view, timed per call."""
+    import torch
+    pos, target, radius = SPLAT_CAMERAS.get(sc.name, ((0.0, 1.5, 0.9), (0.0, 0.0, 0.0), 0.1))
+    Wd, Hd = 1920, 1080
+    cam = pv.PvCamera.make(pos, target, (0.0, 1.0, 0.0), math.radians(60.0), Wd, Hd)
+    img = torch.zeros(Hd, Wd, 3, dtype=torch.float32, device=dev)
+    work = torch.empty(pv.pv_splat_workspace_bytes(Wd, Hd), dtype=torch.uint8, device=dev)
+    ms = []
+    for i in range(W + K):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record(stream)
+        pv.pv_splat(h, P, cam, radius, img, work)
+        e[1].record(stream)
+        if i >= W:
+            ms.append(e)
+    torch.cuda.synchronize()
+    t = float(np.mean([a.elapsed_time(b) for a, b in ms]))
+    lit = float((img.sum(-1) > 0).float().mean())
+    return {"resolution": [Wd, Hd], "camera": {"pos": pos, "target": target, "fov_y_deg": 60.0},
+            "radius": radius, "ms": t, "lit_fraction": lit, "photons": int(((P.info.view(torch.int32) >> 22) & 15)
+                                                                            .clamp(max=sc.max_bounces).sum())}
 
 
 def time_dm(pv, sc, mode, tau, seed, K, W, xfs, lts, stream, dev):

@@ -326,6 +326,31 @@ int pv_set_traversal_limit(pv_scene* s, uint32_t max_visits);
  * recorded since the last call (then clear it), or PV_OK. */
 int pv_read_device_status(pv_scene* s);
 
+/* Screen-space photon splat: the renderer's "splat/gather" step of Fig. 2,
+ * whose method the paper only cites, as a plain radius kernel.  A pinhole
+ * camera at ``pos`` looks at ``target`` (``up`` fixes the roll; vertical field
+ * of view ``fov_y`` radians; width x height pixels, rays through pixel
+ * centres).  Every pixel's primary ray finds its visible point p (normal
+ * facing the camera, albedo rho of its object); every stored photon x with
+ * energy E whose incoming segment arrives on the visible side adds
+ *   rho / pi * E * 2 (1 - s^2) / (pi r^2),   s = |p - x| / radius < 1
+ * to the pixel (the kernel integrates to 1 over a plane).  A photon whose
+ * kernel cube reaches within 1e-3 scene diagonals of the camera plane is
+ * skipped.  d_image: float32 [height][width][3] device memory, cleared and
+ * written.  d_work: pv_splat_workspace_bytes(width, height) bytes of
+ * 16-byte-aligned device memory (the per-pixel visible points).  PV_ERR_ARG
+ * for a degenerate camera (zero size, fov outside (0, 3.1), up parallel to the
+ * view direction), radius <= 0, or a small or misaligned workspace. */
+typedef struct {
+  float pos[3], target[3], up[3];
+  float fov_y;
+  uint32_t width, height;
+} pv_camera;
+
+size_t pv_splat_workspace_bytes(uint32_t width, uint32_t height);
+int pv_splat(pv_scene* s, const pv_paths* paths, const pv_camera* cam, float radius, float* d_image, void* d_work,
+             size_t work_bytes, void* stream);
+
 /* Number of cells of light ``light``'s distribution map (0: none), or
  * PV_ERR_ARG.  pv_read_distribution_map synchronises the scene's last stream
  * and copies its current counts DM_C to h_counts (host, that many entries). */

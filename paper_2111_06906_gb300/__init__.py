@@ -34,7 +34,8 @@ EXPORTS = ["pv_build_scene", "pv_update_dynamic", "pv_verify_paths", "pv_retrace
            "pv_read_device_status", "pv_destroy_scene", "pv_status_string", "pv_theta_size", "pv_theta_current",
            "pv_model_deposit", "pv_adjoint_deposit", "pv_budget_list", "pv_batch_create", "pv_batch_frame",
            "pv_batch_autotune", "pv_batch_tuning", "pv_batch_set_config", "pv_batch_get_config", "pv_batch_step_times",
-           "pv_batch_destroy", "pv_distribution_map_cells", "pv_read_distribution_map"]
+           "pv_batch_destroy", "pv_distribution_map_cells", "pv_read_distribution_map", "pv_splat_workspace_bytes",
+           "pv_splat"]
 PV_BATCH_MAX_SCENES = 32
 PV_STATIC_COMPACT_MAX_PATHS = 1 << 26
 
@@ -69,6 +70,21 @@ class PvVerifyParams(C.Structure):
 class PvAtlas(C.Structure):
     _fields_ = [("data", C.c_void_p), ("width", C.c_uint32), ("height", C.c_uint32), ("x0", C.c_float),
                 ("z0", C.c_float), ("x1", C.c_float), ("z1", C.c_float), ("scale_log2", C.c_int32)]
+
+
+class PvCamera(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("target", C.c_float * 3), ("up", C.c_float * 3), ("fov_y", C.c_float),
+                ("width", C.c_uint32), ("height", C.c_uint32)]
+
+    @classmethod
+    def make(cls, pos, target, up, fov_y, width, height):
+        c = cls()
+        c.pos[:] = [float(v) for v in pos]
+        c.target[:] = [float(v) for v in target]
+        c.up[:] = [float(v) for v in up]
+        c.fov_y = float(fov_y)
+        c.width, c.height = int(width), int(height)
+        return c
 
 
 class PvBatchScene(C.Structure):
@@ -124,12 +140,15 @@ def load():
         L.pv_batch_step_times.argtypes = [P, P]
         L.pv_batch_destroy.argtypes = [P]
         L.pv_distribution_map_cells.argtypes = [P, C.c_uint32]
+        L.pv_splat_workspace_bytes.argtypes = [C.c_uint32, C.c_uint32]
+        L.pv_splat_workspace_bytes.restype = C.c_size_t
+        L.pv_splat.argtypes = [P, C.POINTER(PvPaths), C.POINTER(PvCamera), C.c_float, P, P, C.c_size_t, P]
         L.pv_read_distribution_map.argtypes = [P, C.c_uint32, P]
         L.pv_batch_destroy.restype = None
         L.pv_status_string.argtypes = [C.c_int]
         L.pv_status_string.restype = C.c_char_p
         for name in EXPORTS:
-            if name not in ("pv_destroy_scene", "pv_status_string", "pv_batch_destroy"):
+            if name not in ("pv_destroy_scene", "pv_status_string", "pv_batch_destroy", "pv_splat_workspace_bytes"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -447,6 +466,18 @@ def pv_batch_destroy(batch: Batch) -> None:
     if batch and batch.handle:
         load().pv_batch_destroy(batch.handle)
         batch.handle = None
+
+
+def pv_splat_workspace_bytes(width: int, height: int) -> int:
+    return int(load().pv_splat_workspace_bytes(int(width), int(height)))
+
+
+def pv_splat(scene, paths: Paths, cam: PvCamera, radius: float, image, work, stream=None) -> None:
+    """Splat the stored photons into ``image`` (float32 [h, w, 3] device
+    tensor, written); ``work``: device tensor of pv_splat_workspace_bytes."""
+    ps = paths.struct()
+    _check("pv_splat", load().pv_splat(scene, C.byref(ps), C.byref(cam), float(radius), _ptr(image), _ptr(work),
+                                        int(work.numel() * work.element_size()), _stream(stream)))
 
 
 def pv_distribution_map_cells(scene, light: int) -> int:
