@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-dm", action="store_true", help="skip the distribution-map frame measurement")
     ap.add_argument("--no-splat", action="store_true", help="skip the 1920x1080 screen-space splat measurement")
     ap.add_argument("--tune-frames", type=int, default=1, help="batch16: frames per tuner candidate")
+    ap.add_argument("--build-flags", type=int, default=0, help="pv_scene_desc flags (2: Morton-code static tree)")
     return ap.parse_args()
 
 
@@ -196,7 +197,7 @@ def run_ours(args, ws, rank, local):
 
     t0 = time.time()
     h = pv.pv_build_scene(sc.verts, sc.tri_object, sc.object_dynamic, sc.object_albedo, lts[1], B, sc.diag,
-                          object_xform=xfs[1])
+                          object_xform=xfs[1], flags=args.build_flags)
     build_s = time.time() - t0
     P = pv.Paths.allocate(N, B, dev)
     A = args.atlas
@@ -373,7 +374,7 @@ def run_ours(args, ws, rank, local):
            "listed_per_frame": agg("n_listed", st_reuse), "mean_photons_per_path": mean_L,
            "retrace_node_visits_per_ray": agg("node_visits", st_retrace) / max(agg("trace_rays", st_retrace), 1),
            "retrace_tri_tests_per_ray": agg("tri_tests", st_retrace) / max(agg("trace_rays", st_retrace), 1),
-           "scene_build_s": build_s, "device_status": [status, status2]}
+           "scene_build_s": build_s, "build_flags": args.build_flags, "device_status": [status, status2]}
     launches_per_frame = 2 + (3 if mode == 2 else 2) + 1 + 1
     out = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws, "steps": K, "warmup": W,
            "ms_per_step": reuse_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

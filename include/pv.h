@@ -60,7 +60,10 @@ enum {
   PV_FLAG_TEST_OLD_TRIS = 1u,   /* exact tests also test the old pose's triangles */
   PV_FLAG_ERROR_EXACT = 2u      /* ERROR mode flags segments with triangles, not boxes */
 };
-enum { PV_BUILD_DYN_REBUILD = 1u };  /* rebuild dynamic BVHs every frame instead of refitting */
+enum {
+  PV_BUILD_DYN_REBUILD = 1u,   /* rebuild dynamic BVHs every frame instead of refitting */
+  PV_BUILD_STATIC_LBVH = 2u    /* static tree from Morton codes (default: binned surface-area heuristic) */
+};
 
 #define PV_MAX_LIGHTS 4
 #define PV_MAX_DYN_OBJECTS 64

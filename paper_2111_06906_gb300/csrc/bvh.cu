@@ -523,6 +523,124 @@ static void make_refs(const float* verts, const std::vector<uint32_t>& prims, st
   }
 }
 
+// ---- static tree by binned surface-area heuristic (host, once per scene)
+//
+// Top-down: each range of references is split where sum(area(child box) x
+// references) over 32 centroid bins per axis is smallest (Wald, "On fast
+// construction of SAH-based bounding volume hierarchies", 2007); a range with
+// coincident centroids splits at its middle.  Output: the references in leaf
+// order, and per internal node (root 0, creation order) its two children
+// (internal index, or ~leaf position), its leaf range and the parent links
+// the bottom-up fit uses.  The fit computes the boxes and the collapse to
+// wide nodes follows, as for the Morton tree.
+struct SahOut {
+  std::vector<uint32_t> order;
+  std::vector<int4> d;
+  std::vector<uint32_t> node_parent, leaf_parent;
+};
+
+static void sah_build(const std::vector<float>& box, uint32_t n, SahOut& out) {
+  constexpr int K = 32;
+  out.order.resize(n);
+  for (uint32_t i = 0; i < n; ++i) out.order[i] = i;
+  out.d.assign(n > 1 ? n - 1 : 0, make_int4(0, 0, 0, 0));
+  out.node_parent.assign(n, 0u);
+  out.leaf_parent.assign(n, 0u);
+  if (n < 2) return;
+  std::vector<float> cen(3 * (size_t)n);
+  for (uint32_t i = 0; i < n; ++i)
+    for (int k = 0; k < 3; ++k) cen[3 * (size_t)i + k] = 0.5f * (box[6 * (size_t)i + k] + box[6 * (size_t)i + 3 + k]);
+  auto area = [](const float* b) {
+    const float ex = std::max(b[3] - b[0], 0.f), ey = std::max(b[4] - b[1], 0.f), ez = std::max(b[5] - b[2], 0.f);
+    return ex * ey + ey * ez + ez * ex;
+  };
+  auto grow = [](float* b, const float* c) {
+    for (int k = 0; k < 3; ++k) {
+      b[k] = std::min(b[k], c[k]);
+      b[3 + k] = std::max(b[3 + k], c[3 + k]);
+    }
+  };
+  struct Task { uint32_t b, e; int node; };
+  std::vector<Task> todo{{0u, n, 0}};
+  int next = 1;
+  uint32_t* idx = out.order.data();
+  while (!todo.empty()) {
+    const Task t = todo.back();
+    todo.pop_back();
+    float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (uint32_t i = t.b; i < t.e; ++i)
+      for (int k = 0; k < 3; ++k) {
+        clo[k] = std::min(clo[k], cen[3 * (size_t)idx[i] + k]);
+        chi[k] = std::max(chi[k], cen[3 * (size_t)idx[i] + k]);
+      }
+    int best_axis = -1, best_bin = 0;
+    float best_cost = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+      const float ext = chi[a] - clo[a];
+      if (!(ext > 0.f)) continue;
+      uint32_t cnt[K] = {};
+      float bb[K][6];
+      for (int q = 0; q < K; ++q) {
+        bb[q][0] = bb[q][1] = bb[q][2] = INFINITY;
+        bb[q][3] = bb[q][4] = bb[q][5] = -INFINITY;
+      }
+      const float sc = (float)K / ext;
+      for (uint32_t i = t.b; i < t.e; ++i) {
+        const int q = std::min(K - 1, (int)((cen[3 * (size_t)idx[i] + a] - clo[a]) * sc));
+        ++cnt[q];
+        grow(bb[q], &box[6 * (size_t)idx[i]]);
+      }
+      float rarea[K];
+      uint32_t rcnt[K];
+      float acc[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+      uint32_t c = 0;
+      for (int q = K - 1; q > 0; --q) {
+        grow(acc, bb[q]);
+        c += cnt[q];
+        rarea[q] = area(acc);
+        rcnt[q] = c;
+      }
+      float lacc[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+      uint32_t lc = 0;
+      for (int q = 0; q < K - 1; ++q) {            // split between bins q and q + 1
+        grow(lacc, bb[q]);
+        lc += cnt[q];
+        if (lc == 0 || rcnt[q + 1] == 0) continue;
+        const float cost = area(lacc) * (float)lc + rarea[q + 1] * (float)rcnt[q + 1];
+        if (cost < best_cost) {
+          best_cost = cost;
+          best_axis = a;
+          best_bin = q;
+        }
+      }
+    }
+    uint32_t mid;
+    if (best_axis < 0) {
+      mid = t.b + (t.e - t.b) / 2;                  // coincident centroids: split the range
+    } else {
+      const float sc = (float)K / (chi[best_axis] - clo[best_axis]);
+      uint32_t* m = std::partition(idx + t.b, idx + t.e, [&](uint32_t r) {
+        return std::min(K - 1, (int)((cen[3 * (size_t)r + best_axis] - clo[best_axis]) * sc)) <= best_bin;
+      });
+      mid = (uint32_t)(m - idx);
+      if (mid == t.b || mid == t.e) mid = t.b + (t.e - t.b) / 2;
+    }
+    int child[2];
+    const uint32_t lo[2] = {t.b, mid}, hi[2] = {mid, t.e};
+    for (int side = 0; side < 2; ++side) {
+      if (hi[side] - lo[side] == 1) {
+        child[side] = ~(int)lo[side];
+        out.leaf_parent[lo[side]] = ((uint32_t)t.node << 1) | (uint32_t)side;
+      } else {
+        child[side] = next++;
+        out.node_parent[child[side]] = ((uint32_t)t.node << 1) | (uint32_t)side;
+        todo.push_back({lo[side], hi[side], child[side]});
+      }
+    }
+    out.d[t.node] = make_int4(child[0], child[1], (int)t.b, (int)t.e - 1);
+  }
+}
+
 int build_bvh(pv_scene* s, const float* h_verts, const std::vector<uint32_t>& static_prims, cudaStream_t st) {
   int rc = PV_OK;
   auto fail = [&](cudaError_t e) {
@@ -595,11 +713,27 @@ int build_bvh(pv_scene* s, const float* h_verts, const std::vector<uint32_t>& st
       fail(cudaMemcpyAsync(d_prim, static_prims.data(), static_prims.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
       fail(cudaMemcpyAsync(d_rtri, ref_tri.data(), ns * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
       fail(cudaMemcpyAsync(d_rbox, ref_box.data(), 6 * (size_t)ns * sizeof(float), cudaMemcpyHostToDevice, st));
-      k_morton_static<<<blocks(ns, 256), 256, 0, st>>>(d_rbox, ns, f, k0, v0);
-      radix_sort(k0, v0, k1, v1, ns, hist, 0, 64, st);
+      const bool sah = !(s->flags & PV_BUILD_STATIC_LBVH);
+      if (sah) {
+        SahOut t;
+        sah_build(ref_box, ns, t);
+        std::vector<Node> hn(ns > 1 ? ns - 1 : 0);
+        for (size_t i = 0; i < hn.size(); ++i) {
+          std::memset(&hn[i], 0, sizeof(Node));
+          hn[i].d = t.d[i];
+        }
+        fail(cudaMemcpyAsync(v0, t.order.data(), ns * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+        if (!hn.empty()) fail(cudaMemcpyAsync(s->nodes, hn.data(), hn.size() * sizeof(Node), cudaMemcpyHostToDevice, st));
+        fail(cudaMemcpyAsync(np, t.node_parent.data(), ns * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+        fail(cudaMemcpyAsync(lp, t.leaf_parent.data(), ns * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+        fail(cudaStreamSynchronize(st));             // the host vectors go out of scope
+      } else {
+        k_morton_static<<<blocks(ns, 256), 256, 0, st>>>(d_rbox, ns, f, k0, v0);
+        radix_sort(k0, v0, k1, v1, ns, hist, 0, 64, st);
+      }
       k_gather_static<<<blocks(ns, 256), 256, 0, st>>>(d_v, d_rtri, d_rbox, v0, d_prim, ns, s->tris, d_lbox);
       if (ns >= 2) {
-        k_karras<<<blocks(ns - 1, 256), 256, 0, st>>>(k0, (int)ns, s->nodes, 0, 0, np, lp, nullptr, nullptr);
+        if (!sah) k_karras<<<blocks(ns - 1, 256), 256, 0, st>>>(k0, (int)ns, s->nodes, 0, 0, np, lp, nullptr, nullptr);
         fail(cudaMemsetAsync(flags, 0, ns * sizeof(uint32_t), st));
         k_fit<<<blocks(ns, 256), 256, 0, st>>>(s->nodes, np, lp, flags, s->tris, d_lbox, (int)ns);
         s->s_root = 0;
