@@ -39,6 +39,9 @@ WORKLOADS = {
     "batch16": "16 independent districts: 10k to 2M tris, 50k to 3M paths (12.4M in all), 1 to 3 lights, "
                "bounce caps 1 to 7, 1 to 4 moving tori; one batched graph-captured frame per step, tuned",
 }
+# DRAM bytes (read + write) of one k_trace launch of a timed reuse frame, from the ncu captures
+# summarised in profiles/kernels_city.md and profiles/kernels_villa.md (same kernel code)
+TRACE_TRAFFIC = {"city": 40775936 + 21240576, "villa": 118639360 + 86860544}
 OPS_PER_NODE = 107    # FP32-pipe ops per wide-node visit (four slab tests + ordering network), from the source
 OPS_PER_TRI = 40      # FP32-pipe ops per Moller-Trumbore test, counted from the source
 SM_COUNT, FP32_LANES = 152, 128
@@ -346,7 +349,8 @@ def run_ours(args, ws, rank, local):
         ops_peak = SM_COUNT * FP32_LANES * pk.get("sm_max_mhz", 2070.0) * 1e6
         achieved = ops / (reuse_parts[2] * 1e-3)
         roof = {"kernel": "k_trace (pv_retrace_invalid)", "bound": "alu", "achieved": achieved / 1e12,
-                "peak": ops_peak / 1e12, "unit": "Top/s", "frac": achieved / ops_peak, "traffic": None,
+                "peak": ops_peak / 1e12, "unit": "Top/s", "frac": achieved / ops_peak,
+                "traffic": TRACE_TRAFFIC.get(args.workload), "traffic_unit": "bytes per launch (ncu)",
                 "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x max SM clock"}
     elif names[dom] == "verify":
         listed = agg("n_listed", st_reuse)
