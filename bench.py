@@ -4,10 +4,12 @@
 One step = one frame of the reuse pipeline on the seeded city workload
 (200k static triangles, 4 moving tori, a 1x1 m area light translating
 0.1 m/frame, 1M photon paths of up to 7 bounces, error-based mode with
-tau = 1 %):  pv_update_dynamic -> pv_verify_paths (origin update, dynamic
-occlusions, Alg. 1 continuation, compaction) -> pv_retrace_invalid ->
-pv_deposit.  The same library's trace-all frame (pv_update_dynamic ->
-pv_trace_all -> pv_deposit) is timed beside it.
+tau = 1 %):  pv_update_dynamic -> pv_verify_retrace (origin update, dynamic
+occlusions, compaction, then Alg. 1 continuation fused with the re-trace)
+-> pv_deposit.  The same frames through the separate calls
+(pv_verify_paths -> pv_retrace_invalid) and the same library's trace-all
+frame (pv_update_dynamic -> pv_trace_all -> pv_deposit) are timed beside
+it.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on a bounded sample of the same workload instead.
@@ -217,8 +219,7 @@ def run_ours(args, ws, rank, local):
 
     def reuse_frame(f, st):
         pv.pv_update_dynamic(h, xfs[f], lts[f])
-        pv.pv_verify_paths(h, P, mode, tau, 0, lst, cnt, st)
-        pv.pv_retrace_invalid(h, P, lst, cnt, seed, f, st)
+        pv.pv_verify_retrace(h, P, mode, tau, 0, seed, f, st)
         pv.pv_deposit(h, P, atlas, sc.atlas_rect, scale)
 
     def timed_loop(fn, first_frame, rows_a, rows_b):
@@ -233,7 +234,13 @@ def run_ours(args, ws, rank, local):
             e[4].record(stream)
         return ev
 
-    def reuse_body(f, st_v, st_r, e):
+    def fused_body(f, st_v, st_r, e):
+        pv.pv_verify_retrace(h, P, mode, tau, 0, seed, f, st_v)
+        e[2].record(stream)
+        e[3].record(stream)
+        pv.pv_deposit(h, P, atlas, sc.atlas_rect, scale)
+
+    def separate_body(f, st_v, st_r, e):
         pv.pv_verify_paths(h, P, mode, tau, 0, lst, cnt, st_v)
         e[2].record(stream)
         pv.pv_retrace_invalid(h, P, lst, cnt, seed, f, st_r)
@@ -253,29 +260,49 @@ def run_ours(args, ws, rank, local):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- reuse pipeline
+    # ---- reuse pipeline, one call from verification to re-trace (headline)
     for i in range(W):
         frame += 1
         reuse_frame(frame, stats[-1])
+    pv.pv_stage_timing(h, K)                   # the library records its stages' events in the timed frames
     barrier()
     clocks = Clocks(local)
     with clocks:
         start = torch.cuda.Event(enable_timing=True)
         stop = torch.cuda.Event(enable_timing=True)
         start.record(stream)
-        ev = timed_loop(reuse_body, frame + 1, stats[:K], stats[K:2 * K])
+        ev = timed_loop(fused_body, frame + 1, stats[:K], stats[K:2 * K])
         stop.record(stream)
         barrier()
     frame += K
     reuse_ms = start.elapsed_time(stop) / K
     parts = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in ev])
     reuse_parts = parts.mean(axis=0)
-    st_verify = [pv.stats_dict(stats[i]) for i in range(K)]
-    st_retrace = [pv.stats_dict(stats[K + i]) for i in range(K)]
-    st_reuse = [{k: a[k] + b[k] for k in a} for a, b in zip(st_verify, st_retrace)]
+    stage_ms = pv.pv_stage_times(h, K).mean(axis=0)     # k_verify, compaction, fused kernel, whole call
+    pv.pv_stage_timing(h, 0)
+    st_reuse = [pv.stats_dict(stats[i]) for i in range(K)]
     info_np = P.info.cpu().numpy().view(np.uint32)
     mean_L = float(((info_np >> 22) & 15).mean())
     status = pv.pv_read_device_status(h)
+
+    # ---- the same frames through the separate calls (pv_verify_paths, then pv_retrace_invalid)
+    for i in range(W):
+        frame += 1
+        pv.pv_update_dynamic(h, xfs[frame], lts[frame])
+        pv.pv_verify_paths(h, P, mode, tau, 0, lst, cnt, stats[-1])
+        pv.pv_retrace_invalid(h, P, lst, cnt, seed, frame, stats[-1])
+        pv.pv_deposit(h, P, atlas, sc.atlas_rect, scale)
+    barrier()
+    start3 = torch.cuda.Event(enable_timing=True)
+    stop3 = torch.cuda.Event(enable_timing=True)
+    start3.record(stream)
+    ev3 = timed_loop(separate_body, frame + 1, stats[:K], stats[K:2 * K])
+    stop3.record(stream)
+    barrier()
+    frame += K
+    sep_ms = start3.elapsed_time(stop3) / K
+    sep_parts = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in ev3]).mean(axis=0)
+    st_retrace = [pv.stats_dict(stats[K + i]) for i in range(K)]
 
     # ---- trace-all baseline (same library, same GPU)
     for i in range(W):
@@ -340,30 +367,20 @@ def run_ours(args, ws, rank, local):
         return
 
     pk, pk_kind = peaks()
-    names = ["update", "verify", "retrace", "deposit"]
-    dom = int(np.argmax(reuse_parts))
+    names = ["update", "verify_retrace", "-", "deposit"]
     agg = lambda key, rows: float(np.mean([r[key] for r in rows]))
-    roof = None
-    if names[dom] == "retrace":
-        ops = OPS_PER_NODE * agg("node_visits", st_retrace) + OPS_PER_TRI * agg("tri_tests", st_retrace)
-        ops_peak = SM_COUNT * FP32_LANES * pk.get("sm_max_mhz", 2070.0) * 1e6
-        achieved = ops / (reuse_parts[2] * 1e-3)
-        roof = {"kernel": "k_trace (pv_retrace_invalid)", "bound": "alu", "achieved": achieved / 1e12,
-                "peak": ops_peak / 1e12, "unit": "Top/s", "frac": achieved / ops_peak,
-                "traffic": TRACE_TRAFFIC.get(args.workload), "traffic_unit": "bytes per launch (ncu)",
-                "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x max SM clock"}
-    elif names[dom] == "verify":
-        listed = agg("n_listed", st_reuse)
-        byts = N * (4 + 12 + 16 * mean_L) + 4 * N + 4 * listed
-        achieved = byts / (reuse_parts[1] * 1e-3) / 1e9
-        roof = {"kernel": "k_verify+k_continue+k_compact (pv_verify_paths)", "bound": "hbm", "achieved": achieved,
-                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                "peak_kind": pk_kind}
-    else:
-        byts = N * 4 + N * mean_L * 32
-        achieved = byts / (reuse_parts[dom] * 1e-3) / 1e9
-        roof = {"kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_kind": pk_kind}
+    # dominant kernel: the re-trace kernel of pv_verify_retrace (Alg. 1 fused with the re-trace in error
+    # mode), timed by the library's own events; its traversal work comes from the counted node visits and
+    # triangle tests of the call (k_verify traverses only for moving point lights: vis_rays = 0 here)
+    fused = mode == 2
+    ops = OPS_PER_NODE * agg("node_visits", st_reuse) + OPS_PER_TRI * agg("tri_tests", st_reuse)
+    ops_peak = SM_COUNT * FP32_LANES * pk.get("sm_max_mhz", 2070.0) * 1e6
+    achieved = ops / (float(stage_ms[2]) * 1e-3)
+    roof = {"kernel": "k_cont_trace (pv_verify_retrace)" if fused else "k_trace (pv_verify_retrace)", "bound": "alu",
+            "achieved": achieved / 1e12, "peak": ops_peak / 1e12, "unit": "Top/s", "frac": achieved / ops_peak,
+            "duration_ms": float(stage_ms[2]),
+            "traffic": TRACE_TRAFFIC.get(args.workload), "traffic_unit": "bytes per launch (ncu)",
+            "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x max SM clock"}
     rays_reuse = agg("vis_rays", st_reuse) + agg("cont_rays", st_reuse) + agg("trace_rays", st_reuse)
     rays_trace = agg("trace_rays", st_trace)
     value = ws * N / (reuse_ms * 1e-3)
@@ -372,14 +389,25 @@ def run_ours(args, ws, rank, local):
            "l2": "inputs larger than L2 (path buffers %.0f MB)" % (N * (4 + 12 + 32 * B) / 1e6),
            "reuse_ms_per_frame": reuse_ms, "trace_all_ms_per_frame": trace_ms,
            "speedup_vs_trace_all": trace_ms / reuse_ms,
-           "reuse_ms_parts": dict(zip(names, [float(x) for x in reuse_parts])),
-           "trace_all_ms_parts": dict(zip(names, [float(x) for x in parts2])),
+           "reuse_ms_parts": {"update": float(reuse_parts[0]), "verify_retrace": float(reuse_parts[1]),
+                              "deposit": float(reuse_parts[3])},
+           "verify_retrace_stages_ms": {"k_verify": float(stage_ms[0]), "compaction": float(stage_ms[1]),
+                                        "k_cont_trace" if fused else "k_trace": float(stage_ms[2]),
+                                        "call": float(stage_ms[3])},
+           "separate_calls": {"ms_per_frame": sep_ms,
+                              "parts": dict(zip(["update", "verify", "retrace", "deposit"],
+                                                [float(x) for x in sep_parts]))},
+           "trace_all_ms_parts": dict(zip(["update", "-", "trace_all", "deposit"], [float(x) for x in parts2])),
            "rays_per_frame_reuse": rays_reuse, "rays_per_frame_trace_all": rays_trace,
-           "listed_per_frame": agg("n_listed", st_reuse), "mean_photons_per_path": mean_L,
+           "listed_per_frame": agg("n_listed", st_reuse), "cont_paths_per_frame": agg("n_cont", st_reuse),
+           "tails_per_frame": agg("n_tail", st_reuse), "vis_rays_per_frame": agg("vis_rays", st_reuse),
+           "mean_photons_per_path": mean_L,
            "retrace_node_visits_per_ray": agg("node_visits", st_retrace) / max(agg("trace_rays", st_retrace), 1),
            "retrace_tri_tests_per_ray": agg("tri_tests", st_retrace) / max(agg("trace_rays", st_retrace), 1),
            "scene_build_s": build_s, "build_flags": args.build_flags, "device_status": [status, status2]}
-    launches_per_frame = 2 + (3 if mode == 2 else 2) + 1 + 1
+    # kernels per reuse frame: pose update (k_update_objects, k_fit, k_wide_refit, k_build_top), k_verify,
+    # k_compact, k_cont_trace (k_continue + k_trace outside error mode: k_trace only), k_deposit
+    launches_per_frame = 4 + 3 + 1
     out = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws, "steps": K, "warmup": W,
            "ms_per_step": reuse_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roof,

@@ -230,6 +230,36 @@ int pv_retrace_invalid(pv_scene* s, const pv_paths* paths, const uint32_t* d_lis
                        const uint32_t* d_count, uint64_t seed, uint32_t frame,
                        pv_frame_stats* d_stats, void* stream);
 
+/* One frame's verification and re-trace in one call (Fig. 2 from "verify
+ * paths" to "trace rays"): the path records and every d_stats counter come
+ * out bit for bit as after pv_verify_paths followed by pv_retrace_invalid on
+ * its list with the seed and frame of ``params``.  No list is returned.  In
+ * PV_MODE_ERROR, when something moved and no light has a distribution map,
+ * Alg. 1 runs inside the persistent re-trace kernel: its closest-hit queries
+ * interleave with the re-trace rays, and a path failing Eq. 2 goes on to its
+ * re-trace from the failing vertex at once; the paths are processed in
+ * another order, never with other arithmetic.  Otherwise the same kernels as
+ * the two separate calls run.  The list is kept in the scene's workspace, so
+ * calls on one scene must not overlap.  Errors as pv_verify_paths. */
+int pv_verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params* params,
+                      pv_frame_stats* d_stats, void* stream);
+
+/* Stage timing of pv_verify_retrace (no paper counterpart).  With n > 0,
+ * each later call records four CUDA events on its stream -- at its start,
+ * after k_verify, before its re-trace kernel, at its end -- keeping the last
+ * n calls in a ring; n = 0 turns it off.  Creates (and destroys) events and
+ * synchronises with the scene's last stream, so call it outside any timed or
+ * captured region.  PV_ERR_ARG for n > 4096. */
+int pv_stage_timing(pv_scene* s, uint32_t n);
+
+/* Milliseconds of the recorded calls, oldest first, four per call (``ms``
+ * holds 4 n floats): [0] verification (k_verify), [1] what runs between it
+ * and the re-trace kernel (the compaction; without fusion also the
+ * continuation and the distribution-map steps), [2] the re-trace kernel
+ * (with fusion: Alg. 1 and the re-trace), [3] the whole call.  *count
+ * receives the number of calls recorded (at most n).  Waits for the events. */
+int pv_stage_times(pv_scene* s, float* ms, uint32_t* count);
+
 /* Baseline of Sec. 5: re-trace every path from the light (no reuse). */
 int pv_trace_all(pv_scene* s, const pv_paths* paths, uint64_t seed, uint32_t frame,
                  pv_frame_stats* d_stats, void* stream);

@@ -30,7 +30,8 @@ PV_BUILD_STATIC_LBVH = 2
 PV_INFO_NSEG_SHIFT, PV_INFO_START_SHIFT = 22, 26
 PV_INFO_REPLACE, PV_INFO_REUSE_LIGHT = 1 << 30, 1 << 31
 
-EXPORTS = ["pv_build_scene", "pv_update_dynamic", "pv_verify_paths", "pv_retrace_invalid", "pv_trace_all",
+EXPORTS = ["pv_build_scene", "pv_update_dynamic", "pv_verify_paths", "pv_retrace_invalid", "pv_verify_retrace",
+           "pv_stage_timing", "pv_stage_times", "pv_trace_all",
            "pv_compact_replace", "pv_compact_replace_static", "pv_deposit", "pv_set_traversal_limit",
            "pv_read_device_status", "pv_destroy_scene", "pv_status_string", "pv_theta_size", "pv_theta_current",
            "pv_model_deposit", "pv_adjoint_deposit", "pv_budget_list", "pv_batch_create", "pv_batch_frame",
@@ -118,6 +119,9 @@ def load():
         L.pv_update_dynamic.argtypes = [P, P, P, P]
         L.pv_verify_paths.argtypes = [P, C.POINTER(PvPaths), C.POINTER(PvVerifyParams), P, P, P, P]
         L.pv_retrace_invalid.argtypes = [P, C.POINTER(PvPaths), P, P, C.c_uint64, C.c_uint32, P, P]
+        L.pv_verify_retrace.argtypes = [P, C.POINTER(PvPaths), C.POINTER(PvVerifyParams), P, P]
+        L.pv_stage_timing.argtypes = [P, C.c_uint32]
+        L.pv_stage_times.argtypes = [P, P, P]
         L.pv_trace_all.argtypes = [P, C.POINTER(PvPaths), C.c_uint64, C.c_uint32, P, P]
         L.pv_compact_replace.argtypes = [P, C.POINTER(PvPaths), P, P, P]
         L.pv_compact_replace_static.argtypes = [P, C.c_uint32, P, P, P]
@@ -264,6 +268,27 @@ def pv_retrace_invalid(scene, paths: Paths, d_list, d_count, seed: int, frame: i
     ps = paths.struct()
     _check("pv_retrace_invalid", load().pv_retrace_invalid(scene, C.byref(ps), _ptr(d_list), _ptr(d_count),
                                                             int(seed), int(frame), _ptr(d_stats), _stream(stream)))
+
+
+def pv_verify_retrace(scene, paths: Paths, mode: int, tau: float, flags: int, seed: int, frame: int, d_stats=None,
+                      stream=None) -> None:
+    """pv_verify_paths + pv_retrace_invalid in one call (same records and counters, no list)."""
+    ps = paths.struct()
+    prm = PvVerifyParams(int(mode), float(tau), int(flags), int(frame), int(seed))
+    _check("pv_verify_retrace", load().pv_verify_retrace(scene, C.byref(ps), C.byref(prm), _ptr(d_stats),
+                                                          _stream(stream)))
+
+
+def pv_stage_timing(scene, n: int) -> None:
+    _check("pv_stage_timing", load().pv_stage_timing(scene, int(n)))
+
+
+def pv_stage_times(scene, n: int) -> np.ndarray:
+    """[calls, 4] milliseconds of the last recorded pv_verify_retrace calls (see include/pv.h)."""
+    ms = np.zeros(4 * max(int(n), 1), np.float32)
+    cnt = C.c_uint32(0)
+    _check("pv_stage_times", load().pv_stage_times(scene, ms.ctypes.data_as(C.c_void_p), C.byref(cnt)))
+    return ms[:4 * cnt.value].reshape(cnt.value, 4)
 
 
 def pv_trace_all(scene, paths: Paths, seed: int, frame: int, d_stats=None, stream=None) -> None:

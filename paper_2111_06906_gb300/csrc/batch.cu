@@ -213,13 +213,13 @@ __global__ void __launch_bounds__(128) k_b_continue(const BScene* B, const BFram
     if (i < total) {
       const uint32_t sc = scene_of(s_pre, n_scenes, i);
       const ContArgs& A = s_C[sc];
-      uint32_t c_rays = 0, c_tail = 0, c_upd = 0, c_trunc = 0;
+      ContCounters cc;
       Work wk;
-      continue_path<S>(s_sv[sc], s_root[sc], A, A.list[i - s_pre[sc]], c_rays, c_tail, c_upd, c_trunc, wk);
-      if (c_rays) atomicAdd(s_cnt + 4 * sc + 0, c_rays);
-      if (c_tail) atomicAdd(s_cnt + 4 * sc + 1, c_tail);
-      if (c_upd) atomicAdd(s_cnt + 4 * sc + 2, c_upd);
-      if (c_trunc) atomicAdd(s_cnt + 4 * sc + 3, c_trunc);
+      continue_path<S>(s_sv[sc], s_root[sc], A, A.list[i - s_pre[sc]], cc, wk);
+      if (cc.rays) atomicAdd(s_cnt + 4 * sc + 0, cc.rays);
+      if (cc.tail) atomicAdd(s_cnt + 4 * sc + 1, cc.tail);
+      if (cc.upd) atomicAdd(s_cnt + 4 * sc + 2, cc.upd);
+      if (cc.trunc) atomicAdd(s_cnt + 4 * sc + 3, cc.trunc);
       if (wk.nodes) atomicAdd(s_cnt64 + 2 * sc + 0, (unsigned long long)wk.nodes);
       if (wk.tris) atomicAdd(s_cnt64 + 2 * sc + 1, (unsigned long long)wk.tris);
     }
@@ -332,27 +332,11 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, 6) k_b_trace(const BScene*
     for (int i = 0; i < kSteps && !done; ++i) done = trav_step<S>(sv, r, t, stk, st.excl, wk);
     if (!done) continue;
     ++c_rays;
-    if (t.best < 0) {                          // escaped: the path ends
-      finish(A, st);
-      has_ray = false;
-      flush();
-      continue;
-    }
-    const Tri T = load_tri(sv.tris, t.best);
-    const int prim = __float_as_int(T.v0.w);
-    const float3 x = make_float3(fmaf(t.tbest, r.d.x, r.o.x), fmaf(t.tbest, r.d.y, r.o.y), fmaf(t.tbest, r.d.z, r.o.z));
-    const float rad = st.radius + t.tbest;
-    const uint32_t n = A.n;
-    A.pa[(size_t)st.k * n + st.pid] = make_float4(x.x, x.y, x.z, __int_as_float(prim));
-    A.pb[(size_t)st.k * n + st.pid] = make_float4(st.E.x, st.E.y, st.E.z, rad);
-    ++st.k;
-    ++c_photons;
-    if (st.k >= sv.B || !scatter(sv, A, st, r, x, prim, cross(f3(T.e1), f3(T.e2)), r.d, st.E, rad)) {
-      finish(A, st);
-      has_ray = false;
-      flush();
-    } else {
+    if (trace_hit(sv, A, st, r, t, c_photons)) {
       trav_begin(t, s_root[sc]);
+    } else {
+      has_ray = false;
+      flush();
     }
   }
   __syncthreads();

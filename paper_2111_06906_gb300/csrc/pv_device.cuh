@@ -18,7 +18,10 @@
 
 namespace pvk {
 
-constexpr int kStack = 64;            // traversal stack entries (BVH depth bound)
+#ifndef PV_STACK
+#define PV_STACK 64
+#endif
+constexpr int kStack = PV_STACK;      // traversal stack entries (BVH depth bound)
 constexpr int kMaxDyn = PV_MAX_DYN_OBJECTS;
 
 struct __align__(16) Node {

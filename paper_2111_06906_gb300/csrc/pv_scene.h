@@ -70,6 +70,7 @@ struct pv_scene {
   // per-frame workspace
   uint32_t* ws_mask = nullptr;       // [n_paths] intersected-segment masks (error mode)
   uint32_t* ws_cont = nullptr;       // [n_paths] continuation list
+  uint32_t* ws_list = nullptr;       // [n_paths] re-trace list of pv_verify_retrace
   uint64_t* ws_tiles = nullptr;      // [n_tiles + 1] decoupled look-back tile states
   uint32_t n_tiles = 0;
   uint32_t* ws_ctr = nullptr;        // [16] work counters
@@ -88,10 +89,17 @@ struct pv_scene {
   int* status = nullptr;             // sticky device status
   cudaStream_t last_stream = nullptr;
 
-  int verify_blocks = 0, trace_blocks = 0, cont_blocks = 0;
+  int verify_blocks = 0, trace_blocks = 0, cont_blocks = 0, cont_trace_blocks = 0;
+  // stage timing of pv_verify_retrace: a ring of stage_n calls, four events each
+  std::vector<cudaEvent_t> stage_ev;
+  uint32_t stage_n = 0, stage_next = 0, stage_count = 0;
   uint32_t visit_limit = 0;          // 0 = default cap (see view())
   uint32_t stack_need = 0;           // traversal stack entries the wide tree can need (0 = not yet measured)
 };
+
+namespace pvk {
+struct ContArgs;                     // verify_core.cuh
+}
 
 namespace pvh {
 
@@ -102,7 +110,7 @@ constexpr int kCompactItems = 16;    // paths per thread in the compaction tile
 constexpr uint32_t kTile = kCompactThreads * kCompactItems;
 
 // work counter slots in ws_ctr
-enum { CTR_CONT = 0, CTR_TRACE = 1, CTR_TILE = 2, CTR_ALL = 3 };
+enum { CTR_CONT = 0, CTR_TRACE = 1, CTR_TILE = 2, CTR_ALL = 3, CTR_LIST = 4 };
 
 pvk::SceneView view(const pv_scene* s);
 pvk::FrameLights frame_lights(const pv_scene* s);
@@ -137,6 +145,9 @@ void launch_compact(pv_scene* s, const uint32_t* info, uint32_t n, uint32_t* lis
 // trace.cu
 void launch_trace(pv_scene* s, const pv_paths* p, const uint32_t* list, const uint32_t* count, uint64_t seed,
                   uint32_t frame, pv_frame_stats* stats, cudaStream_t st);
+// Alg. 1 over the continuation list C fused with the re-trace of ``list``
+void launch_cont_trace(pv_scene* s, const pv_paths* p, const pvk::ContArgs& C, const uint32_t* list,
+                       const uint32_t* count, uint64_t seed, uint32_t frame, pv_frame_stats* stats, cudaStream_t st);
 
 // verify.cu: argument checks shared by the entry points
 int check_paths(const pv_scene* s, const pv_paths* p);

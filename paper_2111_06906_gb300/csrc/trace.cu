@@ -11,6 +11,7 @@
 #include <cstdlib>
 
 #include "trace_core.cuh"
+#include "verify_core.cuh"
 
 using namespace pvk;
 
@@ -30,7 +31,6 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS) k_tra
   __shared__ unsigned long long s_red64[32];
   const int root = *sv.root;
   const uint32_t total = A.list ? *A.count : A.n;
-  const uint32_t n = A.n;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   Work wk;
@@ -67,25 +67,8 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS) k_tra
     for (int i = 0; i < kStepsPerIter && !done; ++i) done = trav_step(sv, r, t, stk, s.excl, wk);
     if (!done) continue;
     ++c_rays;
-    if (t.best < 0) {                         // escaped: the path ends
-      finish(A, s);
-      has_ray = false;
-      continue;
-    }
-    const Tri T = load_tri(sv.tris, t.best);
-    const int prim = __float_as_int(T.v0.w);
-    const float3 x = make_float3(fmaf(t.tbest, r.d.x, r.o.x), fmaf(t.tbest, r.d.y, r.o.y), fmaf(t.tbest, r.d.z, r.o.z));
-    const float rad = s.radius + t.tbest;
-    A.pa[(size_t)s.k * n + s.pid] = make_float4(x.x, x.y, x.z, __int_as_float(prim));
-    A.pb[(size_t)s.k * n + s.pid] = make_float4(s.E.x, s.E.y, s.E.z, rad);
-    ++s.k;
-    ++c_photons;
-    if (s.k >= sv.B || !scatter(sv, A, s, r, x, prim, cross(f3(T.e1), f3(T.e2)), r.d, s.E, rad)) {
-      finish(A, s);
-      has_ray = false;
-    } else {
-      trav_begin(t, root);
-    }
+    if (trace_hit(sv, A, s, r, t, c_photons)) trav_begin(t, root);
+    else has_ray = false;
   }
   uint32_t* const ctr[2] = {A.stats ? &A.stats->trace_rays : nullptr, A.stats ? &A.stats->photons_written : nullptr};
   const uint32_t val[2] = {c_rays, c_photons};
@@ -94,22 +77,137 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS) k_tra
   block_add64(A.stats ? (unsigned long long*)&A.stats->tri_tests : nullptr, wk.tris, s_red64);
 }
 
+
+// Alg. 1 (Sec. 3.3) fused with the re-trace.  The work items are the paths
+// the box test sent to Alg. 1, then the paths verification itself marked for
+// re-tracing.  A continuation lane runs Alg. 1's closest-hit queries through
+// the same resumable traversal as the re-trace rays, so its queries
+// interleave with other lanes' rays instead of holding a separate kernel to
+// its slowest chain; a path whose Eq. 2 test fails goes on to its re-trace
+// from the failing vertex in the same lane.  Every path sees the same
+// arithmetic as in k_continue followed by k_trace, so the records are
+// identical; only the order in which paths are processed differs.
+__device__ __forceinline__ void cont_flush(ContCounters& cc, uint32_t* s_cnt) {
+  if (cc.rays) atomicAdd(s_cnt + 0, cc.rays);
+  if (cc.tail) atomicAdd(s_cnt + 1, cc.tail);
+  if (cc.upd) atomicAdd(s_cnt + 2, cc.upd);
+  if (cc.trunc) atomicAdd(s_cnt + 3, cc.trunc);
+}
+
+__global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS)
+    k_cont_trace(SceneView sv, FrameLights L, TraceArgs A, ContArgs C) {
+  __shared__ uint32_t s_red[32 * 2];
+  __shared__ unsigned long long s_red64[32];
+  __shared__ uint32_t s_cnt[4];
+  if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0u;
+  __syncthreads();
+  const int root = *sv.root;
+  const uint32_t n_cont = min(*C.count, C.n);
+  const uint32_t total = n_cont + min(*A.count, A.n);
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  Work wk;
+  PathState s;
+  Ray r;
+  Trav t;
+  int stk[kStack];
+  uint32_t cmask = 0, cmeta = 0;             // Alg. 1 state beyond s.k (segment), s.E (a_orig), s.excl (a_prim)
+  bool has_ray = false, exhausted = false, cont = false;
+  uint32_t c_rays = 0, c_photons = 0;
+  for (uint32_t guard = 0; guard < (1u << 30); ++guard) {
+    const bool need = !has_ray && !exhausted;
+    const unsigned nm = __ballot_sync(0xffffffffu, need);
+    if (nm) {
+      const int leader = __ffs(nm) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(A.ticket, (uint32_t)__popc(nm));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (need) {
+        const uint32_t idx = base + __popc(nm & lt);
+        if (idx < n_cont) {
+          ContCounters cc;
+          s.pid = C.list[idx];
+          if (cont_begin(sv, C, s.pid, s.cell, s.k, cmask, cmeta, s.E, s.excl, r, cc)) {
+            trav_begin(t, root);
+            has_ray = true;
+            cont = true;
+          }
+          cont_flush(cc, s_cnt);
+        } else if (idx < total) {
+          if (init_path(sv, L, A, idx - n_cont, s, r)) {
+            trav_begin(t, root);
+            has_ray = true;
+            cont = false;
+          }
+        } else {
+          exhausted = true;
+        }
+      }
+    }
+    if (__all_sync(0xffffffffu, exhausted && !has_ray)) break;
+    if (!has_ray) continue;
+    bool done = false;
+#pragma unroll 1
+    for (int i = 0; i < kStepsPerIter && !done; ++i) done = trav_step(sv, r, t, stk, s.excl, wk);
+    if (!done) continue;
+    if (cont) {
+      ContCounters cc;
+      float3 a_cur;
+      int o = cont_hit(sv, C, s.pid, s.cell, s.k, cmask, cmeta, s.E, s.excl, r, t.best, t.tbest, a_cur, cc);
+      if (o == kContNext && !cont_next(sv, C, s.pid, s.cell, s.k, cmask, cmeta, s.E, s.excl, a_cur, r, cc))
+        o = kContDone;
+      cont_flush(cc, s_cnt);
+      if (o == kContNext) {
+        trav_begin(t, root);
+      } else if (o == kContTail && init_pid(sv, L, A, s.pid, false, s, r)) {
+        cont = false;                            // Eq. 2 failed: re-trace from the failing vertex
+        trav_begin(t, root);
+      } else {
+        has_ray = false;
+      }
+      continue;
+    }
+    ++c_rays;
+    if (trace_hit(sv, A, s, r, t, c_photons)) trav_begin(t, root);
+    else has_ray = false;
+  }
+  uint32_t* const ctr[2] = {A.stats ? &A.stats->trace_rays : nullptr, A.stats ? &A.stats->photons_written : nullptr};
+  const uint32_t val[2] = {c_rays, c_photons};
+  block_add_n<2>(ctr, val, s_red);           // synchronises the block: s_cnt is complete
+  if (threadIdx.x == 0 && A.stats) {
+    if (s_cnt[0]) atomicAdd(&A.stats->cont_rays, s_cnt[0]);
+    if (s_cnt[1]) {                            // the tails join the re-trace list
+      atomicAdd(&A.stats->n_tail, s_cnt[1]);
+      atomicAdd(&A.stats->n_listed, s_cnt[1]);
+    }
+    if (s_cnt[2]) atomicAdd(&A.stats->n_updated, s_cnt[2]);
+    if (s_cnt[3]) atomicAdd(&A.stats->n_truncated, s_cnt[3]);
+  }
+  block_add64(A.stats ? (unsigned long long*)&A.stats->node_visits : nullptr, wk.nodes, s_red64);
+  block_add64(A.stats ? (unsigned long long*)&A.stats->tri_tests : nullptr, wk.tris, s_red64);
+}
+
 }  // namespace
 
 namespace pvh {
 
-void launch_trace(pv_scene* s, const pv_paths* p, const uint32_t* list, const uint32_t* count, uint64_t seed,
-                  uint32_t frame, pv_frame_stats* stats, cudaStream_t st) {
-  if (!s->trace_blocks) {
-    int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace, kTraceThreads, 0);
-    // tuning override: persistent blocks per SM (at most the occupancy limit)
-    if (const char* e = std::getenv("PV_TRACE_BLOCKS_PER_SM")) {
-      const int want = std::atoi(e);
-      if (want > 0 && want < per) per = want;
-    }
-    s->trace_blocks = (per > 0 ? per : 1) * s->num_sms;
+namespace {
+
+// persistent blocks of a kernel: its occupancy limit on every SM, or fewer
+// when PV_TRACE_BLOCKS_PER_SM asks for fewer (a tuning override)
+template <typename K>
+int persistent_blocks(const pv_scene* s, K kernel) {
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kTraceThreads, 0);
+  if (const char* e = std::getenv("PV_TRACE_BLOCKS_PER_SM")) {
+    const int want = std::atoi(e);
+    if (want > 0 && want < per) per = want;
   }
+  return (per > 0 ? per : 1) * s->num_sms;
+}
+
+TraceArgs trace_args(pv_scene* s, const pv_paths* p, const uint32_t* list, const uint32_t* count, uint64_t seed,
+                     uint32_t frame, pv_frame_stats* stats) {
   TraceArgs A;
   A.n = p->n;
   A.info = p->info;
@@ -122,8 +220,25 @@ void launch_trace(pv_scene* s, const pv_paths* p, const uint32_t* list, const ui
   A.seed = seed;
   A.frame = frame;
   A.stats = stats;
+  return A;
+}
+
+}  // namespace
+
+void launch_trace(pv_scene* s, const pv_paths* p, const uint32_t* list, const uint32_t* count, uint64_t seed,
+                  uint32_t frame, pv_frame_stats* stats, cudaStream_t st) {
+  if (!s->trace_blocks) s->trace_blocks = persistent_blocks(s, k_trace);
+  const TraceArgs A = trace_args(s, p, list, count, seed, frame, stats);
   cudaMemsetAsync(A.ticket, 0, sizeof(uint32_t), st);
   if (p->n) k_trace<<<s->trace_blocks, kTraceThreads, 0, st>>>(view(s), frame_lights(s), A);
+}
+
+void launch_cont_trace(pv_scene* s, const pv_paths* p, const ContArgs& C, const uint32_t* list, const uint32_t* count,
+                       uint64_t seed, uint32_t frame, pv_frame_stats* stats, cudaStream_t st) {
+  if (!s->cont_trace_blocks) s->cont_trace_blocks = persistent_blocks(s, k_cont_trace);
+  const TraceArgs A = trace_args(s, p, list, count, seed, frame, stats);
+  cudaMemsetAsync(A.ticket, 0, sizeof(uint32_t), st);
+  if (p->n) k_cont_trace<<<s->cont_trace_blocks, kTraceThreads, 0, st>>>(view(s), frame_lights(s), A, C);
 }
 
 }  // namespace pvh

@@ -55,11 +55,10 @@ __device__ __forceinline__ float3 load_origin(const TraceArgs& A, uint32_t p) {
   return make_float3(A.origin[p], A.origin[A.n + p], A.origin[2 * (size_t)A.n + p]);
 }
 
-// Set up the first ray of list entry idx; false if the path ends at once.
-__device__ __forceinline__ bool init_path(const SceneView& sv, const FrameLights& L, const TraceArgs& A, uint32_t idx, PathState& s,
-                          Ray& r) {
-  const bool all = A.list == nullptr;
-  const uint32_t pid = all ? idx : A.list[idx];
+// Set up the first ray of path pid (``all``: a full trace from the light,
+// else a re-trace as its info word says); false if the path ends at once.
+__device__ __forceinline__ bool init_pid(const SceneView& sv, const FrameLights& L, const TraceArgs& A, uint32_t pid,
+                                         bool all, PathState& s, Ray& r) {
   const uint32_t n = A.n;
   s.pid = pid;
   const uint32_t w = all ? 0u : A.info[pid];
@@ -106,6 +105,38 @@ __device__ __forceinline__ bool init_path(const SceneView& sv, const FrameLights
   const float3 xprev = start >= 2 ? f3(A.pa[(size_t)(start - 2) * n + pid]) : load_origin(A, pid);
   const int prim = __float_as_int(v.w);
   if (!scatter(sv, A, s, r, f3(v), prim, prim_normal(sv, prim, false), normalize_exact(f3(v) - xprev), f3(e), e.w)) {
+    finish(A, s);
+    return false;
+  }
+  return true;
+}
+
+// Set up the first ray of list entry idx; false if the path ends at once.
+__device__ __forceinline__ bool init_path(const SceneView& sv, const FrameLights& L, const TraceArgs& A, uint32_t idx,
+                                          PathState& s, Ray& r) {
+  const bool all = A.list == nullptr;
+  return init_pid(sv, L, A, all ? idx : A.list[idx], all, s, r);
+}
+
+// The ray of path s ended (hit t.best at t.tbest, or escaped): store its
+// photon and set up the next bounce.  False once the path is finished (its
+// info word written).
+__device__ __forceinline__ bool trace_hit(const SceneView& sv, const TraceArgs& A, PathState& s, Ray& r, const Trav& t,
+                                          uint32_t& c_photons) {
+  if (t.best < 0) {                          // escaped: the path ends
+    finish(A, s);
+    return false;
+  }
+  const Tri T = load_tri(sv.tris, t.best);
+  const int prim = __float_as_int(T.v0.w);
+  const float3 x = make_float3(fmaf(t.tbest, r.d.x, r.o.x), fmaf(t.tbest, r.d.y, r.o.y), fmaf(t.tbest, r.d.z, r.o.z));
+  const float rad = s.radius + t.tbest;
+  const uint32_t n = A.n;
+  A.pa[(size_t)s.k * n + s.pid] = make_float4(x.x, x.y, x.z, __int_as_float(prim));
+  A.pb[(size_t)s.k * n + s.pid] = make_float4(s.E.x, s.E.y, s.E.z, rad);
+  ++s.k;
+  ++c_photons;
+  if (s.k >= sv.B || !scatter(sv, A, s, r, x, prim, cross(f3(T.e1), f3(T.e2)), r.d, s.E, rad)) {
     finish(A, s);
     return false;
   }

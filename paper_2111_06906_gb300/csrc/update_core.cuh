@@ -69,6 +69,25 @@ struct XformParams {
   uint32_t n_dyn;
 };
 
+// Object-local corners v (9 floats) of one triangle under the 3x4 row-major
+// pose m; widens the tight box (lo, hi) by the transformed corners.
+__device__ __forceinline__ Tri xform_tri(const float* m, const float* v, uint32_t prim, float* lo, float* hi) {
+  float w[9];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      w[3 * k + r] = fmaf(m[4 * r + 0], v[3 * k + 0], fmaf(m[4 * r + 1], v[3 * k + 1], fmaf(m[4 * r + 2], v[3 * k + 2], m[4 * r + 3])));
+      lo[r] = fminf(lo[r], w[3 * k + r]);
+      hi[r] = fmaxf(hi[r], w[3 * k + r]);
+    }
+  Tri T;
+  T.v0 = make_float4(w[0], w[1], w[2], __int_as_float((int)prim));
+  T.e1 = make_float4(w[3] - w[0], w[4] - w[1], w[5] - w[2], 0.f);
+  T.e2 = make_float4(w[6] - w[0], w[7] - w[1], w[8] - w[2], 0.f);
+  return T;
+}
+
 // One block (256 threads) per dynamic slot: keep the previous pose (transform
 // and tight box), and for a moved object transform its object-local corners to
 // the new pose and reduce the new tight box.
@@ -87,23 +106,7 @@ __device__ __forceinline__ void update_object(const float* xf_slot, bool moved, 
   if (!moved) return;
   float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
   const uint32_t b = o->tri_begin, e = b + o->tri_count;
-  for (uint32_t i = b + threadIdx.x; i < e; i += blockDim.x) {
-    const float* v = local + 9 * (size_t)i;
-    float w[9];
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        w[3 * k + r] = fmaf(m[4 * r + 0], v[3 * k + 0], fmaf(m[4 * r + 1], v[3 * k + 1], fmaf(m[4 * r + 2], v[3 * k + 2], m[4 * r + 3])));
-        lo[r] = fminf(lo[r], w[3 * k + r]);
-        hi[r] = fmaxf(hi[r], w[3 * k + r]);
-      }
-    Tri T;
-    T.v0 = make_float4(w[0], w[1], w[2], __int_as_float((int)prim[i]));
-    T.e1 = make_float4(w[3] - w[0], w[4] - w[1], w[5] - w[2], 0.f);
-    T.e2 = make_float4(w[6] - w[0], w[7] - w[1], w[8] - w[2], 0.f);
-    tris[i] = T;
-  }
+  for (uint32_t i = b + threadIdx.x; i < e; i += blockDim.x) tris[i] = xform_tri(m, local + 9 * (size_t)i, prim[i], lo, hi);
   for (int k = 0; k < 3; ++k) {
     red[k][threadIdx.x] = lo[k];
     red[3 + k][threadIdx.x] = hi[k];

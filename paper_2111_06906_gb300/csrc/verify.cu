@@ -6,6 +6,8 @@
 // k_continue (persistent, over the paths k_verify flagged in error mode):
 //   the error-based threshold continuation of Sec. 3.3, Alg. 1 and Eq. 2.
 // Then the replace bits are compacted into the re-trace list (compact.cu).
+#include <algorithm>
+
 #include "verify_core.cuh"
 
 using namespace pvk;
@@ -18,13 +20,13 @@ __global__ void __launch_bounds__(pvh::kVerifyThreads) k_verify(SceneView sv, Fr
   verify_block<kPointVis, kExact>(sv, L, A, blockIdx.x * blockDim.x + threadIdx.x, sm);
 }
 
-__global__ void __launch_bounds__(128) k_continue(SceneView sv, ContArgs A) {
+__global__ void __launch_bounds__(128, 6) k_continue(SceneView sv, ContArgs A) {
   __shared__ uint32_t s_red[32 * 4];
   __shared__ unsigned long long s_red64[32];
   const int root = *sv.root;
   const uint32_t total = *A.count;
   const int lane = threadIdx.x & 31;
-  uint32_t c_rays = 0, c_tail = 0, c_upd = 0, c_trunc = 0;
+  ContCounters cc;
   Work wk;
   for (uint32_t guard = 0; guard < (1u << 26); ++guard) {
     uint32_t base = 0;
@@ -32,12 +34,12 @@ __global__ void __launch_bounds__(128) k_continue(SceneView sv, ContArgs A) {
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= total) break;
     const uint32_t i = base + lane;
-    if (i < total) continue_path(sv, root, A, A.list[i], c_rays, c_tail, c_upd, c_trunc, wk);
+    if (i < total) continue_path(sv, root, A, A.list[i], cc, wk);
     __syncwarp();
   }
   uint32_t* const ctr[4] = {A.stats ? &A.stats->cont_rays : nullptr, A.stats ? &A.stats->n_tail : nullptr,
                             A.stats ? &A.stats->n_updated : nullptr, A.stats ? &A.stats->n_truncated : nullptr};
-  const uint32_t val[4] = {c_rays, c_tail, c_upd, c_trunc};
+  const uint32_t val[4] = {cc.rays, cc.tail, cc.upd, cc.trunc};
   block_add_n<4>(ctr, val, s_red);
   block_add64(A.stats ? (unsigned long long*)&A.stats->node_visits : nullptr, wk.nodes, s_red64);
   block_add64(A.stats ? (unsigned long long*)&A.stats->tri_tests : nullptr, wk.tris, s_red64);
@@ -54,17 +56,37 @@ int check_paths(const pv_scene* s, const pv_paths* p) {
 }
 }  // namespace pvh
 
-extern "C" int pv_verify_paths(pv_scene* s, const pv_paths* paths, const pv_verify_params* params, uint32_t* d_list,
-                               uint32_t* d_count, pv_frame_stats* d_stats, void* stream) {
-  int rc = pvh::check_paths(s, paths);
+namespace {
+
+int check_verify(const pv_scene* s, const pv_paths* paths, const pv_verify_params* params) {
+  const int rc = pvh::check_paths(s, paths);
   if (rc != PV_OK) return rc;
-  if (!params || !d_list || !d_count) return PV_ERR_ARG;
+  if (!params) return PV_ERR_ARG;
   if (params->mode < PV_MODE_NAIVE_AABB || params->mode > PV_MODE_ERROR || !(params->tau >= 0.0f)) return PV_ERR_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  s->last_stream = st;
+  return PV_OK;
+}
+
+ContArgs cont_args(pv_scene* s, const pv_paths* paths, const pv_verify_params* params, pv_frame_stats* d_stats) {
+  ContArgs C;
+  C.n = paths->n;
+  C.info = paths->info;
+  C.origin = paths->origin;
+  C.pa = reinterpret_cast<float4*>(paths->pa);
+  C.pb = reinterpret_cast<const float4*>(paths->pb);
+  C.mask = s->ws_mask;
+  C.list = s->ws_cont;
+  C.count = s->ws_ctr + pvh::CTR_ALL;
+  C.ticket = s->ws_ctr + pvh::CTR_CONT;
+  C.tau = params->tau;
+  C.stats = d_stats;
+  return C;
+}
+
+// Work counters reset, DM_C of moved lights with a map cleared, then k_verify
+// (Sec. 3.1 + 3.2).  ``cont``: Alg. 1 has paths to look at this frame.
+int launch_verify(pv_scene* s, const pv_paths* paths, const pv_verify_params* params, pv_frame_stats* d_stats,
+                  const SceneView& sv, const FrameLights& L, cudaStream_t st, bool& cont) {
   const uint32_t n = paths->n;
-  const SceneView sv = pvh::view(s);
-  const FrameLights L = pvh::frame_lights(s);
   if (cudaMemsetAsync(s->ws_ctr, 0, 16 * sizeof(uint32_t), st) != cudaSuccess) return PV_ERR_CUDA;
   for (uint32_t l = 0; l < s->n_lights; ++l)       // DM_C of moved lights with a map is counted afresh
     if (L.dm[l].dims && ((L.moved_mask >> l) & 1u))
@@ -95,27 +117,106 @@ extern "C" int pv_verify_paths(pv_scene* s, const pv_paths* paths, const pv_veri
     else if (exact) k_verify<false, true><<<grid, pvh::kVerifyThreads, 0, st>>>(sv, L, A);
     else k_verify<false, false><<<grid, pvh::kVerifyThreads, 0, st>>>(sv, L, A);
   }
-  if (n && params->mode == PV_MODE_ERROR && (s->moved || L.moved_mask)) {
-    if (!s->cont_blocks) {
-      int per = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_continue, 128, 0);
-      s->cont_blocks = (per > 0 ? per : 1) * s->num_sms;
-    }
-    ContArgs C;
-    C.n = n;
-    C.info = paths->info;
-    C.origin = paths->origin;
-    C.pa = reinterpret_cast<float4*>(paths->pa);
-    C.pb = reinterpret_cast<const float4*>(paths->pb);
-    C.mask = s->ws_mask;
-    C.list = s->ws_cont;
-    C.count = s->ws_ctr + pvh::CTR_ALL;
-    C.ticket = s->ws_ctr + pvh::CTR_CONT;
-    C.tau = params->tau;
-    C.stats = d_stats;
-    k_continue<<<s->cont_blocks, 128, 0, st>>>(sv, C);
+  cont = n && params->mode == PV_MODE_ERROR && (s->moved || L.moved_mask);
+  return PV_OK;
+}
+
+void launch_continue(pv_scene* s, const SceneView& sv, const ContArgs& C, cudaStream_t st) {
+  if (!s->cont_blocks) {
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_continue, 128, 0);
+    s->cont_blocks = (per > 0 ? per : 1) * s->num_sms;
   }
+  k_continue<<<s->cont_blocks, 128, 0, st>>>(sv, C);
+}
+
+}  // namespace
+
+extern "C" int pv_verify_paths(pv_scene* s, const pv_paths* paths, const pv_verify_params* params, uint32_t* d_list,
+                               uint32_t* d_count, pv_frame_stats* d_stats, void* stream) {
+  int rc = check_verify(s, paths, params);
+  if (rc != PV_OK) return rc;
+  if (!d_list || !d_count) return PV_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  s->last_stream = st;
+  const SceneView sv = pvh::view(s);
+  const FrameLights L = pvh::frame_lights(s);
+  bool cont = false;
+  if ((rc = launch_verify(s, paths, params, d_stats, sv, L, st, cont)) != PV_OK) return rc;
+  if (cont) launch_continue(s, sv, cont_args(s, paths, params, d_stats), st);
   if (s->has_dm && (rc = pvh::dm_frame(s, paths, L, params, d_stats, st)) != PV_OK) return rc;
-  pvh::launch_compact(s, paths->info, n, d_list, d_count, d_stats ? &d_stats->n_listed : nullptr, st);
+  pvh::launch_compact(s, paths->info, paths->n, d_list, d_count, d_stats ? &d_stats->n_listed : nullptr, st);
   return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
+}
+
+extern "C" int pv_verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params* params,
+                                 pv_frame_stats* d_stats, void* stream) {
+  int rc = check_verify(s, paths, params);
+  if (rc != PV_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  s->last_stream = st;
+  const SceneView sv = pvh::view(s);
+  const FrameLights L = pvh::frame_lights(s);
+  cudaEvent_t* ev = s->stage_n ? &s->stage_ev[4 * s->stage_next] : nullptr;
+  auto mark = [&](int k) {
+    if (ev) cudaEventRecord(ev[k], st);
+  };
+  mark(0);
+  bool cont = false;
+  if ((rc = launch_verify(s, paths, params, d_stats, sv, L, st, cont)) != PV_OK) return rc;
+  mark(1);
+  const ContArgs C = cont_args(s, paths, params, d_stats);
+  uint32_t* const list = s->ws_list;
+  uint32_t* const count = s->ws_ctr + pvh::CTR_LIST;
+  uint32_t* const listed = d_stats ? &d_stats->n_listed : nullptr;
+  if (cont && !s->has_dm) {
+    // the paths k_verify marked, then Alg. 1 and the re-trace in one persistent kernel
+    pvh::launch_compact(s, paths->info, paths->n, list, count, listed, st);
+    mark(2);
+    pvh::launch_cont_trace(s, paths, C, list, count, params->seed, params->frame, d_stats, st);
+  } else {
+    // distribution maps prune and fill after Alg. 1 and before the list is final
+    if (cont) launch_continue(s, sv, C, st);
+    if (s->has_dm && (rc = pvh::dm_frame(s, paths, L, params, d_stats, st)) != PV_OK) return rc;
+    pvh::launch_compact(s, paths->info, paths->n, list, count, listed, st);
+    mark(2);
+    pvh::launch_trace(s, paths, list, count, params->seed, params->frame, d_stats, st);
+  }
+  mark(3);
+  if (ev) {
+    s->stage_next = (s->stage_next + 1) % s->stage_n;
+    s->stage_count = std::min(s->stage_count + 1, s->stage_n);
+  }
+  return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
+}
+
+extern "C" int pv_stage_timing(pv_scene* s, uint32_t n) {
+  if (!s || n > 4096) return PV_ERR_ARG;
+  if (s->last_stream && cudaStreamSynchronize(s->last_stream) != cudaSuccess) return PV_ERR_CUDA;
+  for (cudaEvent_t e : s->stage_ev)
+    if (e) cudaEventDestroy(e);
+  s->stage_ev.assign(4 * (size_t)n, nullptr);
+  s->stage_n = s->stage_next = s->stage_count = 0;
+  for (auto& e : s->stage_ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      e = nullptr;
+      return PV_ERR_CUDA;
+    }
+  s->stage_n = n;
+  return PV_OK;
+}
+
+extern "C" int pv_stage_times(pv_scene* s, float* ms, uint32_t* count) {
+  if (!s || !ms || !count) return PV_ERR_ARG;
+  const uint32_t c = s->stage_count;
+  for (uint32_t i = 0; i < c; ++i) {
+    const uint32_t k = (s->stage_next + s->stage_n - c + i) % s->stage_n;
+    cudaEvent_t* ev = &s->stage_ev[4 * k];
+    if (cudaEventSynchronize(ev[3]) != cudaSuccess) return PV_ERR_CUDA;
+    for (int j = 0; j < 3; ++j)
+      if (cudaEventElapsedTime(ms + 4 * i + j, ev[j], ev[j + 1]) != cudaSuccess) return PV_ERR_CUDA;
+    if (cudaEventElapsedTime(ms + 4 * i + 3, ev[0], ev[3]) != cudaSuccess) return PV_ERR_CUDA;
+  }
+  *count = c;
+  return PV_OK;
 }

@@ -437,106 +437,162 @@ struct ContArgs {
   pv_frame_stats* stats;
 };
 
-// Alg. 1 for one path whose intersected segments are ``mask``.  Vertices are
-// read from and updated in the path buffer as the loop advances; only the
-// origin of the current segment (current and original position) is carried
-// in registers.
-template <int S = kStack>
-__device__ __forceinline__ void continue_path(const SceneView& sv, int root, const ContArgs& A, uint32_t p, uint32_t& c_rays,
-                              uint32_t& c_tail, uint32_t& c_upd, uint32_t& c_trunc, Work& wk) {
+// Alg. 1 as a resumable state machine, so that a persistent kernel can
+// interleave its ray queries with other rays.  Between two queries a path's
+// state is: the segment ``seg`` whose query is in flight; ``mask`` (bits 0-15
+// the segments the box test intersected, bits 16-31 the segments whose origin
+// moved); ``meta`` (bits 0-3 the path length, then "origin carried" and
+// "vertices updated"); the original position ``a_orig`` and primitive
+// ``a_prim`` of the segment's origin.  The current origin is the query ray's
+// origin, and ``a_prim`` doubles as the query's exclusion (the light origin
+// of segment 1 carries -1).  Vertices are read from and updated in the path
+// buffer as the loop advances.
+constexpr uint32_t kContCarried = 1u << 4;     // the segment's origin moved and is carried in registers
+constexpr uint32_t kContUpdated = 1u << 5;     // some vertex was moved
+enum { kContNext = 0, kContDone = 1, kContTail = 2 };
+
+struct ContCounters {
+  uint32_t rays = 0, tail = 0, upd = 0, trunc = 0;
+};
+
+// stored vertex k of path p (0 = origin, primitive -1)
+__device__ __forceinline__ float4 cont_vertex(const ContArgs& A, uint32_t p, uint32_t k) {
   const uint32_t n = A.n;
-  const uint32_t w = A.info[p];
-  const uint32_t cell = w & PV_INFO_CELL_MASK;
-  uint32_t nseg = min(info_nseg(w), sv.B);
-  const uint32_t mask = A.mask[p];
-  const float3 org = make_float3(A.origin[p], A.origin[n + p], A.origin[2 * (size_t)n + p]);
-  auto vertex = [&](uint32_t k) -> float4 {        // stored vertex k (0 = origin)
-    return k == 0 ? make_float4(org.x, org.y, org.z, __int_as_float(-1)) : A.pa[(size_t)(k - 1) * n + p];
-  };
-  uint32_t moved_origin = 0;
-  bool updated = false, a_valid = false;
-  int done = 0;
-  float3 a_cur = org, a_orig = org;
-  int a_prim = -1;
-  uint32_t seg = __ffs(mask) - 1;
+  return k == 0 ? make_float4(A.origin[p], A.origin[n + p], A.origin[2 * (size_t)n + p], __int_as_float(-1))
+                : A.pa[(size_t)(k - 1) * n + p];
+}
+
+// The path is kept (possibly shortened or with moved vertices).
+__device__ __forceinline__ void cont_finish(const ContArgs& A, uint32_t p, uint32_t cell, uint32_t meta,
+                                            ContCounters& cc) {
+  A.info[p] = info_make(cell, meta & 15u, 0, false, false);
+  if (meta & kContUpdated) ++cc.upd;
+}
+
+// Set up the query of the next segment from ``seg`` on that needs one; false
+// once the path is finished (its info word written).  ``a_cur`` is the
+// carried origin (used when kContCarried is set).
+__device__ __forceinline__ bool cont_next(const SceneView& sv, const ContArgs& A, uint32_t p, uint32_t cell,
+                                          uint32_t& seg, uint32_t& mask, uint32_t& meta, float3& a_orig, int& a_prim,
+                                          float3 a_cur, Ray& r, ContCounters& cc) {
+  const uint32_t nseg = meta & 15u;
   while (seg <= nseg) {
-    if (!((mask >> seg) & 1u) && !((moved_origin >> seg) & 1u)) {
+    if (!((mask >> seg) & 1u) && !((mask >> (16 + seg)) & 1u)) {
       ++seg;
-      a_valid = false;
+      meta &= ~kContCarried;
       continue;
     }
-    if (!a_valid) {
-      const float4 v = vertex(seg - 1);
+    if (!(meta & kContCarried)) {
+      const float4 v = cont_vertex(A, p, seg - 1);
       a_cur = a_orig = f3(v);
       a_prim = __float_as_int(v.w);
     }
-    const float4 bv = vertex(seg);
-    const float3 b = f3(bv);
-    const int b_prim = __float_as_int(bv.w);
-    const float3 d = normalize_exact(b - a_cur);
-    const Ray r = make_ray(a_cur, d, sv.tmin);
-    Hit h;
-    ++c_rays;
-    if (!closest_hit<S>(sv, root, r, seg == 1 ? -1 : a_prim, h, wk)) {   // escaped: the path ends here
-      nseg = seg - 1;
-      ++c_trunc;
-      done = 1;
-      break;
-    }
-    const Tri T = load_tri(sv.tris, h.tri);
-    const int pn = __float_as_int(T.v0.w);
-    const float3 xn = make_float3(fmaf(h.t, d.x, a_cur.x), fmaf(h.t, d.y, a_cur.y), fmaf(h.t, d.z, a_cur.z));
-    const bool close = pn == b_prim && maxabs3(xn - b) <= sv.close_tol;
-    if (seg == nseg) {                                                  // last photon: move it
-      A.pa[(size_t)(seg - 1) * n + p] = make_float4(xn.x, xn.y, xn.z, __int_as_float(pn));
-      updated = true;
-      done = 1;
-      break;
-    }
-    const float4 cv = vertex(seg + 1);                                  // stored next photon
-    const float3 c = f3(cv);
-    const float3 EO = f3(A.pb[(size_t)seg * n + p]);
-    float3 EN = EO;
-    if (!close) {
-      const float4 albn = __ldg(sv.prim_alb + pn);
-      const float3 nn = normalize(cross(f3(T.e1), f3(T.e2)));
-      const float3 nsn = dot(nn, d) < 0.0f ? nn : -1.0f * nn;
-      const float3 wv = c - xn;
-      const float wl = sqrtf(dot(wv, wv));
-      const float cosn = wl > 0.0f ? fmaxf(0.0f, dot(nsn, (1.0f / wl) * wv)) : 0.0f;
-      const float4 albo = __ldg(sv.prim_alb + b_prim);
-      const float3 no = normalize(prim_normal(sv, b_prim, true));
-      const float3 dino = normalize_exact(b - a_orig);
-      const float3 nso = dot(no, dino) < 0.0f ? no : -1.0f * no;
-      const float coso = dot(nso, normalize_exact(c - b));
-      const float3 Ei = f3(A.pb[(size_t)(seg - 1) * n + p]);
-      const float f = coso > 0.0f ? cosn / (albo.w * coso) : 0.0f;
-      EN = make_float3(Ei.x * albn.x * f, Ei.y * albn.y * f, Ei.z * albn.z * f);
-    }
-    if (!energy_close(EN, EO, A.tau)) {                                // Eq. 2 fails: re-trace from here
-      A.pa[(size_t)(seg - 1) * n + p] = make_float4(xn.x, xn.y, xn.z, __int_as_float(pn));
-      A.info[p] = info_make(cell, seg, seg, true, false);
-      ++c_tail;
-      done = 2;
-      break;
-    }
-    if (close && !((mask >> (seg + 1)) & 1u) && !slot_moved(sv, pn) && !slot_moved(sv, __float_as_int(cv.w))) {
-      seg += 2;                                                         // next segment known valid
-      a_valid = false;
-      continue;
-    }
-    A.pa[(size_t)(seg - 1) * n + p] = make_float4(xn.x, xn.y, xn.z, __int_as_float(pn));
-    a_cur = xn;                                                         // origin of the next segment moved
-    a_orig = b;
-    a_prim = pn;
-    a_valid = true;
-    updated = true;
-    moved_origin |= 1u << (seg + 1);
-    ++seg;
+    const float3 b = f3(cont_vertex(A, p, seg));
+    r = make_ray(a_cur, normalize_exact(b - a_cur), sv.tmin);
+    ++cc.rays;
+    return true;
   }
-  if (done != 2) {
-    A.info[p] = info_make(cell, nseg, 0, false, false);
-    if (updated) ++c_upd;
+  cont_finish(A, p, cell, meta, cc);
+  return false;
+}
+
+// Start Alg. 1 on path p; false if it needs no query (finished).
+__device__ __forceinline__ bool cont_begin(const SceneView& sv, const ContArgs& A, uint32_t p, uint32_t& cell,
+                                           uint32_t& seg, uint32_t& mask, uint32_t& meta, float3& a_orig, int& a_prim,
+                                           Ray& r, ContCounters& cc) {
+  const uint32_t w = A.info[p];
+  cell = w & PV_INFO_CELL_MASK;
+  meta = min(info_nseg(w), sv.B);
+  mask = A.mask[p] & 0xFFFFu;
+  seg = __ffs(mask) - 1;
+  return cont_next(sv, A, p, cell, seg, mask, meta, a_orig, a_prim, a_orig, r, cc);
+}
+
+// Take the result of the query of segment ``seg`` (hit triangle ``tri`` at
+// ``t``, tri < 0 for none).  kContNext: continue with cont_next from the
+// returned ``a_cur``; kContDone: the path is kept (info written); kContTail:
+// Eq. 2 failed, the path is marked for re-tracing from vertex ``seg``.
+__device__ __forceinline__ int cont_hit(const SceneView& sv, const ContArgs& A, uint32_t p, uint32_t cell,
+                                        uint32_t& seg, uint32_t& mask, uint32_t& meta, float3& a_orig, int& a_prim,
+                                        const Ray& r, int tri, float t, float3& a_cur, ContCounters& cc) {
+  const uint32_t n = A.n;
+  if (tri < 0) {                                                       // escaped: the path ends here
+    meta = (meta & ~15u) | (seg - 1);
+    ++cc.trunc;
+    cont_finish(A, p, cell, meta, cc);
+    return kContDone;
+  }
+  a_cur = r.o;
+  const float3 d = r.d;
+  const float4 bv = cont_vertex(A, p, seg);
+  const float3 b = f3(bv);
+  const int b_prim = __float_as_int(bv.w);
+  const Tri T = load_tri(sv.tris, tri);
+  const int pn = __float_as_int(T.v0.w);
+  const float3 xn = make_float3(fmaf(t, d.x, a_cur.x), fmaf(t, d.y, a_cur.y), fmaf(t, d.z, a_cur.z));
+  const bool close = pn == b_prim && maxabs3(xn - b) <= sv.close_tol;
+  if (seg == (meta & 15u)) {                                           // last photon: move it
+    A.pa[(size_t)(seg - 1) * n + p] = make_float4(xn.x, xn.y, xn.z, __int_as_float(pn));
+    meta |= kContUpdated;
+    cont_finish(A, p, cell, meta, cc);
+    return kContDone;
+  }
+  const float4 cv = cont_vertex(A, p, seg + 1);                       // stored next photon
+  const float3 c = f3(cv);
+  const float3 EO = f3(A.pb[(size_t)seg * n + p]);
+  float3 EN = EO;
+  if (!close) {
+    const float4 albn = __ldg(sv.prim_alb + pn);
+    const float3 nn = normalize(cross(f3(T.e1), f3(T.e2)));
+    const float3 nsn = dot(nn, d) < 0.0f ? nn : -1.0f * nn;
+    const float3 wv = c - xn;
+    const float wl = sqrtf(dot(wv, wv));
+    const float cosn = wl > 0.0f ? fmaxf(0.0f, dot(nsn, (1.0f / wl) * wv)) : 0.0f;
+    const float4 albo = __ldg(sv.prim_alb + b_prim);
+    const float3 no = normalize(prim_normal(sv, b_prim, true));
+    const float3 dino = normalize_exact(b - a_orig);
+    const float3 nso = dot(no, dino) < 0.0f ? no : -1.0f * no;
+    const float coso = dot(nso, normalize_exact(c - b));
+    const float3 Ei = f3(A.pb[(size_t)(seg - 1) * n + p]);
+    const float f = coso > 0.0f ? cosn / (albo.w * coso) : 0.0f;
+    EN = make_float3(Ei.x * albn.x * f, Ei.y * albn.y * f, Ei.z * albn.z * f);
+  }
+  if (!energy_close(EN, EO, A.tau)) {                                 // Eq. 2 fails: re-trace from here
+    A.pa[(size_t)(seg - 1) * n + p] = make_float4(xn.x, xn.y, xn.z, __int_as_float(pn));
+    A.info[p] = info_make(cell, seg, seg, true, false);
+    ++cc.tail;
+    return kContTail;
+  }
+  if (close && !((mask >> (seg + 1)) & 1u) && !slot_moved(sv, pn) && !slot_moved(sv, __float_as_int(cv.w))) {
+    seg += 2;                                                          // next segment known valid
+    meta &= ~kContCarried;
+    return kContNext;
+  }
+  A.pa[(size_t)(seg - 1) * n + p] = make_float4(xn.x, xn.y, xn.z, __int_as_float(pn));
+  a_cur = xn;                                                          // origin of the next segment moved
+  a_orig = b;
+  a_prim = pn;
+  meta |= kContCarried | kContUpdated;
+  mask |= 1u << (16 + seg + 1);
+  ++seg;
+  return kContNext;
+}
+
+// Alg. 1 for one path, its queries run to completion one after the other.
+template <int S = kStack>
+__device__ __forceinline__ void continue_path(const SceneView& sv, int root, const ContArgs& A, uint32_t p,
+                                              ContCounters& cc, Work& wk) {
+  uint32_t cell, seg, mask, meta;
+  float3 a_orig = make_float3(0.f, 0.f, 0.f);
+  int a_prim = -1;
+  Ray r;
+  bool more = cont_begin(sv, A, p, cell, seg, mask, meta, a_orig, a_prim, r, cc);
+  for (uint32_t guard = 0; more && guard < 64; ++guard) {
+    Hit h;
+    closest_hit<S>(sv, root, r, a_prim, h, wk);
+    float3 a_cur;
+    const int o = cont_hit(sv, A, p, cell, seg, mask, meta, a_orig, a_prim, r, h.tri, h.t, a_cur, cc);
+    more = o == kContNext && cont_next(sv, A, p, cell, seg, mask, meta, a_orig, a_prim, a_cur, r, cc);
   }
 }
 
