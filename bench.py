@@ -556,8 +556,9 @@ def time_adjoint(pv, h, P, sc, N, A, K, W, stream, dev):
 # ----------------------------------------------------------------------------- batch of 16 scenes
 def run_batch(args, ws, rank, local):
     """Sixteen uneven scenes per frame: the batched, tuned, graph-replayed
-    frame against the same scenes driven one after another through the
-    single-scene calls (same frames, bit-identical results) and against
+    frame (Alg. 1 fused with the re-trace) against the same scenes driven
+    one after another through the single-scene calls (pv_update_dynamic,
+    pv_verify_retrace: same frames, bit-identical results) and against
     trace-all of every scene."""
     import torch
 
@@ -592,7 +593,9 @@ def run_batch(args, ws, rank, local):
     with torch.cuda.stream(stream):
         B = make(1)
     build_s = time.time() - t0
-    batch = pv.pv_batch_create(B, mode, tau, 0, stream)
+    # no lists asked for: Alg. 1 runs inside the batched re-trace kernel
+    batch = pv.pv_batch_create([(h, P, None, None, st, seed) for (h, P, lst, cnt, st, seed) in B], mode, tau, 0,
+                               stream)
     frame = 1
 
     def batch_frame(f):
@@ -640,16 +643,14 @@ def run_batch(args, ws, rank, local):
     for f in range(2, first):
         for sc, (h, P, lst, cnt, st, seed) in zip(scs, A):
             pv.pv_update_dynamic(h, sc.xforms(f), sc.lights(f), stream)
-            pv.pv_verify_paths(h, P, mode, tau, 0, lst, cnt, None, stream)
-            pv.pv_retrace_invalid(h, P, lst, cnt, seed, f, None, stream)
+            pv.pv_verify_retrace(h, P, mode, tau, 0, seed, f, None, stream)
     stream.synchronize()
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2.record(stream)
     for f in range(first, first + K):
         for sc, (h, P, lst, cnt, st, seed) in zip(scs, A):
             pv.pv_update_dynamic(h, sc.xforms(f), sc.lights(f), stream)
-            pv.pv_verify_paths(h, P, mode, tau, 0, lst, cnt, st, stream)
-            pv.pv_retrace_invalid(h, P, lst, cnt, seed, f, st, stream)
+            pv.pv_verify_retrace(h, P, mode, tau, 0, seed, f, st, stream)
     e3.record(stream)
     stream.synchronize()
     seq_ms = e2.elapsed_time(e3) / K
@@ -689,9 +690,9 @@ def run_batch(args, ws, rank, local):
                         "achieved": achieved / 1e12, "peak": ops_peak / 1e12, "unit": "Top/s",
                         "frac": achieved / ops_peak, "traffic": None,
                         "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x max SM clock"},
-           # graph nodes per frame: prologue, object update, leaf refit, wide refit, top level, verify,
-           # continuation, compaction, re-trace
-           "gpu_launches": 9 * K, "clocks": clocks.summary()}
+           # graph kernel nodes per frame: prologue, object update, leaf refit, wide refit, top level, verify,
+           # compaction, Alg. 1 + re-trace
+           "gpu_launches": 8 * K, "clocks": clocks.summary()}
     print(json.dumps(out), flush=True)
 
 

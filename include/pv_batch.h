@@ -40,7 +40,11 @@ typedef struct pv_batch pv_batch;
  * PV_BUILD_DYN_REBUILD (the graph replays refits); paths are its path
  * buffers (pv_paths rules), d_list [paths.n] and d_count receive the frame's
  * re-trace list (device, caller-owned), d_stats (optional, device) is
- * accumulated like the single-scene calls' counters. */
+ * accumulated like the single-scene calls' counters.  d_list and d_count
+ * NULL for every scene of a batch: no lists are returned, and Alg. 1 runs
+ * inside the persistent re-trace kernel as in pv_verify_retrace (records and
+ * counters as pv_verify_retrace leaves them, which are those of the
+ * separate calls). */
 typedef struct {
   pv_scene* scene;
   pv_paths paths;
@@ -68,7 +72,8 @@ typedef struct {
 } pv_batch_config;
 
 /* Create a batch over n (1..PV_BATCH_MAX_SCENES) scenes verified with the
- * same params; each scene must appear once.  The scenes stay owned by the
+ * same params; each scene must appear once; lists for every scene or for
+ * none (PV_ERR_ARG otherwise).  The scenes stay owned by the
  * caller and must outlive the batch; while the batch exists they are driven
  * only through pv_batch_frame.  Allocates the batch's device tables and
  * pinned staging (synchronous).  PV_ERR_ARG for bad arguments,
@@ -104,8 +109,9 @@ int pv_batch_get_config(const pv_batch* b, pv_batch_config* cfg);
 
 /* Per-frame CUDA-event times (milliseconds, mean over its tuning frames) of
  * the configuration the tuner kept: [0] pose update, [1] verify,
- * [2] continuation, [3] compaction, [4] re-trace.  PV_ERR_STATE before a
- * tuning run has finished. */
+ * [2] continuation, [3] compaction, [4] re-trace (without lists: [2] is 0
+ * and [4] holds Alg. 1 with the re-trace).  PV_ERR_STATE before a tuning run
+ * has finished. */
 int pv_batch_step_times(const pv_batch* b, float* ms5);
 
 /* Synchronise the batch's last stream and free it (the scenes remain). */

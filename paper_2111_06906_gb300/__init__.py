@@ -415,13 +415,14 @@ class Batch:
 
 
 def pv_batch_create(items, mode: int, tau: float, flags: int = 0, stream=None) -> Batch:
-    """items: sequence of (scene, Paths, d_list, d_count, d_stats or None, seed)."""
+    """items: sequence of (scene, Paths, d_list, d_count, d_stats or None, seed); d_list and d_count None
+    for every scene: no lists, Alg. 1 fused with the re-trace."""
     arr = (PvBatchScene * len(items))()
     for i, (scene, paths, d_list, d_count, d_stats, seed) in enumerate(items):
         arr[i].scene = scene.value if isinstance(scene, C.c_void_p) else scene
         arr[i].paths = paths.struct()
-        arr[i].d_list = d_list.data_ptr()
-        arr[i].d_count = d_count.data_ptr()
+        arr[i].d_list = d_list.data_ptr() if d_list is not None else None
+        arr[i].d_count = d_count.data_ptr() if d_count is not None else None
         arr[i].d_stats = d_stats.data_ptr() if d_stats is not None else None
         arr[i].seed = int(seed)
     prm = PvVerifyParams(int(mode), float(tau), int(flags), 0, 0)

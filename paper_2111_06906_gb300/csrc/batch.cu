@@ -350,6 +350,189 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, 6) k_b_trace(const BScene*
   }
 }
 
+// ---------------------------------------------------------------- Alg. 1 fused with the re-trace
+// Shared-memory layout of the fused kernel: per scene its view, both
+// argument records, root and counters; then the prefixes of the
+// continuation and re-trace counts.
+struct FusedLayout {
+  uint32_t sv, cargs, targs, root, cnt, cnt64, cpre, pre, bytes;
+  __host__ __device__ FusedLayout(uint32_t n) {
+    auto up = [](uint32_t x) { return (x + 15u) & ~15u; };
+    sv = 0;
+    cargs = up(sv + n * (uint32_t)sizeof(SceneView));
+    targs = up(cargs + n * (uint32_t)sizeof(ContArgs));
+    root = up(targs + n * (uint32_t)sizeof(TraceArgs));
+    cnt = up(root + n * 4u);
+    cnt64 = up(cnt + n * 6u * 4u);
+    cpre = up(cnt64 + n * 2u * 8u);
+    pre = up(cpre + (n + 1u) * 4u);
+    bytes = up(pre + (n + 1u) * 4u);
+  }
+};
+
+// minimum resident blocks per SM of the fused kernel (a compile-time tuning knob)
+#ifndef PV_BATCH_CT_MIN_BLOCKS
+#define PV_BATCH_CT_MIN_BLOCKS 7
+#endif
+
+// k_cont_trace of trace.cu over all scenes: the work items are every
+// scene's continuation list, then every scene's re-trace list; each lane
+// carries the scene of its current path.  Per-path arithmetic is that of
+// k_b_continue followed by k_b_trace.
+template <int kSteps, int S>
+__global__ void __launch_bounds__(pvh::kTraceThreads, PV_BATCH_CT_MIN_BLOCKS) k_b_cont_trace(const BScene* B, const BFrame* F,
+                                                                       uint32_t n_scenes, BCounters* bc) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const FusedLayout lay(n_scenes);
+  SceneView* s_sv = reinterpret_cast<SceneView*>(smem + lay.sv);
+  ContArgs* s_C = reinterpret_cast<ContArgs*>(smem + lay.cargs);
+  TraceArgs* s_T = reinterpret_cast<TraceArgs*>(smem + lay.targs);
+  int* s_root = reinterpret_cast<int*>(smem + lay.root);
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + lay.cnt);
+  unsigned long long* s_cnt64 = reinterpret_cast<unsigned long long*>(smem + lay.cnt64);
+  uint32_t* s_cpre = reinterpret_cast<uint32_t*>(smem + lay.cpre);
+  uint32_t* s_pre = reinterpret_cast<uint32_t*>(smem + lay.pre);
+  for (uint32_t s = 0; s < n_scenes; ++s) {
+    copy_words(s_sv + s, &B[s].sv, sizeof(SceneView), threadIdx.x, blockDim.x);
+    copy_words(s_C + s, &B[s].C, sizeof(ContArgs), threadIdx.x, blockDim.x);
+    copy_words(s_T + s, &B[s].T, sizeof(TraceArgs), threadIdx.x, blockDim.x);
+  }
+  for (uint32_t i = threadIdx.x; i < 6 * n_scenes; i += blockDim.x) s_cnt[i] = 0u;
+  for (uint32_t i = threadIdx.x; i < 2 * n_scenes; i += blockDim.x) s_cnt64[i] = 0ull;
+  __syncthreads();
+  if (threadIdx.x < n_scenes) {
+    s_sv[threadIdx.x].moved = F[threadIdx.x].moved;
+    s_T[threadIdx.x].frame = F[threadIdx.x].frame;
+    s_root[threadIdx.x] = *B[threadIdx.x].sv.root;
+  }
+  if (threadIdx.x == 0) {
+    s_cpre[0] = 0;
+    s_pre[0] = 0;
+    for (uint32_t s = 0; s < n_scenes; ++s) {
+      s_cpre[s + 1] = s_cpre[s] + min(*B[s].C.count, B[s].C.n);
+      s_pre[s + 1] = s_pre[s] + min(*B[s].T.count, B[s].T.n);
+    }
+  }
+  __syncthreads();
+  const uint32_t n_cont = s_cpre[n_scenes];
+  const uint32_t total = n_cont + s_pre[n_scenes];
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  Work wk;
+  PathState st;
+  Ray r;
+  Trav t;
+  int stk[S];
+  uint32_t sc = 0, c_rays = 0, c_photons = 0, cmask = 0, cmeta = 0;
+  bool has_ray = false, exhausted = false, cont = false;
+  auto flush = [&]() {                         // the finished path's counters to its scene
+    uint32_t* c = s_cnt + 6 * sc;
+    if (c_rays) atomicAdd(c + 0, c_rays);
+    if (c_photons) atomicAdd(c + 1, c_photons);
+    if (wk.nodes) atomicAdd(s_cnt64 + 2 * sc + 0, (unsigned long long)wk.nodes);
+    if (wk.tris) atomicAdd(s_cnt64 + 2 * sc + 1, (unsigned long long)wk.tris);
+    c_rays = c_photons = 0;
+    wk.nodes = wk.tris = 0;
+  };
+  auto cont_flush = [&](const ContCounters& cc) {   // Alg. 1's counters of one step, to the lane's scene
+    uint32_t* c = s_cnt + 6 * sc;
+    if (cc.rays) atomicAdd(c + 2, cc.rays);
+    if (cc.tail) atomicAdd(c + 3, cc.tail);
+    if (cc.upd) atomicAdd(c + 4, cc.upd);
+    if (cc.trunc) atomicAdd(c + 5, cc.trunc);
+  };
+  for (uint32_t guard = 0; guard < kGuard; ++guard) {
+    const bool need = !has_ray && !exhausted;
+    const unsigned nm = __ballot_sync(0xffffffffu, need);
+    if (nm) {
+      const int leader = __ffs(nm) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(&bc->trace, (uint32_t)__popc(nm));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (need) {
+        const uint32_t idx = base + __popc(nm & lt);
+        if (idx < n_cont) {
+          sc = scene_of(s_cpre, n_scenes, idx);
+          const ContArgs& C = s_C[sc];
+          st.pid = C.list[idx - s_cpre[sc]];
+          ContCounters cc;
+          const bool go = cont_begin(s_sv[sc], C, st.pid, st.cell, st.k, cmask, cmeta, st.E, st.excl, r, cc);
+          cont_flush(cc);
+          if (go) {
+            trav_begin(t, s_root[sc]);
+            has_ray = true;
+            cont = true;
+          } else {
+            flush();
+          }
+        } else if (idx < total) {
+          const uint32_t j = idx - n_cont;
+          sc = scene_of(s_pre, n_scenes, j);
+          if (init_path(s_sv[sc], F[sc].L, s_T[sc], j - s_pre[sc], st, r)) {
+            trav_begin(t, s_root[sc]);
+            has_ray = true;
+            cont = false;
+          } else {
+            flush();
+          }
+        } else {
+          exhausted = true;
+        }
+      }
+    }
+    if (__all_sync(0xffffffffu, exhausted && !has_ray)) break;
+    if (!has_ray) continue;
+    const SceneView& sv = s_sv[sc];
+    bool done = false;
+#pragma unroll 1
+    for (int i = 0; i < kSteps && !done; ++i) done = trav_step<S>(sv, r, t, stk, st.excl, wk);
+    if (!done) continue;
+    if (cont) {
+      const ContArgs& C = s_C[sc];
+      ContCounters cc;
+      float3 a_cur;
+      int o = cont_hit(sv, C, st.pid, st.cell, st.k, cmask, cmeta, st.E, st.excl, r, t.best, t.tbest, a_cur, cc);
+      if (o == kContNext && !cont_next(sv, C, st.pid, st.cell, st.k, cmask, cmeta, st.E, st.excl, a_cur, r, cc))
+        o = kContDone;
+      cont_flush(cc);
+      if (o == kContNext) {
+        trav_begin(t, s_root[sc]);
+      } else if (o == kContTail && init_pid(sv, F[sc].L, s_T[sc], st.pid, false, st, r)) {
+        cont = false;                          // Eq. 2 failed: re-trace from the failing vertex
+        trav_begin(t, s_root[sc]);
+      } else {
+        has_ray = false;
+        flush();
+      }
+      continue;
+    }
+    ++c_rays;
+    if (trace_hit(sv, s_T[sc], st, r, t, c_photons)) {
+      trav_begin(t, s_root[sc]);
+    } else {
+      has_ray = false;
+      flush();
+    }
+  }
+  __syncthreads();
+  for (uint32_t s = threadIdx.x; s < n_scenes; s += blockDim.x) {
+    pv_frame_stats* stt = s_T[s].stats;
+    if (!stt) continue;
+    const uint32_t* c = s_cnt + 6 * s;
+    if (c[0]) atomicAdd(&stt->trace_rays, c[0]);
+    if (c[1]) atomicAdd(&stt->photons_written, c[1]);
+    if (c[2]) atomicAdd(&stt->cont_rays, c[2]);
+    if (c[3]) {                                // the tails join the re-trace list
+      atomicAdd(&stt->n_tail, c[3]);
+      atomicAdd(&stt->n_listed, c[3]);
+    }
+    if (c[4]) atomicAdd(&stt->n_updated, c[4]);
+    if (c[5]) atomicAdd(&stt->n_truncated, c[5]);
+    if (s_cnt64[2 * s + 0]) atomicAdd((unsigned long long*)&stt->node_visits, s_cnt64[2 * s + 0]);
+    if (s_cnt64[2 * s + 1]) atomicAdd((unsigned long long*)&stt->tri_tests, s_cnt64[2 * s + 1]);
+  }
+}
+
 // ---------------------------------------------------------------- kernel selection
 using VerifyKernel = void (*)(const BScene*, const BFrame*, const uint32_t*);
 using ContKernel = void (*)(const BScene*, const BFrame*, uint32_t, BCounters*);
@@ -370,6 +553,12 @@ VerifyKernel verify_kernel(bool vis, bool exact, bool warp) {
 }
 
 ContKernel cont_kernel(int stack) { return stack == 32 ? k_b_continue<32> : k_b_continue<64>; }
+
+TraceKernel cont_trace_kernel(int steps, int stack) {
+  if (stack == 32)
+    return steps == 4 ? k_b_cont_trace<4, 32> : steps == 16 ? k_b_cont_trace<16, 32> : k_b_cont_trace<8, 32>;
+  return steps == 4 ? k_b_cont_trace<4, 64> : steps == 16 ? k_b_cont_trace<16, 64> : k_b_cont_trace<8, 64>;
+}
 
 TraceKernel trace_kernel(int steps, int stack) {
   if (stack == 32) return steps == 4 ? k_b_trace<4, 32> : steps == 16 ? k_b_trace<16, 32> : k_b_trace<8, 32>;
@@ -403,9 +592,11 @@ struct pv_batch {
   uint32_t n_fit = 0;
   uint32_t* d_rtab = nullptr;
   uint32_t n_refit = 0;
-  size_t smem_cont = 0, smem_trace = 0;
+  bool fused = false;                         // no lists asked for: Alg. 1 runs inside the re-trace kernel
+  size_t smem_cont = 0, smem_trace = 0, smem_ct = 0;
   int occ_cont[2] = {1, 1};                   // resident blocks per SM: [stack 32, 64]
   int occ_trace[3][2] = {{1, 1}, {1, 1}, {1, 1}};   // [steps 4, 8, 16][stack 32, 64]
+  int occ_ct[3][2] = {{1, 1}, {1, 1}, {1, 1}};      // fused kernel, same indices
   uint32_t stack_need = 0;                    // largest over the scenes
   pv_batch_config cfg{0, 256, 8, 0, 64};
   cudaGraph_t graph[2] = {};
@@ -470,6 +661,16 @@ int enqueue_frame(pv_batch* b, cudaStream_t st, bool vis, const pv_batch_config&
   verify_kernel(vis, b->exact, c.verify_mapping == 1)<<<b->n_vtiles[ti], c.verify_threads, 0, st>>>(
       b->d_scenes, b->d_frames, b->d_vtab[ti]);
   mark(2);
+  if (b->fused) {                             // compaction of what verify marked, then Alg. 1 + re-trace
+    mark(3);
+    k_b_compact<<<b->n_ctiles, pvh::kCompactThreads, 0, st>>>(b->d_scenes, b->d_ctab, b->d_ctr);
+    mark(4);
+    const TraceKernel ctk = cont_trace_kernel(c.trace_steps, c.stack);
+    ctk<<<persistent_blocks(b, b->occ_ct[steps_index(c.trace_steps)][stack_index(c.stack)], c.trace_blocks),
+          pvh::kTraceThreads, b->smem_ct, st>>>(b->d_scenes, b->d_frames, n, b->d_ctr);
+    mark(5);
+    return cuda_rc(cudaGetLastError());
+  }
   if (b->params.mode == PV_MODE_ERROR) {
     const ContKernel ck = cont_kernel(c.stack);
     ck<<<persistent_blocks(b, b->occ_cont[stack_index(c.stack)], 0), 128, b->smem_cont, st>>>(
@@ -617,9 +818,11 @@ extern "C" int pv_batch_create(const pv_batch_scene* scenes, uint32_t n, const p
   if (!scenes || !params || n == 0) return PV_ERR_ARG;
   if (n > kBatchMax) return PV_ERR_LIMIT;
   if (params->mode < PV_MODE_NAIVE_AABB || params->mode > PV_MODE_ERROR || !(params->tau >= 0.0f)) return PV_ERR_ARG;
+  const bool fused = !scenes[0].d_list;       // lists for every scene, or for none
   for (uint32_t i = 0; i < n; ++i) {
     const pv_batch_scene& it = scenes[i];
-    if (pvh::check_paths(it.scene, &it.paths) != PV_OK || !it.d_list || !it.d_count) return PV_ERR_ARG;
+    if (pvh::check_paths(it.scene, &it.paths) != PV_OK) return PV_ERR_ARG;
+    if (!it.d_list != fused || !it.d_count != fused) return PV_ERR_ARG;
     if ((it.scene->flags & PV_BUILD_DYN_REBUILD) || it.scene->has_dm) return PV_ERR_STATE;
     for (uint32_t j = 0; j < i; ++j)
       if (scenes[j].scene == it.scene) return PV_ERR_ARG;
@@ -628,6 +831,7 @@ extern "C" int pv_batch_create(const pv_batch_scene* scenes, uint32_t n, const p
   pv_batch* b = new pv_batch;
   b->items.assign(scenes, scenes + n);
   b->n = n;
+  b->fused = fused;
   b->params = *params;
   b->exact = params->mode == PV_MODE_NAIVE_EXACT ||
              (params->mode == PV_MODE_ERROR && (params->flags & PV_FLAG_ERROR_EXACT));
@@ -676,8 +880,10 @@ extern "C" int pv_batch_create(const pv_batch_scene* scenes, uint32_t n, const p
     B.T.origin = p.origin;
     B.T.pa = reinterpret_cast<float4*>(p.pa);
     B.T.pb = reinterpret_cast<float4*>(p.pb);
-    B.T.list = scenes[i].d_list;
-    B.T.count = scenes[i].d_count;
+    uint32_t* const list = fused ? s->ws_list : scenes[i].d_list;
+    uint32_t* const count = fused ? s->ws_ctr + pvh::CTR_LIST : scenes[i].d_count;
+    B.T.list = list;
+    B.T.count = count;
     B.T.ticket = nullptr;
     B.T.seed = scenes[i].seed;
     B.T.frame = 0;
@@ -705,8 +911,8 @@ extern "C" int pv_batch_create(const pv_batch_scene* scenes, uint32_t n, const p
     B.root = s->root;
     B.n_tiles = (p.n + pvh::kTile - 1) / pvh::kTile;
     B.tiles = reinterpret_cast<unsigned long long*>(s->ws_tiles);
-    B.list = scenes[i].d_list;
-    B.count = scenes[i].d_count;
+    B.list = list;
+    B.count = count;
     B.stat_listed = scenes[i].d_stats ? &scenes[i].d_stats->n_listed : nullptr;
     B.ctr = s->ws_ctr;
     for (int k = 0; k < 3; ++k)
@@ -759,6 +965,7 @@ extern "C" int pv_batch_create(const pv_batch_scene* scenes, uint32_t n, const p
   if (rc == PV_OK) {
     b->smem_cont = PersistLayout<ContArgs>(n).bytes;
     b->smem_trace = PersistLayout<TraceArgs>(n).bytes;
+    b->smem_ct = FusedLayout(n).bytes;
     for (int s : {32, 64}) {
       const void* ck = (const void*)cont_kernel(s);
       fail(cuda_rc(cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_cont)));
@@ -768,6 +975,10 @@ extern "C" int pv_batch_create(const pv_batch_scene* scenes, uint32_t n, const p
         fail(cuda_rc(cudaFuncSetAttribute(tk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_trace)));
         fail(cuda_rc(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->occ_trace[steps_index(steps)][stack_index(s)],
                                                                    tk, pvh::kTraceThreads, b->smem_trace)));
+        const void* ctk = (const void*)cont_trace_kernel(steps, s);
+        fail(cuda_rc(cudaFuncSetAttribute(ctk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_ct)));
+        fail(cuda_rc(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->occ_ct[steps_index(steps)][stack_index(s)],
+                                                                   ctk, pvh::kTraceThreads, b->smem_ct)));
       }
     }
     if (b->stack_need <= 32) b->cfg.stack = 32;

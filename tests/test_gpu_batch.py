@@ -72,22 +72,23 @@ class Lane:
         self.s1 = pv.new_stats()
         self.s2 = pv.new_stats()
 
-    def item(self):
-        return (self.h2, self.P2, self.l2, self.c2, self.s2, self.seed)
+    def item(self, lists=True):
+        return (self.h2, self.P2, self.l2 if lists else None, self.c2 if lists else None, self.s2, self.seed)
 
     def single_frame(self, f, mode, tau, flags):
         pv.pv_update_dynamic(self.h1, self.sc.xforms(f), self.sc.lights(f))
         pv.pv_verify_paths(self.h1, self.P1, mode, tau, flags, self.l1, self.c1, self.s1)
         pv.pv_retrace_invalid(self.h1, self.P1, self.l1, self.c1, self.seed, f, self.s1)
 
-    def compare(self, traversal_counters=True):
+    def compare(self, traversal_counters=True, lists=True):
         torch = _torch()
         for a, b in ((self.P1.info, self.P2.info), (self.P1.origin, self.P2.origin), (self.P1.pa, self.P2.pa),
                      (self.P1.pb, self.P2.pb)):
             assert torch.equal(a.view(torch.int32), b.view(torch.int32))
-        n1, n2 = int(self.c1.item()), int(self.c2.item())
-        assert n1 == n2
-        assert torch.equal(self.l1[:n1], self.l2[:n2])
+        if lists:
+            n1, n2 = int(self.c1.item()), int(self.c2.item())
+            assert n1 == n2
+            assert torch.equal(self.l1[:n1], self.l2[:n2])
         d1, d2 = pv.stats_dict(self.s1), pv.stats_dict(self.s2)
         if not traversal_counters:
             for k in ("node_visits", "tri_tests"):
@@ -101,13 +102,13 @@ class Lane:
             pv.pv_destroy_scene(h)
 
 
-def _run(lanes, batch, frames, mode, tau, flags, traversal_counters=True):
+def _run(lanes, batch, frames, mode, tau, flags, traversal_counters=True, lists=True):
     for f in frames:
         for ln in lanes:
             ln.single_frame(f, mode, tau, flags)
         pv.pv_batch_frame(batch, [ln.sc.xforms(f) for ln in lanes], [ln.sc.lights(f) for ln in lanes], f)
         for ln in lanes:
-            ln.compare(traversal_counters)
+            ln.compare(traversal_counters, lists)
 
 
 CONFIGS = [
@@ -140,6 +141,48 @@ def test_batch_modes_match_single_scene_calls(mode, flags, mapping):
     pv.pv_batch_set_config(b, verify_mapping=mapping)
     _run(lanes, b, range(2, 5), mode, 0.01, flags, traversal_counters=mapping == 0)
     pv.pv_batch_destroy(b)
+    for ln in lanes:
+        ln.close()
+
+
+@pytest.mark.parametrize("cfg", CONFIGS, ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()) or "default")
+def test_fused_batch_matches_single_scene_calls(cfg):
+    """Batches without lists run Alg. 1 inside the re-trace kernel; records and counters stay those of
+    the separate single-scene calls."""
+    lanes = [Lane(sc, 13 + 5 * i) for i, sc in enumerate(_mix())]
+    b = pv.pv_batch_create([ln.item(lists=False) for ln in lanes], pv.PV_MODE_ERROR, 0.01)
+    if cfg:
+        pv.pv_batch_set_config(b, **cfg)
+    _run(lanes, b, range(2, 7), pv.PV_MODE_ERROR, 0.01, 0, traversal_counters=cfg.get("verify_mapping", 0) == 0,
+         lists=False)
+    pv.pv_batch_destroy(b)
+    for ln in lanes:
+        ln.close()
+
+
+@pytest.mark.parametrize("mode,flags", [(pv.PV_MODE_NAIVE_AABB, 0), (pv.PV_MODE_ERROR, pv.PV_FLAG_ERROR_EXACT)])
+def test_fused_batch_modes_and_tuner(mode, flags):
+    lanes = [Lane(sc, 7 + i) for i, sc in enumerate(_mix()[:4])]
+    b = pv.pv_batch_create([ln.item(lists=False) for ln in lanes], mode, 0.01, flags)
+    pv.pv_batch_autotune(b, 1)
+    f = 2
+    while pv.pv_batch_tuning(b):
+        _run(lanes, b, [f], mode, 0.01, flags, traversal_counters=False, lists=False)
+        f += 1
+        assert f < 60
+    times = pv.pv_batch_step_times(b)
+    assert times[2] < 0.05 * times[4] and times[4] > 0.0          # no separate continuation kernel
+    cfg = pv.pv_batch_get_config(b)
+    _run(lanes, b, range(f, f + 3), mode, 0.01, flags, traversal_counters=cfg["verify_mapping"] == 0, lists=False)
+    pv.pv_batch_destroy(b)
+    for ln in lanes:
+        ln.close()
+
+
+def test_batch_lists_for_some_scenes_only_is_refused():
+    lanes = [Lane(sc, 3 + i) for i, sc in enumerate(_mix()[:2])]
+    with pytest.raises(pv.PvError):
+        pv.pv_batch_create([lanes[0].item(lists=True), lanes[1].item(lists=False)], pv.PV_MODE_ERROR, 0.01)
     for ln in lanes:
         ln.close()
 
