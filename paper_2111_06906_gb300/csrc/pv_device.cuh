@@ -413,19 +413,6 @@ __device__ __forceinline__ bool any_hit_all(const SceneView& sv, int root, const
   return best >= 0;
 }
 
-// Hint the cache to fetch the next traversal item (wide node, or the leaf's
-// first triangle) while the current step finishes: the line is then on its
-// way when the next step loads it.
-#ifndef PV_PREFETCH
-#define PV_PREFETCH 1
-#endif
-__device__ __forceinline__ void prefetch_ref(const WNode* nodes, const Tri* tris, int ref) {
-#if PV_PREFETCH
-  const void* p = ref >= 0 ? static_cast<const void*>(nodes + ref) : static_cast<const void*>(tris + leaf_first(ref));
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-#endif
-}
-
 // Resumable traversal state of one ray (used by the persistent kernels).
 struct Trav {
   int node, sp, best;
@@ -459,7 +446,6 @@ __device__ __forceinline__ bool trav_step(const SceneView& sv, const Ray& r, Tra
         return true;
       }
       if (next != INT32_MIN) {
-        prefetch_ref(sv.nodes, sv.tris, next);
         t.node = next;
         return false;
       }
@@ -469,7 +455,6 @@ __device__ __forceinline__ bool trav_step(const SceneView& sv, const Ray& r, Tra
   }
   if (t.sp == 0) return true;
   t.node = stk[--t.sp];
-  prefetch_ref(sv.nodes, sv.tris, t.node);
   return false;
 }
 
