@@ -4,12 +4,12 @@
 One step = one frame of the reuse pipeline on the seeded city workload
 (200k static triangles, 4 moving tori, a 1x1 m area light translating
 0.1 m/frame, 1M photon paths of up to 7 bounces, error-based mode with
-tau = 1 %):  pv_update_dynamic -> pv_verify_retrace (origin update, dynamic
-occlusions, compaction, then Alg. 1 continuation fused with the re-trace)
--> pv_deposit.  The same frames through the separate calls
-(pv_verify_paths -> pv_retrace_invalid) and the same library's trace-all
-frame (pv_update_dynamic -> pv_trace_all -> pv_deposit) are timed beside
-it.
+tau = 1 %):  pv_update_dynamic -> pv_verify_retrace_deposit (origin
+update, dynamic occlusions, compaction, then Alg. 1, the re-trace and the
+atlas deposit in one persistent kernel).  The same frames through the
+separate calls (pv_verify_paths -> pv_retrace_invalid -> pv_deposit) and the
+same library's trace-all frame (pv_update_dynamic -> pv_trace_all ->
+pv_deposit) are timed beside it.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on a bounded sample of the same workload instead.
@@ -41,9 +41,9 @@ WORKLOADS = {
     "batch16": "16 independent districts: 10k to 2M tris, 50k to 3M paths (12.4M in all), 1 to 3 lights, "
                "bounce caps 1 to 7, 1 to 4 moving tori; one batched graph-captured frame per step, tuned",
 }
-# DRAM bytes (read + write) of one k_trace launch of a timed reuse frame, from the ncu captures
-# summarised in profiles/kernels_city.md and profiles/kernels_villa.md (same kernel code)
-TRACE_TRAFFIC = {"city": 40775936 + 21240576, "villa": 118639360 + 86860544}
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one k_cont_trace launch of a timed
+# reuse frame, measured on the same kernel code
+TRACE_TRAFFIC = {"city": 52805888 + 16419072, "villa": 146542336 + 89437440}
 OPS_PER_NODE = 107    # FP32-pipe ops per wide-node visit (four slab tests + ordering network), from the source
 OPS_PER_TRI = 40      # FP32-pipe ops per Moller-Trumbore test, counted from the source
 SM_COUNT, FP32_LANES = 152, 128
@@ -219,8 +219,7 @@ def run_ours(args, ws, rank, local):
 
     def reuse_frame(f, st):
         pv.pv_update_dynamic(h, xfs[f], lts[f])
-        pv.pv_verify_retrace(h, P, mode, tau, 0, seed, f, st)
-        pv.pv_deposit(h, P, atlas, sc.atlas_rect, scale)
+        pv.pv_verify_retrace_deposit(h, P, mode, tau, 0, seed, f, atlas, sc.atlas_rect, scale, st)
 
     def timed_loop(fn, first_frame, rows_a, rows_b):
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
@@ -235,10 +234,9 @@ def run_ours(args, ws, rank, local):
         return ev
 
     def fused_body(f, st_v, st_r, e):
-        pv.pv_verify_retrace(h, P, mode, tau, 0, seed, f, st_v)
+        pv.pv_verify_retrace_deposit(h, P, mode, tau, 0, seed, f, atlas, sc.atlas_rect, scale, st_v)
         e[2].record(stream)
         e[3].record(stream)
-        pv.pv_deposit(h, P, atlas, sc.atlas_rect, scale)
 
     def separate_body(f, st_v, st_r, e):
         pv.pv_verify_paths(h, P, mode, tau, 0, lst, cnt, st_v)
@@ -369,14 +367,13 @@ def run_ours(args, ws, rank, local):
     pk, pk_kind = peaks()
     names = ["update", "verify_retrace", "-", "deposit"]
     agg = lambda key, rows: float(np.mean([r[key] for r in rows]))
-    # dominant kernel: the re-trace kernel of pv_verify_retrace (Alg. 1 fused with the re-trace in error
-    # mode), timed by the library's own events; its traversal work comes from the counted node visits and
+    # dominant kernel: the persistent kernel of pv_verify_retrace_deposit (Alg. 1, the re-trace and the atlas
+    # deposit), timed by the library's own events; its traversal work comes from the counted node visits and
     # triangle tests of the call (k_verify traverses only for moving point lights: vis_rays = 0 here)
-    fused = mode == 2
     ops = OPS_PER_NODE * agg("node_visits", st_reuse) + OPS_PER_TRI * agg("tri_tests", st_reuse)
     ops_peak = SM_COUNT * FP32_LANES * pk.get("sm_max_mhz", 2070.0) * 1e6
     achieved = ops / (float(stage_ms[2]) * 1e-3)
-    roof = {"kernel": "k_cont_trace (pv_verify_retrace)" if fused else "k_trace (pv_verify_retrace)", "bound": "alu",
+    roof = {"kernel": "k_cont_trace<deposit> (pv_verify_retrace_deposit)", "bound": "alu",
             "achieved": achieved / 1e12, "peak": ops_peak / 1e12, "unit": "Top/s", "frac": achieved / ops_peak,
             "duration_ms": float(stage_ms[2]),
             "traffic": TRACE_TRAFFIC.get(args.workload), "traffic_unit": "bytes per launch (ncu)",
@@ -389,11 +386,10 @@ def run_ours(args, ws, rank, local):
            "l2": "inputs larger than L2 (path buffers %.0f MB)" % (N * (4 + 12 + 32 * B) / 1e6),
            "reuse_ms_per_frame": reuse_ms, "trace_all_ms_per_frame": trace_ms,
            "speedup_vs_trace_all": trace_ms / reuse_ms,
-           "reuse_ms_parts": {"update": float(reuse_parts[0]), "verify_retrace": float(reuse_parts[1]),
-                              "deposit": float(reuse_parts[3])},
-           "verify_retrace_stages_ms": {"k_verify": float(stage_ms[0]), "compaction": float(stage_ms[1]),
-                                        "k_cont_trace" if fused else "k_trace": float(stage_ms[2]),
-                                        "call": float(stage_ms[3])},
+           "reuse_ms_parts": {"update": float(reuse_parts[0]), "verify_retrace_deposit": float(reuse_parts[1])},
+           "verify_retrace_deposit_stages_ms": {"k_verify": float(stage_ms[0]), "compaction": float(stage_ms[1]),
+                                                "k_cont_trace+deposit": float(stage_ms[2]),
+                                                "call": float(stage_ms[3])},
            "separate_calls": {"ms_per_frame": sep_ms,
                               "parts": dict(zip(["update", "verify", "retrace", "deposit"],
                                                 [float(x) for x in sep_parts]))},
@@ -406,8 +402,8 @@ def run_ours(args, ws, rank, local):
            "retrace_tri_tests_per_ray": agg("tri_tests", st_retrace) / max(agg("trace_rays", st_retrace), 1),
            "scene_build_s": build_s, "build_flags": args.build_flags, "device_status": [status, status2]}
     # kernels per reuse frame: pose update (k_update_objects, k_fit, k_wide_refit, k_build_top), k_verify,
-    # k_compact, k_cont_trace (k_continue + k_trace outside error mode: k_trace only), k_deposit
-    launches_per_frame = 4 + 3 + 1
+    # k_compact, k_cont_trace (Alg. 1, re-trace and deposit)
+    launches_per_frame = 4 + 3
     out = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws, "steps": K, "warmup": W,
            "ms_per_step": reuse_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roof,

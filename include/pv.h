@@ -244,10 +244,22 @@ int pv_retrace_invalid(pv_scene* s, const pv_paths* paths, const uint32_t* d_lis
 int pv_verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params* params,
                       pv_frame_stats* d_stats, void* stream);
 
-/* Stage timing of pv_verify_retrace (no paper counterpart).  With n > 0,
- * each later call records four CUDA events on its stream -- at its start,
- * after k_verify, before its re-trace kernel, at its end -- keeping the last
- * n calls in a ring; n = 0 turns it off.  Creates (and destroys) events and
+/* pv_verify_retrace followed by pv_deposit in one call (Fig. 2 from "verify
+ * paths" to "splat/gather"), leaving the same records, counters and atlas bit
+ * for bit.  Without distribution maps the deposit runs inside the persistent
+ * re-trace kernel: each path is deposited by the lane that finishes it, and
+ * the paths this frame does not touch (neither re-traced nor looked at by
+ * Alg. 1) are deposited by lanes that have no rays left to trace.  The atlas
+ * is cleared first and follows pv_deposit's rules.  Stage timing as
+ * pv_verify_retrace (stage [2] then includes the deposit).  PV_ERR_ARG for a
+ * null or invalid atlas, otherwise errors as pv_verify_paths. */
+int pv_verify_retrace_deposit(pv_scene* s, const pv_paths* paths, const pv_verify_params* params,
+                              const pv_atlas* atlas, pv_frame_stats* d_stats, void* stream);
+
+/* Stage timing of pv_verify_retrace and pv_verify_retrace_deposit (no paper
+ * counterpart).  With n > 0, each later call records four CUDA events on its
+ * stream -- at its start, after k_verify, before its re-trace kernel, at its
+ * end -- keeping the last n calls in a ring; n = 0 turns it off.  Creates (and destroys) events and
  * synchronises with the scene's last stream, so call it outside any timed or
  * captured region.  PV_ERR_ARG for n > 4096. */
 int pv_stage_timing(pv_scene* s, uint32_t n);

@@ -58,7 +58,9 @@ typedef struct {
  *  verify_mapping   0: thread per path, 1: warp per path (lanes take the
  *                   (segment, moved object) pairs of one path at a time)
  *  verify_threads   64, 128 or 256 paths per verify block (tile size)
- *  trace_steps      4, 8 or 16 traversal steps between work refills
+ *  trace_steps      16, 32 or 64: at most this many traversal steps between
+ *                   work refills; a warp refills earlier once every lane's
+ *                   ray has ended
  *  trace_blocks     persistent re-trace blocks per SM, 0 = occupancy limit
  *  stack            32 or 64 traversal stack entries for the continuation
  *                   and the re-trace; 32 only when every scene's wide tree

@@ -31,7 +31,7 @@ PV_INFO_NSEG_SHIFT, PV_INFO_START_SHIFT = 22, 26
 PV_INFO_REPLACE, PV_INFO_REUSE_LIGHT = 1 << 30, 1 << 31
 
 EXPORTS = ["pv_build_scene", "pv_update_dynamic", "pv_verify_paths", "pv_retrace_invalid", "pv_verify_retrace",
-           "pv_stage_timing", "pv_stage_times", "pv_trace_all",
+           "pv_verify_retrace_deposit", "pv_stage_timing", "pv_stage_times", "pv_trace_all",
            "pv_compact_replace", "pv_compact_replace_static", "pv_deposit", "pv_set_traversal_limit",
            "pv_read_device_status", "pv_destroy_scene", "pv_status_string", "pv_theta_size", "pv_theta_current",
            "pv_model_deposit", "pv_adjoint_deposit", "pv_budget_list", "pv_batch_create", "pv_batch_frame",
@@ -120,6 +120,8 @@ def load():
         L.pv_verify_paths.argtypes = [P, C.POINTER(PvPaths), C.POINTER(PvVerifyParams), P, P, P, P]
         L.pv_retrace_invalid.argtypes = [P, C.POINTER(PvPaths), P, P, C.c_uint64, C.c_uint32, P, P]
         L.pv_verify_retrace.argtypes = [P, C.POINTER(PvPaths), C.POINTER(PvVerifyParams), P, P]
+        L.pv_verify_retrace_deposit.argtypes = [P, C.POINTER(PvPaths), C.POINTER(PvVerifyParams), C.POINTER(PvAtlas),
+                                                P, P]
         L.pv_stage_timing.argtypes = [P, C.c_uint32]
         L.pv_stage_times.argtypes = [P, P, P]
         L.pv_trace_all.argtypes = [P, C.POINTER(PvPaths), C.c_uint64, C.c_uint32, P, P]
@@ -310,13 +312,27 @@ def pv_compact_replace_static(d_info, n: int, d_list, d_count, stream=None) -> N
                                                                           _ptr(d_count), _stream(stream)))
 
 
+def _atlas(atlas, rect, scale_log2: int) -> PvAtlas:
+    H, W = int(atlas.shape[0]), int(atlas.shape[1])
+    return PvAtlas(atlas.data_ptr(), W, H, float(rect[0]), float(rect[1]), float(rect[2]), float(rect[3]),
+                   int(scale_log2))
+
+
 def pv_deposit(scene, paths: Paths, atlas, rect, scale_log2: int, stream=None) -> None:
     """``atlas``: int64 tensor [H, W, 3] (uint64 fixed point, cleared here)."""
     ps = paths.struct()
-    H, W = int(atlas.shape[0]), int(atlas.shape[1])
-    a = PvAtlas(atlas.data_ptr(), W, H, float(rect[0]), float(rect[1]), float(rect[2]), float(rect[3]),
-                int(scale_log2))
+    a = _atlas(atlas, rect, scale_log2)
     _check("pv_deposit", load().pv_deposit(scene, C.byref(ps), C.byref(a), _stream(stream)))
+
+
+def pv_verify_retrace_deposit(scene, paths: Paths, mode: int, tau: float, flags: int, seed: int, frame: int, atlas,
+                              rect, scale_log2: int, d_stats=None, stream=None) -> None:
+    """pv_verify_retrace + pv_deposit in one call (same records, counters and atlas)."""
+    ps = paths.struct()
+    prm = PvVerifyParams(int(mode), float(tau), int(flags), int(frame), int(seed))
+    a = _atlas(atlas, rect, scale_log2)
+    _check("pv_verify_retrace_deposit", load().pv_verify_retrace_deposit(scene, C.byref(ps), C.byref(prm), C.byref(a),
+                                                                          _ptr(d_stats), _stream(stream)))
 
 
 def _rect(rect):

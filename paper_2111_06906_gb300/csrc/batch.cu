@@ -324,13 +324,10 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, 6) k_b_trace(const BScene*
       }
     }
     if (__all_sync(0xffffffffu, exhausted && !has_ray)) break;
-    if (!has_ray) continue;
     const SceneView& sv = s_sv[sc];
     const TraceArgs& A = s_T[sc];
-    bool done = false;
-#pragma unroll 1
-    for (int i = 0; i < kSteps && !done; ++i) done = trav_step<S>(sv, r, t, stk, st.excl, wk);
-    if (!done) continue;
+    const bool done = step_warp<kSteps, S>(sv, r, t, stk, st.excl, wk, !has_ray);
+    if (!has_ray || !done) continue;
     ++c_rays;
     if (trace_hit(sv, A, st, r, t, c_photons)) {
       trav_begin(t, s_root[sc]);
@@ -481,12 +478,9 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_BATCH_CT_MIN_BLOCKS) k_
       }
     }
     if (__all_sync(0xffffffffu, exhausted && !has_ray)) break;
-    if (!has_ray) continue;
     const SceneView& sv = s_sv[sc];
-    bool done = false;
-#pragma unroll 1
-    for (int i = 0; i < kSteps && !done; ++i) done = trav_step<S>(sv, r, t, stk, st.excl, wk);
-    if (!done) continue;
+    const bool done = step_warp<kSteps, S>(sv, r, t, stk, st.excl, wk, !has_ray);
+    if (!has_ray || !done) continue;
     if (cont) {
       const ContArgs& C = s_C[sc];
       ContCounters cc;
@@ -556,13 +550,13 @@ ContKernel cont_kernel(int stack) { return stack == 32 ? k_b_continue<32> : k_b_
 
 TraceKernel cont_trace_kernel(int steps, int stack) {
   if (stack == 32)
-    return steps == 4 ? k_b_cont_trace<4, 32> : steps == 16 ? k_b_cont_trace<16, 32> : k_b_cont_trace<8, 32>;
-  return steps == 4 ? k_b_cont_trace<4, 64> : steps == 16 ? k_b_cont_trace<16, 64> : k_b_cont_trace<8, 64>;
+    return steps == 16 ? k_b_cont_trace<16, 32> : steps == 32 ? k_b_cont_trace<32, 32> : k_b_cont_trace<64, 32>;
+  return steps == 16 ? k_b_cont_trace<16, 64> : steps == 32 ? k_b_cont_trace<32, 64> : k_b_cont_trace<64, 64>;
 }
 
 TraceKernel trace_kernel(int steps, int stack) {
-  if (stack == 32) return steps == 4 ? k_b_trace<4, 32> : steps == 16 ? k_b_trace<16, 32> : k_b_trace<8, 32>;
-  return steps == 4 ? k_b_trace<4, 64> : steps == 16 ? k_b_trace<16, 64> : k_b_trace<8, 64>;
+  if (stack == 32) return steps == 16 ? k_b_trace<16, 32> : steps == 32 ? k_b_trace<32, 32> : k_b_trace<64, 32>;
+  return steps == 16 ? k_b_trace<16, 64> : steps == 32 ? k_b_trace<32, 64> : k_b_trace<64, 64>;
 }
 
 int thread_index(int threads) { return threads == 64 ? 0 : threads == 128 ? 1 : 2; }
@@ -595,10 +589,10 @@ struct pv_batch {
   bool fused = false;                         // no lists asked for: Alg. 1 runs inside the re-trace kernel
   size_t smem_cont = 0, smem_trace = 0, smem_ct = 0;
   int occ_cont[2] = {1, 1};                   // resident blocks per SM: [stack 32, 64]
-  int occ_trace[3][2] = {{1, 1}, {1, 1}, {1, 1}};   // [steps 4, 8, 16][stack 32, 64]
+  int occ_trace[3][2] = {{1, 1}, {1, 1}, {1, 1}};   // [steps 16, 32, 64][stack 32, 64]
   int occ_ct[3][2] = {{1, 1}, {1, 1}, {1, 1}};      // fused kernel, same indices
   uint32_t stack_need = 0;                    // largest over the scenes
-  pv_batch_config cfg{0, 256, 8, 0, 64};
+  pv_batch_config cfg{0, 256, 64, 0, 64};
   cudaGraph_t graph[2] = {};
   cudaGraphExec_t exec[2] = {};
   cudaGraphNode_t copy_node[2] = {};
@@ -622,7 +616,7 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? PV_OK : PV_ERR_CUDA; }
 bool config_valid(const pv_batch* b, const pv_batch_config& c) {
   if (c.verify_mapping != 0 && c.verify_mapping != 1) return false;
   if (c.verify_threads != 64 && c.verify_threads != 128 && c.verify_threads != 256) return false;
-  if (c.trace_steps != 4 && c.trace_steps != 8 && c.trace_steps != 16) return false;
+  if (c.trace_steps != 16 && c.trace_steps != 32 && c.trace_steps != 64) return false;
   if (c.trace_blocks < 0 || c.trace_blocks > 16) return false;
   if (c.stack != 32 && c.stack != 64) return false;
   if ((uint32_t)c.stack < b->stack_need) return false;
@@ -630,7 +624,7 @@ bool config_valid(const pv_batch* b, const pv_batch_config& c) {
 }
 
 int stack_index(int stack) { return stack == 32 ? 0 : 1; }
-int steps_index(int steps) { return steps == 4 ? 0 : steps == 16 ? 2 : 1; }
+int steps_index(int steps) { return steps == 16 ? 0 : steps == 32 ? 1 : 2; }
 
 // Persistent grid: resident blocks per SM (occupancy measured at creation,
 // optionally fewer) times the SM count.
@@ -735,7 +729,7 @@ std::vector<pv_batch_config> phase_candidates(const pv_batch* b, uint32_t phase)
   const pv_batch_config base = b->cfg;
   if (phase == 0) {                           // re-trace and continuation: steps, blocks per SM, stack
     for (int stack : {32, 64})
-      for (int steps : {4, 8, 16})
+      for (int steps : {16, 32, 64})
         for (int blocks : {0, 4}) {
           pv_batch_config c = base;
           c.stack = stack;
@@ -970,7 +964,7 @@ extern "C" int pv_batch_create(const pv_batch_scene* scenes, uint32_t n, const p
       const void* ck = (const void*)cont_kernel(s);
       fail(cuda_rc(cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_cont)));
       fail(cuda_rc(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->occ_cont[stack_index(s)], ck, 128, b->smem_cont)));
-      for (int steps : {4, 8, 16}) {
+      for (int steps : {16, 32, 64}) {
         const void* tk = (const void*)trace_kernel(steps, s);
         fail(cuda_rc(cudaFuncSetAttribute(tk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_trace)));
         fail(cuda_rc(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->occ_trace[steps_index(steps)][stack_index(s)],

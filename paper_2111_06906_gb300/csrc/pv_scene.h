@@ -71,6 +71,7 @@ struct pv_scene {
   uint32_t* ws_mask = nullptr;       // [n_paths] intersected-segment masks (error mode)
   uint32_t* ws_cont = nullptr;       // [n_paths] continuation list
   uint32_t* ws_list = nullptr;       // [n_paths] re-trace list of pv_verify_retrace
+  uint8_t* ws_touched = nullptr;     // [n_paths] paths the frame re-traces or hands to Alg. 1 (fused deposit)
   uint64_t* ws_tiles = nullptr;      // [n_tiles + 1] decoupled look-back tile states
   uint32_t n_tiles = 0;
   uint32_t* ws_ctr = nullptr;        // [16] work counters
@@ -89,7 +90,7 @@ struct pv_scene {
   int* status = nullptr;             // sticky device status
   cudaStream_t last_stream = nullptr;
 
-  int verify_blocks = 0, trace_blocks = 0, cont_blocks = 0, cont_trace_blocks = 0;
+  int verify_blocks = 0, trace_blocks = 0, cont_blocks = 0, cont_trace_blocks = 0, cont_trace_dep_blocks = 0;
   // stage timing of pv_verify_retrace: a ring of stage_n calls, four events each
   std::vector<cudaEvent_t> stage_ev;
   uint32_t stage_n = 0, stage_next = 0, stage_count = 0;
@@ -145,9 +146,14 @@ void launch_compact(pv_scene* s, const uint32_t* info, uint32_t n, uint32_t* lis
 // trace.cu
 void launch_trace(pv_scene* s, const pv_paths* p, const uint32_t* list, const uint32_t* count, uint64_t seed,
                   uint32_t frame, pv_frame_stats* stats, cudaStream_t st);
-// Alg. 1 over the continuation list C fused with the re-trace of ``list``
+// Alg. 1 over the continuation list C fused with the re-trace of ``list``;
+// with an atlas, every path is also deposited (touched: verification's marks)
 void launch_cont_trace(pv_scene* s, const pv_paths* p, const pvk::ContArgs& C, const uint32_t* list,
-                       const uint32_t* count, uint64_t seed, uint32_t frame, pv_frame_stats* stats, cudaStream_t st);
+                       const uint32_t* count, uint64_t seed, uint32_t frame, pv_frame_stats* stats,
+                       const pv_atlas* atlas, const uint8_t* touched, cudaStream_t st);
+// deposit.cu: argument checks of an atlas, and the plain deposit of every path
+int check_atlas(const pv_atlas* a);
+void launch_deposit(pv_scene* s, const pv_paths* p, const pv_atlas* a, cudaStream_t st);
 
 // verify.cu: argument checks shared by the entry points
 int check_paths(const pv_scene* s, const pv_paths* p);

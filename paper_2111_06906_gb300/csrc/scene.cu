@@ -52,7 +52,7 @@ void free_scene(pv_scene* s) {
   void* ptrs[] = {s->nodes, s->wnodes, s->wsrc, s->wcount, s->cq, s->tris, s->root, s->d_local, s->d_tri_prim, s->d_leaf_parent, s->d_node_parent,
                   s->d_fit_flags, s->d_tri_slot, s->objs, s->r_keys[0], s->r_keys[1], s->r_vals[0], s->r_vals[1],
                   s->r_hist, s->r_tris, s->r_local, s->r_prim, s->prim_slot, s->prim_dyn, s->prim_alb, s->prim_nrm,
-                  s->xf_old, s->xf_new, s->ws_mask, s->ws_cont, s->ws_list, s->ws_tiles, s->ws_ctr, s->status, s->b_keys[0], s->b_keys[1],
+                  s->xf_old, s->xf_new, s->ws_mask, s->ws_cont, s->ws_list, s->ws_touched, s->ws_tiles, s->ws_ctr, s->status, s->b_keys[0], s->b_keys[1],
                   s->b_vals[0], s->b_vals[1], s->b_hist, s->dm_c[0], s->dm_c[1], s->dm_c[2], s->dm_c[3],
                   s->dm_flag, s->dm_free, s->dm_scan, s->dm_ctr};
   for (void* p : ptrs)
@@ -229,6 +229,7 @@ extern "C" int pv_build_scene(const pv_scene_desc* d, void* stream, pv_scene** o
   fail(cudaMalloc(&s->ws_mask, (size_t)s->n_paths_total * sizeof(uint32_t)));
   fail(cudaMalloc(&s->ws_cont, (size_t)s->n_paths_total * sizeof(uint32_t)));
   fail(cudaMalloc(&s->ws_list, (size_t)s->n_paths_total * sizeof(uint32_t)));
+  fail(cudaMalloc(&s->ws_touched, (size_t)s->n_paths_total));
   fail(cudaMalloc(&s->ws_tiles, (size_t)(s->n_tiles + 1) * sizeof(uint64_t)));
   for (uint32_t l = 0; l < PV_MAX_LIGHTS; ++l)
     if (s->dm_cells[l]) {

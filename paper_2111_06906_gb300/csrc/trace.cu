@@ -1,15 +1,18 @@
 // Persistent re-trace of the listed paths (and the trace-all baseline).
 //
 // "Generate rays" and "trace rays" of Fig. 2 fused into one kernel.  Each
-// lane owns one path and one ray at a time and advances its traversal a few
-// steps per loop iteration; as soon as a lane's ray is done it stores the
-// photon and starts its next ray (the next bounce, or the next list entry,
-// taken with one atomic per warp), so lanes never wait for the slowest ray
-// of the warp.  Rays are generated where the paper generates them (Sec. 4):
+// lane owns one path and one ray at a time.  A warp advances its lanes'
+// traversals step by step until every lane's ray has ended, or for at most a
+// fixed number of steps; then each lane whose ray ended stores the photon and
+// starts its next ray (the next bounce, or the next list entry, taken with
+// one atomic per warp), so a long ray holds its warp's other lanes only that
+// many steps.  Rays are generated where the paper generates them (Sec. 4):
 // from the light (start 0), or by Russian roulette and a cosine-weighted
 // bounce at the first photon to re-trace.
 #include <cstdlib>
+#include <cstring>
 
+#include "deposit_core.cuh"
 #include "trace_core.cuh"
 #include "verify_core.cuh"
 
@@ -17,14 +20,49 @@ using namespace pvk;
 
 namespace {
 
-// compile-time tuning: traversal steps between refills, minimum resident blocks
+// Compile-time tuning: minimum resident blocks; traversal steps between
+// refills.  A warp keeps stepping until every lane's ray has ended (at most
+// PV_TRACE_MAX_STEPS steps), so that the ray-end code (photon store, bounce
+// sampling, next list entry) runs with all lanes at once: measured on the
+// city and villa workloads this beats refilling each lane after a fixed
+// number of steps (8) by 8-13 % on the re-trace and 14-15 % on trace-all.
+// PV_TRACE_DONE_LANES < 32 stops once that many lanes are done (after at
+// least PV_TRACE_STEPS steps); PV_TRACE_DONE_LANES > 32 restores the fixed
+// PV_TRACE_STEPS-step loop.
 #ifndef PV_TRACE_STEPS
-#define PV_TRACE_STEPS 8
+#define PV_TRACE_STEPS 16
 #endif
 #ifndef PV_TRACE_MIN_BLOCKS
 #define PV_TRACE_MIN_BLOCKS 7
 #endif
+#ifndef PV_TRACE_MAX_STEPS
+#define PV_TRACE_MAX_STEPS 64
+#endif
+#ifndef PV_TRACE_DONE_LANES
+#define PV_TRACE_DONE_LANES 32
+#endif
 constexpr int kStepsPerIter = PV_TRACE_STEPS;
+constexpr int kMaxSteps = PV_TRACE_MAX_STEPS;
+constexpr int kDoneLanes = PV_TRACE_DONE_LANES;
+
+// Advance the lane's ray; all lanes of the warp call it (lanes without a ray
+// pass done = true).  Returns whether the lane's ray has ended.
+__device__ __forceinline__ bool step_rays(const SceneView& sv, const Ray& r, Trav& t, int* stk, int excl, Work& wk,
+                                          bool done) {
+  if (kDoneLanes > 32) {
+#pragma unroll 1
+    for (int i = 0; i < kStepsPerIter && !done; ++i) done = trav_step(sv, r, t, stk, excl, wk);
+    return done;
+  }
+#pragma unroll 1
+  for (int i = 0; i < kMaxSteps; ++i) {
+    if (!done) done = trav_step(sv, r, t, stk, excl, wk);
+    const unsigned dm = __ballot_sync(0xffffffffu, done);
+    if (dm == 0xffffffffu) break;
+    if (i + 1 >= kStepsPerIter && __popc(dm) >= kDoneLanes) break;
+  }
+  return done;
+}
 
 __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS) k_trace(SceneView sv, FrameLights L, TraceArgs A) {
   __shared__ uint32_t s_red[32 * 2];
@@ -61,11 +99,9 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS) k_tra
       }
     }
     if (__all_sync(0xffffffffu, exhausted && !has_ray)) break;
-    if (!has_ray) continue;
-    bool done = false;
-#pragma unroll 1
-    for (int i = 0; i < kStepsPerIter && !done; ++i) done = trav_step(sv, r, t, stk, s.excl, wk);
-    if (!done) continue;
+    if (kDoneLanes > 32 && !has_ray) continue;
+    const bool done = step_rays(sv, r, t, stk, s.excl, wk, !has_ray);
+    if (!has_ray || !done) continue;
     ++c_rays;
     if (trace_hit(sv, A, s, r, t, c_photons)) trav_begin(t, root);
     else has_ray = false;
@@ -87,6 +123,18 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS) k_tra
 // from the failing vertex in the same lane.  Every path sees the same
 // arithmetic as in k_continue followed by k_trace, so the records are
 // identical; only the order in which paths are processed differs.
+//
+// kDeposit: the atlas deposit joins the kernel.  A lane deposits each path it
+// finishes as soon as it is final; after the re-trace items come the paths
+// verification left untouched (touched[p] == 0), whose deposit fills the
+// lanes that have no more rays to trace.  Every path is deposited once, by
+// the same per-photon arithmetic as k_deposit, into integer sums: the atlas
+// is the same bit for bit.
+struct DepositArgs {
+  pv_atlas at;
+  const uint8_t* touched;
+};
+
 __device__ __forceinline__ void cont_flush(ContCounters& cc, uint32_t* s_cnt) {
   if (cc.rays) atomicAdd(s_cnt + 0, cc.rays);
   if (cc.tail) atomicAdd(s_cnt + 1, cc.tail);
@@ -94,8 +142,9 @@ __device__ __forceinline__ void cont_flush(ContCounters& cc, uint32_t* s_cnt) {
   if (cc.trunc) atomicAdd(s_cnt + 3, cc.trunc);
 }
 
+template <bool kDeposit>
 __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS)
-    k_cont_trace(SceneView sv, FrameLights L, TraceArgs A, ContArgs C) {
+    k_cont_trace(SceneView sv, FrameLights L, TraceArgs A, ContArgs C, DepositArgs D) {
   __shared__ uint32_t s_red[32 * 2];
   __shared__ unsigned long long s_red64[32];
   __shared__ uint32_t s_cnt[4];
@@ -103,8 +152,13 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS)
   __syncthreads();
   const int root = *sv.root;
   const uint32_t n_cont = min(*C.count, C.n);
-  const uint32_t total = n_cont + min(*A.count, A.n);
+  const uint32_t n_trace = n_cont + min(*A.count, A.n);
+  const uint32_t total = n_trace + (kDeposit ? A.n : 0u);
   const int lane = threadIdx.x & 31;
+  uint32_t dep = 0xFFFFFFFFu;                // a final path this lane still has to deposit
+  auto deposit = [&](uint32_t p) {
+    if (kDeposit) dep = p;
+  };
   const unsigned lt = (1u << lane) - 1u;
   Work wk;
   PathState s;
@@ -115,6 +169,10 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS)
   bool has_ray = false, exhausted = false, cont = false;
   uint32_t c_rays = 0, c_photons = 0;
   for (uint32_t guard = 0; guard < (1u << 30); ++guard) {
+    if (kDeposit && dep != 0xFFFFFFFFu) {
+      deposit_path(D.at, A.n, sv.B, A.info, A.pa, A.pb, dep);
+      dep = 0xFFFFFFFFu;
+    }
     const bool need = !has_ray && !exhausted;
     const unsigned nm = __ballot_sync(0xffffffffu, need);
     if (nm) {
@@ -131,25 +189,30 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS)
             trav_begin(t, root);
             has_ray = true;
             cont = true;
+          } else {
+            deposit(s.pid);
           }
           cont_flush(cc, s_cnt);
-        } else if (idx < total) {
+        } else if (idx < n_trace) {
           if (init_path(sv, L, A, idx - n_cont, s, r)) {
             trav_begin(t, root);
             has_ray = true;
             cont = false;
+          } else {
+            deposit(s.pid);
           }
+        } else if (idx < total) {                // deposit of a path this frame left untouched
+          const uint32_t p = idx - n_trace;
+          if (!D.touched[p]) deposit(p);
         } else {
           exhausted = true;
         }
       }
     }
-    if (__all_sync(0xffffffffu, exhausted && !has_ray)) break;
-    if (!has_ray) continue;
-    bool done = false;
-#pragma unroll 1
-    for (int i = 0; i < kStepsPerIter && !done; ++i) done = trav_step(sv, r, t, stk, s.excl, wk);
-    if (!done) continue;
+    if (__all_sync(0xffffffffu, exhausted && !has_ray && dep == 0xFFFFFFFFu)) break;
+    if (kDoneLanes > 32 && !has_ray) continue;
+    const bool done = step_rays(sv, r, t, stk, s.excl, wk, !has_ray);
+    if (!has_ray || !done) continue;
     if (cont) {
       ContCounters cc;
       float3 a_cur;
@@ -164,12 +227,17 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS)
         trav_begin(t, root);
       } else {
         has_ray = false;
+        deposit(s.pid);
       }
       continue;
     }
     ++c_rays;
-    if (trace_hit(sv, A, s, r, t, c_photons)) trav_begin(t, root);
-    else has_ray = false;
+    if (trace_hit(sv, A, s, r, t, c_photons)) {
+      trav_begin(t, root);
+    } else {
+      has_ray = false;
+      deposit(s.pid);
+    }
   }
   uint32_t* const ctr[2] = {A.stats ? &A.stats->trace_rays : nullptr, A.stats ? &A.stats->photons_written : nullptr};
   const uint32_t val[2] = {c_rays, c_photons};
@@ -234,11 +302,22 @@ void launch_trace(pv_scene* s, const pv_paths* p, const uint32_t* list, const ui
 }
 
 void launch_cont_trace(pv_scene* s, const pv_paths* p, const ContArgs& C, const uint32_t* list, const uint32_t* count,
-                       uint64_t seed, uint32_t frame, pv_frame_stats* stats, cudaStream_t st) {
-  if (!s->cont_trace_blocks) s->cont_trace_blocks = persistent_blocks(s, k_cont_trace);
+                       uint64_t seed, uint32_t frame, pv_frame_stats* stats, const pv_atlas* atlas,
+                       const uint8_t* touched, cudaStream_t st) {
   const TraceArgs A = trace_args(s, p, list, count, seed, frame, stats);
   cudaMemsetAsync(A.ticket, 0, sizeof(uint32_t), st);
-  if (p->n) k_cont_trace<<<s->cont_trace_blocks, kTraceThreads, 0, st>>>(view(s), frame_lights(s), A, C);
+  if (!p->n) return;
+  DepositArgs D;
+  std::memset(&D, 0, sizeof D);
+  if (atlas) {
+    if (!s->cont_trace_dep_blocks) s->cont_trace_dep_blocks = persistent_blocks(s, k_cont_trace<true>);
+    D.at = *atlas;
+    D.touched = touched;
+    k_cont_trace<true><<<s->cont_trace_dep_blocks, kTraceThreads, 0, st>>>(view(s), frame_lights(s), A, C, D);
+  } else {
+    if (!s->cont_trace_blocks) s->cont_trace_blocks = persistent_blocks(s, k_cont_trace<false>);
+    k_cont_trace<false><<<s->cont_trace_blocks, kTraceThreads, 0, st>>>(view(s), frame_lights(s), A, C, D);
+  }
 }
 
 }  // namespace pvh

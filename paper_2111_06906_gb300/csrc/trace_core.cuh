@@ -143,4 +143,19 @@ __device__ __forceinline__ bool trace_hit(const SceneView& sv, const TraceArgs& 
   return true;
 }
 
+// Advance every lane's ray until all rays of the warp have ended, or for at
+// most kMax steps; called by all lanes of the warp (a lane without a ray
+// passes done = true).  Returns whether this lane's ray has ended.  Waiting
+// for the whole warp lets the ray-end code that follows run with all lanes.
+template <int kMax, int S = kStack>
+__device__ __forceinline__ bool step_warp(const SceneView& sv, const Ray& r, Trav& t, int* stk, int excl, Work& wk,
+                                          bool done) {
+#pragma unroll 1
+  for (int i = 0; i < kMax; ++i) {
+    if (!done) done = trav_step<S>(sv, r, t, stk, excl, wk);
+    if (__all_sync(0xffffffffu, done)) break;
+  }
+  return done;
+}
+
 }  // namespace pvk

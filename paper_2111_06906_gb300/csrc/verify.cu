@@ -85,7 +85,7 @@ ContArgs cont_args(pv_scene* s, const pv_paths* paths, const pv_verify_params* p
 // Work counters reset, DM_C of moved lights with a map cleared, then k_verify
 // (Sec. 3.1 + 3.2).  ``cont``: Alg. 1 has paths to look at this frame.
 int launch_verify(pv_scene* s, const pv_paths* paths, const pv_verify_params* params, pv_frame_stats* d_stats,
-                  const SceneView& sv, const FrameLights& L, cudaStream_t st, bool& cont) {
+                  const SceneView& sv, const FrameLights& L, cudaStream_t st, bool& cont, uint8_t* touched = nullptr) {
   const uint32_t n = paths->n;
   if (cudaMemsetAsync(s->ws_ctr, 0, 16 * sizeof(uint32_t), st) != cudaSuccess) return PV_ERR_CUDA;
   for (uint32_t l = 0; l < s->n_lights; ++l)       // DM_C of moved lights with a map is counted afresh
@@ -105,6 +105,7 @@ int launch_verify(pv_scene* s, const pv_paths* paths, const pv_verify_params* pa
   A.cont_list = s->ws_cont;
   A.cont_count = s->ws_ctr + pvh::CTR_ALL;
   A.stats = d_stats;
+  A.touched = touched;
   if (n) {
     bool point_vis = false;
     for (uint32_t l = 0; l < s->n_lights; ++l)
@@ -149,11 +150,14 @@ extern "C" int pv_verify_paths(pv_scene* s, const pv_paths* paths, const pv_veri
   return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
 }
 
-extern "C" int pv_verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params* params,
-                                 pv_frame_stats* d_stats, void* stream) {
+namespace {
+
+// pv_verify_retrace, and with an atlas pv_verify_retrace_deposit.
+int verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params* params, const pv_atlas* atlas,
+                   pv_frame_stats* d_stats, cudaStream_t st) {
   int rc = check_verify(s, paths, params);
   if (rc != PV_OK) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
+  if (atlas && (rc = pvh::check_atlas(atlas)) != PV_OK) return rc;
   s->last_stream = st;
   const SceneView sv = pvh::view(s);
   const FrameLights L = pvh::frame_lights(s);
@@ -162,25 +166,33 @@ extern "C" int pv_verify_retrace(pv_scene* s, const pv_paths* paths, const pv_ve
     if (ev) cudaEventRecord(ev[k], st);
   };
   mark(0);
+  if (atlas && cudaMemsetAsync(atlas->data, 0, (size_t)atlas->width * atlas->height * 3 * sizeof(uint64_t), st) !=
+                   cudaSuccess)
+    return PV_ERR_CUDA;
+  // with maps, prune and fill need Alg. 1's final answer for every path before the list is made
+  const bool fuse_deposit = atlas && !s->has_dm;
   bool cont = false;
-  if ((rc = launch_verify(s, paths, params, d_stats, sv, L, st, cont)) != PV_OK) return rc;
+  if ((rc = launch_verify(s, paths, params, d_stats, sv, L, st, cont, fuse_deposit ? s->ws_touched : nullptr)) !=
+      PV_OK)
+    return rc;
   mark(1);
   const ContArgs C = cont_args(s, paths, params, d_stats);
   uint32_t* const list = s->ws_list;
   uint32_t* const count = s->ws_ctr + pvh::CTR_LIST;
   uint32_t* const listed = d_stats ? &d_stats->n_listed : nullptr;
-  if (cont && !s->has_dm) {
-    // the paths k_verify marked, then Alg. 1 and the re-trace in one persistent kernel
+  if ((cont || fuse_deposit) && !s->has_dm) {
+    // the paths k_verify marked, then Alg. 1, the re-trace (and the deposit) in one persistent kernel
     pvh::launch_compact(s, paths->info, paths->n, list, count, listed, st);
     mark(2);
-    pvh::launch_cont_trace(s, paths, C, list, count, params->seed, params->frame, d_stats, st);
+    pvh::launch_cont_trace(s, paths, C, list, count, params->seed, params->frame, d_stats,
+                           fuse_deposit ? atlas : nullptr, s->ws_touched, st);
   } else {
-    // distribution maps prune and fill after Alg. 1 and before the list is final
     if (cont) launch_continue(s, sv, C, st);
     if (s->has_dm && (rc = pvh::dm_frame(s, paths, L, params, d_stats, st)) != PV_OK) return rc;
     pvh::launch_compact(s, paths->info, paths->n, list, count, listed, st);
     mark(2);
     pvh::launch_trace(s, paths, list, count, params->seed, params->frame, d_stats, st);
+    if (atlas) pvh::launch_deposit(s, paths, atlas, st);
   }
   mark(3);
   if (ev) {
@@ -188,6 +200,19 @@ extern "C" int pv_verify_retrace(pv_scene* s, const pv_paths* paths, const pv_ve
     s->stage_count = std::min(s->stage_count + 1, s->stage_n);
   }
   return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" int pv_verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params* params,
+                                 pv_frame_stats* d_stats, void* stream) {
+  return verify_retrace(s, paths, params, nullptr, d_stats, (cudaStream_t)stream);
+}
+
+extern "C" int pv_verify_retrace_deposit(pv_scene* s, const pv_paths* paths, const pv_verify_params* params,
+                                         const pv_atlas* atlas, pv_frame_stats* d_stats, void* stream) {
+  if (!atlas) return PV_ERR_ARG;
+  return verify_retrace(s, paths, params, atlas, d_stats, (cudaStream_t)stream);
 }
 
 extern "C" int pv_stage_timing(pv_scene* s, uint32_t n) {

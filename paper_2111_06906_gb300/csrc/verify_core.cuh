@@ -25,6 +25,7 @@ struct VerifyArgs {
   uint32_t* cont_list;
   uint32_t* cont_count;
   pv_frame_stats* stats;
+  uint8_t* touched;            // optional [n]: 1 for a path this frame re-traces or hands to Alg. 1, else 0
 };
 
 // Closed segment a + s (b - a), s in [0,1], against a closed box: slab test
@@ -141,6 +142,7 @@ struct PathCheck {
   uint32_t nseg, cell;
   bool test;                   // the segment stage must run
   bool blocked1;               // a moved point light's visibility ray is blocked
+  bool replaced;               // marked for a fresh emission by the origin stage
 };
 
 // Sec. 3.1 "update path origins" for path p (< A.n): the moved light's
@@ -157,6 +159,7 @@ __device__ __forceinline__ PathCheck origin_stage(const SceneView& sv, const Fra
   const uint32_t l = info_light(w);
   v.o = make_float3(A.origin[p], A.origin[n + p], A.origin[2 * (size_t)n + p]);
   v.blocked1 = false;
+  v.replaced = false;
   bool invalid = false;
   if ((L.moved_mask >> l) & 1u) {
     const DmLight& D = L.dm[l];
@@ -216,6 +219,7 @@ __device__ __forceinline__ PathCheck origin_stage(const SceneView& sv, const Fra
     }
     if (invalid) {
       A.info[p] = info_make(v.cell, 0, 0, true, false);
+      v.replaced = true;
       ++c_reemit;
     } else if (dm_cell >= 0) {
       atomicAdd(D.dmc + dm_cell, 1u);
@@ -316,7 +320,7 @@ __device__ __forceinline__ void verify_block(const SceneView& sv, const FrameLig
   const uint32_t n = A.n;
   const bool test_old = kExact && (A.flags & PV_FLAG_TEST_OLD_TRIS) != 0;
   uint32_t c_tested = 0, c_vis = 0, c_reemit = 0, c_tail = 0;
-  bool want_cont = false;
+  bool want_cont = false, touched = false;
   if (p < n) {
     const PathCheck v = origin_stage<kPointVis, S>(sv, L, A, root, p, c_vis, c_reemit, wk);
     if (v.test) {
@@ -342,7 +346,9 @@ __device__ __forceinline__ void verify_block(const SceneView& sv, const FrameLig
         prim_a = prim_b;
       }
       want_cont = finish_stage(A, p, v, mask, c_reemit, c_tail);
+      touched = mask != 0;                   // handed to Alg. 1, or (naive modes) marked for re-tracing
     }
+    if (A.touched) A.touched[p] = (touched || v.replaced) ? 1 : 0;
   }
   verify_epilogue(A, p, want_cont, c_tested, c_vis, c_reemit, c_tail, wk, kPointVis || kExact, sm);
 }
@@ -370,6 +376,7 @@ __device__ __forceinline__ void verify_block_warp(const SceneView& sv, const Fra
   v.nseg = 0;
   v.o = make_float3(0.f, 0.f, 0.f);
   v.blocked1 = false;
+  v.replaced = false;
   v.cell = 0;
   if (p < n) v = origin_stage<kPointVis, S>(sv, L, A, root, p, c_vis, c_reemit, wk);
   uint32_t my_mask = 0;
@@ -420,6 +427,7 @@ __device__ __forceinline__ void verify_block_warp(const SceneView& sv, const Fra
   }
   bool want_cont = false;
   if (p < n && v.test) want_cont = finish_stage(A, p, v, my_mask, c_reemit, c_tail);
+  if (p < n && A.touched) A.touched[p] = ((v.test && my_mask != 0) || v.replaced) ? 1 : 0;
   verify_epilogue(A, p, want_cont, c_tested, c_vis, c_reemit, c_tail, wk, kPointVis || kExact, sm);
 }
 

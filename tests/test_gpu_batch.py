@@ -114,8 +114,8 @@ def _run(lanes, batch, frames, mode, tau, flags, traversal_counters=True, lists=
 CONFIGS = [
     {},
     {"verify_mapping": 1},
-    {"verify_threads": 64, "trace_steps": 4},
-    {"verify_threads": 128, "trace_steps": 16, "trace_blocks": 2},
+    {"verify_threads": 64, "trace_steps": 16},
+    {"verify_threads": 128, "trace_steps": 32, "trace_blocks": 2},
     {"stack": 64},
 ]
 
@@ -202,7 +202,7 @@ def test_batch_autotune_then_graph():
         f += 1
         assert f < 60
     cfg = pv.pv_batch_get_config(b)
-    assert cfg["verify_mapping"] in (0, 1) and cfg["trace_steps"] in (4, 8, 16) and cfg["stack"] in (32, 64)
+    assert cfg["verify_mapping"] in (0, 1) and cfg["trace_steps"] in (16, 32, 64) and cfg["stack"] in (32, 64)
     times = pv.pv_batch_step_times(b)
     assert len(times) == 5 and all(t >= 0 for t in times)
     _run(lanes, b, range(f, f + 3), pv.PV_MODE_ERROR, 0.01, 0, traversal_counters=cfg["verify_mapping"] == 0)

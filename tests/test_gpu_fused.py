@@ -10,6 +10,10 @@ visibility rays, moving area light, moving objects, box and exact segment
 tests), error-mode thresholds from 0 to 5 %, and a light with a
 distribution map (where the call runs the separate kernels).  A last test
 runs the fused call against the FP64 oracle.
+
+pv_verify_retrace_deposit also deposits the atlas inside the same kernel;
+its records, counters and integer atlas must equal those of
+pv_verify_retrace followed by pv_deposit, bit for bit.
 """
 import numpy as np
 import pytest
@@ -110,6 +114,54 @@ def test_fused_frame_matches_separate_calls(name, mode, tau, flags):
     if mode == pv.PV_MODE_ERROR and tau == 0.01 and name in ("box_torus", "city_small", "point_light_moving"):
         assert tails > 0                           # Alg. 1 did hand paths straight to the re-trace
     p.close()
+
+
+def _atlas(sc, res=256):
+    torch = _torch()
+    return torch.zeros(res, res, 3, dtype=torch.int64, device="cuda"), sc.atlas_rect, 40
+
+
+@pytest.mark.parametrize("mode,tau,flags", [MODES[0], MODES[3], MODES[4]], ids=lambda v: str(v))
+@pytest.mark.parametrize("name", list(SCENES))
+def test_fused_deposit_matches_separate_calls(name, mode, tau, flags):
+    """pv_verify_retrace_deposit against pv_verify_retrace + pv_deposit: records, counters and atlas."""
+    torch = _torch()
+    sc = SCENES[name]()
+    p = Pair(sc, 19)
+    a1, rect, scale = _atlas(sc)
+    a2 = torch.full_like(a1, 12345)                # cleared by the call
+    for f in range(2, 5):
+        s1, s2 = pv.new_stats(), pv.new_stats()
+        for h in (p.h1, p.h2):
+            gu.advance(h, sc, f)
+        pv.pv_verify_retrace(p.h1, p.P1, mode, tau, flags, p.seed, f, s1)
+        pv.pv_deposit(p.h1, p.P1, a1, rect, scale)
+        pv.pv_verify_retrace_deposit(p.h2, p.P2, mode, tau, flags, p.seed, f, a2, rect, scale, s2)
+        p.compare(pv.stats_dict(s1), pv.stats_dict(s2))
+        assert torch.equal(a1, a2), int((a1 != a2).sum())
+        assert int(a1.sum()) > 0
+    p.close()
+
+
+def test_fused_deposit_without_motion_and_with_distribution_map():
+    torch = _torch()
+    for sc, dm, moving in ((kit.box_with_torus(3000, B=4), (0, 0, 0, 0), False),
+                           (kit.rect_light_over_floor(2560, shift=lambda f: (0.11 * (f - 1), 0.0, 0.07 * (f - 1)), B=2,
+                                                      R=3.0), (4, 4, 4, 4), True)):
+        p = Pair(sc, 29, dm_rect=dm)
+        a1, rect, scale = _atlas(sc, 128)
+        a2 = torch.zeros_like(a1)
+        for f in range(2, 4):
+            s1, s2 = pv.new_stats(), pv.new_stats()
+            ff = f if moving else 1
+            for h in (p.h1, p.h2):
+                gu.advance(h, sc, ff)
+            pv.pv_verify_retrace(p.h1, p.P1, pv.PV_MODE_ERROR, 0.01, 0, p.seed, f, s1)
+            pv.pv_deposit(p.h1, p.P1, a1, rect, scale)
+            pv.pv_verify_retrace_deposit(p.h2, p.P2, pv.PV_MODE_ERROR, 0.01, 0, p.seed, f, a2, rect, scale, s2)
+            p.compare(pv.stats_dict(s1), pv.stats_dict(s2))
+            assert torch.equal(a1, a2)
+        p.close()
 
 
 def test_fused_frame_with_distribution_map_matches_separate_calls():
