@@ -250,8 +250,9 @@ def pv_build_scene(verts, tri_object, object_dynamic, object_albedo, lights, max
 
 
 def pv_update_dynamic(scene, xforms=None, lights=None, stream=None) -> None:
+    """``lights``: a list of lights, or an array already packed by make_lights."""
     xf = None if xforms is None else np.ascontiguousarray(xforms, np.float32)
-    la = None if lights is None else make_lights(lights)
+    la = None if lights is None else (lights if isinstance(lights, C.Array) else make_lights(lights))
     _check("pv_update_dynamic", load().pv_update_dynamic(
         scene, None if xf is None else xf.ctypes.data_as(C.c_void_p), None if la is None else C.cast(la, C.c_void_p),
         _stream(stream)))
@@ -447,30 +448,37 @@ def pv_batch_create(items, mode: int, tau: float, flags: int = 0, stream=None) -
     return Batch(h, len(items))
 
 
+class BatchPoses:
+    """The per-scene poses of one batched frame, marshalled once: xforms / lights are per scene a float32
+    [n_objects, 12] array / list of lights, or None (whole argument or per entry).  Reusable."""
+
+    def __init__(self, n: int, xforms, lights):
+        self.keep = []
+        self.xf = None
+        if xforms is not None:
+            self.xf = (C.c_void_p * n)()
+            for i, x in enumerate(xforms):
+                if x is not None:
+                    a = np.ascontiguousarray(x, np.float32)
+                    self.keep.append(a)
+                    self.xf[i] = a.ctypes.data
+        self.lt = None
+        if lights is not None:
+            self.lt = (C.c_void_p * n)()
+            for i, l in enumerate(lights):
+                if l is not None:
+                    a = make_lights(l)
+                    self.keep.append(a)
+                    self.lt[i] = C.cast(a, C.c_void_p).value
+
+
 def pv_batch_frame(batch: Batch, xforms, lights, frame: int, stream=None) -> None:
-    """xforms / lights: per scene a float32 [n_objects, 12] array / list of
-    lights, or None (whole argument or per entry)."""
-    n = batch.n
-    keep = []
-    xf = None
-    if xforms is not None:
-        xf = (C.c_void_p * n)()
-        for i, x in enumerate(xforms):
-            if x is not None:
-                a = np.ascontiguousarray(x, np.float32)
-                keep.append(a)
-                xf[i] = a.ctypes.data
-    lt = None
-    if lights is not None:
-        lt = (C.c_void_p * n)()
-        for i, l in enumerate(lights):
-            if l is not None:
-                a = make_lights(l)
-                keep.append(a)
-                lt[i] = C.cast(a, C.c_void_p).value
-    _check("pv_batch_frame", load().pv_batch_frame(batch.handle, None if xf is None else C.cast(xf, C.c_void_p),
-                                                    None if lt is None else C.cast(lt, C.c_void_p), int(frame),
-                                                    _stream(stream)))
+    """xforms / lights as BatchPoses takes them, or a BatchPoses as ``xforms`` (``lights`` ignored)."""
+    poses = xforms if isinstance(xforms, BatchPoses) else BatchPoses(batch.n, xforms, lights)
+    _check("pv_batch_frame", load().pv_batch_frame(batch.handle,
+                                                    None if poses.xf is None else C.cast(poses.xf, C.c_void_p),
+                                                    None if poses.lt is None else C.cast(poses.lt, C.c_void_p),
+                                                    int(frame), _stream(stream)))
 
 
 def pv_batch_autotune(batch: Batch, frames_per_candidate: int = 1) -> None:

@@ -24,7 +24,10 @@ NVCC = os.environ.get("NVCC", "nvcc")
 
 def _flags(extra=()):
     user = os.environ.get("PV_NVCC_FLAGS", "").split()      # extra definitions for tuning builds
-    return ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
+    # --fmad=false: a product and a sum stay two roundings unless the source asks for fmaf, so every
+    # kernel that shares a device function computes it identically (the entry points promise
+    # bit-identical records whichever kernel traced a path)
+    return ["-O3", "--fmad=false", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
             "-I", CSRC, *ARCH, *user, *extra]
 
 
