@@ -39,6 +39,7 @@ struct BScene {
   const uint32_t* d_tri_prim;
   Tri* dtris;
   DynObj* objs;
+  MovedGroups* groups;
   float* xf_old;
   float* xf_new;
   const Node* bnodes;                         // all binary nodes (the wide refit sources index them)
@@ -135,6 +136,7 @@ __global__ void k_b_build_top(const BScene* S, const BFrame* F) {
   if (threadIdx.x != 0 || !F[s].moved) return;
   const BScene& B = S[s];
   build_top(B.wnodes, B.tris, B.top_off, B.s_wroot, B.objs, (int)B.n_dyn, B.root);
+  if (B.groups) build_moved_groups(B.objs, (int)B.n_dyn, F[s].moved, B.groups);
 }
 
 // ---------------------------------------------------------------- verify
@@ -886,6 +888,7 @@ extern "C" int pv_batch_create(const pv_batch_scene* scenes, uint32_t n, const p
     B.d_tri_prim = s->d_tri_prim;
     B.dtris = s->tris + s->d_tri_off;
     B.objs = s->objs;
+    B.groups = s->groups;
     B.xf_old = s->xf_old;
     B.xf_new = s->xf_new;
     B.bnodes = s->nodes;

@@ -402,9 +402,10 @@ __global__ void k_wide_refit(const Node* bnodes, const int* wsrc, const uint32_t
 }
 
 __global__ void k_build_top(WNode* wnodes, const Tri* tris, int top_off, int static_root, const DynObj* objs, int n_dyn,
-                            int* root_out) {
+                            int* root_out, uint64_t moved, MovedGroups* groups) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   build_top(wnodes, tris, top_off, static_root, objs, n_dyn, root_out);
+  if (groups) build_moved_groups(objs, n_dyn, moved, groups);
 }
 
 
@@ -802,6 +803,8 @@ int build_bvh(pv_scene* s, const float* h_verts, const std::vector<uint32_t>& st
   fail(cudaMalloc(&s->d_node_parent, nd * sizeof(uint32_t)));
   fail(cudaMalloc(&s->d_fit_flags, nd * sizeof(uint32_t)));
   fail(cudaMalloc(&s->objs, s->n_dyn * sizeof(DynObj)));
+  fail(cudaMalloc(&s->groups, sizeof(MovedGroups)));
+  fail(cudaMemset(s->groups, 0, sizeof(MovedGroups)));
   for (int b = 0; b < 2; ++b) {
     fail(cudaMalloc(&s->r_keys[b], nd * sizeof(uint64_t)));
     fail(cudaMalloc(&s->r_vals[b], nd * sizeof(uint32_t)));
@@ -881,7 +884,8 @@ void launch_update_dynamic(pv_scene* s, cudaStream_t st) {
     }
   }
   if (s->moved || !s->top_built) {
-    k_build_top<<<1, 32, 0, st>>>(s->wnodes, s->tris, (int)s->w_top_off, s->s_wroot, s->objs, (int)s->n_dyn, s->root);
+    k_build_top<<<1, 32, 0, st>>>(s->wnodes, s->tris, (int)s->w_top_off, s->s_wroot, s->objs, (int)s->n_dyn, s->root,
+                                  s->moved, s->groups);
     s->top_built = true;
   }
 }

@@ -84,6 +84,20 @@ struct DmLight {
   uint32_t* dmc;             // DM_C [cells]
 };
 
+// The moved objects in spatial groups of up to four, rebuilt with the top
+// level each frame in which objects move: sorted along the axis of widest
+// centroid spread, cut into consecutive groups.  A group's box is the union
+// of its members' old-and-new boxes, so the Sec. 3.2 box test can reject a
+// segment against a group before testing its members, with the same result.
+constexpr int kGroupSize = 4;
+constexpr int kMaxGroups = (kMaxDyn + kGroupSize - 1) / kGroupSize;
+struct MovedGroups {
+  uint32_t n;                                  // groups in use
+  uint32_t pad;
+  float box[kMaxGroups][6];                    // lo xyz, hi xyz
+  int8_t slot[kMaxGroups][kGroupSize];         // member slots, -1 past the last
+};
+
 // light state passed by value to the kernels
 struct FrameLights {
   LightPose cur[PV_MAX_LIGHTS];
@@ -101,6 +115,7 @@ struct SceneView {
   const Tri* tris;           // [static references | dynamic triangles]
   const int* root;           // device word: root child index of the whole scene (INT32_MIN = empty)
   const DynObj* objs;
+  const MovedGroups* groups;   // moved objects in groups (valid in frames where objects moved)
   uint32_t n_dyn;
   const uint8_t* prim_slot;  // [n_tris] 255 = static, else dynamic slot
   const uint32_t* prim_dyn;  // [n_tris] index into the dynamic arrays (dynamic prims)

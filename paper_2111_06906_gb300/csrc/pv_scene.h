@@ -41,6 +41,7 @@ struct pv_scene {
   uint32_t* d_fit_flags = nullptr;   // [n_dyn_tris] arrival counters for the bottom-up pass
   uint8_t* d_tri_slot = nullptr;     // [n_dyn_tris] slot per dynamic triangle
   pvk::DynObj* objs = nullptr;       // [n_dyn]
+  pvk::MovedGroups* groups = nullptr;  // the moved objects' groups of this frame
   std::vector<pvk::DynObj> h_objs;
   std::vector<std::vector<uint32_t>> dyn_tris_of;   // slot -> primitive ids (build only)
   // rebuild scratch (PV_BUILD_DYN_REBUILD)

@@ -283,4 +283,60 @@ __device__ __forceinline__ void build_top(WNode* wnodes, const Tri* tris, int to
   *root_out = top_off;
 }
 
+// The moved objects' groups of this frame (see MovedGroups): one thread.
+__device__ __forceinline__ void build_moved_groups(const DynObj* objs, int n_dyn, uint64_t moved, MovedGroups* g) {
+  float box[kMaxDyn][6];
+  int slot[kMaxDyn];
+  int n = 0;
+  for (int s = 0; s < n_dyn && s < kMaxDyn; ++s) {
+    if (!((moved >> s) & 1ull)) continue;
+    for (int k = 0; k < 3; ++k) {
+      box[n][k] = fminf(objs[s].box_new[k], objs[s].box_old[k]);
+      box[n][3 + k] = fmaxf(objs[s].box_new[3 + k], objs[s].box_old[3 + k]);
+    }
+    slot[n++] = s;
+  }
+  float clo[3] = {3e38f, 3e38f, 3e38f}, chi[3] = {-3e38f, -3e38f, -3e38f};
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < 3; ++k) {
+      const float c = 0.5f * (box[i][k] + box[i][3 + k]);
+      clo[k] = fminf(clo[k], c);
+      chi[k] = fmaxf(chi[k], c);
+    }
+  int ax = 0;
+  for (int k = 1; k < 3; ++k)
+    if (chi[k] - clo[k] > chi[ax] - clo[ax]) ax = k;
+  int order[kMaxDyn];
+  for (int i = 0; i < n; ++i) order[i] = i;
+  for (int i = 1; i < n; ++i) {                 // insertion sort by centroid along ax
+    const int v = order[i];
+    const float cv = box[v][ax] + box[v][3 + ax];
+    int j = i - 1;
+    while (j >= 0 && box[order[j]][ax] + box[order[j]][3 + ax] > cv) {
+      order[j + 1] = order[j];
+      --j;
+    }
+    order[j + 1] = v;
+  }
+  const int ng = (n + kGroupSize - 1) / kGroupSize;
+  for (int q = 0; q < ng; ++q) {
+    float b[6] = {3e38f, 3e38f, 3e38f, -3e38f, -3e38f, -3e38f};
+    for (int m = 0; m < kGroupSize; ++m) {
+      const int i = q * kGroupSize + m;
+      if (i < n) {
+        const int o = order[i];
+        for (int k = 0; k < 3; ++k) {
+          b[k] = fminf(b[k], box[o][k]);
+          b[3 + k] = fmaxf(b[3 + k], box[o][3 + k]);
+        }
+        g->slot[q][m] = (int8_t)slot[o];
+      } else {
+        g->slot[q][m] = -1;
+      }
+    }
+    for (int k = 0; k < 6; ++k) g->box[q][k] = b[k];
+  }
+  g->n = (uint32_t)ng;
+}
+
 }  // namespace pvk

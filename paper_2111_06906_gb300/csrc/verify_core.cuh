@@ -110,13 +110,42 @@ __device__ __forceinline__ bool seg_vs_object(const SceneView& sv, const Seg& g,
   return false;
 }
 
-// Segment a->b against every moved object; box tests first reject against
-// the union of all moved boxes (a superset of each, so the result is the same).
+// Moved-object groups staged in shared memory (MovedGroups).
+struct GroupSmem {
+  float box[kMaxGroups][6];
+  int8_t slot[kMaxGroups][kGroupSize];
+  int n;
+};
+
+// Segment a->b against every moved object.  Box tests reject first against
+// the union of all moved boxes, then against each group's box, and test a
+// group's members only when its box is met.  A box that contains another
+// never rejects what the slab test accepts for the inner one (the slab
+// bounds are monotone in the face coordinates), so the result is that of
+// testing every moved object.
 template <int S = kStack>
-__device__ __forceinline__ bool seg_vs_moved(const SceneView& sv, const float* cull, const float* uni, bool boxes,
-                                             bool test_old, float3 a, float3 b, Work& wk) {
+__device__ __forceinline__ bool seg_vs_moved(const SceneView& sv, const float* cull, const float* uni,
+                                             const GroupSmem& gs, bool boxes, bool test_old, float3 a, float3 b,
+                                             Work& wk) {
   const Seg g = seg_prep(sv, a, b, boxes);
-  if (boxes && !seg_box(g.inv, g.aoi, uni + 6 * kMaxDyn)) return false;
+  if (boxes) {
+    if (!seg_box(g.inv, g.aoi, uni + 6 * kMaxDyn)) return false;
+    if (gs.n == 0) {                           // no group table: every moved object in turn
+      for (uint64_t m = sv.moved; m; m &= m - 1)
+        if (seg_box(g.inv, g.aoi, uni + 6 * (__ffsll((long long)m) - 1))) return true;
+      return false;
+    }
+    for (int q = 0; q < gs.n; ++q) {
+      if (!seg_box(g.inv, g.aoi, gs.box[q])) continue;
+#pragma unroll
+      for (int m = 0; m < kGroupSize; ++m) {
+        const int s = gs.slot[q][m];
+        if (s < 0) break;
+        if (seg_box(g.inv, g.aoi, uni + 6 * s)) return true;
+      }
+    }
+    return false;
+  }
   for (uint64_t m = sv.moved; m; m &= m - 1)
     if (seg_vs_object<S>(sv, g, cull, uni, boxes, test_old, __ffsll((long long)m) - 1, wk)) return true;
   return false;
@@ -130,6 +159,7 @@ __device__ __forceinline__ uint32_t* field(pv_frame_stats* s, size_t off) {
 struct VerifySmem {
   float cull[kMaxDyn * 6];
   float uni[(kMaxDyn + 1) * 6];
+  GroupSmem groups;
   uint32_t red[32 * 6];
   unsigned long long red64[32];
   int mslot[kMaxDyn];          // moved slots in ascending order (warp mapping)
@@ -260,6 +290,13 @@ __device__ __forceinline__ bool finish_stage(const VerifyArgs& A, uint32_t p, co
 // Block prologue: moved objects' boxes, their union, and the moved-slot list.
 __device__ __forceinline__ void verify_smem_init(const SceneView& sv, VerifySmem& sm) {
   load_boxes(sv, sm.cull, sm.uni);
+  // this frame's groups of the moved objects (none without a group table)
+  const bool have = sv.moved && sv.groups;
+  const int ng = have ? (int)min(sv.groups->n, (uint32_t)kMaxGroups) : 0;
+  for (int i = threadIdx.x; i < ng * 6; i += blockDim.x) sm.groups.box[i / 6][i % 6] = sv.groups->box[i / 6][i % 6];
+  for (int i = threadIdx.x; i < ng * kGroupSize; i += blockDim.x)
+    sm.groups.slot[i / kGroupSize][i % kGroupSize] = sv.groups->slot[i / kGroupSize][i % kGroupSize];
+  if (threadIdx.x == 0) sm.groups.n = ng;
   if (threadIdx.x == 0) {
     int k = 0;
     for (uint64_t m = sv.moved; m; m &= m - 1) sm.mslot[k++] = __ffsll((long long)m) - 1;
@@ -335,8 +372,8 @@ __device__ __forceinline__ void verify_block(const SceneView& sv, const FrameLig
         bool hit = slot_hit(sv, k, prim_a, prim_b, v.blocked1);
         if (!hit && sv.moved) {
           ++c_tested;
-          hit = kExact ? seg_vs_moved<S>(sv, sm.cull, sm.uni, false, test_old, a, b, wk)
-                       : seg_vs_moved<S>(sv, sm.cull, sm.uni, true, false, a, b, wk);
+          hit = kExact ? seg_vs_moved<S>(sv, sm.cull, sm.uni, sm.groups, false, test_old, a, b, wk)
+                       : seg_vs_moved<S>(sv, sm.cull, sm.uni, sm.groups, true, false, a, b, wk);
         }
         if (hit) {
           mask |= 1u << k;
