@@ -231,20 +231,45 @@ __device__ __forceinline__ Ray make_ray(float3 o, float3 d, float tmin) {
   return r;
 }
 
+// A wide node's child boxes as seen by one ray: along each axis the plane
+// the ray meets first ("near": lo for a positive direction component, hi for
+// a negative one) and the other ("far"), picked by the load address.
+struct WNodeRay {
+  float4 nx, fx, ny, fy, nz, fz;
+  int4 child;
+};
+
+__device__ __forceinline__ WNodeRay load_wnode_ray(const WNode* nodes, int i, const Ray& r) {
+  const float4* p = reinterpret_cast<const float4*>(nodes + i);
+  const uint32_t sx = __float_as_uint(r.inv.x) >> 31, sy = __float_as_uint(r.inv.y) >> 31;
+  const uint32_t sz = __float_as_uint(r.inv.z) >> 31;
+  WNodeRay n;
+  n.nx = __ldg(p + sx);
+  n.fx = __ldg(p + (1u - sx));
+  n.ny = __ldg(p + 2u + sy);
+  n.fy = __ldg(p + (3u - sy));
+  n.nz = __ldg(p + 4u + sz);
+  n.fz = __ldg(p + (5u - sz));
+  n.child = __ldg(reinterpret_cast<const int4*>(p + 6));
+  return n;
+}
+
 // The four child boxes of a wide node against the ray within [tmin, tmax]:
-// entry distances, hit mask (bit c = child c).
-__device__ __forceinline__ uint32_t box4(const Ray& r, float tmax, const WNode& n, float t[4]) {
-  const float lx[4] = {n.lox.x, n.lox.y, n.lox.z, n.lox.w}, hx[4] = {n.hix.x, n.hix.y, n.hix.z, n.hix.w};
-  const float ly[4] = {n.loy.x, n.loy.y, n.loy.z, n.loy.w}, hy[4] = {n.hiy.x, n.hiy.y, n.hiy.z, n.hiy.w};
-  const float lz[4] = {n.loz.x, n.loz.y, n.loz.z, n.loz.w}, hz[4] = {n.hiz.x, n.hiz.y, n.hiz.z, n.hiz.w};
+// entry distances, hit mask (bit c = child c).  For a box with lo <= hi the
+// near plane's distance is exactly the smaller of the two slab distances
+// (fmaf is monotone in the plane coordinate), so this is the classic slab
+// test without its per-axis min / max; an unused slot (lo > hi) misses.
+__device__ __forceinline__ uint32_t box4(const Ray& r, float tmax, const WNodeRay& n, float t[4]) {
+  const float nx[4] = {n.nx.x, n.nx.y, n.nx.z, n.nx.w}, fx[4] = {n.fx.x, n.fx.y, n.fx.z, n.fx.w};
+  const float ny[4] = {n.ny.x, n.ny.y, n.ny.z, n.ny.w}, fy[4] = {n.fy.x, n.fy.y, n.fy.z, n.fy.w};
+  const float nz[4] = {n.nz.x, n.nz.y, n.nz.z, n.nz.w}, fz[4] = {n.fz.x, n.fz.y, n.fz.z, n.fz.w};
   uint32_t mask = 0;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const float x0 = fmaf(lx[c], r.inv.x, r.ooi.x), x1 = fmaf(hx[c], r.inv.x, r.ooi.x);
-    const float y0 = fmaf(ly[c], r.inv.y, r.ooi.y), y1 = fmaf(hy[c], r.inv.y, r.ooi.y);
-    const float z0 = fmaf(lz[c], r.inv.z, r.ooi.z), z1 = fmaf(hz[c], r.inv.z, r.ooi.z);
-    const float tn = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), r.tmin));
-    const float tf = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tmax));
+    const float tn = fmaxf(fmaxf(fmaf(nx[c], r.inv.x, r.ooi.x), fmaf(ny[c], r.inv.y, r.ooi.y)),
+                           fmaxf(fmaf(nz[c], r.inv.z, r.ooi.z), r.tmin));
+    const float tf = fminf(fminf(fmaf(fx[c], r.inv.x, r.ooi.x), fmaf(fy[c], r.inv.y, r.ooi.y)),
+                           fminf(fmaf(fz[c], r.inv.z, r.ooi.z), tmax));
     t[c] = tn;
     mask |= (tn <= tf ? 1u : 0u) << c;
   }
@@ -278,19 +303,6 @@ __device__ __forceinline__ bool tri_hit(const Ray& r, const Tri& T, float tmax, 
   return t > r.tmin && t < tmax;
 }
 
-__device__ __forceinline__ WNode load_wnode(const WNode* nodes, int i) {
-  const float4* p = reinterpret_cast<const float4*>(nodes + i);
-  WNode n;
-  n.lox = __ldg(p);
-  n.hix = __ldg(p + 1);
-  n.loy = __ldg(p + 2);
-  n.hiy = __ldg(p + 3);
-  n.loz = __ldg(p + 4);
-  n.hiz = __ldg(p + 5);
-  n.child = __ldg(reinterpret_cast<const int4*>(p + 6));
-  return n;
-}
-
 __device__ __forceinline__ Tri load_tri(const Tri* tris, int i) {
   const float4* p = reinterpret_cast<const float4*>(tris + i);
   Tri t;
@@ -320,7 +332,7 @@ __device__ __forceinline__ void cswap(float& ka, int& va, float& kb, int& vb) {
 }
 
 template <int S = kStack>
-__device__ __forceinline__ bool visit_wide(const WNode& n, const Ray& r, float tbest, int* stk, int& sp, int& next) {
+__device__ __forceinline__ bool visit_wide(const WNodeRay& n, const Ray& r, float tbest, int* stk, int& sp, int& next) {
   float t[4];
   const uint32_t mask = box4(r, tbest, n, t);
   const int m = __popc(mask);
@@ -382,7 +394,7 @@ __device__ __forceinline__ bool traverse(const WNode* nodes, const Tri* tris, in
       }
       if (node >= 0) {
         ++wk.nodes;
-        const WNode n = load_wnode(nodes, node);
+        const WNodeRay n = load_wnode_ray(nodes, node, r);
         int next;
         if (!visit_wide<S>(n, r, tbest, stack, sp, next)) {
           record_error(status, PV_ERR_STACK);
@@ -454,7 +466,7 @@ __device__ __forceinline__ bool trav_step(const SceneView& sv, const Ray& r, Tra
     }
     if (t.node >= 0) {
       ++wk.nodes;
-      const WNode n = load_wnode(sv.nodes, t.node);
+      const WNodeRay n = load_wnode_ray(sv.nodes, t.node, r);
       int next;
       if (!visit_wide<S>(n, r, t.tbest, stk, t.sp, next)) {
         record_error(sv.status, PV_ERR_STACK);

@@ -171,7 +171,7 @@ def test_fused_batch_modes_and_tuner(mode, flags):
         f += 1
         assert f < 60
     times = pv.pv_batch_step_times(b)
-    assert times[2] < 0.05 * times[4] and times[4] > 0.0          # no separate continuation kernel
+    assert times[2] < 0.02 and times[4] > 0.0          # no separate continuation kernel: only event spacing
     cfg = pv.pv_batch_get_config(b)
     _run(lanes, b, range(f, f + 3), mode, 0.01, flags, traversal_counters=cfg["verify_mapping"] == 0, lists=False)
     pv.pv_batch_destroy(b)
