@@ -401,9 +401,9 @@ def run_ours(args, ws, rank, local):
            "retrace_node_visits_per_ray": agg("node_visits", st_retrace) / max(agg("trace_rays", st_retrace), 1),
            "retrace_tri_tests_per_ray": agg("tri_tests", st_retrace) / max(agg("trace_rays", st_retrace), 1),
            "scene_build_s": build_s, "build_flags": args.build_flags, "device_status": [status, status2]}
-    # kernels per reuse frame: pose update (k_update_objects, k_fit, k_wide_refit, k_build_top), k_verify,
-    # k_compact, k_cont_trace (Alg. 1, re-trace and deposit)
-    launches_per_frame = 4 + 3
+    # kernels per reuse frame: pose update (k_refit_wide, k_frame_top), k_verify, k_compact, k_cont_trace
+    # (Alg. 1, re-trace and deposit)
+    launches_per_frame = 2 + 3
     out = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws, "steps": K, "warmup": W,
            "ms_per_step": reuse_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roof,
@@ -697,9 +697,9 @@ def run_batch(args, ws, rank, local):
                         "achieved": achieved / 1e12, "peak": ops_peak / 1e12, "unit": "Top/s",
                         "frac": achieved / ops_peak, "traffic": None,
                         "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x max SM clock"},
-           # graph kernel nodes per frame: prologue, object update, leaf refit, wide refit, top level, verify,
+           # graph kernel nodes per frame: prologue, transform + wide refit, poses + top level, verify,
            # compaction, Alg. 1 + re-trace
-           "gpu_launches": 8 * K, "clocks": clocks.summary()}
+           "gpu_launches": 6 * K, "clocks": clocks.summary()}
     print(json.dumps(out), flush=True)
 
 

@@ -48,6 +48,12 @@ struct BScene {
   const uint32_t* leaf_parent;
   uint32_t* fit_flags;
   uint32_t n_dyn_tris, n_dyn;
+  const uint8_t* tri_slot;
+  const uint32_t* t_link;
+  const uint32_t* w_link;
+  const uint8_t* w_nch;
+  uint32_t* w_arrive;
+  int* obox;
   const int* wsrc_dyn;
   const uint32_t* wcount_dyn;
   WNode* wnodes_dyn;
@@ -94,7 +100,7 @@ __device__ __forceinline__ uint32_t scene_of(const uint32_t* pre, uint32_t n, ui
   return lo;
 }
 
-// Per-frame zeroing of every scene's counters, tile states and refit flags.
+// Per-frame zeroing of every scene's counters and tile states.
 __global__ void k_b_prologue(const BScene* S, const BFrame* F, BCounters* bc) {
   const uint32_t s = blockIdx.x;
   const BScene& B = S[s];
@@ -105,36 +111,40 @@ __global__ void k_b_prologue(const BScene* S, const BFrame* F, BCounters* bc) {
   }
   if (threadIdx.x < 16) B.ctr[threadIdx.x] = 0u;
   for (uint32_t i = threadIdx.x; i < B.n_tiles; i += blockDim.x) B.tiles[i] = 0ull;
-  if (F[s].moved)
-    for (uint32_t i = threadIdx.x; i < B.n_dyn_tris; i += blockDim.x) B.fit_flags[i] = 0u;
 }
 
 // ---------------------------------------------------------------- pose update
-__global__ void __launch_bounds__(256) k_b_update_objects(const BScene* S, const BFrame* F, const uint32_t* tab) {
-  const uint32_t s = tab[2 * blockIdx.x], slot = tab[2 * blockIdx.x + 1];
-  const BScene& B = S[s];
-  update_object(F[s].xf[slot], ((F[s].moved >> slot) & 1ull) != 0, B.d_local, B.d_tri_prim, B.dtris, B.objs,
-                B.xf_old, B.xf_new, slot);
+// Per 256-triangle chunk of one scene (tab: scene, first triangle): the
+// moved objects' triangles to the new pose and the direct wide refit.
+__global__ void __launch_bounds__(256) k_b_refit_wide(const BScene* S, const BFrame* F, const uint32_t* tab) {
+  const uint32_t sc = tab[2 * blockIdx.x], i = tab[2 * blockIdx.x + 1] + threadIdx.x;
+  const BScene& B = S[sc];
+  const uint64_t moved = F[sc].moved;
+  const uint32_t s = i < B.n_dyn_tris ? B.tri_slot[i] : 0u;
+  const bool mv = i < B.n_dyn_tris && ((moved >> s) & 1ull);
+  RefitArgs R;
+  R.local = B.d_local;
+  R.prim = B.d_tri_prim;
+  R.tri_slot = B.tri_slot;
+  R.dtris = B.dtris;
+  R.n = B.n_dyn_tris;
+  R.t_link = B.t_link;
+  R.w_link = B.w_link;
+  R.w_nch = B.w_nch;
+  R.w_arrive = B.w_arrive;
+  R.wdyn = B.wnodes_dyn;
+  R.obox = B.obox;
+  refit_tri(F[sc].xf[mv ? s : 0], mv, s, R, i);
 }
 
-__global__ void __launch_bounds__(256) k_b_fit(const BScene* S, const BFrame* F, const uint32_t* tab) {
-  const uint32_t s = tab[2 * blockIdx.x], i = tab[2 * blockIdx.x + 1] + threadIdx.x;
-  const BScene& B = S[s];
-  if (!F[s].moved || i >= B.n_dyn_tris || B.n_dyn_tris < 2) return;
-  fit_leaf(B.dnodes, B.node_parent, B.leaf_parent, B.fit_flags, B.dtris, nullptr, (int)i);
-}
-
-__global__ void __launch_bounds__(256) k_b_wide_refit(const BScene* S, const BFrame* F, const uint32_t* tab) {
-  const uint32_t s = tab[2 * blockIdx.x], w = tab[2 * blockIdx.x + 1] + threadIdx.x;
-  const BScene& B = S[s];
-  if (!F[s].moved || w >= *B.wcount_dyn) return;
-  wide_refit_node(B.bnodes, B.wsrc_dyn, B.wnodes_dyn, w);
-}
-
-__global__ void k_b_build_top(const BScene* S, const BFrame* F) {
+// One block of 32 threads per scene: pose bookkeeping of every slot, then
+// (when objects moved) the top level and the moved objects' groups.
+__global__ void k_b_frame_top(const BScene* S, const BFrame* F) {
   const uint32_t s = blockIdx.x;
-  if (threadIdx.x != 0 || !F[s].moved) return;
   const BScene& B = S[s];
+  if (B.objs) pose_bookkeeping(F[s].xf, F[s].moved, B.n_dyn, B.objs, B.xf_old, B.xf_new, B.obox);
+  __syncthreads();
+  if (threadIdx.x != 0 || !F[s].moved) return;
   build_top(B.wnodes, B.tris, B.top_off, B.s_wroot, B.objs, (int)B.n_dyn, B.root);
   if (B.groups) build_moved_groups(B.objs, (int)B.n_dyn, F[s].moved, B.groups);
 }
@@ -582,12 +592,8 @@ struct pv_batch {
   uint32_t n_vtiles[3] = {};
   uint32_t* d_ctab = nullptr;
   uint32_t n_ctiles = 0;
-  uint32_t* d_utab = nullptr;
-  uint32_t n_upd = 0;
   uint32_t* d_ftab = nullptr;
   uint32_t n_fit = 0;
-  uint32_t* d_rtab = nullptr;
-  uint32_t n_refit = 0;
   bool fused = false;                         // no lists asked for: Alg. 1 runs inside the re-trace kernel
   size_t smem_cont = 0, smem_trace = 0, smem_ct = 0;
   int occ_cont[2] = {1, 1};                   // resident blocks per SM: [stack 32, 64]
@@ -648,10 +654,8 @@ int enqueue_frame(pv_batch* b, cudaStream_t st, bool vis, const pv_batch_config&
     return PV_ERR_CUDA;
   mark(0);
   k_b_prologue<<<n, 256, 0, st>>>(b->d_scenes, b->d_frames, b->d_ctr);
-  if (b->n_upd) k_b_update_objects<<<b->n_upd, 256, 0, st>>>(b->d_scenes, b->d_frames, b->d_utab);
-  if (b->n_fit) k_b_fit<<<b->n_fit, 256, 0, st>>>(b->d_scenes, b->d_frames, b->d_ftab);
-  if (b->n_refit) k_b_wide_refit<<<b->n_refit, 256, 0, st>>>(b->d_scenes, b->d_frames, b->d_rtab);
-  k_b_build_top<<<n, 32, 0, st>>>(b->d_scenes, b->d_frames);
+  if (b->n_fit) k_b_refit_wide<<<b->n_fit, 256, 0, st>>>(b->d_scenes, b->d_frames, b->d_ftab);
+  k_b_frame_top<<<n, 32, 0, st>>>(b->d_scenes, b->d_frames);
   mark(1);
   const int ti = thread_index(c.verify_threads);
   verify_kernel(vis, b->exact, c.verify_mapping == 1)<<<b->n_vtiles[ti], c.verify_threads, 0, st>>>(
@@ -791,7 +795,7 @@ void free_batch(pv_batch* b) {
   for (auto& e : b->ev)
     if (e) cudaEventDestroy(e);
   void* ptrs[] = {b->d_scenes, b->d_frames, b->d_ctr, b->d_vtab[0], b->d_vtab[1], b->d_vtab[2],
-                  b->d_ctab, b->d_utab, b->d_ftab, b->d_rtab};
+                  b->d_ctab, b->d_ftab};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->h_stage) cudaFreeHost(b->h_stage);
@@ -836,7 +840,7 @@ extern "C" int pv_batch_create(const pv_batch_scene* scenes, uint32_t n, const p
   auto fail = [&](int r) { if (r != PV_OK && rc == PV_OK) rc = r; };
   // static per-scene records and work tables
   std::vector<BScene> hs(n);
-  std::vector<uint32_t> vt[3], ct, ut, ft, rt;
+  std::vector<uint32_t> vt[3], ct, ft;
   const uint32_t vthreads[3] = {64, 128, 256};
   for (uint32_t i = 0; i < n && rc == PV_OK; ++i) {
     pv_scene* s = scenes[i].scene;
@@ -898,6 +902,12 @@ extern "C" int pv_batch_create(const pv_batch_scene* scenes, uint32_t n, const p
     B.fit_flags = s->d_fit_flags;
     B.n_dyn_tris = s->n_dyn_tris;
     B.n_dyn = s->n_dyn;
+    B.tri_slot = s->d_tri_slot;
+    B.t_link = s->t_link;
+    B.w_link = s->w_link;
+    B.w_nch = s->w_nch;
+    B.w_arrive = s->w_arrive;
+    B.obox = s->obox;
     B.wsrc_dyn = s->wsrc + 4 * (size_t)s->w_dyn_off;
     B.wcount_dyn = s->wcount + 1;
     B.wnodes_dyn = s->wnodes + s->w_dyn_off;
@@ -921,27 +931,14 @@ extern "C" int pv_batch_create(const pv_batch_scene* scenes, uint32_t n, const p
       ct.push_back(i);
       ct.push_back(t);
     }
-    if (s->n_dyn_tris)
-      for (uint32_t sl = 0; sl < s->n_dyn; ++sl) {
-        ut.push_back(i);
-        ut.push_back(sl);
-      }
-    if (s->n_dyn_tris >= 2)
-      for (uint32_t base = 0; base < s->n_dyn_tris; base += 256) {
-        ft.push_back(i);
-        ft.push_back(base);
-      }
-    if (s->n_dyn_tris > (uint32_t)kLeafMax)
-      for (uint32_t base = 0; base < s->w_top_off - s->w_dyn_off; base += 256) {
-        rt.push_back(i);
-        rt.push_back(base);
-      }
+    for (uint32_t base = 0; base < s->n_dyn_tris; base += 256) {
+      ft.push_back(i);
+      ft.push_back(base);
+    }
   }
   for (int k = 0; k < 3; ++k) b->n_vtiles[k] = (uint32_t)vt[k].size() / 2;
   b->n_ctiles = (uint32_t)ct.size() / 2;
-  b->n_upd = (uint32_t)ut.size() / 2;
   b->n_fit = (uint32_t)ft.size() / 2;
-  b->n_refit = (uint32_t)rt.size() / 2;
   if (rc == PV_OK) {
     if (cudaMalloc(&b->d_scenes, n * sizeof(BScene)) != cudaSuccess ||
         cudaMalloc(&b->d_frames, n * sizeof(BFrame)) != cudaSuccess ||
@@ -951,9 +948,7 @@ extern "C" int pv_batch_create(const pv_batch_scene* scenes, uint32_t n, const p
   }
   for (int k = 0; k < 3 && rc == PV_OK; ++k) fail(upload_table(vt[k], &b->d_vtab[k]));
   if (rc == PV_OK) fail(upload_table(ct, &b->d_ctab));
-  if (rc == PV_OK) fail(upload_table(ut, &b->d_utab));
   if (rc == PV_OK) fail(upload_table(ft, &b->d_ftab));
-  if (rc == PV_OK) fail(upload_table(rt, &b->d_rtab));
   if (rc == PV_OK) fail(cuda_rc(cudaMemcpy(b->d_scenes, hs.data(), n * sizeof(BScene), cudaMemcpyHostToDevice)));
   for (int k = 0; k < kRing && rc == PV_OK; ++k)
     fail(cuda_rc(cudaEventCreateWithFlags(&b->slot_ev[k], cudaEventDisableTiming)));

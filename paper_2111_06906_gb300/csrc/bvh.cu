@@ -408,6 +408,48 @@ __global__ void k_build_top(WNode* wnodes, const Tri* tris, int top_off, int sta
   if (groups) build_moved_groups(objs, n_dyn, moved, groups);
 }
 
+// Parent links of the dynamic objects' wide nodes and of their triangles,
+// after a collapse (the links start all ~0u: roots, one-triangle objects).
+__global__ void k_wide_links(const WNode* wdyn, const uint32_t* n_wide, int w_off, uint32_t tri_off, uint32_t* w_link,
+                             uint8_t* w_nch, uint32_t* t_link) {
+  const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= *n_wide) return;
+  const int4 ch = wdyn[w].child;
+  const int c4[4] = {ch.x, ch.y, ch.z, ch.w};
+  uint32_t m = 0;
+  for (int c = 0; c < 4; ++c) {
+    const int r = c4[c];
+    if (r == INT32_MIN) continue;
+    ++m;
+    const uint32_t link = (w << 2) | (uint32_t)c;
+    if (r >= 0) {
+      w_link[r - w_off] = link;
+    } else {
+      const uint32_t f = leaf_first(r) - tri_off;
+      for (uint32_t k = 0; k < leaf_count(r); ++k) t_link[f + k] = link;
+    }
+  }
+  w_nch[w] = (uint8_t)m;
+}
+
+__global__ void __launch_bounds__(256) k_refit_wide(XformParams P, RefitArgs R) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t s = i < R.n ? R.tri_slot[i] : 0u;
+  const bool mv = i < R.n && ((P.moved >> s) & 1ull);
+  refit_tri(P.xf[mv ? s : 0], mv, s, R, i);
+}
+
+// Pose bookkeeping of every slot, then (when objects moved) the top level
+// and the moved objects' groups.  One block of 32 threads.
+__global__ void k_frame_top(XformParams P, DynObj* objs, float* xf_old, float* xf_new, int* obox, WNode* wnodes,
+                            const Tri* tris, int top_off, int static_root, int* root_out, MovedGroups* groups) {
+  pose_bookkeeping(P.xf, P.moved, P.n_dyn, objs, xf_old, xf_new, obox);
+  __syncthreads();
+  if (threadIdx.x != 0 || !P.moved) return;
+  build_top(wnodes, tris, top_off, static_root, objs, (int)P.n_dyn, root_out);
+  if (groups) build_moved_groups(objs, (int)P.n_dyn, P.moved, groups);
+}
+
 
 }  // namespace pvk
 
@@ -805,6 +847,17 @@ int build_bvh(pv_scene* s, const float* h_verts, const std::vector<uint32_t>& st
   fail(cudaMalloc(&s->objs, s->n_dyn * sizeof(DynObj)));
   fail(cudaMalloc(&s->groups, sizeof(MovedGroups)));
   fail(cudaMemset(s->groups, 0, sizeof(MovedGroups)));
+  fail(cudaMalloc(&s->w_link, nd * sizeof(uint32_t)));
+  fail(cudaMalloc(&s->w_nch, nd * sizeof(uint8_t)));
+  fail(cudaMalloc(&s->w_arrive, nd * sizeof(uint32_t)));
+  fail(cudaMalloc(&s->t_link, nd * sizeof(uint32_t)));
+  fail(cudaMalloc(&s->obox, kMaxDyn * 6 * sizeof(int)));
+  fail(cudaMemset(s->w_arrive, 0, nd * sizeof(uint32_t)));
+  {
+    int ob[kMaxDyn * 6];
+    for (int i = 0; i < kMaxDyn * 6; ++i) ob[i] = ord_of(i % 6 < 3 ? 3.0e38f : -3.0e38f);
+    fail(cudaMemcpy(s->obox, ob, sizeof ob, cudaMemcpyHostToDevice));
+  }
   for (int b = 0; b < 2; ++b) {
     fail(cudaMalloc(&s->r_keys[b], nd * sizeof(uint64_t)));
     fail(cudaMalloc(&s->r_vals[b], nd * sizeof(uint32_t)));
@@ -850,6 +903,27 @@ void launch_update_dynamic(pv_scene* s, cudaStream_t st) {
     for (uint32_t sl = 0; sl < s->n_dyn; ++sl) std::memcpy(P.xf[sl], &s->h_xf_new[12 * sl], 12 * sizeof(float));
     P.moved = s->moved;
     P.n_dyn = s->n_dyn;
+    if (s->top_built && !(s->flags & PV_BUILD_DYN_REBUILD) && kLeafMax == 1) {
+      // refit frames: transform + wide refit in one kernel, bookkeeping and top level in another
+      if (s->moved) {
+        RefitArgs R;
+        R.local = s->d_local;
+        R.prim = s->d_tri_prim;
+        R.tri_slot = s->d_tri_slot;
+        R.dtris = dtris;
+        R.n = n;
+        R.t_link = s->t_link;
+        R.w_link = s->w_link;
+        R.w_nch = s->w_nch;
+        R.w_arrive = s->w_arrive;
+        R.wdyn = s->wnodes + s->w_dyn_off;
+        R.obox = s->obox;
+        k_refit_wide<<<blocks(n, 256), 256, 0, st>>>(P, R);
+      }
+      k_frame_top<<<1, 32, 0, st>>>(P, s->objs, s->xf_old, s->xf_new, s->obox, s->wnodes, s->tris, (int)s->w_top_off,
+                                    s->s_wroot, s->root, s->groups);
+      return;
+    }
     k_update_objects<<<s->n_dyn, 256, 0, st>>>(P, s->d_local, s->d_tri_prim, dtris, s->objs, s->xf_old, s->xf_new);
     if (s->moved) {
       if (s->flags & PV_BUILD_DYN_REBUILD) {
@@ -871,10 +945,15 @@ void launch_update_dynamic(pv_scene* s, cudaStream_t st) {
                                               (int)n);
       }
       if (collapse) {
-        // wide nodes of the dynamic objects (topology from the binary tree)
+        // wide nodes of the dynamic objects (topology from the binary tree), and their parent links
         k_collapse<<<1, 1024, 0, st>>>(s->nodes, (int)s->d_tri_off, 0, s->objs, (int)s->n_dyn, s->cq,
                                        s->cq + 2 * s->q_cap, s->q_cap, s->wnodes, s->wsrc + 4 * (size_t)s->w_dyn_off,
                                        (int)s->w_dyn_off, s->wcount + 1, s->status);
+        cudaMemsetAsync(s->w_link, 0xFF, n * sizeof(uint32_t), st);
+        cudaMemsetAsync(s->t_link, 0xFF, n * sizeof(uint32_t), st);
+        const uint32_t cap = std::max<uint32_t>(s->w_top_off - s->w_dyn_off, 1);
+        k_wide_links<<<blocks(cap, 256), 256, 0, st>>>(s->wnodes + s->w_dyn_off, s->wcount + 1, (int)s->w_dyn_off,
+                                                        s->d_tri_off, s->w_link, s->w_nch, s->t_link);
       } else if (n > (uint32_t)kLeafMax) {
         // refit: refresh the wide boxes from the binary slots
         const uint32_t cap = s->w_top_off - s->w_dyn_off;

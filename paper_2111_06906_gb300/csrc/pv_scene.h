@@ -39,6 +39,12 @@ struct pv_scene {
   uint32_t* d_leaf_parent = nullptr; // [n_dyn_tris] parent << 1 | side
   uint32_t* d_node_parent = nullptr; // [n_dyn_tris] parent << 1 | side of internal nodes
   uint32_t* d_fit_flags = nullptr;   // [n_dyn_tris] arrival counters for the bottom-up pass
+  // direct refit of the dynamic wide nodes (after the first collapse)
+  uint32_t* w_link = nullptr;        // [n_dyn_tris] dynamic wide node -> parent (local << 2 | slot), ~0u at a root
+  uint8_t* w_nch = nullptr;          // [n_dyn_tris] children in use per dynamic wide node
+  uint32_t* w_arrive = nullptr;      // [n_dyn_tris] children refitted this frame (reset by the last)
+  uint32_t* t_link = nullptr;        // [n_dyn_tris] dynamic triangle -> parent wide node (local << 2 | slot)
+  int* obox = nullptr;               // [kMaxDyn][6] exact new boxes of the frame, order-preserving integers
   uint8_t* d_tri_slot = nullptr;     // [n_dyn_tris] slot per dynamic triangle
   pvk::DynObj* objs = nullptr;       // [n_dyn]
   pvk::MovedGroups* groups = nullptr;  // the moved objects' groups of this frame

@@ -4,6 +4,8 @@
 // refresh of the wide nodes from it, and the top level over the static root
 // and the object roots.
 #pragma once
+#include <cstring>
+
 #include "pv_scene.h"
 
 namespace pvk {
@@ -63,6 +65,19 @@ __device__ __forceinline__ void fit_leaf(Node* nodes, const uint32_t* node_paren
   }
 }
 
+// Order-preserving integer image of a float (monotone over all non-NaN
+// values), so that minima and maxima can be taken by integer atomics.
+__host__ __device__ __forceinline__ int ord_of(float f) {
+#ifdef __CUDA_ARCH__
+  const int i = __float_as_int(f);
+#else
+  int i;
+  memcpy(&i, &f, 4);
+#endif
+  return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float of_ord(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
+
 struct XformParams {
   float xf[kMaxDyn][12];
   uint64_t moved;
@@ -86,6 +101,101 @@ __device__ __forceinline__ Tri xform_tri(const float* m, const float* v, uint32_
   T.e1 = make_float4(w[3] - w[0], w[4] - w[1], w[5] - w[2], 0.f);
   T.e2 = make_float4(w[6] - w[0], w[7] - w[1], w[8] - w[2], 0.f);
   return T;
+}
+
+// Direct refit of the dynamic objects' wide nodes, one thread per dynamic
+// triangle: a moved object's triangle goes to the new pose, its exact box
+// joins the object's box (integer atomics), and its padded box is written
+// into its slot of the parent wide node; the last child to arrive at a node
+// takes the union of the node's children up to the parent, and so on to the
+// object's root.  The boxes are the same minima and maxima of the same
+// padded leaf boxes that the binary refit gathers, so the wide nodes come out
+// identical, in a third of the dependent levels.
+struct RefitArgs {
+  const float* local;
+  const uint32_t* prim;
+  const uint8_t* tri_slot;
+  Tri* dtris;
+  uint32_t n;
+  const uint32_t* t_link;
+  const uint32_t* w_link;
+  const uint8_t* w_nch;
+  uint32_t* w_arrive;
+  WNode* wdyn;
+  int* obox;
+};
+
+__device__ __forceinline__ void refit_tri(const float* xf_slot, bool moved_lane, uint32_t s, const RefitArgs& R,
+                                          uint32_t i) {
+  const int lane = threadIdx.x & 31;
+  float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+  Tri T;
+  if (moved_lane) {
+    T = xform_tri(xf_slot, R.local + 9 * (size_t)i, R.prim[i], lo, hi);
+    R.dtris[i] = T;
+  }
+  // the lanes of one object reduce its exact box, one of them adds it
+  const unsigned same = __match_any_sync(0xffffffffu, moved_lane ? (int)s : -1);
+  if (!moved_lane) return;
+  const int leader = __ffs(same) - 1;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int l = __reduce_min_sync(same, ord_of(lo[k]));
+    const int h = __reduce_max_sync(same, ord_of(hi[k]));
+    if (lane == leader) {
+      atomicMin(R.obox + 6 * s + k, l);
+      atomicMax(R.obox + 6 * s + 3 + k, h);
+    }
+  }
+  float3 blo, bhi;
+  tri_box(T, blo, bhi);
+  pad_box(blo, bhi);
+  uint32_t link = R.t_link[i];
+  for (int guard = 0; guard < 64 && link != 0xFFFFFFFFu; ++guard) {
+    const uint32_t w = link >> 2, c = link & 3u;
+    WNode* nd = R.wdyn + w;
+    (&nd->lox.x)[c] = blo.x;
+    (&nd->hix.x)[c] = bhi.x;
+    (&nd->loy.x)[c] = blo.y;
+    (&nd->hiy.x)[c] = bhi.y;
+    (&nd->loz.x)[c] = blo.z;
+    (&nd->hiz.x)[c] = bhi.z;
+    __threadfence();
+    const uint32_t m = R.w_nch[w];
+    if (atomicAdd(R.w_arrive + w, 1u) + 1u < m) return;
+    R.w_arrive[w] = 0u;                        // every child of this frame has arrived
+    blo = make_float3(3.0e38f, 3.0e38f, 3.0e38f);
+    bhi = make_float3(-3.0e38f, -3.0e38f, -3.0e38f);
+    for (uint32_t q = 0; q < m; ++q) {
+      blo.x = fminf(blo.x, __ldcg(&nd->lox.x + q));
+      blo.y = fminf(blo.y, __ldcg(&nd->loy.x + q));
+      blo.z = fminf(blo.z, __ldcg(&nd->loz.x + q));
+      bhi.x = fmaxf(bhi.x, __ldcg(&nd->hix.x + q));
+      bhi.y = fmaxf(bhi.y, __ldcg(&nd->hiy.x + q));
+      bhi.z = fmaxf(bhi.z, __ldcg(&nd->hiz.x + q));
+    }
+    link = R.w_link[w];
+  }
+}
+
+// Per-frame pose bookkeeping of every dynamic slot (what update_object does
+// besides transforming): the new pose becomes the old one; a moved object's
+// new box is this frame's reduced exact box, whose accumulator is reset.
+// Called by all threads of one block.
+__device__ __forceinline__ void pose_bookkeeping(const float (*xf)[12], uint64_t moved, uint32_t n_dyn, DynObj* objs,
+                                                 float* xf_old, float* xf_new, int* obox) {
+  for (uint32_t i = threadIdx.x; i < n_dyn * 12; i += blockDim.x) {
+    xf_old[i] = xf_new[i];
+    xf_new[i] = xf[i / 12][i % 12];
+  }
+  for (uint32_t i = threadIdx.x; i < n_dyn * 6; i += blockDim.x) {
+    const uint32_t sl = i / 6, k = i % 6;
+    objs[sl].box_old[k] = objs[sl].box_new[k];
+    if ((moved >> sl) & 1ull) {
+      objs[sl].box_new[k] = of_ord(obox[i]);
+      obox[i] = ord_of(k < 3 ? 3.0e38f : -3.0e38f);
+    }
+  }
 }
 
 // One block (256 threads) per dynamic slot: keep the previous pose (transform
