@@ -196,7 +196,7 @@ def run_ours(args, ws, rank, local):
     tau = sc.tau if args.tau is None else args.tau
     seed = sc.seed + 7919 * rank
     N, B = sc.n_paths, sc.max_bounces
-    frames_needed = 3 * (args.warmup + args.steps) + 8
+    frames_needed = 4 * (args.warmup + args.steps) + 8     # reuse, separate calls, trace-all, end to end
     xfs = {f: sc.xforms(f) for f in range(1, frames_needed + 1)}
     lts = {f: sc.lights(f) for f in range(1, frames_needed + 1)}
 

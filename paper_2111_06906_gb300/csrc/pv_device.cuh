@@ -183,7 +183,7 @@ __device__ __forceinline__ float4 rng4(uint64_t seed, uint32_t path, uint32_t ve
 // Orthonormal basis about unit n (Duff et al., JCGT 2017), branch on n.z >= 0.
 __device__ __forceinline__ void onb(float3 n, float3& b1, float3& b2) {
   const float sg = n.z >= 0.0f ? 1.0f : -1.0f;
-  const float a = -1.0f / (sg + n.z);
+  const float a = -__frcp_rn(sg + n.z);     // = -1 / (sg + n.z), correctly rounded
   const float b = n.x * n.y * a;
   b1 = make_float3(1.0f + sg * n.x * n.x * a, sg * b, -sg * n.x);
   b2 = make_float3(b, sg + n.y * n.y * a, -n.y);
@@ -223,9 +223,10 @@ __device__ __forceinline__ Ray make_ray(float3 o, float3 d, float tmin) {
   r.o = o;
   r.d = d;
   const float e = 1e-20f;
-  r.inv = make_float3(1.0f / (fabsf(d.x) > e ? d.x : copysignf(e, d.x)),
-                      1.0f / (fabsf(d.y) > e ? d.y : copysignf(e, d.y)),
-                      1.0f / (fabsf(d.z) > e ? d.z : copysignf(e, d.z)));
+  // __frcp_rn: the correctly rounded 1 / x, i.e. exactly what IEEE division gives
+  r.inv = make_float3(__frcp_rn(fabsf(d.x) > e ? d.x : copysignf(e, d.x)),
+                      __frcp_rn(fabsf(d.y) > e ? d.y : copysignf(e, d.y)),
+                      __frcp_rn(fabsf(d.z) > e ? d.z : copysignf(e, d.z)));
   r.ooi = make_float3(-o.x * r.inv.x, -o.y * r.inv.y, -o.z * r.inv.z);
   r.tmin = tmin;
   return r;
@@ -292,7 +293,7 @@ __device__ __forceinline__ bool tri_hit(const Ray& r, const Tri& T, float tmax, 
   const float3 p = cross(r.d, e2);
   const float det = dot(e1, p);
   if (det == 0.0f) return false;
-  const float inv = 1.0f / det;
+  const float inv = __frcp_rn(det);         // correctly rounded, as 1.0f / det
   const float3 s = r.o - f3(T.v0);
   const float u = dot(s, p) * inv;
   if (!(u >= 0.0f && u <= 1.0f)) return false;

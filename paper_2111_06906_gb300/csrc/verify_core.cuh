@@ -136,7 +136,7 @@ __device__ __forceinline__ bool seg_vs_moved(const SceneView& sv, const float* c
       return false;
     }
     for (int q = 0; q < gs.n; ++q) {
-      if (!seg_box(g.inv, g.aoi, gs.box[q])) continue;
+      if (gs.n > 1 && !seg_box(g.inv, g.aoi, gs.box[q])) continue;   // one group: its box is the union
 #pragma unroll
       for (int m = 0; m < kGroupSize; ++m) {
         const int s = gs.slot[q][m];
@@ -592,7 +592,7 @@ __device__ __forceinline__ int cont_hit(const SceneView& sv, const ContArgs& A, 
     const float3 nsn = dot(nn, d) < 0.0f ? nn : -1.0f * nn;
     const float3 wv = c - xn;
     const float wl = sqrtf(dot(wv, wv));
-    const float cosn = wl > 0.0f ? fmaxf(0.0f, dot(nsn, (1.0f / wl) * wv)) : 0.0f;
+    const float cosn = wl > 0.0f ? fmaxf(0.0f, dot(nsn, __frcp_rn(wl) * wv)) : 0.0f;
     const float4 albo = __ldg(sv.prim_alb + b_prim);
     const float3 no = normalize(prim_normal(sv, b_prim, true));
     const float3 dino = normalize_exact(b - a_orig);
