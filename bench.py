@@ -41,9 +41,9 @@ WORKLOADS = {
     "batch16": "16 independent districts: 10k to 2M tris, 50k to 3M paths (12.4M in all), 1 to 3 lights, "
                "bounce caps 1 to 7, 1 to 4 moving tori; one batched graph-captured frame per step, tuned",
 }
-# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one k_cont_trace launch of a timed
-# reuse frame, measured on the same kernel code
-TRACE_TRAFFIC = {"city": 52805888 + 16419072, "villa": 146542336 + 89437440}
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one k_cont_trace<deposit> launch of a
+# timed reuse frame, measured on the same kernel code
+TRACE_TRAFFIC = {"city": 207107328 + 21058048, "villa": 942739968 + 105475584}
 OPS_PER_NODE = 107    # FP32-pipe ops per wide-node visit (four slab tests + ordering network), from the source
 OPS_PER_TRI = 40      # FP32-pipe ops per Moller-Trumbore test, counted from the source
 SM_COUNT, FP32_LANES = 152, 128
