@@ -144,9 +144,10 @@ __global__ void k_b_frame_top(const BScene* S, const BFrame* F) {
   const BScene& B = S[s];
   if (B.objs) pose_bookkeeping(F[s].xf, F[s].moved, B.n_dyn, B.objs, B.xf_old, B.xf_new, B.obox);
   __syncthreads();
-  if (threadIdx.x != 0 || !F[s].moved) return;
-  build_top(B.wnodes, B.tris, B.top_off, B.s_wroot, B.objs, (int)B.n_dyn, B.root);
-  if (B.groups) build_moved_groups(B.objs, (int)B.n_dyn, F[s].moved, B.groups);
+  if (!F[s].moved) return;
+  build_top_block(B.wnodes, B.tris, B.top_off, B.s_wroot, B.objs, (int)B.n_dyn, B.root);
+  __syncthreads();
+  if (B.groups) build_moved_groups_block(B.objs, (int)B.n_dyn, F[s].moved, B.groups);
 }
 
 // ---------------------------------------------------------------- verify

@@ -403,9 +403,9 @@ __global__ void k_wide_refit(const Node* bnodes, const int* wsrc, const uint32_t
 
 __global__ void k_build_top(WNode* wnodes, const Tri* tris, int top_off, int static_root, const DynObj* objs, int n_dyn,
                             int* root_out, uint64_t moved, MovedGroups* groups) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  build_top(wnodes, tris, top_off, static_root, objs, n_dyn, root_out);
-  if (groups) build_moved_groups(objs, n_dyn, moved, groups);
+  build_top_block(wnodes, tris, top_off, static_root, objs, n_dyn, root_out);
+  __syncthreads();
+  if (groups) build_moved_groups_block(objs, n_dyn, moved, groups);
 }
 
 // Parent links of the dynamic objects' wide nodes and of their triangles,
@@ -445,9 +445,10 @@ __global__ void k_frame_top(XformParams P, DynObj* objs, float* xf_old, float* x
                             const Tri* tris, int top_off, int static_root, int* root_out, MovedGroups* groups) {
   pose_bookkeeping(P.xf, P.moved, P.n_dyn, objs, xf_old, xf_new, obox);
   __syncthreads();
-  if (threadIdx.x != 0 || !P.moved) return;
-  build_top(wnodes, tris, top_off, static_root, objs, (int)P.n_dyn, root_out);
-  if (groups) build_moved_groups(objs, (int)P.n_dyn, P.moved, groups);
+  if (!P.moved) return;
+  build_top_block(wnodes, tris, top_off, static_root, objs, (int)P.n_dyn, root_out);
+  __syncthreads();
+  if (groups) build_moved_groups_block(objs, (int)P.n_dyn, P.moved, groups);
 }
 
 

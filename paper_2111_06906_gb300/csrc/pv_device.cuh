@@ -287,7 +287,7 @@ __device__ __forceinline__ bool box1(const Ray& r, float tmax, const float* bx, 
   return tenter <= e;
 }
 
-// Moller-Trumbore (1997) on the closed triangle, t in (tmin, tmax).
+// Moller-Trumbore (1997) on the closed triangle, t in (tmin, tmax].
 __device__ __forceinline__ bool tri_hit(const Ray& r, const Tri& T, float tmax, float& t) {
   const float3 e1 = f3(T.e1), e2 = f3(T.e2);
   const float3 p = cross(r.d, e2);
@@ -301,7 +301,7 @@ __device__ __forceinline__ bool tri_hit(const Ray& r, const Tri& T, float tmax, 
   const float v = dot(r.d, q) * inv;
   if (!(v >= 0.0f && u + v <= 1.0f)) return false;
   t = dot(e2, q) * inv;
-  return t > r.tmin && t < tmax;
+  return t > r.tmin && t <= tmax;
 }
 
 __device__ __forceinline__ Tri load_tri(const Tri* tris, int i) {
@@ -367,7 +367,10 @@ __device__ __forceinline__ bool visit_leaf(const Tri* tris, int ref, const Ray& 
     ++wk.tris;
     const Tri T = load_tri(tris, (int)(first + i));
     float t;
-    if (__float_as_int(T.v0.w) != exclude && tri_hit(r, T, tbest, t)) {
+    // closest first, the lower triangle index among equal distances: the answer does not depend on
+    // the order in which leaves are visited
+    if (__float_as_int(T.v0.w) != exclude && tri_hit(r, T, tbest, t) &&
+        (t < tbest || (best >= 0 && (int)(first + i) < best))) {
       tbest = t;
       best = (int)(first + i);
       any = true;

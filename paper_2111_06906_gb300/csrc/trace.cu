@@ -54,6 +54,7 @@ __device__ __forceinline__ bool step_rays(const SceneView& sv, const Ray& r, Tra
     for (int i = 0; i < kStepsPerIter && !done; ++i) done = trav_step(sv, r, t, stk, excl, wk);
     return done;
   }
+  if (kDoneLanes >= 32) return step_warp<kMaxSteps>(sv, r, t, stk, excl, wk, done);
 #pragma unroll 1
   for (int i = 0; i < kMaxSteps; ++i) {
     if (!done) done = trav_step(sv, r, t, stk, excl, wk);

@@ -307,24 +307,43 @@ __device__ __forceinline__ void ref_box(const WNode* wnodes, const Tri* tris, in
   }
 }
 
-// Top level over the static root and the dynamic objects' roots, rebuilt
-// every frame by one thread: entries sorted along the axis of largest
-// centroid spread and cut into four consecutive groups, recursively.
-__device__ __forceinline__ void build_top(WNode* wnodes, const Tri* tris, int top_off, int static_root, const DynObj* objs,
-                                          int n_dyn, int* root_out) {
-  float box[kMaxDyn + 1][6];
-  int ref[kMaxDyn + 1];
+// Top level over the static root and the dynamic objects' roots, rebuilt in
+// every frame in which objects move: entries sorted along the axis of
+// largest centroid spread and cut into four consecutive groups,
+// recursively.  build_top_from builds it by one thread from n entries
+// (reference, box) in slot order.
+__device__ __forceinline__ void build_top_from(float (*box)[6], const int* ref, int n, WNode* wnodes, int top_off,
+                                               int* root_out);
+
+// The top level over the static root and the objects' roots: the entries'
+// boxes are gathered by all threads of the block into shared memory (the
+// dependent loads of the roots overlap), then thread 0 builds.  Called by
+// every thread of the block.
+__device__ __forceinline__ void build_top_block(WNode* wnodes, const Tri* tris, int top_off, int static_root,
+                                                const DynObj* objs, int n_dyn, int* root_out) {
+  __shared__ float s_box[kMaxDyn + 1][6];
+  __shared__ int s_ref[kMaxDyn + 1];
+  for (int e = threadIdx.x; e <= n_dyn; e += blockDim.x) {   // entry 0: the static root; 1 + s: slot s
+    const int r = e == 0 ? static_root : objs[e - 1].wroot;
+    s_ref[e] = r;
+    if (r != INT32_MIN) ref_box(wnodes, tris, r, s_box[e]);
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   int n = 0;
-  if (static_root != INT32_MIN) {
-    ref_box(wnodes, tris, static_root, box[n]);
-    ref[n++] = static_root;
+  for (int e = 0; e <= n_dyn; ++e) {           // keep the valid entries in order
+    if (s_ref[e] == INT32_MIN) continue;
+    if (n != e) {
+      s_ref[n] = s_ref[e];
+      for (int k = 0; k < 6; ++k) s_box[n][k] = s_box[e][k];
+    }
+    ++n;
   }
-  for (int s = 0; s < n_dyn; ++s) {
-    const int r = objs[s].wroot;
-    if (r == INT32_MIN) continue;
-    ref_box(wnodes, tris, r, box[n]);
-    ref[n++] = r;
-  }
+  build_top_from(s_box, s_ref, n, wnodes, top_off, root_out);
+}
+
+__device__ __forceinline__ void build_top_from(float (*box)[6], const int* ref, int n, WNode* wnodes, int top_off,
+                                               int* root_out) {
   if (n == 0) {
     *root_out = INT32_MIN;
     return;
@@ -393,19 +412,34 @@ __device__ __forceinline__ void build_top(WNode* wnodes, const Tri* tris, int to
   *root_out = top_off;
 }
 
-// The moved objects' groups of this frame (see MovedGroups): one thread.
-__device__ __forceinline__ void build_moved_groups(const DynObj* objs, int n_dyn, uint64_t moved, MovedGroups* g) {
-  float box[kMaxDyn][6];
-  int slot[kMaxDyn];
-  int n = 0;
-  for (int s = 0; s < n_dyn && s < kMaxDyn; ++s) {
-    if (!((moved >> s) & 1ull)) continue;
-    for (int k = 0; k < 3; ++k) {
-      box[n][k] = fminf(objs[s].box_new[k], objs[s].box_old[k]);
-      box[n][3 + k] = fmaxf(objs[s].box_new[3 + k], objs[s].box_old[3 + k]);
-    }
-    slot[n++] = s;
+// The moved objects' groups of this frame (see MovedGroups) from their n
+// old-and-new boxes (box[i], slot[i]) in slot order: one thread.
+__device__ __forceinline__ void moved_groups_from(float (*box)[6], const int* slot, int n, MovedGroups* g);
+
+// Gathered by every thread of the block (the slots' boxes load side by
+// side), grouped by thread 0.  Called by every thread of the block.
+__device__ __forceinline__ void build_moved_groups_block(const DynObj* objs, int n_dyn, uint64_t moved, MovedGroups* g) {
+  __shared__ float s_box[kMaxDyn][6];
+  __shared__ int s_slot[kMaxDyn];
+  const int nd = min(n_dyn, kMaxDyn);
+  for (int i = threadIdx.x; i < nd * 6; i += blockDim.x) {
+    const int s = i / 6, k = i % 6;
+    if ((moved >> s) & 1ull)
+      s_box[s][k] = k < 3 ? fminf(objs[s].box_new[k], objs[s].box_old[k]) : fmaxf(objs[s].box_new[k], objs[s].box_old[k]);
   }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  int n = 0;
+  for (int s = 0; s < nd; ++s) {               // the moved slots, in order
+    if (!((moved >> s) & 1ull)) continue;
+    if (n != s)
+      for (int k = 0; k < 6; ++k) s_box[n][k] = s_box[s][k];
+    s_slot[n++] = s;
+  }
+  moved_groups_from(s_box, s_slot, n, g);
+}
+
+__device__ __forceinline__ void moved_groups_from(float (*box)[6], const int* slot, int n, MovedGroups* g) {
   float clo[3] = {3e38f, 3e38f, 3e38f}, chi[3] = {-3e38f, -3e38f, -3e38f};
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < 3; ++k) {

@@ -14,10 +14,19 @@ using namespace pvk;
 
 namespace {
 
+// PV_VERIFY_FLAT: error mode deals the warp's segments out to its lanes
+// (verify_block_flat); 0 keeps thread per path throughout.
+#ifndef PV_VERIFY_FLAT
+#define PV_VERIFY_FLAT 1
+#endif
+
 template <bool kPointVis, bool kExact>
 __global__ void __launch_bounds__(pvh::kVerifyThreads) k_verify(SceneView sv, FrameLights L, VerifyArgs A) {
   __shared__ VerifySmem sm;
-  verify_block<kPointVis, kExact>(sv, L, A, blockIdx.x * blockDim.x + threadIdx.x, sm);
+  if (PV_VERIFY_FLAT && A.mode == PV_MODE_ERROR)
+    verify_block_flat<kPointVis, kExact>(sv, L, A, blockIdx.x * blockDim.x + threadIdx.x, sm);
+  else
+    verify_block<kPointVis, kExact>(sv, L, A, blockIdx.x * blockDim.x + threadIdx.x, sm);
 }
 
 __global__ void __launch_bounds__(128, 6) k_continue(SceneView sv, ContArgs A) {

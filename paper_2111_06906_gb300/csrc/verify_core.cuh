@@ -104,7 +104,7 @@ __device__ __forceinline__ bool seg_vs_object(const SceneView& sv, const Seg& g,
       T.e1 = make_float4(w[3] - w[0], w[4] - w[1], w[5] - w[2], 0.f);
       T.e2 = make_float4(w[6] - w[0], w[7] - w[1], w[8] - w[2], 0.f);
       float t;
-      if (tri_hit(g.r, T, g.tmax, t)) return true;
+      if (tri_hit(g.r, T, g.tmax, t) && t < g.tmax) return true;
     }
   }
   return false;
@@ -164,6 +164,8 @@ struct VerifySmem {
   unsigned long long red64[32];
   int mslot[kMaxDyn];          // moved slots in ascending order (warp mapping)
   int n_moved;
+  uint32_t hitmask[256];       // flat mapping: intersected segments of each thread's path
+  uint32_t slotmask[256];      // flat mapping: segments decided by a moved primitive at an end
 };
 
 // Result of the origin stage for one path.
@@ -639,6 +641,87 @@ __device__ __forceinline__ void continue_path(const SceneView& sv, int root, con
     const int o = cont_hit(sv, A, p, cell, seg, mask, meta, a_orig, a_prim, r, h.tri, h.t, a_cur, cc);
     more = o == kContNext && cont_next(sv, A, p, cell, seg, mask, meta, a_orig, a_prim, a_cur, r, cc);
   }
+}
+
+// Flat segment mapping: each lane runs the origin stage of its own path,
+// then the warp deals all segments of its 32 paths out to its lanes, 32 at
+// a time, so lanes with short paths do not idle while long ones finish.  A
+// segment's answer is OR-ed into its path's mask in shared memory.  Same
+// masks, decisions and counters as verify_block: every segment of a tested
+// path is tested there too in error mode, the only mode this mapping serves
+// (the naive modes stop at a path's first hit).  Blocks of at most 256.
+template <bool kPointVis, bool kExact, int S = kStack>
+__device__ __forceinline__ void verify_block_flat(const SceneView& sv, const FrameLights& L, const VerifyArgs& A,
+                                                  uint32_t p, VerifySmem& sm) {
+  verify_smem_init(sv, sm);
+  Work wk;
+  const int root = *sv.root;
+  const uint32_t n = A.n;
+  const int lane = threadIdx.x & 31;
+  const uint32_t wbase = threadIdx.x & ~31u;
+  const bool test_old = kExact && (A.flags & PV_FLAG_TEST_OLD_TRIS) != 0;
+  uint32_t c_tested = 0, c_vis = 0, c_reemit = 0, c_tail = 0;
+  PathCheck v;
+  v.test = false;
+  v.nseg = 0;
+  v.o = make_float3(0.f, 0.f, 0.f);
+  v.blocked1 = false;
+  v.replaced = false;
+  v.cell = 0;
+  if (p < n) v = origin_stage<kPointVis, S>(sv, L, A, root, p, c_vis, c_reemit, wk);
+  sm.hitmask[threadIdx.x] = 0u;
+  sm.slotmask[threadIdx.x] = 0u;
+  // segments of the warp's tested paths, numbered by an inclusive prefix over the lanes
+  const uint32_t cnt = (p < n && v.test) ? v.nseg : 0u;
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  __syncwarp();
+  for (uint32_t base = 0; base < total; base += 32) {
+    const uint32_t q = base + lane;
+    uint32_t lo = 0, hi = 31;                  // owner: first lane whose inclusive count exceeds q
+#pragma unroll
+    for (int it = 0; it < 5; ++it) {
+      const uint32_t mid = (lo + hi) >> 1;
+      const uint32_t im = __shfl_sync(0xffffffffu, incl, mid);
+      if (q < im) hi = mid;
+      else lo = mid + 1;
+    }
+    const uint32_t owner = lo;
+    const uint32_t o_incl = __shfl_sync(0xffffffffu, incl, owner), o_cnt = __shfl_sync(0xffffffffu, cnt, owner);
+    const uint32_t po = __shfl_sync(0xffffffffu, p, owner);
+    const float ox = __shfl_sync(0xffffffffu, v.o.x, owner), oy = __shfl_sync(0xffffffffu, v.o.y, owner);
+    const float oz = __shfl_sync(0xffffffffu, v.o.z, owner);
+    const bool blocked1 = __shfl_sync(0xffffffffu, v.blocked1, owner);
+    if (q >= total) continue;
+    const uint32_t k = q - (o_incl - o_cnt) + 1;    // segment k of path po, 1 .. nseg
+    const float4 vb = A.pa[(size_t)(k - 1) * n + po];
+    const float4 va = k >= 2 ? A.pa[(size_t)(k - 2) * n + po] : make_float4(ox, oy, oz, __int_as_float(-1));
+    const int prim_b = __float_as_int(vb.w), prim_a = __float_as_int(va.w);
+    bool hit = slot_hit(sv, k, prim_a, prim_b, blocked1);
+    if (hit) {
+      atomicOr(&sm.slotmask[wbase + owner], 1u << k);
+    } else if (sv.moved) {
+      hit = kExact ? seg_vs_moved<S>(sv, sm.cull, sm.uni, sm.groups, false, test_old, f3(va), f3(vb), wk)
+                   : seg_vs_moved<S>(sv, sm.cull, sm.uni, sm.groups, true, false, f3(va), f3(vb), wk);
+    }
+    if (hit) atomicOr(&sm.hitmask[wbase + owner], 1u << k);
+  }
+  __syncwarp();
+  bool want_cont = false;
+  if (p < n && v.test) {
+    const uint32_t mask = sm.hitmask[threadIdx.x];
+    if (sv.moved && v.nseg >= 1) c_tested = __popc(~sm.slotmask[threadIdx.x] & ((2u << v.nseg) - 2u));
+    want_cont = finish_stage(A, p, v, mask, c_reemit, c_tail);
+    if (A.touched) A.touched[p] = (mask != 0 || v.replaced) ? 1 : 0;
+  } else if (p < n && A.touched) {
+    A.touched[p] = v.replaced ? 1 : 0;
+  }
+  verify_epilogue(A, p, want_cont, c_tested, c_vis, c_reemit, c_tail, wk, kPointVis || kExact, sm);
 }
 
 }  // namespace pvk
