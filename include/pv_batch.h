@@ -56,7 +56,9 @@ typedef struct {
 
 /* Launch configuration of the batched kernels.
  *  verify_mapping   0: thread per path, 1: warp per path (lanes take the
- *                   (segment, moved object) pairs of one path at a time)
+ *                   (segment, moved object) pairs of one path at a time),
+ *                   2: flat (each warp deals the segments of its 32 paths
+ *                   out to its lanes; PV_MODE_ERROR only)
  *  verify_threads   64, 128 or 256 paths per verify block (tile size)
  *  trace_steps      16, 32 or 64: at most this many traversal steps between
  *                   work refills; a warp refills earlier once every lane's

@@ -153,7 +153,7 @@ __global__ void k_b_frame_top(const BScene* S, const BFrame* F) {
 // ---------------------------------------------------------------- verify
 // One block = one tile of one scene (tab: scene, tile); the scene's view,
 // lights and arguments are staged in shared memory.
-template <bool kPointVis, bool kExact, bool kWarp>
+template <bool kPointVis, bool kExact, int kMap>
 __global__ void __launch_bounds__(256) k_b_verify(const BScene* S, const BFrame* F, const uint32_t* tab) {
   __shared__ VerifySmem sm;
   __shared__ SceneView s_sv;
@@ -167,7 +167,8 @@ __global__ void __launch_bounds__(256) k_b_verify(const BScene* S, const BFrame*
   if (threadIdx.x == 0) s_sv.moved = F[sc].moved;
   __syncthreads();
   const uint32_t p = tile * blockDim.x + threadIdx.x;
-  if (kWarp) verify_block_warp<kPointVis, kExact>(s_sv, s_L, s_V, p, sm);
+  if (kMap == 2) verify_block_flat<kPointVis, kExact>(s_sv, s_L, s_V, p, sm);
+  else if (kMap == 1) verify_block_warp<kPointVis, kExact>(s_sv, s_L, s_V, p, sm);
   else verify_block<kPointVis, kExact>(s_sv, s_L, s_V, p, sm);
 }
 
@@ -545,18 +546,13 @@ using VerifyKernel = void (*)(const BScene*, const BFrame*, const uint32_t*);
 using ContKernel = void (*)(const BScene*, const BFrame*, uint32_t, BCounters*);
 using TraceKernel = void (*)(const BScene*, const BFrame*, uint32_t, BCounters*);
 
-VerifyKernel verify_kernel(bool vis, bool exact, bool warp) {
-  const int k = (vis ? 4 : 0) | (exact ? 2 : 0) | (warp ? 1 : 0);
-  switch (k) {
-    case 0: return k_b_verify<false, false, false>;
-    case 1: return k_b_verify<false, false, true>;
-    case 2: return k_b_verify<false, true, false>;
-    case 3: return k_b_verify<false, true, true>;
-    case 4: return k_b_verify<true, false, false>;
-    case 5: return k_b_verify<true, false, true>;
-    case 6: return k_b_verify<true, true, false>;
-    default: return k_b_verify<true, true, true>;
-  }
+VerifyKernel verify_kernel(bool vis, bool exact, int mapping) {
+  static const VerifyKernel table[2][2][3] = {
+      {{k_b_verify<false, false, 0>, k_b_verify<false, false, 1>, k_b_verify<false, false, 2>},
+       {k_b_verify<false, true, 0>, k_b_verify<false, true, 1>, k_b_verify<false, true, 2>}},
+      {{k_b_verify<true, false, 0>, k_b_verify<true, false, 1>, k_b_verify<true, false, 2>},
+       {k_b_verify<true, true, 0>, k_b_verify<true, true, 1>, k_b_verify<true, true, 2>}}};
+  return table[vis ? 1 : 0][exact ? 1 : 0][mapping < 0 || mapping > 2 ? 0 : mapping];
 }
 
 ContKernel cont_kernel(int stack) { return stack == 32 ? k_b_continue<32> : k_b_continue<64>; }
@@ -623,7 +619,8 @@ namespace {
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? PV_OK : PV_ERR_CUDA; }
 
 bool config_valid(const pv_batch* b, const pv_batch_config& c) {
-  if (c.verify_mapping != 0 && c.verify_mapping != 1) return false;
+  if (c.verify_mapping < 0 || c.verify_mapping > 2) return false;
+  if (c.verify_mapping == 2 && b->params.mode != PV_MODE_ERROR) return false;   // flat: error mode only
   if (c.verify_threads != 64 && c.verify_threads != 128 && c.verify_threads != 256) return false;
   if (c.trace_steps != 16 && c.trace_steps != 32 && c.trace_steps != 64) return false;
   if (c.trace_blocks < 0 || c.trace_blocks > 16) return false;
@@ -659,7 +656,7 @@ int enqueue_frame(pv_batch* b, cudaStream_t st, bool vis, const pv_batch_config&
   k_b_frame_top<<<n, 32, 0, st>>>(b->d_scenes, b->d_frames);
   mark(1);
   const int ti = thread_index(c.verify_threads);
-  verify_kernel(vis, b->exact, c.verify_mapping == 1)<<<b->n_vtiles[ti], c.verify_threads, 0, st>>>(
+  verify_kernel(vis, b->exact, c.verify_mapping)<<<b->n_vtiles[ti], c.verify_threads, 0, st>>>(
       b->d_scenes, b->d_frames, b->d_vtab[ti]);
   mark(2);
   if (b->fused) {                             // compaction of what verify marked, then Alg. 1 + re-trace
@@ -745,7 +742,7 @@ std::vector<pv_batch_config> phase_candidates(const pv_batch* b, uint32_t phase)
           if (config_valid(b, c)) out.push_back(c);
         }
   } else {                                    // verify: mapping and tile size
-    for (int mapping : {0, 1})
+    for (int mapping : {0, 1, 2})
       for (int threads : {64, 128, 256}) {
         pv_batch_config c = base;
         c.verify_mapping = mapping;

@@ -114,6 +114,7 @@ def _run(lanes, batch, frames, mode, tau, flags, traversal_counters=True, lists=
 CONFIGS = [
     {},
     {"verify_mapping": 1},
+    {"verify_mapping": 2, "verify_threads": 64},
     {"verify_threads": 64, "trace_steps": 16},
     {"verify_threads": 128, "trace_steps": 32, "trace_blocks": 2},
     {"stack": 64},
@@ -126,7 +127,7 @@ def test_batch_matches_single_scene_calls(cfg):
     b = pv.pv_batch_create([ln.item() for ln in lanes], pv.PV_MODE_ERROR, 0.01)
     if cfg:
         pv.pv_batch_set_config(b, **cfg)
-    _run(lanes, b, range(2, 7), pv.PV_MODE_ERROR, 0.01, 0, traversal_counters=cfg.get("verify_mapping", 0) == 0)
+    _run(lanes, b, range(2, 7), pv.PV_MODE_ERROR, 0.01, 0, traversal_counters=cfg.get("verify_mapping", 0) != 1)
     pv.pv_batch_destroy(b)
     for ln in lanes:
         ln.close()
@@ -139,7 +140,17 @@ def test_batch_modes_match_single_scene_calls(mode, flags, mapping):
     lanes = [Lane(sc, 3 + i) for i, sc in enumerate(_mix()[:4])]
     b = pv.pv_batch_create([ln.item() for ln in lanes], mode, 0.01, flags)
     pv.pv_batch_set_config(b, verify_mapping=mapping)
-    _run(lanes, b, range(2, 5), mode, 0.01, flags, traversal_counters=mapping == 0)
+    _run(lanes, b, range(2, 5), mode, 0.01, flags, traversal_counters=mapping != 1)
+    pv.pv_batch_destroy(b)
+    for ln in lanes:
+        ln.close()
+
+
+def test_batch_flat_mapping_error_exact_matches_single_scene_calls():
+    lanes = [Lane(sc, 5 + i) for i, sc in enumerate(_mix()[:4])]
+    b = pv.pv_batch_create([ln.item() for ln in lanes], pv.PV_MODE_ERROR, 0.01, pv.PV_FLAG_ERROR_EXACT)
+    pv.pv_batch_set_config(b, verify_mapping=2)
+    _run(lanes, b, range(2, 5), pv.PV_MODE_ERROR, 0.01, pv.PV_FLAG_ERROR_EXACT)
     pv.pv_batch_destroy(b)
     for ln in lanes:
         ln.close()
@@ -153,7 +164,7 @@ def test_fused_batch_matches_single_scene_calls(cfg):
     b = pv.pv_batch_create([ln.item(lists=False) for ln in lanes], pv.PV_MODE_ERROR, 0.01)
     if cfg:
         pv.pv_batch_set_config(b, **cfg)
-    _run(lanes, b, range(2, 7), pv.PV_MODE_ERROR, 0.01, 0, traversal_counters=cfg.get("verify_mapping", 0) == 0,
+    _run(lanes, b, range(2, 7), pv.PV_MODE_ERROR, 0.01, 0, traversal_counters=cfg.get("verify_mapping", 0) != 1,
          lists=False)
     pv.pv_batch_destroy(b)
     for ln in lanes:
@@ -173,7 +184,7 @@ def test_fused_batch_modes_and_tuner(mode, flags):
     times = pv.pv_batch_step_times(b)
     assert times[2] < 0.02 and times[4] > 0.0          # no separate continuation kernel: only event spacing
     cfg = pv.pv_batch_get_config(b)
-    _run(lanes, b, range(f, f + 3), mode, 0.01, flags, traversal_counters=cfg["verify_mapping"] == 0, lists=False)
+    _run(lanes, b, range(f, f + 3), mode, 0.01, flags, traversal_counters=cfg["verify_mapping"] != 1, lists=False)
     pv.pv_batch_destroy(b)
     for ln in lanes:
         ln.close()
@@ -202,10 +213,10 @@ def test_batch_autotune_then_graph():
         f += 1
         assert f < 60
     cfg = pv.pv_batch_get_config(b)
-    assert cfg["verify_mapping"] in (0, 1) and cfg["trace_steps"] in (16, 32, 64) and cfg["stack"] in (32, 64)
+    assert cfg["verify_mapping"] in (0, 1, 2) and cfg["trace_steps"] in (16, 32, 64) and cfg["stack"] in (32, 64)
     times = pv.pv_batch_step_times(b)
     assert len(times) == 5 and all(t >= 0 for t in times)
-    _run(lanes, b, range(f, f + 3), pv.PV_MODE_ERROR, 0.01, 0, traversal_counters=cfg["verify_mapping"] == 0)
+    _run(lanes, b, range(f, f + 3), pv.PV_MODE_ERROR, 0.01, 0, traversal_counters=cfg["verify_mapping"] != 1)
     pv.pv_batch_destroy(b)
     for ln in lanes:
         ln.close()
@@ -257,7 +268,12 @@ def test_batch_argument_errors():
     hr = gu.lib_scene(sc, flags=pv.PV_BUILD_DYN_REBUILD)
     with pytest.raises(pv.PvError):                   # rebuild mode cannot be replayed
         pv.pv_batch_create([(hr, P, lst, cnt, None, 1)], pv.PV_MODE_ERROR, 0.01)
+    bn = pv.pv_batch_create([(h, P, lst, cnt, None, 1)], pv.PV_MODE_NAIVE_AABB, 0.01)
+    with pytest.raises(pv.PvError):                   # the flat mapping serves error mode only
+        pv.pv_batch_set_config(bn, verify_mapping=2)
+    pv.pv_batch_destroy(bn)
     b = pv.pv_batch_create([(h, P, lst, cnt, None, 1)], pv.PV_MODE_ERROR, 0.01)
+    pv.pv_batch_set_config(b, verify_mapping=2)
     with pytest.raises(pv.PvError):
         pv.pv_batch_set_config(b, trace_steps=5)
     with pytest.raises(pv.PvError):
