@@ -266,10 +266,12 @@ int pv_stage_timing(pv_scene* s, uint32_t n);
 
 /* Milliseconds of the recorded calls, oldest first, four per call (``ms``
  * holds 4 n floats): [0] verification (k_verify), [1] what runs between it
- * and the re-trace kernel (the compaction; without fusion also the
- * continuation and the distribution-map steps), [2] the re-trace kernel
- * (with fusion: Alg. 1 and the re-trace), [3] the whole call.  *count
- * receives the number of calls recorded (at most n).  Waits for the events. */
+ * and the re-trace kernel (nothing with fusion, where k_verify appends the
+ * re-trace list itself; otherwise the continuation, the distribution-map
+ * steps and the compaction), [2] the re-trace kernel (with fusion: Alg. 1,
+ * the re-trace and, for pv_verify_retrace_deposit, the deposit), [3] the
+ * whole call.  *count receives the number of calls recorded (at most n).
+ * Waits for the events. */
 int pv_stage_times(pv_scene* s, float* ms, uint32_t* count);
 
 /* Baseline of Sec. 5: re-trace every path from the light (no reuse). */

@@ -94,7 +94,8 @@ ContArgs cont_args(pv_scene* s, const pv_paths* paths, const pv_verify_params* p
 // Work counters reset, DM_C of moved lights with a map cleared, then k_verify
 // (Sec. 3.1 + 3.2).  ``cont``: Alg. 1 has paths to look at this frame.
 int launch_verify(pv_scene* s, const pv_paths* paths, const pv_verify_params* params, pv_frame_stats* d_stats,
-                  const SceneView& sv, const FrameLights& L, cudaStream_t st, bool& cont, uint8_t* touched = nullptr) {
+                  const SceneView& sv, const FrameLights& L, cudaStream_t st, bool& cont, uint8_t* touched = nullptr,
+                  bool direct_list = false) {
   const uint32_t n = paths->n;
   if (cudaMemsetAsync(s->ws_ctr, 0, 16 * sizeof(uint32_t), st) != cudaSuccess) return PV_ERR_CUDA;
   for (uint32_t l = 0; l < s->n_lights; ++l)       // DM_C of moved lights with a map is counted afresh
@@ -115,6 +116,8 @@ int launch_verify(pv_scene* s, const pv_paths* paths, const pv_verify_params* pa
   A.cont_count = s->ws_ctr + pvh::CTR_ALL;
   A.stats = d_stats;
   A.touched = touched;
+  A.list_out = direct_list ? s->ws_list : nullptr;           // the marked paths, appended (no compaction)
+  A.list_count = direct_list ? s->ws_ctr + pvh::CTR_LIST : nullptr;
   if (n) {
     bool point_vis = false;
     for (uint32_t l = 0; l < s->n_lights; ++l)
@@ -180,8 +183,10 @@ int verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params* p
     return PV_ERR_CUDA;
   // with maps, prune and fill need Alg. 1's final answer for every path before the list is made
   const bool fuse_deposit = atlas && !s->has_dm;
+  const bool will_cont = paths->n && params->mode == PV_MODE_ERROR && (s->moved || L.moved_mask);
+  const bool fused = (will_cont || fuse_deposit) && !s->has_dm;
   bool cont = false;
-  if ((rc = launch_verify(s, paths, params, d_stats, sv, L, st, cont, fuse_deposit ? s->ws_touched : nullptr)) !=
+  if ((rc = launch_verify(s, paths, params, d_stats, sv, L, st, cont, fuse_deposit ? s->ws_touched : nullptr, fused)) !=
       PV_OK)
     return rc;
   mark(1);
@@ -189,9 +194,8 @@ int verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params* p
   uint32_t* const list = s->ws_list;
   uint32_t* const count = s->ws_ctr + pvh::CTR_LIST;
   uint32_t* const listed = d_stats ? &d_stats->n_listed : nullptr;
-  if ((cont || fuse_deposit) && !s->has_dm) {
-    // the paths k_verify marked, then Alg. 1, the re-trace (and the deposit) in one persistent kernel
-    pvh::launch_compact(s, paths->info, paths->n, list, count, listed, st);
+  if (fused) {
+    // k_verify appended the paths it marked; then Alg. 1, the re-trace (and the deposit) in one kernel
     mark(2);
     pvh::launch_cont_trace(s, paths, C, list, count, params->seed, params->frame, d_stats,
                            fuse_deposit ? atlas : nullptr, s->ws_touched, st);

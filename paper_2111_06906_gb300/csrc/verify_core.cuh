@@ -26,6 +26,8 @@ struct VerifyArgs {
   uint32_t* cont_count;
   pv_frame_stats* stats;
   uint8_t* touched;            // optional [n]: 1 for a path this frame re-traces or hands to Alg. 1, else 0
+  uint32_t* list_out;          // optional: the paths marked for re-tracing are appended here (unordered),
+  uint32_t* list_count;        // counted here and in stats->n_listed (instead of a compaction)
 };
 
 // Closed segment a + s (b - a), s in [0,1], against a closed box: slab test
@@ -160,7 +162,7 @@ struct VerifySmem {
   float cull[kMaxDyn * 6];
   float uni[(kMaxDyn + 1) * 6];
   GroupSmem groups;
-  uint32_t red[32 * 6];
+  uint32_t red[32 * 7];
   unsigned long long red64[32];
   int mslot[kMaxDyn];          // moved slots in ascending order (warp mapping)
   int n_moved;
@@ -318,25 +320,33 @@ __device__ __forceinline__ void verify_smem_init(const SceneView& sv, VerifySmem
 }
 
 // Block epilogue: continuation list (one atomic per warp) and counters.
-__device__ __forceinline__ void verify_epilogue(const VerifyArgs& A, uint32_t p, bool want_cont, uint32_t c_tested,
-                                                uint32_t c_vis, uint32_t c_reemit, uint32_t c_tail, const Work& wk,
-                                                bool traversed, VerifySmem& sm) {
-  const unsigned wm = __ballot_sync(0xffffffffu, want_cont);
-  if (wm) {
-    const int lane = threadIdx.x & 31, leader = __ffs(wm) - 1;
-    uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(A.cont_count, (uint32_t)__popc(wm));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (want_cont) A.cont_list[base + __popc(wm & ((1u << lane) - 1u))] = p;
-  }
-  uint32_t* const ctr[6] = {field(A.stats, offsetof(pv_frame_stats, n_paths)),
+// Append the calling lanes' paths with ``want`` set to list[count] (one
+// atomic per warp).
+__device__ __forceinline__ void warp_append(bool want, uint32_t p, uint32_t* list, uint32_t* count) {
+  const unsigned wm = __ballot_sync(0xffffffffu, want);
+  if (!wm) return;
+  const int lane = threadIdx.x & 31, leader = __ffs(wm) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(wm));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (want) list[base + __popc(wm & ((1u << lane) - 1u))] = p;
+}
+
+__device__ __forceinline__ void verify_epilogue(const VerifyArgs& A, uint32_t p, bool want_cont, bool listed,
+                                                uint32_t c_tested, uint32_t c_vis, uint32_t c_reemit, uint32_t c_tail,
+                                                const Work& wk, bool traversed, VerifySmem& sm) {
+  warp_append(want_cont, p, A.cont_list, A.cont_count);
+  if (A.list_out) warp_append(listed, p, A.list_out, A.list_count);
+  uint32_t* const ctr[7] = {field(A.stats, offsetof(pv_frame_stats, n_paths)),
                             field(A.stats, offsetof(pv_frame_stats, segments_tested)),
                             field(A.stats, offsetof(pv_frame_stats, vis_rays)),
                             field(A.stats, offsetof(pv_frame_stats, n_reemit)),
                             field(A.stats, offsetof(pv_frame_stats, n_tail)),
-                            field(A.stats, offsetof(pv_frame_stats, n_cont))};
-  const uint32_t val[6] = {p < A.n ? 1u : 0u, c_tested, c_vis, c_reemit, c_tail, want_cont ? 1u : 0u};
-  block_add_n<6>(ctr, val, sm.red);
+                            field(A.stats, offsetof(pv_frame_stats, n_cont)),
+                            A.list_out ? field(A.stats, offsetof(pv_frame_stats, n_listed)) : nullptr};
+  const uint32_t val[7] = {p < A.n ? 1u : 0u, c_tested, c_vis, c_reemit, c_tail, want_cont ? 1u : 0u,
+                           listed ? 1u : 0u};
+  block_add_n<7>(ctr, val, sm.red);
   if (traversed) {
     block_add64(A.stats ? (unsigned long long*)&A.stats->node_visits : nullptr, wk.nodes, sm.red64);
     block_add64(A.stats ? (unsigned long long*)&A.stats->tri_tests : nullptr, wk.tris, sm.red64);
@@ -359,7 +369,7 @@ __device__ __forceinline__ void verify_block(const SceneView& sv, const FrameLig
   const uint32_t n = A.n;
   const bool test_old = kExact && (A.flags & PV_FLAG_TEST_OLD_TRIS) != 0;
   uint32_t c_tested = 0, c_vis = 0, c_reemit = 0, c_tail = 0;
-  bool want_cont = false, touched = false;
+  bool want_cont = false, touched = false, listed = false;
   if (p < n) {
     const PathCheck v = origin_stage<kPointVis, S>(sv, L, A, root, p, c_vis, c_reemit, wk);
     if (v.test) {
@@ -386,10 +396,12 @@ __device__ __forceinline__ void verify_block(const SceneView& sv, const FrameLig
       }
       want_cont = finish_stage(A, p, v, mask, c_reemit, c_tail);
       touched = mask != 0;                   // handed to Alg. 1, or (naive modes) marked for re-tracing
+      listed = mask != 0 && A.mode != PV_MODE_ERROR;
     }
     if (A.touched) A.touched[p] = (touched || v.replaced) ? 1 : 0;
+    listed = listed || v.replaced;
   }
-  verify_epilogue(A, p, want_cont, c_tested, c_vis, c_reemit, c_tail, wk, kPointVis || kExact, sm);
+  verify_epilogue(A, p, want_cont, listed, c_tested, c_vis, c_reemit, c_tail, wk, kPointVis || kExact, sm);
 }
 
 // Warp per path: each lane runs the origin stage of its own path, then the
@@ -467,7 +479,8 @@ __device__ __forceinline__ void verify_block_warp(const SceneView& sv, const Fra
   bool want_cont = false;
   if (p < n && v.test) want_cont = finish_stage(A, p, v, my_mask, c_reemit, c_tail);
   if (p < n && A.touched) A.touched[p] = ((v.test && my_mask != 0) || v.replaced) ? 1 : 0;
-  verify_epilogue(A, p, want_cont, c_tested, c_vis, c_reemit, c_tail, wk, kPointVis || kExact, sm);
+  const bool listed = p < n && (v.replaced || (v.test && my_mask != 0 && !error_mode));
+  verify_epilogue(A, p, want_cont, listed, c_tested, c_vis, c_reemit, c_tail, wk, kPointVis || kExact, sm);
 }
 
 struct ContArgs {
@@ -721,7 +734,8 @@ __device__ __forceinline__ void verify_block_flat(const SceneView& sv, const Fra
   } else if (p < n && A.touched) {
     A.touched[p] = v.replaced ? 1 : 0;
   }
-  verify_epilogue(A, p, want_cont, c_tested, c_vis, c_reemit, c_tail, wk, kPointVis || kExact, sm);
+  verify_epilogue(A, p, want_cont, p < n && v.replaced, c_tested, c_vis, c_reemit, c_tail, wk, kPointVis || kExact,
+                  sm);
 }
 
 }  // namespace pvk
