@@ -434,7 +434,7 @@ def time_splat(pv, h, P, sc, K, W, stream, dev):
     Wd, Hd = 1920, 1080
     cam = pv.PvCamera.make(pos, target, (0.0, 1.0, 0.0), math.radians(60.0), Wd, Hd)
     img = torch.zeros(Hd, Wd, 3, dtype=torch.float32, device=dev)
-    work = torch.empty(pv.pv_splat_workspace_bytes(Wd, Hd), dtype=torch.uint8, device=dev)
+    work = torch.empty(pv.pv_splat_workspace_bytes(h, Wd, Hd), dtype=torch.uint8, device=dev)
     ms = []
     for i in range(W + K):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]

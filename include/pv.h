@@ -383,18 +383,21 @@ int pv_read_device_status(pv_scene* s);
  *   rho / pi * E * 2 (1 - s^2) / (pi r^2),   s = |p - x| / radius < 1
  * to the pixel (the kernel integrates to 1 over a plane).  A photon whose
  * kernel cube reaches within 1e-3 scene diagonals of the camera plane is
- * skipped.  d_image: float32 [height][width][3] device memory, cleared and
- * written.  d_work: pv_splat_workspace_bytes(width, height) bytes of
- * 16-byte-aligned device memory (the per-pixel visible points).  PV_ERR_ARG
- * for a degenerate camera (zero size, fov outside (0, 3.1), up parallel to the
- * view direction), radius <= 0, or a small or misaligned workspace. */
+ * skipped.  Evaluated as a gather over a hashed grid of the photons, so the
+ * sum's order within a pixel is not fixed.  d_image: float32
+ * [height][width][3] device memory, written.  d_work:
+ * pv_splat_workspace_bytes(s, width, height) bytes of 256-byte-aligned
+ * device memory (visible points, photon grid).  PV_ERR_ARG for a degenerate
+ * camera (zero size, fov outside (0, 3.1), up parallel to the view
+ * direction), radius <= 0, or a small or misaligned workspace; PV_ERR_LIMIT
+ * for more than 2^27 paths. */
 typedef struct {
   float pos[3], target[3], up[3];
   float fov_y;
   uint32_t width, height;
 } pv_camera;
 
-size_t pv_splat_workspace_bytes(uint32_t width, uint32_t height);
+size_t pv_splat_workspace_bytes(const pv_scene* s, uint32_t width, uint32_t height);
 int pv_splat(pv_scene* s, const pv_paths* paths, const pv_camera* cam, float radius, float* d_image, void* d_work,
              size_t work_bytes, void* stream);
 

@@ -147,7 +147,7 @@ def load():
         L.pv_batch_step_times.argtypes = [P, P]
         L.pv_batch_destroy.argtypes = [P]
         L.pv_distribution_map_cells.argtypes = [P, C.c_uint32]
-        L.pv_splat_workspace_bytes.argtypes = [C.c_uint32, C.c_uint32]
+        L.pv_splat_workspace_bytes.argtypes = [P, C.c_uint32, C.c_uint32]
         L.pv_splat_workspace_bytes.restype = C.c_size_t
         L.pv_splat.argtypes = [P, C.POINTER(PvPaths), C.POINTER(PvCamera), C.c_float, P, P, C.c_size_t, P]
         L.pv_read_distribution_map.argtypes = [P, C.c_uint32, P]
@@ -519,8 +519,8 @@ def pv_batch_destroy(batch: Batch) -> None:
         batch.handle = None
 
 
-def pv_splat_workspace_bytes(width: int, height: int) -> int:
-    return int(load().pv_splat_workspace_bytes(int(width), int(height)))
+def pv_splat_workspace_bytes(scene, width: int, height: int) -> int:
+    return int(load().pv_splat_workspace_bytes(scene, int(width), int(height)))
 
 
 def pv_splat(scene, paths: Paths, cam: PvCamera, radius: float, image, work, stream=None) -> None:

@@ -56,7 +56,7 @@ def test_splat_matches_oracle(name):
     gu.upload(P, op)
     cam = pv.PvCamera.make(pos, target, up, math.radians(60.0), W, H)
     img = torch.zeros(H, W, 3, dtype=torch.float32, device="cuda")
-    work = torch.empty(pv.pv_splat_workspace_bytes(W, H), dtype=torch.uint8, device="cuda")
+    work = torch.empty(pv.pv_splat_workspace_bytes(h, W, H), dtype=torch.uint8, device="cuda")
     pv.pv_splat(h, P, cam, radius, img, work)
     got = img.cpu().numpy().astype(np.float64)
     ok = ~amb
@@ -74,7 +74,7 @@ def test_splat_argument_errors():
     h = gu.lib_scene(sc)
     P = pv.Paths.allocate(sc.n_paths, sc.max_bounces)
     img = torch.zeros(10, 10, 3, device="cuda")
-    work = torch.empty(pv.pv_splat_workspace_bytes(10, 10), dtype=torch.uint8, device="cuda")
+    work = torch.empty(pv.pv_splat_workspace_bytes(h, 10, 10), dtype=torch.uint8, device="cuda")
     good = ((0.0, 1.0, 0.9), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0))
     for cam, r, wk in [(pv.PvCamera.make(*good, 1.0, 10, 10), 0.0, work),
                        (pv.PvCamera.make(*good, 0.0, 10, 10), 0.1, work),
@@ -87,7 +87,7 @@ def test_splat_argument_errors():
 
 def test_splat_full_hd_city():
     """1920 x 1080 splat of the city's 1M traced paths: finite, non-negative,
-    lit, and repeatable up to the order of the float atomics."""
+    lit, and repeatable up to the order of each pixel's sum."""
     torch = _torch()
     sc = scenes.city()
     h = gu.lib_scene(sc)
@@ -95,7 +95,7 @@ def test_splat_full_hd_city():
     pv.pv_trace_all(h, P, 5, 1)
     W, H = 1920, 1080
     cam = pv.PvCamera.make((0.0, 45.0, 35.0), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), math.radians(60.0), W, H)
-    work = torch.empty(pv.pv_splat_workspace_bytes(W, H), dtype=torch.uint8, device="cuda")
+    work = torch.empty(pv.pv_splat_workspace_bytes(h, W, H), dtype=torch.uint8, device="cuda")
     a = torch.zeros(H, W, 3, device="cuda")
     b = torch.zeros(H, W, 3, device="cuda")
     pv.pv_splat(h, P, cam, 0.3, a, work)
