@@ -164,6 +164,29 @@ def test_fused_deposit_without_motion_and_with_distribution_map():
         p.close()
 
 
+@pytest.mark.parametrize("B", [1, 15])
+def test_fused_deposit_bounce_caps(B):
+    """The shortest and the longest stored paths (1 and 15 bounces) through the fused deposit call."""
+    torch = _torch()
+    sc = kit.box_with_torus(3000, B=B)
+    p = Pair(sc, 43)
+    a1, rect, scale = _atlas(sc, 64)
+    a2 = torch.zeros_like(a1)
+    for f in range(2, 5):
+        s1, s2 = pv.new_stats(), pv.new_stats()
+        for h in (p.h1, p.h2):
+            gu.advance(h, sc, f)
+        pv.pv_verify_paths(p.h1, p.P1, pv.PV_MODE_ERROR, 0.01, 0, p.lst, p.cnt, s1, seed=p.seed, frame=f)
+        pv.pv_retrace_invalid(p.h1, p.P1, p.lst, p.cnt, p.seed, f, s1)
+        pv.pv_deposit(p.h1, p.P1, a1, rect, scale)
+        pv.pv_verify_retrace_deposit(p.h2, p.P2, pv.PV_MODE_ERROR, 0.01, 0, p.seed, f, a2, rect, scale, s2)
+        p.compare(pv.stats_dict(s1), pv.stats_dict(s2))
+        assert torch.equal(a1, a2)
+    L = (p.P2.info.cpu().numpy().view(np.uint32) >> 22) & 15
+    assert L.max() <= B and (B == 1 or L.max() > 4)
+    p.close()
+
+
 def test_fused_frame_with_distribution_map_matches_separate_calls():
     sc = kit.rect_light_over_floor(2560, shift=lambda f: (0.11 * (f - 1), 0.0, 0.07 * (f - 1)), B=2, R=3.0)
     p = Pair(sc, 23, dm_rect=(4, 4, 4, 4))

@@ -224,8 +224,48 @@ def _sampled_full_size(sc, n_sample, mode=2, tau=0.01, frames=(1, 2)):
     pv.pv_destroy_scene(h)
 
 
+def _sampled_full_size_fused(sc, n_sample, tau=0.01):
+    """The benchmark's call at full size: pv_update_dynamic + pv_verify_retrace_deposit (Alg. 1, re-trace
+    and deposit in one kernel) on sampled paths against the oracle, and its atlas against pv_deposit of
+    the same records (bit for bit)."""
+    torch = _t()
+    h = gu.lib_scene(sc)
+    P = pv.Paths.allocate(sc.n_paths, sc.max_bounces)
+    pv.pv_trace_all(h, P, sc.seed, 1)
+    ids = np.sort(np.random.default_rng(7).choice(sc.n_paths, n_sample, replace=False)).astype(np.uint32)
+    o = oracle.OracleScene(sc)
+    o.set_frames(1, 1)
+    op = o.trace(ids, sc.seed, 1)
+    gu.assert_parity(gu.compare(gu.download(P, ids), op, sc.diag))
+    gu.advance(h, sc, 2)
+    A = 1024
+    atlas = torch.zeros(A, A, 3, dtype=torch.int64, device="cuda")
+    st = pv.new_stats()
+    pv.pv_verify_retrace_deposit(h, P, 2, tau, 0, sc.seed, 2, atlas, sc.atlas_rect, 40, st)
+    o.set_frames(1, 2)
+    q = op.copy()
+    o.verify(q, 2, tau)
+    o.retrace(q, sc.seed, 2)
+    r = gu.compare(gu.download(P, ids), q, sc.diag)
+    print("fused", r, pv.stats_dict(st))
+    gu.assert_parity(r)
+    ref = torch.zeros_like(atlas)
+    pv.pv_deposit(h, P, ref, sc.atlas_rect, 40)
+    assert torch.equal(atlas, ref)
+    assert pv.pv_read_device_status(h) == 0
+    pv.pv_destroy_scene(h)
+
+
 def test_city_full_size_sampled():
     _sampled_full_size(scenes.city(), 1500)
+
+
+def test_city_full_size_fused_sampled():
+    _sampled_full_size_fused(scenes.city(), 1500)
+
+
+def test_villa_full_size_fused_sampled():
+    _sampled_full_size_fused(scenes.villa(), 240)
 
 
 def test_villa_full_size_sampled():
