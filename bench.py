@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-dm", action="store_true", help="skip the distribution-map frame measurement")
     ap.add_argument("--no-splat", action="store_true", help="skip the 1920x1080 screen-space splat measurement")
-    ap.add_argument("--tune-frames", type=int, default=1, help="batch16: frames per tuner candidate")
+    ap.add_argument("--tune-frames", type=int, default=3, help="batch16: frames per tuner candidate")
     ap.add_argument("--build-flags", type=int, default=0, help="pv_scene_desc flags (2: Morton-code static tree)")
     return ap.parse_args()
 
@@ -196,7 +196,7 @@ def run_ours(args, ws, rank, local):
     tau = sc.tau if args.tau is None else args.tau
     seed = sc.seed + 7919 * rank
     N, B = sc.n_paths, sc.max_bounces
-    frames_needed = 4 * (args.warmup + args.steps) + 8     # reuse, separate calls, trace-all, end to end
+    frames_needed = args.warmup + args.steps + 2      # every loop restarts at frame 1: the same frames timed
     xfs = {f: sc.xforms(f) for f in range(1, frames_needed + 1)}
     lts = {f: sc.lights(f) for f in range(1, frames_needed + 1)}
 
@@ -214,12 +214,18 @@ def run_ours(args, ws, rank, local):
     stats = torch.zeros(4 * K + 2, pv.STATS_WORDS, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
-    pv.pv_trace_all(h, P, seed, 1)
-    frame = 1
+    def restart():
+        # back to the pose of frame 1 and a fresh bootstrap, so that every loop below runs frames 2, 3, ...
+        pv.pv_update_dynamic(h, xfs[1], lts[1])
+        pv.pv_trace_all(h, P, seed, 1)
+        return 1
 
-    def reuse_frame(f, st):
+    frame = restart()
+
+    def reuse_frame(f, st, at=None):
         pv.pv_update_dynamic(h, xfs[f], lts[f])
-        pv.pv_verify_retrace_deposit(h, P, mode, tau, 0, seed, f, atlas, sc.atlas_rect, scale, st)
+        pv.pv_verify_retrace_deposit(h, P, mode, tau, 0, seed, f, atlas if at is None else at, sc.atlas_rect, scale,
+                                     st)
 
     def timed_loop(fn, first_frame, rows_a, rows_b):
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
@@ -258,32 +264,74 @@ def run_ours(args, ws, rank, local):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- reuse pipeline, one call from verification to re-trace (headline)
+    # ---- reuse pipeline, one call from verification to re-trace (headline): only the two events that bracket
+    # the K frames, nothing recorded between the library's launches
     for i in range(W):
         frame += 1
         reuse_frame(frame, stats[-1])
-    pv.pv_stage_timing(h, K)                   # the library records its stages' events in the timed frames
     barrier()
     clocks = Clocks(local)
     with clocks:
         start = torch.cuda.Event(enable_timing=True)
         stop = torch.cuda.Event(enable_timing=True)
         start.record(stream)
-        ev = timed_loop(fused_body, frame + 1, stats[:K], stats[K:2 * K])
+        for i in range(K):
+            reuse_frame(frame + 1 + i, stats[i])
         stop.record(stream)
         barrier()
     frame += K
     reuse_ms = start.elapsed_time(stop) / K
-    parts = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in ev])
-    reuse_parts = parts.mean(axis=0)
-    stage_ms = pv.pv_stage_times(h, K).mean(axis=0)     # k_verify, compaction, fused kernel, whole call
-    pv.pv_stage_timing(h, 0)
     st_reuse = [pv.stats_dict(stats[i]) for i in range(K)]
     info_np = P.info.cpu().numpy().view(np.uint32)
     mean_L = float(((info_np >> 22) & 15).mean())
     status = pv.pv_read_device_status(h)
 
+    # ---- the same frames again with events between the calls and the library's own stage events
+    frame = restart()
+    for i in range(W):
+        frame += 1
+        reuse_frame(frame, stats[-1])
+    pv.pv_stage_timing(h, K)                   # the library records its stages' events in the timed frames
+    barrier()
+    ev = timed_loop(fused_body, frame + 1, stats[K:2 * K], stats[K:2 * K])
+    barrier()
+    frame += K
+    reuse_parts = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in ev]).mean(axis=0)
+    stage_ms = pv.pv_stage_times(h, K).mean(axis=0)     # k_verify, compaction, fused kernel, whole call
+    pv.pv_stage_timing(h, 0)
+    instrumented_ms = float(np.mean([e[0].elapsed_time(e[4]) for e in ev]))
+    same = all(pv.stats_dict(stats[K + i]) == st_reuse[i] for i in range(K))
+
+    # ---- the same frames with the atlas carried from frame to frame (pv_verify_retrace_deposit_delta): only the
+    # paths a frame changes leave and re-enter it; the final atlas must equal the full deposit's
+    atlas_full = atlas.clone()
+    atlas_delta = torch.zeros_like(atlas)
+    frame = restart()
+    pv.pv_deposit(h, P, atlas_delta, sc.atlas_rect, scale)
+
+    def delta_frame(f, st):
+        pv.pv_update_dynamic(h, xfs[f], lts[f])
+        pv.pv_verify_retrace_deposit_delta(h, P, mode, tau, 0, seed, f, atlas_delta, sc.atlas_rect, scale, st)
+
+    for i in range(W):
+        frame += 1
+        delta_frame(frame, stats[-1])
+    barrier()
+    start4 = torch.cuda.Event(enable_timing=True)
+    stop4 = torch.cuda.Event(enable_timing=True)
+    start4.record(stream)
+    for i in range(K):
+        delta_frame(frame + 1 + i, stats[-1])
+    stop4.record(stream)
+    barrier()
+    frame += K
+    delta_ms = start4.elapsed_time(stop4) / K
+    delta_equal = bool(torch.equal(atlas_delta, atlas_full))
+    del atlas_full, atlas_delta
+
     # ---- the same frames through the separate calls (pv_verify_paths, then pv_retrace_invalid)
+    frame = restart()
+    stats[:2 * K].zero_()                      # counters accumulate
     for i in range(W):
         frame += 1
         pv.pv_update_dynamic(h, xfs[frame], lts[frame])
@@ -302,7 +350,8 @@ def run_ours(args, ws, rank, local):
     sep_parts = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in ev3]).mean(axis=0)
     st_retrace = [pv.stats_dict(stats[K + i]) for i in range(K)]
 
-    # ---- trace-all baseline (same library, same GPU)
+    # ---- trace-all baseline (same library, same GPU), on the same frames
+    frame = restart()
     for i in range(W):
         frame += 1
         pv.pv_update_dynamic(h, xfs[frame], lts[frame])
@@ -320,31 +369,51 @@ def run_ours(args, ws, rank, local):
     parts2 = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in ev2]).mean(axis=0)
     st_trace = [pv.stats_dict(stats[3 * K + i]) for i in range(K)]
 
-    # ---- end to end through the API: host poses in, atlas and stats out (pinned), every frame
+    # ---- end to end through the API: host poses in, atlas and stats out (pinned), every frame.  Two atlases
+    # alternate: frame i's result is copied to the host on a copy stream while frame i + 1 computes, and the
+    # host waits for frame i's copy before it launches frame i + 2
     e2e = None
     if not args.no_e2e:
-        host_atlas = torch.empty(A, A, 3, dtype=torch.int64, pin_memory=True)
-        host_stats = torch.empty(pv.STATS_WORDS, dtype=torch.int32, pin_memory=True)
-        # continue the reuse pipeline from a fresh bootstrap
-        pv.pv_trace_all(h, P, seed, frame)
+        atl = [atlas, torch.zeros_like(atlas)]
+        host_atlas = [torch.empty(A, A, 3, dtype=torch.int64, pin_memory=True) for _ in range(2)]
+        host_stats = [torch.empty(pv.STATS_WORDS, dtype=torch.int32, pin_memory=True) for _ in range(2)]
+        copy_stream = torch.cuda.Stream(device=dev)
+        done = [torch.cuda.Event(), torch.cuda.Event()]
+        copied = [None, None]
+
+        def e2e_frame(i, f):
+            b = i % 2
+            if copied[b] is not None:
+                copied[b].synchronize()           # the host has frame i - 2's result; its buffers are free
+                stream.wait_event(copied[b])
+            reuse_frame(f, stats[-1 - b], atl[b])
+            done[b].record(stream)
+            copy_stream.wait_event(done[b])
+            with torch.cuda.stream(copy_stream):
+                host_atlas[b].copy_(atl[b], non_blocking=True)
+                host_stats[b].copy_(stats[-1 - b], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(copy_stream)
+            copied[b] = ev
+
+        # the same frames as the device-timed loop, from a fresh bootstrap
+        frame = restart()
         for i in range(W):
             frame += 1
-            reuse_frame(frame, stats[-2])
-            host_atlas.copy_(atlas, non_blocking=True)
-            host_stats.copy_(stats[-2], non_blocking=True)
-            stream.synchronize()
+            e2e_frame(i, frame)
+        for ev in copied:
+            ev.synchronize()
         barrier()
         t = time.perf_counter()
         for i in range(K):
             frame += 1
-            reuse_frame(frame, stats[-2])
-            host_atlas.copy_(atlas, non_blocking=True)
-            host_stats.copy_(stats[-2], non_blocking=True)
-            stream.synchronize()
+            e2e_frame(i, frame)
+        for ev in copied:
+            ev.synchronize()
         e2e_s = (time.perf_counter() - t) / K
         h2d = 12 * 4 * int(sc.object_dynamic.sum()) + 64 * len(lts[1])
         e2e = {"value": None, "unit": "paths/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": int(host_atlas.numel() * 8 + host_stats.numel() * 4), "_s": e2e_s}
+               "d2h_bytes_per_step": int(host_atlas[0].numel() * 8 + host_stats[0].numel() * 4), "_s": e2e_s}
     # ---- differentiable model: forward splat and adjoint of an L2 atlas loss
     adjoint = None if args.no_adjoint else time_adjoint(pv, h, P, sc, N, A, K, W, stream, dev)
     # ---- screen-space splat of the current records at 1920 x 1080
@@ -387,6 +456,9 @@ def run_ours(args, ws, rank, local):
            "reuse_ms_per_frame": reuse_ms, "trace_all_ms_per_frame": trace_ms,
            "speedup_vs_trace_all": trace_ms / reuse_ms,
            "reuse_ms_parts": {"update": float(reuse_parts[0]), "verify_retrace_deposit": float(reuse_parts[1])},
+           "instrumented_ms_per_frame": instrumented_ms, "instrumented_counters_match": same,
+           "delta_deposit": {"call": "pv_verify_retrace_deposit_delta", "ms_per_frame": delta_ms,
+                             "paths_per_s": ws * N / (delta_ms * 1e-3), "atlas_equal_to_full_deposit": delta_equal},
            "verify_retrace_deposit_stages_ms": {"k_verify": float(stage_ms[0]), "compaction": float(stage_ms[1]),
                                                 "k_cont_trace+deposit": float(stage_ms[2]),
                                                 "call": float(stage_ms[3])},

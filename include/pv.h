@@ -256,7 +256,22 @@ int pv_verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params
 int pv_verify_retrace_deposit(pv_scene* s, const pv_paths* paths, const pv_verify_params* params,
                               const pv_atlas* atlas, pv_frame_stats* d_stats, void* stream);
 
-/* Stage timing of pv_verify_retrace and pv_verify_retrace_deposit (no paper
+/* pv_verify_retrace_deposit for an atlas that already holds pv_deposit of
+ * ``paths`` as they are on entry (same atlas rectangle, resolution and
+ * scale; e.g. pv_deposit after pv_trace_all, then this call every frame).
+ * The atlas is not cleared: each path the frame re-traces or hands to
+ * Alg. 1 has its entry photons taken out (the same fixed-point values,
+ * subtracted modulo 2^64) and its final photons added; untouched paths are
+ * not read.  Since the texel sums are integers, the atlas on return is the
+ * one pv_verify_retrace_deposit leaves, bit for bit, and records and
+ * counters are the same too.  With distribution maps the call clears the
+ * atlas and deposits every path, as pv_verify_retrace_deposit.  An atlas
+ * that does not hold the entry deposit gives an atlas that does not either
+ * (the error is carried, not detected).  Errors as pv_verify_retrace_deposit. */
+int pv_verify_retrace_deposit_delta(pv_scene* s, const pv_paths* paths, const pv_verify_params* params,
+                                    const pv_atlas* atlas, pv_frame_stats* d_stats, void* stream);
+
+/* Stage timing of pv_verify_retrace and the two deposit forms (no paper
  * counterpart).  With n > 0, each later call records four CUDA events on its
  * stream -- at its start, after k_verify, before its re-trace kernel, at its
  * end -- keeping the last n calls in a ring; n = 0 turns it off.  Creates (and destroys) events and
@@ -269,7 +284,7 @@ int pv_stage_timing(pv_scene* s, uint32_t n);
  * and the re-trace kernel (nothing with fusion, where k_verify appends the
  * re-trace list itself; otherwise the continuation, the distribution-map
  * steps and the compaction), [2] the re-trace kernel (with fusion: Alg. 1,
- * the re-trace and, for pv_verify_retrace_deposit, the deposit), [3] the
+ * the re-trace and, with an atlas, the deposit), [3] the
  * whole call.  *count receives the number of calls recorded (at most n).
  * Waits for the events. */
 int pv_stage_times(pv_scene* s, float* ms, uint32_t* count);

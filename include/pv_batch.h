@@ -20,8 +20,9 @@
  * every (segment, object) pair it tests.
  *
  * The tuner (pv_batch_autotune) runs the next frames eagerly with candidate
- * configurations, times each step with CUDA events, keeps the fastest
- * candidate per step and then captures the graph with it.
+ * configurations in two phases (re-trace parameters, then the verify
+ * mapping), times each step with CUDA events, keeps per phase the candidate
+ * whose whole frame is fastest and then captures the graph with it.
  */
 #ifndef PV_BATCH_H
 #define PV_BATCH_H
@@ -99,8 +100,10 @@ int pv_batch_frame(pv_batch* b, const float* const* xforms, const pv_light* cons
                    void* stream);
 
 /* Start tuning: the next frames run eagerly, frames_per_candidate frames per
- * candidate configuration (at least 1), then the fastest candidate per step
- * is kept and the graph is captured again.  PV_ERR_ARG for a null batch. */
+ * candidate configuration (at least 1), the candidates taken in turn (round
+ * robin, so frame-to-frame drift of the workload weighs on all of them
+ * alike); then the candidate with the fastest whole frame is kept and the
+ * graph is captured again.  PV_ERR_ARG for a null batch. */
 int pv_batch_autotune(pv_batch* b, uint32_t frames_per_candidate);
 
 /* 1 while tuning, 0 otherwise; negative status for a null batch. */

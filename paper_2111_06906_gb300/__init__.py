@@ -31,7 +31,7 @@ PV_INFO_NSEG_SHIFT, PV_INFO_START_SHIFT = 22, 26
 PV_INFO_REPLACE, PV_INFO_REUSE_LIGHT = 1 << 30, 1 << 31
 
 EXPORTS = ["pv_build_scene", "pv_update_dynamic", "pv_verify_paths", "pv_retrace_invalid", "pv_verify_retrace",
-           "pv_verify_retrace_deposit", "pv_stage_timing", "pv_stage_times", "pv_trace_all",
+           "pv_verify_retrace_deposit", "pv_verify_retrace_deposit_delta", "pv_stage_timing", "pv_stage_times", "pv_trace_all",
            "pv_compact_replace", "pv_compact_replace_static", "pv_deposit", "pv_set_traversal_limit",
            "pv_read_device_status", "pv_destroy_scene", "pv_status_string", "pv_theta_size", "pv_theta_current",
            "pv_model_deposit", "pv_adjoint_deposit", "pv_budget_list", "pv_batch_create", "pv_batch_frame",
@@ -122,6 +122,8 @@ def load():
         L.pv_verify_retrace.argtypes = [P, C.POINTER(PvPaths), C.POINTER(PvVerifyParams), P, P]
         L.pv_verify_retrace_deposit.argtypes = [P, C.POINTER(PvPaths), C.POINTER(PvVerifyParams), C.POINTER(PvAtlas),
                                                 P, P]
+        L.pv_verify_retrace_deposit_delta.argtypes = [P, C.POINTER(PvPaths), C.POINTER(PvVerifyParams),
+                                                      C.POINTER(PvAtlas), P, P]
         L.pv_stage_timing.argtypes = [P, C.c_uint32]
         L.pv_stage_times.argtypes = [P, P, P]
         L.pv_trace_all.argtypes = [P, C.POINTER(PvPaths), C.c_uint64, C.c_uint32, P, P]
@@ -334,6 +336,18 @@ def pv_verify_retrace_deposit(scene, paths: Paths, mode: int, tau: float, flags:
     a = _atlas(atlas, rect, scale_log2)
     _check("pv_verify_retrace_deposit", load().pv_verify_retrace_deposit(scene, C.byref(ps), C.byref(prm), C.byref(a),
                                                                           _ptr(d_stats), _stream(stream)))
+
+
+def pv_verify_retrace_deposit_delta(scene, paths: Paths, mode: int, tau: float, flags: int, seed: int, frame: int,
+                                    atlas, rect, scale_log2: int, d_stats=None, stream=None) -> None:
+    """pv_verify_retrace_deposit on an atlas that holds the deposit of the entry records (not cleared: the
+    touched paths' entry photons are taken out and their final photons added; same atlas bit for bit)."""
+    ps = paths.struct()
+    prm = PvVerifyParams(int(mode), float(tau), int(flags), int(frame), int(seed))
+    a = _atlas(atlas, rect, scale_log2)
+    _check("pv_verify_retrace_deposit_delta",
+           load().pv_verify_retrace_deposit_delta(scene, C.byref(ps), C.byref(prm), C.byref(a), _ptr(d_stats),
+                                                  _stream(stream)))
 
 
 def _rect(rect):

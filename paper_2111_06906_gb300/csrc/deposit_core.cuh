@@ -19,10 +19,12 @@ __device__ __forceinline__ int atlas_texel(float p, float lo, float hi, uint32_t
   return (int)f;
 }
 
-// The photons of path p (its info word's count, at most B) into the atlas.
-__device__ __forceinline__ void deposit_path(const pv_atlas& at, uint32_t n, uint32_t B, const uint32_t* info,
-                                             const float4* pa, const float4* pb, uint32_t p) {
-  const uint32_t L = min(info_nseg(__ldcs(info + p)), B);
+// The first L photons of path p into the atlas, added (kSub false) or taken
+// back out (kSub true: the same fixed-point values, negated modulo 2^64, so
+// that a deposit followed by its removal leaves every texel's sum as it was).
+template <bool kSub = false>
+__device__ __forceinline__ void deposit_rows(const pv_atlas& at, uint32_t n, uint32_t L, const float4* pa,
+                                             const float4* pb, uint32_t p) {
   for (uint32_t k = 0; k < L; ++k) {
     // streaming loads: the path buffers must not evict the atlas from L2
     const float4 x = __ldcs(pa + (size_t)k * n + p);
@@ -30,10 +32,18 @@ __device__ __forceinline__ void deposit_path(const pv_atlas& at, uint32_t n, uin
     const int tx = atlas_texel(x.x, at.x0, at.x1, at.width);
     const int tz = atlas_texel(x.z, at.z0, at.z1, at.height);
     unsigned long long* t = reinterpret_cast<unsigned long long*>(at.data) + 3 * ((size_t)tz * at.width + tx);
-    atomicAdd(t + 0, __float2ull_rn(ldexpf(e.x, at.scale_log2)));
-    atomicAdd(t + 1, __float2ull_rn(ldexpf(e.y, at.scale_log2)));
-    atomicAdd(t + 2, __float2ull_rn(ldexpf(e.z, at.scale_log2)));
+    const unsigned long long v[3] = {__float2ull_rn(ldexpf(e.x, at.scale_log2)),
+                                     __float2ull_rn(ldexpf(e.y, at.scale_log2)),
+                                     __float2ull_rn(ldexpf(e.z, at.scale_log2))};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) atomicAdd(t + c, kSub ? 0ull - v[c] : v[c]);
   }
+}
+
+// The photons of path p (its info word's count, at most B) into the atlas.
+__device__ __forceinline__ void deposit_path(const pv_atlas& at, uint32_t n, uint32_t B, const uint32_t* info,
+                                             const float4* pa, const float4* pb, uint32_t p) {
+  deposit_rows<false>(at, n, min(info_nseg(__ldcs(info + p)), B), pa, pb, p);
 }
 
 }  // namespace pvk

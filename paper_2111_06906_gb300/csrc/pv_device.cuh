@@ -255,6 +255,19 @@ __device__ __forceinline__ WNodeRay load_wnode_ray(const WNode* nodes, int i, co
   return n;
 }
 
+// Three-input minimum / maximum: one instruction on sm_100 and later, with the
+// NaN rule of fminf / fmaxf (a NaN operand is ignored unless all are NaN).
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
 // The four child boxes of a wide node against the ray within [tmin, tmax]:
 // entry distances, hit mask (bit c = child c).  For a box with lo <= hi the
 // near plane's distance is exactly the smaller of the two slab distances
@@ -267,9 +280,9 @@ __device__ __forceinline__ uint32_t box4(const Ray& r, float tmax, const WNodeRa
   uint32_t mask = 0;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const float tn = fmaxf(fmaxf(fmaf(nx[c], r.inv.x, r.ooi.x), fmaf(ny[c], r.inv.y, r.ooi.y)),
+    const float tn = fmax3(fmaf(nx[c], r.inv.x, r.ooi.x), fmaf(ny[c], r.inv.y, r.ooi.y),
                            fmaxf(fmaf(nz[c], r.inv.z, r.ooi.z), r.tmin));
-    const float tf = fminf(fminf(fmaf(fx[c], r.inv.x, r.ooi.x), fmaf(fy[c], r.inv.y, r.ooi.y)),
+    const float tf = fmin3(fmaf(fx[c], r.inv.x, r.ooi.x), fmaf(fy[c], r.inv.y, r.ooi.y),
                            fminf(fmaf(fz[c], r.inv.z, r.ooi.z), tmax));
     t[c] = tn;
     mask |= (tn <= tf ? 1u : 0u) << c;
@@ -282,8 +295,8 @@ __device__ __forceinline__ bool box1(const Ray& r, float tmax, const float* bx, 
   const float x0 = fmaf(bx[0], r.inv.x, r.ooi.x), x1 = fmaf(bx[3], r.inv.x, r.ooi.x);
   const float y0 = fmaf(bx[1], r.inv.y, r.ooi.y), y1 = fmaf(bx[4], r.inv.y, r.ooi.y);
   const float z0 = fmaf(bx[2], r.inv.z, r.ooi.z), z1 = fmaf(bx[5], r.inv.z, r.ooi.z);
-  tenter = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), r.tmin));
-  const float e = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tmax));
+  tenter = fmax3(fminf(x0, x1), fminf(y0, y1), fmaxf(fminf(z0, z1), r.tmin));
+  const float e = fmin3(fmaxf(x0, x1), fmaxf(y0, y1), fminf(fmaxf(z0, z1), tmax));
   return tenter <= e;
 }
 

@@ -154,10 +154,11 @@ void launch_compact(pv_scene* s, const uint32_t* info, uint32_t n, uint32_t* lis
 void launch_trace(pv_scene* s, const pv_paths* p, const uint32_t* list, const uint32_t* count, uint64_t seed,
                   uint32_t frame, pv_frame_stats* stats, cudaStream_t st);
 // Alg. 1 over the continuation list C fused with the re-trace of ``list``;
-// with an atlas, every path is also deposited (touched: verification's marks)
+// with an atlas, every path is also deposited (touched: verification's marks;
+// delta: the atlas holds the entry records' deposit, only listed paths change it)
 void launch_cont_trace(pv_scene* s, const pv_paths* p, const pvk::ContArgs& C, const uint32_t* list,
                        const uint32_t* count, uint64_t seed, uint32_t frame, pv_frame_stats* stats,
-                       const pv_atlas* atlas, const uint8_t* touched, cudaStream_t st);
+                       const pv_atlas* atlas, const uint8_t* touched, bool delta, cudaStream_t st);
 // deposit.cu: argument checks of an atlas, and the plain deposit of every path
 int check_atlas(const pv_atlas* a);
 void launch_deposit(pv_scene* s, const pv_paths* p, const pv_atlas* a, cudaStream_t st);

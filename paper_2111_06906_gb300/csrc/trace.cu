@@ -131,9 +131,17 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS) k_tra
 // lanes that have no more rays to trace.  Every path is deposited once, by
 // the same per-photon arithmetic as k_deposit, into integer sums: the atlas
 // is the same bit for bit.
+//
+// delta: the atlas already holds the deposit of the records as they were on
+// entry.  A lane that takes a listed path first removes that path's entry
+// photons (their count is in the touched byte, read before verification
+// rewrote the info word) and deposits its final photons when it finishes it;
+// untouched paths are not visited.  Integer sums make the result the same,
+// bit for bit, as a cleared atlas with every path deposited.
 struct DepositArgs {
   pv_atlas at;
   const uint8_t* touched;
+  uint32_t delta;
 };
 
 __device__ __forceinline__ void cont_flush(ContCounters& cc, uint32_t* s_cnt) {
@@ -154,7 +162,7 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS)
   const int root = *sv.root;
   const uint32_t n_cont = min(*C.count, C.n);
   const uint32_t n_trace = n_cont + min(*A.count, A.n);
-  const uint32_t total = n_trace + (kDeposit ? A.n : 0u);
+  const uint32_t total = n_trace + (kDeposit && !D.delta ? A.n : 0u);
   const int lane = threadIdx.x & 31;
   uint32_t dep = 0xFFFFFFFFu;                // a final path this lane still has to deposit
   auto deposit = [&](uint32_t p) {
@@ -183,6 +191,11 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS)
       base = __shfl_sync(0xffffffffu, base, leader);
       if (need) {
         const uint32_t idx = base + __popc(nm & lt);
+        if (kDeposit && D.delta && idx < n_trace) {      // the path's entry photons leave the atlas
+          const uint32_t p = idx < n_cont ? C.list[idx] : (A.list ? A.list[idx - n_cont] : idx - n_cont);
+          const uint32_t code = D.touched[p];
+          if (code) deposit_rows<true>(D.at, A.n, min(code - 1u, sv.B), A.pa, A.pb, p);
+        }
         if (idx < n_cont) {
           ContCounters cc;
           s.pid = C.list[idx];
@@ -304,7 +317,7 @@ void launch_trace(pv_scene* s, const pv_paths* p, const uint32_t* list, const ui
 
 void launch_cont_trace(pv_scene* s, const pv_paths* p, const ContArgs& C, const uint32_t* list, const uint32_t* count,
                        uint64_t seed, uint32_t frame, pv_frame_stats* stats, const pv_atlas* atlas,
-                       const uint8_t* touched, cudaStream_t st) {
+                       const uint8_t* touched, bool delta, cudaStream_t st) {
   const TraceArgs A = trace_args(s, p, list, count, seed, frame, stats);
   cudaMemsetAsync(A.ticket, 0, sizeof(uint32_t), st);
   if (!p->n) return;
@@ -314,6 +327,7 @@ void launch_cont_trace(pv_scene* s, const pv_paths* p, const ContArgs& C, const 
     if (!s->cont_trace_dep_blocks) s->cont_trace_dep_blocks = persistent_blocks(s, k_cont_trace<true>);
     D.at = *atlas;
     D.touched = touched;
+    D.delta = delta ? 1u : 0u;
     k_cont_trace<true><<<s->cont_trace_dep_blocks, kTraceThreads, 0, st>>>(view(s), frame_lights(s), A, C, D);
   } else {
     if (!s->cont_trace_blocks) s->cont_trace_blocks = persistent_blocks(s, k_cont_trace<false>);

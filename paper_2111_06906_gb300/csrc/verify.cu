@@ -166,7 +166,7 @@ namespace {
 
 // pv_verify_retrace, and with an atlas pv_verify_retrace_deposit.
 int verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params* params, const pv_atlas* atlas,
-                   pv_frame_stats* d_stats, cudaStream_t st) {
+                   bool delta, pv_frame_stats* d_stats, cudaStream_t st) {
   int rc = check_verify(s, paths, params);
   if (rc != PV_OK) return rc;
   if (atlas && (rc = pvh::check_atlas(atlas)) != PV_OK) return rc;
@@ -178,7 +178,9 @@ int verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params* p
     if (ev) cudaEventRecord(ev[k], st);
   };
   mark(0);
-  if (atlas && cudaMemsetAsync(atlas->data, 0, (size_t)atlas->width * atlas->height * 3 * sizeof(uint64_t), st) !=
+  // with maps the deposit runs as its own kernel over every path: the delta form starts from a cleared atlas too
+  if (s->has_dm) delta = false;
+  if (atlas && !delta && cudaMemsetAsync(atlas->data, 0, (size_t)atlas->width * atlas->height * 3 * sizeof(uint64_t), st) !=
                    cudaSuccess)
     return PV_ERR_CUDA;
   // with maps, prune and fill need Alg. 1's final answer for every path before the list is made
@@ -198,7 +200,7 @@ int verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params* p
     // k_verify appended the paths it marked; then Alg. 1, the re-trace (and the deposit) in one kernel
     mark(2);
     pvh::launch_cont_trace(s, paths, C, list, count, params->seed, params->frame, d_stats,
-                           fuse_deposit ? atlas : nullptr, s->ws_touched, st);
+                           fuse_deposit ? atlas : nullptr, s->ws_touched, delta, st);
   } else {
     if (cont) launch_continue(s, sv, C, st);
     if (s->has_dm && (rc = pvh::dm_frame(s, paths, L, params, d_stats, st)) != PV_OK) return rc;
@@ -219,13 +221,19 @@ int verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params* p
 
 extern "C" int pv_verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params* params,
                                  pv_frame_stats* d_stats, void* stream) {
-  return verify_retrace(s, paths, params, nullptr, d_stats, (cudaStream_t)stream);
+  return verify_retrace(s, paths, params, nullptr, false, d_stats, (cudaStream_t)stream);
 }
 
 extern "C" int pv_verify_retrace_deposit(pv_scene* s, const pv_paths* paths, const pv_verify_params* params,
                                          const pv_atlas* atlas, pv_frame_stats* d_stats, void* stream) {
   if (!atlas) return PV_ERR_ARG;
-  return verify_retrace(s, paths, params, atlas, d_stats, (cudaStream_t)stream);
+  return verify_retrace(s, paths, params, atlas, false, d_stats, (cudaStream_t)stream);
+}
+
+extern "C" int pv_verify_retrace_deposit_delta(pv_scene* s, const pv_paths* paths, const pv_verify_params* params,
+                                               const pv_atlas* atlas, pv_frame_stats* d_stats, void* stream) {
+  if (!atlas) return PV_ERR_ARG;
+  return verify_retrace(s, paths, params, atlas, true, d_stats, (cudaStream_t)stream);
 }
 
 extern "C" int pv_stage_timing(pv_scene* s, uint32_t n) {

@@ -25,7 +25,8 @@ struct VerifyArgs {
   uint32_t* cont_list;
   uint32_t* cont_count;
   pv_frame_stats* stats;
-  uint8_t* touched;            // optional [n]: 1 for a path this frame re-traces or hands to Alg. 1, else 0
+  uint8_t* touched;            // optional [n]: 0 for a path this frame leaves as it is; for one it re-traces or
+                               // hands to Alg. 1, 1 + the photon count it had on entry (at most 16)
   uint32_t* list_out;          // optional: the paths marked for re-tracing are appended here (unordered),
   uint32_t* list_count;        // counted here and in stats->n_listed (instead of a compaction)
 };
@@ -39,8 +40,8 @@ __device__ __forceinline__ bool seg_box(float3 inv, float3 aoi, const float* bx)
   const float x0 = fmaf(bx[0], inv.x, aoi.x), x1 = fmaf(bx[3], inv.x, aoi.x);
   const float y0 = fmaf(bx[1], inv.y, aoi.y), y1 = fmaf(bx[4], inv.y, aoi.y);
   const float z0 = fmaf(bx[2], inv.z, aoi.z), z1 = fmaf(bx[5], inv.z, aoi.z);
-  const float t0 = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.0f));
-  const float t1 = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), 1.0f));
+  const float t0 = fmax3(fminf(x0, x1), fminf(y0, y1), fmaxf(fminf(z0, z1), 0.0f));
+  const float t1 = fmin3(fmaxf(x0, x1), fmaxf(y0, y1), fminf(fmaxf(z0, z1), 1.0f));
   return t0 <= t1;
 }
 
@@ -178,6 +179,12 @@ struct PathCheck {
   bool blocked1;               // a moved point light's visibility ray is blocked
   bool replaced;               // marked for a fresh emission by the origin stage
 };
+
+// The touched byte of a path: 0 if untouched, else 1 + the photon count of
+// its record on entry (v.nseg is read before any rewrite of the info word).
+__device__ __forceinline__ uint8_t touched_code(bool touched, const PathCheck& v) {
+  return touched ? (uint8_t)(1u + v.nseg) : (uint8_t)0;
+}
 
 // Sec. 3.1 "update path origins" for path p (< A.n): the moved light's
 // emission point is re-derived; a path that cannot be kept is marked for a
@@ -398,7 +405,7 @@ __device__ __forceinline__ void verify_block(const SceneView& sv, const FrameLig
       touched = mask != 0;                   // handed to Alg. 1, or (naive modes) marked for re-tracing
       listed = mask != 0 && A.mode != PV_MODE_ERROR;
     }
-    if (A.touched) A.touched[p] = (touched || v.replaced) ? 1 : 0;
+    if (A.touched) A.touched[p] = touched_code(touched || v.replaced, v);
     listed = listed || v.replaced;
   }
   verify_epilogue(A, p, want_cont, listed, c_tested, c_vis, c_reemit, c_tail, wk, kPointVis || kExact, sm);
@@ -478,7 +485,7 @@ __device__ __forceinline__ void verify_block_warp(const SceneView& sv, const Fra
   }
   bool want_cont = false;
   if (p < n && v.test) want_cont = finish_stage(A, p, v, my_mask, c_reemit, c_tail);
-  if (p < n && A.touched) A.touched[p] = ((v.test && my_mask != 0) || v.replaced) ? 1 : 0;
+  if (p < n && A.touched) A.touched[p] = touched_code((v.test && my_mask != 0) || v.replaced, v);
   const bool listed = p < n && (v.replaced || (v.test && my_mask != 0 && !error_mode));
   verify_epilogue(A, p, want_cont, listed, c_tested, c_vis, c_reemit, c_tail, wk, kPointVis || kExact, sm);
 }
@@ -730,9 +737,9 @@ __device__ __forceinline__ void verify_block_flat(const SceneView& sv, const Fra
     const uint32_t mask = sm.hitmask[threadIdx.x];
     if (sv.moved && v.nseg >= 1) c_tested = __popc(~sm.slotmask[threadIdx.x] & ((2u << v.nseg) - 2u));
     want_cont = finish_stage(A, p, v, mask, c_reemit, c_tail);
-    if (A.touched) A.touched[p] = (mask != 0 || v.replaced) ? 1 : 0;
+    if (A.touched) A.touched[p] = touched_code(mask != 0 || v.replaced, v);
   } else if (p < n && A.touched) {
-    A.touched[p] = v.replaced ? 1 : 0;
+    A.touched[p] = touched_code(v.replaced, v);
   }
   verify_epilogue(A, p, want_cont, p < n && v.replaced, c_tested, c_vis, c_reemit, c_tail, wk, kPointVis || kExact,
                   sm);

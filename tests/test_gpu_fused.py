@@ -233,3 +233,83 @@ def test_fused_frame_against_oracle():
             gu.upload(P, op)                          # continue both sides from the oracle's records
         assert pv.pv_read_device_status(h) == 0
         pv.pv_destroy_scene(h)
+
+
+DELTA_MODES = [MODES[0], MODES[2], MODES[3], MODES[4], MODES[5]]
+
+
+@pytest.mark.parametrize("mode,tau,flags", DELTA_MODES, ids=lambda v: str(v))
+@pytest.mark.parametrize("name", list(SCENES))
+def test_delta_deposit_matches_full_deposit(name, mode, tau, flags):
+    """pv_verify_retrace_deposit_delta on an atlas carried from frame to frame against
+    pv_verify_retrace_deposit on a cleared one: records, counters and atlas equal bit for bit every frame,
+    re-emitted paths (moving lights), Alg. 1 paths, tails and naive re-traces included."""
+    torch = _torch()
+    sc = SCENES[name]()
+    p = Pair(sc, 47)
+    a1, rect, scale = _atlas(sc)
+    a2 = torch.zeros_like(a1)
+    pv.pv_deposit(p.h2, p.P2, a2, rect, scale)        # the entry records' deposit
+    changed = 0
+    for f in range(2, 6):
+        s1, s2 = pv.new_stats(), pv.new_stats()
+        for h in (p.h1, p.h2):
+            gu.advance(h, sc, f)
+        pv.pv_verify_retrace_deposit(p.h1, p.P1, mode, tau, flags, p.seed, f, a1, rect, scale, s1)
+        pv.pv_verify_retrace_deposit_delta(p.h2, p.P2, mode, tau, flags, p.seed, f, a2, rect, scale, s2)
+        d1, d2 = pv.stats_dict(s1), pv.stats_dict(s2)
+        p.compare(d1, d2)
+        assert torch.equal(a1, a2), int((a1 != a2).sum())
+        changed += d2["n_listed"] + d2["n_cont"]
+    assert changed > 0
+    p.close()
+
+
+def test_delta_deposit_without_motion_and_with_distribution_map():
+    """Nothing moved: the carried atlas stays as it was.  Distribution maps: the delta call clears and
+    deposits every path, so a wrong entry atlas does not survive."""
+    torch = _torch()
+    sc = kit.box_with_torus(3000, B=4)
+    p = Pair(sc, 53)
+    a, rect, scale = _atlas(sc, 128)
+    pv.pv_deposit(p.h2, p.P2, a, rect, scale)
+    before = a.clone()
+    pv.pv_update_dynamic(p.h2, sc.xforms(1), sc.lights(1))
+    st = pv.new_stats()
+    pv.pv_verify_retrace_deposit_delta(p.h2, p.P2, pv.PV_MODE_ERROR, 0.01, 0, p.seed, 2, a, rect, scale, st)
+    assert pv.stats_dict(st)["n_listed"] == 0
+    assert torch.equal(a, before)
+    p.close()
+
+    sc = kit.rect_light_over_floor(2560, shift=lambda f: (0.11 * (f - 1), 0.0, 0.07 * (f - 1)), B=2, R=3.0)
+    p = Pair(sc, 59, dm_rect=(4, 4, 4, 4))
+    a1, rect, scale = _atlas(sc, 128)
+    a2 = torch.full_like(a1, 777)                         # not the entry deposit: the call must not rely on it
+    for f in range(2, 4):
+        s1, s2 = pv.new_stats(), pv.new_stats()
+        for h in (p.h1, p.h2):
+            gu.advance(h, sc, f)
+        pv.pv_verify_retrace_deposit(p.h1, p.P1, pv.PV_MODE_ERROR, 0.01, 0, p.seed, f, a1, rect, scale, s1)
+        pv.pv_verify_retrace_deposit_delta(p.h2, p.P2, pv.PV_MODE_ERROR, 0.01, 0, p.seed, f, a2, rect, scale, s2)
+        p.compare(pv.stats_dict(s1), pv.stats_dict(s2))
+        assert torch.equal(a1, a2)
+    p.close()
+
+
+@pytest.mark.parametrize("B", [1, 15])
+def test_delta_deposit_bounce_caps(B):
+    torch = _torch()
+    sc = kit.box_with_torus(3000, B=B)
+    p = Pair(sc, 61)
+    a1, rect, scale = _atlas(sc, 64)
+    a2 = torch.zeros_like(a1)
+    pv.pv_deposit(p.h2, p.P2, a2, rect, scale)
+    for f in range(2, 5):
+        s1, s2 = pv.new_stats(), pv.new_stats()
+        for h in (p.h1, p.h2):
+            gu.advance(h, sc, f)
+        pv.pv_verify_retrace_deposit(p.h1, p.P1, pv.PV_MODE_ERROR, 0.01, 0, p.seed, f, a1, rect, scale, s1)
+        pv.pv_verify_retrace_deposit_delta(p.h2, p.P2, pv.PV_MODE_ERROR, 0.01, 0, p.seed, f, a2, rect, scale, s2)
+        p.compare(pv.stats_dict(s1), pv.stats_dict(s2))
+        assert torch.equal(a1, a2)
+    p.close()
