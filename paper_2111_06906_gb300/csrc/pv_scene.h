@@ -97,7 +97,8 @@ struct pv_scene {
   int* status = nullptr;             // sticky device status
   cudaStream_t last_stream = nullptr;
 
-  int verify_blocks = 0, trace_blocks = 0, cont_blocks = 0, cont_trace_blocks = 0, cont_trace_dep_blocks = 0;
+  int verify_blocks = 0, trace_blocks = 0, cont_blocks = 0, cont_trace_blocks = 0, cont_trace_dep_blocks = 0,
+      cont_trace_delta_blocks = 0;
   // stage timing of pv_verify_retrace: a ring of stage_n calls, four events each
   std::vector<cudaEvent_t> stage_ev;
   uint32_t stage_n = 0, stage_next = 0, stage_count = 0;

@@ -125,23 +125,21 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS) k_tra
 // arithmetic as in k_continue followed by k_trace, so the records are
 // identical; only the order in which paths are processed differs.
 //
-// kDeposit: the atlas deposit joins the kernel.  A lane deposits each path it
+// With a deposit (kDep 1) the atlas deposit joins the kernel.  A lane deposits each path it
 // finishes as soon as it is final; after the re-trace items come the paths
 // verification left untouched (touched[p] == 0), whose deposit fills the
 // lanes that have no more rays to trace.  Every path is deposited once, by
 // the same per-photon arithmetic as k_deposit, into integer sums: the atlas
 // is the same bit for bit.
 //
-// delta: the atlas already holds the deposit of the records as they were on
-// entry.  A lane that takes a listed path first removes that path's entry
-// photons (their count is in the touched byte, read before verification
-// rewrote the info word) and deposits its final photons when it finishes it;
-// untouched paths are not visited.  Integer sums make the result the same,
-// bit for bit, as a cleared atlas with every path deposited.
+// kDep 2: the atlas already holds the deposit of the records as they were on
+// entry, and k_verify has taken the touched paths' entry photons out of it.
+// A lane deposits the final photons of each path it finishes; untouched
+// paths are not visited.  Integer sums make the result the same, bit for
+// bit, as a cleared atlas with every path deposited.
 struct DepositArgs {
   pv_atlas at;
   const uint8_t* touched;
-  uint32_t delta;
 };
 
 __device__ __forceinline__ void cont_flush(ContCounters& cc, uint32_t* s_cnt) {
@@ -151,7 +149,8 @@ __device__ __forceinline__ void cont_flush(ContCounters& cc, uint32_t* s_cnt) {
   if (cc.trunc) atomicAdd(s_cnt + 3, cc.trunc);
 }
 
-template <bool kDeposit>
+// kDep: 0 no deposit, 1 deposit into a cleared atlas, 2 carried atlas (delta).
+template <int kDep>
 __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS)
     k_cont_trace(SceneView sv, FrameLights L, TraceArgs A, ContArgs C, DepositArgs D) {
   __shared__ uint32_t s_red[32 * 2];
@@ -162,7 +161,8 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS)
   const int root = *sv.root;
   const uint32_t n_cont = min(*C.count, C.n);
   const uint32_t n_trace = n_cont + min(*A.count, A.n);
-  const uint32_t total = n_trace + (kDeposit && !D.delta ? A.n : 0u);
+  constexpr bool kDeposit = kDep != 0;
+  const uint32_t total = n_trace + (kDep == 1 ? A.n : 0u);
   const int lane = threadIdx.x & 31;
   uint32_t dep = 0xFFFFFFFFu;                // a final path this lane still has to deposit
   auto deposit = [&](uint32_t p) {
@@ -191,11 +191,6 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS)
       base = __shfl_sync(0xffffffffu, base, leader);
       if (need) {
         const uint32_t idx = base + __popc(nm & lt);
-        if (kDeposit && D.delta && idx < n_trace) {      // the path's entry photons leave the atlas
-          const uint32_t p = idx < n_cont ? C.list[idx] : (A.list ? A.list[idx - n_cont] : idx - n_cont);
-          const uint32_t code = D.touched[p];
-          if (code) deposit_rows<true>(D.at, A.n, min(code - 1u, sv.B), A.pa, A.pb, p);
-        }
         if (idx < n_cont) {
           ContCounters cc;
           s.pid = C.list[idx];
@@ -324,14 +319,18 @@ void launch_cont_trace(pv_scene* s, const pv_paths* p, const ContArgs& C, const 
   DepositArgs D;
   std::memset(&D, 0, sizeof D);
   if (atlas) {
-    if (!s->cont_trace_dep_blocks) s->cont_trace_dep_blocks = persistent_blocks(s, k_cont_trace<true>);
     D.at = *atlas;
     D.touched = touched;
-    D.delta = delta ? 1u : 0u;
-    k_cont_trace<true><<<s->cont_trace_dep_blocks, kTraceThreads, 0, st>>>(view(s), frame_lights(s), A, C, D);
+    if (delta) {
+      if (!s->cont_trace_delta_blocks) s->cont_trace_delta_blocks = persistent_blocks(s, k_cont_trace<2>);
+      k_cont_trace<2><<<s->cont_trace_delta_blocks, kTraceThreads, 0, st>>>(view(s), frame_lights(s), A, C, D);
+    } else {
+      if (!s->cont_trace_dep_blocks) s->cont_trace_dep_blocks = persistent_blocks(s, k_cont_trace<1>);
+      k_cont_trace<1><<<s->cont_trace_dep_blocks, kTraceThreads, 0, st>>>(view(s), frame_lights(s), A, C, D);
+    }
   } else {
-    if (!s->cont_trace_blocks) s->cont_trace_blocks = persistent_blocks(s, k_cont_trace<false>);
-    k_cont_trace<false><<<s->cont_trace_blocks, kTraceThreads, 0, st>>>(view(s), frame_lights(s), A, C, D);
+    if (!s->cont_trace_blocks) s->cont_trace_blocks = persistent_blocks(s, k_cont_trace<0>);
+    k_cont_trace<0><<<s->cont_trace_blocks, kTraceThreads, 0, st>>>(view(s), frame_lights(s), A, C, D);
   }
 }
 

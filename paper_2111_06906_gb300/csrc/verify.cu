@@ -7,6 +7,7 @@
 //   the error-based threshold continuation of Sec. 3.3, Alg. 1 and Eq. 2.
 // Then the replace bits are compacted into the re-trace list (compact.cu).
 #include <algorithm>
+#include <cstring>
 
 #include "verify_core.cuh"
 
@@ -95,7 +96,7 @@ ContArgs cont_args(pv_scene* s, const pv_paths* paths, const pv_verify_params* p
 // (Sec. 3.1 + 3.2).  ``cont``: Alg. 1 has paths to look at this frame.
 int launch_verify(pv_scene* s, const pv_paths* paths, const pv_verify_params* params, pv_frame_stats* d_stats,
                   const SceneView& sv, const FrameLights& L, cudaStream_t st, bool& cont, uint8_t* touched = nullptr,
-                  bool direct_list = false) {
+                  bool direct_list = false, const pv_atlas* sub = nullptr) {
   const uint32_t n = paths->n;
   if (cudaMemsetAsync(s->ws_ctr, 0, 16 * sizeof(uint32_t), st) != cudaSuccess) return PV_ERR_CUDA;
   for (uint32_t l = 0; l < s->n_lights; ++l)       // DM_C of moved lights with a map is counted afresh
@@ -116,6 +117,8 @@ int launch_verify(pv_scene* s, const pv_paths* paths, const pv_verify_params* pa
   A.cont_count = s->ws_ctr + pvh::CTR_ALL;
   A.stats = d_stats;
   A.touched = touched;
+  std::memset(&A.sub, 0, sizeof A.sub);
+  if (sub && touched) A.sub = *sub;             // a carried atlas: touched paths' entry photons leave it here
   A.list_out = direct_list ? s->ws_list : nullptr;           // the marked paths, appended (no compaction)
   A.list_count = direct_list ? s->ws_ctr + pvh::CTR_LIST : nullptr;
   if (n) {
@@ -188,8 +191,8 @@ int verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params* p
   const bool will_cont = paths->n && params->mode == PV_MODE_ERROR && (s->moved || L.moved_mask);
   const bool fused = (will_cont || fuse_deposit) && !s->has_dm;
   bool cont = false;
-  if ((rc = launch_verify(s, paths, params, d_stats, sv, L, st, cont, fuse_deposit ? s->ws_touched : nullptr, fused)) !=
-      PV_OK)
+  if ((rc = launch_verify(s, paths, params, d_stats, sv, L, st, cont, fuse_deposit ? s->ws_touched : nullptr, fused,
+                          delta ? atlas : nullptr)) != PV_OK)
     return rc;
   mark(1);
   const ContArgs C = cont_args(s, paths, params, d_stats);

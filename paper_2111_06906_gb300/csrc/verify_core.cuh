@@ -7,6 +7,7 @@
 // continue_path: the error-based threshold continuation of Sec. 3.3, Alg. 1
 //   and Eq. 2, for one path flagged by verify_block in error mode.
 #pragma once
+#include "deposit_core.cuh"
 #include "dm_core.cuh"
 #include "pv_scene.h"
 
@@ -27,6 +28,8 @@ struct VerifyArgs {
   pv_frame_stats* stats;
   uint8_t* touched;            // optional [n]: 0 for a path this frame leaves as it is; for one it re-traces or
                                // hands to Alg. 1, 1 + the photon count it had on entry (at most 16)
+  pv_atlas sub;                // optional (sub.data non-null, with touched): a carried atlas from which each
+                               // touched path's entry photons are subtracted here, before anything rewrites them
   uint32_t* list_out;          // optional: the paths marked for re-tracing are appended here (unordered),
   uint32_t* list_count;        // counted here and in stats->n_listed (instead of a compaction)
 };
@@ -184,6 +187,15 @@ struct PathCheck {
 // its record on entry (v.nseg is read before any rewrite of the info word).
 __device__ __forceinline__ uint8_t touched_code(bool touched, const PathCheck& v) {
   return touched ? (uint8_t)(1u + v.nseg) : (uint8_t)0;
+}
+
+// Record path p's touched byte; with a carried atlas, take a touched path's
+// entry photons out of it (pa / pb are not written before the re-trace kernel).
+__device__ __forceinline__ void mark_touched(const VerifyArgs& A, uint32_t p, bool touched, const PathCheck& v) {
+  if (!A.touched) return;
+  const uint8_t code = touched_code(touched, v);
+  A.touched[p] = code;
+  if (code && A.sub.data) deposit_rows<true>(A.sub, A.n, code - 1u, A.pa, A.pb, p);
 }
 
 // Sec. 3.1 "update path origins" for path p (< A.n): the moved light's
@@ -405,7 +417,7 @@ __device__ __forceinline__ void verify_block(const SceneView& sv, const FrameLig
       touched = mask != 0;                   // handed to Alg. 1, or (naive modes) marked for re-tracing
       listed = mask != 0 && A.mode != PV_MODE_ERROR;
     }
-    if (A.touched) A.touched[p] = touched_code(touched || v.replaced, v);
+    mark_touched(A, p, touched || v.replaced, v);
     listed = listed || v.replaced;
   }
   verify_epilogue(A, p, want_cont, listed, c_tested, c_vis, c_reemit, c_tail, wk, kPointVis || kExact, sm);
@@ -485,7 +497,7 @@ __device__ __forceinline__ void verify_block_warp(const SceneView& sv, const Fra
   }
   bool want_cont = false;
   if (p < n && v.test) want_cont = finish_stage(A, p, v, my_mask, c_reemit, c_tail);
-  if (p < n && A.touched) A.touched[p] = touched_code((v.test && my_mask != 0) || v.replaced, v);
+  if (p < n) mark_touched(A, p, (v.test && my_mask != 0) || v.replaced, v);
   const bool listed = p < n && (v.replaced || (v.test && my_mask != 0 && !error_mode));
   verify_epilogue(A, p, want_cont, listed, c_tested, c_vis, c_reemit, c_tail, wk, kPointVis || kExact, sm);
 }
@@ -737,9 +749,9 @@ __device__ __forceinline__ void verify_block_flat(const SceneView& sv, const Fra
     const uint32_t mask = sm.hitmask[threadIdx.x];
     if (sv.moved && v.nseg >= 1) c_tested = __popc(~sm.slotmask[threadIdx.x] & ((2u << v.nseg) - 2u));
     want_cont = finish_stage(A, p, v, mask, c_reemit, c_tail);
-    if (A.touched) A.touched[p] = touched_code(mask != 0 || v.replaced, v);
-  } else if (p < n && A.touched) {
-    A.touched[p] = touched_code(v.replaced, v);
+    mark_touched(A, p, mask != 0 || v.replaced, v);
+  } else if (p < n) {
+    mark_touched(A, p, v.replaced, v);
   }
   verify_epilogue(A, p, want_cont, p < n && v.replaced, c_tested, c_vis, c_reemit, c_tail, wk, kPointVis || kExact,
                   sm);
