@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, 6) k_b_trace(const BScene*
   PathState st;
   Ray r;
   Trav t;
-  int stk[S];
+  TStack<S> stk;
   uint32_t sc = 0, c_rays = 0, c_photons = 0;
   bool has_ray = false, exhausted = false;
   auto flush = [&]() {                         // the finished path's counters to its scene
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_BATCH_CT_MIN_BLOCKS) k_
   PathState st;
   Ray r;
   Trav t;
-  int stk[S];
+  TStack<S> stk;
   uint32_t sc = 0, c_rays = 0, c_photons = 0, cmask = 0, cmeta = 0;
   bool has_ray = false, exhausted = false, cont = false;
   auto flush = [&]() {                         // the finished path's counters to its scene

@@ -345,8 +345,37 @@ __device__ __forceinline__ void cswap(float& ka, int& va, float& kb, int& vb) {
   va = v;
 }
 
-template <int S = kStack>
-__device__ __forceinline__ bool visit_wide(const WNodeRay& n, const Ray& r, float tbest, int* stk, int& sp, int& next) {
+// Traversal stack of one thread, S entries.  The first SH entries live in
+// shared memory, entry i at sh[i * STRIDE] with STRIDE = the block's thread
+// count: the lanes of a warp then touch 32 different banks whatever their
+// stack depths, where a local-memory stack spreads divergent depths over as
+// many cache lines.  Deeper entries live in a local array.  SH = 0 is a
+// plain local stack.
+template <int S, int SH = 0, int STRIDE = 1>
+struct TStack {
+  static constexpr int kSize = S;
+  int* sh;                                    // this thread's first shared entry
+  int loc[S > SH ? S - SH : 1];
+  __device__ __forceinline__ int get(int i) const {
+    if (SH == 0) return loc[i];
+    if (SH >= S) return sh[i * STRIDE];
+    return i < SH ? sh[i * STRIDE] : loc[i - SH];
+  }
+  __device__ __forceinline__ void set(int i, int v) {
+    if (SH == 0) {
+      loc[i] = v;
+    } else if (SH >= S) {
+      sh[i * STRIDE] = v;
+    } else if (i < SH) {
+      sh[i * STRIDE] = v;
+    } else {
+      loc[i - SH] = v;
+    }
+  }
+};
+
+template <int S = kStack, class Stk>
+__device__ __forceinline__ bool visit_wide(const WNodeRay& n, const Ray& r, float tbest, Stk& stk, int& sp, int& next) {
   float t[4];
   const uint32_t mask = box4(r, tbest, n, t);
   const int m = __popc(mask);
@@ -364,9 +393,9 @@ __device__ __forceinline__ bool visit_wide(const WNodeRay& n, const Ray& r, floa
   cswap(k1, v1, k3, v3);
   cswap(k1, v1, k2, v2);
   if (sp + m - 1 > S) return false;
-  if (m >= 4) stk[sp++] = v3;
-  if (m >= 3) stk[sp++] = v2;
-  if (m >= 2) stk[sp++] = v1;
+  if (m >= 4) stk.set(sp++, v3);
+  if (m >= 3) stk.set(sp++, v2);
+  if (m >= 2) stk.set(sp++, v1);
   next = v0;
   return true;
 }
@@ -399,7 +428,7 @@ __device__ __forceinline__ bool visit_leaf(const Tri* tris, int ref, const Ray& 
 template <bool ANY, int S = kStack>
 __device__ __forceinline__ bool traverse(const WNode* nodes, const Tri* tris, int root, const Ray& r, float& tbest,
                                          int& best, int exclude, uint32_t max_visits, int* status, Work& wk) {
-  int stack[S];
+  TStack<S> stack;
   int sp = 0;
   int node = root;
   uint32_t visits = 0;
@@ -426,7 +455,7 @@ __device__ __forceinline__ bool traverse(const WNode* nodes, const Tri* tris, in
       }
     }
     if (sp == 0) return true;
-    node = stack[--sp];
+    node = stack.get(--sp);
   }
 }
 
@@ -474,8 +503,8 @@ __device__ __forceinline__ void trav_begin(Trav& t, int root) {
 
 // One traversal step (one wide node or one leaf range); true once the ray is done.
 // ``stk`` holds S entries.
-template <int S = kStack>
-__device__ __forceinline__ bool trav_step(const SceneView& sv, const Ray& r, Trav& t, int* stk, int exclude, Work& wk) {
+template <int S = kStack, class Stk>
+__device__ __forceinline__ bool trav_step(const SceneView& sv, const Ray& r, Trav& t, Stk& stk, int exclude, Work& wk) {
   if (t.node != INT32_MIN) {
     if (++t.visits > sv.max_visits) {
       record_error(sv.status, PV_ERR_ITER_CAP);
@@ -498,7 +527,7 @@ __device__ __forceinline__ bool trav_step(const SceneView& sv, const Ray& r, Tra
     }
   }
   if (t.sp == 0) return true;
-  t.node = stk[--t.sp];
+  t.node = stk.get(--t.sp);
   return false;
 }
 
@@ -509,6 +538,14 @@ __device__ __forceinline__ uint32_t info_make(uint32_t cell, uint32_t nseg, uint
   return (cell & PV_INFO_CELL_MASK) | (nseg << PV_INFO_NSEG_SHIFT) | (start << PV_INFO_START_SHIFT) |
          (rep ? PV_INFO_REPLACE : 0u) | (reuse ? PV_INFO_REUSE_LIGHT : 0u);
 }
+
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// programmatic stream serialisation waits in grid_dependency_wait() until the
+// kernel before it has completed and its memory operations are visible; for
+// an ordinary launch the wait returns at once.  launch_dependents() lets the
+// next such kernel be scheduled once every block of this one has issued it.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
 // Warp-aggregated add of ``v`` to a device counter (the calling lanes only).
 __device__ __forceinline__ void warp_add(uint32_t* ctr, uint32_t v) {

@@ -12,6 +12,7 @@
 struct pv_scene {
   int device = 0;
   int num_sms = 0;
+  int verify_blocks_per_sm[4] = {0, 0, 0, 0};   // resident k_verify blocks per SM, by (point vis, exact)
   uint32_t n_tris = 0, n_objects = 0, n_static = 0, n_dyn_tris = 0, n_dyn = 0;
   uint32_t B = 0;
   float diag = 0.f, tmin = 0.f, close_tol = 0.f;

@@ -41,13 +41,23 @@ namespace {
 #ifndef PV_TRACE_DONE_LANES
 #define PV_TRACE_DONE_LANES 32
 #endif
+// Traversal stack entries kept in shared memory (the rest in local memory).
+// Measured on the city and villa workloads, 8, 16 or 32 shared entries made
+// the re-trace and trace-all kernels 5-7 % slower than a local-memory stack,
+// so the default keeps none.
+#ifndef PV_TRACE_STACK_SHARED
+#define PV_TRACE_STACK_SHARED 0
+#endif
+constexpr int kStackShared = PV_TRACE_STACK_SHARED < kStack ? PV_TRACE_STACK_SHARED : kStack;
+using TraceStack = TStack<kStack, kStackShared, pvh::kTraceThreads>;
+constexpr int kStackSharedWords = kStackShared > 0 ? kStackShared * pvh::kTraceThreads : 1;
 constexpr int kStepsPerIter = PV_TRACE_STEPS;
 constexpr int kMaxSteps = PV_TRACE_MAX_STEPS;
 constexpr int kDoneLanes = PV_TRACE_DONE_LANES;
 
 // Advance the lane's ray; all lanes of the warp call it (lanes without a ray
 // pass done = true).  Returns whether the lane's ray has ended.
-__device__ __forceinline__ bool step_rays(const SceneView& sv, const Ray& r, Trav& t, int* stk, int excl, Work& wk,
+__device__ __forceinline__ bool step_rays(const SceneView& sv, const Ray& r, Trav& t, TraceStack& stk, int excl, Work& wk,
                                           bool done) {
   if (kDoneLanes > 32) {
 #pragma unroll 1
@@ -76,7 +86,9 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS) k_tra
   PathState s;
   Ray r;
   Trav t;
-  int stk[kStack];
+  __shared__ int s_stk[kStackSharedWords];
+  TraceStack stk;
+  stk.sh = s_stk + threadIdx.x;
   bool has_ray = false, exhausted = false;
   uint32_t c_rays = 0, c_photons = 0;
   for (uint32_t guard = 0; guard < (1u << 30); ++guard) {
@@ -150,6 +162,10 @@ __device__ __forceinline__ void cont_flush(ContCounters& cc, uint32_t* s_cnt) {
 }
 
 // kDep: 0 no deposit, 1 deposit into a cleared atlas, 2 carried atlas (delta).
+//
+// Launched as a programmatic dependent of k_verify: its blocks may be placed
+// on the SMs while k_verify's last blocks run, and wait here until k_verify
+// has finished and its writes are visible (a no-op for an ordinary launch).
 template <int kDep>
 __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS)
     k_cont_trace(SceneView sv, FrameLights L, TraceArgs A, ContArgs C, DepositArgs D) {
@@ -157,6 +173,7 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS)
   __shared__ unsigned long long s_red64[32];
   __shared__ uint32_t s_cnt[4];
   if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0u;
+  grid_dependency_wait();
   __syncthreads();
   const int root = *sv.root;
   const uint32_t n_cont = min(*C.count, C.n);
@@ -173,7 +190,9 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS)
   PathState s;
   Ray r;
   Trav t;
-  int stk[kStack];
+  __shared__ int s_stk[kStackSharedWords];
+  TraceStack stk;
+  stk.sh = s_stk + threadIdx.x;
   uint32_t cmask = 0, cmeta = 0;             // Alg. 1 state beyond s.k (segment), s.E (a_orig), s.excl (a_prim)
   bool has_ray = false, exhausted = false, cont = false;
   uint32_t c_rays = 0, c_photons = 0;
@@ -310,11 +329,29 @@ void launch_trace(pv_scene* s, const pv_paths* p, const uint32_t* list, const ui
   if (p->n) k_trace<<<s->trace_blocks, kTraceThreads, 0, st>>>(view(s), frame_lights(s), A);
 }
 
+// k_cont_trace as a programmatic dependent launch: it may start while the
+// kernel before it on the stream (k_verify) is finishing.
+template <int kDep>
+void launch_cont_trace_pdl(int blocks, const SceneView& sv, const FrameLights& L, const TraceArgs& A,
+                           const ContArgs& C, const DepositArgs& D, cudaStream_t st) {
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof cfg);
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(kTraceThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_cont_trace<kDep>, sv, L, A, C, D);
+}
+
 void launch_cont_trace(pv_scene* s, const pv_paths* p, const ContArgs& C, const uint32_t* list, const uint32_t* count,
                        uint64_t seed, uint32_t frame, pv_frame_stats* stats, const pv_atlas* atlas,
                        const uint8_t* touched, bool delta, cudaStream_t st) {
+  // the ticket was cleared with the other work counters before k_verify
   const TraceArgs A = trace_args(s, p, list, count, seed, frame, stats);
-  cudaMemsetAsync(A.ticket, 0, sizeof(uint32_t), st);
   if (!p->n) return;
   DepositArgs D;
   std::memset(&D, 0, sizeof D);
@@ -323,14 +360,14 @@ void launch_cont_trace(pv_scene* s, const pv_paths* p, const ContArgs& C, const 
     D.touched = touched;
     if (delta) {
       if (!s->cont_trace_delta_blocks) s->cont_trace_delta_blocks = persistent_blocks(s, k_cont_trace<2>);
-      k_cont_trace<2><<<s->cont_trace_delta_blocks, kTraceThreads, 0, st>>>(view(s), frame_lights(s), A, C, D);
+      launch_cont_trace_pdl<2>(s->cont_trace_delta_blocks, view(s), frame_lights(s), A, C, D, st);
     } else {
       if (!s->cont_trace_dep_blocks) s->cont_trace_dep_blocks = persistent_blocks(s, k_cont_trace<1>);
-      k_cont_trace<1><<<s->cont_trace_dep_blocks, kTraceThreads, 0, st>>>(view(s), frame_lights(s), A, C, D);
+      launch_cont_trace_pdl<1>(s->cont_trace_dep_blocks, view(s), frame_lights(s), A, C, D, st);
     }
   } else {
     if (!s->cont_trace_blocks) s->cont_trace_blocks = persistent_blocks(s, k_cont_trace<0>);
-    k_cont_trace<0><<<s->cont_trace_blocks, kTraceThreads, 0, st>>>(view(s), frame_lights(s), A, C, D);
+    launch_cont_trace_pdl<0>(s->cont_trace_blocks, view(s), frame_lights(s), A, C, D, st);
   }
 }
 

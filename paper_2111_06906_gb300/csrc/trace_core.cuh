@@ -147,8 +147,8 @@ __device__ __forceinline__ bool trace_hit(const SceneView& sv, const TraceArgs& 
 // most kMax steps; called by all lanes of the warp (a lane without a ray
 // passes done = true).  Returns whether this lane's ray has ended.  Waiting
 // for the whole warp lets the ray-end code that follows run with all lanes.
-template <int kMax, int S = kStack>
-__device__ __forceinline__ bool step_warp(const SceneView& sv, const Ray& r, Trav& t, int* stk, int excl, Work& wk,
+template <int kMax, int S = kStack, class Stk>
+__device__ __forceinline__ bool step_warp(const SceneView& sv, const Ray& r, Trav& t, Stk& stk, int excl, Work& wk,
                                           bool done) {
 #pragma unroll 1
   for (int i = 0; i < kMax; ++i) {

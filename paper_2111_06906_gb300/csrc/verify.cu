@@ -17,17 +17,75 @@ namespace {
 
 // PV_VERIFY_FLAT: error mode deals the warp's segments out to its lanes
 // (verify_block_flat); 0 keeps thread per path throughout.
+// PV_VERIFY_PERSISTENT: in that mapping each block loops over tiles of
+// paths, so the block prologue and the counter reductions run once per block.
 #ifndef PV_VERIFY_FLAT
 #define PV_VERIFY_FLAT 1
 #endif
+#ifndef PV_VERIFY_PERSISTENT
+#define PV_VERIFY_PERSISTENT 1
+#endif
+// Resident blocks asked of the register allocator for the box-only kernel:
+// 5 (51 registers) beat the 4 that 56 registers allow by 7 % on the villa
+// workload.  The variants with traversal code keep their registers (they
+// would spill).
+#ifndef PV_VERIFY_MIN_BLOCKS
+#define PV_VERIFY_MIN_BLOCKS 5
+#endif
+constexpr bool kVerifyLoop = PV_VERIFY_FLAT && PV_VERIFY_PERSISTENT;
 
+// One thread per path, or (error mode, kVerifyLoop) a grid of resident
+// blocks looping over tiles.  The dependent re-trace kernel may be scheduled
+// as soon as every block has started.
+template <bool kPointVis, bool kExact>
+__device__ __forceinline__ void verify_kernel(const SceneView& sv, const FrameLights& L, const VerifyArgs& A,
+                                              VerifySmem& sm) {
+  launch_dependents();
+  if (PV_VERIFY_FLAT && A.mode == PV_MODE_ERROR) {
+    if (kVerifyLoop) verify_tiles_flat<kPointVis, kExact>(sv, L, A, blockIdx.x, gridDim.x, sm);
+    else verify_block_flat<kPointVis, kExact>(sv, L, A, blockIdx.x * blockDim.x + threadIdx.x, sm);
+  } else {
+    verify_block<kPointVis, kExact>(sv, L, A, blockIdx.x * blockDim.x + threadIdx.x, sm);
+  }
+}
+
+// With visibility rays or triangle tests (traversal code inside).
 template <bool kPointVis, bool kExact>
 __global__ void __launch_bounds__(pvh::kVerifyThreads) k_verify(SceneView sv, FrameLights L, VerifyArgs A) {
   __shared__ VerifySmem sm;
-  if (PV_VERIFY_FLAT && A.mode == PV_MODE_ERROR)
-    verify_block_flat<kPointVis, kExact>(sv, L, A, blockIdx.x * blockDim.x + threadIdx.x, sm);
-  else
-    verify_block<kPointVis, kExact>(sv, L, A, blockIdx.x * blockDim.x + threadIdx.x, sm);
+  verify_kernel<kPointVis, kExact>(sv, L, A, sm);
+}
+
+// Box tests only, the common case.
+__global__ void __launch_bounds__(pvh::kVerifyThreads, PV_VERIFY_MIN_BLOCKS) k_verify_box(SceneView sv, FrameLights L,
+                                                                                         VerifyArgs A) {
+  __shared__ VerifySmem sm;
+  verify_kernel<false, false>(sv, L, A, sm);
+}
+
+// Blocks of a k_verify kernel for n paths: every tile, or in the looping
+// mapping at most the resident blocks of all SMs.
+template <typename K>
+uint32_t verify_grid(pv_scene* s, K kernel, int& per, uint32_t n, int32_t mode) {
+  const uint32_t tiles = (n + pvh::kVerifyThreads - 1) / pvh::kVerifyThreads;
+  if (!kVerifyLoop || mode != PV_MODE_ERROR) return tiles;
+  if (!per) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, pvh::kVerifyThreads, 0);
+    if (per < 1) per = 1;
+  }
+  return std::min<uint32_t>(tiles, (uint32_t)per * (uint32_t)s->num_sms);
+}
+
+template <bool kPointVis, bool kExact>
+void launch_k_verify(pv_scene* s, const SceneView& sv, const FrameLights& L, const VerifyArgs& A, cudaStream_t st) {
+  int& per = s->verify_blocks_per_sm[(kPointVis ? 2 : 0) + (kExact ? 1 : 0)];
+  if (!kPointVis && !kExact) {
+    const uint32_t grid = verify_grid(s, k_verify_box, per, A.n, A.mode);
+    k_verify_box<<<grid, pvh::kVerifyThreads, 0, st>>>(sv, L, A);
+  } else {
+    const uint32_t grid = verify_grid(s, k_verify<kPointVis, kExact>, per, A.n, A.mode);
+    k_verify<kPointVis, kExact><<<grid, pvh::kVerifyThreads, 0, st>>>(sv, L, A);
+  }
 }
 
 __global__ void __launch_bounds__(128, 6) k_continue(SceneView sv, ContArgs A) {
@@ -127,11 +185,10 @@ int launch_verify(pv_scene* s, const pv_paths* paths, const pv_verify_params* pa
       if (((L.moved_mask >> l) & 1u) && s->lights_new[l].type == PV_LIGHT_POINT) point_vis = true;
     const bool exact = params->mode == PV_MODE_NAIVE_EXACT ||
                        (params->mode == PV_MODE_ERROR && (params->flags & PV_FLAG_ERROR_EXACT));
-    const dim3 grid((n + pvh::kVerifyThreads - 1) / pvh::kVerifyThreads);
-    if (point_vis && exact) k_verify<true, true><<<grid, pvh::kVerifyThreads, 0, st>>>(sv, L, A);
-    else if (point_vis) k_verify<true, false><<<grid, pvh::kVerifyThreads, 0, st>>>(sv, L, A);
-    else if (exact) k_verify<false, true><<<grid, pvh::kVerifyThreads, 0, st>>>(sv, L, A);
-    else k_verify<false, false><<<grid, pvh::kVerifyThreads, 0, st>>>(sv, L, A);
+    if (point_vis && exact) launch_k_verify<true, true>(s, sv, L, A, st);
+    else if (point_vis) launch_k_verify<true, false>(s, sv, L, A, st);
+    else if (exact) launch_k_verify<false, true>(s, sv, L, A, st);
+    else launch_k_verify<false, false>(s, sv, L, A, st);
   }
   cont = n && params->mode == PV_MODE_ERROR && (s->moved || L.moved_mask);
   return PV_OK;
@@ -183,13 +240,13 @@ int verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params* p
   mark(0);
   // with maps the deposit runs as its own kernel over every path: the delta form starts from a cleared atlas too
   if (s->has_dm) delta = false;
-  if (atlas && !delta && cudaMemsetAsync(atlas->data, 0, (size_t)atlas->width * atlas->height * 3 * sizeof(uint64_t), st) !=
-                   cudaSuccess)
-    return PV_ERR_CUDA;
   // with maps, prune and fill need Alg. 1's final answer for every path before the list is made
   const bool fuse_deposit = atlas && !s->has_dm;
   const bool will_cont = paths->n && params->mode == PV_MODE_ERROR && (s->moved || L.moved_mask);
   const bool fused = (will_cont || fuse_deposit) && !s->has_dm;
+  if (atlas && !delta &&
+      cudaMemsetAsync(atlas->data, 0, (size_t)atlas->width * atlas->height * 3 * sizeof(uint64_t), st) != cudaSuccess)
+    return PV_ERR_CUDA;
   bool cont = false;
   if ((rc = launch_verify(s, paths, params, d_stats, sv, L, st, cont, fuse_deposit ? s->ws_touched : nullptr, fused,
                           delta ? atlas : nullptr)) != PV_OK)

@@ -351,11 +351,24 @@ __device__ __forceinline__ void warp_append(bool want, uint32_t p, uint32_t* lis
   if (want) list[base + __popc(wm & ((1u << lane) - 1u))] = p;
 }
 
-__device__ __forceinline__ void verify_epilogue(const VerifyArgs& A, uint32_t p, bool want_cont, bool listed,
-                                                uint32_t c_tested, uint32_t c_vis, uint32_t c_reemit, uint32_t c_tail,
-                                                const Work& wk, bool traversed, VerifySmem& sm) {
+// Verification counters of one thread, summed over the paths it handled.
+struct VerifyCount {
+  uint32_t paths = 0, tested = 0, vis = 0, reemit = 0, tail = 0, cont = 0, listed = 0;
+};
+
+// Per-path end of verification: list appends (one atomic per warp) and counts.
+__device__ __forceinline__ void verify_tile_end(const VerifyArgs& A, uint32_t p, bool want_cont, bool listed,
+                                                VerifyCount& vc) {
   warp_append(want_cont, p, A.cont_list, A.cont_count);
   if (A.list_out) warp_append(listed, p, A.list_out, A.list_count);
+  vc.paths += p < A.n ? 1u : 0u;
+  vc.cont += want_cont ? 1u : 0u;
+  vc.listed += listed ? 1u : 0u;
+}
+
+// Block-wide counter sums, one atomic per counter per block (all threads call).
+__device__ __forceinline__ void verify_counts_flush(const VerifyArgs& A, const VerifyCount& vc, const Work& wk,
+                                                    bool traversed, VerifySmem& sm) {
   uint32_t* const ctr[7] = {field(A.stats, offsetof(pv_frame_stats, n_paths)),
                             field(A.stats, offsetof(pv_frame_stats, segments_tested)),
                             field(A.stats, offsetof(pv_frame_stats, vis_rays)),
@@ -363,13 +376,24 @@ __device__ __forceinline__ void verify_epilogue(const VerifyArgs& A, uint32_t p,
                             field(A.stats, offsetof(pv_frame_stats, n_tail)),
                             field(A.stats, offsetof(pv_frame_stats, n_cont)),
                             A.list_out ? field(A.stats, offsetof(pv_frame_stats, n_listed)) : nullptr};
-  const uint32_t val[7] = {p < A.n ? 1u : 0u, c_tested, c_vis, c_reemit, c_tail, want_cont ? 1u : 0u,
-                           listed ? 1u : 0u};
+  const uint32_t val[7] = {vc.paths, vc.tested, vc.vis, vc.reemit, vc.tail, vc.cont, vc.listed};
   block_add_n<7>(ctr, val, sm.red);
   if (traversed) {
     block_add64(A.stats ? (unsigned long long*)&A.stats->node_visits : nullptr, wk.nodes, sm.red64);
     block_add64(A.stats ? (unsigned long long*)&A.stats->tri_tests : nullptr, wk.tris, sm.red64);
   }
+}
+
+__device__ __forceinline__ void verify_epilogue(const VerifyArgs& A, uint32_t p, bool want_cont, bool listed,
+                                                uint32_t c_tested, uint32_t c_vis, uint32_t c_reemit, uint32_t c_tail,
+                                                const Work& wk, bool traversed, VerifySmem& sm) {
+  VerifyCount vc;
+  vc.tested = c_tested;
+  vc.vis = c_vis;
+  vc.reemit = c_reemit;
+  vc.tail = c_tail;
+  verify_tile_end(A, p, want_cont, listed, vc);
+  verify_counts_flush(A, vc, wk, traversed, sm);
 }
 
 // kPointVis: a moved point light needs visibility rays; kExact: segments are
@@ -683,16 +707,12 @@ __device__ __forceinline__ void continue_path(const SceneView& sv, int root, con
 // path is tested there too in error mode, the only mode this mapping serves
 // (the naive modes stop at a path's first hit).  Blocks of at most 256.
 template <bool kPointVis, bool kExact, int S = kStack>
-__device__ __forceinline__ void verify_block_flat(const SceneView& sv, const FrameLights& L, const VerifyArgs& A,
-                                                  uint32_t p, VerifySmem& sm) {
-  verify_smem_init(sv, sm);
-  Work wk;
-  const int root = *sv.root;
+__device__ __forceinline__ void verify_tile_flat(const SceneView& sv, const FrameLights& L, const VerifyArgs& A,
+                                                 int root, uint32_t p, VerifySmem& sm, VerifyCount& vc, Work& wk) {
   const uint32_t n = A.n;
   const int lane = threadIdx.x & 31;
   const uint32_t wbase = threadIdx.x & ~31u;
   const bool test_old = kExact && (A.flags & PV_FLAG_TEST_OLD_TRIS) != 0;
-  uint32_t c_tested = 0, c_vis = 0, c_reemit = 0, c_tail = 0;
   PathCheck v;
   v.test = false;
   v.nseg = 0;
@@ -700,7 +720,7 @@ __device__ __forceinline__ void verify_block_flat(const SceneView& sv, const Fra
   v.blocked1 = false;
   v.replaced = false;
   v.cell = 0;
-  if (p < n) v = origin_stage<kPointVis, S>(sv, L, A, root, p, c_vis, c_reemit, wk);
+  if (p < n) v = origin_stage<kPointVis, S>(sv, L, A, root, p, vc.vis, vc.reemit, wk);
   sm.hitmask[threadIdx.x] = 0u;
   sm.slotmask[threadIdx.x] = 0u;
   // segments of the warp's tested paths, numbered by an inclusive prefix over the lanes
@@ -747,14 +767,38 @@ __device__ __forceinline__ void verify_block_flat(const SceneView& sv, const Fra
   bool want_cont = false;
   if (p < n && v.test) {
     const uint32_t mask = sm.hitmask[threadIdx.x];
-    if (sv.moved && v.nseg >= 1) c_tested = __popc(~sm.slotmask[threadIdx.x] & ((2u << v.nseg) - 2u));
-    want_cont = finish_stage(A, p, v, mask, c_reemit, c_tail);
+    if (sv.moved && v.nseg >= 1) vc.tested += __popc(~sm.slotmask[threadIdx.x] & ((2u << v.nseg) - 2u));
+    want_cont = finish_stage(A, p, v, mask, vc.reemit, vc.tail);
     mark_touched(A, p, mask != 0 || v.replaced, v);
   } else if (p < n) {
     mark_touched(A, p, v.replaced, v);
   }
-  verify_epilogue(A, p, want_cont, p < n && v.replaced, c_tested, c_vis, c_reemit, c_tail, wk, kPointVis || kExact,
-                  sm);
+  verify_tile_end(A, p, want_cont, p < n && v.replaced, vc);
+}
+
+template <bool kPointVis, bool kExact, int S = kStack>
+__device__ __forceinline__ void verify_block_flat(const SceneView& sv, const FrameLights& L, const VerifyArgs& A,
+                                                  uint32_t p, VerifySmem& sm) {
+  verify_smem_init(sv, sm);
+  Work wk;
+  VerifyCount vc;
+  verify_tile_flat<kPointVis, kExact, S>(sv, L, A, *sv.root, p, sm, vc, wk);
+  verify_counts_flush(A, vc, wk, kPointVis || kExact, sm);
+}
+
+// The flat mapping over tiles t = first, first + stride, ... of blockDim.x
+// paths, with the block prologue and the counter reductions done once.
+template <bool kPointVis, bool kExact, int S = kStack>
+__device__ __forceinline__ void verify_tiles_flat(const SceneView& sv, const FrameLights& L, const VerifyArgs& A,
+                                                  uint32_t first, uint32_t stride, VerifySmem& sm) {
+  verify_smem_init(sv, sm);
+  Work wk;
+  VerifyCount vc;
+  const int root = *sv.root;
+  const uint32_t tiles = (A.n + blockDim.x - 1) / blockDim.x;
+  for (uint32_t t = first; t < tiles; t += stride)
+    verify_tile_flat<kPointVis, kExact, S>(sv, L, A, root, t * blockDim.x + threadIdx.x, sm, vc, wk);
+  verify_counts_flush(A, vc, wk, kPointVis || kExact, sm);
 }
 
 }  // namespace pvk
