@@ -151,25 +151,45 @@ __global__ void k_b_frame_top(const BScene* S, const BFrame* F) {
 }
 
 // ---------------------------------------------------------------- verify
-// One block = one tile of one scene (tab: scene, tile); the scene's view,
-// lights and arguments are staged in shared memory.
+// Resident blocks loop over the tile table (tab: scene, tile), in steps of
+// the grid.  Entries of one scene are consecutive in the table, so a block
+// stages a scene's view, lights, arguments and moved-object boxes in shared
+// memory when its next entry belongs to another scene, and adds that scene's
+// counters when it leaves it.
+// Box-only variants are held to 5 resident blocks of 256 threads (51 registers), as the single-scene kernel.
 template <bool kPointVis, bool kExact, int kMap>
-__global__ void __launch_bounds__(256) k_b_verify(const BScene* S, const BFrame* F, const uint32_t* tab) {
+__global__ void __launch_bounds__(256, (kPointVis || kExact) ? 2 : 5) k_b_verify(const BScene* S, const BFrame* F,
+                                                                                  const uint32_t* tab, uint32_t n_entries) {
   __shared__ VerifySmem sm;
   __shared__ SceneView s_sv;
   __shared__ FrameLights s_L;
   __shared__ VerifyArgs s_V;
-  const uint32_t sc = tab[2 * blockIdx.x], tile = tab[2 * blockIdx.x + 1];
-  copy_words(&s_sv, &S[sc].sv, sizeof(SceneView), threadIdx.x, blockDim.x);
-  copy_words(&s_L, &F[sc].L, sizeof(FrameLights), threadIdx.x, blockDim.x);
-  copy_words(&s_V, &S[sc].V, sizeof(VerifyArgs), threadIdx.x, blockDim.x);
-  __syncthreads();
-  if (threadIdx.x == 0) s_sv.moved = F[sc].moved;
-  __syncthreads();
-  const uint32_t p = tile * blockDim.x + threadIdx.x;
-  if (kMap == 2) verify_block_flat<kPointVis, kExact>(s_sv, s_L, s_V, p, sm);
-  else if (kMap == 1) verify_block_warp<kPointVis, kExact>(s_sv, s_L, s_V, p, sm);
-  else verify_block<kPointVis, kExact>(s_sv, s_L, s_V, p, sm);
+  uint32_t cur = 0xFFFFFFFFu;
+  int root = 0;
+  Work wk;
+  VerifyCount vc;
+  for (uint32_t e = blockIdx.x; e < n_entries; e += gridDim.x) {
+    const uint32_t sc = tab[2 * e], tile = tab[2 * e + 1];
+    if (sc != cur) {
+      if (cur != 0xFFFFFFFFu) {
+        verify_counts_flush(s_V, vc, wk, kPointVis || kExact, sm);
+        vc = VerifyCount();
+        wk = Work();
+      }
+      __syncthreads();                         // the previous scene's shared state is no longer read
+      copy_words(&s_sv, &S[sc].sv, sizeof(SceneView), threadIdx.x, blockDim.x);
+      copy_words(&s_L, &F[sc].L, sizeof(FrameLights), threadIdx.x, blockDim.x);
+      copy_words(&s_V, &S[sc].V, sizeof(VerifyArgs), threadIdx.x, blockDim.x);
+      __syncthreads();
+      if (threadIdx.x == 0) s_sv.moved = F[sc].moved;
+      __syncthreads();
+      verify_smem_init(s_sv, sm);
+      root = *s_sv.root;
+      cur = sc;
+    }
+    verify_tile<kPointVis, kExact, kMap>(s_sv, s_L, s_V, root, tile * blockDim.x + threadIdx.x, sm, vc, wk);
+  }
+  if (cur != 0xFFFFFFFFu) verify_counts_flush(s_V, vc, wk, kPointVis || kExact, sm);
 }
 
 // Shared-memory layout of the persistent kernels: per scene its view, its
@@ -542,7 +562,7 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_BATCH_CT_MIN_BLOCKS) k_
 }
 
 // ---------------------------------------------------------------- kernel selection
-using VerifyKernel = void (*)(const BScene*, const BFrame*, const uint32_t*);
+using VerifyKernel = void (*)(const BScene*, const BFrame*, const uint32_t*, uint32_t);
 using ContKernel = void (*)(const BScene*, const BFrame*, uint32_t, BCounters*);
 using TraceKernel = void (*)(const BScene*, const BFrame*, uint32_t, BCounters*);
 
@@ -586,6 +606,7 @@ struct pv_batch {
   bool slot_used[kRing] = {};
   uint32_t next_slot = 0;
   uint32_t* d_vtab[3] = {};                   // verify tiles of 64, 128, 256 paths
+  int occ_verify[2][3][3] = {};               // resident verify blocks per SM: [vis][mapping][tile size]
   uint32_t n_vtiles[3] = {};
   uint32_t* d_ctab = nullptr;
   uint32_t n_ctiles = 0;
@@ -656,8 +677,14 @@ int enqueue_frame(pv_batch* b, cudaStream_t st, bool vis, const pv_batch_config&
   k_b_frame_top<<<n, 32, 0, st>>>(b->d_scenes, b->d_frames);
   mark(1);
   const int ti = thread_index(c.verify_threads);
-  verify_kernel(vis, b->exact, c.verify_mapping)<<<b->n_vtiles[ti], c.verify_threads, 0, st>>>(
-      b->d_scenes, b->d_frames, b->d_vtab[ti]);
+  const VerifyKernel vk = verify_kernel(vis, b->exact, c.verify_mapping);
+  int& per = b->occ_verify[vis ? 1 : 0][c.verify_mapping < 0 || c.verify_mapping > 2 ? 0 : c.verify_mapping][ti];
+  if (!per) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, vk, c.verify_threads, 0);
+    if (per < 1) per = 1;
+  }
+  const uint32_t grid = std::min<uint32_t>(b->n_vtiles[ti], (uint32_t)per * (uint32_t)b->num_sms);
+  vk<<<grid, c.verify_threads, 0, st>>>(b->d_scenes, b->d_frames, b->d_vtab[ti], b->n_vtiles[ti]);
   mark(2);
   if (b->fused) {                             // compaction of what verify marked, then Alg. 1 + re-trace
     mark(3);

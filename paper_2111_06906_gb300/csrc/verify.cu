@@ -17,8 +17,8 @@ namespace {
 
 // PV_VERIFY_FLAT: error mode deals the warp's segments out to its lanes
 // (verify_block_flat); 0 keeps thread per path throughout.
-// PV_VERIFY_PERSISTENT: in that mapping each block loops over tiles of
-// paths, so the block prologue and the counter reductions run once per block.
+// PV_VERIFY_PERSISTENT: each block loops over tiles of paths, so the block
+// prologue and the counter reductions run once per block.
 #ifndef PV_VERIFY_FLAT
 #define PV_VERIFY_FLAT 1
 #endif
@@ -34,18 +34,20 @@ namespace {
 #endif
 constexpr bool kVerifyLoop = PV_VERIFY_FLAT && PV_VERIFY_PERSISTENT;
 
-// One thread per path, or (error mode, kVerifyLoop) a grid of resident
-// blocks looping over tiles.  The dependent re-trace kernel may be scheduled
+// Flat segment mapping in error mode, else thread per path; with
+// kVerifyLoop a grid of resident blocks looping over tiles.  The dependent re-trace kernel may be scheduled
 // as soon as every block has started.
 template <bool kPointVis, bool kExact>
 __device__ __forceinline__ void verify_kernel(const SceneView& sv, const FrameLights& L, const VerifyArgs& A,
                                               VerifySmem& sm) {
   launch_dependents();
-  if (PV_VERIFY_FLAT && A.mode == PV_MODE_ERROR) {
-    if (kVerifyLoop) verify_tiles_flat<kPointVis, kExact>(sv, L, A, blockIdx.x, gridDim.x, sm);
-    else verify_block_flat<kPointVis, kExact>(sv, L, A, blockIdx.x * blockDim.x + threadIdx.x, sm);
+  const bool flat = PV_VERIFY_FLAT && A.mode == PV_MODE_ERROR;
+  if (kVerifyLoop) {
+    if (flat) verify_tiles<kPointVis, kExact, 2>(sv, L, A, blockIdx.x, gridDim.x, sm);
+    else verify_tiles<kPointVis, kExact, 0>(sv, L, A, blockIdx.x, gridDim.x, sm);
   } else {
-    verify_block<kPointVis, kExact>(sv, L, A, blockIdx.x * blockDim.x + threadIdx.x, sm);
+    if (flat) verify_block_flat<kPointVis, kExact>(sv, L, A, blockIdx.x * blockDim.x + threadIdx.x, sm);
+    else verify_block<kPointVis, kExact>(sv, L, A, blockIdx.x * blockDim.x + threadIdx.x, sm);
   }
 }
 
@@ -63,12 +65,12 @@ __global__ void __launch_bounds__(pvh::kVerifyThreads, PV_VERIFY_MIN_BLOCKS) k_v
   verify_kernel<false, false>(sv, L, A, sm);
 }
 
-// Blocks of a k_verify kernel for n paths: every tile, or in the looping
-// mapping at most the resident blocks of all SMs.
+// Blocks of a k_verify kernel for n paths: every tile, or with the tile
+// loop at most the resident blocks of all SMs.
 template <typename K>
-uint32_t verify_grid(pv_scene* s, K kernel, int& per, uint32_t n, int32_t mode) {
+uint32_t verify_grid(pv_scene* s, K kernel, int& per, uint32_t n) {
   const uint32_t tiles = (n + pvh::kVerifyThreads - 1) / pvh::kVerifyThreads;
-  if (!kVerifyLoop || mode != PV_MODE_ERROR) return tiles;
+  if (!kVerifyLoop) return tiles;
   if (!per) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, pvh::kVerifyThreads, 0);
     if (per < 1) per = 1;
@@ -80,10 +82,10 @@ template <bool kPointVis, bool kExact>
 void launch_k_verify(pv_scene* s, const SceneView& sv, const FrameLights& L, const VerifyArgs& A, cudaStream_t st) {
   int& per = s->verify_blocks_per_sm[(kPointVis ? 2 : 0) + (kExact ? 1 : 0)];
   if (!kPointVis && !kExact) {
-    const uint32_t grid = verify_grid(s, k_verify_box, per, A.n, A.mode);
+    const uint32_t grid = verify_grid(s, k_verify_box, per, A.n);
     k_verify_box<<<grid, pvh::kVerifyThreads, 0, st>>>(sv, L, A);
   } else {
-    const uint32_t grid = verify_grid(s, k_verify<kPointVis, kExact>, per, A.n, A.mode);
+    const uint32_t grid = verify_grid(s, k_verify<kPointVis, kExact>, per, A.n);
     k_verify<kPointVis, kExact><<<grid, pvh::kVerifyThreads, 0, st>>>(sv, L, A);
   }
 }

@@ -384,17 +384,6 @@ __device__ __forceinline__ void verify_counts_flush(const VerifyArgs& A, const V
   }
 }
 
-__device__ __forceinline__ void verify_epilogue(const VerifyArgs& A, uint32_t p, bool want_cont, bool listed,
-                                                uint32_t c_tested, uint32_t c_vis, uint32_t c_reemit, uint32_t c_tail,
-                                                const Work& wk, bool traversed, VerifySmem& sm) {
-  VerifyCount vc;
-  vc.tested = c_tested;
-  vc.vis = c_vis;
-  vc.reemit = c_reemit;
-  vc.tail = c_tail;
-  verify_tile_end(A, p, want_cont, listed, vc);
-  verify_counts_flush(A, vc, wk, traversed, sm);
-}
 
 // kPointVis: a moved point light needs visibility rays; kExact: segments are
 // tested against triangles (not only boxes).  Specialised so the common case
@@ -404,17 +393,13 @@ __device__ __forceinline__ void verify_epilogue(const VerifyArgs& A, uint32_t p,
 // idles), Sec. 3.2's segments in order from the light; called by every thread
 // of the block (block reductions inside).
 template <bool kPointVis, bool kExact, int S = kStack>
-__device__ __forceinline__ void verify_block(const SceneView& sv, const FrameLights& L, const VerifyArgs& A, uint32_t p,
-                                             VerifySmem& sm) {
-  verify_smem_init(sv, sm);
-  Work wk;
-  const int root = *sv.root;
+__device__ __forceinline__ void verify_tile_thread(const SceneView& sv, const FrameLights& L, const VerifyArgs& A,
+                                                   int root, uint32_t p, VerifySmem& sm, VerifyCount& vc, Work& wk) {
   const uint32_t n = A.n;
   const bool test_old = kExact && (A.flags & PV_FLAG_TEST_OLD_TRIS) != 0;
-  uint32_t c_tested = 0, c_vis = 0, c_reemit = 0, c_tail = 0;
   bool want_cont = false, touched = false, listed = false;
   if (p < n) {
-    const PathCheck v = origin_stage<kPointVis, S>(sv, L, A, root, p, c_vis, c_reemit, wk);
+    const PathCheck v = origin_stage<kPointVis, S>(sv, L, A, root, p, vc.vis, vc.reemit, wk);
     if (v.test) {
       // ---- Sec. 3.2: segments in order, starting from the light
       uint32_t mask = 0;
@@ -426,7 +411,7 @@ __device__ __forceinline__ void verify_block(const SceneView& sv, const FrameLig
         const int prim_b = __float_as_int(vb.w);
         bool hit = slot_hit(sv, k, prim_a, prim_b, v.blocked1);
         if (!hit && sv.moved) {
-          ++c_tested;
+          ++vc.tested;
           hit = kExact ? seg_vs_moved<S>(sv, sm.cull, sm.uni, sm.groups, false, test_old, a, b, wk)
                        : seg_vs_moved<S>(sv, sm.cull, sm.uni, sm.groups, true, false, a, b, wk);
         }
@@ -437,14 +422,24 @@ __device__ __forceinline__ void verify_block(const SceneView& sv, const FrameLig
         a = b;
         prim_a = prim_b;
       }
-      want_cont = finish_stage(A, p, v, mask, c_reemit, c_tail);
+      want_cont = finish_stage(A, p, v, mask, vc.reemit, vc.tail);
       touched = mask != 0;                   // handed to Alg. 1, or (naive modes) marked for re-tracing
       listed = mask != 0 && A.mode != PV_MODE_ERROR;
     }
     mark_touched(A, p, touched || v.replaced, v);
     listed = listed || v.replaced;
   }
-  verify_epilogue(A, p, want_cont, listed, c_tested, c_vis, c_reemit, c_tail, wk, kPointVis || kExact, sm);
+  verify_tile_end(A, p, want_cont, listed, vc);
+}
+
+template <bool kPointVis, bool kExact, int S = kStack>
+__device__ __forceinline__ void verify_block(const SceneView& sv, const FrameLights& L, const VerifyArgs& A, uint32_t p,
+                                             VerifySmem& sm) {
+  verify_smem_init(sv, sm);
+  Work wk;
+  VerifyCount vc;
+  verify_tile_thread<kPointVis, kExact, S>(sv, L, A, *sv.root, p, sm, vc, wk);
+  verify_counts_flush(A, vc, wk, kPointVis || kExact, sm);
 }
 
 // Warp per path: each lane runs the origin stage of its own path, then the
@@ -454,17 +449,13 @@ __device__ __forceinline__ void verify_block(const SceneView& sv, const FrameLig
 // follows verify_block's sequential order, while the traversal counters
 // count every pair tested here.
 template <bool kPointVis, bool kExact, int S = kStack>
-__device__ __forceinline__ void verify_block_warp(const SceneView& sv, const FrameLights& L, const VerifyArgs& A,
-                                                  uint32_t p, VerifySmem& sm) {
-  verify_smem_init(sv, sm);
-  Work wk;
-  const int root = *sv.root;
+__device__ __forceinline__ void verify_tile_warp(const SceneView& sv, const FrameLights& L, const VerifyArgs& A,
+                                                 int root, uint32_t p, VerifySmem& sm, VerifyCount& vc, Work& wk) {
   const uint32_t n = A.n;
   const int lane = threadIdx.x & 31;
   const bool test_old = kExact && (A.flags & PV_FLAG_TEST_OLD_TRIS) != 0;
   const bool error_mode = A.mode == PV_MODE_ERROR;
   const int n_moved = sm.n_moved;
-  uint32_t c_tested = 0, c_vis = 0, c_reemit = 0, c_tail = 0;
   PathCheck v;
   v.test = false;
   v.nseg = 0;
@@ -472,7 +463,7 @@ __device__ __forceinline__ void verify_block_warp(const SceneView& sv, const Fra
   v.blocked1 = false;
   v.replaced = false;
   v.cell = 0;
-  if (p < n) v = origin_stage<kPointVis, S>(sv, L, A, root, p, c_vis, c_reemit, wk);
+  if (p < n) v = origin_stage<kPointVis, S>(sv, L, A, root, p, vc.vis, vc.reemit, wk);
   uint32_t my_mask = 0;
   for (unsigned todo = __ballot_sync(0xffffffffu, v.test); todo; todo &= todo - 1) {
     const int j = __ffs(todo) - 1;
@@ -515,15 +506,25 @@ __device__ __forceinline__ void verify_block_warp(const SceneView& sv, const Fra
         m = 1u << last;
       }
       // segments sequential verification would have tested: 1..last, not slot-hit
-      if (sv.moved && last >= 1) c_tested += __popc(~smask & ((2u << last) - 2u));
+      if (sv.moved && last >= 1) vc.tested += __popc(~smask & ((2u << last) - 2u));
       my_mask = m;
     }
   }
   bool want_cont = false;
-  if (p < n && v.test) want_cont = finish_stage(A, p, v, my_mask, c_reemit, c_tail);
+  if (p < n && v.test) want_cont = finish_stage(A, p, v, my_mask, vc.reemit, vc.tail);
   if (p < n) mark_touched(A, p, (v.test && my_mask != 0) || v.replaced, v);
   const bool listed = p < n && (v.replaced || (v.test && my_mask != 0 && !error_mode));
-  verify_epilogue(A, p, want_cont, listed, c_tested, c_vis, c_reemit, c_tail, wk, kPointVis || kExact, sm);
+  verify_tile_end(A, p, want_cont, listed, vc);
+}
+
+template <bool kPointVis, bool kExact, int S = kStack>
+__device__ __forceinline__ void verify_block_warp(const SceneView& sv, const FrameLights& L, const VerifyArgs& A,
+                                                  uint32_t p, VerifySmem& sm) {
+  verify_smem_init(sv, sm);
+  Work wk;
+  VerifyCount vc;
+  verify_tile_warp<kPointVis, kExact, S>(sv, L, A, *sv.root, p, sm, vc, wk);
+  verify_counts_flush(A, vc, wk, kPointVis || kExact, sm);
 }
 
 struct ContArgs {
@@ -786,18 +787,29 @@ __device__ __forceinline__ void verify_block_flat(const SceneView& sv, const Fra
   verify_counts_flush(A, vc, wk, kPointVis || kExact, sm);
 }
 
-// The flat mapping over tiles t = first, first + stride, ... of blockDim.x
-// paths, with the block prologue and the counter reductions done once.
-template <bool kPointVis, bool kExact, int S = kStack>
-__device__ __forceinline__ void verify_tiles_flat(const SceneView& sv, const FrameLights& L, const VerifyArgs& A,
-                                                  uint32_t first, uint32_t stride, VerifySmem& sm) {
+// One tile of paths p (this thread's) in mapping kMap: 0 thread per path,
+// 1 warp per path, 2 flat segments (error mode).  No block-wide barrier
+// inside: the caller staged the block prologue and sums the counters.
+template <bool kPointVis, bool kExact, int kMap, int S = kStack>
+__device__ __forceinline__ void verify_tile(const SceneView& sv, const FrameLights& L, const VerifyArgs& A, int root,
+                                            uint32_t p, VerifySmem& sm, VerifyCount& vc, Work& wk) {
+  if (kMap == 2) verify_tile_flat<kPointVis, kExact, S>(sv, L, A, root, p, sm, vc, wk);
+  else if (kMap == 1) verify_tile_warp<kPointVis, kExact, S>(sv, L, A, root, p, sm, vc, wk);
+  else verify_tile_thread<kPointVis, kExact, S>(sv, L, A, root, p, sm, vc, wk);
+}
+
+// Mapping kMap over tiles t = first, first + stride, ... of blockDim.x paths,
+// with the block prologue and the counter reductions done once.
+template <bool kPointVis, bool kExact, int kMap, int S = kStack>
+__device__ __forceinline__ void verify_tiles(const SceneView& sv, const FrameLights& L, const VerifyArgs& A,
+                                             uint32_t first, uint32_t stride, VerifySmem& sm) {
   verify_smem_init(sv, sm);
   Work wk;
   VerifyCount vc;
   const int root = *sv.root;
   const uint32_t tiles = (A.n + blockDim.x - 1) / blockDim.x;
   for (uint32_t t = first; t < tiles; t += stride)
-    verify_tile_flat<kPointVis, kExact, S>(sv, L, A, root, t * blockDim.x + threadIdx.x, sm, vc, wk);
+    verify_tile<kPointVis, kExact, kMap, S>(sv, L, A, root, t * blockDim.x + threadIdx.x, sm, vc, wk);
   verify_counts_flush(A, vc, wk, kPointVis || kExact, sm);
 }
 
