@@ -683,7 +683,7 @@ int enqueue_frame(pv_batch* b, cudaStream_t st, bool vis, const pv_batch_config&
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, vk, c.verify_threads, 0);
     if (per < 1) per = 1;
   }
-  const uint32_t grid = std::min<uint32_t>(b->n_vtiles[ti], (uint32_t)per * (uint32_t)b->num_sms);
+  const uint32_t grid = std::min<uint32_t>(b->n_vtiles[ti], pvh::verify_block_cap((uint32_t)per * (uint32_t)b->num_sms));
   vk<<<grid, c.verify_threads, 0, st>>>(b->d_scenes, b->d_frames, b->d_vtab[ti], b->n_vtiles[ti]);
   mark(2);
   if (b->fused) {                             // compaction of what verify marked, then Alg. 1 + re-trace

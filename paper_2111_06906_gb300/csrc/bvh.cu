@@ -432,11 +432,39 @@ __global__ void k_wide_links(const WNode* wdyn, const uint32_t* n_wide, int w_of
   w_nch[w] = (uint8_t)m;
 }
 
-__global__ void __launch_bounds__(256) k_refit_wide(XformParams P, RefitArgs R) {
+// Refit frames in one launch: the direct refit (refit_tri), then the last
+// block to finish runs the frame's pose bookkeeping, the top level and the
+// moved-object groups (what k_frame_top does alone when nothing moved).
+struct TopArgs {
+  uint32_t* done;              // blocks finished (reset by the last)
+  DynObj* objs;
+  float* xf_old;
+  float* xf_new;
+  WNode* wnodes;               // the whole wide array
+  const Tri* tris;
+  int top_off, static_root;
+  int* root_out;
+  MovedGroups* groups;
+};
+
+__global__ void __launch_bounds__(256) k_refit_wide(XformParams P, RefitArgs R, TopArgs T) {
+  __shared__ bool s_last;
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t s = i < R.n ? R.tri_slot[i] : 0u;
   const bool mv = i < R.n && ((P.moved >> s) & 1ull);
   refit_tri(P.xf[mv ? s : 0], mv, s, R, i);
+  __threadfence();                             // this block's triangles, boxes and object-box atomics
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(T.done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();                             // every block's writes are visible from here
+  if (threadIdx.x == 0) *T.done = 0u;
+  pose_bookkeeping(P.xf, P.moved, P.n_dyn, T.objs, T.xf_old, T.xf_new, R.obox);
+  __syncthreads();
+  build_top_block(T.wnodes, T.tris, T.top_off, T.static_root, T.objs, (int)P.n_dyn, T.root_out);
+  __syncthreads();
+  if (T.groups) build_moved_groups_block(T.objs, (int)P.n_dyn, P.moved, T.groups);
 }
 
 // Pose bookkeeping of every slot, then (when objects moved) the top level
@@ -850,10 +878,10 @@ int build_bvh(pv_scene* s, const float* h_verts, const std::vector<uint32_t>& st
   fail(cudaMemset(s->groups, 0, sizeof(MovedGroups)));
   fail(cudaMalloc(&s->w_link, nd * sizeof(uint32_t)));
   fail(cudaMalloc(&s->w_nch, nd * sizeof(uint8_t)));
-  fail(cudaMalloc(&s->w_arrive, nd * sizeof(uint32_t)));
+  fail(cudaMalloc(&s->w_arrive, (nd + 1) * sizeof(uint32_t)));   // + the refit's block counter
   fail(cudaMalloc(&s->t_link, nd * sizeof(uint32_t)));
   fail(cudaMalloc(&s->obox, kMaxDyn * 6 * sizeof(int)));
-  fail(cudaMemset(s->w_arrive, 0, nd * sizeof(uint32_t)));
+  fail(cudaMemset(s->w_arrive, 0, (nd + 1) * sizeof(uint32_t)));
   {
     int ob[kMaxDyn * 6];
     for (int i = 0; i < kMaxDyn * 6; ++i) ob[i] = ord_of(i % 6 < 3 ? 3.0e38f : -3.0e38f);
@@ -919,7 +947,19 @@ void launch_update_dynamic(pv_scene* s, cudaStream_t st) {
         R.w_arrive = s->w_arrive;
         R.wdyn = s->wnodes + s->w_dyn_off;
         R.obox = s->obox;
-        k_refit_wide<<<blocks(n, 256), 256, 0, st>>>(P, R);
+        TopArgs T;
+        T.done = s->w_arrive + n;              // one word past the arrival counters
+        T.objs = s->objs;
+        T.xf_old = s->xf_old;
+        T.xf_new = s->xf_new;
+        T.wnodes = s->wnodes;
+        T.tris = s->tris;
+        T.top_off = (int)s->w_top_off;
+        T.static_root = s->s_wroot;
+        T.root_out = s->root;
+        T.groups = s->groups;
+        k_refit_wide<<<blocks(n, 256), 256, 0, st>>>(P, R, T);
+        return;
       }
       k_frame_top<<<1, 32, 0, st>>>(P, s->objs, s->xf_old, s->xf_new, s->obox, s->wnodes, s->tris, (int)s->w_top_off,
                                     s->s_wroot, s->root, s->groups);

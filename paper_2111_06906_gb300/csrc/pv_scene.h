@@ -1,6 +1,7 @@
 // Host-side scene object and launch helpers shared by the library's
 // translation units (not part of the public ABI).
 #pragma once
+#include <cstdlib>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -43,7 +44,8 @@ struct pv_scene {
   // direct refit of the dynamic wide nodes (after the first collapse)
   uint32_t* w_link = nullptr;        // [n_dyn_tris] dynamic wide node -> parent (local << 2 | slot), ~0u at a root
   uint8_t* w_nch = nullptr;          // [n_dyn_tris] children in use per dynamic wide node
-  uint32_t* w_arrive = nullptr;      // [n_dyn_tris] children refitted this frame (reset by the last)
+  uint32_t* w_arrive = nullptr;      // [n_dyn_tris] children refitted this frame (reset by the last), then the
+                                     // refit's finished-block count
   uint32_t* t_link = nullptr;        // [n_dyn_tris] dynamic triangle -> parent wide node (local << 2 | slot)
   int* obox = nullptr;               // [kMaxDyn][6] exact new boxes of the frame, order-preserving integers
   uint8_t* d_tri_slot = nullptr;     // [n_dyn_tris] slot per dynamic triangle
@@ -118,6 +120,16 @@ constexpr int kVerifyThreads = 256;
 constexpr int kCompactThreads = 256;
 constexpr int kCompactItems = 16;    // paths per thread in the compaction tile
 constexpr uint32_t kTile = kCompactThreads * kCompactItems;
+
+// Verify blocks for a tile loop: ``resident``, or fewer when the environment
+// variable PV_VERIFY_MAX_BLOCKS asks for fewer (testing and tuning).
+inline uint32_t verify_block_cap(uint32_t resident) {
+  if (const char* e = std::getenv("PV_VERIFY_MAX_BLOCKS")) {
+    const long m = std::strtol(e, nullptr, 10);
+    if (m > 0 && (uint32_t)m < resident) return (uint32_t)m;
+  }
+  return resident;
+}
 
 // work counter slots in ws_ctr
 enum { CTR_CONT = 0, CTR_TRACE = 1, CTR_TILE = 2, CTR_ALL = 3, CTR_LIST = 4 };

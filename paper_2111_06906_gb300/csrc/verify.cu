@@ -66,7 +66,8 @@ __global__ void __launch_bounds__(pvh::kVerifyThreads, PV_VERIFY_MIN_BLOCKS) k_v
 }
 
 // Blocks of a k_verify kernel for n paths: every tile, or with the tile
-// loop at most the resident blocks of all SMs.
+// loop at most the resident blocks of all SMs (fewer when PV_VERIFY_MAX_BLOCKS
+// asks for fewer: a testing and tuning override).
 template <typename K>
 uint32_t verify_grid(pv_scene* s, K kernel, int& per, uint32_t n) {
   const uint32_t tiles = (n + pvh::kVerifyThreads - 1) / pvh::kVerifyThreads;
@@ -75,7 +76,7 @@ uint32_t verify_grid(pv_scene* s, K kernel, int& per, uint32_t n) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, pvh::kVerifyThreads, 0);
     if (per < 1) per = 1;
   }
-  return std::min<uint32_t>(tiles, (uint32_t)per * (uint32_t)s->num_sms);
+  return std::min<uint32_t>(tiles, pvh::verify_block_cap((uint32_t)per * (uint32_t)s->num_sms));
 }
 
 template <bool kPointVis, bool kExact>

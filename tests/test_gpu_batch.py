@@ -146,6 +146,21 @@ def test_batch_modes_match_single_scene_calls(mode, flags, mapping):
         ln.close()
 
 
+@pytest.mark.parametrize("mapping", [0, 1, 2])
+def test_batch_verify_few_blocks_matches_single_scene_calls(monkeypatch, mapping):
+    """Two verify blocks for the whole batch: each block loops over 64-path
+    tiles of every scene in turn and restages the scene's shared state at each
+    change; records, lists and counters stay those of the single-scene calls."""
+    monkeypatch.setenv("PV_VERIFY_MAX_BLOCKS", "2")
+    lanes = [Lane(sc, 9 + i) for i, sc in enumerate(_mix())]
+    b = pv.pv_batch_create([ln.item() for ln in lanes], pv.PV_MODE_ERROR, 0.01)
+    pv.pv_batch_set_config(b, verify_mapping=mapping, verify_threads=64)
+    _run(lanes, b, range(2, 5), pv.PV_MODE_ERROR, 0.01, 0, traversal_counters=mapping != 1)
+    pv.pv_batch_destroy(b)
+    for ln in lanes:
+        ln.close()
+
+
 def test_batch_flat_mapping_error_exact_matches_single_scene_calls():
     lanes = [Lane(sc, 5 + i) for i, sc in enumerate(_mix()[:4])]
     b = pv.pv_batch_create([ln.item() for ln in lanes], pv.PV_MODE_ERROR, 0.01, pv.PV_FLAG_ERROR_EXACT)

@@ -111,6 +111,21 @@ def test_verify_parity_moving_torus(mode, tau, flags):
     _verify_case(kit.box_with_torus(8000, B=4), mode, tau, flags)
 
 
+@pytest.mark.parametrize("mode,tau,flags", [(0, 0.01, 0), (1, 0.01, 0), (2, 0.01, 0),
+                                            (2, 0.01, pv.PV_FLAG_ERROR_EXACT)])
+def test_verify_parity_few_resident_blocks(monkeypatch, mode, tau, flags):
+    """Three verify blocks for 8000 paths: each block loops over about ten
+    256-path tiles, staging its prologue and summing its counters once.  The
+    records and lists match the oracle, and every counter equals that of the
+    default grid."""
+    sc = kit.box_with_torus(8000, B=4)
+    _, _, stats_default, _ = _verify_case(sc, mode, tau, flags)
+    monkeypatch.setenv("PV_VERIFY_MAX_BLOCKS", "3")
+    _, _, stats_few, _ = _verify_case(sc, mode, tau, flags)
+    assert stats_few == stats_default
+    assert stats_few["n_paths"] == 8000
+
+
 def test_verify_parity_area_light_moves_and_tilts():
     a = math.radians(4.0)
     sc = kit.rect_light_over_floor(20_000, shift=lambda f: (0.07 * (f - 1), 0.0, 0.02 * (f - 1)),
