@@ -299,7 +299,9 @@ def run_ours(args, ws, rank, local):
     reuse_parts = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in ev]).mean(axis=0)
     stage_ms = pv.pv_stage_times(h, K).mean(axis=0)     # k_verify, compaction, fused kernel, whole call
     pv.pv_stage_timing(h, 0)
-    instrumented_ms = float(np.mean([e[0].elapsed_time(e[4]) for e in ev]))
+    per_frame = np.array([e[0].elapsed_time(e[4]) for e in ev])
+    instrumented_ms = float(per_frame.mean())
+    reuse_pct = [float(np.percentile(per_frame, q)) for q in (50, 90)]
     same = all(pv.stats_dict(stats[K + i]) == st_reuse[i] for i in range(K))
 
     # ---- the same frames with the atlas carried from frame to frame (pv_verify_retrace_deposit_delta): only the
@@ -367,6 +369,8 @@ def run_ours(args, ws, rank, local):
     frame += K
     trace_ms = start2.elapsed_time(stop2) / K
     parts2 = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in ev2]).mean(axis=0)
+    per_frame2 = np.array([e[0].elapsed_time(e[4]) for e in ev2])
+    trace_pct = [float(np.percentile(per_frame2, q)) for q in (50, 90)]
     st_trace = [pv.stats_dict(stats[3 * K + i]) for i in range(K)]
 
     # ---- end to end through the API: host poses in, atlas and stats out (pinned), every frame.  Two atlases
@@ -457,6 +461,8 @@ def run_ours(args, ws, rank, local):
            "speedup_vs_trace_all": trace_ms / reuse_ms,
            "reuse_ms_parts": {"update": float(reuse_parts[0]), "verify_retrace_deposit": float(reuse_parts[1])},
            "instrumented_ms_per_frame": instrumented_ms, "instrumented_counters_match": same,
+           "per_frame_ms_p50_p90": {"reuse": reuse_pct, "trace_all": trace_pct,
+                                    "note": "from the per-frame events of the instrumented loops"},
            "delta_deposit": {"call": "pv_verify_retrace_deposit_delta", "ms_per_frame": delta_ms,
                              "paths_per_s": ws * N / (delta_ms * 1e-3), "atlas_equal_to_full_deposit": delta_equal},
            "verify_retrace_deposit_stages_ms": {"k_verify": float(stage_ms[0]), "compaction": float(stage_ms[1]),

@@ -5,7 +5,9 @@
 // scene in one grid, thread- or warp-per-path), the Alg. 1 continuation and
 // the re-trace (persistent kernels whose work lists are the concatenation of
 // the scenes' lists, so small scenes share the GPU with large ones), and the
-// compaction (tiles of every scene, one look-back chain per scene).  Per-scene
+// compaction (tiles of every scene, one look-back chain per scene) when the
+// caller asked for lists; without lists verify appends the paths it marks to
+// each scene's work list directly and Alg. 1 runs inside the re-trace.  Per-scene
 // state lives in device tables; the per-frame part (light poses, transforms,
 // moved bits, frame number) is copied from pinned staging by the first node
 // of a CUDA graph that is captured once and replayed every frame.
@@ -686,9 +688,8 @@ int enqueue_frame(pv_batch* b, cudaStream_t st, bool vis, const pv_batch_config&
   const uint32_t grid = std::min<uint32_t>(b->n_vtiles[ti], pvh::verify_block_cap((uint32_t)per * (uint32_t)b->num_sms));
   vk<<<grid, c.verify_threads, 0, st>>>(b->d_scenes, b->d_frames, b->d_vtab[ti], b->n_vtiles[ti]);
   mark(2);
-  if (b->fused) {                             // compaction of what verify marked, then Alg. 1 + re-trace
+  if (b->fused) {                             // verify appended what it marked; then Alg. 1 + re-trace
     mark(3);
-    k_b_compact<<<b->n_ctiles, pvh::kCompactThreads, 0, st>>>(b->d_scenes, b->d_ctab, b->d_ctr);
     mark(4);
     const TraceKernel ctk = cont_trace_kernel(c.trace_steps, c.stack);
     ctk<<<persistent_blocks(b, b->occ_ct[steps_index(c.trace_steps)][stack_index(c.stack)], c.trace_blocks),
@@ -953,6 +954,10 @@ extern "C" int pv_batch_create(const pv_batch_scene* scenes, uint32_t n, const p
     B.list = list;
     B.count = count;
     B.stat_listed = scenes[i].d_stats ? &scenes[i].d_stats->n_listed : nullptr;
+    if (fused) {                               // verify appends the paths it marks: no compaction pass
+      B.V.list_out = list;
+      B.V.list_count = count;
+    }
     B.ctr = s->ws_ctr;
     for (int k = 0; k < 3; ++k)
       for (uint32_t t = 0; t < (p.n + vthreads[k] - 1) / vthreads[k]; ++t) {
