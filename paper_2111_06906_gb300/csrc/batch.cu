@@ -30,6 +30,12 @@ constexpr uint32_t kBatchMax = PV_BATCH_MAX_SCENES;
 constexpr int kRing = 3;                      // pinned staging slots of the per-frame data
 constexpr uint32_t kGuard = 1u << 30;         // bound of the persistent loops
 
+// Minimum resident blocks per SM of the batched re-trace with lists (k_b_trace):
+// 7 fits in 72 registers without spills (8 spills).
+#ifndef PV_BATCH_TRACE_MIN_BLOCKS
+#define PV_BATCH_TRACE_MIN_BLOCKS 7
+#endif
+
 // Static per-scene record (device table).
 struct BScene {
   SceneView sv;                               // sv.moved is taken from the frame record
@@ -291,7 +297,7 @@ __global__ void __launch_bounds__(pvh::kCompactThreads) k_b_compact(const BScene
 // The persistent re-trace of trace.cu over the concatenated lists of all
 // scenes: each lane carries the scene of its current path.
 template <int kSteps, int S>
-__global__ void __launch_bounds__(pvh::kTraceThreads, 6) k_b_trace(const BScene* B, const BFrame* F, uint32_t n_scenes,
+__global__ void __launch_bounds__(pvh::kTraceThreads, PV_BATCH_TRACE_MIN_BLOCKS) k_b_trace(const BScene* B, const BFrame* F, uint32_t n_scenes,
                                                                   BCounters* bc) {
   extern __shared__ __align__(16) unsigned char smem[];
   const PersistLayout<TraceArgs> lay(n_scenes);

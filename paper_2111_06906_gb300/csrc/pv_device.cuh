@@ -130,6 +130,7 @@ struct SceneView {
   uint64_t moved;            // bit s: dynamic slot s moved this frame
   uint32_t max_visits;       // traversal visit cap per ray
   int* status;               // sticky device status word
+  uint32_t n_static_wide;    // wide nodes of the static tree, [0, n_static_wide), in breadth-first order
 };
 
 // ---------------------------------------------------------------- vectors
@@ -252,6 +253,24 @@ __device__ __forceinline__ WNodeRay load_wnode_ray(const WNode* nodes, int i, co
   n.nz = __ldg(p + 4u + sz);
   n.fz = __ldg(p + (5u - sz));
   n.child = __ldg(reinterpret_cast<const int4*>(p + 6));
+  return n;
+}
+
+// The same through a generic pointer: node i comes from ``cache`` (a shared
+// copy of wide nodes [0, n_cache)) when i < n_cache, else from ``nodes``.
+__device__ __forceinline__ WNodeRay load_wnode_ray_cached(const WNode* nodes, const WNode* cache, int n_cache, int i,
+                                                          const Ray& r) {
+  const float4* p = reinterpret_cast<const float4*>((unsigned)i < (unsigned)n_cache ? cache + i : nodes + i);
+  const uint32_t sx = __float_as_uint(r.inv.x) >> 31, sy = __float_as_uint(r.inv.y) >> 31;
+  const uint32_t sz = __float_as_uint(r.inv.z) >> 31;
+  WNodeRay n;
+  n.nx = p[sx];
+  n.fx = p[1u - sx];
+  n.ny = p[2u + sy];
+  n.fy = p[3u - sy];
+  n.nz = p[4u + sz];
+  n.fz = p[5u - sz];
+  n.child = reinterpret_cast<const int4*>(p)[6];
   return n;
 }
 
@@ -502,9 +521,11 @@ __device__ __forceinline__ void trav_begin(Trav& t, int root) {
 }
 
 // One traversal step (one wide node or one leaf range); true once the ray is done.
-// ``stk`` holds S entries.
+// ``stk`` holds S entries.  With ``cache`` non-null, wide nodes below
+// ``n_cache`` are read from that shared copy.
 template <int S = kStack, class Stk>
-__device__ __forceinline__ bool trav_step(const SceneView& sv, const Ray& r, Trav& t, Stk& stk, int exclude, Work& wk) {
+__device__ __forceinline__ bool trav_step(const SceneView& sv, const Ray& r, Trav& t, Stk& stk, int exclude, Work& wk,
+                                          const WNode* cache = nullptr, int n_cache = 0) {
   if (t.node != INT32_MIN) {
     if (++t.visits > sv.max_visits) {
       record_error(sv.status, PV_ERR_ITER_CAP);
@@ -512,7 +533,8 @@ __device__ __forceinline__ bool trav_step(const SceneView& sv, const Ray& r, Tra
     }
     if (t.node >= 0) {
       ++wk.nodes;
-      const WNodeRay n = load_wnode_ray(sv.nodes, t.node, r);
+      const WNodeRay n = cache ? load_wnode_ray_cached(sv.nodes, cache, n_cache, t.node, r)
+                               : load_wnode_ray(sv.nodes, t.node, r);
       int next;
       if (!visit_wide<S>(n, r, t.tbest, stk, t.sp, next)) {
         record_error(sv.status, PV_ERR_STACK);

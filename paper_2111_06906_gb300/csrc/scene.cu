@@ -85,6 +85,7 @@ SceneView view(const pv_scene* s) {
   v.moved = s->moved;
   v.max_visits = s->visit_limit ? s->visit_limit : 2u * (s->n_static_refs + s->n_dyn_tris) + 256u;
   v.status = s->status;
+  v.n_static_wide = s->w_dyn_off;
   return v;
 }
 

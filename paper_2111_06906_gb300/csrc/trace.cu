@@ -59,6 +59,28 @@ namespace {
 constexpr int kStackShared = PV_TRACE_STACK_SHARED < kStack ? PV_TRACE_STACK_SHARED : kStack;
 using TraceStack = TStack<kStack, kStackShared, pvh::kTraceThreads>;
 constexpr int kStackSharedWords = kStackShared > 0 ? kStackShared * pvh::kTraceThreads : 1;
+// Wide nodes of the static tree's top levels copied into shared memory by
+// every block of the persistent kernels (0: none).  Measured on the city and
+// villa workloads, 64, 128 and 192 nodes (8.5-25 KB per block) made the
+// re-trace 5-9 % and trace-all 6-14 % slower: the top nodes are L1 hits
+// anyway, and the copy takes L1 capacity and turns every node load into a
+// generic one.  The default keeps none.
+#ifndef PV_TRACE_NODE_CACHE
+#define PV_TRACE_NODE_CACHE 0
+#endif
+constexpr int kNodeCache = PV_TRACE_NODE_CACHE;
+
+// Copy the first min(kNodeCache, static wide nodes) nodes into ``cache``
+// (all threads of the block); returns how many.
+__device__ __forceinline__ int fill_node_cache(const SceneView& sv, WNode* cache) {
+  if (kNodeCache == 0) return 0;
+  const int n = (int)min((uint32_t)kNodeCache, sv.n_static_wide);
+  const float4* src = reinterpret_cast<const float4*>(sv.nodes);
+  float4* dst = reinterpret_cast<float4*>(cache);
+  for (int i = threadIdx.x; i < n * 8; i += blockDim.x) dst[i] = __ldg(src + i);
+  __syncthreads();
+  return n;
+}
 constexpr int kStepsPerIter = PV_TRACE_STEPS;
 constexpr int kMaxSteps = PV_TRACE_MAX_STEPS;
 constexpr int kDoneLanes = PV_TRACE_DONE_LANES;
@@ -66,16 +88,16 @@ constexpr int kDoneLanes = PV_TRACE_DONE_LANES;
 // Advance the lane's ray; all lanes of the warp call it (lanes without a ray
 // pass done = true).  Returns whether the lane's ray has ended.
 __device__ __forceinline__ bool step_rays(const SceneView& sv, const Ray& r, Trav& t, TraceStack& stk, int excl, Work& wk,
-                                          bool done) {
+                                          bool done, const WNode* cache, int n_cache) {
   if (kDoneLanes > 32) {
 #pragma unroll 1
-    for (int i = 0; i < kStepsPerIter && !done; ++i) done = trav_step(sv, r, t, stk, excl, wk);
+    for (int i = 0; i < kStepsPerIter && !done; ++i) done = trav_step(sv, r, t, stk, excl, wk, cache, n_cache);
     return done;
   }
-  if (kDoneLanes >= 32) return step_warp<kMaxSteps>(sv, r, t, stk, excl, wk, done);
+  if (kDoneLanes >= 32) return step_warp<kMaxSteps>(sv, r, t, stk, excl, wk, done, cache, n_cache);
 #pragma unroll 1
   for (int i = 0; i < kMaxSteps; ++i) {
-    if (!done) done = trav_step(sv, r, t, stk, excl, wk);
+    if (!done) done = trav_step(sv, r, t, stk, excl, wk, cache, n_cache);
     const unsigned dm = __ballot_sync(0xffffffffu, done);
     if (dm == 0xffffffffu) break;
     if (i + 1 >= kStepsPerIter && __popc(dm) >= kDoneLanes) break;
@@ -97,6 +119,9 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS) k_tra
   __shared__ int s_stk[kStackSharedWords];
   TraceStack stk;
   stk.sh = s_stk + threadIdx.x;
+  __shared__ WNode s_nodes[kNodeCache > 0 ? kNodeCache : 1];
+  const int n_cache = fill_node_cache(sv, s_nodes);
+  const WNode* const cache = kNodeCache > 0 ? s_nodes : nullptr;
   bool has_ray = false, exhausted = false;
   uint32_t c_rays = 0, c_photons = 0;
   for (uint32_t guard = 0; guard < (1u << 30); ++guard) {
@@ -121,7 +146,7 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS) k_tra
     }
     if (__all_sync(0xffffffffu, exhausted && !has_ray)) break;
     if (kDoneLanes > 32 && !has_ray) continue;
-    const bool done = step_rays(sv, r, t, stk, s.excl, wk, !has_ray);
+    const bool done = step_rays(sv, r, t, stk, s.excl, wk, !has_ray, cache, n_cache);
     if (!has_ray || !done) continue;
     ++c_rays;
     if (trace_hit(sv, A, s, r, t, c_photons)) trav_begin(t, root);
@@ -201,6 +226,9 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_CONT_TRACE_MIN_BLOCKS)
   __shared__ int s_stk[kStackSharedWords];
   TraceStack stk;
   stk.sh = s_stk + threadIdx.x;
+  __shared__ WNode s_nodes[kNodeCache > 0 ? kNodeCache : 1];
+  const int n_cache = fill_node_cache(sv, s_nodes);
+  const WNode* const cache = kNodeCache > 0 ? s_nodes : nullptr;
   uint32_t cmask = 0, cmeta = 0;             // Alg. 1 state beyond s.k (segment), s.E (a_orig), s.excl (a_prim)
   bool has_ray = false, exhausted = false, cont = false;
   uint32_t c_rays = 0, c_photons = 0;
@@ -247,7 +275,7 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_CONT_TRACE_MIN_BLOCKS)
     }
     if (__all_sync(0xffffffffu, exhausted && !has_ray && dep == 0xFFFFFFFFu)) break;
     if (kDoneLanes > 32 && !has_ray) continue;
-    const bool done = step_rays(sv, r, t, stk, s.excl, wk, !has_ray);
+    const bool done = step_rays(sv, r, t, stk, s.excl, wk, !has_ray, cache, n_cache);
     if (!has_ray || !done) continue;
     if (cont) {
       ContCounters cc;

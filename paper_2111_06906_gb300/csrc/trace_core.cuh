@@ -149,10 +149,10 @@ __device__ __forceinline__ bool trace_hit(const SceneView& sv, const TraceArgs& 
 // for the whole warp lets the ray-end code that follows run with all lanes.
 template <int kMax, int S = kStack, class Stk>
 __device__ __forceinline__ bool step_warp(const SceneView& sv, const Ray& r, Trav& t, Stk& stk, int excl, Work& wk,
-                                          bool done) {
+                                          bool done, const WNode* cache = nullptr, int n_cache = 0) {
 #pragma unroll 1
   for (int i = 0; i < kMax; ++i) {
-    if (!done) done = trav_step<S>(sv, r, t, stk, excl, wk);
+    if (!done) done = trav_step<S>(sv, r, t, stk, excl, wk, cache, n_cache);
     if (__all_sync(0xffffffffu, done)) break;
   }
   return done;
