@@ -43,7 +43,7 @@ WORKLOADS = {
 }
 # DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one k_cont_trace<deposit> launch of a
 # timed reuse frame, measured on the same kernel code
-TRACE_TRAFFIC = {"city": 204820736 + 21092864, "villa": 939411456 + 104371456}
+TRACE_TRAFFIC = {"city": 204794112 + 21009664, "villa": 940165632 + 104417536}
 OPS_PER_NODE = 107    # FP32-pipe ops per wide-node visit (four slab tests + ordering network), from the source
 OPS_PER_TRI = 40      # FP32-pipe ops per Moller-Trumbore test, counted from the source
 SM_COUNT, FP32_LANES = 152, 128
