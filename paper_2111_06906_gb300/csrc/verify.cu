@@ -1,8 +1,9 @@
 // Per-frame verification of stored photon paths.
 //
-// k_verify (one thread per path, streaming the 2-D photon array row by row):
-//   Sec. 3.1 "update path origins" fused with Sec. 3.2 "dynamic occlusions"
-//   as in Sec. 4 (origins first, then the ordered segment tests).
+// k_verify_box / k_verify (resident blocks looping over tiles of paths,
+// streaming the 2-D photon array row by row): Sec. 3.1 "update path
+// origins" fused with Sec. 3.2 "dynamic occlusions" as in Sec. 4 (origins
+// first, then the segment tests).
 // k_continue (persistent, over the paths k_verify flagged in error mode):
 //   the error-based threshold continuation of Sec. 3.3, Alg. 1 and Eq. 2.
 // Then the replace bits are compacted into the re-trace list (compact.cu).

@@ -1,11 +1,13 @@
 // Device code of path verification shared by the single-scene kernels
 // (verify.cu) and the batched kernels (batch.cu).
 //
-// verify_block: Sec. 3.1 "update path origins" fused with Sec. 3.2 "dynamic
-//   occlusions" as in Sec. 4 (origins first, then the ordered segment tests),
-//   one thread per path.
+// verify_tile_thread / _warp / _flat: Sec. 3.1 "update path origins" fused
+//   with Sec. 3.2 "dynamic occlusions" as in Sec. 4 (origins first, then the
+//   segment tests) for one tile of paths, thread per path, warp per path or
+//   with the warp's segments dealt out to its lanes; verify_tiles loops a
+//   block over tiles, verify_block* runs one tile as a whole block.
 // continue_path: the error-based threshold continuation of Sec. 3.3, Alg. 1
-//   and Eq. 2, for one path flagged by verify_block in error mode.
+//   and Eq. 2, for one path flagged by the verification in error mode.
 #pragma once
 #include "deposit_core.cuh"
 #include "dm_core.cuh"
