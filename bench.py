@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-dm", action="store_true", help="skip the distribution-map frame measurement")
     ap.add_argument("--no-splat", action="store_true", help="skip the 1920x1080 screen-space splat measurement")
-    ap.add_argument("--tune-frames", type=int, default=3, help="batch16: frames per tuner candidate")
+    ap.add_argument("--tune-frames", type=int, default=16, help="batch16: frames per tuner candidate")
     ap.add_argument("--build-flags", type=int, default=0, help="pv_scene_desc flags (2: Morton-code static tree)")
     return ap.parse_args()
 

@@ -30,6 +30,11 @@ constexpr uint32_t kBatchMax = PV_BATCH_MAX_SCENES;
 constexpr int kRing = 3;                      // pinned staging slots of the per-frame data
 constexpr uint32_t kGuard = 1u << 30;         // bound of the persistent loops
 
+// Minimum resident blocks per SM of the batched flat-mapping verify (k_b_verify<.., 2>).
+#ifndef PV_BATCH_FLAT_MIN_BLOCKS
+#define PV_BATCH_FLAT_MIN_BLOCKS 5
+#endif
+
 // Minimum resident blocks per SM of the batched re-trace with lists (k_b_trace):
 // 7 fits in 72 registers without spills (8 spills).
 #ifndef PV_BATCH_TRACE_MIN_BLOCKS
@@ -166,7 +171,7 @@ __global__ void k_b_frame_top(const BScene* S, const BFrame* F) {
 // counters when it leaves it.
 // Box-only variants are held to 5 resident blocks of 256 threads (51 registers), as the single-scene kernel.
 template <bool kPointVis, bool kExact, int kMap>
-__global__ void __launch_bounds__(256, (kPointVis || kExact) ? 2 : 5) k_b_verify(const BScene* S, const BFrame* F,
+__global__ void __launch_bounds__(256, (kPointVis || kExact) ? 2 : (kMap == 2 ? PV_BATCH_FLAT_MIN_BLOCKS : 5)) k_b_verify(const BScene* S, const BFrame* F,
                                                                                   const uint32_t* tab, uint32_t n_entries) {
   __shared__ VerifySmem sm;
   __shared__ SceneView s_sv;
