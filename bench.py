@@ -44,6 +44,10 @@ WORKLOADS = {
 # DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one k_cont_trace<deposit> launch of a
 # timed reuse frame, measured on the same kernel code
 TRACE_TRAFFIC = {"city": 204794112 + 21009664, "villa": 940165632 + 104417536}
+# warp instructions issued by one launch of the same kernel (ncu smsp__inst_executed.sum, same capture), and the
+# average active lanes per issued instruction (smsp__thread_inst_executed_per_inst_executed.ratio)
+TRACE_WARP_INST = {"city": (173336291, 9.57), "villa": (592380139, 12.04)}
+SCHEDULERS_PER_SM = 4
 OPS_PER_NODE = 107    # FP32-pipe ops per wide-node visit (four slab tests + ordering network), from the source
 OPS_PER_TRI = 40      # FP32-pipe ops per Moller-Trumbore test, counted from the source
 SM_COUNT, FP32_LANES = 152, 128
@@ -451,6 +455,15 @@ def run_ours(args, ws, rank, local):
             "duration_ms": float(stage_ms[2]),
             "traffic": TRACE_TRAFFIC.get(args.workload), "traffic_unit": "bytes per launch (ncu)",
             "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x max SM clock"}
+    if args.workload in TRACE_WARP_INST:
+        # the same kernel against the issue rate: warp instructions per launch (ncu) over the live duration,
+        # against one instruction per scheduler per clock; lanes per instruction give the SIMT efficiency
+        inst, lanes = TRACE_WARP_INST[args.workload]
+        issue_peak = SM_COUNT * SCHEDULERS_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6
+        issue = inst / (float(stage_ms[2]) * 1e-3)
+        roof["issue"] = {"achieved": issue / 1e9, "peak": issue_peak / 1e9, "unit": "G warp-inst/s",
+                         "frac": issue / issue_peak, "active_lanes_per_inst": lanes, "simt_efficiency": lanes / 32.0,
+                         "source": "warp instructions per launch from ncu, duration live"}
     rays_reuse = agg("vis_rays", st_reuse) + agg("cont_rays", st_reuse) + agg("trace_rays", st_reuse)
     rays_trace = agg("trace_rays", st_trace)
     value = ws * N / (reuse_ms * 1e-3)
