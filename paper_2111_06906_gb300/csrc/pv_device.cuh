@@ -89,7 +89,10 @@ struct DmLight {
 // centroid spread, cut into consecutive groups.  A group's box is the union
 // of its members' old-and-new boxes, so the Sec. 3.2 box test can reject a
 // segment against a group before testing its members, with the same result.
-constexpr int kGroupSize = 4;
+#ifndef PV_GROUP_SIZE
+#define PV_GROUP_SIZE 4
+#endif
+constexpr int kGroupSize = PV_GROUP_SIZE;
 constexpr int kMaxGroups = (kMaxDyn + kGroupSize - 1) / kGroupSize;
 struct MovedGroups {
   uint32_t n;                                  // groups in use
