@@ -61,6 +61,8 @@ struct BScene {
   const uint32_t* leaf_parent;
   uint32_t* fit_flags;
   uint32_t n_dyn_tris, n_dyn;
+  uint32_t refit_blocks;                      // k_b_refit_wide blocks of this scene (0: k_b_frame_top does its top)
+  uint32_t* refit_done;                       // of them, finished this frame (reset by the last)
   const uint8_t* tri_slot;
   const uint32_t* t_link;
   const uint32_t* w_link;
@@ -129,7 +131,10 @@ __global__ void k_b_prologue(const BScene* S, const BFrame* F, BCounters* bc) {
 // ---------------------------------------------------------------- pose update
 // Per 256-triangle chunk of one scene (tab: scene, first triangle): the
 // moved objects' triangles to the new pose and the direct wide refit.
+// The last block of a scene to finish then does the scene's pose
+// bookkeeping, top level and moved-object groups (k_b_frame_top's work).
 __global__ void __launch_bounds__(256) k_b_refit_wide(const BScene* S, const BFrame* F, const uint32_t* tab) {
+  __shared__ bool s_last;
   const uint32_t sc = tab[2 * blockIdx.x], i = tab[2 * blockIdx.x + 1] + threadIdx.x;
   const BScene& B = S[sc];
   const uint64_t moved = F[sc].moved;
@@ -148,6 +153,19 @@ __global__ void __launch_bounds__(256) k_b_refit_wide(const BScene* S, const BFr
   R.wdyn = B.wnodes_dyn;
   R.obox = B.obox;
   refit_tri(F[sc].xf[mv ? s : 0], mv, s, R, i);
+  __threadfence();                             // this block's triangles, boxes and object-box atomics
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(B.refit_done, 1u) == B.refit_blocks - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();                             // the scene's other blocks' writes are visible from here
+  if (threadIdx.x == 0) *B.refit_done = 0u;
+  pose_bookkeeping(F[sc].xf, moved, B.n_dyn, B.objs, B.xf_old, B.xf_new, B.obox);
+  __syncthreads();
+  if (!moved) return;
+  build_top_block(B.wnodes, B.tris, B.top_off, B.s_wroot, B.objs, (int)B.n_dyn, B.root);
+  __syncthreads();
+  if (B.groups) build_moved_groups_block(B.objs, (int)B.n_dyn, moved, B.groups);
 }
 
 // One block of 32 threads per scene: pose bookkeeping of every slot, then
@@ -155,6 +173,7 @@ __global__ void __launch_bounds__(256) k_b_refit_wide(const BScene* S, const BFr
 __global__ void k_b_frame_top(const BScene* S, const BFrame* F) {
   const uint32_t s = blockIdx.x;
   const BScene& B = S[s];
+  if (B.refit_blocks) return;                  // the scene's last refit block did it
   if (B.objs) pose_bookkeeping(F[s].xf, F[s].moved, B.n_dyn, B.objs, B.xf_old, B.xf_new, B.obox);
   __syncthreads();
   if (!F[s].moved) return;
@@ -625,6 +644,7 @@ struct pv_batch {
   uint32_t n_ctiles = 0;
   uint32_t* d_ftab = nullptr;
   uint32_t n_fit = 0;
+  bool top_alone = false;                     // some scene has no refit blocks: k_b_frame_top runs
   bool fused = false;                         // no lists asked for: Alg. 1 runs inside the re-trace kernel
   size_t smem_cont = 0, smem_trace = 0, smem_ct = 0;
   int occ_cont[2] = {1, 1};                   // resident blocks per SM: [stack 32, 64]
@@ -687,7 +707,7 @@ int enqueue_frame(pv_batch* b, cudaStream_t st, bool vis, const pv_batch_config&
   mark(0);
   k_b_prologue<<<n, 256, 0, st>>>(b->d_scenes, b->d_frames, b->d_ctr);
   if (b->n_fit) k_b_refit_wide<<<b->n_fit, 256, 0, st>>>(b->d_scenes, b->d_frames, b->d_ftab);
-  k_b_frame_top<<<n, 32, 0, st>>>(b->d_scenes, b->d_frames);
+  if (b->top_alone) k_b_frame_top<<<n, 32, 0, st>>>(b->d_scenes, b->d_frames);
   mark(1);
   const int ti = thread_index(c.verify_threads);
   const VerifyKernel vk = verify_kernel(vis, b->exact, c.verify_mapping);
@@ -979,10 +999,14 @@ extern "C" int pv_batch_create(const pv_batch_scene* scenes, uint32_t n, const p
       ct.push_back(i);
       ct.push_back(t);
     }
+    B.refit_blocks = 0;
     for (uint32_t base = 0; base < s->n_dyn_tris; base += 256) {
       ft.push_back(i);
       ft.push_back(base);
+      ++B.refit_blocks;
     }
+    B.refit_done = s->w_arrive ? s->w_arrive + s->n_dyn_tris : nullptr;   // the word after the arrival counters
+    if (!B.refit_blocks) b->top_alone = true;
   }
   for (int k = 0; k < 3; ++k) b->n_vtiles[k] = (uint32_t)vt[k].size() / 2;
   b->n_ctiles = (uint32_t)ct.size() / 2;
