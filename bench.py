@@ -1,15 +1,20 @@
 #!/usr/bin/env python
 """Benchmark of the per-frame path-verification hot path on one GB300.
 
-One step = one frame of the reuse pipeline on the seeded city workload
-(200k static triangles, 4 moving tori, a 1x1 m area light translating
-0.1 m/frame, 1M photon paths of up to 7 bounces, error-based mode with
-tau = 1 %):  pv_update_dynamic -> pv_verify_retrace_deposit (origin
-update, dynamic occlusions, compaction, then Alg. 1, the re-trace and the
-atlas deposit in one persistent kernel).  The same frames through the
-separate calls (pv_verify_paths -> pv_retrace_invalid -> pv_deposit) and the
-same library's trace-all frame (pv_update_dynamic -> pv_trace_all ->
-pv_deposit) are timed beside it.
+One step = one frame of the reuse pipeline on the seeded villa workload
+(2M static triangles, 10 yawing tori of 5000 triangles, a ceiling point
+light, a static area light and a moving, tilting torch; 3M photon paths of up
+to 7 bounces; error-based mode with tau = 1 %):  pv_update_dynamic ->
+pv_verify_retrace_deposit (origin update, dynamic occlusions, then Alg. 1, the
+re-trace and the atlas deposit in one persistent kernel).  Beside it, on the
+same frames: the same library's trace-all frame (pv_update_dynamic ->
+pv_trace_all -> pv_deposit), the separate calls (pv_verify_paths ->
+pv_retrace_invalid -> pv_deposit), tau in {0, 0.5, 1, 5} % over 60 frames,
+the naive modes of Sec. 3.2 against the error-based one, the same villa with
+its ceiling point light moving (visibility rays in the origin update), and
+per-kernel durations set against the measured HBM bandwidth and the measured
+FP32 fused multiply-add rate.  The city workload and the 16-scene batch are
+measured after it as secondary fields of the same line.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on a bounded sample of the same workload instead.
@@ -17,6 +22,7 @@ oracle on a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -33,24 +39,23 @@ sys.path.insert(0, ROOT)
 METRIC = "photon paths verified+reused+retraced/s and frame ms vs trace-all on 1 GB300"
 MODES = {"naive_aabb": 0, "naive_exact": 1, "error": 2}
 WORKLOADS = {
-    "city": "procedural city: 100x100 m floor, 16666 random boxes (200k static tris), 4 tori of 2048 tris on "
-            "sinusoidal paths (2 m amplitude), 1x1 m area light translating 0.1 m/frame; 1M paths, <=7 bounces",
     "villa": "villa-shaped interior: 4x3 rooms, 2M static tris (30% clutter), 10 yawing tori of 5000 tris, "
              "point light + static area light + moving tilting torch; 3M paths, <=7 bounces",
+    "city": "procedural city: 100x100 m floor, 16666 random boxes (200k static tris), 4 tori of 2048 tris on "
+            "sinusoidal paths (2 m amplitude), 1x1 m area light translating 0.1 m/frame; 1M paths, <=7 bounces",
     "tiny_box": "open 2x2x2 box (10 tris) + moving unit cube (12 tris), point light; 10k paths, <=3 bounces",
     "batch16": "16 independent districts: 10k to 2M tris, 50k to 3M paths (12.4M in all), 1 to 3 lights, "
                "bounce caps 1 to 7, 1 to 4 moving tori; one batched graph-captured frame per step, tuned",
 }
-# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one k_cont_trace<deposit> launch of a
-# timed reuse frame, measured on the same kernel code
-TRACE_TRAFFIC = {"city": 204794112 + 21009664, "villa": 940165632 + 104417536}
-# warp instructions issued by one launch of the same kernel (ncu smsp__inst_executed.sum, same capture), and the
-# average active lanes per issued instruction (smsp__thread_inst_executed_per_inst_executed.ratio)
-TRACE_WARP_INST = {"city": (173336291, 9.57), "villa": (592380139, 12.04)}
-SCHEDULERS_PER_SM = 4
-OPS_PER_NODE = 107    # FP32-pipe ops per wide-node visit (four slab tests + ordering network), from the source
-OPS_PER_TRI = 40      # FP32-pipe ops per Moller-Trumbore test, counted from the source
-SM_COUNT, FP32_LANES = 152, 128
+# Algorithmic FP32 work of a traversal: 20 operations per ray-box slab test (four per 4-wide node) and 35 per
+# watertight ray-triangle test, times the node visits and triangle tests the library counts.
+OPS_PER_SLAB, OPS_PER_TRI = 20, 35
+OPS_PER_NODE = 4 * OPS_PER_SLAB
+# DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum) of the reuse frame's kernels, from
+# the capture recorded under profiles/.  They hold only for the kernel sources they were captured on: the digest
+# of csrc/ and include/ at capture time.  Any other source digest reports no traffic.
+NCU_TRAFFIC = {"digest": None, "villa": {}, "city": {}}
+TAUS = (0.0, 0.005, 0.01, 0.05)
 
 
 def parse():
@@ -59,16 +64,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="city", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="villa", choices=list(WORKLOADS))
     ap.add_argument("--mode", default="error", choices=list(MODES))
     ap.add_argument("--tau", type=float, default=None)
     ap.add_argument("--atlas", type=int, default=1024)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--sweep-frames", type=int, default=60, help="frames per tau / mode / moving-point-light row")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-dm", action="store_true", help="skip the distribution-map frame measurement")
     ap.add_argument("--no-splat", action="store_true", help="skip the 1920x1080 screen-space splat measurement")
+    ap.add_argument("--no-sweeps", action="store_true", help="skip the tau, mode and moving-point-light rows")
+    ap.add_argument("--no-secondary", action="store_true", help="villa only: skip the city and batch16 fields")
     ap.add_argument("--tune-frames", type=int, default=16, help="batch16: frames per tuner candidate")
     ap.add_argument("--build-flags", type=int, default=0, help="pv_scene_desc flags (2: Morton-code static tree)")
     return ap.parse_args()
@@ -87,6 +95,19 @@ def peaks():
             return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def source_digest() -> str:
+    """Digest of the library's kernel sources and headers (csrc/, include/)."""
+    h = hashlib.sha256()
+    dirs = [os.path.join(ROOT, "paper_2111_06906_gb300", "csrc"), os.path.join(ROOT, "include")]
+    for d in dirs:
+        for f in sorted(os.listdir(d)):
+            if f.endswith((".cu", ".cuh", ".h")):
+                h.update(f.encode())
+                with open(os.path.join(d, f), "rb") as fh:
+                    h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 class Clocks:
@@ -181,9 +202,461 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm), "source": self.source}
 
 
-def scene_for(name, rank=0):
+def scene_for(name, **kw):
     import scenes
-    return scenes.by_name(name)
+    return scenes.by_name(name, **kw)
+
+
+def fma_peak(pv, torch, dev, sms, stream):
+    """The FP32 fused multiply-add rate of this GPU: the library's probe kernel
+    over 8 blocks of 256 threads per SM, median of 7 timed launches."""
+    blocks = 8 * sms
+    sink = torch.zeros(blocks, dtype=torch.float32, device=dev)
+    ms, fmas = [], 0
+    for i in range(10):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fmas = pv.pv_fma_probe(blocks, 512, sink)
+        e1.record(stream)
+        if i >= 3:
+            ms.append((e0, e1))
+    torch.cuda.synchronize()
+    t = float(np.median([a.elapsed_time(b) for a, b in ms]))
+    rate = fmas / (t * 1e-3)
+    return {"kernel": "k_fma_probe", "top_s": rate / 1e12, "fmas_per_launch": fmas, "ms": t, "blocks": blocks,
+            "threads_per_block": 256, "sm_count": sms,
+            "note": "FP32 fused multiply-adds per second (one FMA = one op), 8 independent chains per thread"}
+
+
+# ----------------------------------------------------------------------------- one workload on one scene
+class Workload:
+    """One scene, its path buffers and atlas, and the frame loops timed on it."""
+
+    def __init__(self, pv, torch, sc, args, dev, stream, rank, K, W, frames_needed):
+        self.pv, self.torch, self.sc, self.args, self.dev, self.stream = pv, torch, sc, args, dev, stream
+        self.K, self.W = K, W
+        self.mode = MODES[args.mode]
+        self.tau = sc.tau if args.tau is None else args.tau
+        self.seed = sc.seed + 7919 * rank
+        self.N, self.B = sc.n_paths, sc.max_bounces
+        self.xfs = {f: np.ascontiguousarray(sc.xforms(f), np.float32) for f in range(1, frames_needed + 1)}
+        self.lts = {f: pv.make_lights(sc.lights(f)) for f in range(1, frames_needed + 1)}
+        t0 = time.time()
+        self.h = pv.pv_build_scene(sc.verts, sc.tri_object, sc.object_dynamic, sc.object_albedo, sc.lights(1), self.B,
+                                   sc.diag, object_xform=self.xfs[1], flags=args.build_flags)
+        self.build_s = time.time() - t0
+        self.P = pv.Paths.allocate(self.N, self.B, dev)
+        A = args.atlas
+        self.A = A
+        self.atlas = torch.zeros(A, A, 3, dtype=torch.int64, device=dev)
+        self.scale = 40 if sc.name != "tiny_box" else 31
+        self.lst = torch.zeros(self.N, dtype=torch.int32, device=dev)
+        self.cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.lst2 = torch.zeros(self.N, dtype=torch.int32, device=dev)
+        self.cnt2 = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.stats = torch.zeros(2 * K + 2, pv.STATS_WORDS, dtype=torch.int32, device=dev)
+
+    def ev(self):
+        return self.torch.cuda.Event(enable_timing=True)
+
+    def barrier(self, ws):
+        self.torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        self.torch.cuda.synchronize()
+
+    def restart(self, lts=None):
+        """Back to the poses of frame 1 and a fresh trace-all, so every loop runs frames 2, 3, ..."""
+        lts = lts or self.lts
+        self.pv.pv_update_dynamic(self.h, self.xfs[1], lts[1])
+        self.pv.pv_trace_all(self.h, self.P, self.seed, 1)
+        return 1
+
+    def reuse_frame(self, f, st, atlas=None, mode=None, tau=None, lts=None, flags=0):
+        lts = lts or self.lts
+        self.pv.pv_update_dynamic(self.h, self.xfs[f], lts[f])
+        self.pv.pv_verify_retrace_deposit(self.h, self.P, self.mode if mode is None else mode,
+                                          self.tau if tau is None else tau, flags, self.seed, f,
+                                          self.atlas if atlas is None else atlas, self.sc.atlas_rect, self.scale, st)
+
+    def mean_photons(self):
+        info = self.P.info.cpu().numpy().view(np.uint32)
+        return float(np.minimum((info >> 22) & 15, self.B).mean())
+
+    # ---- the headline: K reuse frames, only the two events that bracket them
+    def headline(self, ws, local):
+        frame = self.restart()
+        for _ in range(self.W):
+            frame += 1
+            self.reuse_frame(frame, self.stats[-1])
+        self.barrier(ws)
+        clocks = Clocks(local)
+        with clocks:
+            start, stop = self.ev(), self.ev()
+            start.record(self.stream)
+            for i in range(self.K):
+                self.reuse_frame(frame + 1 + i, self.stats[i])
+            stop.record(self.stream)
+            self.barrier(ws)
+        self.first_timed = frame + 1
+        ms = start.elapsed_time(stop) / self.K
+        rows = [self.pv.stats_dict(self.stats[i]) for i in range(self.K)]
+        return ms, rows, clocks.summary(), self.mean_photons(), self.pv.pv_read_device_status(self.h)
+
+    # ---- the same frames with per-frame events and the library's stage events
+    def instrumented(self, ws, rows_head):
+        pv, K = self.pv, self.K
+        frame = self.restart()
+        for _ in range(self.W):
+            frame += 1
+            self.reuse_frame(frame, self.stats[-1])
+        pv.pv_stage_timing(self.h, K)
+        self.barrier(ws)
+        ev = []
+        for i in range(K):
+            f = frame + 1 + i
+            e = [self.ev() for _ in range(3)]
+            e[0].record(self.stream)
+            pv.pv_update_dynamic(self.h, self.xfs[f], self.lts[f])
+            e[1].record(self.stream)
+            pv.pv_verify_retrace_deposit(self.h, self.P, self.mode, self.tau, 0, self.seed, f, self.atlas,
+                                         self.sc.atlas_rect, self.scale, self.stats[K + i])
+            e[2].record(self.stream)
+            ev.append(e)
+        self.barrier(ws)
+        stages = pv.pv_stage_times(self.h, K)
+        pv.pv_stage_timing(self.h, 0)
+        per_frame = np.array([e[0].elapsed_time(e[2]) for e in ev])
+        update = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+        same = all(pv.stats_dict(self.stats[K + i]) == rows_head[i] for i in range(K))
+        return {"per_frame_ms": per_frame, "update_ms": update,
+                "stages_ms": dict(zip(pv.STAGES, [float(x) for x in stages.mean(axis=0)])), "counters_match": same}
+
+    # ---- atlas carried from frame to frame
+    def delta(self, ws):
+        pv, torch = self.pv, self.torch
+        atlas_full = self.atlas.clone()
+        atlas_delta = torch.zeros_like(self.atlas)
+        frame = self.restart()
+        pv.pv_deposit(self.h, self.P, atlas_delta, self.sc.atlas_rect, self.scale)
+
+        def delta_frame(f):
+            pv.pv_update_dynamic(self.h, self.xfs[f], self.lts[f])
+            pv.pv_verify_retrace_deposit_delta(self.h, self.P, self.mode, self.tau, 0, self.seed, f, atlas_delta,
+                                               self.sc.atlas_rect, self.scale, self.stats[-1])
+
+        for _ in range(self.W):
+            frame += 1
+            delta_frame(frame)
+        self.barrier(ws)
+        s, e = self.ev(), self.ev()
+        s.record(self.stream)
+        for i in range(self.K):
+            delta_frame(frame + 1 + i)
+        e.record(self.stream)
+        self.barrier(ws)
+        ms = s.elapsed_time(e) / self.K
+        equal = bool(torch.equal(atlas_delta, atlas_full))
+        return {"call": "pv_verify_retrace_deposit_delta", "ms_per_frame": ms, "paths_per_s": self.N / (ms * 1e-3),
+                "atlas_equal_to_full_deposit": equal}
+
+    # ---- the separate calls, with events between them; then the compaction alone on each frame's marks
+    def separate(self, ws):
+        pv, K = self.pv, self.K
+        frame = self.restart()
+        self.stats[:2 * K].zero_()                  # counters accumulate
+        for _ in range(self.W):
+            frame += 1
+            pv.pv_update_dynamic(self.h, self.xfs[frame], self.lts[frame])
+            pv.pv_verify_paths(self.h, self.P, self.mode, self.tau, 0, self.lst, self.cnt, self.stats[-1])
+            pv.pv_retrace_invalid(self.h, self.P, self.lst, self.cnt, self.seed, frame, self.stats[-1])
+            pv.pv_deposit(self.h, self.P, self.atlas, self.sc.atlas_rect, self.scale)
+        self.barrier(ws)
+        s, e = self.ev(), self.ev()
+        ev = []
+        s.record(self.stream)
+        for i in range(K):
+            f = frame + 1 + i
+            x = [self.ev() for _ in range(5)]
+            x[0].record(self.stream)
+            pv.pv_update_dynamic(self.h, self.xfs[f], self.lts[f])
+            x[1].record(self.stream)
+            pv.pv_verify_paths(self.h, self.P, self.mode, self.tau, 0, self.lst, self.cnt, self.stats[i])
+            x[2].record(self.stream)
+            pv.pv_retrace_invalid(self.h, self.P, self.lst, self.cnt, self.seed, f, self.stats[K + i])
+            x[3].record(self.stream)
+            pv.pv_deposit(self.h, self.P, self.atlas, self.sc.atlas_rect, self.scale)
+            x[4].record(self.stream)
+            ev.append(x)
+        e.record(self.stream)
+        self.barrier(ws)
+        ms = s.elapsed_time(e) / K
+        parts = np.array([[x[j].elapsed_time(x[j + 1]) for j in range(4)] for x in ev]).mean(axis=0)
+        rows_v = [pv.stats_dict(self.stats[i]) for i in range(K)]
+        rows_r = [pv.stats_dict(self.stats[K + i]) for i in range(K)]
+        # the compaction alone (pv_compact_replace, the k_compact kernel) on the marks of each verified frame
+        frame = self.restart()
+        cms = []
+        for i in range(self.W + K):
+            frame += 1
+            pv.pv_update_dynamic(self.h, self.xfs[frame], self.lts[frame])
+            pv.pv_verify_paths(self.h, self.P, self.mode, self.tau, 0, self.lst, self.cnt, self.stats[-1])
+            a, b = self.ev(), self.ev()
+            a.record(self.stream)
+            pv.pv_compact_replace(self.h, self.P, self.lst2, self.cnt2)
+            b.record(self.stream)
+            pv.pv_retrace_invalid(self.h, self.P, self.lst, self.cnt, self.seed, frame, self.stats[-1])
+            if i >= self.W:
+                cms.append((a, b))
+        self.barrier(ws)
+        compact_ms = float(np.mean([a.elapsed_time(b) for a, b in cms]))
+        return {"ms_per_frame": ms, "parts": dict(zip(["update", "verify", "retrace", "deposit"],
+                                                      [float(v) for v in parts])),
+                "compact_ms": compact_ms}, rows_v, rows_r
+
+    # ---- trace-all on the same frames
+    def trace_all(self, ws):
+        pv, K = self.pv, self.K
+        frame = self.restart()
+        for _ in range(self.W):
+            frame += 1
+            pv.pv_update_dynamic(self.h, self.xfs[frame], self.lts[frame])
+            pv.pv_trace_all(self.h, self.P, self.seed, frame, self.stats[-1])
+            pv.pv_deposit(self.h, self.P, self.atlas, self.sc.atlas_rect, self.scale)
+        self.stats[:K].zero_()
+        self.barrier(ws)
+        s, e = self.ev(), self.ev()
+        ev = []
+        s.record(self.stream)
+        for i in range(K):
+            f = frame + 1 + i
+            x = [self.ev() for _ in range(4)]
+            x[0].record(self.stream)
+            pv.pv_update_dynamic(self.h, self.xfs[f], self.lts[f])
+            x[1].record(self.stream)
+            pv.pv_trace_all(self.h, self.P, self.seed, f, self.stats[i])
+            x[2].record(self.stream)
+            pv.pv_deposit(self.h, self.P, self.atlas, self.sc.atlas_rect, self.scale)
+            x[3].record(self.stream)
+            ev.append(x)
+        e.record(self.stream)
+        self.barrier(ws)
+        ms = s.elapsed_time(e) / K
+        parts = np.array([[x[j].elapsed_time(x[j + 1]) for j in range(3)] for x in ev]).mean(axis=0)
+        per_frame = np.array([x[0].elapsed_time(x[3]) for x in ev])
+        rows = [pv.stats_dict(self.stats[i]) for i in range(K)]
+        return ms, dict(zip(["update", "trace_all", "deposit"], [float(v) for v in parts])), per_frame, rows, \
+            self.mean_photons()
+
+    # ---- end to end through the public API: host poses in, atlas and stats out (pinned), every frame
+    def end_to_end(self, ws):
+        """Two atlases alternate: frame i's result is copied to the host on a
+        copy stream while frame i + 1 computes, and the host waits for frame
+        i's copy before it launches frame i + 2."""
+        torch, K = self.torch, self.K
+        A = self.A
+        atl = [self.atlas, torch.zeros_like(self.atlas)]
+        host_atlas = [torch.empty(A, A, 3, dtype=torch.int64, pin_memory=True) for _ in range(2)]
+        host_stats = [torch.empty(self.pv.STATS_WORDS, dtype=torch.int32, pin_memory=True) for _ in range(2)]
+        copy_stream = torch.cuda.Stream(device=self.dev)
+        done = [torch.cuda.Event(), torch.cuda.Event()]
+        copied = [None, None]
+
+        def e2e_frame(i, f):
+            b = i % 2
+            if copied[b] is not None:
+                copied[b].synchronize()           # the host has frame i - 2's result; its buffers are free
+                self.stream.wait_event(copied[b])
+            self.reuse_frame(f, self.stats[-1 - b], atl[b])
+            done[b].record(self.stream)
+            copy_stream.wait_event(done[b])
+            with torch.cuda.stream(copy_stream):
+                host_atlas[b].copy_(atl[b], non_blocking=True)
+                host_stats[b].copy_(self.stats[-1 - b], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(copy_stream)
+            copied[b] = ev
+
+        frame = self.restart()
+        for i in range(self.W):
+            frame += 1
+            e2e_frame(i, frame)
+        for ev in copied:
+            ev.synchronize()
+        self.barrier(ws)
+        t = time.perf_counter()
+        for i in range(K):
+            frame += 1
+            e2e_frame(i, frame)
+        for ev in copied:
+            ev.synchronize()
+        e2e_s = (time.perf_counter() - t) / K
+        h2d = 12 * 4 * int(self.sc.object_dynamic.sum()) + 64 * len(self.sc.lights(1))
+        return {"value": None, "unit": "paths/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": int(host_atlas[0].numel() * 8 + host_stats[0].numel() * 4), "_s": e2e_s}
+
+    # ---- F frames from a fresh trace-all with one setting: mean frame time and per-frame counters
+    def run_frames(self, F, mode=None, tau=None, lts=None, stage=False, flags=0):
+        """Frames 2..F+1 from a fresh trace-all, timed together; with ``stage``
+        the same frames again with the library's stage events."""
+        pv = self.pv
+        lts = lts or self.lts
+        self.restart(lts)
+        self.stats[-2].zero_()
+        self.torch.cuda.synchronize()
+        s, e = self.ev(), self.ev()
+        s.record(self.stream)
+        for f in range(2, F + 2):
+            self.reuse_frame(f, self.stats[-2], mode=mode, tau=tau, lts=lts, flags=flags)
+        e.record(self.stream)
+        self.torch.cuda.synchronize()
+        ms = s.elapsed_time(e) / F
+        st = pv.stats_dict(self.stats[-2])
+        per = {k: v / F for k, v in st.items()}
+        out = {"frames": F, "ms_per_frame": ms, "paths_per_s": self.N / (ms * 1e-3),
+               "rays_per_frame": per["vis_rays"] + per["cont_rays"] + per["trace_rays"],
+               "vis_rays_per_frame": per["vis_rays"], "cont_rays_per_frame": per["cont_rays"],
+               "retrace_rays_per_frame": per["trace_rays"], "listed_per_frame": per["n_listed"],
+               "cont_paths_per_frame": per["n_cont"], "reemit_per_frame": per["n_reemit"],
+               "tails_per_frame": per["n_tail"], "updated_per_frame": per["n_updated"]}
+        if stage:
+            self.restart(lts)
+            pv.pv_stage_timing(self.h, F)
+            for f in range(2, F + 2):
+                self.reuse_frame(f, self.stats[-1], mode=mode, tau=tau, lts=lts, flags=flags)
+            t = pv.pv_stage_times(self.h, F).mean(axis=0)
+            pv.pv_stage_timing(self.h, 0)
+            out["stages_ms"] = dict(zip(pv.STAGES, [float(x) for x in t]))
+        out["device_status"] = pv.pv_read_device_status(self.h)
+        return out
+
+    def destroy(self):
+        self.pv.pv_destroy_scene(self.h)
+
+
+def kernel_table(w, head_rows, inst, sep, rows_v, rows_r, ta, rows_ta, L_reuse, L_ta, hbm_peak, fma):
+    """Per-kernel durations (CUDA events) against the algorithmic bytes each
+    kernel must move (and, for traversals, the algorithmic FP32 work)."""
+    agg = lambda key, rows: float(np.mean([r[key] for r in rows]))
+    N = w.N
+    n_dyn_tris = int((w.sc.object_dynamic[w.sc.tri_object] != 0).sum())
+    photons = N * L_reuse                                   # stored photons after a reuse frame
+    listed, tails, cont = agg("n_listed", head_rows), agg("n_tail", head_rows), agg("n_cont", head_rows)
+    new_photons = agg("photons_written", head_rows)
+    traffic = NCU_TRAFFIC.get(w.sc.name, {}) if NCU_TRAFFIC.get("digest") == source_digest() else {}
+
+    def row(kernel, where, ms, nbytes, unit_note, ops=None):
+        r = {"kernel": kernel, "timed": where, "duration_ms": ms, "algorithmic_bytes": nbytes,
+             "bytes_per_unit": unit_note, "achieved_gbs": nbytes / (ms * 1e-3) / 1e9,
+             "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm_peak, "traffic": traffic.get(kernel)}
+        if ops is not None:
+            r["algorithmic_ops"] = ops
+            r["achieved_top_s"] = ops / (ms * 1e-3) / 1e12
+            r["alu_frac"] = ops / (ms * 1e-3) / 1e12 / fma["top_s"]
+        return r
+
+    ops = lambda rows: OPS_PER_NODE * agg("node_visits", rows) + OPS_PER_TRI * agg("tri_tests", rows)
+    st = inst["stages_ms"]
+    t = [
+        row("k_refit_wide", "pose update of the instrumented reuse frames", inst["update_ms"],
+            n_dyn_tris * (36 + 48 + 128 / 3.0),
+            "per dynamic triangle: 36 B object-local corners read, 48 B world triangle written, a third of a "
+            "128 B wide node written"),
+        row("k_verify_box", "stage events of pv_verify_retrace_deposit", st["k_verify"],
+            N * (16 + 1) + 16.0 * photons + 8.0 * (listed - tails) + 4.0 * cont,
+            "per path 4 B info + 12 B origin read, 1 B touched mark written; 16 B per stored photon (position row) "
+            "read; 4 B info + 4 B list entry per listed path; 4 B per Alg. 1 list entry"),
+        row("k_cont_trace<deposit>", "stage events of pv_verify_retrace_deposit", st["retrace_kernel"],
+            N * 4 + 32.0 * photons + 8.0 * (listed + cont) + 32.0 * new_photons + 32.0 * L_reuse * cont,
+            "deposit: 4 B info + 32 B per stored photon read; re-trace: 4 B list entry + 4 B info per listed or "
+            "Alg. 1 path, 32 B per new photon written; Alg. 1: 32 B per stored photon of each path it checks",
+            ops(head_rows)),
+        row("k_compact", "pv_compact_replace on each verified frame's marks", sep["compact_ms"],
+            N * 4 + 4.0 * agg("n_listed", rows_v), "4 B info read per path, 4 B per listed id written"),
+        row("k_trace (re-trace)", "pv_retrace_invalid of the separate calls", sep["parts"]["retrace"],
+            8.0 * agg("n_listed", rows_v) + 32.0 * agg("photons_written", rows_r) + 32.0 * agg("n_tail", rows_v),
+            "4 B list entry + 4 B info per listed path, 32 B start photon read per tail, 32 B per new photon "
+            "written", ops(rows_r)),
+        row("k_deposit", "pv_deposit of the separate calls", sep["parts"]["deposit"], N * 4 + 32.0 * photons,
+            "4 B info per path + 32 B per stored photon read (the atlas stays in L2)"),
+        row("k_trace (trace-all)", "pv_trace_all of the trace-all frames", ta["trace_all"],
+            N * 16 + 32.0 * agg("photons_written", rows_ta),
+            "12 B origin + 4 B info written per path, 32 B per photon written", ops(rows_ta)),
+    ]
+    return t
+
+
+def measure(pv, torch, sc, args, dev, stream, ws, rank, local, fma, full: bool):
+    """Every loop on one workload; ``full`` adds the tau, mode and moving-point-light rows."""
+    K, W = args.steps, args.warmup
+    F = args.sweep_frames
+    frames_needed = max(W + K + 2, F + 2)
+    w = Workload(pv, torch, sc, args, dev, stream, rank, K, W, frames_needed)
+    pk, pk_kind = peaks()
+    reuse_ms, head_rows, clocks, L_reuse, status = w.headline(ws, local)
+    inst = w.instrumented(ws, head_rows)
+    delta = w.delta(ws)
+    sep, rows_v, rows_r = w.separate(ws)
+    trace_ms, ta_parts, ta_per_frame, rows_ta, L_ta = w.trace_all(ws)
+    e2e = None if args.no_e2e else w.end_to_end(ws)
+    agg = lambda key, rows: float(np.mean([r[key] for r in rows]))
+    kt = kernel_table(w, head_rows, inst, sep, rows_v, rows_r, ta_parts, rows_ta, L_reuse, L_ta, pk["hbm_gbs"], fma)
+    rays_reuse = agg("vis_rays", head_rows) + agg("cont_rays", head_rows) + agg("trace_rays", head_rows)
+    res = {"workload": f"{sc.name}: {WORKLOADS[sc.name]}", "paths": w.N, "max_bounces": w.B, "mode": args.mode,
+           "tau": w.tau, "frames_timed": K, "first_timed_frame": w.first_timed,
+           "l2": "inputs larger than L2 (path buffers %.0f MB)" % (w.N * (4 + 12 + 32 * w.B) / 1e6),
+           "reuse_ms_per_frame": reuse_ms, "trace_all_ms_per_frame": trace_ms,
+           "speedup_vs_trace_all": trace_ms / reuse_ms,
+           "reuse_ms_parts": {"update": inst["update_ms"],
+                              "verify_retrace_deposit": float(np.mean(inst["per_frame_ms"])) - inst["update_ms"]},
+           "instrumented_ms_per_frame": float(np.mean(inst["per_frame_ms"])),
+           "instrumented_counters_match": inst["counters_match"],
+           "per_frame_ms_p50_p90": {"reuse": [float(np.percentile(inst["per_frame_ms"], q)) for q in (50, 90)],
+                                    "trace_all": [float(np.percentile(ta_per_frame, q)) for q in (50, 90)],
+                                    "note": "from the per-frame events of the instrumented loops"},
+           "verify_retrace_deposit_stages_ms": inst["stages_ms"],
+           "delta_deposit": delta, "separate_calls": sep, "trace_all_ms_parts": ta_parts,
+           "rays_per_frame_reuse": rays_reuse, "rays_per_frame_trace_all": agg("trace_rays", rows_ta),
+           "listed_per_frame": agg("n_listed", head_rows), "cont_paths_per_frame": agg("n_cont", head_rows),
+           "tails_per_frame": agg("n_tail", head_rows), "vis_rays_per_frame": agg("vis_rays", head_rows),
+           "mean_photons_per_path": L_reuse,
+           "retrace_node_visits_per_ray": agg("node_visits", rows_r) / max(agg("trace_rays", rows_r), 1),
+           "retrace_tri_tests_per_ray": agg("tri_tests", rows_r) / max(agg("trace_rays", rows_r), 1),
+           "scene_build_s": w.build_s, "build_flags": args.build_flags, "kernels": kt}
+    if full and not args.no_sweeps:
+        res["tau_sweep"] = {f"{tau:g}": w.run_frames(F, tau=tau) for tau in TAUS}
+        for row in res["tau_sweep"].values():
+            row["speedup_vs_trace_all"] = trace_ms / row["ms_per_frame"]
+        res["modes_tau_1pct"] = {m: w.run_frames(F, mode=MODES[m], tau=0.01) for m in MODES}
+        # error mode with the moved objects' triangles in place of their boxes (PV_FLAG_ERROR_EXACT)
+        res["modes_tau_1pct"]["error_triangle_tests"] = w.run_frames(F, mode=MODES["error"], tau=0.01, flags=2)
+        res["modes_tau_1pct"]["trace_all_rays_per_frame"] = agg("trace_rays", rows_ta)
+        if sc.name == "villa":
+            import scenes
+            vp = scenes.villa(moving_light="point")
+            lts = {f: pv.make_lights(vp.lights(f)) for f in range(1, F + 2)}
+            row = w.run_frames(F, lts=lts, stage=True)
+            row["light"] = "ceiling point light moving 0.05 m/frame on a 1 m loop, torch static"
+            row["speedup_vs_trace_all"] = trace_ms / row["ms_per_frame"]
+            res["moving_point_light"] = row
+    out = {"res": res, "value": w.N / (reuse_ms * 1e-3), "reuse_ms": reuse_ms, "trace_ms": trace_ms, "e2e": e2e,
+           "clocks": clocks, "kernels": kt, "N": w.N}
+    if not args.no_splat and sc.name != "tiny_box":
+        res["splat"] = time_splat(pv, w.h, w.P, sc, K, W, stream, dev)
+    if not args.no_adjoint and sc.name == "city":
+        res["adjoint"] = time_adjoint(pv, w.h, w.P, sc, w.N, w.A, K, W, stream, dev)
+    res["device_status"] = [status, pv.pv_read_device_status(w.h)]
+    w.destroy()
+    del w
+    torch.cuda.empty_cache()
+    if not args.no_dm and sc.name == "city":
+        xfs = {f: sc.xforms(f) for f in range(1, W + K + 3)}
+        lts = {f: sc.lights(f) for f in range(1, W + K + 3)}
+        res["distribution_maps"] = time_dm(pv, sc, MODES[args.mode], res["tau"], sc.seed + 7919 * rank, K, W, xfs,
+                                           lts, stream, dev)
+        torch.cuda.empty_cache()
+    return out
 
 
 # ----------------------------------------------------------------------------- ours
@@ -195,322 +668,60 @@ def run_ours(args, ws, rank, local):
     pvbuild.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    sc = scene_for(args.workload)
-    mode = MODES[args.mode]
-    tau = sc.tau if args.tau is None else args.tau
-    seed = sc.seed + 7919 * rank
-    N, B = sc.n_paths, sc.max_bounces
-    frames_needed = args.warmup + args.steps + 2      # every loop restarts at frame 1: the same frames timed
-    xfs = {f: sc.xforms(f) for f in range(1, frames_needed + 1)}
-    lts = {f: sc.lights(f) for f in range(1, frames_needed + 1)}
-
-    t0 = time.time()
-    h = pv.pv_build_scene(sc.verts, sc.tri_object, sc.object_dynamic, sc.object_albedo, lts[1], B, sc.diag,
-                          object_xform=xfs[1], flags=args.build_flags)
-    build_s = time.time() - t0
-    P = pv.Paths.allocate(N, B, dev)
-    A = args.atlas
-    atlas = torch.zeros(A, A, 3, dtype=torch.int64, device=dev)
-    scale = 40 if args.workload != "tiny_box" else 31
-    lst = torch.zeros(N, dtype=torch.int32, device=dev)
-    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
-    K, W = args.steps, args.warmup
-    stats = torch.zeros(4 * K + 2, pv.STATS_WORDS, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
-
-    def restart():
-        # back to the pose of frame 1 and a fresh bootstrap, so that every loop below runs frames 2, 3, ...
-        pv.pv_update_dynamic(h, xfs[1], lts[1])
-        pv.pv_trace_all(h, P, seed, 1)
-        return 1
-
-    frame = restart()
-
-    def reuse_frame(f, st, at=None):
-        pv.pv_update_dynamic(h, xfs[f], lts[f])
-        pv.pv_verify_retrace_deposit(h, P, mode, tau, 0, seed, f, atlas if at is None else at, sc.atlas_rect, scale,
-                                     st)
-
-    def timed_loop(fn, first_frame, rows_a, rows_b):
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
-        for i in range(K):
-            f = first_frame + i
-            e = ev[i]
-            e[0].record(stream)
-            pv.pv_update_dynamic(h, xfs[f], lts[f])
-            e[1].record(stream)
-            fn(f, rows_a[i], rows_b[i], e)
-            e[4].record(stream)
-        return ev
-
-    def fused_body(f, st_v, st_r, e):
-        pv.pv_verify_retrace_deposit(h, P, mode, tau, 0, seed, f, atlas, sc.atlas_rect, scale, st_v)
-        e[2].record(stream)
-        e[3].record(stream)
-
-    def separate_body(f, st_v, st_r, e):
-        pv.pv_verify_paths(h, P, mode, tau, 0, lst, cnt, st_v)
-        e[2].record(stream)
-        pv.pv_retrace_invalid(h, P, lst, cnt, seed, f, st_r)
-        e[3].record(stream)
-        pv.pv_deposit(h, P, atlas, sc.atlas_rect, scale)
-
-    def trace_body(f, st_v, st_r, e):
-        e[2].record(stream)
-        pv.pv_trace_all(h, P, seed, f, st_r)
-        e[3].record(stream)
-        pv.pv_deposit(h, P, atlas, sc.atlas_rect, scale)
-
-    def barrier():
-        torch.cuda.synchronize()
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    # ---- reuse pipeline, one call from verification to re-trace (headline): only the two events that bracket
-    # the K frames, nothing recorded between the library's launches
-    for i in range(W):
-        frame += 1
-        reuse_frame(frame, stats[-1])
-    barrier()
-    clocks = Clocks(local)
-    with clocks:
-        start = torch.cuda.Event(enable_timing=True)
-        stop = torch.cuda.Event(enable_timing=True)
-        start.record(stream)
-        for i in range(K):
-            reuse_frame(frame + 1 + i, stats[i])
-        stop.record(stream)
-        barrier()
-    frame += K
-    reuse_ms = start.elapsed_time(stop) / K
-    st_reuse = [pv.stats_dict(stats[i]) for i in range(K)]
-    info_np = P.info.cpu().numpy().view(np.uint32)
-    mean_L = float(((info_np >> 22) & 15).mean())
-    status = pv.pv_read_device_status(h)
-
-    # ---- the same frames again with events between the calls and the library's own stage events
-    frame = restart()
-    for i in range(W):
-        frame += 1
-        reuse_frame(frame, stats[-1])
-    pv.pv_stage_timing(h, K)                   # the library records its stages' events in the timed frames
-    barrier()
-    ev = timed_loop(fused_body, frame + 1, stats[K:2 * K], stats[K:2 * K])
-    barrier()
-    frame += K
-    reuse_parts = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in ev]).mean(axis=0)
-    stage_ms = pv.pv_stage_times(h, K).mean(axis=0)     # k_verify, compaction, fused kernel, whole call
-    pv.pv_stage_timing(h, 0)
-    per_frame = np.array([e[0].elapsed_time(e[4]) for e in ev])
-    instrumented_ms = float(per_frame.mean())
-    reuse_pct = [float(np.percentile(per_frame, q)) for q in (50, 90)]
-    same = all(pv.stats_dict(stats[K + i]) == st_reuse[i] for i in range(K))
-
-    # ---- the same frames with the atlas carried from frame to frame (pv_verify_retrace_deposit_delta): only the
-    # paths a frame changes leave and re-enter it; the final atlas must equal the full deposit's
-    atlas_full = atlas.clone()
-    atlas_delta = torch.zeros_like(atlas)
-    frame = restart()
-    pv.pv_deposit(h, P, atlas_delta, sc.atlas_rect, scale)
-
-    def delta_frame(f, st):
-        pv.pv_update_dynamic(h, xfs[f], lts[f])
-        pv.pv_verify_retrace_deposit_delta(h, P, mode, tau, 0, seed, f, atlas_delta, sc.atlas_rect, scale, st)
-
-    for i in range(W):
-        frame += 1
-        delta_frame(frame, stats[-1])
-    barrier()
-    start4 = torch.cuda.Event(enable_timing=True)
-    stop4 = torch.cuda.Event(enable_timing=True)
-    start4.record(stream)
-    for i in range(K):
-        delta_frame(frame + 1 + i, stats[-1])
-    stop4.record(stream)
-    barrier()
-    frame += K
-    delta_ms = start4.elapsed_time(stop4) / K
-    delta_equal = bool(torch.equal(atlas_delta, atlas_full))
-    del atlas_full, atlas_delta
-
-    # ---- the same frames through the separate calls (pv_verify_paths, then pv_retrace_invalid)
-    frame = restart()
-    stats[:2 * K].zero_()                      # counters accumulate
-    for i in range(W):
-        frame += 1
-        pv.pv_update_dynamic(h, xfs[frame], lts[frame])
-        pv.pv_verify_paths(h, P, mode, tau, 0, lst, cnt, stats[-1])
-        pv.pv_retrace_invalid(h, P, lst, cnt, seed, frame, stats[-1])
-        pv.pv_deposit(h, P, atlas, sc.atlas_rect, scale)
-    barrier()
-    start3 = torch.cuda.Event(enable_timing=True)
-    stop3 = torch.cuda.Event(enable_timing=True)
-    start3.record(stream)
-    ev3 = timed_loop(separate_body, frame + 1, stats[:K], stats[K:2 * K])
-    stop3.record(stream)
-    barrier()
-    frame += K
-    sep_ms = start3.elapsed_time(stop3) / K
-    sep_parts = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in ev3]).mean(axis=0)
-    st_retrace = [pv.stats_dict(stats[K + i]) for i in range(K)]
-
-    # ---- trace-all baseline (same library, same GPU), on the same frames
-    frame = restart()
-    for i in range(W):
-        frame += 1
-        pv.pv_update_dynamic(h, xfs[frame], lts[frame])
-        pv.pv_trace_all(h, P, seed, frame, stats[-1])
-        pv.pv_deposit(h, P, atlas, sc.atlas_rect, scale)
-    barrier()
-    start2 = torch.cuda.Event(enable_timing=True)
-    stop2 = torch.cuda.Event(enable_timing=True)
-    start2.record(stream)
-    ev2 = timed_loop(trace_body, frame + 1, stats[2 * K:3 * K], stats[3 * K:4 * K])
-    stop2.record(stream)
-    barrier()
-    frame += K
-    trace_ms = start2.elapsed_time(stop2) / K
-    parts2 = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in ev2]).mean(axis=0)
-    per_frame2 = np.array([e[0].elapsed_time(e[4]) for e in ev2])
-    trace_pct = [float(np.percentile(per_frame2, q)) for q in (50, 90)]
-    st_trace = [pv.stats_dict(stats[3 * K + i]) for i in range(K)]
-
-    # ---- end to end through the API: host poses in, atlas and stats out (pinned), every frame.  Two atlases
-    # alternate: frame i's result is copied to the host on a copy stream while frame i + 1 computes, and the
-    # host waits for frame i's copy before it launches frame i + 2
-    e2e = None
-    if not args.no_e2e:
-        atl = [atlas, torch.zeros_like(atlas)]
-        host_atlas = [torch.empty(A, A, 3, dtype=torch.int64, pin_memory=True) for _ in range(2)]
-        host_stats = [torch.empty(pv.STATS_WORDS, dtype=torch.int32, pin_memory=True) for _ in range(2)]
-        copy_stream = torch.cuda.Stream(device=dev)
-        done = [torch.cuda.Event(), torch.cuda.Event()]
-        copied = [None, None]
-
-        def e2e_frame(i, f):
-            b = i % 2
-            if copied[b] is not None:
-                copied[b].synchronize()           # the host has frame i - 2's result; its buffers are free
-                stream.wait_event(copied[b])
-            reuse_frame(f, stats[-1 - b], atl[b])
-            done[b].record(stream)
-            copy_stream.wait_event(done[b])
-            with torch.cuda.stream(copy_stream):
-                host_atlas[b].copy_(atl[b], non_blocking=True)
-                host_stats[b].copy_(stats[-1 - b], non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(copy_stream)
-            copied[b] = ev
-
-        # the same frames as the device-timed loop, from a fresh bootstrap
-        frame = restart()
-        for i in range(W):
-            frame += 1
-            e2e_frame(i, frame)
-        for ev in copied:
-            ev.synchronize()
-        barrier()
-        t = time.perf_counter()
-        for i in range(K):
-            frame += 1
-            e2e_frame(i, frame)
-        for ev in copied:
-            ev.synchronize()
-        e2e_s = (time.perf_counter() - t) / K
-        h2d = 12 * 4 * int(sc.object_dynamic.sum()) + 64 * len(lts[1])
-        e2e = {"value": None, "unit": "paths/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": int(host_atlas[0].numel() * 8 + host_stats[0].numel() * 4), "_s": e2e_s}
-    # ---- differentiable model: forward splat and adjoint of an L2 atlas loss
-    adjoint = None if args.no_adjoint else time_adjoint(pv, h, P, sc, N, A, K, W, stream, dev)
-    # ---- screen-space splat of the current records at 1920 x 1080
-    splat = None if args.no_splat or args.workload == "tiny_box" else time_splat(pv, h, P, sc, K, W, stream, dev)
-    # ---- the same reuse frames with distribution maps on the lights (Sec. 3.1)
-    dm = None if args.no_dm or args.workload == "tiny_box" else time_dm(pv, sc, mode, tau, seed, K, W, xfs, lts,
-                                                                          stream, dev)
-    status2 = pv.pv_read_device_status(h)
-    pv.pv_destroy_scene(h)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fma = fma_peak(pv, torch, dev, sms, stream)
+    head = measure(pv, torch, scene_for(args.workload), args, dev, stream, ws, rank, local, fma, full=True)
+    secondary = {}
+    if args.workload == "villa" and not args.no_secondary:
+        city = measure(pv, torch, scene_for("city"), args, dev, stream, ws, rank, local, fma, full=False)
+        secondary["city"] = dict(city["res"], value_paths_per_s=city["value"])
+        b16 = run_batch(args, ws, rank, local, print_line=False)
+        if b16 is not None:
+            secondary["batch16"] = b16
 
     # ---- max over ranks
-    vals = torch.tensor([reuse_ms, trace_ms, e2e["_s"] if e2e else 0.0], dtype=torch.float64, device=dev)
+    e2e = head["e2e"]
+    vals = torch.tensor([head["reuse_ms"], head["trace_ms"], e2e["_s"] if e2e else 0.0], dtype=torch.float64,
+                        device=dev)
     if ws > 1:
         import torch.distributed as dist
         dist.all_reduce(vals, op=dist.ReduceOp.MAX)
     reuse_ms, trace_ms, e2e_s = vals.tolist()
     if rank != 0:
         return
-
     pk, pk_kind = peaks()
-    names = ["update", "verify_retrace", "-", "deposit"]
-    agg = lambda key, rows: float(np.mean([r[key] for r in rows]))
-    # dominant kernel: the persistent kernel of pv_verify_retrace_deposit (Alg. 1, the re-trace and the atlas
-    # deposit), timed by the library's own events; its traversal work comes from the counted node visits and
-    # triangle tests of the call (k_verify traverses only for moving point lights: vis_rays = 0 here)
-    ops = OPS_PER_NODE * agg("node_visits", st_reuse) + OPS_PER_TRI * agg("tri_tests", st_reuse)
-    ops_peak = SM_COUNT * FP32_LANES * pk.get("sm_max_mhz", 2070.0) * 1e6
-    achieved = ops / (float(stage_ms[2]) * 1e-3)
-    roof = {"kernel": "k_cont_trace<deposit> (pv_verify_retrace_deposit)", "bound": "alu",
-            "achieved": achieved / 1e12, "peak": ops_peak / 1e12, "unit": "Top/s", "frac": achieved / ops_peak,
-            "duration_ms": float(stage_ms[2]),
-            "traffic": TRACE_TRAFFIC.get(args.workload), "traffic_unit": "bytes per launch (ncu)",
-            "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x max SM clock"}
-    if args.workload in TRACE_WARP_INST:
-        # the same kernel against the issue rate: warp instructions per launch (ncu) over the live duration,
-        # against one instruction per scheduler per clock; lanes per instruction give the SIMT efficiency
-        inst, lanes = TRACE_WARP_INST[args.workload]
-        issue_peak = SM_COUNT * SCHEDULERS_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6
-        issue = inst / (float(stage_ms[2]) * 1e-3)
-        roof["issue"] = {"achieved": issue / 1e9, "peak": issue_peak / 1e9, "unit": "G warp-inst/s",
-                         "frac": issue / issue_peak, "active_lanes_per_inst": lanes, "simt_efficiency": lanes / 32.0,
-                         "source": "warp instructions per launch from ncu, duration live"}
-    rays_reuse = agg("vis_rays", st_reuse) + agg("cont_rays", st_reuse) + agg("trace_rays", st_reuse)
-    rays_trace = agg("trace_rays", st_trace)
-    value = ws * N / (reuse_ms * 1e-3)
-    cfg = {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "paths": N, "max_bounces": B,
-           "mode": args.mode, "tau": tau, "frames_timed": K,
-           "l2": "inputs larger than L2 (path buffers %.0f MB)" % (N * (4 + 12 + 32 * B) / 1e6),
-           "reuse_ms_per_frame": reuse_ms, "trace_all_ms_per_frame": trace_ms,
-           "speedup_vs_trace_all": trace_ms / reuse_ms,
-           "reuse_ms_parts": {"update": float(reuse_parts[0]), "verify_retrace_deposit": float(reuse_parts[1])},
-           "instrumented_ms_per_frame": instrumented_ms, "instrumented_counters_match": same,
-           "per_frame_ms_p50_p90": {"reuse": reuse_pct, "trace_all": trace_pct,
-                                    "note": "from the per-frame events of the instrumented loops"},
-           "delta_deposit": {"call": "pv_verify_retrace_deposit_delta", "ms_per_frame": delta_ms,
-                             "paths_per_s": ws * N / (delta_ms * 1e-3), "atlas_equal_to_full_deposit": delta_equal},
-           "verify_retrace_deposit_stages_ms": {"k_verify": float(stage_ms[0]), "compaction": float(stage_ms[1]),
-                                                "k_cont_trace+deposit": float(stage_ms[2]),
-                                                "call": float(stage_ms[3])},
-           "separate_calls": {"ms_per_frame": sep_ms,
-                              "parts": dict(zip(["update", "verify", "retrace", "deposit"],
-                                                [float(x) for x in sep_parts]))},
-           "trace_all_ms_parts": dict(zip(["update", "-", "trace_all", "deposit"], [float(x) for x in parts2])),
-           "rays_per_frame_reuse": rays_reuse, "rays_per_frame_trace_all": rays_trace,
-           "listed_per_frame": agg("n_listed", st_reuse), "cont_paths_per_frame": agg("n_cont", st_reuse),
-           "tails_per_frame": agg("n_tail", st_reuse), "vis_rays_per_frame": agg("vis_rays", st_reuse),
-           "mean_photons_per_path": mean_L,
-           "retrace_node_visits_per_ray": agg("node_visits", st_retrace) / max(agg("trace_rays", st_retrace), 1),
-           "retrace_tri_tests_per_ray": agg("tri_tests", st_retrace) / max(agg("trace_rays", st_retrace), 1),
-           "scene_build_s": build_s, "build_flags": args.build_flags, "device_status": [status, status2]}
+    cfg = head["res"]
+    cfg["reuse_ms_per_frame"], cfg["trace_all_ms_per_frame"] = reuse_ms, trace_ms
+    cfg["speedup_vs_trace_all"] = trace_ms / reuse_ms
+    cfg.update(secondary)
+    dom = next(k for k in head["kernels"] if k["kernel"] == "k_cont_trace<deposit>")
+    roof = {"kernel": "k_cont_trace<deposit> (pv_verify_retrace_deposit: Alg. 1, re-trace, deposit)",
+            "bound": "alu", "achieved": dom["achieved_top_s"], "peak": fma["top_s"], "unit": "Top/s",
+            "frac": dom["achieved_top_s"] / fma["top_s"], "traffic": dom["traffic"],
+            "traffic_note": "ncu DRAM bytes per launch, null unless captured on these kernel sources",
+            "duration_ms": dom["duration_ms"],
+            "peak_kind": "measured: k_fma_probe, FP32 fused multiply-adds per second on this GPU",
+            "algorithmic_ops": dom["algorithmic_ops"],
+            "ops_rule": f"{OPS_PER_NODE} per 4-wide node visit ({OPS_PER_SLAB} per slab test), {OPS_PER_TRI} per "
+                        "triangle test, times the counted visits and tests",
+            "hbm": {"achieved": dom["achieved_gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": dom["hbm_frac"],
+                    "algorithmic_bytes": dom["algorithmic_bytes"], "peak_kind": pk_kind},
+            "fma_probe": fma, "hbm_peak": {"value": pk["hbm_gbs"], "unit": "GB/s", "kind": pk_kind},
+            "kernels": head["kernels"], "source_digest": source_digest()}
     # kernels per reuse frame: the pose update with the top level (k_refit_wide), k_verify_box, and k_cont_trace
-    # (Alg. 1, re-trace and deposit); the two memsets of the call are not kernels of the library
+    # (Alg. 1, re-trace and deposit); the call's two memsets are not kernels of the library
     launches_per_frame = 3
-    out = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws, "steps": K, "warmup": W,
-           "ms_per_step": reuse_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roof,
-           "gpu_launches": launches_per_frame * K, "clocks": clocks.summary()}
-    if adjoint:
-        cfg["adjoint"] = adjoint
-    if dm:
-        cfg["distribution_maps"] = dm
-    if splat:
-        cfg["splat"] = splat
+    out = {"metric": METRIC, "value": ws * head["N"] / (reuse_ms * 1e-3), "unit": "paths/s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": reuse_ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+           "roofline": roof, "gpu_launches": launches_per_frame * args.steps, "clocks": head["clocks"]}
     if e2e:
-        e2e["value"] = ws * N / e2e_s
+        e2e["value"] = ws * head["N"] / e2e_s
         e2e.pop("_s")
         out["e2e"] = e2e
     if not args.no_cpu_baseline and ws == 1:
-        out["cpu_baseline"] = cpu_baseline(args.workload, mode, tau, args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(args.workload, MODES[args.mode], cfg["tau"], args.cpu_seconds)
     print(json.dumps(out), flush=True)
 
 
@@ -604,7 +815,7 @@ def time_adjoint(pv, h, P, sc, N, A, K, W, stream, dev):
     dth = torch.zeros_like(th0)
     score = torch.zeros(N, dtype=torch.float32, device=dev)
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
-    fwd, bwd = [], []
+    fwd = []
     for i in range(W + K):
         flush.zero_()
         At.zero_()
@@ -641,7 +852,7 @@ def time_adjoint(pv, h, P, sc, N, A, K, W, stream, dev):
 
 
 # ----------------------------------------------------------------------------- batch of 16 scenes
-def run_batch(args, ws, rank, local):
+def run_batch(args, ws, rank, local, print_line=True):
     """Sixteen uneven scenes per frame: the batched, tuned, graph-replayed
     frame (Alg. 1 fused with the re-trace) against the same scenes driven
     one after another through the single-scene calls (pv_update_dynamic,
@@ -662,27 +873,24 @@ def run_batch(args, ws, rank, local):
     stream = torch.cuda.Stream(device=dev)
     n_total = sum(sc.n_paths for sc in scs)
 
-    def make(copy):
+    def make():
         out = []
         for i, sc in enumerate(scs):
             h = pv.pv_build_scene(sc.verts, sc.tri_object, sc.object_dynamic, sc.object_albedo, sc.lights(1),
                                   sc.max_bounces, sc.diag, object_xform=sc.xforms(1), stream=stream)
             P = pv.Paths.allocate(sc.n_paths, sc.max_bounces, dev)
-            lst = torch.zeros(sc.n_paths, dtype=torch.int32, device=dev)
-            cnt = torch.zeros(1, dtype=torch.int32, device=dev)
             st = pv.new_stats(dev)
             seed = sc.seed + 7919 * rank
             pv.pv_trace_all(h, P, seed, 1, None, stream)
-            out.append((h, P, lst, cnt, st, seed))
+            out.append((h, P, st, seed))
         return out
 
     t0 = time.time()
     with torch.cuda.stream(stream):
-        B = make(1)
+        B = make()
     build_s = time.time() - t0
     # no lists asked for: Alg. 1 runs inside the batched re-trace kernel
-    batch = pv.pv_batch_create([(h, P, None, None, st, seed) for (h, P, lst, cnt, st, seed) in B], mode, tau, 0,
-                               stream)
+    batch = pv.pv_batch_create([(h, P, None, None, st, seed) for (h, P, st, seed) in B], mode, tau, 0, stream)
     frame = 1
 
     # every frame's poses marshalled before the run, so the timed loop holds only the library call
@@ -706,7 +914,7 @@ def run_batch(args, ws, rank, local):
         poses[f] = pv.BatchPoses(len(scs), [sc.xforms(f) for sc in scs], [sc.lights(f) for sc in scs])
     with torch.cuda.stream(stream):
         for x in B:
-            x[4].zero_()                      # counters of the timed frames only
+            x[2].zero_()                      # counters of the timed frames only
     stream.synchronize()
     first = frame + 1
     clocks = Clocks(local)
@@ -723,7 +931,7 @@ def run_batch(args, ws, rank, local):
     batch_ms = e0.elapsed_time(e1) / K
     cfg = pv.pv_batch_get_config(batch)
     step_ms = pv.pv_batch_step_times(batch)
-    stats_b = [pv.stats_dict(x[4]) for x in B]
+    stats_b = [pv.stats_dict(x[2]) for x in B]
     pv.pv_batch_destroy(batch)
     status_b = [pv.pv_read_device_status(x[0]) for x in B]
     for x in B:
@@ -733,9 +941,9 @@ def run_batch(args, ws, rank, local):
 
     # the same frames, scene after scene through the single-scene calls
     with torch.cuda.stream(stream):
-        A = make(0)
+        A = make()
     for f in range(2, first):
-        for sc, (h, P, lst, cnt, st, seed) in zip(scs, A):
+        for sc, (h, P, st, seed) in zip(scs, A):
             pv.pv_update_dynamic(h, sc.xforms(f), sc.lights(f), stream)
             pv.pv_verify_retrace(h, P, mode, tau, 0, seed, f, None, stream)
     stream.synchronize()
@@ -744,7 +952,7 @@ def run_batch(args, ws, rank, local):
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2.record(stream)
     for f in range(first, first + K):
-        for (xf, lt), (h, P, lst, cnt, st, seed) in zip(pre[f], A):
+        for (xf, lt), (h, P, st, seed) in zip(pre[f], A):
             pv.pv_update_dynamic(h, xf, lt, stream)
             pv.pv_verify_retrace(h, P, mode, tau, 0, seed, f, st, stream)
     e3.record(stream)
@@ -756,7 +964,7 @@ def run_batch(args, ws, rank, local):
     e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e4.record(stream)
     for f in range(first + K, first + 2 * K):
-        for (xf, lt), (h, P, lst, cnt, st, seed) in zip(pre[f], A):
+        for (xf, lt), (h, P, st, seed) in zip(pre[f], A):
             pv.pv_update_dynamic(h, xf, lt, stream)
             pv.pv_trace_all(h, P, seed, f, None, stream)
     e5.record(stream)
@@ -765,33 +973,31 @@ def run_batch(args, ws, rank, local):
     status_a = [pv.pv_read_device_status(x[0]) for x in A]
     for x in A:
         pv.pv_destroy_scene(x[0])
+    del A
+    torch.cuda.empty_cache()
     if rank != 0:
-        return
+        return None
     agg = lambda key, rows: float(sum(r[key] for r in rows)) / K
-    pk, pk_kind = peaks()
-    ops = OPS_PER_NODE * agg("node_visits", stats_b) + OPS_PER_TRI * agg("tri_tests", stats_b)
-    ops_peak = SM_COUNT * FP32_LANES * pk.get("sm_max_mhz", 2070.0) * 1e6
-    achieved = ops / (batch_ms * 1e-3)
+    summary = {"workload": f"batch16: {WORKLOADS['batch16']}", "paths": n_total, "mode": args.mode, "tau": tau,
+               "frames_timed": K, "l2": "inputs larger than L2", "batch_frame_ms": batch_ms,
+               "value_paths_per_s": ws * n_total / (batch_ms * 1e-3),
+               "batch_frame_wall_ms": wall * 1e3, "sequential_single_scene_ms": seq_ms,
+               "speedup_vs_sequential": seq_ms / batch_ms, "trace_all_ms": trace_ms,
+               "speedup_vs_trace_all": trace_ms / batch_ms, "tuned_config": cfg, "tune_frames": tune_frames,
+               "tuned_step_ms": dict(zip(["update", "verify", "continue", "compact", "retrace"], step_ms)),
+               "listed_per_frame": agg("n_listed", stats_b), "rays_per_frame": agg("trace_rays", stats_b)
+               + agg("cont_rays", stats_b) + agg("vis_rays", stats_b),
+               "scene_build_s": build_s, "device_status": status_b + status_a, "clocks": clocks.summary()}
+    if not print_line:
+        return summary
     out = {"metric": METRIC, "value": ws * n_total / (batch_ms * 1e-3), "unit": "paths/s", "n_gpus": ws, "steps": K,
            "warmup": W, "ms_per_step": batch_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"batch16: {WORKLOADS['batch16']}", "paths": n_total, "mode": args.mode, "tau": tau,
-                      "frames_timed": K, "l2": "inputs larger than L2", "batch_frame_ms": batch_ms,
-                      "batch_frame_wall_ms": wall * 1e3, "sequential_single_scene_ms": seq_ms,
-                      "speedup_vs_sequential": seq_ms / batch_ms, "trace_all_ms": trace_ms,
-                      "speedup_vs_trace_all": trace_ms / batch_ms, "tuned_config": cfg, "tune_frames": tune_frames,
-                      "tuned_step_ms": dict(zip(["update", "verify", "continue", "compact", "retrace"], step_ms)),
-                      "listed_per_frame": agg("n_listed", stats_b), "rays_per_frame": agg("trace_rays", stats_b)
-                      + agg("cont_rays", stats_b) + agg("vis_rays", stats_b),
-                      "scene_build_s": build_s, "device_status": status_b + status_a},
-           "roofline": {"kernel": "whole batched frame (traversal-bound)", "bound": "alu",
-                        "achieved": achieved / 1e12, "peak": ops_peak / 1e12, "unit": "Top/s",
-                        "frac": achieved / ops_peak, "traffic": None,
-                        "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x max SM clock"},
-           # graph kernel nodes per frame: prologue, transform + wide refit, poses + top level, verify,
-           # compaction, Alg. 1 + re-trace
-           "gpu_launches": 6 * K, "clocks": clocks.summary()}
+           "dtype": "f32", "data": "synthetic", "config": summary,
+           # graph kernel nodes per frame: prologue, transform + wide refit with the top levels, verify, Alg. 1 +
+           # re-trace
+           "gpu_launches": 4 * K, "clocks": clocks.summary()}
     print(json.dumps(out), flush=True)
+    return summary
 
 
 # ----------------------------------------------------------------------------- oracle
@@ -813,22 +1019,33 @@ def _oracle_frame(o, sc, p, mode, tau, f):
     oracle.deposit(p, 1024, 1024, sc.atlas_rect)
 
 
+CPU_SAMPLE = {"villa": 200, "city": 4000, "tiny_box": 10000}
+
+
 def cpu_baseline(workload, mode, tau, seconds):
-    """The oracle as it stands, on this host's cores, on a bounded sample."""
+    """The oracle as it stands, on this host's cores, on a bounded sample:
+    the sample's paths traced at frame 1 (untimed), then frames 2..30 run in
+    order with frames 2, 15 and 30 timed (fewer when the time bound ends the
+    run first); the full frame's time is extrapolated from the sample."""
     import oracle
-    n_sample = {"city": 4000, "villa": 600, "tiny_box": 10000}[workload]
+    n_sample = CPU_SAMPLE[workload]
     sc, o, p = _oracle_sample(workload, n_sample)
-    t = time.perf_counter()
-    frames = 0
-    f = 1
-    while time.perf_counter() - t < seconds and frames < 60:
-        f += 1
+    timed = {2, 15, 30}
+    ts = {}
+    t_all = time.perf_counter()
+    for f in range(2, 31):
+        t = time.perf_counter()
         _oracle_frame(o, sc, p, mode, tau, f)
-        frames += 1
-    dt = time.perf_counter() - t
-    return {"value": n_sample * frames / dt, "unit": "paths/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{n_sample} seeded paths of the {workload} workload, frames 2..{f} "
-                      f"(verify + retrace + deposit, FP64 brute force over all {sc.n_tris} triangles)"}
+        if f in timed:
+            ts[f] = time.perf_counter() - t
+        if time.perf_counter() - t_all > seconds and ts:
+            break
+    dt = float(np.mean(list(ts.values())))
+    return {"value": n_sample / dt, "unit": "paths/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n_sample} seeded paths of the {workload} workload (verify + retrace + deposit, FP64 brute "
+                      f"force over all {sc.n_tris} triangles), frames {sorted(ts)} timed of the run from frame 2",
+            "frame_s": {str(k): v for k, v in sorted(ts.items())},
+            "full_frame_s_extrapolated": sc.n_paths * dt / n_sample}
 
 
 def run_reference(args, ws, rank):

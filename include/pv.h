@@ -251,7 +251,7 @@ int pv_verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params
  * the paths this frame does not touch (neither re-traced nor looked at by
  * Alg. 1) are deposited by lanes that have no rays left to trace.  The atlas
  * is cleared first and follows pv_deposit's rules.  Stage timing as
- * pv_verify_retrace (stage [2] then includes the deposit).  PV_ERR_ARG for a
+ * pv_verify_retrace (stage [3] then includes the deposit).  PV_ERR_ARG for a
  * null or invalid atlas, otherwise errors as pv_verify_paths. */
 int pv_verify_retrace_deposit(pv_scene* s, const pv_paths* paths, const pv_verify_params* params,
                               const pv_atlas* atlas, pv_frame_stats* d_stats, void* stream);
@@ -272,19 +272,23 @@ int pv_verify_retrace_deposit_delta(pv_scene* s, const pv_paths* paths, const pv
                                     const pv_atlas* atlas, pv_frame_stats* d_stats, void* stream);
 
 /* Stage timing of pv_verify_retrace and the two deposit forms (no paper
- * counterpart).  With n > 0, each later call records four CUDA events on its
- * stream -- at its start, after k_verify, before its re-trace kernel, at its
- * end -- keeping the last n calls in a ring; n = 0 turns it off.  Creates (and destroys) events and
- * synchronises with the scene's last stream, so call it outside any timed or
- * captured region.  PV_ERR_ARG for n > 4096. */
+ * counterpart).  With n > 0, each later call records five CUDA events on its
+ * stream -- at its start, after its clears (atlas, counters), after k_verify,
+ * before its re-trace kernel, at its end -- keeping the last n calls in a
+ * ring; n = 0 turns it off.  The events between the kernels also keep the
+ * re-trace kernel from starting before k_verify has ended, so a timed call
+ * takes a little longer than an untimed one.  Creates (and destroys) events
+ * and synchronises with the scene's last stream, so call it outside any
+ * timed or captured region.  PV_ERR_ARG for n > 4096. */
 int pv_stage_timing(pv_scene* s, uint32_t n);
 
-/* Milliseconds of the recorded calls, oldest first, four per call (``ms``
- * holds 4 n floats): [0] verification (k_verify), [1] what runs between it
- * and the re-trace kernel (nothing with fusion, where k_verify appends the
- * re-trace list itself; otherwise the continuation, the distribution-map
- * steps and the compaction), [2] the re-trace kernel (with fusion: Alg. 1,
- * the re-trace and, with an atlas, the deposit), [3] the
+/* Milliseconds of the recorded calls, oldest first, five per call (``ms``
+ * holds 5 n floats): [0] the clears before verification (the atlas of the
+ * deposit forms, the work counters), [1] verification (k_verify), [2] what
+ * runs between it and the re-trace kernel (nothing with fusion, where
+ * k_verify appends the re-trace list itself; otherwise the continuation, the
+ * distribution-map steps and the compaction), [3] the re-trace kernel (with
+ * fusion: Alg. 1, the re-trace and, with an atlas, the deposit), [4] the
  * whole call.  *count receives the number of calls recorded (at most n).
  * Waits for the events. */
 int pv_stage_times(pv_scene* s, float* ms, uint32_t* count);
@@ -311,8 +315,10 @@ int pv_compact_replace(pv_scene* s, const pv_paths* paths, uint32_t* d_list, uin
  * n returns PV_ERR_LIMIT.  The first call on a device looks up the array's
  * device address (make that first call before any stream capture).  All calls
  * share the array, so calls that overlap on the GPU race; serialise them (one
- * stream, or events).  Returns PV_ERR_ARG for null pointers.  Device-side
- * errors of this call are not recorded. */
+ * stream, or events).  Returns PV_ERR_ARG for null pointers.  No scene
+ * holds a status word for this call: if a tile's look-back ever waits past
+ * its spin cap (a predecessor tile never published its sum), the call writes
+ * 0xFFFFFFFF to *d_count, and the list is then incomplete. */
 #define PV_STATIC_COMPACT_MAX_PATHS (1u << 26)
 int pv_compact_replace_static(const uint32_t* d_info, uint32_t n, uint32_t* d_list, uint32_t* d_count,
                               void* stream);
@@ -376,6 +382,16 @@ int pv_adjoint_deposit(pv_scene* s, const pv_paths* paths, const float* d_theta,
  * inside pv_verify_paths).  PV_ERR_ARG for null pointers. */
 int pv_budget_list(pv_scene* s, const uint32_t* d_list, const uint32_t* d_count, const float* d_score,
                    uint32_t budget, uint32_t* d_out, uint32_t* d_out_count, void* stream);
+
+/* FP32 fused multiply-add probe (no paper counterpart): the measured
+ * denominator of the traversal kernels' ALU roofline.  Enqueues one kernel of
+ * ``blocks`` blocks of 256 threads; every thread runs 8 independent chains of
+ * 16 * ``iters`` dependent fmaf, so the FMA pipe bounds it.  *fmas (host)
+ * receives the number of fused multiply-adds the kernel executes; time it
+ * with events on ``stream``.  d_sink: device memory of ``blocks`` floats,
+ * written only in a case that the kernel's inputs never reach.  PV_ERR_ARG
+ * for zero blocks or iterations or a null pointer. */
+int pv_fma_probe(uint32_t blocks, uint32_t iters, float* d_sink, uint64_t* fmas, void* stream);
 
 /* Cap the BVH node visits of every ray query (0 restores the default, which
  * no query on a valid tree reaches).  A query that reaches the cap stops,

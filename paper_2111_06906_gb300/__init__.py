@@ -37,7 +37,7 @@ EXPORTS = ["pv_build_scene", "pv_update_dynamic", "pv_verify_paths", "pv_retrace
            "pv_model_deposit", "pv_adjoint_deposit", "pv_budget_list", "pv_batch_create", "pv_batch_frame",
            "pv_batch_autotune", "pv_batch_tuning", "pv_batch_set_config", "pv_batch_get_config", "pv_batch_step_times",
            "pv_batch_destroy", "pv_distribution_map_cells", "pv_read_distribution_map", "pv_splat_workspace_bytes",
-           "pv_splat"]
+           "pv_splat", "pv_fma_probe"]
 PV_BATCH_MAX_SCENES = 32
 PV_STATIC_COMPACT_MAX_PATHS = 1 << 26
 
@@ -153,6 +153,7 @@ def load():
         L.pv_splat_workspace_bytes.restype = C.c_size_t
         L.pv_splat.argtypes = [P, C.POINTER(PvPaths), C.POINTER(PvCamera), C.c_float, P, P, C.c_size_t, P]
         L.pv_read_distribution_map.argtypes = [P, C.c_uint32, P]
+        L.pv_fma_probe.argtypes = [C.c_uint32, C.c_uint32, P, P, P]
         L.pv_batch_destroy.restype = None
         L.pv_status_string.argtypes = [C.c_int]
         L.pv_status_string.restype = C.c_char_p
@@ -288,12 +289,24 @@ def pv_stage_timing(scene, n: int) -> None:
     _check("pv_stage_timing", load().pv_stage_timing(scene, int(n)))
 
 
+STAGES = ["clears", "k_verify", "between", "retrace_kernel", "call"]
+
+
 def pv_stage_times(scene, n: int) -> np.ndarray:
-    """[calls, 4] milliseconds of the last recorded pv_verify_retrace calls (see include/pv.h)."""
-    ms = np.zeros(4 * max(int(n), 1), np.float32)
+    """[calls, 5] milliseconds of the last recorded pv_verify_retrace calls, columns as ``STAGES``
+    (see include/pv.h)."""
+    E = len(STAGES)
+    ms = np.zeros(E * max(int(n), 1), np.float32)
     cnt = C.c_uint32(0)
     _check("pv_stage_times", load().pv_stage_times(scene, ms.ctypes.data_as(C.c_void_p), C.byref(cnt)))
-    return ms[:4 * cnt.value].reshape(cnt.value, 4)
+    return ms[:E * cnt.value].reshape(cnt.value, E)
+
+
+def pv_fma_probe(blocks: int, iters: int, d_sink, stream=None) -> int:
+    """Enqueue the FP32 fused multiply-add probe; returns how many FMAs it executes."""
+    fmas = C.c_uint64(0)
+    _check("pv_fma_probe", load().pv_fma_probe(int(blocks), int(iters), _ptr(d_sink), C.byref(fmas), _stream(stream)))
+    return int(fmas.value)
 
 
 def pv_trace_all(scene, paths: Paths, seed: int, frame: int, d_stats=None, stream=None) -> None:

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpv.so")
-SOURCES = ["scene.cu", "bvh.cu", "verify.cu", "compact.cu", "trace.cu", "deposit.cu", "adjoint.cu", "batch.cu", "dm.cu", "splat.cu"]
+SOURCES = ["scene.cu", "bvh.cu", "verify.cu", "compact.cu", "trace.cu", "deposit.cu", "adjoint.cu", "batch.cu", "dm.cu", "splat.cu", "probe.cu"]
 HEADERS = ["pv_device.cuh", "pv_scene.h", "verify_core.cuh", "trace_core.cuh", "compact_core.cuh",
            "update_core.cuh", "dm_core.cuh", "deposit_core.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

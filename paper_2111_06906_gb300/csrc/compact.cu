@@ -7,14 +7,16 @@ using namespace pvk;
 
 namespace {
 
+// ``failed``: null, or a word cleared before the launch that a tile giving
+// up on its look-back sets (the count then reads kCompactFailed).
 __global__ void __launch_bounds__(pvh::kCompactThreads) k_compact(const uint32_t* info, uint32_t n, uint32_t* list,
                                                                     uint32_t* count, unsigned long long* tiles,
                                                                     uint32_t* ticket, uint32_t n_tiles, int* status,
-                                                                    uint32_t* stat_listed) {
+                                                                    uint32_t* stat_listed, uint32_t* failed) {
   __shared__ CompactSmem sm;
   if (threadIdx.x == 0) sm.tile = atomicAdd(ticket, 1u);
   __syncthreads();
-  compact_tile(info, n, list, count, tiles, sm.tile, n_tiles, status, stat_listed, sm);
+  compact_tile(info, n, list, count, tiles, sm.tile, n_tiles, status, stat_listed, sm, failed);
 }
 
 }  // namespace
@@ -31,7 +33,7 @@ void launch_compact(pv_scene* s, const uint32_t* info, uint32_t n, uint32_t* lis
   cudaMemsetAsync(s->ws_tiles, 0, (size_t)n_tiles * sizeof(uint64_t), st);
   cudaMemsetAsync(s->ws_ctr + CTR_TILE, 0, sizeof(uint32_t), st);
   k_compact<<<n_tiles, kCompactThreads, 0, st>>>(info, n, list, count, reinterpret_cast<unsigned long long*>(s->ws_tiles),
-                                                 s->ws_ctr + CTR_TILE, n_tiles, s->status, stats_listed);
+                                                 s->ws_ctr + CTR_TILE, n_tiles, s->status, stats_listed, nullptr);
 }
 
 }  // namespace pvh
@@ -59,7 +61,8 @@ namespace {
 
 constexpr uint32_t kStaticTiles = (PV_STATIC_COMPACT_MAX_PATHS + pvh::kTile - 1) / pvh::kTile;
 
-// tile states [0, kStaticTiles), then the tile ticket (low 32 bits of the last word)
+// tile states [0, kStaticTiles), then the last word: the tile ticket (low 32
+// bits) and the give-up flag (high 32 bits)
 static __device__ __align__(256) unsigned long long g_compact_scratch[kStaticTiles + 1];
 
 std::mutex g_scratch_mutex;
@@ -94,11 +97,12 @@ extern "C" int pv_compact_replace_static(const uint32_t* d_info, uint32_t n, uin
   const uint32_t n_tiles = (n + pvh::kTile - 1) / pvh::kTile;
   unsigned long long* tiles = static_cast<unsigned long long*>(base);
   uint32_t* ticket = reinterpret_cast<uint32_t*>(tiles + kStaticTiles);
-  // the previous call's tile states and ticket are still in the array: clear them
+  uint32_t* failed = ticket + 1;
+  // the previous call's tile states, ticket and flag are still in the array: clear them
   if (cudaMemsetAsync(tiles, 0, (size_t)n_tiles * sizeof(unsigned long long), st) != cudaSuccess ||
-      cudaMemsetAsync(ticket, 0, sizeof(uint32_t), st) != cudaSuccess)
+      cudaMemsetAsync(ticket, 0, 2 * sizeof(uint32_t), st) != cudaSuccess)
     return PV_ERR_CUDA;
   k_compact<<<n_tiles, pvh::kCompactThreads, 0, st>>>(d_info, n, d_list, d_count, tiles, ticket, n_tiles, nullptr,
-                                                      nullptr);
+                                                      nullptr, failed);
   return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
 }

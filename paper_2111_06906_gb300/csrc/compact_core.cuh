@@ -24,9 +24,18 @@ struct CompactSmem {
 // called by every thread of a kCompactThreads block.  Tiles of one array must
 // take their indices in increasing order of start (an atomic ticket), so
 // every tile a look-back waits on has already started.
+//
+// A look-back that waits longer than kSpinCap for a predecessor gives up and
+// publishes a partial prefix.  It records PV_ERR_ITER_CAP in ``status``, and
+// when ``failed`` is given it sets that word before publishing.  The last tile
+// reads ``failed`` after its own look-back (every tile above a stuck one can
+// only complete through a tile that gave up, whose flag it then sees) and
+// writes kCompactFailed as the count instead of a wrong one.
+constexpr uint32_t kCompactFailed = 0xFFFFFFFFu;
+
 __device__ __forceinline__ void compact_tile(const uint32_t* info, uint32_t n, uint32_t* list, uint32_t* count,
                                              unsigned long long* tiles, uint32_t tile, uint32_t n_tiles, int* status,
-                                             uint32_t* stat_listed, CompactSmem& sm) {
+                                             uint32_t* stat_listed, CompactSmem& sm, uint32_t* failed = nullptr) {
   constexpr int kWarps = pvh::kCompactThreads / 32;
   uint32_t& s_prefix = sm.prefix;
   uint32_t* const s_warp = sm.warp;
@@ -82,6 +91,10 @@ __device__ __forceinline__ void compact_tile(const uint32_t* info, uint32_t n, u
         if (f == 0ull) {
           if (++spins > kSpinCap) {                // predecessor never published: give up, flag it
             record_error(status, PV_ERR_ITER_CAP);
+            if (failed) {
+              atomicExch(failed, 1u);
+              __threadfence();                     // the flag is visible before the partial prefix
+            }
             break;
           }
           continue;
@@ -99,8 +112,13 @@ __device__ __forceinline__ void compact_tile(const uint32_t* info, uint32_t n, u
   for (int j = 0; j < pvh::kCompactItems; ++j)
     if ((flags >> j) & 1u) list[pos++] = base + j;
   if (tile == n_tiles - 1 && threadIdx.x == 0) {
-    *count = s_prefix + tile_total;
-    if (stat_listed) atomicAdd(stat_listed, s_prefix + tile_total);
+    bool gave_up = false;
+    if (failed) {
+      __threadfence();
+      gave_up = atomicAdd(failed, 0u) != 0u;
+    }
+    *count = gave_up ? kCompactFailed : s_prefix + tile_total;
+    if (stat_listed && !gave_up) atomicAdd(stat_listed, s_prefix + tile_total);
   }
 }
 

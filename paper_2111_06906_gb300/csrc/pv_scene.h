@@ -102,7 +102,7 @@ struct pv_scene {
 
   int verify_blocks = 0, trace_blocks = 0, cont_blocks = 0, cont_trace_blocks = 0, cont_trace_dep_blocks = 0,
       cont_trace_delta_blocks = 0;
-  // stage timing of pv_verify_retrace: a ring of stage_n calls, four events each
+  // stage timing of pv_verify_retrace: a ring of stage_n calls, pvh::kStageEvents events each
   std::vector<cudaEvent_t> stage_ev;
   uint32_t stage_n = 0, stage_next = 0, stage_count = 0;
   uint32_t visit_limit = 0;          // 0 = default cap (see view())
@@ -115,6 +115,7 @@ struct ContArgs;                     // verify_core.cuh
 
 namespace pvh {
 
+constexpr int kStageEvents = 5;      // events per timed pv_verify_retrace call
 constexpr int kTraceThreads = 128;
 constexpr int kVerifyThreads = 256;
 constexpr int kCompactThreads = 256;

@@ -156,15 +156,17 @@ ContArgs cont_args(pv_scene* s, const pv_paths* paths, const pv_verify_params* p
 
 // Work counters reset, DM_C of moved lights with a map cleared, then k_verify
 // (Sec. 3.1 + 3.2).  ``cont``: Alg. 1 has paths to look at this frame.
+template <typename OnCleared = void (*)()>
 int launch_verify(pv_scene* s, const pv_paths* paths, const pv_verify_params* params, pv_frame_stats* d_stats,
                   const SceneView& sv, const FrameLights& L, cudaStream_t st, bool& cont, uint8_t* touched = nullptr,
-                  bool direct_list = false, const pv_atlas* sub = nullptr) {
+                  bool direct_list = false, const pv_atlas* sub = nullptr, OnCleared on_cleared = [] {}) {
   const uint32_t n = paths->n;
   if (cudaMemsetAsync(s->ws_ctr, 0, 16 * sizeof(uint32_t), st) != cudaSuccess) return PV_ERR_CUDA;
   for (uint32_t l = 0; l < s->n_lights; ++l)       // DM_C of moved lights with a map is counted afresh
     if (L.dm[l].dims && ((L.moved_mask >> l) & 1u))
       if (cudaMemsetAsync(L.dm[l].dmc, 0, (size_t)L.dm[l].cells * sizeof(uint32_t), st) != cudaSuccess)
         return PV_ERR_CUDA;
+  on_cleared();
   VerifyArgs A;
   A.n = n;
   A.info = paths->info;
@@ -237,7 +239,7 @@ int verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params* p
   s->last_stream = st;
   const SceneView sv = pvh::view(s);
   const FrameLights L = pvh::frame_lights(s);
-  cudaEvent_t* ev = s->stage_n ? &s->stage_ev[4 * s->stage_next] : nullptr;
+  cudaEvent_t* ev = s->stage_n ? &s->stage_ev[pvh::kStageEvents * s->stage_next] : nullptr;
   auto mark = [&](int k) {
     if (ev) cudaEventRecord(ev[k], st);
   };
@@ -253,27 +255,27 @@ int verify_retrace(pv_scene* s, const pv_paths* paths, const pv_verify_params* p
     return PV_ERR_CUDA;
   bool cont = false;
   if ((rc = launch_verify(s, paths, params, d_stats, sv, L, st, cont, fuse_deposit ? s->ws_touched : nullptr, fused,
-                          delta ? atlas : nullptr)) != PV_OK)
+                          delta ? atlas : nullptr, [&] { mark(1); })) != PV_OK)
     return rc;
-  mark(1);
+  mark(2);
   const ContArgs C = cont_args(s, paths, params, d_stats);
   uint32_t* const list = s->ws_list;
   uint32_t* const count = s->ws_ctr + pvh::CTR_LIST;
   uint32_t* const listed = d_stats ? &d_stats->n_listed : nullptr;
   if (fused) {
     // k_verify appended the paths it marked; then Alg. 1, the re-trace (and the deposit) in one kernel
-    mark(2);
+    mark(3);
     pvh::launch_cont_trace(s, paths, C, list, count, params->seed, params->frame, d_stats,
                            fuse_deposit ? atlas : nullptr, s->ws_touched, delta, st);
   } else {
     if (cont) launch_continue(s, sv, C, st);
     if (s->has_dm && (rc = pvh::dm_frame(s, paths, L, params, d_stats, st)) != PV_OK) return rc;
     pvh::launch_compact(s, paths->info, paths->n, list, count, listed, st);
-    mark(2);
+    mark(3);
     pvh::launch_trace(s, paths, list, count, params->seed, params->frame, d_stats, st);
     if (atlas) pvh::launch_deposit(s, paths, atlas, st);
   }
-  mark(3);
+  mark(4);
   if (ev) {
     s->stage_next = (s->stage_next + 1) % s->stage_n;
     s->stage_count = std::min(s->stage_count + 1, s->stage_n);
@@ -305,7 +307,7 @@ extern "C" int pv_stage_timing(pv_scene* s, uint32_t n) {
   if (s->last_stream && cudaStreamSynchronize(s->last_stream) != cudaSuccess) return PV_ERR_CUDA;
   for (cudaEvent_t e : s->stage_ev)
     if (e) cudaEventDestroy(e);
-  s->stage_ev.assign(4 * (size_t)n, nullptr);
+  s->stage_ev.assign(pvh::kStageEvents * (size_t)n, nullptr);
   s->stage_n = s->stage_next = s->stage_count = 0;
   for (auto& e : s->stage_ev)
     if (cudaEventCreate(&e) != cudaSuccess) {
@@ -320,12 +322,13 @@ extern "C" int pv_stage_times(pv_scene* s, float* ms, uint32_t* count) {
   if (!s || !ms || !count) return PV_ERR_ARG;
   const uint32_t c = s->stage_count;
   for (uint32_t i = 0; i < c; ++i) {
+    constexpr int E = pvh::kStageEvents;
     const uint32_t k = (s->stage_next + s->stage_n - c + i) % s->stage_n;
-    cudaEvent_t* ev = &s->stage_ev[4 * k];
-    if (cudaEventSynchronize(ev[3]) != cudaSuccess) return PV_ERR_CUDA;
-    for (int j = 0; j < 3; ++j)
-      if (cudaEventElapsedTime(ms + 4 * i + j, ev[j], ev[j + 1]) != cudaSuccess) return PV_ERR_CUDA;
-    if (cudaEventElapsedTime(ms + 4 * i + 3, ev[0], ev[3]) != cudaSuccess) return PV_ERR_CUDA;
+    cudaEvent_t* ev = &s->stage_ev[E * k];
+    if (cudaEventSynchronize(ev[E - 1]) != cudaSuccess) return PV_ERR_CUDA;
+    for (int j = 0; j < E - 1; ++j)
+      if (cudaEventElapsedTime(ms + E * i + j, ev[j], ev[j + 1]) != cudaSuccess) return PV_ERR_CUDA;
+    if (cudaEventElapsedTime(ms + E * i + E - 1, ev[0], ev[E - 1]) != cudaSuccess) return PV_ERR_CUDA;
   }
   *count = c;
   return PV_OK;

@@ -349,12 +349,20 @@ def city(n_paths: int = 1_000_000, seed: int = 2, n_boxes: int = 16_666) -> Scen
                  _xform_fn=xf, _light_fn=lf)
 
 
-def villa(n_paths_per_light: int = 1_000_000, seed: int = 3, n_static: int = 2_000_000) -> Scene:
+def villa(n_paths_per_light: int = 1_000_000, seed: int = 3, n_static: int = 2_000_000,
+          moving_light: str = "torch") -> Scene:
     """Villa-shaped interior: 4x3 rooms of 5x5x3 m with 1x2.1 m doors, exactly
     ``n_static`` static triangles (tessellated shell, detailed furniture boxes,
     30 % small clutter), 10 dynamic tori (5000 triangles, translating with
     amplitude 1 m and yawing 2 deg/frame), a ceiling point light, a static
-    0.5x0.5 m ceiling area light and a moving, tilting 0.3x0.3 m torch."""
+    0.5x0.5 m ceiling area light and a moving, tilting 0.3x0.3 m torch.
+
+    ``moving_light = "point"``: the torch stays at its first pose and the
+    ceiling point light moves instead, 0.05 m/frame along a 1 m radius loop
+    under the ceiling of its room (the case whose origin update needs a
+    visibility ray per path)."""
+    if moving_light not in ("torch", "point"):
+        raise ValueError("villa: moving_light is 'torch' or 'point'")
     st = Stream(seed, 1)
     b = _Builder()
     NX, NZ, RS, H = 4, 3, 5.0, 3.0
@@ -478,6 +486,11 @@ def villa(n_paths_per_light: int = 1_000_000, seed: int = 3, n_static: int = 2_0
 
     def lf(frame: int) -> List[Light]:
         f = frame - 1
+        fp = f if moving_light == "point" else 0
+        ang_p = 0.05 * fp                # the ceiling light's loop: 0.05 m/frame, radius 1 m
+        p_pos = (2.5 + math.cos(ang_p) - 1.0, 2.9, 2.5 + math.sin(ang_p))
+        if moving_light == "point":
+            f = 0
         ang = 0.05 * f / 1.0            # 0.05 m/frame along a 1 m radius loop
         cxk, czk = 3 * RS + 2.5, 2 * RS + 2.5
         pos = (cxk + math.cos(ang), 2.5, czk + math.sin(ang))    # above the furniture (<= 2.2 m)
@@ -486,7 +499,7 @@ def villa(n_paths_per_light: int = 1_000_000, seed: int = 3, n_static: int = 2_0
         nrm = (0.0, -math.cos(tilt), math.sin(tilt))
         tan = (1.0, 0.0, 0.0)
         return [
-            Light(LIGHT_POINT, (2.5, 2.9, 2.5), power=P, n_paths=n_paths_per_light),
+            Light(LIGHT_POINT, p_pos, power=P, n_paths=n_paths_per_light),
             Light(LIGHT_RECT, (2 * RS + 2.5, 2.98, RS + 2.5), (0.0, -1.0, 0.0), (1.0, 0.0, 0.0),
                   (0.5, 0.5), P, n_paths_per_light),
             Light(LIGHT_RECT, pos, nrm, tan, (0.3, 0.3), P, n_paths_per_light),

@@ -126,6 +126,12 @@ def test_host_argument_errors_need_no_gpu(lib):
     assert lib.pv_deposit(None, None, None, None) == -1
     assert lib.pv_read_device_status(None) == -1
     assert lib.pv_set_traversal_limit(None, 1) == -1
+    assert lib.pv_stage_timing(None, 1) == -1
+    fm = C.c_uint64(0)
+    sink = C.c_void_p(16)
+    assert lib.pv_fma_probe(0, 1, sink, C.byref(fm), None) == -1
+    assert lib.pv_fma_probe(1, 0, sink, C.byref(fm), None) == -1
+    assert lib.pv_fma_probe(1, 1, None, C.byref(fm), None) == -1
     lib.pv_destroy_scene(None)
     b = C.c_void_p()
     prm = pv.PvVerifyParams(2, 0.01, 0)

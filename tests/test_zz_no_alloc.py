@@ -30,7 +30,8 @@ def test_rejects_sizes_beyond_the_limit():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("n", [3 * 4096 + 77, 100_003])
+@pytest.mark.parametrize("n", [3 * 4096 + 77, 100_003, pv.PV_STATIC_COMPACT_MAX_PATHS - 1,
+                               pv.PV_STATIC_COMPACT_MAX_PATHS])
 def test_matches_scene_compaction_on_two_calls_in_a_row(n):
     import torch
     from paper_2111_06906_gb300 import build
@@ -58,5 +59,9 @@ def test_matches_scene_compaction_on_two_calls_in_a_row(n):
         c = int(ref_cnt.item())
         assert int(got_cnt.item()) == c == int(bits.sum())
         assert torch.equal(got_list[:c], ref_list[:c]), f"call {call}"
+        if n >= pv.PV_STATIC_COMPACT_MAX_PATHS - 1:    # the array's last tile and its ticket word are in use
+            assert np.array_equal(got_list[:c].cpu().numpy(), np.flatnonzero(bits).astype(np.int32))
     assert pv.pv_read_device_status(h) == 0
     pv.pv_destroy_scene(h)
+    del P
+    torch.cuda.empty_cache()
