@@ -207,24 +207,29 @@ def scene_for(name, **kw):
     return scenes.by_name(name, **kw)
 
 
-def fma_peak(pv, torch, dev, sms, stream):
+def fma_peak(pv, torch, dev, sms, stream, local):
     """The FP32 fused multiply-add rate of this GPU: the library's probe kernel
-    over 8 blocks of 256 threads per SM, median of 7 timed launches."""
+    over 8 blocks of 256 threads per SM, median of 10 timed launches after 40
+    untimed ones, SM clock sampled meanwhile."""
     blocks = 8 * sms
     sink = torch.zeros(blocks, dtype=torch.float32, device=dev)
     ms, fmas = [], 0
-    for i in range(10):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        fmas = pv.pv_fma_probe(blocks, 512, sink)
-        e1.record(stream)
-        if i >= 3:
-            ms.append((e0, e1))
-    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    with clocks:
+        for i in range(50):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fmas = pv.pv_fma_probe(blocks, 512, sink)
+            e1.record(stream)
+            if i >= 40:
+                ms.append((e0, e1))
+        torch.cuda.synchronize()
     t = float(np.median([a.elapsed_time(b) for a, b in ms]))
     rate = fmas / (t * 1e-3)
+    ck = clocks.summary()
     return {"kernel": "k_fma_probe", "top_s": rate / 1e12, "fmas_per_launch": fmas, "ms": t, "blocks": blocks,
-            "threads_per_block": 256, "sm_count": sms,
+            "threads_per_block": 256, "sm_count": sms, "sm_mhz": ck.get("sm_mhz"),
+            "fma_per_sm_per_clock": rate / (sms * ck["sm_mhz"] * 1e6) if ck.get("sm_mhz") else None,
             "note": "FP32 fused multiply-adds per second (one FMA = one op), 8 independent chains per thread"}
 
 
@@ -670,7 +675,7 @@ def run_ours(args, ws, rank, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    fma = fma_peak(pv, torch, dev, sms, stream)
+    fma = fma_peak(pv, torch, dev, sms, stream, local)
     head = measure(pv, torch, scene_for(args.workload), args, dev, stream, ws, rank, local, fma, full=True)
     secondary = {}
     if args.workload == "villa" and not args.no_secondary:

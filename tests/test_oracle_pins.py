@@ -336,6 +336,45 @@ def test_area_light_in_plane_translation_closed_form():
     assert np.array_equal(r.origin, p.origin)
 
 
+def test_area_light_failed_update_keeps_origin():
+    """Sec. 3.1: DM_C counts only the paths "successfully updated"; the others
+    are invalidated during the origin update.  A path whose update fails keeps
+    the origin it had (its info word carries the decision; the re-trace emits
+    it afresh), and a path whose update succeeds gets the point where its
+    stored direction meets the new light plane, inside the rectangle."""
+    N = 20_000
+    a = math.radians(6.0)
+    # lifted by 0.4 m, moved 0.3 m in x and tilted: some paths leave the rectangle, some fail Eq. 2 at tau = 2 %
+    sc = kit.rect_light_over_floor(N, shift=lambda f: (0.3 * (f - 1), 0.4 * (f - 1), 0.0),
+                                   normal=lambda f: (0.0, -1.0, 0.0) if f == 1 else (0.0, -math.cos(a), math.sin(a)))
+    o, p = _traced(sc)
+    o.set_frames(1, 2)
+    for tau in (math.inf, 0.02):
+        q = p.copy()
+        _, st = o.verify(q, 2, tau)
+        failed = ((q.info & oracle.INFO_REPLACE) != 0) & (q.start == 0)
+        kept = ~failed & (p.nseg > 0)
+        assert 0.05 * N < failed.sum() < 0.95 * N
+        assert np.array_equal(q.origin[failed], p.origin[failed])
+        L2 = sc.lights(2)[0]
+        c = np.array(L2.pos, np.float64)
+        n = np.array(L2.normal, np.float64)
+        t = np.array(L2.tangent, np.float64)
+        b = np.cross(n, t)
+        org = q.origin[kept].astype(np.float64)
+        assert np.abs((org - c) @ n).max() < 1e-5            # on the new plane
+        assert (np.abs((org - c) @ t) <= 0.5 + 1e-5).all() and (np.abs((org - c) @ b) <= 0.5 + 1e-5).all()
+        x1 = p.photons[kept, 0, :3].astype(np.float64)
+        d_old = x1 - p.origin[kept]
+        d_new = x1 - org
+        cosang = (d_old * d_new).sum(1) / np.linalg.norm(d_old, axis=1) / np.linalg.norm(d_new, axis=1)
+        assert (cosang > 1.0 - 1e-9).all()                     # the stored direction is kept
+        if tau == math.inf:
+            inf_failed = failed.sum()
+        else:
+            assert st["energy_tests"] > 0 and failed.sum() > inf_failed
+
+
 def test_area_light_flip_and_tilt():
     N = 20_000
     flip = kit.rect_light_over_floor(N, normal=lambda f: (0.0, -1.0, 0.0) if f == 1 else (0.0, 1.0, 0.0))
