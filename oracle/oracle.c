@@ -253,6 +253,19 @@ static uint32_t light_of(const or_scene* s, uint32_t pid) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* decision scripts                                                          */
+/* ------------------------------------------------------------------------ */
+/* An ambiguous decision with n_alt possible outcomes: the outcome the script
+ * gives it (0, the FP64 decision, without a script or past its end). */
+static int choose(or_choice* ch, int n_alt) {
+  if (!ch || n_alt < 2) return 0;
+  const int j = ch->pos++;
+  if (j < ch->n_script) return ch->script[j] < n_alt ? ch->script[j] : 0;
+  if (j == ch->n_script && ch->n_alt_next == 0) ch->n_alt_next = n_alt;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* ray / triangle with ambiguity                                             */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -326,8 +339,10 @@ static void cv_push(candvec* v, const cand_t* c) {
  * the eps perturbation: the nearest hit is itself ambiguous, an ambiguous
  * triangle lies in front of (or level with) it, or another hit lies within
  * the combined t tolerance. */
+#define OR_MAX_HIT_ALTS 8
+
 static int32_t closest_hit(const or_scene* s, int p, const double* o, const double* d, double tlo,
-                           int32_t exclude, double* t_out, int* amb_out) {
+                           int32_t exclude, double* t_out, int* amb_out, or_choice* ch) {
   candvec cv = {0, 0, 0};
   int32_t best = -1;
   double best_t = INFINITY;
@@ -360,6 +375,51 @@ static int32_t closest_hit(const or_scene* s, int p, const double* o, const doub
     if (c->amb && c->t - c->epst < best_t + best_eps) amb = 1;
     if (c->hit && fabs(c->t - best_t) < c->epst + best_eps) amb = 1;
   }
+  if (amb && ch) {
+    /* the outcomes the band admits: the FP64 nearest hit first; then, nearest
+     * first, every triangle that could be hit in front of it or level with it;
+     * and if the nearest hit could itself be missed, the next hit (or a miss) */
+    int32_t alt_p[OR_MAX_HIT_ALTS];
+    double alt_t[OR_MAX_HIT_ALTS];
+    int na = 0;
+    alt_p[na] = best; alt_t[na] = best_t; ++na;
+    int best_amb = 0;
+    for (size_t i = 0; i < cv.n; ++i)
+      if (cv.c[i].prim == best && cv.c[i].amb) best_amb = 1;
+    for (;;) {                                   /* insertion by distance, skipping what is listed */
+      const cand_t* pick = NULL;
+      for (size_t i = 0; i < cv.n; ++i) {
+        const cand_t* c = &cv.c[i];
+        int listed = 0;
+        for (int k = 0; k < na; ++k) listed |= alt_p[k] == c->prim;
+        if (listed) continue;
+        const int admit = best < 0 ? c->amb
+                                   : (c->amb && c->t - c->epst < best_t + best_eps) ||
+                                         (c->hit && fabs(c->t - best_t) < c->epst + best_eps);
+        if (admit && (!pick || c->t < pick->t)) pick = c;
+      }
+      if (!pick || na == OR_MAX_HIT_ALTS) break;
+      alt_p[na] = pick->prim; alt_t[na] = pick->t; ++na;
+    }
+    if (best >= 0 && best_amb && na < OR_MAX_HIT_ALTS) {
+      const cand_t* next = NULL;                 /* the nearest other hit, if the nearest is missed */
+      for (size_t i = 0; i < cv.n; ++i) {
+        const cand_t* c = &cv.c[i];
+        if (c->prim == best || !c->hit) continue;
+        if (!next || c->t < next->t) next = c;
+      }
+      int listed = 0;
+      for (int k = 0; k < na; ++k) listed |= next ? alt_p[k] == next->prim : alt_p[k] < 0;
+      if (!listed) {
+        alt_p[na] = next ? next->prim : -1;
+        alt_t[na] = next ? next->t : INFINITY;
+        ++na;
+      }
+    }
+    const int k = choose(ch, na);
+    best = alt_p[k];
+    best_t = alt_t[k];
+  }
   free(cv.c);
   *t_out = best_t;
   *amb_out = amb;
@@ -369,7 +429,7 @@ static int32_t closest_hit(const or_scene* s, int p, const double* o, const doub
 int32_t or_closest_hit(const or_scene* s, const double o[3], const double d[3], double tlo,
                        int32_t exclude, double* t_out, int32_t* amb) {
   int a = 0;
-  int32_t r = closest_hit(s, 1, o, d, tlo, exclude, t_out, &a);
+  int32_t r = closest_hit(s, 1, o, d, tlo, exclude, t_out, &a, NULL);
   *amb = a;
   return r;
 }
@@ -378,7 +438,7 @@ int32_t or_closest_hit(const or_scene* s, const double o[3], const double d[3], 
  * triangles (all triangles if list == NULL) at pose p.  *amb is set when no
  * robust hit exists but some triangle is ambiguous. */
 static int any_hit(const or_scene* s, int p, const uint32_t* list, uint32_t count, const double* a,
-                   const double* b, int32_t exclude, int* amb) {
+                   const double* b, int32_t exclude, int* amb, or_choice* ch) {
   double d[3];
   sub3(b, a, d);
   double len = norm3(d);
@@ -402,6 +462,7 @@ static int any_hit(const or_scene* s, int p, const uint32_t* list, uint32_t coun
     if (c.amb) any_amb = 1;
   }
   *amb = any_amb;
+  if (any_amb && choose(ch, 2)) any = !any;       /* only ambiguous triangles decide: either answer */
   return any;
 }
 
@@ -451,9 +512,9 @@ static void unit_normal(const or_scene* s, int p, int32_t prim, double n[3]) {
 }
 
 /* Orthonormal basis around unit n (Duff, Burgess, Christensen, Hery, Kensler,
- * Liani, Villemin, JCGT 2017), with the branch taken on n.z >= 0. */
-static void onb(const double* n, double* b1, double* b2) {
-  double sg = n[2] >= 0.0 ? 1.0 : -1.0;
+ * Liani, Villemin, JCGT 2017); the branch sg = +1 is the one taken for
+ * n.z >= 0 and sg = -1 the one for n.z < 0. */
+static void onb(const double* n, double sg, double* b1, double* b2) {
   double a = -1.0 / (sg + n[2]);
   double b = n[0] * n[1] * a;
   b1[0] = 1.0 + sg * n[0] * n[0] * a; b1[1] = sg * b; b1[2] = -sg * n[0];
@@ -490,15 +551,26 @@ static void emit(const or_light* L, const double* u, double* o, double* d) {
   }
 }
 
-/* Facing normal: the geometric normal flipped against the incoming ray. */
-static void facing(const or_scene* s, int p, int32_t prim, const double* d_in, double* ns, int* amb) {
+/* Facing normal: the geometric normal flipped against the incoming ray.
+ * With ``branch`` the orthonormal basis branch about it too (+1 for
+ * n.z >= 0).  Either decision may be ambiguous: a script then picks it. */
+static void facing(const or_scene* s, int p, int32_t prim, const double* d_in, double* ns, int* amb,
+                   or_choice* ch, double* branch) {
   double n[3];
   unit_normal(s, p, prim, n);
   double c = dot3(n, d_in);
-  if (fabs(c) < 1e-6) *amb = 1;
   double sg = c < 0.0 ? 1.0 : -1.0;
+  if (fabs(c) < 1e-6) {
+    *amb = 1;
+    if (choose(ch, 2)) sg = -sg;
+  }
   ns[0] = sg * n[0]; ns[1] = sg * n[1]; ns[2] = sg * n[2];
-  if (ns[2] != 0.0 && fabs(ns[2]) < 1e-6) *amb = 1;   /* basis branch near n.z = 0 */
+  double br = ns[2] >= 0.0 ? 1.0 : -1.0;
+  if (ns[2] != 0.0 && fabs(ns[2]) < 1e-6) {   /* basis branch near n.z = 0 */
+    *amb = 1;
+    if (branch && choose(ch, 2)) br = -br;
+  }
+  if (branch) *branch = br;
 }
 
 static inline uint32_t info_nseg(uint32_t w) { return (w >> OR_INFO_NSEG_SHIFT) & 15u; }
@@ -684,7 +756,7 @@ void or_dm_set_counts(or_scene* s, uint32_t light, const uint32_t* in) {
  * E_{k+1} = E_k * albedo / q).  Returns the new photon count. */
 static uint32_t extend_path(const or_scene* s, uint32_t pid, uint64_t seed, uint32_t frame, uint32_t k,
                             double* o, double* d, double* E, double radius, const float* origin,
-                            or_photon* ph, uint32_t* amb, uint64_t* rays) {
+                            or_photon* ph, uint32_t* amb, uint64_t* rays, or_choice* ch) {
   int32_t excl = -1;
   for (;;) {
     if (k >= 1) {
@@ -700,11 +772,11 @@ static uint32_t extend_path(const or_scene* s, uint32_t pid, uint64_t seed, uint
       f2d(v->pos, xk);
       sub3(xk, xin, din);
       normalize3(din);
-      double ns[3], b1[3], b2[3];
+      double ns[3], b1[3], b2[3], br;
       int a = 0;
-      facing(s, 1, v->prim, din, ns, &a);
+      facing(s, 1, v->prim, din, ns, &a, ch, &br);
       if (a) *amb |= OR_AMB_TRACE;
-      onb(ns, b1, b2);
+      onb(ns, br, b1, b2);
       cosine_dir(ns, b1, b2, u[0], u[1], d);
       for (int c = 0; c < 3; ++c) E[c] = (double)v->E[c] * (double)alb[c] / q;
       f2d(v->pos, o);
@@ -713,7 +785,7 @@ static uint32_t extend_path(const or_scene* s, uint32_t pid, uint64_t seed, uint
     }
     double t;
     int a = 0;
-    int32_t prim = closest_hit(s, 1, o, d, s->tmin, excl, &t, &a);
+    int32_t prim = closest_hit(s, 1, o, d, s->tmin, excl, &t, &a, ch);
     (*rays)++;
     if (a) *amb |= OR_AMB_TRACE;
     if (prim < 0) break;
@@ -729,36 +801,45 @@ static uint32_t extend_path(const or_scene* s, uint32_t pid, uint64_t seed, uint
   return k;
 }
 
+/* One path traced from the light; returns its rays. */
+static uint64_t trace_path(const or_scene* s, uint32_t pid, uint64_t seed, uint32_t frame, uint32_t* info,
+                           float* org, or_photon* ph, uint32_t* amb, or_choice* ch) {
+  uint32_t l = light_of(s, pid);
+  const or_light* L = &s->light[1][l];
+  double u[4], o[3], d[3], E[3];
+  rng4(seed, pid, 0, frame, u);
+  uint32_t cell = 0;
+  if (s->dm_c[l]) {                          /* stratified over the distribution map */
+    cell = dm_stratified(s, l, pid - s->light_first[l]);
+    dm_restrict(s, l, cell, u);
+  }
+  emit(L, u, o, d);
+  for (int c = 0; c < 3; ++c) E[c] = (double)L->power[c] / (double)L->n_paths;
+  for (int c = 0; c < 3; ++c) org[c] = (float)o[c];
+  f2d(org, o);
+  *amb = 0;
+  uint64_t r = 0;
+  uint32_t k = extend_path(s, pid, seed, frame, 0, o, d, E, 0.0, org, ph, amb, &r, ch);
+  *info = info_make((l << 20) | cell, k, 0, 0, 0);
+  return r;
+}
+
 void or_trace(const or_scene* s, const uint32_t* ids, uint32_t n, uint64_t seed, uint32_t frame,
               uint32_t* info, float* origin, or_photon* photons, uint32_t* amb, or_stats* st) {
   uint64_t rays = 0;
 #pragma omp parallel for schedule(dynamic, 8) reduction(+ : rays)
-  for (uint32_t i = 0; i < n; ++i) {
-    uint32_t pid = ids[i];
-    uint32_t l = light_of(s, pid);
-    const or_light* L = &s->light[1][l];
-    double u[4], o[3], d[3], E[3];
-    rng4(seed, pid, 0, frame, u);
-    uint32_t cell = 0;
-    if (s->dm_c[l]) {                          /* stratified over the distribution map */
-      cell = dm_stratified(s, l, pid - s->light_first[l]);
-      dm_restrict(s, l, cell, u);
-    }
-    emit(L, u, o, d);
-    for (int c = 0; c < 3; ++c) E[c] = (double)L->power[c] / (double)L->n_paths;
-    float* org = origin + 3 * (size_t)i;
-    for (int c = 0; c < 3; ++c) org[c] = (float)o[c];
-    f2d(org, o);
-    amb[i] = 0;
-    uint64_t r = 0;
-    uint32_t k = extend_path(s, pid, seed, frame, 0, o, d, E, 0.0, org, photons + (size_t)i * s->B, &amb[i], &r);
-    rays += r;
-    info[i] = info_make((l << 20) | cell, k, 0, 0, 0);
-  }
+  for (uint32_t i = 0; i < n; ++i)
+    rays += trace_path(s, ids[i], seed, frame, &info[i], origin + 3 * (size_t)i, photons + (size_t)i * s->B, &amb[i],
+                       NULL);
   if (st) {
     st->paths += n;
     st->trace_rays += rays;
   }
+}
+
+void or_trace_path(const or_scene* s, uint32_t pid, uint64_t seed, uint32_t frame, uint32_t* info, float* origin,
+                   or_photon* photons, uint32_t* amb, or_choice* ch) {
+  trace_path(s, pid, seed, frame, info, origin, photons, amb, ch);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -791,7 +872,8 @@ static int obj_moved(const or_scene* s, int32_t prim) { return prim >= 0 && s->m
  * moved object; the exact test (naive-exact mode, or error mode with
  * OR_FLAG_ERROR_EXACT) tests the open segment against the moved objects'
  * triangles at the new pose (and the old pose with OR_FLAG_TEST_OLD_TRIS). */
-static int seg_vs_moved(const or_scene* s, int mode, uint32_t flags, const double* a, const double* b, int* amb) {
+static int seg_vs_moved(const or_scene* s, int mode, uint32_t flags, const double* a, const double* b, int* amb,
+                        or_choice* ch) {
   int any = 0, any_amb = 0;
   for (uint32_t m = 0; m < s->n_moved; ++m) {
     uint32_t o = s->moved_list[m];
@@ -807,10 +889,10 @@ static int seg_vs_moved(const or_scene* s, int mode, uint32_t flags, const doubl
     } else {
       const uint32_t* lst = s->obj_tris + s->obj_first[o];
       uint32_t cnt = s->obj_first[o + 1] - s->obj_first[o];
-      hit = any_hit(s, 1, lst, cnt, a, b, -1, &am);
+      hit = any_hit(s, 1, lst, cnt, a, b, -1, &am, NULL);
       if (!(hit && !am) && (flags & OR_FLAG_TEST_OLD_TRIS)) {
         int am2 = 0;
-        int h2 = any_hit(s, 0, lst, cnt, a, b, -1, &am2);
+        int h2 = any_hit(s, 0, lst, cnt, a, b, -1, &am2, NULL);
         if (h2 && !am2) {
           hit = 1;
           am = 0;
@@ -828,7 +910,276 @@ static int seg_vs_moved(const or_scene* s, int mode, uint32_t flags, const doubl
     if (am) any_amb = 1;
   }
   *amb = any_amb;
+  if (any_amb && choose(ch, 2)) any = !any;       /* no object decides robustly: either answer */
   return any;
+}
+
+/* per-path counters of a verification */
+typedef struct {
+  uint64_t seg_t, seg_a, vis, cont, et, ea, nre, ntail, nupd, ntr;
+} vcount;
+
+/* One path of or_verify (everything before the distribution-map steps):
+ * origins, dynamic occlusions and Alg. 1.  *counted: the path keeps its
+ * origin on a moved light with a map (it counts in DM_C). */
+static void verify_path(const or_scene* s, uint32_t pid, int32_t mode, double tau, uint32_t flags, uint32_t* info,
+                        float* origin, or_photon* photons, uint32_t* seg_mask, uint32_t* ambv, uint8_t* counted,
+                        vcount* vc, or_choice* ch) {
+  uint32_t w = *info;
+  uint32_t cell = w & OR_INFO_CELL_MASK;
+  uint32_t L = info_nseg(w);
+  uint32_t l = light_of(s, pid);
+  or_photon* ph = photons;
+  float* org = origin;
+  uint32_t amb = 0;
+  int seg1_blocked = 0;
+  *seg_mask = 0;
+
+  /* ---- Sec. 3.1 "update path origins" ---- */
+  if (s->light_moved[l]) {
+    const or_light* Ln = &s->light[1][l];
+    const or_light* Lo = &s->light[0][l];
+    int invalid = 0;
+    int dm_cell = -1;
+    if (L > 0 && s->dm_c[l]) {               /* Compute DM_C: the parametrisation decides */
+      float u[4];
+      if (dm_param(Ln, ph[0].pos, org, u)) dm_cell = (int)dm_cell_of_u(s, l, u);
+    }
+    if (L == 0 || (s->dm_c[l] && dm_cell < 0)) {
+      invalid = 1;          /* an escaped path has no vertex to re-aim at; or off the map */
+    } else if (Ln->type == 0) {
+      for (int c = 0; c < 3; ++c) org[c] = Ln->pos[c];
+      double a[3], b[3];
+      f2d(org, a);
+      f2d(ph[0].pos, b);
+      int am = 0;
+      seg1_blocked = any_hit(s, 1, NULL, 0, a, b, ph[0].prim, &am, ch);
+      vc->vis++;
+      if (am) amb |= OR_AMB_VERIFY;
+    } else {
+      double x1[3], o0[3], d[3], c[3], nn[3], tt[3], bb[3], no[3];
+      f2d(ph[0].pos, x1);
+      f2d(org, o0);
+      sub3(x1, o0, d);
+      normalize3(d);
+      f2d(Ln->pos, c); f2d(Ln->normal, nn); f2d(Ln->tangent, tt);
+      cross3(nn, tt, bb);
+      /* with a distribution map the float32 parametrisation has decided
+       * validity; the double-precision tests below decide it otherwise */
+      const int by_map = s->dm_c[l] != NULL;
+      double ndv = dot3(nn, d);
+      int facing_light = ndv > 0.0;
+      if (!by_map && fabs(ndv) < 1e-6) {
+        amb |= OR_AMB_LIGHT;
+        if (choose(ch, 2)) facing_light = !facing_light;
+      }
+      if (!by_map && !facing_light) {
+        invalid = 1;
+      } else {
+        double x1c[3];
+        sub3(x1, c, x1c);
+        double tp = dot3(nn, x1c) / ndv;
+        int in_front = tp > 0.0;
+        if (!by_map && fabs(tp) < s->eps) {
+          amb |= OR_AMB_LIGHT;
+          if (choose(ch, 2)) in_front = !in_front;
+        }
+        if (!by_map && !in_front) {
+          invalid = 1;
+        } else {
+          double op[3], rel[3];
+          for (int k = 0; k < 3; ++k) op[k] = x1[k] - tp * d[k];
+          sub3(op, c, rel);
+          double su = dot3(tt, rel), sv = dot3(bb, rel);
+          double hw = 0.5 * Ln->size[0], hh = 0.5 * Ln->size[1];
+          if (!by_map) {
+            int outside = fabs(su) > hw || fabs(sv) > hh;
+            if (fabs(fabs(su) - hw) < s->eps || fabs(fabs(sv) - hh) < s->eps) {
+              amb |= OR_AMB_LIGHT;
+              if (choose(ch, 2)) outside = !outside;
+            }
+            if (outside) invalid = 1;
+          }
+          if (!invalid && s->light_tilted[l]) {
+            f2d(Lo->normal, no);
+            double ratio = ndv / dot3(no, d);
+            double EN[3];
+            for (int k = 0; k < 3; ++k) EN[k] = (double)ph[0].E[k] * ratio;
+            int near = 0;
+            vc->et++;
+            int pass = energy_close(EN, ph[0].E, tau, &near);
+            if (near) {
+              vc->ea++;
+              amb |= OR_AMB_ENERGY;
+              if (choose(ch, 2)) pass = !pass;
+            }
+            if (!pass) invalid = 1;
+          }
+          if (!invalid)
+            for (int k = 0; k < 3; ++k) org[k] = (float)op[k];
+        }
+      }
+    }
+    if (invalid) {
+      *info = info_make(cell, 0, 0, 1, 0);
+      vc->nre++;
+      *ambv = amb;
+      return;
+    }
+    if (dm_cell >= 0) {
+      cell = (l << 20) | (uint32_t)dm_cell;
+      *info = (w & ~OR_INFO_CELL_MASK) | cell;
+      *counted = 1;
+    }
+  }
+
+  /* ---- Sec. 3.2 "dynamic occlusions": segments in order from the light ---- */
+  uint32_t mask = 0;
+  for (uint32_t k = 1; k <= L; ++k) {
+    double a[3], b[3];
+    if (k == 1) f2d(org, a); else f2d(ph[k - 2].pos, a);
+    f2d(ph[k - 1].pos, b);
+    int hit = obj_moved(s, ph[k - 1].prim) || (k >= 2 && obj_moved(s, ph[k - 2].prim)) || (k == 1 && seg1_blocked);
+    if (!hit) {
+      int am = 0;
+      hit = seg_vs_moved(s, mode, flags, a, b, &am, ch);
+      vc->seg_t++;
+      if (am) { vc->seg_a++; amb |= OR_AMB_VERIFY; }
+    }
+    if (hit) {
+      mask |= 1u << k;
+      if (mode != OR_MODE_ERROR) break;
+    }
+  }
+  *seg_mask = mask;
+  if (!mask) {
+    *ambv = amb;
+    return;
+  }
+  uint32_t first = 0;
+  while (!((mask >> first) & 1u)) ++first;
+
+  if (mode != OR_MODE_ERROR) {
+    if (first == 1) {
+      *info = info_make(cell, 0, 0, 1, 1);   /* keep light position and direction */
+      vc->nre++;
+    } else {
+      *info = info_make(cell, first - 1, first - 1, 1, 0);
+      vc->ntail++;
+    }
+    *ambv = amb;
+    return;
+  }
+
+  /* ---- Sec. 3.3, Alg. 1: error-based threshold continuation ---- */
+  double xo[16][3];      /* original vertex positions, 0 = origin */
+  int32_t po[16];
+  f2d(org, xo[0]);
+  po[0] = -1;
+  for (uint32_t k = 1; k <= L; ++k) { f2d(ph[k - 1].pos, xo[k]); po[k] = ph[k - 1].prim; }
+  uint32_t moved_origin = 0;
+  int updated = 0, done = 0;
+  uint32_t seg = first;
+  while (seg <= L && !done) {
+    if (!((mask >> seg) & 1u) && !((moved_origin >> seg) & 1u)) { ++seg; continue; }
+    double a[3], b[3], d[3];
+    if (seg == 1) f2d(org, a); else f2d(ph[seg - 2].pos, a);
+    f2d(ph[seg - 1].pos, b);
+    sub3(b, a, d);
+    normalize3(d);
+    int32_t excl = seg == 1 ? -1 : ph[seg - 2].prim;
+    double t;
+    int am = 0;
+    int32_t pn = closest_hit(s, 1, a, d, s->tmin, excl, &t, &am, ch);
+    vc->cont++;
+    if (am) amb |= OR_AMB_CONT;
+    if (pn < 0) {                       /* nothing hit: the path ends here */
+      L = seg - 1;
+      vc->ntr++;
+      done = 1;
+      break;
+    }
+    float xn[3];
+    double xnd[3];
+    for (int c = 0; c < 3; ++c) { xn[c] = (float)(a[c] + t * d[c]); xnd[c] = xn[c]; }
+    double dx = 0.0;
+    for (int c = 0; c < 3; ++c) dx = fmax(dx, fabs(xnd[c] - b[c]));
+    int close = pn == ph[seg - 1].prim && dx <= s->close_tol;
+    if (pn == ph[seg - 1].prim && fabs(dx - s->close_tol) < s->eps) {
+      amb |= OR_AMB_CONT;
+      if (choose(ch, 2)) close = !close;
+    }
+    if (seg == L) {                     /* last photon: move it, nothing follows */
+      for (int c = 0; c < 3; ++c) ph[seg - 1].pos[c] = xn[c];
+      ph[seg - 1].prim = pn;
+      updated = 1;
+      done = 1;
+      break;
+    }
+    double EN[3];
+    const float* EO = ph[seg].E;
+    if (close) {
+      for (int c = 0; c < 3; ++c) EN[c] = EO[c];
+    } else {
+      /* new vertex: albedo, facing normal, direction to the stored next photon */
+      const float* albn = s->albedo + 3 * (size_t)s->tri_object[pn];
+      double nsn[3], w[3], xnext[3];
+      int af = 0;
+      facing(s, 1, pn, d, nsn, &af, ch, NULL);
+      f2d(ph[seg].pos, xnext);
+      sub3(xnext, xnd, w);
+      double wl = norm3(w);
+      double cosn = 0.0;
+      if (wl > 0.0) {
+        w[0] /= wl; w[1] /= wl; w[2] /= wl;
+        cosn = fmax(0.0, dot3(nsn, w));
+      }
+      /* old vertex (old pose): RR probability, facing normal, sampled direction */
+      const float* albo = s->albedo + 3 * (size_t)s->tri_object[po[seg]];
+      double q = max3(albo);
+      double dino[3], nso[3], wo[3];
+      sub3(xo[seg], xo[seg - 1], dino);
+      normalize3(dino);
+      int af2 = 0;
+      facing(s, 0, po[seg], dino, nso, &af2, ch, NULL);
+      if (af || af2) amb |= OR_AMB_CONT;
+      sub3(xo[seg + 1], xo[seg], wo);
+      normalize3(wo);
+      double coso = dot3(nso, wo);
+      for (int c = 0; c < 3; ++c)
+        EN[c] = coso > 0.0 ? (double)ph[seg - 1].E[c] * (double)albn[c] * cosn / (q * coso) : 0.0;
+    }
+    int near = 0;
+    vc->et++;
+    int pass = energy_close(EN, EO, tau, &near);
+    if (near && !close) {
+      vc->ea++;
+      amb |= OR_AMB_ENERGY;
+      if (choose(ch, 2)) pass = !pass;
+    }
+    if (!pass) {                        /* re-trace from the new vertex */
+      for (int c = 0; c < 3; ++c) ph[seg - 1].pos[c] = xn[c];
+      ph[seg - 1].prim = pn;
+      *info = info_make(cell, seg, seg, 1, 0);
+      vc->ntail++;
+      done = 2;
+      break;
+    }
+    if (close && !((mask >> (seg + 1)) & 1u) && !obj_moved(s, pn) && !obj_moved(s, ph[seg].prim)) {
+      seg += 2;                         /* next segment known valid: skip its check */
+      continue;
+    }
+    for (int c = 0; c < 3; ++c) ph[seg - 1].pos[c] = xn[c];
+    ph[seg - 1].prim = pn;
+    updated = 1;
+    moved_origin |= 1u << (seg + 1);
+    ++seg;
+  }
+  if (done != 2) {
+    *info = info_make(cell, L, 0, 0, 0);
+    if (updated) vc->nupd++;
+  }
+  *ambv = amb;
 }
 
 void or_verify(const or_scene* s, const uint32_t* ids, uint32_t n, int32_t mode, double tau,
@@ -839,238 +1190,11 @@ void or_verify(const or_scene* s, const uint32_t* ids, uint32_t n, int32_t mode,
   uint8_t* counted = (uint8_t*)calloc(n ? n : 1, 1);
 #pragma omp parallel for schedule(dynamic, 8) reduction(+ : seg_t, seg_a, vis, cont, et, ea, nre, ntail, nupd, ntr)
   for (uint32_t i = 0; i < n; ++i) {
-    uint32_t pid = ids[i];
-    uint32_t w = info[i];
-    uint32_t cell = w & OR_INFO_CELL_MASK;
-    uint32_t L = info_nseg(w);
-    uint32_t l = light_of(s, pid);
-    or_photon* ph = photons + (size_t)i * s->B;
-    float* org = origin + 3 * (size_t)i;
-    uint32_t amb = 0;
-    int seg1_blocked = 0;
-    seg_mask[i] = 0;
-
-    /* ---- Sec. 3.1 "update path origins" ---- */
-    if (s->light_moved[l]) {
-      const or_light* Ln = &s->light[1][l];
-      const or_light* Lo = &s->light[0][l];
-      int invalid = 0;
-      int dm_cell = -1;
-      if (L > 0 && s->dm_c[l]) {               /* Compute DM_C: the parametrisation decides */
-        float u[4];
-        if (dm_param(Ln, ph[0].pos, org, u)) dm_cell = (int)dm_cell_of_u(s, l, u);
-      }
-      if (L == 0 || (s->dm_c[l] && dm_cell < 0)) {
-        invalid = 1;          /* an escaped path has no vertex to re-aim at; or off the map */
-      } else if (Ln->type == 0) {
-        for (int c = 0; c < 3; ++c) org[c] = Ln->pos[c];
-        double a[3], b[3];
-        f2d(org, a);
-        f2d(ph[0].pos, b);
-        int am = 0;
-        seg1_blocked = any_hit(s, 1, NULL, 0, a, b, ph[0].prim, &am);
-        vis++;
-        if (am) amb |= OR_AMB_VERIFY;
-      } else {
-        double x1[3], o0[3], d[3], c[3], nn[3], tt[3], bb[3], no[3];
-        f2d(ph[0].pos, x1);
-        f2d(org, o0);
-        sub3(x1, o0, d);
-        normalize3(d);
-        f2d(Ln->pos, c); f2d(Ln->normal, nn); f2d(Ln->tangent, tt);
-        cross3(nn, tt, bb);
-        /* with a distribution map the float32 parametrisation has decided
-         * validity; the double-precision tests below decide it otherwise */
-        const int by_map = s->dm_c[l] != NULL;
-        double ndv = dot3(nn, d);
-        if (!by_map && fabs(ndv) < 1e-6) amb |= OR_AMB_LIGHT;
-        if (!by_map && !(ndv > 0.0)) {
-          invalid = 1;
-        } else {
-          double x1c[3];
-          sub3(x1, c, x1c);
-          double tp = dot3(nn, x1c) / ndv;
-          if (!by_map && fabs(tp) < s->eps) amb |= OR_AMB_LIGHT;
-          if (!by_map && !(tp > 0.0)) {
-            invalid = 1;
-          } else {
-            double op[3], rel[3];
-            for (int k = 0; k < 3; ++k) op[k] = x1[k] - tp * d[k];
-            sub3(op, c, rel);
-            double su = dot3(tt, rel), sv = dot3(bb, rel);
-            double hw = 0.5 * Ln->size[0], hh = 0.5 * Ln->size[1];
-            if (!by_map) {
-              if (fabs(fabs(su) - hw) < s->eps || fabs(fabs(sv) - hh) < s->eps) amb |= OR_AMB_LIGHT;
-              if (fabs(su) > hw || fabs(sv) > hh) invalid = 1;
-            }
-            if (!invalid && s->light_tilted[l]) {
-              f2d(Lo->normal, no);
-              double ratio = ndv / dot3(no, d);
-              double EN[3];
-              for (int k = 0; k < 3; ++k) EN[k] = (double)ph[0].E[k] * ratio;
-              int near = 0;
-              et++;
-              if (!energy_close(EN, ph[0].E, tau, &near)) invalid = 1;
-              if (near) { ea++; amb |= OR_AMB_ENERGY; }
-            }
-            if (!invalid)
-              for (int k = 0; k < 3; ++k) org[k] = (float)op[k];
-          }
-        }
-      }
-      if (invalid) {
-        info[i] = info_make(cell, 0, 0, 1, 0);
-        nre++;
-        ambv[i] = amb;
-        continue;
-      }
-      if (dm_cell >= 0) {
-        cell = (l << 20) | (uint32_t)dm_cell;
-        info[i] = (w & ~OR_INFO_CELL_MASK) | cell;
-        counted[i] = 1;
-      }
-    }
-
-    /* ---- Sec. 3.2 "dynamic occlusions": segments in order from the light ---- */
-    uint32_t mask = 0;
-    for (uint32_t k = 1; k <= L; ++k) {
-      double a[3], b[3];
-      if (k == 1) f2d(org, a); else f2d(ph[k - 2].pos, a);
-      f2d(ph[k - 1].pos, b);
-      int hit = obj_moved(s, ph[k - 1].prim) || (k >= 2 && obj_moved(s, ph[k - 2].prim)) || (k == 1 && seg1_blocked);
-      if (!hit) {
-        int am = 0;
-        hit = seg_vs_moved(s, mode, flags, a, b, &am);
-        seg_t++;
-        if (am) { seg_a++; amb |= OR_AMB_VERIFY; }
-      }
-      if (hit) {
-        mask |= 1u << k;
-        if (mode != OR_MODE_ERROR) break;
-      }
-    }
-    seg_mask[i] = mask;
-    if (!mask) {
-      ambv[i] = amb;
-      continue;
-    }
-    uint32_t first = 0;
-    while (!((mask >> first) & 1u)) ++first;
-
-    if (mode != OR_MODE_ERROR) {
-      if (first == 1) {
-        info[i] = info_make(cell, 0, 0, 1, 1);   /* keep light position and direction */
-        nre++;
-      } else {
-        info[i] = info_make(cell, first - 1, first - 1, 1, 0);
-        ntail++;
-      }
-      ambv[i] = amb;
-      continue;
-    }
-
-    /* ---- Sec. 3.3, Alg. 1: error-based threshold continuation ---- */
-    double xo[16][3];      /* original vertex positions, 0 = origin */
-    int32_t po[16];
-    f2d(org, xo[0]);
-    po[0] = -1;
-    for (uint32_t k = 1; k <= L; ++k) { f2d(ph[k - 1].pos, xo[k]); po[k] = ph[k - 1].prim; }
-    uint32_t moved_origin = 0;
-    int updated = 0, done = 0;
-    uint32_t seg = first;
-    while (seg <= L && !done) {
-      if (!((mask >> seg) & 1u) && !((moved_origin >> seg) & 1u)) { ++seg; continue; }
-      double a[3], b[3], d[3];
-      if (seg == 1) f2d(org, a); else f2d(ph[seg - 2].pos, a);
-      f2d(ph[seg - 1].pos, b);
-      sub3(b, a, d);
-      normalize3(d);
-      int32_t excl = seg == 1 ? -1 : ph[seg - 2].prim;
-      double t;
-      int am = 0;
-      int32_t pn = closest_hit(s, 1, a, d, s->tmin, excl, &t, &am);
-      cont++;
-      if (am) amb |= OR_AMB_CONT;
-      if (pn < 0) {                       /* nothing hit: the path ends here */
-        L = seg - 1;
-        ntr++;
-        done = 1;
-        break;
-      }
-      float xn[3];
-      double xnd[3];
-      for (int c = 0; c < 3; ++c) { xn[c] = (float)(a[c] + t * d[c]); xnd[c] = xn[c]; }
-      double dx = 0.0;
-      for (int c = 0; c < 3; ++c) dx = fmax(dx, fabs(xnd[c] - b[c]));
-      int close = pn == ph[seg - 1].prim && dx <= s->close_tol;
-      if (pn == ph[seg - 1].prim && fabs(dx - s->close_tol) < s->eps) amb |= OR_AMB_CONT;
-      if (seg == L) {                     /* last photon: move it, nothing follows */
-        for (int c = 0; c < 3; ++c) ph[seg - 1].pos[c] = xn[c];
-        ph[seg - 1].prim = pn;
-        updated = 1;
-        done = 1;
-        break;
-      }
-      double EN[3];
-      const float* EO = ph[seg].E;
-      if (close) {
-        for (int c = 0; c < 3; ++c) EN[c] = EO[c];
-      } else {
-        /* new vertex: albedo, facing normal, direction to the stored next photon */
-        const float* albn = s->albedo + 3 * (size_t)s->tri_object[pn];
-        double nsn[3], w[3], xnext[3];
-        int af = 0;
-        facing(s, 1, pn, d, nsn, &af);
-        f2d(ph[seg].pos, xnext);
-        sub3(xnext, xnd, w);
-        double wl = norm3(w);
-        double cosn = 0.0;
-        if (wl > 0.0) {
-          w[0] /= wl; w[1] /= wl; w[2] /= wl;
-          cosn = fmax(0.0, dot3(nsn, w));
-        }
-        /* old vertex (old pose): RR probability, facing normal, sampled direction */
-        const float* albo = s->albedo + 3 * (size_t)s->tri_object[po[seg]];
-        double q = max3(albo);
-        double dino[3], nso[3], wo[3];
-        sub3(xo[seg], xo[seg - 1], dino);
-        normalize3(dino);
-        int af2 = 0;
-        facing(s, 0, po[seg], dino, nso, &af2);
-        if (af || af2) amb |= OR_AMB_CONT;
-        sub3(xo[seg + 1], xo[seg], wo);
-        normalize3(wo);
-        double coso = dot3(nso, wo);
-        for (int c = 0; c < 3; ++c)
-          EN[c] = coso > 0.0 ? (double)ph[seg - 1].E[c] * (double)albn[c] * cosn / (q * coso) : 0.0;
-      }
-      int near = 0;
-      et++;
-      int pass = energy_close(EN, EO, tau, &near);
-      if (near && !close) { ea++; amb |= OR_AMB_ENERGY; }
-      if (!pass) {                        /* re-trace from the new vertex */
-        for (int c = 0; c < 3; ++c) ph[seg - 1].pos[c] = xn[c];
-        ph[seg - 1].prim = pn;
-        info[i] = info_make(cell, seg, seg, 1, 0);
-        ntail++;
-        done = 2;
-        break;
-      }
-      if (close && !((mask >> (seg + 1)) & 1u) && !obj_moved(s, pn) && !obj_moved(s, ph[seg].prim)) {
-        seg += 2;                         /* next segment known valid: skip its check */
-        continue;
-      }
-      for (int c = 0; c < 3; ++c) ph[seg - 1].pos[c] = xn[c];
-      ph[seg - 1].prim = pn;
-      updated = 1;
-      moved_origin |= 1u << (seg + 1);
-      ++seg;
-    }
-    if (done != 2) {
-      info[i] = info_make(cell, L, 0, 0, 0);
-      if (updated) nupd++;
-    }
-    ambv[i] = amb;
+    vcount c = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    verify_path(s, ids[i], mode, tau, flags, &info[i], origin + 3 * (size_t)i, photons + (size_t)i * s->B,
+                &seg_mask[i], &ambv[i], &counted[i], &c, NULL);
+    seg_t += c.seg_t; seg_a += c.seg_a; vis += c.vis; cont += c.cont; et += c.et;
+    ea += c.ea; nre += c.nre; ntail += c.ntail; nupd += c.nupd; ntr += c.ntr;
   }
   /* ---- Compute DM_C, prune paths (Eq. 1, mark then edit), fill DM_C (Sec. 3.1) ---- */
   uint64_t npr = 0, nfi = 0;
@@ -1167,47 +1291,65 @@ uint32_t or_compact(const uint32_t* info, uint32_t n, uint32_t* list) {
   return c;
 }
 
+/* One path of or_retrace; returns its rays. */
+static uint64_t retrace_path(const or_scene* s, uint32_t pid, uint64_t seed, uint32_t frame, uint32_t* info,
+                             float* org, or_photon* ph, uint32_t* ambv, or_choice* ch) {
+  uint32_t w = *info;
+  if (!(w & OR_INFO_REPLACE)) return 0;
+  uint32_t l = light_of(s, pid);
+  const or_light* L = &s->light[1][l];
+  uint32_t start = info_start(w);
+  double o[3], d[3], E[3];
+  uint32_t k;
+  uint64_t r = 0;
+  if (start == 0) {
+    if (w & OR_INFO_REUSE_LIGHT) {
+      double x1[3];
+      f2d(org, o);
+      f2d(ph[0].pos, x1);
+      sub3(x1, o, d);
+      normalize3(d);
+      for (int c = 0; c < 3; ++c) E[c] = ph[0].E[c];
+    } else {
+      double u[4];
+      rng4(seed, pid, 0, frame, u);
+      if (s->dm_c[l]) dm_restrict(s, l, w & 0xFFFFFu, u);   /* within the path's cell */
+      emit(L, u, o, d);
+      for (int c = 0; c < 3; ++c) org[c] = (float)o[c];
+      f2d(org, o);
+      for (int c = 0; c < 3; ++c) E[c] = (double)L->power[c] / (double)L->n_paths;
+    }
+    k = extend_path(s, pid, seed, frame, 0, o, d, E, 0.0, org, ph, ambv, &r, ch);
+  } else {
+    k = extend_path(s, pid, seed, frame, start, o, d, E, 0.0, org, ph, ambv, &r, ch);
+  }
+  *info = info_make(w & OR_INFO_CELL_MASK, k, 0, 0, 0);
+  return r;
+}
+
 void or_retrace(const or_scene* s, const uint32_t* ids, uint32_t n, uint64_t seed, uint32_t frame,
                 uint32_t* info, float* origin, or_photon* photons, uint32_t* ambv, or_stats* st) {
   uint64_t rays = 0;
 #pragma omp parallel for schedule(dynamic, 8) reduction(+ : rays)
-  for (uint32_t i = 0; i < n; ++i) {
-    uint32_t w = info[i];
-    if (!(w & OR_INFO_REPLACE)) continue;
-    uint32_t pid = ids[i];
-    uint32_t l = light_of(s, pid);
-    const or_light* L = &s->light[1][l];
-    uint32_t start = info_start(w);
-    or_photon* ph = photons + (size_t)i * s->B;
-    float* org = origin + 3 * (size_t)i;
-    double o[3], d[3], E[3];
-    uint32_t k;
-    uint64_t r = 0;
-    if (start == 0) {
-      if (w & OR_INFO_REUSE_LIGHT) {
-        double x1[3];
-        f2d(org, o);
-        f2d(ph[0].pos, x1);
-        sub3(x1, o, d);
-        normalize3(d);
-        for (int c = 0; c < 3; ++c) E[c] = ph[0].E[c];
-      } else {
-        double u[4];
-        rng4(seed, pid, 0, frame, u);
-        if (s->dm_c[l]) dm_restrict(s, l, w & 0xFFFFFu, u);   /* within the path's cell */
-        emit(L, u, o, d);
-        for (int c = 0; c < 3; ++c) org[c] = (float)o[c];
-        f2d(org, o);
-        for (int c = 0; c < 3; ++c) E[c] = (double)L->power[c] / (double)L->n_paths;
-      }
-      k = extend_path(s, pid, seed, frame, 0, o, d, E, 0.0, org, ph, &ambv[i], &r);
-    } else {
-      k = extend_path(s, pid, seed, frame, start, o, d, E, 0.0, org, ph, &ambv[i], &r);
-    }
-    rays += r;
-    info[i] = info_make(w & OR_INFO_CELL_MASK, k, 0, 0, 0);
-  }
+  for (uint32_t i = 0; i < n; ++i)
+    rays += retrace_path(s, ids[i], seed, frame, &info[i], origin + 3 * (size_t)i, photons + (size_t)i * s->B,
+                         &ambv[i], NULL);
   if (st) st->trace_rays += rays;
+}
+
+void or_retrace_path(const or_scene* s, uint32_t pid, uint64_t seed, uint32_t frame, uint32_t* info,
+                     float* origin, or_photon* photons, uint32_t* amb, or_choice* ch) {
+  retrace_path(s, pid, seed, frame, info, origin, photons, amb, ch);
+}
+
+int32_t or_verify_path(const or_scene* s, uint32_t pid, int32_t mode, double tau, uint32_t flags, uint32_t* info,
+                       float* origin, or_photon* photons, uint32_t* seg_mask, uint32_t* amb, or_choice* ch) {
+  for (uint32_t l = 0; l < s->n_lights; ++l)
+    if (s->dm_c[l]) return -1;
+  vcount c = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  uint8_t counted = 0;
+  verify_path(s, pid, mode, tau, flags, info, origin, photons, seg_mask, amb, &counted, &c, ch);
+  return 0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1305,7 +1447,7 @@ void or_splat(const or_scene* s, const uint32_t* ids, uint32_t n, const uint32_t
     normalize3(d);
     double t;
     int a = 0;
-    const int32_t prim = closest_hit(s, 1, pos, d, 0.0, -1, &t, &a);
+    const int32_t prim = closest_hit(s, 1, pos, d, 0.0, -1, &t, &a, NULL);
     amb[px] = (uint8_t)(a != 0);
     gprim[px] = prim;
     if (prim >= 0) {

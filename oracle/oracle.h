@@ -16,7 +16,9 @@
  * Alongside each result the oracle reports whether the result is ambiguous:
  * whether a perturbation of 1e-6 x scene diagonal (edge/plane proximity), a
  * near-tie in Eq. 2 or in the AreClose test of Alg. 1 could flip a decision.
- * Such paths are excluded from bit-exact comparison and counted.
+ * For such a path the per-path entry points below take a decision script and
+ * give, one run per script, every record the path admits when each ambiguous
+ * decision takes each of its possible outcomes.
  */
 #ifndef PV_ORACLE_H
 #define PV_ORACLE_H
@@ -213,6 +215,37 @@ void or_adjoint(const or_scene* s, const uint32_t* ids, uint32_t n, const uint32
  * prim id or -1, writes the distance, ambiguity flag. */
 int32_t or_closest_hit(const or_scene* s, const double o[3], const double d[3], double tlo,
                        int32_t exclude, double* t_out, int32_t* amb);
+
+/* Decision script of one path.  Where a decision is ambiguous (see above),
+ * alternative 0 is the FP64 decision and alternatives 1.. are the other
+ * outcomes a perturbation within the band could give: the other side of a
+ * box, plane, edge, light extent or Eq. 2 / AreClose threshold, the other
+ * facing side or orthonormal-basis branch, and for a closest hit every
+ * triangle that could be the nearest within the band (nearest first), or a
+ * miss.  The j-th ambiguous decision met takes script[j] (alternative 0 past
+ * the end of the script); ``pos`` counts the ambiguous decisions met so far
+ * and ``n_alt_next`` receives the number of alternatives of the first one
+ * past the script (left 0 if there is none).  With no script (NULL choice)
+ * every decision is the FP64 one. */
+typedef struct {
+  const uint8_t* script;
+  int32_t n_script;
+  int32_t pos;
+  int32_t n_alt_next;
+} or_choice;
+
+/* One path through one step under a decision script (``ch`` carries the
+ * script's position from call to call): the records of path ``pid`` --
+ * info, origin[3], photons[B], amb -- are updated in place exactly as
+ * or_trace / or_verify / or_retrace update them.  or_verify_path writes the
+ * intersected-segment mask and returns -1 (doing nothing) for a scene with a
+ * distribution map, whose prune and fill steps need every path at once. */
+void or_trace_path(const or_scene* s, uint32_t pid, uint64_t seed, uint32_t frame, uint32_t* info, float* origin,
+                   or_photon* photons, uint32_t* amb, or_choice* ch);
+int32_t or_verify_path(const or_scene* s, uint32_t pid, int32_t mode, double tau, uint32_t flags, uint32_t* info,
+                       float* origin, or_photon* photons, uint32_t* seg_mask, uint32_t* amb, or_choice* ch);
+void or_retrace_path(const or_scene* s, uint32_t pid, uint64_t seed, uint32_t frame, uint32_t* info,
+                     float* origin, or_photon* photons, uint32_t* amb, or_choice* ch);
 
 /* Number of OpenMP threads the oracle uses. */
 int32_t or_num_threads(void);

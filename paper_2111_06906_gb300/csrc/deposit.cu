@@ -9,8 +9,9 @@ namespace {
 
 __global__ void __launch_bounds__(256) k_deposit(uint32_t n, uint32_t B, const uint32_t* info, const float4* pa,
                                                  const float4* pb, pv_atlas at) {
+  const AtlasMap am = atlas_map(at);
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
-    deposit_path(at, n, B, info, pa, pb, p);
+    deposit_path(am, n, B, info, pa, pb, p);
 }
 
 }  // namespace

@@ -2,7 +2,7 @@
 // fused continuation + re-trace + deposit kernel (trace.cu): every stored
 // photon's incident energy goes to the texel of its position in a top-down
 // XZ atlas, accumulated in unsigned 64-bit fixed point (E * 2^scale_log2,
-// exact power-of-two scaling then round to nearest) so that the sum does not
+// exact power-of-two scaling then round to nearest even) so that the sum does not
 // depend on the order of the atomics.  The texel decision is made in FP32
 // with explicitly rounded operations (no fused multiply-add).
 #pragma once
@@ -10,8 +10,10 @@
 
 namespace pvk {
 
-__device__ __forceinline__ int atlas_texel(float p, float lo, float hi, uint32_t res) {
-  const float scale = __fdiv_rn((float)res, __fsub_rn(hi, lo));
+// Texel of coordinate p over [lo, hi) with res texels, given the mapping's
+// scale = res / (hi - lo) (correctly rounded FP32 division, computed once per
+// atlas by AtlasMap): explicitly rounded FP32, no fused multiply-add.
+__device__ __forceinline__ int atlas_texel(float p, float lo, float scale, uint32_t res) {
   const float u = __fmul_rn(__fsub_rn(p, lo), scale);
   const float f = floorf(u);
   if (!(f >= 0.0f)) return 0;
@@ -19,31 +21,66 @@ __device__ __forceinline__ int atlas_texel(float p, float lo, float hi, uint32_t
   return (int)f;
 }
 
+// An atlas with its two texel scales, worked out once per thread.
+struct AtlasMap {
+  pv_atlas at;
+  float sx, sz;
+};
+
+__device__ __forceinline__ AtlasMap atlas_map(const pv_atlas& at) {
+  AtlasMap m;
+  m.at = at;
+  m.sx = __fdiv_rn((float)at.width, __fsub_rn(at.x1, at.x0));
+  m.sz = __fdiv_rn((float)at.height, __fsub_rn(at.z1, at.z0));
+  return m;
+}
+
+// E * 2^s rounded to the nearest integer, ties to even, saturated to the
+// unsigned 64-bit range: the value of float E is m * 2^(e - 150) with its
+// 24-bit significand m, so the fixed-point value is m shifted by e - 150 + s,
+// rounded on the bits shifted out.  Integer operations only: a float to
+// 64-bit integer conversion instruction runs on the FP64 pipe, which is
+// narrow on this GPU.  E <= 0 and NaN give 0, +inf gives 2^64 - 1.
+__device__ __forceinline__ unsigned long long fixed_point(float E, int s) {
+  const uint32_t b = __float_as_uint(E);
+  if ((int32_t)b <= 0) return 0ull;                           // +0, negative numbers, negative NaNs
+  const uint32_t ex = b >> 23;
+  if (ex == 255u) return (b & 0x7FFFFFu) ? 0ull : ~0ull;      // NaN, +inf
+  const uint32_t m = ex ? (b & 0x7FFFFFu) | 0x800000u : b;    // subnormals: exponent 1, no hidden bit
+  const int sh = (int)(ex ? ex : 1u) - 150 + s;               // value = m * 2^sh
+  if (sh >= 0) return sh > 40 ? ~0ull : (unsigned long long)m << sh;   // m < 2^24: fits for sh <= 40
+  const int r = -sh;
+  if (r > 24) return 0ull;                                    // value < 2^24 / 2^25 = 1 / 2
+  const uint32_t q = m >> r;
+  const uint32_t rem = m & ((1u << r) - 1u), half = 1u << (r - 1);
+  return q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u);
+}
+
 // The first L photons of path p into the atlas, added (kSub false) or taken
 // back out (kSub true: the same fixed-point values, negated modulo 2^64, so
 // that a deposit followed by its removal leaves every texel's sum as it was).
 template <bool kSub = false>
-__device__ __forceinline__ void deposit_rows(const pv_atlas& at, uint32_t n, uint32_t L, const float4* pa,
+__device__ __forceinline__ void deposit_rows(const AtlasMap& am, uint32_t n, uint32_t L, const float4* pa,
                                              const float4* pb, uint32_t p) {
+  const pv_atlas& at = am.at;
   for (uint32_t k = 0; k < L; ++k) {
     // streaming loads: the path buffers must not evict the atlas from L2
     const float4 x = __ldcs(pa + (size_t)k * n + p);
     const float4 e = __ldcs(pb + (size_t)k * n + p);
-    const int tx = atlas_texel(x.x, at.x0, at.x1, at.width);
-    const int tz = atlas_texel(x.z, at.z0, at.z1, at.height);
+    const int tx = atlas_texel(x.x, at.x0, am.sx, at.width);
+    const int tz = atlas_texel(x.z, at.z0, am.sz, at.height);
     unsigned long long* t = reinterpret_cast<unsigned long long*>(at.data) + 3 * ((size_t)tz * at.width + tx);
-    const unsigned long long v[3] = {__float2ull_rn(ldexpf(e.x, at.scale_log2)),
-                                     __float2ull_rn(ldexpf(e.y, at.scale_log2)),
-                                     __float2ull_rn(ldexpf(e.z, at.scale_log2))};
+    const unsigned long long v[3] = {fixed_point(e.x, at.scale_log2), fixed_point(e.y, at.scale_log2),
+                                     fixed_point(e.z, at.scale_log2)};
 #pragma unroll
     for (int c = 0; c < 3; ++c) atomicAdd(t + c, kSub ? 0ull - v[c] : v[c]);
   }
 }
 
 // The photons of path p (its info word's count, at most B) into the atlas.
-__device__ __forceinline__ void deposit_path(const pv_atlas& at, uint32_t n, uint32_t B, const uint32_t* info,
+__device__ __forceinline__ void deposit_path(const AtlasMap& am, uint32_t n, uint32_t B, const uint32_t* info,
                                              const float4* pa, const float4* pb, uint32_t p) {
-  deposit_rows<false>(at, n, min(info_nseg(__ldcs(info + p)), B), pa, pb, p);
+  deposit_rows<false>(am, n, min(info_nseg(__ldcs(info + p)), B), pa, pb, p);
 }
 
 }  // namespace pvk

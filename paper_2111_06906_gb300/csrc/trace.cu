@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_CONT_TRACE_MIN_BLOCKS)
   uint32_t c_rays = 0, c_photons = 0;
   for (uint32_t guard = 0; guard < (1u << 30); ++guard) {
     if (kDeposit && dep != 0xFFFFFFFFu) {
-      deposit_path(D.at, A.n, sv.B, A.info, A.pa, A.pb, dep);
+      deposit_path(atlas_map(D.at), A.n, sv.B, A.info, A.pa, A.pb, dep);   // scales per path: no registers held
       dep = 0xFFFFFFFFu;
     }
     const bool need = !has_ray && !exhausted;

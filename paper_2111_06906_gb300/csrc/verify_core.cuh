@@ -197,7 +197,7 @@ __device__ __forceinline__ void mark_touched(const VerifyArgs& A, uint32_t p, bo
   if (!A.touched) return;
   const uint8_t code = touched_code(touched, v);
   A.touched[p] = code;
-  if (code && A.sub.data) deposit_rows<true>(A.sub, A.n, code - 1u, A.pa, A.pb, p);
+  if (code && A.sub.data) deposit_rows<true>(atlas_map(A.sub), A.n, code - 1u, A.pa, A.pb, p);
 }
 
 // Sec. 3.1 "update path origins" for path p (< A.n): the moved light's

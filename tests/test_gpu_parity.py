@@ -169,6 +169,83 @@ def test_deposit_parity_tiny_box():
     pv.pv_destroy_scene(h)
 
 
+def _exact_atlas(info, pa, pb, W, H, rect, S):
+    """The deposit's definition on the host: texel from FP32 arithmetic without
+    fused operations, energy E * 2^S rounded to the nearest integer (ties to
+    even; exact in float64 for the values used here), summed in uint64."""
+    f32 = np.float32
+    sx = f32(W) / (f32(rect[2]) - f32(rect[0]))
+    sz = f32(H) / (f32(rect[3]) - f32(rect[1]))
+    L = np.minimum((info >> 22) & 15, pa.shape[0])
+    k, p = np.nonzero(np.arange(pa.shape[0])[:, None] < L[None, :])
+    x, z, E = pa[k, p, 0], pa[k, p, 2], pb[k, p, :3]
+
+    def texel(c, lo, sc, res):
+        f = np.floor((c - f32(lo)) * sc)
+        return np.where(f >= 0, np.minimum(f, res - 1), 0).astype(np.int64)
+
+    t = texel(z, rect[1], sz, H) * W + texel(x, rect[0], sx, W)
+    v = np.rint(E.astype(np.float64) * 2.0 ** S)
+    assert v.max() < 2.0 ** 53
+    out = np.zeros((H * W, 3), np.uint64)
+    np.add.at(out, t, v.astype(np.uint64))
+    return out.reshape(H, W, 3)
+
+
+def test_deposit_fixed_point_exact_tiny_box():
+    """Every texel of pv_deposit equals the exact integer sum of the rounded
+    fixed-point photon energies (no tolerance)."""
+    torch = _t()
+    sc = scenes.tiny_box()
+    h = gu.lib_scene(sc)
+    P = pv.Paths.allocate(sc.n_paths, sc.max_bounces)
+    pv.pv_trace_all(h, P, 1, 1)
+    W = H = 256
+    S = 31
+    atlas = torch.zeros(H, W, 3, dtype=torch.int64, device="cuda")
+    pv.pv_deposit(h, P, atlas, sc.atlas_rect, S)
+    want = _exact_atlas(P.info.cpu().numpy().view(np.uint32), P.pa.cpu().numpy(), P.pb.cpu().numpy(), W, H,
+                        sc.atlas_rect, S)
+    assert np.array_equal(atlas.cpu().numpy().view(np.uint64), want)
+    assert (want > 0).sum() > 1000
+    pv.pv_destroy_scene(h)
+
+
+def test_deposit_fixed_point_rounding_cases():
+    """Energies at the edges of the fixed-point rounding -- zero, subnormals,
+    exact halves (ties go to the even neighbour), the largest values below
+    2^(53-S), and random magnitudes over many exponents -- deposited through
+    pv_deposit equal the exact rounded sums."""
+    torch = _t()
+    n, B, S = 4096, 2, 31
+    lights = lambda f: [scenes.Light(scenes.LIGHT_POINT, (0.0, 1.0, 0.0), n_paths=n)]
+    sc = kit.build([(kit.quad((-1, 0, -1), (0, 0, 2), (2, 0, 0)), (0.5,) * 3, False)], lights, B=B, diag=3.0)
+    h = gu.lib_scene(sc)
+    P = pv.Paths.allocate(n, B)
+    rng = np.random.default_rng(5)
+    q = np.float32(2.0 ** -S)
+    special = np.array([0.0, 1e-45, 1e-40, 0.5 * q, 1.5 * q, 2.5 * q, 3.5 * q, 0.49999997 * q, 0.50000006 * q,
+                        q, 1e-3, 0.1, 1.0, 2.0 ** 21 - 1.0, 3.0e6, 4194303.5, 1.25 * q, 7.5 * q],
+                       np.float32)
+    E = np.exp2(rng.uniform(-40, 21, (B, n, 3))).astype(np.float32)
+    E.reshape(-1)[:special.size * 4] = np.tile(special, 4)
+    pos = rng.uniform(-1.0, 1.0, (B, n, 3)).astype(np.float32)
+    pa = np.concatenate([pos, np.zeros((B, n, 1), np.float32)], -1)
+    pb = np.concatenate([E, np.ones((B, n, 1), np.float32)], -1)
+    ids = np.arange(n)
+    info = (np.where(ids < 64, 2, ids % 3).astype(np.uint32) << 22)   # 0, 1 or 2 photons; the first 64 paths two
+    P.info.copy_(torch.as_tensor(info.view(np.int32), device="cuda"))
+    P.pa.copy_(torch.as_tensor(pa, device="cuda"))
+    P.pb.copy_(torch.as_tensor(pb, device="cuda"))
+    W = H = 64
+    rect = (-1.0, -1.0, 1.0, 1.0)
+    atlas = torch.zeros(H, W, 3, dtype=torch.int64, device="cuda")
+    pv.pv_deposit(h, P, atlas, rect, S)
+    want = _exact_atlas(info, pa, pb, W, H, rect, S)
+    assert np.array_equal(atlas.cpu().numpy().view(np.uint64), want)
+    pv.pv_destroy_scene(h)
+
+
 @pytest.mark.parametrize("n", [1, 31, 4095, 4096, 4097, 3 * 4096 + 5, 100_003])
 def test_compaction_sizes(n):
     torch = _t()
