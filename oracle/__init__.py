@@ -76,10 +76,15 @@ class Camera(C.Structure):
 class _Stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "paths", "segments_tested", "segments_amb", "vis_rays", "cont_rays", "trace_rays",
-        "energy_tests", "energy_amb", "n_reemit", "n_tail", "n_updated", "n_truncated", "n_pruned", "n_filled")]
+        "energy_tests", "energy_amb", "n_reemit", "n_tail", "n_updated", "n_truncated", "n_pruned", "n_filled",
+        "rays_amb")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class _Choice(C.Structure):
+    _fields_ = [("script", C.c_void_p), ("n_script", C.c_int32), ("pos", C.c_int32), ("n_alt_next", C.c_int32)]
 
 
 _lib = None
@@ -121,6 +126,10 @@ def lib():
         L.or_closest_hit.restype = C.c_int32
         L.or_closest_hit.argtypes = [P, P, P, C.c_double, C.c_int32, P, P]
         L.or_num_threads.restype = C.c_int32
+        L.or_trace_path.argtypes = [P, C.c_uint32, C.c_uint64, C.c_uint32, P, P, P, P, P]
+        L.or_verify_path.restype = C.c_int32
+        L.or_verify_path.argtypes = [P, C.c_uint32, C.c_int32, C.c_double, C.c_uint32, P, P, P, P, P, P]
+        L.or_retrace_path.argtypes = [P, C.c_uint32, C.c_uint64, C.c_uint32, P, P, P, P, P]
         L.or_theta_size.restype = C.c_uint32
         L.or_theta_size.argtypes = [P]
         L.or_theta_current.argtypes = [P, P]
@@ -163,13 +172,55 @@ def _lights(ls):
 
 @dataclass
 class Paths:
-    """Oracle-side path records for a subset of path ids."""
+    """Oracle-side path records for a subset of path ids.
+
+    For the paths whose decisions may be ambiguous the records also carry
+    what is needed to list their admissible outcomes: ``snap`` holds the
+    records at the last point they were checked (or uploaded), ``pending``
+    the steps applied since, and ``branches`` -- for paths that met an
+    ambiguous decision earlier -- the oracle records, at ``snap`` time, that
+    every check so far has accepted (see ``OracleScene.outcomes``)."""
     ids: np.ndarray                 # uint32 [n]
     info: np.ndarray                # uint32 [n]
     origin: np.ndarray              # float32 [n,3]
     photons: np.ndarray             # float32 [n,B,8]
     amb: np.ndarray                 # uint32 [n] ambiguity bits (accumulated)
     stats: dict = field(default_factory=dict)
+    snap: tuple = None              # (info, origin, photons) at the last check; None: before the first trace
+    pending: list = field(default_factory=list)     # steps since snap: (kind, frames, args)
+    branches: dict = field(default_factory=dict)    # position -> [(info, origin, photons)] at snap time
+    oracle: object = field(default=None, repr=False)
+
+    def record(self, i: int):
+        return int(self.info[i]), self.origin[i].copy(), self.photons[i].copy()
+
+    def subset(self, idx) -> "Paths":
+        """The paths at positions ``idx``, with their snapshot, pending steps
+        and accepted branches."""
+        idx = np.asarray(idx, np.int64)
+        pos = {int(j): k for k, j in enumerate(idx)}
+        snap = None if self.snap is None else tuple(a[idx].copy() for a in self.snap)
+        br = {pos[i]: list(v) for i, v in self.branches.items() if i in pos}
+        return Paths(self.ids[idx].copy(), self.info[idx].copy(), self.origin[idx].copy(), self.photons[idx].copy(),
+                     self.amb[idx].copy(), dict(self.stats), snap, list(self.pending), br, self.oracle)
+
+    def adopt_branches(self) -> None:
+        """Paths with an ambiguous decision take the first record the last
+        check accepted (an oracle record: the outcome the device's result
+        agreed with) in place of the oracle's default outcome; e.g. before
+        comparing quantities computed from the records, such as a deposit."""
+        for i, recs in self.branches.items():
+            self.info[i], self.origin[i], self.photons[i] = recs[0][0], recs[0][1], recs[0][2]
+            if self.snap is not None:
+                self.snap[0][i], self.snap[1][i], self.snap[2][i] = recs[0][0], recs[0][1], recs[0][2]
+            self.branches[i] = [recs[0]]
+
+    def rebase(self) -> None:
+        """The current records become the shared starting point (e.g. after
+        uploading them to the device): no pending steps, no branches."""
+        self.snap = (self.info.copy(), self.origin.copy(), self.photons.copy())
+        self.pending = []
+        self.branches = {}
 
     @property
     def nseg(self) -> np.ndarray:
@@ -184,8 +235,10 @@ class Paths:
         return self.photons[..., 3].view(np.int32)
 
     def copy(self) -> "Paths":
+        snap = None if self.snap is None else tuple(a.copy() for a in self.snap)
         return Paths(self.ids.copy(), self.info.copy(), self.origin.copy(), self.photons.copy(),
-                     self.amb.copy(), dict(self.stats))
+                     self.amb.copy(), dict(self.stats), snap, list(self.pending),
+                     {k: list(v) for k, v in self.branches.items()}, self.oracle)
 
 
 class OracleScene:
@@ -203,6 +256,7 @@ class OracleScene:
         self._h = L.or_scene_create(_p(v), scene.n_tris, _p(to), scene.n_objects, _p(dy), _p(al),
                                     float(scene.diag), self.B)
         self.frames = None
+        self._poses = None
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -220,7 +274,13 @@ class OracleScene:
         lo, ln = _lights(lights_old), _lights(lights_new)
         lib().or_scene_set_poses(self._h, _p(xo), _p(xn), C.cast(lo, C.c_void_p),
                                  C.cast(ln, C.c_void_p), len(lights_new))
+        self._poses = (xo, xn, list(lights_old), list(lights_new))
         self.frames = None
+
+    def _restore_poses(self, poses, frames) -> None:
+        if poses is not None:
+            self.set_poses(*poses)
+        self.frames = frames
 
     def trace(self, ids, seed: int, frame: int) -> Paths:
         ids = np.ascontiguousarray(ids, np.uint32)
@@ -231,6 +291,8 @@ class OracleScene:
         lib().or_trace(self._h, _p(ids), n, seed, frame, _p(p.info), _p(p.origin), _p(p.photons),
                        _p(p.amb), C.byref(st))
         p.stats = st.as_dict()
+        p.oracle = self
+        p.pending = [("trace", self.frames, (int(seed), int(frame)))]
         return p
 
     def verify(self, paths: Paths, mode: int, tau: float, flags: int = 0, seed: int = 0, frame: int = 0):
@@ -244,6 +306,7 @@ class OracleScene:
         lib().or_verify(self._h, _p(paths.ids), n, mode, float(tau), flags, int(seed), int(frame), _p(paths.info),
                         _p(paths.origin), _p(paths.photons), _p(mask), _p(amb), C.byref(st))
         paths.amb |= amb
+        paths.pending.append(("verify", self.frames, (int(mode), float(tau), int(flags))))
         return mask, st.as_dict()
 
     def retrace(self, paths: Paths, seed: int, frame: int) -> dict:
@@ -253,7 +316,70 @@ class OracleScene:
         lib().or_retrace(self._h, _p(paths.ids), n, seed, frame, _p(paths.info), _p(paths.origin),
                          _p(paths.photons), _p(amb), C.byref(st))
         paths.amb |= amb
+        paths.pending.append(("retrace", self.frames, (int(seed), int(frame))))
         return st.as_dict()
+
+    # ---- admissible outcomes of the paths whose decisions are ambiguous
+    def run_path(self, steps, pid: int, rec, script=()):
+        """``steps`` (kind, frames, args) applied to one path record under a
+        decision script; returns ((info, origin, photons), n_alt_next), or
+        None when a step cannot run per path (a distribution map, or poses
+        not set through set_frames)."""
+        L = lib()
+        info = np.array([rec[0]], np.uint32)
+        org = np.ascontiguousarray(rec[1], np.float32).copy()
+        ph = np.ascontiguousarray(rec[2], np.float32).copy()
+        amb = np.zeros(1, np.uint32)
+        mask = np.zeros(1, np.uint32)
+        sc = np.ascontiguousarray(script, np.uint8)
+        ch = _Choice(sc.ctypes.data if sc.size else None, int(sc.size), 0, 0)
+        for kind, frames, args in steps:
+            if frames is None:
+                return None
+            if self.frames != frames:
+                self.set_frames(*frames)
+            if kind == "trace":
+                L.or_trace_path(self._h, pid, args[0], args[1], _p(info), _p(org), _p(ph), _p(amb), C.byref(ch))
+            elif kind == "verify":
+                if L.or_verify_path(self._h, pid, args[0], args[1], args[2], _p(info), _p(org), _p(ph), _p(mask),
+                                    _p(amb), C.byref(ch)) != 0:
+                    return None
+            else:
+                L.or_retrace_path(self._h, pid, args[0], args[1], _p(info), _p(org), _p(ph), _p(amb), C.byref(ch))
+        return (int(info[0]), org, ph), int(ch.n_alt_next)
+
+    def outcomes(self, steps, pid: int, rec, max_runs: int = 96, max_depth: int = 12):
+        """Every record path ``pid`` can end with when ``steps`` run from record
+        ``rec`` and each ambiguous decision takes each of its admissible
+        outcomes (depth-first over decision scripts).  Returns (records,
+        complete); complete is False when the run or depth bound cut the
+        search, and records is None when the steps cannot run per path.  The
+        scene's poses are as before on return."""
+        poses, frames = getattr(self, "_poses", None), self.frames
+        try:
+            return self._outcomes(steps, pid, rec, max_runs, max_depth)
+        finally:
+            if self.frames != frames:
+                self._restore_poses(poses, frames)
+
+    def _outcomes(self, steps, pid, rec, max_runs, max_depth):
+        out, stack, runs = [], [()], 0
+        while stack:
+            script = stack.pop()
+            r = self.run_path(steps, pid, rec, script)
+            if r is None:
+                return None, False
+            runs += 1
+            rec_out, n_alt = r
+            if n_alt == 0 or len(script) >= max_depth:
+                out.append(rec_out)
+                if n_alt:
+                    return out, False
+            else:
+                stack.extend(script + (c,) for c in reversed(range(n_alt)))
+            if runs >= max_runs and stack:
+                return out, False
+        return out, True
 
     # ---- screen-space splat (Fig. 2 splat/gather, radius kernel)
     def splat(self, paths: Paths, cam: "Camera", radius: float):

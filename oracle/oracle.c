@@ -753,10 +753,11 @@ void or_dm_set_counts(or_scene* s, uint32_t light, const uint32_t* in) {
  * stored already.  For k == 0 the first ray (o, d) carrying E is given;
  * for k >= 1 the path first scatters at photon k (Russian roulette with
  * q = max albedo, cosine-weighted direction about the facing normal,
- * E_{k+1} = E_k * albedo / q).  Returns the new photon count. */
+ * E_{k+1} = E_k * albedo / q).  Returns the new photon count; rays[0]
+ * counts the rays traced, rays[1] those whose answer is ambiguous. */
 static uint32_t extend_path(const or_scene* s, uint32_t pid, uint64_t seed, uint32_t frame, uint32_t k,
                             double* o, double* d, double* E, double radius, const float* origin,
-                            or_photon* ph, uint32_t* amb, uint64_t* rays, or_choice* ch) {
+                            or_photon* ph, uint32_t* amb, uint64_t rays[2], or_choice* ch) {
   int32_t excl = -1;
   for (;;) {
     if (k >= 1) {
@@ -786,8 +787,11 @@ static uint32_t extend_path(const or_scene* s, uint32_t pid, uint64_t seed, uint
     double t;
     int a = 0;
     int32_t prim = closest_hit(s, 1, o, d, s->tmin, excl, &t, &a, ch);
-    (*rays)++;
-    if (a) *amb |= OR_AMB_TRACE;
+    rays[0]++;
+    if (a) {
+      *amb |= OR_AMB_TRACE;
+      rays[1]++;
+    }
     if (prim < 0) break;
     or_photon* v = &ph[k];
     for (int c = 0; c < 3; ++c) {
@@ -801,9 +805,9 @@ static uint32_t extend_path(const or_scene* s, uint32_t pid, uint64_t seed, uint
   return k;
 }
 
-/* One path traced from the light; returns its rays. */
-static uint64_t trace_path(const or_scene* s, uint32_t pid, uint64_t seed, uint32_t frame, uint32_t* info,
-                           float* org, or_photon* ph, uint32_t* amb, or_choice* ch) {
+/* One path traced from the light; adds its rays and ambiguous rays to rays[2]. */
+static void trace_path(const or_scene* s, uint32_t pid, uint64_t seed, uint32_t frame, uint32_t* info,
+                       float* org, or_photon* ph, uint32_t* amb, uint64_t rays[2], or_choice* ch) {
   uint32_t l = light_of(s, pid);
   const or_light* L = &s->light[1][l];
   double u[4], o[3], d[3], E[3];
@@ -818,28 +822,32 @@ static uint64_t trace_path(const or_scene* s, uint32_t pid, uint64_t seed, uint3
   for (int c = 0; c < 3; ++c) org[c] = (float)o[c];
   f2d(org, o);
   *amb = 0;
-  uint64_t r = 0;
-  uint32_t k = extend_path(s, pid, seed, frame, 0, o, d, E, 0.0, org, ph, amb, &r, ch);
+  uint32_t k = extend_path(s, pid, seed, frame, 0, o, d, E, 0.0, org, ph, amb, rays, ch);
   *info = info_make((l << 20) | cell, k, 0, 0, 0);
-  return r;
 }
 
 void or_trace(const or_scene* s, const uint32_t* ids, uint32_t n, uint64_t seed, uint32_t frame,
               uint32_t* info, float* origin, or_photon* photons, uint32_t* amb, or_stats* st) {
-  uint64_t rays = 0;
-#pragma omp parallel for schedule(dynamic, 8) reduction(+ : rays)
-  for (uint32_t i = 0; i < n; ++i)
-    rays += trace_path(s, ids[i], seed, frame, &info[i], origin + 3 * (size_t)i, photons + (size_t)i * s->B, &amb[i],
-                       NULL);
+  uint64_t rays = 0, rays_a = 0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : rays, rays_a)
+  for (uint32_t i = 0; i < n; ++i) {
+    uint64_t r[2] = {0, 0};
+    trace_path(s, ids[i], seed, frame, &info[i], origin + 3 * (size_t)i, photons + (size_t)i * s->B, &amb[i], r,
+               NULL);
+    rays += r[0];
+    rays_a += r[1];
+  }
   if (st) {
     st->paths += n;
     st->trace_rays += rays;
+    st->rays_amb += rays_a;
   }
 }
 
 void or_trace_path(const or_scene* s, uint32_t pid, uint64_t seed, uint32_t frame, uint32_t* info, float* origin,
                    or_photon* photons, uint32_t* amb, or_choice* ch) {
-  trace_path(s, pid, seed, frame, info, origin, photons, amb, ch);
+  uint64_t r[2] = {0, 0};
+  trace_path(s, pid, seed, frame, info, origin, photons, amb, r, ch);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -916,7 +924,7 @@ static int seg_vs_moved(const or_scene* s, int mode, uint32_t flags, const doubl
 
 /* per-path counters of a verification */
 typedef struct {
-  uint64_t seg_t, seg_a, vis, cont, et, ea, nre, ntail, nupd, ntr;
+  uint64_t seg_t, seg_a, vis, cont, et, ea, nre, ntail, nupd, ntr, rays_a;
 } vcount;
 
 /* One path of or_verify (everything before the distribution-map steps):
@@ -955,7 +963,10 @@ static void verify_path(const or_scene* s, uint32_t pid, int32_t mode, double ta
       int am = 0;
       seg1_blocked = any_hit(s, 1, NULL, 0, a, b, ph[0].prim, &am, ch);
       vc->vis++;
-      if (am) amb |= OR_AMB_VERIFY;
+      if (am) {
+        amb |= OR_AMB_VERIFY;
+        vc->rays_a++;
+      }
     } else {
       double x1[3], o0[3], d[3], c[3], nn[3], tt[3], bb[3], no[3];
       f2d(ph[0].pos, x1);
@@ -1092,7 +1103,10 @@ static void verify_path(const or_scene* s, uint32_t pid, int32_t mode, double ta
     int am = 0;
     int32_t pn = closest_hit(s, 1, a, d, s->tmin, excl, &t, &am, ch);
     vc->cont++;
-    if (am) amb |= OR_AMB_CONT;
+    if (am) {
+      amb |= OR_AMB_CONT;
+      vc->rays_a++;
+    }
     if (pn < 0) {                       /* nothing hit: the path ends here */
       L = seg - 1;
       vc->ntr++;
@@ -1185,16 +1199,16 @@ static void verify_path(const or_scene* s, uint32_t pid, int32_t mode, double ta
 void or_verify(const or_scene* s, const uint32_t* ids, uint32_t n, int32_t mode, double tau,
                uint32_t flags, uint64_t seed, uint32_t frame, uint32_t* info, float* origin, or_photon* photons,
                uint32_t* seg_mask, uint32_t* ambv, or_stats* st) {
-  uint64_t seg_t = 0, seg_a = 0, vis = 0, cont = 0, et = 0, ea = 0, nre = 0, ntail = 0, nupd = 0, ntr = 0;
+  uint64_t seg_t = 0, seg_a = 0, vis = 0, cont = 0, et = 0, ea = 0, nre = 0, ntail = 0, nupd = 0, ntr = 0, rays_a = 0;
   /* paths of a moved light with a distribution map that keep their origin (counted in DM_C) */
   uint8_t* counted = (uint8_t*)calloc(n ? n : 1, 1);
-#pragma omp parallel for schedule(dynamic, 8) reduction(+ : seg_t, seg_a, vis, cont, et, ea, nre, ntail, nupd, ntr)
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : seg_t, seg_a, vis, cont, et, ea, nre, ntail, nupd, ntr, rays_a)
   for (uint32_t i = 0; i < n; ++i) {
-    vcount c = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    vcount c = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     verify_path(s, ids[i], mode, tau, flags, &info[i], origin + 3 * (size_t)i, photons + (size_t)i * s->B,
                 &seg_mask[i], &ambv[i], &counted[i], &c, NULL);
     seg_t += c.seg_t; seg_a += c.seg_a; vis += c.vis; cont += c.cont; et += c.et;
-    ea += c.ea; nre += c.nre; ntail += c.ntail; nupd += c.nupd; ntr += c.ntr;
+    ea += c.ea; nre += c.nre; ntail += c.ntail; nupd += c.nupd; ntr += c.ntr; rays_a += c.rays_a;
   }
   /* ---- Compute DM_C, prune paths (Eq. 1, mark then edit), fill DM_C (Sec. 3.1) ---- */
   uint64_t npr = 0, nfi = 0;
@@ -1281,6 +1295,7 @@ void or_verify(const or_scene* s, const uint32_t* ids, uint32_t n, int32_t mode,
     st->n_tail += ntail;
     st->n_updated += nupd;
     st->n_truncated += ntr;
+    st->rays_amb += rays_a;
   }
 }
 
@@ -1291,17 +1306,16 @@ uint32_t or_compact(const uint32_t* info, uint32_t n, uint32_t* list) {
   return c;
 }
 
-/* One path of or_retrace; returns its rays. */
-static uint64_t retrace_path(const or_scene* s, uint32_t pid, uint64_t seed, uint32_t frame, uint32_t* info,
-                             float* org, or_photon* ph, uint32_t* ambv, or_choice* ch) {
+/* One path of or_retrace; adds its rays and ambiguous rays to rays[2]. */
+static void retrace_path(const or_scene* s, uint32_t pid, uint64_t seed, uint32_t frame, uint32_t* info,
+                         float* org, or_photon* ph, uint32_t* ambv, uint64_t rays[2], or_choice* ch) {
   uint32_t w = *info;
-  if (!(w & OR_INFO_REPLACE)) return 0;
+  if (!(w & OR_INFO_REPLACE)) return;
   uint32_t l = light_of(s, pid);
   const or_light* L = &s->light[1][l];
   uint32_t start = info_start(w);
   double o[3], d[3], E[3];
   uint32_t k;
-  uint64_t r = 0;
   if (start == 0) {
     if (w & OR_INFO_REUSE_LIGHT) {
       double x1[3];
@@ -1319,34 +1333,41 @@ static uint64_t retrace_path(const or_scene* s, uint32_t pid, uint64_t seed, uin
       f2d(org, o);
       for (int c = 0; c < 3; ++c) E[c] = (double)L->power[c] / (double)L->n_paths;
     }
-    k = extend_path(s, pid, seed, frame, 0, o, d, E, 0.0, org, ph, ambv, &r, ch);
+    k = extend_path(s, pid, seed, frame, 0, o, d, E, 0.0, org, ph, ambv, rays, ch);
   } else {
-    k = extend_path(s, pid, seed, frame, start, o, d, E, 0.0, org, ph, ambv, &r, ch);
+    k = extend_path(s, pid, seed, frame, start, o, d, E, 0.0, org, ph, ambv, rays, ch);
   }
   *info = info_make(w & OR_INFO_CELL_MASK, k, 0, 0, 0);
-  return r;
 }
 
 void or_retrace(const or_scene* s, const uint32_t* ids, uint32_t n, uint64_t seed, uint32_t frame,
                 uint32_t* info, float* origin, or_photon* photons, uint32_t* ambv, or_stats* st) {
-  uint64_t rays = 0;
-#pragma omp parallel for schedule(dynamic, 8) reduction(+ : rays)
-  for (uint32_t i = 0; i < n; ++i)
-    rays += retrace_path(s, ids[i], seed, frame, &info[i], origin + 3 * (size_t)i, photons + (size_t)i * s->B,
-                         &ambv[i], NULL);
-  if (st) st->trace_rays += rays;
+  uint64_t rays = 0, rays_a = 0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : rays, rays_a)
+  for (uint32_t i = 0; i < n; ++i) {
+    uint64_t r[2] = {0, 0};
+    retrace_path(s, ids[i], seed, frame, &info[i], origin + 3 * (size_t)i, photons + (size_t)i * s->B, &ambv[i], r,
+                 NULL);
+    rays += r[0];
+    rays_a += r[1];
+  }
+  if (st) {
+    st->trace_rays += rays;
+    st->rays_amb += rays_a;
+  }
 }
 
 void or_retrace_path(const or_scene* s, uint32_t pid, uint64_t seed, uint32_t frame, uint32_t* info,
                      float* origin, or_photon* photons, uint32_t* amb, or_choice* ch) {
-  retrace_path(s, pid, seed, frame, info, origin, photons, amb, ch);
+  uint64_t r[2] = {0, 0};
+  retrace_path(s, pid, seed, frame, info, origin, photons, amb, r, ch);
 }
 
 int32_t or_verify_path(const or_scene* s, uint32_t pid, int32_t mode, double tau, uint32_t flags, uint32_t* info,
                        float* origin, or_photon* photons, uint32_t* seg_mask, uint32_t* amb, or_choice* ch) {
   for (uint32_t l = 0; l < s->n_lights; ++l)
     if (s->dm_c[l]) return -1;
-  vcount c = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  vcount c = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   uint8_t counted = 0;
   verify_path(s, pid, mode, tau, flags, info, origin, photons, seg_mask, amb, &counted, &c, ch);
   return 0;

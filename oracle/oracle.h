@@ -89,6 +89,7 @@ typedef struct {
   uint64_t n_truncated;      /* paths shortened because a re-traced ray missed */
   uint64_t n_pruned;         /* paths pruned by Eq. 1 (distribution maps) */
   uint64_t n_filled;         /* free paths given a distribution-map cell to fill */
+  uint64_t rays_amb;         /* ray queries (trace, Alg. 1, visibility) whose answer is ambiguous */
 } or_stats;
 
 /* Scene: verts [n_tris][3][3] (object-local for dynamic objects),

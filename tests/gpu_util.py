@@ -1,6 +1,7 @@
 """Helpers for the GPU parity tests: build a library scene from a seeded
 scene, move path records between the oracle's AoS form and the library's
-SoA buffers, and compare them field by field."""
+SoA buffers, and compare them field by field (paths with an ambiguous
+decision against every outcome the oracle admits for them)."""
 from __future__ import annotations
 
 import numpy as np
@@ -20,7 +21,8 @@ def advance(h, sc, frame: int) -> None:
 
 
 def upload(paths: pv.Paths, op: oracle.Paths) -> None:
-    """Write oracle records (positions op.ids) into the device buffers."""
+    """Write oracle records (positions op.ids) into the device buffers; both
+    sides start from these records from now on (op is rebased)."""
     import torch
     ids = torch.as_tensor(op.ids.astype(np.int64), device=paths.info.device)
     paths.info[ids] = torch.as_tensor(op.info.view(np.int32), device=paths.info.device)
@@ -28,6 +30,7 @@ def upload(paths: pv.Paths, op: oracle.Paths) -> None:
     ph = np.ascontiguousarray(np.transpose(op.photons, (1, 0, 2)))      # [B, n, 8]
     paths.pa[:, ids] = torch.as_tensor(ph[..., 0:4].copy(), device=paths.info.device)
     paths.pb[:, ids] = torch.as_tensor(ph[..., 4:8].copy(), device=paths.info.device)
+    op.rebase()
 
 
 def download(paths: pv.Paths, ids=None) -> oracle.Paths:
@@ -44,40 +47,112 @@ def download(paths: pv.Paths, ids=None) -> oracle.Paths:
     return oracle.Paths(np.asarray(ids, np.uint32), info, origin, ph, np.zeros(len(ids), np.uint32))
 
 
-def compare(gpu: oracle.Paths, orc: oracle.Paths, diag: float, skip=None, pos_tol=1e-5, e_rtol=1e-5,
-            check_info_bits=True):
-    """Field-by-field comparison of two record sets (same ids), skipping the
-    paths the oracle marks ambiguous.  Returns a dict of counts; every
-    ``bad_*`` entry must be zero for parity."""
-    amb = orc.amb != 0
-    if skip is not None:
-        amb = amb | skip
-    ok = ~amb
-    r = {"n": int(len(gpu.ids)), "ambiguous": int(amb.sum())}
-    gi, oi = gpu.info[ok], orc.info[ok]
+def _mismatch(g_info, g_org, g_ph, o_info, o_org, o_ph, diag, pos_tol, e_rtol, check_info_bits):
+    """Per-path mismatch flags of record arrays (same shapes) and the largest
+    position and energy differences."""
     if check_info_bits:
-        r["bad_info"] = int((gi != oi).sum())
+        bad_info = g_info != o_info
     else:
-        r["bad_info"] = int((((gi >> 22) & 15) != ((oi >> 22) & 15)).sum())
-    L = np.minimum((gi >> 22) & 15, (oi >> 22) & 15)
-    B = gpu.photons.shape[1]
+        bad_info = ((g_info >> 22) & 15) != ((o_info >> 22) & 15)
+    L = np.minimum((g_info >> 22) & 15, (o_info >> 22) & 15)
+    B = g_ph.shape[1]
     kk = np.arange(B)[None, :] < L[:, None]
-    gp, op = gpu.photons[ok], orc.photons[ok]
-    r["bad_prim"] = int(((gp[..., 3].view(np.int32) != op[..., 3].view(np.int32)) & kk).sum())
-    dpos = np.abs(gp[..., :3].astype(np.float64) - op[..., :3]).max(axis=-1)
-    r["bad_pos"] = int(((dpos > pos_tol * diag) & kk).sum())
-    r["max_dpos_over_diag"] = float((dpos * kk).max() / diag) if kk.any() else 0.0
-    eo = op[..., 4:7].astype(np.float64)
-    de = np.abs(gp[..., 4:7] - eo) / np.maximum(np.abs(eo), 1e-30)
-    r["bad_energy"] = int(((de > e_rtol).any(axis=-1) & kk).sum())
-    r["max_rel_denergy"] = float((de.max(axis=-1) * kk).max()) if kk.any() else 0.0
-    drad = np.abs(gp[..., 7].astype(np.float64) - op[..., 7])
-    r["bad_radius"] = int(((drad > e_rtol * np.abs(op[..., 7]) + pos_tol * diag) & kk).sum())
-    do = np.abs(gpu.origin[ok].astype(np.float64) - orc.origin[ok]).max(axis=-1)
-    r["bad_origin"] = int((do > pos_tol * diag).sum())
+    bad_prim = ((g_ph[..., 3].view(np.int32) != o_ph[..., 3].view(np.int32)) & kk).any(1)
+    dpos = np.abs(g_ph[..., :3].astype(np.float64) - o_ph[..., :3]).max(axis=-1)
+    bad_pos = ((dpos > pos_tol * diag) & kk).any(1)
+    eo = o_ph[..., 4:7].astype(np.float64)
+    de = np.abs(g_ph[..., 4:7] - eo) / np.maximum(np.abs(eo), 1e-30)
+    bad_energy = ((de > e_rtol).any(axis=-1) & kk).any(1)
+    drad = np.abs(g_ph[..., 7].astype(np.float64) - o_ph[..., 7])
+    bad_radius = ((drad > e_rtol * np.abs(o_ph[..., 7]) + pos_tol * diag) & kk).any(1)
+    do = np.abs(g_org.astype(np.float64) - o_org).max(axis=-1)
+    bad_origin = do > pos_tol * diag
+    flags = {"info": bad_info, "prim": bad_prim, "pos": bad_pos, "energy": bad_energy, "radius": bad_radius,
+             "origin": bad_origin}
+    mx = {"max_dpos_over_diag": float((dpos * kk).max() / diag) if kk.any() else 0.0,
+          "max_rel_denergy": float((de.max(axis=-1) * kk).max()) if kk.any() else 0.0}
+    return flags, mx
+
+
+def compare(gpu: oracle.Paths, orc: oracle.Paths, diag: float, skip=None, pos_tol=1e-5, e_rtol=1e-5,
+            check_info_bits=True, sync=True):
+    """Field-by-field comparison of two record sets (same ids).  Paths with no
+    ambiguous decision must match the oracle's records.  A path the oracle
+    flags ambiguous (now or at an earlier check) must match one of the
+    records it admits: the oracle runs the steps since the last check from
+    each record accepted then, with every ambiguous decision taking each of
+    its admissible outcomes (oracle.OracleScene.outcomes).  With ``sync``
+    the accepted records are kept for the next check, and the oracle's own
+    records of those paths become the first accepted one, so that later
+    steps start from the outcome the device took.  ``skip`` excludes paths
+    altogether.  Returns a dict of counts; every ``bad_*`` entry must be
+    zero for parity, and ``ambiguous_unchecked`` counts flagged paths whose
+    steps cannot be listed per path (distribution maps)."""
+    n = int(len(gpu.ids))
+    tracked = np.zeros(n, bool)
+    if orc.branches:
+        tracked[list(orc.branches)] = True
+    amb = (orc.amb != 0) | tracked
+    skipped = np.zeros(n, bool) if skip is None else np.asarray(skip, bool)
+    ok = ~amb & ~skipped
+    r = {"n": n, "ambiguous": int((amb & ~skipped).sum()), "skipped": int(skipped.sum())}
+    flags, mx = _mismatch(gpu.info[ok], gpu.origin[ok], gpu.photons[ok], orc.info[ok], orc.origin[ok],
+                          orc.photons[ok], diag, pos_tol, e_rtol, check_info_bits)
+    for k, v in flags.items():
+        r["bad_" + k] = int(v.sum())
+    r.update(mx)
+    r["ambiguous_matched"] = r["bad_ambiguous"] = r["bad_unresolved"] = r["ambiguous_unchecked"] = 0
+    new_branches = {}
+    o = orc.oracle
+    B = orc.photons.shape[1]
+    for i in np.nonzero(amb & ~skipped)[0].tolist():
+        if orc.snap is None:
+            bases = [(0, np.zeros(3, np.float32), np.zeros((B, 8), np.float32))]
+        else:
+            bases = orc.branches.get(i) or [(int(orc.snap[0][i]), orc.snap[1][i], orc.snap[2][i])]
+        cands, complete, supported = [], True, o is not None
+        for base in bases if supported else []:
+            recs, comp = o.outcomes(orc.pending, int(orc.ids[i]), base)
+            if recs is None:
+                supported = False
+                break
+            cands += recs
+            complete &= comp
+        if not supported:
+            r["ambiguous_unchecked"] += 1
+            continue
+        ci = np.array([c[0] for c in cands], np.uint32)
+        co = np.array([c[1] for c in cands], np.float32).reshape(-1, 3)
+        cp = np.array([c[2] for c in cands], np.float32).reshape(-1, B, 8)
+        m = len(cands)
+        f, _ = _mismatch(np.repeat(gpu.info[i:i + 1], m), np.repeat(gpu.origin[i:i + 1], m, 0),
+                         np.repeat(gpu.photons[i:i + 1], m, 0), ci, co, cp, diag, pos_tol, e_rtol, check_info_bits)
+        good = ~np.any(np.stack(list(f.values())), axis=0) if m else np.zeros(0, bool)
+        if good.any():
+            r["ambiguous_matched"] += 1
+            new_branches[i] = [cands[j] for j in np.nonzero(good)[0]]
+        elif complete:
+            r["bad_ambiguous"] += 1
+        else:
+            r["bad_unresolved"] += 1
+    if sync and orc.oracle is not None:
+        orc.snap = (orc.info.copy(), orc.origin.copy(), orc.photons.copy())
+        orc.pending = []
+        orc.branches = new_branches
+        orc.adopt_branches()              # the oracle goes on from the outcome the device's result agreed with
     return r
 
 
-def assert_parity(r: dict) -> None:
+def assert_parity(r: dict, allow_unchecked: bool = False) -> None:
     bad = {k: v for k, v in r.items() if k.startswith("bad_") and v}
     assert not bad, r
+    assert allow_unchecked or r.get("ambiguous_unchecked", 0) == 0, r
+
+
+def ambiguous_share(*stats) -> float:
+    """Ambiguous queries over all queries in oracle counters (segment tests
+    against moved objects, plus trace, Alg. 1 and visibility rays)."""
+    amb = sum(s.get("segments_amb", 0) + s.get("rays_amb", 0) for s in stats)
+    tot = sum(s.get("segments_tested", 0) + s.get("trace_rays", 0) + s.get("cont_rays", 0) + s.get("vis_rays", 0)
+              for s in stats)
+    return amb / max(tot, 1)
