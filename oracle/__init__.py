@@ -84,7 +84,8 @@ class _Stats(C.Structure):
 
 
 class _Choice(C.Structure):
-    _fields_ = [("script", C.c_void_p), ("n_script", C.c_int32), ("pos", C.c_int32), ("n_alt_next", C.c_int32)]
+    _fields_ = [("script", C.c_void_p), ("n_script", C.c_int32), ("pos", C.c_int32), ("n_alt_next", C.c_int32),
+                ("open", C.c_int32)]
 
 
 _lib = None
@@ -190,6 +191,7 @@ class Paths:
     pending: list = field(default_factory=list)     # steps since snap: (kind, frames, args)
     branches: dict = field(default_factory=dict)    # position -> [(info, origin, photons)] at snap time
     oracle: object = field(default=None, repr=False)
+    opened: set = field(default_factory=set)         # positions whose admissible records could not be listed
 
     def record(self, i: int):
         return int(self.info[i]), self.origin[i].copy(), self.photons[i].copy()
@@ -202,7 +204,8 @@ class Paths:
         snap = None if self.snap is None else tuple(a[idx].copy() for a in self.snap)
         br = {pos[i]: list(v) for i, v in self.branches.items() if i in pos}
         return Paths(self.ids[idx].copy(), self.info[idx].copy(), self.origin[idx].copy(), self.photons[idx].copy(),
-                     self.amb[idx].copy(), dict(self.stats), snap, list(self.pending), br, self.oracle)
+                     self.amb[idx].copy(), dict(self.stats), snap, list(self.pending), br, self.oracle,
+                     {pos[i] for i in self.opened if i in pos})
 
     def adopt_branches(self) -> None:
         """Paths with an ambiguous decision take the first record the last
@@ -221,6 +224,7 @@ class Paths:
         self.snap = (self.info.copy(), self.origin.copy(), self.photons.copy())
         self.pending = []
         self.branches = {}
+        self.opened = set()
 
     @property
     def nseg(self) -> np.ndarray:
@@ -238,7 +242,7 @@ class Paths:
         snap = None if self.snap is None else tuple(a.copy() for a in self.snap)
         return Paths(self.ids.copy(), self.info.copy(), self.origin.copy(), self.photons.copy(),
                      self.amb.copy(), dict(self.stats), snap, list(self.pending),
-                     {k: list(v) for k, v in self.branches.items()}, self.oracle)
+                     {k: list(v) for k, v in self.branches.items()}, self.oracle, set(self.opened))
 
 
 class OracleScene:
@@ -322,9 +326,12 @@ class OracleScene:
     # ---- admissible outcomes of the paths whose decisions are ambiguous
     def run_path(self, steps, pid: int, rec, script=()):
         """``steps`` (kind, frames, args) applied to one path record under a
-        decision script; returns ((info, origin, photons), n_alt_next), or
-        None when a step cannot run per path (a distribution map, or poses
-        not set through set_frames)."""
+        decision script; returns ((info, origin, photons), n_alt_next, open),
+        or None when a step cannot run per path (a distribution map, or poses
+        not set through set_frames).  ``open``: a closest hit of the run met a
+        triangle whose crossing distance the band leaves undetermined over a
+        stretch of the ray (the ray runs within eps of its plane), so records
+        with a hit anywhere on that stretch are admissible as well."""
         L = lib()
         info = np.array([rec[0]], np.uint32)
         org = np.ascontiguousarray(rec[1], np.float32).copy()
@@ -332,7 +339,7 @@ class OracleScene:
         amb = np.zeros(1, np.uint32)
         mask = np.zeros(1, np.uint32)
         sc = np.ascontiguousarray(script, np.uint8)
-        ch = _Choice(sc.ctypes.data if sc.size else None, int(sc.size), 0, 0)
+        ch = _Choice(sc.ctypes.data if sc.size else None, int(sc.size), 0, 0, 0)
         for kind, frames, args in steps:
             if frames is None:
                 return None
@@ -346,15 +353,17 @@ class OracleScene:
                     return None
             else:
                 L.or_retrace_path(self._h, pid, args[0], args[1], _p(info), _p(org), _p(ph), _p(amb), C.byref(ch))
-        return (int(info[0]), org, ph), int(ch.n_alt_next)
+        return (int(info[0]), org, ph), int(ch.n_alt_next), bool(ch.open)
 
     def outcomes(self, steps, pid: int, rec, max_runs: int = 96, max_depth: int = 12):
         """Every record path ``pid`` can end with when ``steps`` run from record
         ``rec`` and each ambiguous decision takes each of its admissible
         outcomes (depth-first over decision scripts).  Returns (records,
-        complete); complete is False when the run or depth bound cut the
-        search, and records is None when the steps cannot run per path.  The
-        scene's poses are as before on return."""
+        complete, open); complete is False when the run or depth bound cut
+        the search, open is True when some run met a hit whose distance the
+        band leaves undetermined over a stretch (see run_path), and records
+        is None when the steps cannot run per path.  The scene's poses are as
+        before on return."""
         poses, frames = getattr(self, "_poses", None), self.frames
         try:
             return self._outcomes(steps, pid, rec, max_runs, max_depth)
@@ -363,23 +372,24 @@ class OracleScene:
                 self._restore_poses(poses, frames)
 
     def _outcomes(self, steps, pid, rec, max_runs, max_depth):
-        out, stack, runs = [], [()], 0
+        out, stack, runs, opened = [], [()], 0, False
         while stack:
             script = stack.pop()
             r = self.run_path(steps, pid, rec, script)
             if r is None:
-                return None, False
+                return None, False, False
             runs += 1
-            rec_out, n_alt = r
+            rec_out, n_alt, op = r
+            opened |= op
             if n_alt == 0 or len(script) >= max_depth:
                 out.append(rec_out)
                 if n_alt:
-                    return out, False
+                    return out, False, opened
             else:
                 stack.extend(script + (c,) for c in reversed(range(n_alt)))
             if runs >= max_runs and stack:
-                return out, False
-        return out, True
+                return out, False, opened
+        return out, True, opened
 
     # ---- screen-space splat (Fig. 2 splat/gather, radius kernel)
     def splat(self, paths: Paths, cam: "Camera", radius: float):

@@ -274,6 +274,11 @@ typedef struct {
   int hit, amb;
 } cand_t;
 
+/* A candidate whose crossing distance the band leaves undetermined over more
+ * than 1e-4 diag (epst = eps / |cos| with eps = 1e-6 diag): the ray runs
+ * within eps of the triangle's plane along that stretch. */
+static int cand_open(const or_scene* s, const cand_t* c) { return c->amb && c->epst > 100.0 * s->eps; }
+
 /* Classify triangle T (v0,v1,v2,n) against the ray o + t d (|d| = 1) for
  * t in (tlo, thi).  Hit: the ray meets the closed triangle inside the open
  * range.  Ambiguous: the ray line passes within eps of an edge line
@@ -416,6 +421,9 @@ static int32_t closest_hit(const or_scene* s, int p, const double* o, const doub
         ++na;
       }
     }
+    for (int k = 0; k < na; ++k)
+      for (size_t i = 0; i < cv.n; ++i)
+        if (cv.c[i].prim == alt_p[k] && cand_open(s, &cv.c[i])) ch->open = 1;
     const int k = choose(ch, na);
     best = alt_p[k];
     best_t = alt_t[k];

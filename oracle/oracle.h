@@ -233,6 +233,9 @@ typedef struct {
   int32_t n_script;
   int32_t pos;
   int32_t n_alt_next;
+  int32_t open;   /* set when a closest hit met a triangle whose crossing distance the band leaves
+                     undetermined over more than 1e-4 diag (a ray running within eps of its plane):
+                     a hit anywhere on that stretch is admissible, which no list of outcomes holds */
 } or_choice;
 
 /* One path through one step under a decision script (``ch`` carries the

@@ -16,52 +16,19 @@ using namespace pvk;
 
 namespace {
 
-constexpr uint32_t kFreshMask = PV_INFO_REPLACE | PV_INFO_REUSE_LIGHT | (15u << PV_INFO_START_SHIFT);
-
-// a fresh emission: replace, start 0, no reuse of the light sample
-__device__ __forceinline__ bool is_fresh(uint32_t w) { return (w & kFreshMask) == PV_INFO_REPLACE; }
-
-__device__ __forceinline__ uint32_t light_of(const FrameLights& L, uint32_t p) {
-  uint32_t l = 0;
-  while (l + 1 < L.n && p >= L.first[l + 1]) ++l;
-  return l;
-}
-
-__device__ __forceinline__ bool dm_moved(const FrameLights& L, uint32_t l) {
-  return L.dm[l].dims != 0 && ((L.moved_mask >> l) & 1u) != 0;
-}
-
 __global__ void k_dm_reset(DmLight D) {
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < D.cells; c += gridDim.x * blockDim.x)
     D.dmc[c] = dm_target(D, c);
 }
 
-// Pass 1: a kept path of a cell with DM_C > DM_T is pruned with probability
-// (DM_C - DM_T) / DM_C (Eq. 1): Philox counter (path, 16, frame), pruned iff
-// draw24 * DM_C < (DM_C - DM_T) * 2^24.  It becomes a fresh emission that
-// still names its old cell (for pass 2).
+// Pass 1 (dm_prune_path), flag[p] = 1 for a pruned path.
 __global__ void __launch_bounds__(256) k_dm_prune(FrameLights L, uint32_t n, uint32_t* info, uint32_t* flag,
                                                   uint64_t seed, uint32_t frame, pv_frame_stats* stats) {
   __shared__ uint32_t s_red[32];
   const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t pruned = 0;
   if (p < n) {
-    const uint32_t l = light_of(L, p);
-    if (dm_moved(L, l)) {
-      const uint32_t w = info[p];
-      if (!is_fresh(w)) {
-        const DmLight& D = L.dm[l];
-        const uint32_t c = w & 0xFFFFFu;
-        const uint32_t dc = D.dmc[c], dt = dm_target(D, c);
-        if (dc > dt) {
-          const uint4 r = philox4x32_10(make_uint4(p, 16u, frame, 0u), make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-          if ((uint64_t)(r.x >> 8) * dc < ((uint64_t)(dc - dt) << 24)) {
-            info[p] = info_make((l << 20) | c, 0, 0, true, false);
-            pruned = 1;
-          }
-        }
-      }
-    }
+    pruned = dm_prune_path(L, p, info, seed, frame);
     flag[p] = pruned;
   }
   uint32_t* const ctr[1] = {stats ? &stats->n_pruned : nullptr};
@@ -69,50 +36,23 @@ __global__ void __launch_bounds__(256) k_dm_prune(FrameLights L, uint32_t n, uin
   block_add_n<1>(ctr, val, s_red);
 }
 
-// Pass 2: the pruned paths leave their cells; every fresh emission of a light
-// with a moved map is flagged free (bit 30, for the compaction) and counted.
+// Pass 2 (dm_commit_path): the pruned paths leave their cells; every fresh
+// emission of a light with a moved map is flagged free (bit 30, for the
+// compaction) and counted.
 __global__ void __launch_bounds__(256) k_dm_commit(FrameLights L, uint32_t n, const uint32_t* info, uint32_t* flag,
                                                    uint32_t* free_count) {
   const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
-  const uint32_t l = light_of(L, p);
-  uint32_t out = 0;
-  if (dm_moved(L, l)) {
-    const uint32_t w = info[p];
-    if (flag[p]) atomicSub(L.dm[l].dmc + (w & 0xFFFFFu), 1u);
-    if (is_fresh(w)) {
-      out = PV_INFO_REPLACE;
-      atomicAdd(free_count + l, 1u);
-    }
-  }
-  flag[p] = out;
+  flag[p] = dm_commit_path(L, p, info, flag[p], free_count);
 }
 
 __global__ void k_dm_deficit(DmLight D, uint32_t* def) {
-  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c <= D.cells; c += gridDim.x * blockDim.x) {
-    if (c == D.cells) {
-      def[c] = 0u;                             // becomes the total after the exclusive scan
-    } else {
-      const uint32_t t = dm_target(D, c), have = D.dmc[c];
-      def[c] = have < t ? t - have : 0u;
-    }
-  }
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c <= D.cells; c += gridDim.x * blockDim.x)
+    def[c] = dm_deficit(D, c);
 }
 
-// Largest cell c with pre[c] <= j (pre: exclusive prefix of the deficits, j < pre[cells]).
-__device__ __forceinline__ uint32_t deficit_cell(const uint32_t* pre, uint32_t cells, uint32_t j) {
-  uint32_t lo = 0, hi = cells;                 // pre[lo] <= j, and j < pre[hi]
-  while (hi - lo > 1) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (pre[mid] <= j) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
-
-// Fill: the j-th free path of light l (ascending ids) takes the cell whose
-// deficit range holds j; once the deficits are used up, the rest spread
-// evenly over the cells.
+// Fill (dm_fill_path) for the free paths of light l, listed after those of
+// the lights before it.
 __global__ void __launch_bounds__(256) k_dm_fill(FrameLights L, uint32_t l, const uint32_t* free_list,
                                                  const uint32_t* free_count, const uint32_t* pre, uint32_t* info,
                                                  pv_frame_stats* stats) {
@@ -121,14 +61,9 @@ __global__ void __launch_bounds__(256) k_dm_fill(FrameLights L, uint32_t l, cons
   const uint32_t F = free_count[l];
   uint32_t off = 0;
   for (uint32_t k = 0; k < l; ++k) off += free_count[k];
-  const uint32_t total = pre[D.cells];
   uint32_t filled = 0;
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < F; j += gridDim.x * blockDim.x) {
-    const uint32_t p = free_list[off + j];
-    const uint32_t c = j < total ? deficit_cell(pre, D.cells, j)
-                                 : (uint32_t)(((uint64_t)(j - total) * D.cells) / (F - total));
-    info[p] = info_make((l << 20) | c, 0, 0, true, false);
-    atomicAdd(D.dmc + c, 1u);
+    dm_fill_path(D, l, free_list[off + j], j, F, pre, info);
     ++filled;
   }
   uint32_t* const ctr[1] = {stats ? &stats->n_filled : nullptr};

@@ -131,4 +131,88 @@ __device__ __forceinline__ void dm_restrict(const DmLight& D, uint32_t c, float4
   }
 }
 
+// ---- the steps after "compute DM_C" (Sec. 3.1), per path or per cell, shared by
+// the single-scene kernels (dm.cu) and the batched ones (batch.cu)
+
+constexpr uint32_t kDmFreshMask = PV_INFO_REPLACE | PV_INFO_REUSE_LIGHT | (15u << PV_INFO_START_SHIFT);
+
+// a fresh emission: replace, start 0, no reuse of the light sample
+__device__ __forceinline__ bool dm_is_fresh(uint32_t w) { return (w & kDmFreshMask) == PV_INFO_REPLACE; }
+
+__device__ __forceinline__ uint32_t dm_light_of(const FrameLights& L, uint32_t p) {
+  uint32_t l = 0;
+  while (l + 1 < L.n && p >= L.first[l + 1]) ++l;
+  return l;
+}
+
+// light l has a map and moved this frame
+__device__ __forceinline__ bool dm_moved(const FrameLights& L, uint32_t l) {
+  return L.dm[l].dims != 0 && ((L.moved_mask >> l) & 1u) != 0;
+}
+
+// Pass 1 for path p: a kept path of a cell with DM_C > DM_T is pruned with
+// probability (DM_C - DM_T) / DM_C (Eq. 1): Philox counter (path, 16,
+// frame), pruned iff draw24 * DM_C < (DM_C - DM_T) * 2^24.  It becomes a
+// fresh emission that still names its old cell (for pass 2).  Returns 1 if
+// pruned.
+__device__ __forceinline__ uint32_t dm_prune_path(const FrameLights& L, uint32_t p, uint32_t* info, uint64_t seed,
+                                                  uint32_t frame) {
+  const uint32_t l = dm_light_of(L, p);
+  if (!dm_moved(L, l)) return 0u;
+  const uint32_t w = info[p];
+  if (dm_is_fresh(w)) return 0u;
+  const DmLight& D = L.dm[l];
+  const uint32_t c = w & 0xFFFFFu;
+  const uint32_t dc = D.dmc[c], dt = dm_target(D, c);
+  if (dc <= dt) return 0u;
+  const uint4 r = philox4x32_10(make_uint4(p, 16u, frame, 0u), make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  if ((uint64_t)(r.x >> 8) * dc >= ((uint64_t)(dc - dt) << 24)) return 0u;
+  info[p] = info_make((l << 20) | c, 0, 0, true, false);
+  return 1u;
+}
+
+// Pass 2 for path p: a pruned path leaves its cell; every fresh emission of a
+// light with a moved map is counted free.  Returns the compaction flag
+// (PV_INFO_REPLACE for a free path).
+__device__ __forceinline__ uint32_t dm_commit_path(const FrameLights& L, uint32_t p, const uint32_t* info,
+                                                   uint32_t pruned, uint32_t* free_count) {
+  const uint32_t l = dm_light_of(L, p);
+  if (!dm_moved(L, l)) return 0u;
+  const uint32_t w = info[p];
+  if (pruned) atomicSub(L.dm[l].dmc + (w & 0xFFFFFu), 1u);
+  if (!dm_is_fresh(w)) return 0u;
+  atomicAdd(free_count + l, 1u);
+  return PV_INFO_REPLACE;
+}
+
+// Deficit of cell c (c == cells: 0, the slot the exclusive scan turns into the total).
+__device__ __forceinline__ uint32_t dm_deficit(const DmLight& D, uint32_t c) {
+  if (c == D.cells) return 0u;
+  const uint32_t t = dm_target(D, c), have = D.dmc[c];
+  return have < t ? t - have : 0u;
+}
+
+// Largest cell c with pre[c] <= j (pre: exclusive prefix of the deficits, j < pre[cells]).
+__device__ __forceinline__ uint32_t dm_deficit_cell(const uint32_t* pre, uint32_t cells, uint32_t j) {
+  uint32_t lo = 0, hi = cells;                 // pre[lo] <= j, and j < pre[hi]
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (pre[mid] <= j) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Fill: the j-th of the F free paths of light l takes the cell whose deficit
+// range holds j; once the deficits are used up, the rest spread evenly over
+// the cells.  Writes the path's info word and counts it in its cell.
+__device__ __forceinline__ void dm_fill_path(const DmLight& D, uint32_t l, uint32_t p, uint32_t j, uint32_t F,
+                                             const uint32_t* pre, uint32_t* info) {
+  const uint32_t total = pre[D.cells];
+  const uint32_t c = j < total ? dm_deficit_cell(pre, D.cells, j)
+                               : (uint32_t)(((uint64_t)(j - total) * D.cells) / (F - total));
+  info[p] = info_make((l << 20) | c, 0, 0, true, false);
+  atomicAdd(D.dmc + c, 1u);
+}
+
 }  // namespace pvk

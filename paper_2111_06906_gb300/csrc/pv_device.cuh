@@ -244,48 +244,17 @@ struct WNodeRay {
   int4 child;
 };
 
-// Both planes of one axis of the four children (32 bytes, 32-byte aligned)
-// in one 256-bit load through the read-only path.
-__device__ __forceinline__ void ldg_pair(const float4* p, float4& lo, float4& hi) {
-  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-      : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
-      : "l"(p));
-}
-
-__device__ __forceinline__ float4 sel4(bool s, float4 a, float4 b) {
-  return make_float4(s ? a.x : b.x, s ? a.y : b.y, s ? a.z : b.z, s ? a.w : b.w);
-}
-
-#ifndef PV_NODE_LOAD256
-#define PV_NODE_LOAD256 0
-#endif
-
 __device__ __forceinline__ WNodeRay load_wnode_ray(const WNode* nodes, int i, const Ray& r) {
   const float4* p = reinterpret_cast<const float4*>(nodes + i);
   const uint32_t sx = __float_as_uint(r.inv.x) >> 31, sy = __float_as_uint(r.inv.y) >> 31;
   const uint32_t sz = __float_as_uint(r.inv.z) >> 31;
   WNodeRay n;
-  if (PV_NODE_LOAD256) {
-    // three 256-bit loads (lo and hi of one axis each) and the child word: four load instructions, the
-    // near and far planes picked in registers
-    float4 lo, hi;
-    ldg_pair(p, lo, hi);
-    n.nx = sel4(sx, hi, lo);
-    n.fx = sel4(sx, lo, hi);
-    ldg_pair(p + 2, lo, hi);
-    n.ny = sel4(sy, hi, lo);
-    n.fy = sel4(sy, lo, hi);
-    ldg_pair(p + 4, lo, hi);
-    n.nz = sel4(sz, hi, lo);
-    n.fz = sel4(sz, lo, hi);
-  } else {
-    n.nx = __ldg(p + sx);
-    n.fx = __ldg(p + (1u - sx));
-    n.ny = __ldg(p + 2u + sy);
-    n.fy = __ldg(p + (3u - sy));
-    n.nz = __ldg(p + 4u + sz);
-    n.fz = __ldg(p + (5u - sz));
-  }
+  n.nx = __ldg(p + sx);
+  n.fx = __ldg(p + (1u - sx));
+  n.ny = __ldg(p + 2u + sy);
+  n.fy = __ldg(p + (3u - sy));
+  n.nz = __ldg(p + 4u + sz);
+  n.fz = __ldg(p + (5u - sz));
   n.child = __ldg(reinterpret_cast<const int4*>(p + 6));
   return n;
 }

@@ -62,10 +62,13 @@ __device__ __forceinline__ Seg seg_prep(const SceneView& sv, float3 a, float3 b,
   Seg g;
   const float3 dv = b - a;
   if (boxes) {
-    const float e = 1e-20f;                 // |1/d| <= 1e20 keeps a * inv finite for any scene size
-    g.inv = make_float3(__frcp_rn(fabsf(dv.x) > e ? dv.x : copysignf(e, dv.x)),
-                        __frcp_rn(fabsf(dv.y) > e ? dv.y : copysignf(e, dv.y)),
-                        __frcp_rn(fabsf(dv.z) > e ? dv.z : copysignf(e, dv.z)));
+    // |1/d| <= 1e20 keeps a * inv finite for any scene size.  An approximate reciprocal (one special-function
+    // instruction, not the correctly rounded division) suffices: its error moves the slab bounds by a few
+    // units in the last place, far inside the band within which a box decision counts as ambiguous
+    const float e = 1e-20f;
+    g.inv = make_float3(__fdividef(1.0f, fabsf(dv.x) > e ? dv.x : copysignf(e, dv.x)),
+                        __fdividef(1.0f, fabsf(dv.y) > e ? dv.y : copysignf(e, dv.y)),
+                        __fdividef(1.0f, fabsf(dv.z) > e ? dv.z : copysignf(e, dv.z)));
     g.aoi = make_float3(-a.x * g.inv.x, -a.y * g.inv.y, -a.z * g.inv.z);
     g.ok = true;
     return g;

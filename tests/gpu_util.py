@@ -86,8 +86,12 @@ def compare(gpu: oracle.Paths, orc: oracle.Paths, diag: float, skip=None, pos_to
     records of those paths become the first accepted one, so that later
     steps start from the outcome the device took.  ``skip`` excludes paths
     altogether.  Returns a dict of counts; every ``bad_*`` entry must be
-    zero for parity, and ``ambiguous_unchecked`` counts flagged paths whose
-    steps cannot be listed per path (distribution maps)."""
+    zero for parity; ``ambiguous_unchecked`` counts flagged paths whose
+    steps cannot be listed per path (distribution maps), and
+    ``ambiguous_open`` flagged paths matching no listed record whose search
+    met a hit distance the band leaves undetermined along a stretch of the
+    ray (a ray within eps of a triangle's plane, where any point of the
+    stretch is an admissible hit): the tests bound both."""
     n = int(len(gpu.ids))
     tracked = np.zeros(n, bool)
     if orc.branches:
@@ -102,22 +106,27 @@ def compare(gpu: oracle.Paths, orc: oracle.Paths, diag: float, skip=None, pos_to
         r["bad_" + k] = int(v.sum())
     r.update(mx)
     r["ambiguous_matched"] = r["bad_ambiguous"] = r["bad_unresolved"] = r["ambiguous_unchecked"] = 0
+    r["ambiguous_open"] = 0
     new_branches = {}
     o = orc.oracle
     B = orc.photons.shape[1]
     for i in np.nonzero(amb & ~skipped)[0].tolist():
+        if i in orc.opened:                   # open at an earlier check: the two sides' records have parted
+            r["ambiguous_open"] += 1
+            continue
         if orc.snap is None:
             bases = [(0, np.zeros(3, np.float32), np.zeros((B, 8), np.float32))]
         else:
             bases = orc.branches.get(i) or [(int(orc.snap[0][i]), orc.snap[1][i], orc.snap[2][i])]
-        cands, complete, supported = [], True, o is not None
+        cands, complete, opened, supported = [], True, False, o is not None
         for base in bases if supported else []:
-            recs, comp = o.outcomes(orc.pending, int(orc.ids[i]), base)
+            recs, comp, op = o.outcomes(orc.pending, int(orc.ids[i]), base)
             if recs is None:
                 supported = False
                 break
             cands += recs
             complete &= comp
+            opened |= op
         if not supported:
             r["ambiguous_unchecked"] += 1
             continue
@@ -131,10 +140,24 @@ def compare(gpu: oracle.Paths, orc: oracle.Paths, diag: float, skip=None, pos_to
         if good.any():
             r["ambiguous_matched"] += 1
             new_branches[i] = [cands[j] for j in np.nonzero(good)[0]]
-        elif complete:
-            r["bad_ambiguous"] += 1
         else:
-            r["bad_unresolved"] += 1
+            # a search that met an undetermined hit distance (a ray within eps of a triangle's plane) cannot list
+            # every admissible record: counted as such, and bounded by the tests; any other miss is a failure
+            key = "ambiguous_open" if opened else ("bad_ambiguous" if complete else "bad_unresolved")
+            r[key] = r.get(key, 0) + 1
+            if opened:
+                orc.opened.add(i)
+            if len(r.setdefault("mismatch_detail", [])) < 4:      # which fields the nearest outcome disagrees on
+                nbad = np.sum(np.stack(list(f.values())), axis=0) if m else np.zeros(0)
+                j = int(np.argmin(nbad)) if m else -1
+                L = int((gpu.info[i] >> 22) & 15)
+                r["mismatch_detail"].append({
+                    "path": int(orc.ids[i]), "amb_bits": int(orc.amb[i]), "outcomes": m, "open": opened,
+                    "fields": [k for k, v in f.items() if m and v[j]],
+                    "gpu_info": hex(int(gpu.info[i])), "oracle_info": hex(int(ci[j])) if m else None,
+                    "gpu_prims": gpu.photons[i, :L, 3].view(np.int32).tolist(),
+                    "oracle_prims": cp[j, :, 3].view(np.int32).tolist() if m else None,
+                    "gpu_pos": gpu.photons[i, :L, :3].tolist(), "oracle_pos": cp[j, :, :3].tolist() if m else None})
     if sync and orc.oracle is not None:
         orc.snap = (orc.info.copy(), orc.origin.copy(), orc.photons.copy())
         orc.pending = []

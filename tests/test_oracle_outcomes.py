@@ -38,7 +38,7 @@ def test_unflagged_paths_admit_only_the_oracle_record(city_trace):
     B = sc.max_bounces
     blank = (0, np.zeros(3, np.float32), np.zeros((B, 8), np.float32))
     for i in np.nonzero(p.amb == 0)[0][:40]:
-        recs, complete = o.outcomes(p.pending, int(p.ids[i]), blank)
+        recs, complete, _ = o.outcomes(p.pending, int(p.ids[i]), blank)
         assert complete and len(recs) == 1
         assert _same(recs[0], p.record(i))
 
@@ -52,7 +52,7 @@ def test_flagged_paths_admit_the_oracle_record_first_and_valid_alternatives(city
     world = sc.world_verts(1)
     several = 0
     for i in flagged:
-        recs, complete = o.outcomes(p.pending, int(p.ids[i]), blank)
+        recs, complete, _ = o.outcomes(p.pending, int(p.ids[i]), blank)
         assert complete
         assert _same(recs[0], p.record(i))
         several += len(recs) > 1
@@ -74,7 +74,7 @@ def test_compare_accepts_an_admitted_alternative_and_rejects_a_planted_mistake(c
     blank = (0, np.zeros(3, np.float32), np.zeros((B, 8), np.float32))
     alt = None
     for i in np.nonzero(p.amb != 0)[0]:
-        recs, _ = o.outcomes(p.pending, int(p.ids[i]), blank)
+        recs, _, _ = o.outcomes(p.pending, int(p.ids[i]), blank)
         for r in recs[1:]:
             if not _same(r, p.record(i)):
                 alt = (i, r)
@@ -117,7 +117,7 @@ def test_verify_outcomes_follow_the_accepted_branch():
     flagged = np.nonzero(q.amb != 0)[0]
     # the trace's flags carry over: paths flagged only there admit just the oracle's verified record
     for i in flagged[:30]:
-        recs, complete = o.outcomes(q.pending, int(q.ids[i]), p.record(i))
+        recs, complete, _ = o.outcomes(q.pending, int(q.ids[i]), p.record(i))
         assert complete and _same(recs[0], q.record(i))
     r = gu.compare(q.copy(), q, sc.diag)        # the oracle's own records pass, and become the branches
     gu.assert_parity(r)
@@ -126,3 +126,31 @@ def test_verify_outcomes_follow_the_accepted_branch():
     r2 = gu.compare(q.copy(), q, sc.diag)
     gu.assert_parity(r2)
     assert o.frames == (1, 2)                   # the enumeration left the scene's poses as they were
+
+
+def test_segments_in_a_surface_plane_are_open():
+    """When Alg. 1 moves a vertex onto a wall, the next segment can end on
+    the same wall plane (two coplanar triangles).  Its query along it
+    runs inside the plane, where the hit distance is undetermined over the
+    triangle: the oracle reports the search as open (any point of that
+    stretch is an admissible hit) instead of listing outcomes."""
+    sc = kit.box_with_torus(8000, B=4)
+    o = oracle.OracleScene(sc)
+    o.set_frames(1, 1)
+    p = o.trace(np.arange(sc.n_paths, dtype=np.uint32), 1, 1)
+    p.rebase()
+    o.set_frames(1, 2)
+    q = p.copy()
+    o.verify(q, oracle.MODE_ERROR, float("inf"))
+    walls = [(0, -1.0), (0, 1.0), (1, 0.0), (1, 2.0), (2, -1.0)]     # the box's planes (axis, coordinate)
+    in_plane, opened = set(), set()
+    for i in np.nonzero(q.amb != 0)[0]:
+        L = int(q.nseg[i])
+        x = q.photons[i, :L, :3]                 # after Alg. 1 moved a vertex onto a wall
+        if any(x[k, a] == c and x[k + 1, a] == c for k in range(L - 1) for a, c in walls):
+            in_plane.add(int(i))
+        _, _, op = o.outcomes(q.pending, int(q.ids[i]), p.record(i))
+        if op:
+            opened.add(int(i))
+    assert len(in_plane) >= 2
+    assert in_plane <= opened
