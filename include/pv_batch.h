@@ -81,9 +81,14 @@ typedef struct {
  * none (PV_ERR_ARG otherwise).  The scenes stay owned by the
  * caller and must outlive the batch; while the batch exists they are driven
  * only through pv_batch_frame.  Allocates the batch's device tables and
- * pinned staging (synchronous).  PV_ERR_ARG for bad arguments,
+ * pinned staging (synchronous).  Scenes with distribution maps (Sec. 3.1)
+ * run compute DM_C (with the origin update), the two-pass prune of Eq. 1 and
+ * the fill inside the frame, with the scene's seed and the frame number
+ * keying the prune draws, as pv_verify_paths does with params seed and
+ * frame; their batch must have lists, since prune and fill need every path's
+ * Alg. 1 answer before the list is made.  PV_ERR_ARG for bad arguments,
  * PV_ERR_LIMIT for too many scenes, PV_ERR_STATE for a scene built with
- * PV_BUILD_DYN_REBUILD or with distribution maps. */
+ * PV_BUILD_DYN_REBUILD, or with distribution maps in a batch without lists. */
 int pv_batch_create(const pv_batch_scene* scenes, uint32_t n, const pv_verify_params* params, void* stream,
                     pv_batch** out);
 

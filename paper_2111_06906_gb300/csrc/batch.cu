@@ -128,6 +128,76 @@ __global__ void k_b_prologue(const BScene* S, const BFrame* F, BCounters* bc) {
   for (uint32_t i = threadIdx.x; i < B.n_tiles; i += blockDim.x) B.tiles[i] = 0ull;
 }
 
+// ---------------------------------------------------------------- distribution maps (Sec. 3.1)
+// The steps of dm.cu for one scene of the batch.  They read the frame's
+// light poses, moved lights and frame number from the scene's frame record,
+// so a captured frame stays right from one replay to the next; a light whose
+// map did not move this frame is left alone, as dm.cu leaves it.
+
+// DM_C of the moved lights with a map, cleared before verification counts it.
+__global__ void k_b_dm_clear(const BFrame* F, uint32_t sc) {
+  const FrameLights& L = F[sc].L;
+  for (uint32_t l = 0; l < L.n; ++l) {
+    if (!dm_moved(L, l)) continue;
+    const DmLight& D = L.dm[l];
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < D.cells; c += gridDim.x * blockDim.x) D.dmc[c] = 0u;
+  }
+}
+
+// Pass 1 of the prune (dm_prune_path, with the scene's seed and the frame's number); flag[p] = 1 when pruned.
+__global__ void __launch_bounds__(256) k_b_dm_prune(const BScene* S, const BFrame* F, uint32_t sc, uint32_t* flag) {
+  __shared__ uint32_t s_red[32];
+  const BScene& B = S[sc];
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t pruned = 0;
+  if (p < B.V.n) {
+    pruned = dm_prune_path(F[sc].L, p, B.V.info, B.T.seed, F[sc].frame);
+    flag[p] = pruned;
+  }
+  uint32_t* const ctr[1] = {B.V.stats ? &B.V.stats->n_pruned : nullptr};
+  const uint32_t val[1] = {pruned};
+  block_add_n<1>(ctr, val, s_red);
+}
+
+// Pass 2 (dm_commit_path): flag[p] becomes the free-path flag for the compaction.
+__global__ void __launch_bounds__(256) k_b_dm_commit(const BScene* S, const BFrame* F, uint32_t sc, uint32_t* flag,
+                                                     uint32_t* free_count) {
+  const BScene& B = S[sc];
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= B.V.n) return;
+  flag[p] = dm_commit_path(F[sc].L, p, B.V.info, flag[p], free_count);
+}
+
+__global__ void k_b_dm_deficit(const BFrame* F, uint32_t sc, uint32_t l, uint32_t* def) {
+  const FrameLights& L = F[sc].L;
+  if (!dm_moved(L, l)) return;
+  const DmLight& D = L.dm[l];
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c <= D.cells; c += gridDim.x * blockDim.x)
+    def[c] = dm_deficit(D, c);
+}
+
+// Fill (dm_fill_path) for the free paths of light l, listed after those of the lights before it.
+__global__ void __launch_bounds__(256) k_b_dm_fill(const BScene* S, const BFrame* F, uint32_t sc, uint32_t l,
+                                                   const uint32_t* free_list, const uint32_t* free_count,
+                                                   const uint32_t* pre) {
+  __shared__ uint32_t s_red[32];
+  const FrameLights& L = F[sc].L;
+  if (!dm_moved(L, l)) return;                 // the same for every thread of the block
+  const BScene& B = S[sc];
+  const DmLight& D = L.dm[l];
+  const uint32_t Fc = free_count[l];
+  uint32_t off = 0;
+  for (uint32_t k = 0; k < l; ++k) off += free_count[k];
+  uint32_t filled = 0;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < Fc; j += gridDim.x * blockDim.x) {
+    dm_fill_path(D, l, free_list[off + j], j, Fc, pre, B.V.info);
+    ++filled;
+  }
+  uint32_t* const ctr[1] = {B.V.stats ? &B.V.stats->n_filled : nullptr};
+  const uint32_t val[1] = {filled};
+  block_add_n<1>(ctr, val, s_red);
+}
+
 // ---------------------------------------------------------------- pose update
 // Per 256-triangle chunk of one scene (tab: scene, first triangle): the
 // moved objects' triangles to the new pose and the direct wide refit.
@@ -706,6 +776,14 @@ int enqueue_frame(pv_batch* b, cudaStream_t st, bool vis, const pv_batch_config&
     return PV_ERR_CUDA;
   mark(0);
   k_b_prologue<<<n, 256, 0, st>>>(b->d_scenes, b->d_frames, b->d_ctr);
+  for (uint32_t i = 0; i < n; ++i) {          // DM_C of moved mapped lights, counted afresh by verification
+    pv_scene* s = b->items[i].scene;
+    if (!s->has_dm) continue;
+    const FrameLights L = pvh::frame_lights(s);
+    uint32_t cells = 0;
+    for (uint32_t l = 0; l < L.n; ++l) cells = std::max(cells, L.dm[l].dims ? L.dm[l].cells : 0u);
+    k_b_dm_clear<<<std::min<uint32_t>((cells + 255) / 256, 8u * (uint32_t)b->num_sms), 256, 0, st>>>(b->d_frames, i);
+  }
   if (b->n_fit) k_b_refit_wide<<<b->n_fit, 256, 0, st>>>(b->d_scenes, b->d_frames, b->d_ftab);
   if (b->top_alone) k_b_frame_top<<<n, 32, 0, st>>>(b->d_scenes, b->d_frames);
   mark(1);
@@ -732,6 +810,30 @@ int enqueue_frame(pv_batch* b, cudaStream_t st, bool vis, const pv_batch_config&
     const ContKernel ck = cont_kernel(c.stack);
     ck<<<persistent_blocks(b, b->occ_cont[stack_index(c.stack)], 0), 128, b->smem_cont, st>>>(
         b->d_scenes, b->d_frames, n, b->d_ctr);
+  }
+  // with distribution maps: prune and fill, which need Alg. 1's final answer for every path
+  for (uint32_t i = 0; i < n; ++i) {
+    pv_scene* s = b->items[i].scene;
+    if (!s->has_dm) continue;
+    const uint32_t np = b->items[i].paths.n, blocks = (np + 255) / 256;
+    if (!np) continue;
+    if (cudaMemsetAsync(s->dm_ctr, 0, 8 * sizeof(uint32_t), st) != cudaSuccess) return PV_ERR_CUDA;
+    k_b_dm_prune<<<blocks, 256, 0, st>>>(b->d_scenes, b->d_frames, i, s->dm_flag);
+    k_b_dm_commit<<<blocks, 256, 0, st>>>(b->d_scenes, b->d_frames, i, s->dm_flag, s->dm_ctr);
+    pvh::launch_compact(s, s->dm_flag, np, s->dm_free, s->dm_ctr + 4, nullptr, st);
+    // that compaction used the scene's tile states: cleared again for the re-trace list's compaction below
+    if (cudaMemsetAsync(s->ws_tiles, 0, (size_t)((np + pvh::kTile - 1) / pvh::kTile) * sizeof(uint64_t), st) !=
+        cudaSuccess)
+      return PV_ERR_CUDA;
+    const FrameLights L = pvh::frame_lights(s);
+    for (uint32_t l = 0; l < L.n; ++l) {
+      if (!L.dm[l].dims) continue;
+      k_b_dm_deficit<<<(L.dm[l].cells + 256) / 256, 256, 0, st>>>(b->d_frames, i, l, s->dm_scan);
+      pvh::exclusive_scan(s->dm_scan, L.dm[l].cells + 1, st);
+      const uint32_t fb = std::min<uint32_t>((s->lights_new[l].n_paths + 255) / 256, 8u * (uint32_t)s->num_sms);
+      k_b_dm_fill<<<std::max<uint32_t>(fb, 1u), 256, 0, st>>>(b->d_scenes, b->d_frames, i, l, s->dm_free, s->dm_ctr,
+                                                             s->dm_scan);
+    }
   }
   mark(3);
   k_b_compact<<<b->n_ctiles, pvh::kCompactThreads, 0, st>>>(b->d_scenes, b->d_ctab, b->d_ctr);
@@ -882,7 +984,9 @@ extern "C" int pv_batch_create(const pv_batch_scene* scenes, uint32_t n, const p
     const pv_batch_scene& it = scenes[i];
     if (pvh::check_paths(it.scene, &it.paths) != PV_OK) return PV_ERR_ARG;
     if (!it.d_list != fused || !it.d_count != fused) return PV_ERR_ARG;
-    if ((it.scene->flags & PV_BUILD_DYN_REBUILD) || it.scene->has_dm) return PV_ERR_STATE;
+    // a graph replays refits, not the data-dependent rebuild; with maps, prune and fill need every path's
+    // Alg. 1 answer before the list is made, so those batches run with lists
+    if ((it.scene->flags & PV_BUILD_DYN_REBUILD) || (it.scene->has_dm && fused)) return PV_ERR_STATE;
     for (uint32_t j = 0; j < i; ++j)
       if (scenes[j].scene == it.scene) return PV_ERR_ARG;
   }

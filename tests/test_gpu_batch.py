@@ -53,13 +53,15 @@ def _mix():
 
 
 class Lane:
-    """One scene driven twice: through the single-scene calls and in a batch."""
+    """One scene driven twice: through the single-scene calls and in a batch
+    (with distribution maps of the given resolutions on its lights)."""
 
-    def __init__(self, sc, seed):
+    def __init__(self, sc, seed, dm_rect=(0, 0, 0, 0), dm_point=(0, 0)):
         torch = _torch()
         self.sc, self.seed = sc, seed
-        self.h1 = gu.lib_scene(sc)
-        self.h2 = gu.lib_scene(sc)
+        self.dm = any(dm_rect) or any(dm_point)
+        self.h1 = gu.lib_scene(sc, dm_rect=dm_rect, dm_point=dm_point)
+        self.h2 = gu.lib_scene(sc, dm_rect=dm_rect, dm_point=dm_point)
         n, B = sc.n_paths, sc.max_bounces
         self.P1 = pv.Paths.allocate(n, B)
         self.P2 = pv.Paths.allocate(n, B)
@@ -77,7 +79,7 @@ class Lane:
 
     def single_frame(self, f, mode, tau, flags):
         pv.pv_update_dynamic(self.h1, self.sc.xforms(f), self.sc.lights(f))
-        pv.pv_verify_paths(self.h1, self.P1, mode, tau, flags, self.l1, self.c1, self.s1)
+        pv.pv_verify_paths(self.h1, self.P1, mode, tau, flags, self.l1, self.c1, self.s1, seed=self.seed, frame=f)
         pv.pv_retrace_invalid(self.h1, self.P1, self.l1, self.c1, self.seed, f, self.s1)
 
     def compare(self, traversal_counters=True, lists=True):
@@ -89,6 +91,9 @@ class Lane:
             n1, n2 = int(self.c1.item()), int(self.c2.item())
             assert n1 == n2
             assert torch.equal(self.l1[:n1], self.l2[:n2])
+        if self.dm:
+            for l in range(len(self.sc.lights(1))):
+                assert np.array_equal(pv.pv_read_distribution_map(self.h1, l), pv.pv_read_distribution_map(self.h2, l))
         d1, d2 = pv.stats_dict(self.s1), pv.stats_dict(self.s2)
         if not traversal_counters:
             for k in ("node_visits", "tri_tests"):
@@ -201,6 +206,48 @@ def test_fused_batch_modes_and_tuner(mode, flags):
     cfg = pv.pv_batch_get_config(b)
     _run(lanes, b, range(f, f + 3), mode, 0.01, flags, traversal_counters=cfg["verify_mapping"] != 1, lists=False)
     pv.pv_batch_destroy(b)
+    for ln in lanes:
+        ln.close()
+
+
+def _dm_lanes(seed0):
+    """Mapped scenes (a translating area light with a 4^4 map, a point light
+    with an 8 x 8 map) beside unmapped ones."""
+    point = kit.floor_and_light(3200, B=2, R=20.0)
+    point._light_fn = lambda f: [Light(LIGHT_POINT, (0.31 * (f - 1), 1.0, -0.17 * (f - 1)), power=(1.0,) * 3,
+                                       n_paths=3200)]
+    rect = kit.rect_light_over_floor(2560, shift=lambda f: (0.11 * (f - 1), 0.0, 0.07 * (f - 1)), B=2, R=3.0)
+    return [Lane(rect, seed0, dm_rect=(4, 4, 4, 4)), Lane(scenes.tiny_box(n_paths=3000), seed0 + 1),
+            Lane(point, seed0 + 2, dm_point=(8, 8)), Lane(kit.box_with_torus(3000, B=3), seed0 + 3)]
+
+
+@pytest.mark.parametrize("mode", [pv.PV_MODE_NAIVE_AABB, pv.PV_MODE_ERROR])
+def test_batch_with_distribution_maps_matches_single_scene_calls(mode):
+    """Compute DM_C (fused with the origin update), prune (Eq. 1, two passes)
+    and fill inside the batched frame, eagerly and replayed from the
+    captured graph: records, lists, counters (pruned and filled included) and
+    every DM_C count equal the single-scene calls'."""
+    lanes = _dm_lanes(31)
+    b = pv.pv_batch_create([ln.item() for ln in lanes], mode, 0.01)
+    pv.pv_batch_autotune(b, 1)
+    f = 2
+    while pv.pv_batch_tuning(b):                       # eager frames, every tuner candidate
+        _run(lanes, b, [f], mode, 0.01, 0, traversal_counters=False)
+        f += 1
+        assert f < 60
+    _run(lanes, b, range(f, f + 4), mode, 0.01, 0,       # graph replays
+         traversal_counters=pv.pv_batch_get_config(b)["verify_mapping"] != 1)
+    tot = pv.stats_dict(lanes[0].s2)
+    assert tot["n_filled"] > 0 and tot["n_pruned"] > 0
+    pv.pv_batch_destroy(b)
+    for ln in lanes:
+        ln.close()
+
+
+def test_batch_with_distribution_maps_needs_lists():
+    lanes = _dm_lanes(41)
+    with pytest.raises(pv.PvError):
+        pv.pv_batch_create([ln.item(lists=False) for ln in lanes], pv.PV_MODE_ERROR, 0.01)
     for ln in lanes:
         ln.close()
 
