@@ -1017,11 +1017,26 @@ def _oracle_sample(workload, n_sample, seed_off=0):
 
 
 def _oracle_frame(o, sc, p, mode, tau, f):
+    """One frame of the oracle on the sample; returns its verify and
+    re-trace counters."""
     import oracle
     o.set_frames(f - 1, f)
-    o.verify(p, mode, tau)
-    o.retrace(p, sc.seed, f)
+    _, sv = o.verify(p, mode, tau)
+    sr = o.retrace(p, sc.seed, f)
     oracle.deposit(p, 1024, 1024, sc.atlas_rect)
+    return sv, sr
+
+
+def _ambiguity(stats):
+    """Queries the oracle flags ambiguous (a decision that a perturbation of
+    1e-6 x the scene diagonal could flip), over all its queries: segment tests
+    against moved objects, trace, Alg. 1 and visibility rays."""
+    amb = sum(s.get("segments_amb", 0) + s.get("rays_amb", 0) for s in stats)
+    seg = sum(s.get("segments_tested", 0) for s in stats)
+    rays = sum(s.get("trace_rays", 0) + s.get("cont_rays", 0) + s.get("vis_rays", 0) for s in stats)
+    return {"ambiguous_queries": int(amb), "segment_tests": int(seg), "rays": int(rays),
+            "share": amb / max(seg + rays, 1),
+            "segments_ambiguous_share": sum(s.get("segments_amb", 0) for s in stats) / max(seg, 1)}
 
 
 CPU_SAMPLE = {"villa": 200, "city": 4000, "tiny_box": 10000}
@@ -1036,11 +1051,11 @@ def cpu_baseline(workload, mode, tau, seconds):
     n_sample = CPU_SAMPLE[workload]
     sc, o, p = _oracle_sample(workload, n_sample)
     timed = {2, 15, 30}
-    ts = {}
+    ts, stats = {}, []
     t_all = time.perf_counter()
     for f in range(2, 31):
         t = time.perf_counter()
-        _oracle_frame(o, sc, p, mode, tau, f)
+        stats += _oracle_frame(o, sc, p, mode, tau, f)
         if f in timed:
             ts[f] = time.perf_counter() - t
         if time.perf_counter() - t_all > seconds and ts:
@@ -1050,7 +1065,8 @@ def cpu_baseline(workload, mode, tau, seconds):
             "sample": f"{n_sample} seeded paths of the {workload} workload (verify + retrace + deposit, FP64 brute "
                       f"force over all {sc.n_tris} triangles), frames {sorted(ts)} timed of the run from frame 2",
             "frame_s": {str(k): v for k, v in sorted(ts.items())},
-            "full_frame_s_extrapolated": sc.n_paths * dt / n_sample}
+            "full_frame_s_extrapolated": sc.n_paths * dt / n_sample,
+            "ambiguity": _ambiguity(stats)}
 
 
 def run_reference(args, ws, rank):

@@ -124,6 +124,8 @@ def lib():
         L.or_retrace.argtypes = [P, P, C.c_uint32, C.c_uint64, C.c_uint32, P, P, P, P, P]
         L.or_deposit.argtypes = [P, C.c_uint32, P, C.c_uint32, C.c_uint32, C.c_uint32,
                                  C.c_float, C.c_float, C.c_float, C.c_float, P]
+        L.or_photon_texels.argtypes = [P, C.c_uint32, P, C.c_uint32, C.c_uint32, C.c_uint32,
+                                       C.c_float, C.c_float, C.c_float, C.c_float, P]
         L.or_closest_hit.restype = C.c_int32
         L.or_closest_hit.argtypes = [P, P, P, C.c_double, C.c_int32, P, P]
         L.or_num_threads.restype = C.c_int32
@@ -480,6 +482,17 @@ def compact(info: np.ndarray) -> np.ndarray:
     out = np.zeros(info.shape[0], np.uint32)
     c = lib().or_compact(_p(info), info.shape[0], _p(out))
     return out[:c]
+
+
+def photon_texels(paths: Paths, width: int, height: int, rect) -> np.ndarray:
+    """int32 [n, B, 2]: the texel (tx, tz) deposit() assigns to each stored
+    photon, (-1, -1) past a path's photon count."""
+    B = paths.photons.shape[1]
+    out = np.zeros((paths.ids.shape[0], B, 2), np.int32)
+    x0, z0, x1, z1 = (float(np.float32(v)) for v in rect)
+    lib().or_photon_texels(_p(np.ascontiguousarray(paths.info)), paths.ids.shape[0],
+                           _p(np.ascontiguousarray(paths.photons)), B, width, height, x0, z0, x1, z1, _p(out))
+    return out
 
 
 def deposit(paths: Paths, width: int, height: int, rect) -> np.ndarray:

@@ -1413,6 +1413,23 @@ void or_deposit(const uint32_t* info, uint32_t n, const or_photon* photons, uint
   }
 }
 
+void or_photon_texels(const uint32_t* info, uint32_t n, const or_photon* photons, uint32_t max_bounces,
+                      uint32_t width, uint32_t height, float x0, float z0, float x1, float z1, int32_t* texels) {
+  for (uint32_t i = 0; i < n; ++i) {
+    const uint32_t L = info_nseg(info[i]);
+    for (uint32_t k = 0; k < max_bounces; ++k) {
+      int32_t* t = texels + 2 * ((size_t)i * max_bounces + k);
+      if (k < L) {
+        const or_photon* v = &photons[(size_t)i * max_bounces + k];
+        t[0] = texel(v->pos[0], x0, x1, width);
+        t[1] = texel(v->pos[2], z0, z1, height);
+      } else {
+        t[0] = t[1] = -1;
+      }
+    }
+  }
+}
+
 int32_t or_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -172,6 +172,11 @@ void or_deposit(const uint32_t* info, uint32_t n, const or_photon* photons, uint
                 uint32_t width, uint32_t height, float x0, float z0, float x1, float z1,
                 double* atlas);
 
+/* The texel (tx, tz) or_deposit assigns to each stored photon: texels
+ * [n][max_bounces][2], (-1, -1) past a path's photon count. */
+void or_photon_texels(const uint32_t* info, uint32_t n, const or_photon* photons, uint32_t max_bounces,
+                      uint32_t width, uint32_t height, float x0, float z0, float x1, float z1, int32_t* texels);
+
 /* Screen-space photon splat (the renderer's "splat/gather" step of Fig. 2;
  * its splatting method is only cited, so a plain radius kernel): pinhole
  * camera at pos looking at target (up vector, vertical field of view fov_y in

@@ -231,11 +231,8 @@ __global__ void __launch_bounds__(256) k_b_refit_wide(const BScene* S, const BFr
   __threadfence();                             // the scene's other blocks' writes are visible from here
   if (threadIdx.x == 0) *B.refit_done = 0u;
   pose_bookkeeping(F[sc].xf, moved, B.n_dyn, B.objs, B.xf_old, B.xf_new, B.obox);
-  __syncthreads();
   if (!moved) return;
-  build_top_block(B.wnodes, B.tris, B.top_off, B.s_wroot, B.objs, (int)B.n_dyn, B.root);
-  __syncthreads();
-  if (B.groups) build_moved_groups_block(B.objs, (int)B.n_dyn, moved, B.groups);
+  build_top_and_groups(B.wnodes, B.tris, B.top_off, B.s_wroot, B.objs, (int)B.n_dyn, B.root, moved, B.groups);
 }
 
 // One block of 32 threads per scene: pose bookkeeping of every slot, then
@@ -245,11 +242,9 @@ __global__ void k_b_frame_top(const BScene* S, const BFrame* F) {
   const BScene& B = S[s];
   if (B.refit_blocks) return;                  // the scene's last refit block did it
   if (B.objs) pose_bookkeeping(F[s].xf, F[s].moved, B.n_dyn, B.objs, B.xf_old, B.xf_new, B.obox);
-  __syncthreads();
   if (!F[s].moved) return;
-  build_top_block(B.wnodes, B.tris, B.top_off, B.s_wroot, B.objs, (int)B.n_dyn, B.root);
-  __syncthreads();
-  if (B.groups) build_moved_groups_block(B.objs, (int)B.n_dyn, F[s].moved, B.groups);
+  build_top_and_groups(B.wnodes, B.tris, B.top_off, B.s_wroot, B.objs, (int)B.n_dyn, B.root, F[s].moved,
+                       B.groups);
 }
 
 // ---------------------------------------------------------------- verify

@@ -403,9 +403,7 @@ __global__ void k_wide_refit(const Node* bnodes, const int* wsrc, const uint32_t
 
 __global__ void k_build_top(WNode* wnodes, const Tri* tris, int top_off, int static_root, const DynObj* objs, int n_dyn,
                             int* root_out, uint64_t moved, MovedGroups* groups) {
-  build_top_block(wnodes, tris, top_off, static_root, objs, n_dyn, root_out);
-  __syncthreads();
-  if (groups) build_moved_groups_block(objs, n_dyn, moved, groups);
+  build_top_and_groups(wnodes, tris, top_off, static_root, objs, n_dyn, root_out, moved, groups);
 }
 
 // Parent links of the dynamic objects' wide nodes and of their triangles,
@@ -461,10 +459,8 @@ __global__ void __launch_bounds__(256) k_refit_wide(XformParams P, RefitArgs R, 
   __threadfence();                             // every block's writes are visible from here
   if (threadIdx.x == 0) *T.done = 0u;
   pose_bookkeeping(P.xf, P.moved, P.n_dyn, T.objs, T.xf_old, T.xf_new, R.obox);
-  __syncthreads();
-  build_top_block(T.wnodes, T.tris, T.top_off, T.static_root, T.objs, (int)P.n_dyn, T.root_out);
-  __syncthreads();
-  if (T.groups) build_moved_groups_block(T.objs, (int)P.n_dyn, P.moved, T.groups);
+  build_top_and_groups(T.wnodes, T.tris, T.top_off, T.static_root, T.objs, (int)P.n_dyn, T.root_out, P.moved,
+                       T.groups);
 }
 
 // Pose bookkeeping of every slot, then (when objects moved) the top level
@@ -472,11 +468,8 @@ __global__ void __launch_bounds__(256) k_refit_wide(XformParams P, RefitArgs R, 
 __global__ void k_frame_top(XformParams P, DynObj* objs, float* xf_old, float* xf_new, int* obox, WNode* wnodes,
                             const Tri* tris, int top_off, int static_root, int* root_out, MovedGroups* groups) {
   pose_bookkeeping(P.xf, P.moved, P.n_dyn, objs, xf_old, xf_new, obox);
-  __syncthreads();
   if (!P.moved) return;
-  build_top_block(wnodes, tris, top_off, static_root, objs, (int)P.n_dyn, root_out);
-  __syncthreads();
-  if (groups) build_moved_groups_block(objs, (int)P.n_dyn, P.moved, groups);
+  build_top_and_groups(wnodes, tris, top_off, static_root, objs, (int)P.n_dyn, root_out, P.moved, groups);
 }
 
 

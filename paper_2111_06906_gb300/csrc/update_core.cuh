@@ -4,6 +4,7 @@
 // refresh of the wide nodes from it, and the top level over the static root
 // and the object roots.
 #pragma once
+#include <climits>
 #include <cstring>
 
 #include "pv_scene.h"
@@ -125,6 +126,17 @@ struct RefitArgs {
   int* obox;
 };
 
+// Arrival of one child at a wide node: an atomic increment of the node's
+// count with release (this thread's slot stores are visible to whoever sees
+// the count) and acquire (the slots of the children that arrived before are
+// visible to this thread's loads) semantics at GPU scope; returns the count
+// before.
+__device__ __forceinline__ uint32_t arrive(uint32_t* count) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
+  return old;
+}
+
 __device__ __forceinline__ void refit_tri(const float* xf_slot, bool moved_lane, uint32_t s, const RefitArgs& R,
                                           uint32_t i) {
   const int lane = threadIdx.x & 31;
@@ -134,19 +146,35 @@ __device__ __forceinline__ void refit_tri(const float* xf_slot, bool moved_lane,
     T = xform_tri(xf_slot, R.local + 9 * (size_t)i, R.prim[i], lo, hi);
     R.dtris[i] = T;
   }
-  // the lanes of one object reduce its exact box, one of them adds it
+  // The object's exact box: the lanes of one object reduce theirs, one of
+  // them adds it to the block's (shared memory), and the block adds its
+  // boxes to the objects' (one global atomic per object and bound that the
+  // block holds, where one per warp made the objects' few words a queue).
+  __shared__ int s_obox[kMaxDyn * 6];
+  for (int j = threadIdx.x; j < kMaxDyn * 6; j += blockDim.x) s_obox[j] = j % 6 < 3 ? INT_MAX : INT_MIN;
+  __syncthreads();
   const unsigned same = __match_any_sync(0xffffffffu, moved_lane ? (int)s : -1);
-  if (!moved_lane) return;
-  const int leader = __ffs(same) - 1;
+  if (moved_lane) {
+    const int leader = __ffs(same) - 1;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const int l = __reduce_min_sync(same, ord_of(lo[k]));
-    const int h = __reduce_max_sync(same, ord_of(hi[k]));
-    if (lane == leader) {
-      atomicMin(R.obox + 6 * s + k, l);
-      atomicMax(R.obox + 6 * s + 3 + k, h);
+    for (int k = 0; k < 3; ++k) {
+      const int l = __reduce_min_sync(same, ord_of(lo[k]));
+      const int h = __reduce_max_sync(same, ord_of(hi[k]));
+      if (lane == leader) {
+        atomicMin(s_obox + 6 * s + k, l);
+        atomicMax(s_obox + 6 * s + 3 + k, h);
+      }
     }
   }
+  __syncthreads();
+  for (int j = threadIdx.x; j < kMaxDyn * 6; j += blockDim.x) {
+    const int v = s_obox[j];
+    if (j % 6 < 3 ? v != INT_MAX : v != INT_MIN) {
+      if (j % 6 < 3) atomicMin(R.obox + j, v);
+      else atomicMax(R.obox + j, v);
+    }
+  }
+  if (!moved_lane) return;
   float3 blo, bhi;
   tri_box(T, blo, bhi);
   pad_box(blo, bhi);
@@ -160,9 +188,8 @@ __device__ __forceinline__ void refit_tri(const float* xf_slot, bool moved_lane,
     (&nd->hiy.x)[c] = bhi.y;
     (&nd->loz.x)[c] = blo.z;
     (&nd->hiz.x)[c] = bhi.z;
-    __threadfence();
     const uint32_t m = R.w_nch[w];
-    if (atomicAdd(R.w_arrive + w, 1u) + 1u < m) return;
+    if (arrive(R.w_arrive + w) + 1u < m) return;
     R.w_arrive[w] = 0u;                        // every child of this frame has arrived
     blo = make_float3(3.0e38f, 3.0e38f, 3.0e38f);
     bhi = make_float3(-3.0e38f, -3.0e38f, -3.0e38f);
@@ -310,177 +337,217 @@ __device__ __forceinline__ void ref_box(const WNode* wnodes, const Tri* tris, in
 // Top level over the static root and the dynamic objects' roots, rebuilt in
 // every frame in which objects move: entries sorted along the axis of
 // largest centroid spread and cut into four consecutive groups,
-// recursively.  build_top_from builds it by one thread from n entries
-// (reference, box) in slot order.
-__device__ __forceinline__ void build_top_from(float (*box)[6], const int* ref, int n, WNode* wnodes, int top_off,
-                                               int* root_out);
+// recursively.  The moved objects' groups (MovedGroups) come from the same
+// sort over the moved objects' old-and-new boxes, cut into runs of
+// kGroupSize.  Both are built by one warp each: the centroid bounds by
+// shuffles, the sort by ranks (entry i goes to position #{j: key_j < key_i}
+// + #{j < i: key_j = key_i}, the stable ascending order), the top level's
+// node ranges by one lane, and the nodes' boxes by a lane per node.
 
-// The top level over the static root and the objects' roots: the entries'
-// boxes are gathered by all threads of the block into shared memory (the
-// dependent loads of the roots overlap), then thread 0 builds.  Called by
-// every thread of the block.
-__device__ __forceinline__ void build_top_block(WNode* wnodes, const Tri* tris, int top_off, int static_root,
-                                                const DynObj* objs, int n_dyn, int* root_out) {
-  __shared__ float s_box[kMaxDyn + 1][6];
-  __shared__ int s_ref[kMaxDyn + 1];
-  for (int e = threadIdx.x; e <= n_dyn; e += blockDim.x) {   // entry 0: the static root; 1 + s: slot s
-    const int r = e == 0 ? static_root : objs[e - 1].wroot;
-    s_ref[e] = r;
-    if (r != INT32_MIN) ref_box(wnodes, tris, r, s_box[e]);
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  int n = 0;
-  for (int e = 0; e <= n_dyn; ++e) {           // keep the valid entries in order
-    if (s_ref[e] == INT32_MIN) continue;
-    if (n != e) {
-      s_ref[n] = s_ref[e];
-      for (int k = 0; k < 6; ++k) s_box[n][k] = s_box[e][k];
-    }
-    ++n;
-  }
-  build_top_from(s_box, s_ref, n, wnodes, top_off, root_out);
-}
-
-__device__ __forceinline__ void build_top_from(float (*box)[6], const int* ref, int n, WNode* wnodes, int top_off,
-                                               int* root_out) {
-  if (n == 0) {
-    *root_out = INT32_MIN;
-    return;
-  }
-  if (n == 1) {
-    *root_out = ref[0];
-    return;
-  }
+// Stable ascending order of n <= kMaxDyn + 1 boxes by the centroid along the
+// axis of largest centroid spread (ties to the first axis).  One warp.
+__device__ __forceinline__ void sort_by_centroid(const float (*box)[6], int n, float* key, int* order, int lane) {
   float clo[3] = {3e38f, 3e38f, 3e38f}, chi[3] = {-3e38f, -3e38f, -3e38f};
-  for (int i = 0; i < n; ++i)
+  for (int i = lane; i < n; i += 32)
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
       const float c = 0.5f * (box[i][k] + box[i][3 + k]);
       clo[k] = fminf(clo[k], c);
       chi[k] = fmaxf(chi[k], c);
     }
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      clo[k] = fminf(clo[k], __shfl_xor_sync(0xffffffffu, clo[k], o));
+      chi[k] = fmaxf(chi[k], __shfl_xor_sync(0xffffffffu, chi[k], o));
+    }
   int ax = 0;
   for (int k = 1; k < 3; ++k)
     if (chi[k] - clo[k] > chi[ax] - clo[ax]) ax = k;
+  for (int i = lane; i < n; i += 32) key[i] = box[i][ax] + box[i][3 + ax];
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) {
+    const float ki = key[i];
+    int r = 0;
+    for (int j = 0; j < n; ++j) {
+      const float kj = key[j];
+      r += (kj < ki) | ((kj == ki) & (j < i));
+    }
+    order[r] = i;
+  }
+  __syncwarp();
+}
+
+constexpr int kMaxTopNodes = 32;               // internal top-level nodes over at most kMaxDyn + 1 entries
+
+struct TopSmem {
+  float box[kMaxDyn + 1][6];                   // entry 0: the static root; 1 + s: slot s
+  int ref[kMaxDyn + 1];
+  float cbox[kMaxDyn + 1][6];                  // the valid entries, in entry order
+  int cref[kMaxDyn + 1];
+  float key[kMaxDyn + 1];
   int order[kMaxDyn + 1];
-  for (int i = 0; i < n; ++i) order[i] = i;
-  for (int i = 1; i < n; ++i) {
-    const int v = order[i];
-    const float cv = box[v][ax] + box[v][3 + ax];
-    int j = i - 1;
-    while (j >= 0 && box[order[j]][ax] + box[order[j]][3 + ax] > cv) {
-      order[j + 1] = order[j];
-      --j;
-    }
-    order[j + 1] = v;
-  }
-  int st_b[kMaxDyn + 2], st_e[kMaxDyn + 2], st_node[kMaxDyn + 2];
-  int sp = 1, next = 1;
-  st_b[0] = 0;
-  st_e[0] = n;
-  st_node[0] = top_off;
-  while (sp > 0) {
-    --sp;
-    const int b = st_b[sp], e = st_e[sp], node = st_node[sp];
-    const int size = e - b;
-    const int groups = size < 4 ? size : 4;
-    float cb[4][6];
-    int child[4];
-    for (int g = 0; g < groups; ++g) {
-      const int gb = b + (size * g) / groups, ge = b + (size * (g + 1)) / groups;
-      for (int k = 0; k < 3; ++k) {
-        cb[g][k] = 3e38f;
-        cb[g][3 + k] = -3e38f;
-      }
-      for (int i = gb; i < ge; ++i)
-        for (int k = 0; k < 3; ++k) {
-          cb[g][k] = fminf(cb[g][k], box[order[i]][k]);
-          cb[g][3 + k] = fmaxf(cb[g][3 + k], box[order[i]][3 + k]);
-        }
-      if (ge - gb == 1) {
-        child[g] = ref[order[gb]];
-      } else {
-        child[g] = top_off + next++;
-        st_b[sp] = gb;
-        st_e[sp] = ge;
-        st_node[sp] = child[g];
-        ++sp;
-      }
-    }
-    write_wide(wnodes + node, cb, child, groups);
-  }
-  *root_out = top_off;
-}
+  int nn;                                      // internal nodes, in the order they are numbered
+  int node[kMaxTopNodes], ng[kMaxTopNodes];
+  int gb[kMaxTopNodes][4], ge[kMaxTopNodes][4], child[kMaxTopNodes][4];
+  int sb[kMaxTopNodes], se[kMaxTopNodes], sn[kMaxTopNodes];
+};
 
-// The moved objects' groups of this frame (see MovedGroups) from their n
-// old-and-new boxes (box[i], slot[i]) in slot order: one thread.
-__device__ __forceinline__ void moved_groups_from(float (*box)[6], const int* slot, int n, MovedGroups* g);
-
-// Gathered by every thread of the block (the slots' boxes load side by
-// side), grouped by thread 0.  Called by every thread of the block.
-__device__ __forceinline__ void build_moved_groups_block(const DynObj* objs, int n_dyn, uint64_t moved, MovedGroups* g) {
-  __shared__ float s_box[kMaxDyn][6];
-  __shared__ int s_slot[kMaxDyn];
-  const int nd = min(n_dyn, kMaxDyn);
-  for (int i = threadIdx.x; i < nd * 6; i += blockDim.x) {
-    const int s = i / 6, k = i % 6;
-    if ((moved >> s) & 1ull)
-      s_box[s][k] = k < 3 ? fminf(objs[s].box_new[k], objs[s].box_old[k]) : fmaxf(objs[s].box_new[k], objs[s].box_old[k]);
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  int n = 0;
-  for (int s = 0; s < nd; ++s) {               // the moved slots, in order
-    if (!((moved >> s) & 1ull)) continue;
-    if (n != s)
-      for (int k = 0; k < 6; ++k) s_box[n][k] = s_box[s][k];
-    s_slot[n++] = s;
-  }
-  moved_groups_from(s_box, s_slot, n, g);
-}
-
-__device__ __forceinline__ void moved_groups_from(float (*box)[6], const int* slot, int n, MovedGroups* g) {
-  float clo[3] = {3e38f, 3e38f, 3e38f}, chi[3] = {-3e38f, -3e38f, -3e38f};
-  for (int i = 0; i < n; ++i)
-    for (int k = 0; k < 3; ++k) {
-      const float c = 0.5f * (box[i][k] + box[i][3 + k]);
-      clo[k] = fminf(clo[k], c);
-      chi[k] = fmaxf(chi[k], c);
-    }
-  int ax = 0;
-  for (int k = 1; k < 3; ++k)
-    if (chi[k] - clo[k] > chi[ax] - clo[ax]) ax = k;
+struct MovedSmem {
+  float box[kMaxDyn][6];                       // moved objects' old u new boxes, in slot order
+  int slot[kMaxDyn];
+  float key[kMaxDyn];
   int order[kMaxDyn];
-  for (int i = 0; i < n; ++i) order[i] = i;
-  for (int i = 1; i < n; ++i) {                 // insertion sort by centroid along ax
-    const int v = order[i];
-    const float cv = box[v][ax] + box[v][3 + ax];
-    int j = i - 1;
-    while (j >= 0 && box[order[j]][ax] + box[order[j]][3 + ax] > cv) {
-      order[j + 1] = order[j];
-      --j;
+};
+
+// The top level from the gathered entries of ts (one warp).
+__device__ __forceinline__ void top_build_warp(TopSmem& ts, int n_dyn, WNode* wnodes, int top_off, int* root_out,
+                                               int lane) {
+  int n = 0;                                   // keep the valid entries in order
+  for (int e0 = 0; e0 <= n_dyn; e0 += 32) {
+    const int e = e0 + lane;
+    const bool v = e <= n_dyn && ts.ref[e] != INT32_MIN;
+    const unsigned b = __ballot_sync(0xffffffffu, v);
+    if (v) {
+      const int j = n + __popc(b & ((1u << lane) - 1u));
+      ts.cref[j] = ts.ref[e];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) ts.cbox[j][k] = ts.box[e][k];
     }
-    order[j + 1] = v;
+    n += __popc(b);
   }
-  const int ng = (n + kGroupSize - 1) / kGroupSize;
-  for (int q = 0; q < ng; ++q) {
+  __syncwarp();
+  if (n <= 1) {
+    if (lane == 0) *root_out = n == 0 ? INT32_MIN : ts.cref[0];
+    return;
+  }
+  sort_by_centroid(ts.cbox, n, ts.key, ts.order, lane);
+  if (lane == 0) {                             // node ranges, numbered as they are pushed
+    int sp = 1, next = 1, nn = 0;
+    ts.sb[0] = 0;
+    ts.se[0] = n;
+    ts.sn[0] = top_off;
+    while (sp > 0 && nn < kMaxTopNodes) {
+      --sp;
+      const int b = ts.sb[sp], e = ts.se[sp], node = ts.sn[sp];
+      const int size = e - b;
+      const int groups = size < 4 ? size : 4;
+      ts.node[nn] = node;
+      ts.ng[nn] = groups;
+      for (int g = 0; g < groups; ++g) {
+        const int gb = b + (size * g) / groups, ge = b + (size * (g + 1)) / groups;
+        ts.gb[nn][g] = gb;
+        ts.ge[nn][g] = ge;
+        if (ge - gb == 1) {
+          ts.child[nn][g] = ts.cref[ts.order[gb]];
+        } else {
+          ts.child[nn][g] = top_off + next++;
+          ts.sb[sp] = gb;
+          ts.se[sp] = ge;
+          ts.sn[sp] = ts.child[nn][g];
+          ++sp;
+        }
+      }
+      ++nn;
+    }
+    ts.nn = nn;
+    *root_out = top_off;
+  }
+  __syncwarp();
+  for (int k = lane; k < ts.nn; k += 32) {     // each node's group boxes, by one lane
+    float cb[4][6];
+    int ch[4];
+    const int groups = ts.ng[k];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        cb[g][c] = 3e38f;
+        cb[g][3 + c] = -3e38f;
+      }
+      ch[g] = INT32_MIN;
+      if (g < groups) {
+        ch[g] = ts.child[k][g];
+        for (int i = ts.gb[k][g]; i < ts.ge[k][g]; ++i) {
+          const float* bx = ts.cbox[ts.order[i]];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            cb[g][c] = fminf(cb[g][c], bx[c]);
+            cb[g][3 + c] = fmaxf(cb[g][3 + c], bx[3 + c]);
+          }
+        }
+      }
+    }
+    write_wide(wnodes + ts.node[k], cb, ch, groups);
+  }
+}
+
+// The moved objects' groups of this frame (one warp).
+__device__ __forceinline__ void moved_groups_warp(MovedSmem& ms, const DynObj* objs, int n_dyn, uint64_t moved,
+                                                  MovedGroups* g, int lane) {
+  const int nd = min(n_dyn, kMaxDyn);
+  int n = 0;                                   // the moved slots, in order
+  for (int s0 = 0; s0 < nd; s0 += 32) {
+    const int s = s0 + lane;
+    const bool m = s < nd && ((moved >> s) & 1ull);
+    const unsigned b = __ballot_sync(0xffffffffu, m);
+    if (m) {
+      const int j = n + __popc(b & ((1u << lane) - 1u));
+      ms.slot[j] = s;
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        ms.box[j][k] = k < 3 ? fminf(objs[s].box_new[k], objs[s].box_old[k])
+                             : fmaxf(objs[s].box_new[k], objs[s].box_old[k]);
+    }
+    n += __popc(b);
+  }
+  __syncwarp();
+  sort_by_centroid(ms.box, n, ms.key, ms.order, lane);
+  const int ngr = (n + kGroupSize - 1) / kGroupSize;
+  for (int q = lane; q < ngr; q += 32) {
     float b[6] = {3e38f, 3e38f, 3e38f, -3e38f, -3e38f, -3e38f};
     for (int m = 0; m < kGroupSize; ++m) {
       const int i = q * kGroupSize + m;
       if (i < n) {
-        const int o = order[i];
+        const int o = ms.order[i];
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
-          b[k] = fminf(b[k], box[o][k]);
-          b[3 + k] = fmaxf(b[3 + k], box[o][3 + k]);
+          b[k] = fminf(b[k], ms.box[o][k]);
+          b[3 + k] = fmaxf(b[3 + k], ms.box[o][3 + k]);
         }
-        g->slot[q][m] = (int8_t)slot[o];
+        g->slot[q][m] = (int8_t)ms.slot[o];
       } else {
         g->slot[q][m] = -1;
       }
     }
+#pragma unroll
     for (int k = 0; k < 6; ++k) g->box[q][k] = b[k];
   }
-  g->n = (uint32_t)ng;
+  if (lane == 0) g->n = (uint32_t)ngr;
+}
+
+// The top level (and, given a group table, the moved objects' groups):
+// every thread of the block gathers the entries' boxes (the dependent loads
+// of the roots overlap), then warp 0 builds the top level while warp 1 (warp
+// 0 too in a one-warp block) builds the groups.  Called by every thread of
+// the block right after pose_bookkeeping: the gather reads nothing that the
+// bookkeeping writes, and its barrier orders the bookkeeping's object boxes
+// before the groups read them.
+__device__ __forceinline__ void build_top_and_groups(WNode* wnodes, const Tri* tris, int top_off, int static_root,
+                                                     const DynObj* objs, int n_dyn, int* root_out, uint64_t moved,
+                                                     MovedGroups* groups) {
+  __shared__ TopSmem ts;
+  __shared__ MovedSmem ms;
+  for (int e = threadIdx.x; e <= n_dyn; e += blockDim.x) {   // entry 0: the static root; 1 + s: slot s
+    const int r = e == 0 ? static_root : objs[e - 1].wroot;
+    ts.ref[e] = r;
+    if (r != INT32_MIN) ref_box(wnodes, tris, r, ts.box[e]);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) top_build_warp(ts, n_dyn, wnodes, top_off, root_out, lane);
+  if (groups && warp == (blockDim.x >= 64 ? 1 : 0)) moved_groups_warp(ms, objs, n_dyn, moved, groups, lane);
 }
 
 }  // namespace pvk

@@ -128,37 +128,73 @@ struct GroupSmem {
   int n;
 };
 
-// Segment a->b against every moved object.  Box tests reject first against
-// the union of all moved boxes, then against each group's box, and test a
-// group's members only when its box is met.  A box that contains another
-// never rejects what the slab test accepts for the inner one (the slab
-// bounds are monotone in the face coordinates), so the result is that of
-// testing every moved object.
+// Axis-aligned bounds of the segment a->b, widened by m = 2^-18 max|coord|
+// + 1e-19, so that every box seg_box accepts overlaps them.  Why m covers
+// seg_box's rounding: a plane distance there is fma(plane, inv, -a inv) with
+// inv within 2^-22 of 1/d and d = fl(b - a); an accepted box has, on each
+// axis, its near distance <= 1 and its far distance >= 0, which puts its
+// near face at most 2^-20 (|b - a| + |a|) <= 3 x 2^-20 max|coord| beyond b
+// and its far face at most 2^-24 |a| short of a (for a direction component
+// clamped to 1e-20, at most 1.01e-20 beyond a).  The overlap test is exact,
+// so it culls no box that seg_box would accept.
+struct SegBounds {
+  float3 lo, hi;
+};
+
+__device__ __forceinline__ SegBounds seg_bounds(float3 a, float3 b) {
+  const float mag = fmax3(fmax3(fabsf(a.x), fabsf(a.y), fabsf(a.z)), fmax3(fabsf(b.x), fabsf(b.y), fabsf(b.z)), 0.0f);
+  const float m = fmaf(mag, 3.814697265625e-06f, 1e-19f);
+  SegBounds s;
+  s.lo = make_float3(fminf(a.x, b.x) - m, fminf(a.y, b.y) - m, fminf(a.z, b.z) - m);
+  s.hi = make_float3(fmaxf(a.x, b.x) + m, fmaxf(a.y, b.y) + m, fmaxf(a.z, b.z) + m);
+  return s;
+}
+
+// Closed box bx (lo xyz, hi xyz) against the widened segment bounds.
+__device__ __forceinline__ bool seg_overlaps(const SegBounds& s, const float* bx) {
+  return (s.lo.x <= bx[3]) & (s.hi.x >= bx[0]) & (s.lo.y <= bx[4]) & (s.hi.y >= bx[1]) & (s.lo.z <= bx[5]) &
+         (s.hi.z >= bx[2]);
+}
+
+// Segment a->b against every moved object.  Box tests cull first by the
+// segment's widened bounds against the union of all moved boxes, then
+// against each group's box, and run the slab test (seg_box) only on members
+// whose box the bounds overlap (its reciprocals computed once the union
+// cull has passed).  Neither cull rejects a box that seg_box accepts
+// (seg_bounds), and a box that contains another overlaps whatever the inner
+// one does, so the result is that of the slab test against every moved
+// object.
 template <int S = kStack>
 __device__ __forceinline__ bool seg_vs_moved(const SceneView& sv, const float* cull, const float* uni,
                                              const GroupSmem& gs, bool boxes, bool test_old, float3 a, float3 b,
                                              Work& wk) {
-  const Seg g = seg_prep(sv, a, b, boxes);
   if (boxes) {
-    if (!seg_box(g.inv, g.aoi, uni + 6 * kMaxDyn)) return false;
+    const SegBounds sb = seg_bounds(a, b);
+    if (!seg_overlaps(sb, uni + 6 * kMaxDyn)) return false;
+    const Seg g = seg_prep(sv, a, b, true);
+    auto slab = [&](const float* bx) { return seg_box(g.inv, g.aoi, bx); };
     if (gs.n == 0) {                           // no group table: every moved object in turn
-      for (uint64_t m = sv.moved; m; m &= m - 1)
-        if (seg_box(g.inv, g.aoi, uni + 6 * (__ffsll((long long)m) - 1))) return true;
+      for (uint64_t m = sv.moved; m; m &= m - 1) {
+        const float* bx = uni + 6 * (__ffsll((long long)m) - 1);
+        if (seg_overlaps(sb, bx) && slab(bx)) return true;
+      }
       return false;
     }
     for (int q = 0; q < gs.n; ++q) {
-      if (gs.n > 1 && !seg_box(g.inv, g.aoi, gs.box[q])) continue;   // one group: its box is the union
+      if (gs.n > 1 && !seg_overlaps(sb, gs.box[q])) continue;   // one group: its box is the union
 #pragma unroll
       for (int m = 0; m < kGroupSize; ++m) {
         const int s = gs.slot[q][m];
         if (s < 0) break;
-        if (seg_box(g.inv, g.aoi, uni + 6 * s)) return true;
+        const float* bx = uni + 6 * s;
+        if (seg_overlaps(sb, bx) && slab(bx)) return true;
       }
     }
     return false;
   }
+  const Seg g = seg_prep(sv, a, b, false);
   for (uint64_t m = sv.moved; m; m &= m - 1)
-    if (seg_vs_object<S>(sv, g, cull, uni, boxes, test_old, __ffsll((long long)m) - 1, wk)) return true;
+    if (seg_vs_object<S>(sv, g, cull, uni, false, test_old, __ffsll((long long)m) - 1, wk)) return true;
   return false;
 }
 

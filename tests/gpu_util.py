@@ -79,15 +79,17 @@ def compare(gpu: oracle.Paths, orc: oracle.Paths, diag: float, skip=None, pos_to
     """Field-by-field comparison of two record sets (same ids).  Paths with no
     ambiguous decision must match the oracle's records.  A path the oracle
     flags ambiguous (now or at an earlier check) must match one of the
-    records it admits: the oracle runs the steps since the last check from
-    each record accepted then, with every ambiguous decision taking each of
-    its admissible outcomes (oracle.OracleScene.outcomes).  With ``sync``
+    records it admits: the oracle's own record (one of them), else one the
+    oracle lists by running the steps since the last check from each record
+    accepted then, with every ambiguous decision taking each of its
+    admissible outcomes (oracle.OracleScene.outcomes).  With ``sync``
     the accepted records are kept for the next check, and the oracle's own
     records of those paths become the first accepted one, so that later
     steps start from the outcome the device took.  ``skip`` excludes paths
     altogether.  Returns a dict of counts; every ``bad_*`` entry must be
-    zero for parity; ``ambiguous_unchecked`` counts flagged paths whose
-    steps cannot be listed per path (distribution maps), and
+    zero for parity; ``ambiguous_unchecked`` counts flagged paths that
+    differ from the oracle's own record and whose steps cannot be listed per
+    path (distribution maps), and
     ``ambiguous_open`` flagged paths matching no listed record whose search
     met a hit distance the band leaves undetermined along a stretch of the
     ray (a ray within eps of a triangle's plane, where any point of the
@@ -110,9 +112,18 @@ def compare(gpu: oracle.Paths, orc: oracle.Paths, diag: float, skip=None, pos_to
     new_branches = {}
     o = orc.oracle
     B = orc.photons.shape[1]
-    for i in np.nonzero(amb & ~skipped)[0].tolist():
+    flagged = np.nonzero(amb & ~skipped)[0]
+    # the oracle's own record is one of the admitted outcomes: a flagged path that matches it needs no listing
+    own, _ = _mismatch(gpu.info[flagged], gpu.origin[flagged], gpu.photons[flagged], orc.info[flagged],
+                       orc.origin[flagged], orc.photons[flagged], diag, pos_tol, e_rtol, check_info_bits)
+    own_ok = ~np.any(np.stack(list(own.values())), axis=0) if len(flagged) else np.zeros(0, bool)
+    for j, i in enumerate(flagged.tolist()):
         if i in orc.opened:                   # open at an earlier check: the two sides' records have parted
             r["ambiguous_open"] += 1
+            continue
+        if own_ok[j]:
+            r["ambiguous_matched"] += 1
+            new_branches[i] = [(int(orc.info[i]), orc.origin[i].copy(), orc.photons[i].copy())]
             continue
         if orc.snap is None:
             bases = [(0, np.zeros(3, np.float32), np.zeros((B, 8), np.float32))]
@@ -164,6 +175,57 @@ def compare(gpu: oracle.Paths, orc: oracle.Paths, diag: float, skip=None, pos_to
         orc.branches = new_branches
         orc.adopt_branches()              # the oracle goes on from the outcome the device's result agreed with
     return r
+
+
+def position_difference(gpu: oracle.Paths, orc: oracle.Paths) -> np.ndarray:
+    """Per stored photon and axis, |gpu - oracle| of the two record sets'
+    positions (same ids): float64 [n, B, 3], 0 past a path's photon count."""
+    L = np.minimum((gpu.info >> 22) & 15, (orc.info >> 22) & 15)
+    kk = np.arange(gpu.photons.shape[1])[None, :] < L[:, None]
+    return np.abs(gpu.photons[..., :3].astype(np.float64) - orc.photons[..., :3]) * kk[..., None]
+
+
+def check_deposit(got: np.ndarray, q: oracle.Paths, width: int, height: int, rect, S: int, band,
+                  e_rtol: float = 1e-5) -> int:
+    """Texel-by-texel check of a device atlas ``got`` (float64 [height,
+    width, 3], energy units) holding the deposit of the paths q, against the
+    oracle's deposit of q.  ``band`` bounds how far the device's photon
+    positions lie from q's (a distance, or per photon and axis [n, B, 3]),
+    so a photon that close to a texel edge may fall on either side: such a
+    photon may land in any texel its position reaches within its band, while
+    every other photon's texel is fixed.  Each texel must hold its fixed
+    photons' energy plus at most that of the edge photons that may land
+    there (within e_rtol and one fixed-point quantum 2^-S per photon), and
+    the atlas's total must match.  Returns the number of edge photons."""
+    band = np.broadcast_to(np.asarray(band, np.float64), q.photons[..., :3].shape)
+    lo, hi = q.copy(), q.copy()
+    for a in (0, 2):
+        lo.photons[..., a] = (q.photons[..., a] - band[..., a]).astype(np.float32)
+        hi.photons[..., a] = (q.photons[..., a] + band[..., a]).astype(np.float32)
+    tl = oracle.photon_texels(lo, width, height, rect)
+    th = oracle.photon_texels(hi, width, height, rect)
+    valid = tl[..., 0] >= 0
+    fixed = valid & (tl == th).all(axis=-1)
+    edge = valid & ~fixed
+    E = q.photons[..., 4:7].astype(np.float64)
+    want, cnt = np.zeros((height, width, 3)), np.zeros((height, width))
+    np.add.at(want, (tl[fixed][:, 1], tl[fixed][:, 0]), E[fixed])
+    np.add.at(cnt, (tl[fixed][:, 1], tl[fixed][:, 0]), 1.0)
+    extra, ecnt = np.zeros_like(want), np.zeros_like(cnt)
+    for (xl, zl), (xh, zh), e in zip(tl[edge], th[edge], E[edge]):
+        for z in {int(zl), int(zh)}:
+            for x in {int(xl), int(xh)}:
+                extra[z, x] += e
+                ecnt[z, x] += 1.0
+    quantum = 2.0 ** -S
+    low = want * (1 - e_rtol) - cnt[..., None] * quantum
+    high = (want + extra) * (1 + e_rtol) + (cnt + ecnt)[..., None] * quantum
+    assert np.all(got >= low), float(np.max(low - got))
+    assert np.all(got <= high), float(np.max(got - high))
+    n_ph = int(valid.sum())
+    total = E[valid].sum(axis=0)
+    assert np.all(np.abs(got.sum(axis=(0, 1)) - total) <= e_rtol * np.abs(total) + n_ph * quantum)
+    return int(edge.sum())
 
 
 def assert_parity(r: dict, allow_unchecked: bool = False) -> None:

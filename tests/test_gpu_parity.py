@@ -349,28 +349,32 @@ def _sampled_full_size_fused(sc, n_sample, check_frames=(2, 15, 30), tau=0.01):
         stats += [ost, ost2]
         if f not in check_frames:
             continue
-        r = gu.compare(gu.download(P, ids), q, sc.diag)
+        g = gu.download(P, ids)
+        r = gu.compare(g, q, sc.diag)
         share = gu.ambiguous_share(*stats)
         print(sc.name, "frame", f, r, "ambiguous query share", share, pv.stats_dict(st))
         gu.assert_parity(r)
         ref = torch.zeros_like(atlas)
         pv.pv_deposit(h, P, ref, sc.atlas_rect, S)
         assert torch.equal(atlas, ref)
-        # the sampled paths alone, deposited on both sides
+        # the sampled paths alone (less those whose records parted at an open search), deposited on both sides
+        keep = np.array([i not in q.opened for i in range(n_sample)])
+        ks = sel[torch.as_tensor(keep, device="cuda")]
         sampled.info.zero_()
-        sampled.info[sel] = P.info[sel]
-        sampled.origin[:, sel] = P.origin[:, sel]
-        sampled.pa[:, sel] = P.pa[:, sel]
-        sampled.pb[:, sel] = P.pb[:, sel]
+        sampled.info[ks] = P.info[ks]
+        sampled.origin[:, ks] = P.origin[:, ks]
+        sampled.pa[:, ks] = P.pa[:, ks]
+        sampled.pb[:, ks] = P.pb[:, ks]
         pv.pv_deposit(h, sampled, ref, sc.atlas_rect, S)
         got = ref.cpu().numpy().astype(np.float64) / 2.0 ** S
-        want = oracle.deposit(q, A, A, sc.atlas_rect)
-        ones = q.copy()
-        ones.photons[..., 4:7] = 1.0
-        cnt = oracle.deposit(ones, A, A, sc.atlas_rect)[..., 0]
-        tol = 1e-5 * np.abs(want) + cnt[..., None] * 2.0 ** -S
-        assert np.all(np.abs(got - want) <= tol), float(np.abs(got - want).max())
-        assert (want > 0).sum() > 1000
+        qk = q.subset(np.nonzero(keep)[0])
+        # each photon may fall on the far side of a texel edge its device position lies across
+        band = 2.0 * gu.position_difference(g.subset(np.nonzero(keep)[0]), qk) + 1e-9 * sc.diag
+        n_edge = gu.check_deposit(got, qk, A, A, sc.atlas_rect, S, band)
+        n_ph = int(np.minimum((qk.info >> 22) & 15, sc.max_bounces).sum())
+        print(sc.name, "frame", f, "sampled photons", n_ph, "near a texel edge", n_edge)
+        assert n_edge <= max(8, 0.01 * n_ph)
+        assert (got > 0).sum() > 1000
     assert pv.pv_read_device_status(h) == 0
     pv.pv_destroy_scene(h)
     return stats
