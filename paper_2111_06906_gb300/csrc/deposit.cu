@@ -10,8 +10,11 @@ namespace {
 __global__ void __launch_bounds__(256) k_deposit(uint32_t n, uint32_t B, const uint32_t* info, const float4* pa,
                                                  const float4* pb, pv_atlas at) {
   const AtlasMap am = atlas_map(at);
-  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
-    deposit_path(am, n, B, info, pa, pb, p);
+  // whole warps loop, so that the photons of each round's 32 paths are dealt out over the lanes
+  for (uint32_t b = blockIdx.x * blockDim.x; b < n; b += gridDim.x * blockDim.x) {
+    const uint32_t p = b + threadIdx.x;
+    deposit_warp(am, n, B, info, pa, pb, p < n ? p : 0xFFFFFFFFu);
+  }
 }
 
 }  // namespace

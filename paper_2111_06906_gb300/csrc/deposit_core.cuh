@@ -83,4 +83,46 @@ __device__ __forceinline__ void deposit_path(const AtlasMap& am, uint32_t n, uin
   deposit_rows<false>(am, n, min(info_nseg(__ldcs(info + p)), B), pa, pb, p);
 }
 
+// The photons of the paths p of the warp's lanes (0xFFFFFFFF: none) into the
+// atlas, dealt out over the lanes: photon q of the warp's list (paths in lane
+// order, each path's photons in order) goes to lane q mod 32, so every lane
+// has a photon in all but the last round, whatever the paths' lengths.
+// Called by all lanes of the warp.
+__device__ __forceinline__ void deposit_warp(const AtlasMap& am, uint32_t n, uint32_t B, const uint32_t* info,
+                                             const float4* pa, const float4* pb, uint32_t p) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t cnt = p != 0xFFFFFFFFu ? min(info_nseg(__ldcs(info + p)), B) : 0u;
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  const pv_atlas& at = am.at;
+  for (uint32_t base = 0; base < total; base += 32) {
+    const uint32_t q = base + lane;
+    uint32_t lo = 0, hi = 31;                  // owner: first lane whose inclusive count exceeds q
+#pragma unroll
+    for (int it = 0; it < 5; ++it) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (q < __shfl_sync(0xffffffffu, incl, mid)) hi = mid;
+      else lo = mid + 1;
+    }
+    const uint32_t o_incl = __shfl_sync(0xffffffffu, incl, lo), o_cnt = __shfl_sync(0xffffffffu, cnt, lo);
+    const uint32_t po = __shfl_sync(0xffffffffu, p, lo);
+    if (q >= total) continue;
+    const uint32_t k = q - (o_incl - o_cnt);
+    // streaming loads: the path buffers must not evict the atlas from L2
+    const float4 x = __ldcs(pa + (size_t)k * n + po);
+    const float4 e = __ldcs(pb + (size_t)k * n + po);
+    const int tx = atlas_texel(x.x, at.x0, am.sx, at.width);
+    const int tz = atlas_texel(x.z, at.z0, am.sz, at.height);
+    unsigned long long* t = reinterpret_cast<unsigned long long*>(at.data) + 3 * ((size_t)tz * at.width + tx);
+    atomicAdd(t, fixed_point(e.x, at.scale_log2));
+    atomicAdd(t + 1, fixed_point(e.y, at.scale_log2));
+    atomicAdd(t + 2, fixed_point(e.z, at.scale_log2));
+  }
+}
+
 }  // namespace pvk

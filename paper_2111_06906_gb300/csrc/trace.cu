@@ -43,6 +43,12 @@ namespace {
 #ifndef PV_CONT_TRACE_MIN_BLOCKS
 #define PV_CONT_TRACE_MIN_BLOCKS 7
 #endif
+// k_cont_trace with the deposit: 1 deals the photons of the paths the warp's
+// lanes finished out over its lanes (deposit_warp), 0 lets each lane deposit
+// its own path's photons.
+#ifndef PV_DEP_WARP
+#define PV_DEP_WARP 1
+#endif
 #ifndef PV_TRACE_MAX_STEPS
 #define PV_TRACE_MAX_STEPS 64
 #endif
@@ -233,7 +239,11 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_CONT_TRACE_MIN_BLOCKS)
   bool has_ray = false, exhausted = false, cont = false;
   uint32_t c_rays = 0, c_photons = 0;
   for (uint32_t guard = 0; guard < (1u << 30); ++guard) {
-    if (kDeposit && dep != 0xFFFFFFFFu) {
+    if (PV_DEP_WARP && kDeposit && __any_sync(0xffffffffu, dep != 0xFFFFFFFFu)) {
+      deposit_warp(atlas_map(D.at), A.n, sv.B, A.info, A.pa, A.pb, dep);   // scales per call: no registers held
+      dep = 0xFFFFFFFFu;
+    }
+    if (!PV_DEP_WARP && kDeposit && dep != 0xFFFFFFFFu) {
       deposit_path(atlas_map(D.at), A.n, sv.B, A.info, A.pa, A.pb, dep);   // scales per path: no registers held
       dep = 0xFFFFFFFFu;
     }
