@@ -84,38 +84,44 @@ __device__ __forceinline__ void deposit_path(const AtlasMap& am, uint32_t n, uin
 }
 
 // The photons of the paths p of the warp's lanes (0xFFFFFFFF: none) into the
-// atlas, dealt out over the lanes: photon q of the warp's list (paths in lane
-// order, each path's photons in order) goes to lane q mod 32, so every lane
-// has a photon in all but the last round, whatever the paths' lengths.
-// Called by all lanes of the warp.
+// atlas, dealt out over the lanes row by row: the warp's photon list is row 0
+// of every lane's path (in lane order), then row 1 of the paths that have
+// one, and so on, and photon q goes to lane q mod 32.  Every lane has a photon
+// in all but the last round, whatever the paths' lengths, and lanes next to
+// each other read the same row of paths next to each other (coalesced when
+// the warp's paths are consecutive).  Called by all lanes of the warp.
 __device__ __forceinline__ void deposit_warp(const AtlasMap& am, uint32_t n, uint32_t B, const uint32_t* info,
                                              const float4* pa, const float4* pb, uint32_t p) {
-  const int lane = threadIdx.x & 31;
+  const uint32_t lane = threadIdx.x & 31u;
   const uint32_t cnt = p != 0xFFFFFFFFu ? min(info_nseg(__ldcs(info + p)), B) : 0u;
-  uint32_t incl = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  const uint32_t rows = __reduce_max_sync(0xffffffffu, cnt);
   const pv_atlas& at = am.at;
-  for (uint32_t base = 0; base < total; base += 32) {
-    const uint32_t q = base + lane;
-    uint32_t lo = 0, hi = 31;                  // owner: first lane whose inclusive count exceeds q
-#pragma unroll
-    for (int it = 0; it < 5; ++it) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (q < __shfl_sync(0xffffffffu, incl, mid)) hi = mid;
-      else lo = mid + 1;
+  // kk: the first row not yet dealt out in full, cum: the photons of the rows before it, m: its paths' lanes
+  uint32_t kk = 0, cum = 0;
+  unsigned m = __ballot_sync(0xffffffffu, cnt > 0u);
+  for (uint32_t base = 0; kk < rows; base += 32) {
+    const uint32_t R = base + lane;            // this lane's photon rank
+    uint32_t k_own = rows, j_own = 0;
+    unsigned m_own = 0u;
+    // the rows this round covers (the same steps on every lane)
+    while (kk < rows && cum < base + 32) {
+      const uint32_t ck = __popc(m);
+      if (R >= cum && R < cum + ck) {
+        k_own = kk;
+        j_own = R - cum;
+        m_own = m;
+      }
+      if (cum + ck > base + 32) break;         // the row goes on in the next round
+      cum += ck;
+      ++kk;
+      m = __ballot_sync(0xffffffffu, cnt > kk);
     }
-    const uint32_t o_incl = __shfl_sync(0xffffffffu, incl, lo), o_cnt = __shfl_sync(0xffffffffu, cnt, lo);
-    const uint32_t po = __shfl_sync(0xffffffffu, p, lo);
-    if (q >= total) continue;
-    const uint32_t k = q - (o_incl - o_cnt);
+    const uint32_t owner = k_own < rows ? __fns(m_own, 0u, (int)j_own + 1) : 0u;
+    const uint32_t po = __shfl_sync(0xffffffffu, p, owner);
+    if (k_own >= rows) continue;
     // streaming loads: the path buffers must not evict the atlas from L2
-    const float4 x = __ldcs(pa + (size_t)k * n + po);
-    const float4 e = __ldcs(pb + (size_t)k * n + po);
+    const float4 x = __ldcs(pa + (size_t)k_own * n + po);
+    const float4 e = __ldcs(pb + (size_t)k_own * n + po);
     const int tx = atlas_texel(x.x, at.x0, am.sx, at.width);
     const int tz = atlas_texel(x.z, at.z0, am.sz, at.height);
     unsigned long long* t = reinterpret_cast<unsigned long long*>(at.data) + 3 * ((size_t)tz * at.width + tx);
