@@ -48,13 +48,22 @@ WORKLOADS = {
                "bounce caps 1 to 7, 1 to 4 moving tori; one batched graph-captured frame per step, tuned",
 }
 # Algorithmic FP32 work of a traversal: 20 operations per ray-box slab test (four per 4-wide node) and 35 per
-# watertight ray-triangle test, times the node visits and triangle tests the library counts.
+# Moller-Trumbore ray-triangle test, times the node visits and triangle tests the library counts.
 OPS_PER_SLAB, OPS_PER_TRI = 20, 35
 OPS_PER_NODE = 4 * OPS_PER_SLAB
-# DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum) of the reuse frame's kernels, from
-# the capture recorded under profiles/.  They hold only for the kernel sources they were captured on: the digest
-# of csrc/ and include/ at capture time.  Any other source digest reports no traffic.
-NCU_TRAFFIC = {"digest": None, "villa": {}, "city": {}}
+# DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, median over the launches of one
+# capture of this benchmark, summarised under profiles/) of the kernels in the per-kernel table.  They hold
+# only for the kernel sources they were captured on: the digest of csrc/ and include/ at capture time.  Any other
+# source digest reports no traffic.
+NCU_TRAFFIC = {
+    "digest": "1954ebdfb5fe3dc7",
+    "villa": {"k_refit_wide": 4268544, "k_verify_box": 367619328, "k_cont_trace<deposit>": 993705856,
+              "k_compact": 12016512, "k_trace (re-trace)": 201598720, "k_deposit": 644223744,
+              "k_trace (trace-all)": 843482880},
+    "city": {"k_refit_wide": 799232, "k_verify_box": 88083328, "k_cont_trace<deposit>": 218559744,
+             "k_compact": 4012288, "k_trace (re-trace)": 55488512, "k_deposit": 160777984,
+             "k_trace (trace-all)": 146506496},
+}
 TAUS = (0.0, 0.005, 0.01, 0.05)
 
 
@@ -554,7 +563,8 @@ def kernel_table(w, head_rows, inst, sep, rows_v, rows_r, ta, rows_ta, L_reuse, 
     def row(kernel, where, ms, nbytes, unit_note, ops=None):
         r = {"kernel": kernel, "timed": where, "duration_ms": ms, "algorithmic_bytes": nbytes,
              "bytes_per_unit": unit_note, "achieved_gbs": nbytes / (ms * 1e-3) / 1e9,
-             "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm_peak, "traffic": traffic.get(kernel)}
+             "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm_peak, "traffic": traffic.get(kernel),
+             "traffic_over_algorithmic": traffic[kernel] / nbytes if kernel in traffic and nbytes else None}
         if ops is not None:
             r["algorithmic_ops"] = ops
             r["achieved_top_s"] = ops / (ms * 1e-3) / 1e12
