@@ -298,6 +298,7 @@ __global__ void __launch_bounds__(1024) k_collapse(const Node* bnodes, int tri_o
                                                    int* qa, int* qb, uint32_t q_cap, WNode* wnodes, int* wsrc,
                                                    int wbase, uint32_t* wcount, int* status) {
   __shared__ uint32_t s_in, s_out, s_next;
+  const int leaf_max = objs ? kLeafMax : kStaticLeafMax;
   if (threadIdx.x == 0) {
     uint32_t cnt = 0, next = 0;
     if (objs) {
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(1024) k_collapse(const Node* bnodes, int tri_o
         int pick = -1;
         float best = -1.f;
         for (int i = 0; i < m; ++i) {
-          if (ref[i] < 0 || range_size(bnodes, ref[i]) <= kLeafMax) continue;
+          if (ref[i] < 0 || range_size(bnodes, ref[i]) <= leaf_max) continue;
           const float ex = box[i][3] - box[i][0], ey = box[i][4] - box[i][1], ez = box[i][5] - box[i][2];
           const float size = PV_DYN_OPEN_BY_COUNT && objs ? (float)range_size(bnodes, ref[i]) : ex * ey + ey * ez + ez * ex;
           if (size > best) {
@@ -373,7 +374,7 @@ __global__ void __launch_bounds__(1024) k_collapse(const Node* bnodes, int tri_o
         } else {
           const int4 dc = bnodes[c].d;
           const int size = dc.w - dc.z + 1;
-          if (size <= kLeafMax) {
+          if (size <= leaf_max) {
             wref[i] = leaf_ref((uint32_t)(tri_off + dc.z), (uint32_t)size);
           } else {
             const uint32_t slot = atomicAdd(&s_out, 1u);
@@ -810,7 +811,7 @@ int build_bvh(pv_scene* s, const float* h_verts, const std::vector<uint32_t>& st
         fail(cudaMemsetAsync(flags, 0, ns * sizeof(uint32_t), st));
         k_fit<<<blocks(ns, 256), 256, 0, st>>>(s->nodes, np, lp, flags, s->tris, d_lbox, (int)ns);
         s->s_root = 0;
-        if (ns <= (uint32_t)kLeafMax) {
+        if (ns <= (uint32_t)kStaticLeafMax) {
           s->s_wroot = leaf_ref(0, ns);
         } else {
           k_collapse<<<1, 1024, 0, st>>>(s->nodes, 0, 0, nullptr, 0, s->cq, s->cq + 2 * s->q_cap, s->q_cap, s->wnodes,
