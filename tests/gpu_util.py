@@ -93,7 +93,7 @@ def compare(gpu: oracle.Paths, orc: oracle.Paths, diag: float, skip=None, pos_to
     ``ambiguous_open`` flagged paths matching no listed record whose search
     met a hit distance the band leaves undetermined along a stretch of the
     ray (a ray within eps of a triangle's plane, where any point of the
-    stretch is an admissible hit): the tests bound both."""
+    stretch is an admissible hit): assert_parity bounds both."""
     n = int(len(gpu.ids))
     tracked = np.zeros(n, bool)
     if orc.branches:
@@ -229,9 +229,14 @@ def check_deposit(got: np.ndarray, q: oracle.Paths, width: int, height: int, rec
 
 
 def assert_parity(r: dict, allow_unchecked: bool = False) -> None:
+    """No mismatch of any kind; no flagged path left unchecked; open searches
+    (the one undetermined case, segments in a surface's plane) at most 2 paths
+    or 0.05 % of them (measured: 6 of 20 000 on the moving torus at tau = inf,
+    none elsewhere)."""
     bad = {k: v for k, v in r.items() if k.startswith("bad_") and v}
     assert not bad, r
     assert allow_unchecked or r.get("ambiguous_unchecked", 0) == 0, r
+    assert r.get("ambiguous_open", 0) <= max(2, 5e-4 * r["n"]), r
 
 
 def ambiguous_share(*stats) -> float:

@@ -309,8 +309,9 @@ def test_batch_against_oracle():
             o.verify(op, pv.PV_MODE_ERROR, 0.01)
             o.retrace(op, seed, f)
             r = gu.compare(gu.download(P), op, sc.diag)
+            print(sc.name, f, {k: r[k] for k in ("n", "ambiguous", "ambiguous_matched", "ambiguous_open")})
             gu.assert_parity(r)
-            assert r["ambiguous"] <= 0.02 * r["n"] + 2, r
+            assert r["ambiguous"] <= 3, r                # measured: 0 to 1 flagged path per frame
             gu.upload(P, op)                          # continue both sides from the oracle's records
     pv.pv_batch_destroy(b)
     for c in ctx:

@@ -228,8 +228,9 @@ def test_fused_frame_against_oracle():
             o.verify(op, pv.PV_MODE_ERROR, 0.01)
             o.retrace(op, seed, f)
             r = gu.compare(gu.download(P), op, sc.diag)
+            print(sc.name, f, {k: r[k] for k in ("n", "ambiguous", "ambiguous_matched", "ambiguous_open")})
             gu.assert_parity(r)
-            assert r["ambiguous"] <= 0.02 * r["n"] + 2, r
+            assert r["ambiguous"] <= 3, r                # measured: 0 to 1 flagged path per frame
             gu.upload(P, op)                          # continue both sides from the oracle's records
         assert pv.pv_read_device_status(h) == 0
         pv.pv_destroy_scene(h)

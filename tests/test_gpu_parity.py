@@ -56,7 +56,7 @@ def test_trace_all_parity_tiny_box():
     r = gu.compare(gu.download(P), op, sc.diag)
     print(r)
     gu.assert_parity(r)
-    assert r["ambiguous"] <= 0.01 * r["n"]
+    assert r["ambiguous"] <= 2                       # measured: none on the tiny box
     s = pv.stats_dict(st)
     assert abs(s["trace_rays"] - op.stats["trace_rays"]) <= 2 * r["ambiguous"]
     pv.pv_destroy_scene(h)
@@ -82,6 +82,9 @@ def _verify_case(sc, mode, tau, flags=0, seed=1, f_old=1, f_new=2, check_retrace
     ol = oracle.compact(q.info)
     amb = set(np.nonzero(q.amb)[0].tolist())
     assert np.all(np.diff(gl.astype(np.int64)) > 0)
+    # the list is exactly the device's marked paths (whose info words the comparison validated, flagged ones
+    # against the oracle's admitted outcomes), and equals the oracle's list wherever no decision was ambiguous
+    assert np.array_equal(gl, oracle.compact(gv.info))
     assert set(gl.tolist()) - amb == set(ol.tolist()) - amb
     print(mode, tau, flags, r, "listed", len(gl), "oracle", len(ol), ost)
     gu.assert_parity(r)
@@ -354,6 +357,7 @@ def _sampled_full_size_fused(sc, n_sample, check_frames=(2, 15, 30), tau=0.01):
         share = gu.ambiguous_share(*stats)
         print(sc.name, "frame", f, r, "ambiguous query share", share, pv.stats_dict(st))
         gu.assert_parity(r)
+        assert share <= 5e-3                         # measured: 1.7e-3 (city), 2.9e-3 (villa)
         ref = torch.zeros_like(atlas)
         pv.pv_deposit(h, P, ref, sc.atlas_rect, S)
         assert torch.equal(atlas, ref)
@@ -448,7 +452,7 @@ def test_multi_frame_chain_tiny_box_and_torus():
             r = gu.compare(gu.download(P), q, sc.diag)
             print(sc.name, f, r)
             gu.assert_parity(r)
-            assert r["ambiguous"] <= 0.02 * r["n"]
+            assert r["ambiguous"] <= 2                   # measured: none in this chain
         assert pv.pv_read_device_status(h) == 0
         pv.pv_destroy_scene(h)
 
