@@ -56,13 +56,13 @@ OPS_PER_NODE = 4 * OPS_PER_SLAB
 # only for the kernel sources they were captured on: the digest of csrc/ and include/ at capture time.  Any other
 # source digest reports no traffic.
 NCU_TRAFFIC = {
-    "digest": "1954ebdfb5fe3dc7",
-    "villa": {"k_refit_wide": 4268544, "k_verify_box": 367619328, "k_cont_trace<deposit>": 993705856,
-              "k_compact": 12016512, "k_trace (re-trace)": 201598720, "k_deposit": 644223744,
-              "k_trace (trace-all)": 843482880},
-    "city": {"k_refit_wide": 799232, "k_verify_box": 88083328, "k_cont_trace<deposit>": 218559744,
-             "k_compact": 4012288, "k_trace (re-trace)": 55488512, "k_deposit": 160777984,
-             "k_trace (trace-all)": 146506496},
+    "digest": "cdb08ae073b9b681",
+    "villa": {"k_refit_wide": 4263552, "k_verify_box": 367641088, "k_cont_trace<deposit>": 993746304,
+              "k_compact": 12016128, "k_trace (re-trace)": 201733632, "k_deposit": 644177408,
+              "k_trace (trace-all)": 843658752},
+    "city": {"k_refit_wide": 821504, "k_verify_box": 88077056, "k_cont_trace<deposit>": 218605312,
+             "k_compact": 4012288, "k_trace (re-trace)": 55464192, "k_deposit": 160478720,
+             "k_trace (trace-all)": 146567168},
 }
 TAUS = (0.0, 0.005, 0.01, 0.05)
 
