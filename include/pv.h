@@ -297,6 +297,16 @@ int pv_stage_times(pv_scene* s, float* ms, uint32_t* count);
 int pv_trace_all(pv_scene* s, const pv_paths* paths, uint64_t seed, uint32_t frame,
                  pv_frame_stats* d_stats, void* stream);
 
+/* pv_trace_all with the deposit of the stand-in for Fig. 2's splat/gather
+ * step in the same kernel: ``atlas`` (caller-owned device memory, layout as
+ * for pv_deposit) is cleared, then each photon is added as it is stored, from
+ * the values written to pa/pb.  Records, counters and atlas are bit-identical
+ * to pv_trace_all followed by pv_deposit (integer additions commute).  This
+ * is the trace-all frame that the reuse frame of pv_verify_retrace_deposit is
+ * measured against.  PV_ERR_ARG for a bad atlas (as pv_deposit). */
+int pv_trace_all_deposit(pv_scene* s, const pv_paths* paths, uint64_t seed, uint32_t frame,
+                         const pv_atlas* atlas, pv_frame_stats* d_stats, void* stream);
+
 /* Ascending ids of the paths whose replace bit is set (Sec. 5.2 pattern:
  * the marked paths packed so that as few blocks as possible process them);
  * single-pass decoupled look-back scan using the scene's workspace. */

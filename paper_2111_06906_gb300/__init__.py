@@ -32,6 +32,7 @@ PV_INFO_REPLACE, PV_INFO_REUSE_LIGHT = 1 << 30, 1 << 31
 
 EXPORTS = ["pv_build_scene", "pv_update_dynamic", "pv_verify_paths", "pv_retrace_invalid", "pv_verify_retrace",
            "pv_verify_retrace_deposit", "pv_verify_retrace_deposit_delta", "pv_stage_timing", "pv_stage_times", "pv_trace_all",
+           "pv_trace_all_deposit",
            "pv_compact_replace", "pv_compact_replace_static", "pv_deposit", "pv_set_traversal_limit",
            "pv_read_device_status", "pv_destroy_scene", "pv_status_string", "pv_theta_size", "pv_theta_current",
            "pv_model_deposit", "pv_adjoint_deposit", "pv_budget_list", "pv_batch_create", "pv_batch_frame",
@@ -127,6 +128,7 @@ def load():
         L.pv_stage_timing.argtypes = [P, C.c_uint32]
         L.pv_stage_times.argtypes = [P, P, P]
         L.pv_trace_all.argtypes = [P, C.POINTER(PvPaths), C.c_uint64, C.c_uint32, P, P]
+        L.pv_trace_all_deposit.argtypes = [P, C.POINTER(PvPaths), C.c_uint64, C.c_uint32, C.POINTER(PvAtlas), P, P]
         L.pv_compact_replace.argtypes = [P, C.POINTER(PvPaths), P, P, P]
         L.pv_compact_replace_static.argtypes = [P, C.c_uint32, P, P, P]
         L.pv_deposit.argtypes = [P, C.POINTER(PvPaths), C.POINTER(PvAtlas), P]
@@ -313,6 +315,15 @@ def pv_trace_all(scene, paths: Paths, seed: int, frame: int, d_stats=None, strea
     ps = paths.struct()
     _check("pv_trace_all", load().pv_trace_all(scene, C.byref(ps), int(seed), int(frame), _ptr(d_stats),
                                                 _stream(stream)))
+
+
+def pv_trace_all_deposit(scene, paths: Paths, seed: int, frame: int, atlas, rect, scale_log2: int, d_stats=None,
+                         stream=None) -> None:
+    """pv_trace_all + pv_deposit in one kernel (same records, counters and atlas)."""
+    ps = paths.struct()
+    a = _atlas(atlas, rect, scale_log2)
+    _check("pv_trace_all_deposit", load().pv_trace_all_deposit(scene, C.byref(ps), int(seed), int(frame), C.byref(a),
+                                                                _ptr(d_stats), _stream(stream)))
 
 
 def pv_compact_replace(scene, paths: Paths, d_list, d_count, stream=None) -> None:

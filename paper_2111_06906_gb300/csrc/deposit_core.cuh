@@ -56,6 +56,17 @@ __device__ __forceinline__ unsigned long long fixed_point(float E, int s) {
   return q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u);
 }
 
+// One photon (position x, energy e) into the atlas.
+__device__ __forceinline__ void deposit_point(const AtlasMap& am, float3 x, float3 e) {
+  const pv_atlas& at = am.at;
+  const int tx = atlas_texel(x.x, at.x0, am.sx, at.width);
+  const int tz = atlas_texel(x.z, at.z0, am.sz, at.height);
+  unsigned long long* t = reinterpret_cast<unsigned long long*>(at.data) + 3 * ((size_t)tz * at.width + tx);
+  atomicAdd(t, fixed_point(e.x, at.scale_log2));
+  atomicAdd(t + 1, fixed_point(e.y, at.scale_log2));
+  atomicAdd(t + 2, fixed_point(e.z, at.scale_log2));
+}
+
 // The first L photons of path p into the atlas, added (kSub false) or taken
 // back out (kSub true: the same fixed-point values, negated modulo 2^64, so
 // that a deposit followed by its removal leaves every texel's sum as it was).
@@ -95,7 +106,6 @@ __device__ __forceinline__ void deposit_warp(const AtlasMap& am, uint32_t n, uin
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t cnt = p != 0xFFFFFFFFu ? min(info_nseg(__ldcs(info + p)), B) : 0u;
   const uint32_t rows = __reduce_max_sync(0xffffffffu, cnt);
-  const pv_atlas& at = am.at;
   // kk: the first row not yet dealt out in full, cum: the photons of the rows before it, m: its paths' lanes
   uint32_t kk = 0, cum = 0;
   unsigned m = __ballot_sync(0xffffffffu, cnt > 0u);
@@ -122,12 +132,7 @@ __device__ __forceinline__ void deposit_warp(const AtlasMap& am, uint32_t n, uin
     // streaming loads: the path buffers must not evict the atlas from L2
     const float4 x = __ldcs(pa + (size_t)k_own * n + po);
     const float4 e = __ldcs(pb + (size_t)k_own * n + po);
-    const int tx = atlas_texel(x.x, at.x0, am.sx, at.width);
-    const int tz = atlas_texel(x.z, at.z0, am.sz, at.height);
-    unsigned long long* t = reinterpret_cast<unsigned long long*>(at.data) + 3 * ((size_t)tz * at.width + tx);
-    atomicAdd(t, fixed_point(e.x, at.scale_log2));
-    atomicAdd(t + 1, fixed_point(e.y, at.scale_log2));
-    atomicAdd(t + 2, fixed_point(e.z, at.scale_log2));
+    deposit_point(am, make_float3(x.x, x.y, x.z), make_float3(e.x, e.y, e.z));
   }
 }
 

@@ -100,8 +100,8 @@ struct pv_scene {
   int* status = nullptr;             // sticky device status
   cudaStream_t last_stream = nullptr;
 
-  int verify_blocks = 0, trace_blocks = 0, cont_blocks = 0, cont_trace_blocks = 0, cont_trace_dep_blocks = 0,
-      cont_trace_delta_blocks = 0;
+  int verify_blocks = 0, trace_blocks = 0, trace_dep_blocks = 0, cont_blocks = 0, cont_trace_blocks = 0,
+      cont_trace_dep_blocks = 0, cont_trace_delta_blocks = 0;
   // stage timing of pv_verify_retrace: a ring of stage_n calls, pvh::kStageEvents events each
   std::vector<cudaEvent_t> stage_ev;
   uint32_t stage_n = 0, stage_next = 0, stage_count = 0;
@@ -166,8 +166,10 @@ void launch_compact(pv_scene* s, const uint32_t* info, uint32_t n, uint32_t* lis
                     uint32_t* stats_listed, cudaStream_t st);
 
 // trace.cu
+// k_trace over ``list`` (nullptr: every path from its light); with an atlas,
+// every photon stored is also deposited into it (the atlas is not cleared here).
 void launch_trace(pv_scene* s, const pv_paths* p, const uint32_t* list, const uint32_t* count, uint64_t seed,
-                  uint32_t frame, pv_frame_stats* stats, cudaStream_t st);
+                  uint32_t frame, pv_frame_stats* stats, cudaStream_t st, const pv_atlas* atlas = nullptr);
 // Alg. 1 over the continuation list C fused with the re-trace of ``list``;
 // with an atlas, every path is also deposited (touched: verification's marks;
 // delta: the atlas holds the entry records' deposit, only listed paths change it)

@@ -111,7 +111,11 @@ __device__ __forceinline__ bool step_rays(const SceneView& sv, const Ray& r, Tra
   return done;
 }
 
-__global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS) k_trace(SceneView sv, FrameLights L, TraceArgs A) {
+// Re-trace (A.list) or trace-all; with kDep every photon stored is also
+// deposited into am's atlas as it is stored (the fused trace-all frame).
+template <bool kDep>
+__global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS)
+    k_trace(SceneView sv, FrameLights L, TraceArgs A, AtlasMap am) {
   __shared__ uint32_t s_red[32 * 2];
   __shared__ unsigned long long s_red64[32];
   const int root = *sv.root;
@@ -155,7 +159,7 @@ __global__ void __launch_bounds__(pvh::kTraceThreads, PV_TRACE_MIN_BLOCKS) k_tra
     const bool done = step_rays(sv, r, t, stk, s.excl, wk, !has_ray, cache, n_cache);
     if (!has_ray || !done) continue;
     ++c_rays;
-    if (trace_hit(sv, A, s, r, t, c_photons)) trav_begin(t, root);
+    if (trace_hit<kDep>(sv, A, s, r, t, c_photons, &am)) trav_begin(t, root);
     else has_ray = false;
   }
   uint32_t* const ctr[2] = {A.stats ? &A.stats->trace_rays : nullptr, A.stats ? &A.stats->photons_written : nullptr};
@@ -368,11 +372,23 @@ TraceArgs trace_args(pv_scene* s, const pv_paths* p, const uint32_t* list, const
 }  // namespace
 
 void launch_trace(pv_scene* s, const pv_paths* p, const uint32_t* list, const uint32_t* count, uint64_t seed,
-                  uint32_t frame, pv_frame_stats* stats, cudaStream_t st) {
-  if (!s->trace_blocks) s->trace_blocks = persistent_blocks(s, k_trace);
+                  uint32_t frame, pv_frame_stats* stats, cudaStream_t st, const pv_atlas* atlas) {
   const TraceArgs A = trace_args(s, p, list, count, seed, frame, stats);
   cudaMemsetAsync(A.ticket, 0, sizeof(uint32_t), st);
-  if (p->n) k_trace<<<s->trace_blocks, kTraceThreads, 0, st>>>(view(s), frame_lights(s), A);
+  if (!p->n) return;
+  AtlasMap am;
+  std::memset(&am, 0, sizeof am);
+  if (atlas) {
+    // the texel scales of atlas_map, in the same IEEE single-precision operations on the host
+    am.at = *atlas;
+    am.sx = (float)atlas->width / (atlas->x1 - atlas->x0);
+    am.sz = (float)atlas->height / (atlas->z1 - atlas->z0);
+    if (!s->trace_dep_blocks) s->trace_dep_blocks = persistent_blocks(s, k_trace<true>);
+    k_trace<true><<<s->trace_dep_blocks, kTraceThreads, 0, st>>>(view(s), frame_lights(s), A, am);
+  } else {
+    if (!s->trace_blocks) s->trace_blocks = persistent_blocks(s, k_trace<false>);
+    k_trace<false><<<s->trace_blocks, kTraceThreads, 0, st>>>(view(s), frame_lights(s), A, am);
+  }
 }
 
 // k_cont_trace as a programmatic dependent launch: it may start while the
@@ -438,5 +454,19 @@ extern "C" int pv_trace_all(pv_scene* s, const pv_paths* paths, uint64_t seed, u
   s->last_stream = st;
   pvh::launch_trace(s, paths, nullptr, nullptr, seed, frame, d_stats, st);
   if (s->has_dm) pvh::dm_reset(s, st);            // a full trace is stratified: DM_C = DM_T
+  return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
+}
+
+extern "C" int pv_trace_all_deposit(pv_scene* s, const pv_paths* paths, uint64_t seed, uint32_t frame,
+                                    const pv_atlas* atlas, pv_frame_stats* d_stats, void* stream) {
+  int rc = pvh::check_paths(s, paths);
+  if (rc != PV_OK) return rc;
+  if ((rc = pvh::check_atlas(atlas)) != PV_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  s->last_stream = st;
+  if (cudaMemsetAsync(atlas->data, 0, (size_t)atlas->width * atlas->height * 3 * sizeof(uint64_t), st) != cudaSuccess)
+    return PV_ERR_CUDA;
+  pvh::launch_trace(s, paths, nullptr, nullptr, seed, frame, d_stats, st, atlas);
+  if (s->has_dm) pvh::dm_reset(s, st);
   return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
 }

@@ -3,6 +3,7 @@
 // paper generates rays (Sec. 4), from the light (start 0) or by Russian
 // roulette and a cosine-weighted bounce at the first photon to re-trace.
 #pragma once
+#include "deposit_core.cuh"
 #include "dm_core.cuh"
 #include "pv_scene.h"
 
@@ -119,10 +120,11 @@ __device__ __forceinline__ bool init_path(const SceneView& sv, const FrameLights
 }
 
 // The ray of path s ended (hit t.best at t.tbest, or escaped): store its
-// photon and set up the next bounce.  False once the path is finished (its
-// info word written).
+// photon (with kDep, also deposit it into am's atlas) and set up the next
+// bounce.  False once the path is finished (its info word written).
+template <bool kDep = false>
 __device__ __forceinline__ bool trace_hit(const SceneView& sv, const TraceArgs& A, PathState& s, Ray& r, const Trav& t,
-                                          uint32_t& c_photons) {
+                                          uint32_t& c_photons, const AtlasMap* am = nullptr) {
   if (t.best < 0) {                          // escaped: the path ends
     finish(A, s);
     return false;
@@ -134,6 +136,7 @@ __device__ __forceinline__ bool trace_hit(const SceneView& sv, const TraceArgs& 
   const uint32_t n = A.n;
   A.pa[(size_t)s.k * n + s.pid] = make_float4(x.x, x.y, x.z, __int_as_float(prim));
   A.pb[(size_t)s.k * n + s.pid] = make_float4(s.E.x, s.E.y, s.E.z, rad);
+  if (kDep) deposit_point(*am, x, s.E);
   ++s.k;
   ++c_photons;
   if (s.k >= sv.B || !scatter(sv, A, s, r, x, prim, cross(f3(T.e1), f3(T.e2)), r.d, s.E, rad)) {

@@ -127,6 +127,7 @@ def test_host_argument_errors_need_no_gpu(lib):
     assert lib.pv_read_device_status(None) == -1
     assert lib.pv_set_traversal_limit(None, 1) == -1
     assert lib.pv_stage_timing(None, 1) == -1
+    assert lib.pv_trace_all_deposit(None, None, 1, 1, None, None, None) == -1
     fm = C.c_uint64(0)
     sink = C.c_void_p(16)
     assert lib.pv_fma_probe(0, 1, sink, C.byref(fm), None) == -1

@@ -314,3 +314,45 @@ def test_delta_deposit_bounce_caps(B):
         p.compare(pv.stats_dict(s1), pv.stats_dict(s2))
         assert torch.equal(a1, a2)
     p.close()
+
+
+@pytest.mark.parametrize("name", ["tiny_box", "box_torus", "point_light_moving", "city_small"])
+def test_trace_all_deposit_matches_separate_calls(name):
+    """pv_trace_all_deposit against pv_trace_all + pv_deposit: records, counters and atlas bit for bit, over
+    three frames of moving geometry and lights, into an atlas that holds stale values before each call."""
+    torch = _torch()
+    sc = SCENES[name]()
+    p = Pair(sc, 23)
+    a1, rect, scale = _atlas(sc)
+    a2 = torch.full_like(a1, 777)                  # cleared by the call
+    for f in range(2, 5):
+        s1, s2 = pv.new_stats(), pv.new_stats()
+        for h in (p.h1, p.h2):
+            gu.advance(h, sc, f)
+        pv.pv_trace_all(p.h1, p.P1, p.seed, f, s1)
+        pv.pv_deposit(p.h1, p.P1, a1, rect, scale)
+        pv.pv_trace_all_deposit(p.h2, p.P2, p.seed, f, a2, rect, scale, s2)
+        p.compare(pv.stats_dict(s1), pv.stats_dict(s2))
+        assert torch.equal(a1, a2), int((a1 != a2).sum())
+        assert int(a1.sum()) > 0
+        a2.fill_(777)
+    p.close()
+
+
+def test_trace_all_deposit_with_distribution_map():
+    """A stratified full trace with a map: the same records, counters and DM_C as pv_trace_all."""
+    torch = _torch()
+    sc = kit.rect_light_over_floor(2560, shift=lambda f: (0.11 * (f - 1), 0.0, 0.07 * (f - 1)), B=2, R=3.0)
+    p = Pair(sc, 31, dm_rect=(4, 4, 4, 4))
+    a1, rect, scale = _atlas(sc, 128)
+    a2 = torch.zeros_like(a1)
+    gu.advance(p.h1, sc, 2)
+    gu.advance(p.h2, sc, 2)
+    s1, s2 = pv.new_stats(), pv.new_stats()
+    pv.pv_trace_all(p.h1, p.P1, p.seed, 2, s1)
+    pv.pv_deposit(p.h1, p.P1, a1, rect, scale)
+    pv.pv_trace_all_deposit(p.h2, p.P2, p.seed, 2, a2, rect, scale, s2)
+    p.compare(pv.stats_dict(s1), pv.stats_dict(s2))
+    assert torch.equal(a1, a2)
+    assert np.array_equal(pv.pv_read_distribution_map(p.h1, 0), pv.pv_read_distribution_map(p.h2, 0))
+    p.close()
