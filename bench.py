@@ -57,13 +57,13 @@ OPS_PER_NODE = 4 * OPS_PER_SLAB
 # only for the kernel sources they were captured on: the digest of csrc/ and include/ at capture time.  Any other
 # source digest reports no traffic.
 NCU_TRAFFIC = {
-    "digest": "cdb08ae073b9b681",
-    "villa": {"k_refit_wide": 4263552, "k_verify_box": 367641088, "k_cont_trace<deposit>": 993746304,
-              "k_compact": 12016128, "k_trace (re-trace)": 201733632, "k_deposit": 644177408,
-              "k_trace (trace-all)": 843658752},
-    "city": {"k_refit_wide": 821504, "k_verify_box": 88077056, "k_cont_trace<deposit>": 218605312,
-             "k_compact": 4012288, "k_trace (re-trace)": 55464192, "k_deposit": 160478720,
-             "k_trace (trace-all)": 146567168},
+    "digest": "11003d2fc344e007",
+    "villa": {"k_refit_wide": 4262144, "k_verify_box": 367586688, "k_cont_trace<deposit>": 992716544,
+              "k_compact": 12016384, "k_trace (re-trace)": 205066880, "k_deposit": 644219136,
+              "k_trace<deposit> (trace-all)": 893325056},
+    "city": {"k_refit_wide": 822016, "k_verify_box": 88084352, "k_cont_trace<deposit>": 218784256,
+             "k_compact": 4012288, "k_trace (re-trace)": 57318144, "k_deposit": 160428800,
+             "k_trace<deposit> (trace-all)": 163592192},
 }
 TAUS = (0.0, 0.005, 0.01, 0.05)
 
