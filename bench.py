@@ -57,13 +57,13 @@ OPS_PER_NODE = 4 * OPS_PER_SLAB
 # only for the kernel sources they were captured on: the digest of csrc/ and include/ at capture time.  Any other
 # source digest reports no traffic.
 NCU_TRAFFIC = {
-    "digest": "11003d2fc344e007",
-    "villa": {"k_refit_wide": 4262144, "k_verify_box": 367586688, "k_cont_trace<deposit>": 992716544,
-              "k_compact": 12016384, "k_trace (re-trace)": 205066880, "k_deposit": 644219136,
-              "k_trace<deposit> (trace-all)": 893325056},
-    "city": {"k_refit_wide": 822016, "k_verify_box": 88084352, "k_cont_trace<deposit>": 218784256,
-             "k_compact": 4012288, "k_trace (re-trace)": 57318144, "k_deposit": 160428800,
-             "k_trace<deposit> (trace-all)": 163592192},
+    "digest": "5e8b2415489ee532",
+    "villa": {"k_refit_wide": 4264448, "k_verify_box": 367660288, "k_cont_trace<deposit>": 992732416,
+              "k_compact": 12016384, "k_trace (re-trace)": 204265344, "k_deposit": 644145664,
+              "k_trace<deposit> (trace-all)": 892198272},
+    "city": {"k_refit_wide": 821504, "k_verify_box": 88121984, "k_cont_trace<deposit>": 218731776,
+             "k_compact": 4012288, "k_trace (re-trace)": 57148672, "k_deposit": 160589056,
+             "k_trace<deposit> (trace-all)": 163150976},
 }
 TAUS = (0.0, 0.005, 0.01, 0.05)
 
