@@ -213,6 +213,7 @@ struct VerifySmem {
   int n_moved;
   uint32_t hitmask[256];       // flat mapping: intersected segments of each thread's path
   uint32_t slotmask[256];      // flat mapping: segments decided by a moved primitive at an end
+  uint16_t seg_owner[256 / 32][32 * PV_MAX_BOUNCES];   // flat mapping, per warp: segment q's lane | k << 5
 };
 
 // Result of the origin stage for one path.
@@ -774,25 +775,20 @@ __device__ __forceinline__ void verify_tile_flat(const SceneView& sv, const Fram
     if (lane >= o) incl += y;
   }
   const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  // each lane enters its segments in the warp's table: entry q = the owning lane and the segment number
+  uint16_t* const tab = sm.seg_owner[threadIdx.x >> 5];
+  for (uint32_t j = 0; j < cnt; ++j) tab[incl - cnt + j] = (uint16_t)(lane | ((j + 1) << 5));
   __syncwarp();
   for (uint32_t base = 0; base < total; base += 32) {
     const uint32_t q = base + lane;
-    uint32_t lo = 0, hi = 31;                  // owner: first lane whose inclusive count exceeds q
-#pragma unroll
-    for (int it = 0; it < 5; ++it) {
-      const uint32_t mid = (lo + hi) >> 1;
-      const uint32_t im = __shfl_sync(0xffffffffu, incl, mid);
-      if (q < im) hi = mid;
-      else lo = mid + 1;
-    }
-    const uint32_t owner = lo;
-    const uint32_t o_incl = __shfl_sync(0xffffffffu, incl, owner), o_cnt = __shfl_sync(0xffffffffu, cnt, owner);
+    const uint32_t e = q < total ? tab[q] : 0u;
+    const uint32_t owner = e & 31u;
     const uint32_t po = __shfl_sync(0xffffffffu, p, owner);
     const float ox = __shfl_sync(0xffffffffu, v.o.x, owner), oy = __shfl_sync(0xffffffffu, v.o.y, owner);
     const float oz = __shfl_sync(0xffffffffu, v.o.z, owner);
     const bool blocked1 = __shfl_sync(0xffffffffu, v.blocked1, owner);
     if (q >= total) continue;
-    const uint32_t k = q - (o_incl - o_cnt) + 1;    // segment k of path po, 1 .. nseg
+    const uint32_t k = e >> 5;                 // segment k of path po, 1 .. nseg
     const float4 vb = A.pa[(size_t)(k - 1) * n + po];
     const float4 va = k >= 2 ? A.pa[(size_t)(k - 2) * n + po] : make_float4(ox, oy, oz, __int_as_float(-1));
     const int prim_b = __float_as_int(vb.w), prim_a = __float_as_int(va.w);
