@@ -57,13 +57,13 @@ OPS_PER_NODE = 4 * OPS_PER_SLAB
 # only for the kernel sources they were captured on: the digest of csrc/ and include/ at capture time.  Any other
 # source digest reports no traffic.
 NCU_TRAFFIC = {
-    "digest": "5e8b2415489ee532",
-    "villa": {"k_refit_wide": 4264448, "k_verify_box": 367660288, "k_cont_trace<deposit>": 992732416,
-              "k_compact": 12016384, "k_trace (re-trace)": 204265344, "k_deposit": 644145664,
-              "k_trace<deposit> (trace-all)": 892198272},
-    "city": {"k_refit_wide": 821504, "k_verify_box": 88121984, "k_cont_trace<deposit>": 218731776,
-             "k_compact": 4012288, "k_trace (re-trace)": 57148672, "k_deposit": 160589056,
-             "k_trace<deposit> (trace-all)": 163150976},
+    "digest": "5958b3c6bf0c1379",
+    "villa": {"k_refit_wide": 4263680, "k_verify_box": 367828096, "k_cont_trace<deposit>": 993080576,
+              "k_compact": 12016256, "k_trace (re-trace)": 204381696, "k_deposit": 644299008,
+              "k_trace<deposit> (trace-all)": 891266816},
+    "city": {"k_refit_wide": 821504, "k_verify_box": 88250752, "k_cont_trace<deposit>": 218612096,
+             "k_compact": 4012288, "k_trace (re-trace)": 57130496, "k_deposit": 160490240,
+             "k_trace<deposit> (trace-all)": 163207296},
 }
 TAUS = (0.0, 0.005, 0.01, 0.05)
 
