@@ -57,13 +57,13 @@ OPS_PER_NODE = 4 * OPS_PER_SLAB
 # only for the kernel sources they were captured on: the digest of csrc/ and include/ at capture time.  Any other
 # source digest reports no traffic.
 NCU_TRAFFIC = {
-    "digest": "5958b3c6bf0c1379",
-    "villa": {"k_refit_wide": 4263680, "k_verify_box": 367828096, "k_cont_trace<deposit>": 993080576,
-              "k_compact": 12016256, "k_trace (re-trace)": 204381696, "k_deposit": 644299008,
-              "k_trace<deposit> (trace-all)": 891266816},
-    "city": {"k_refit_wide": 821504, "k_verify_box": 88250752, "k_cont_trace<deposit>": 218612096,
-             "k_compact": 4012288, "k_trace (re-trace)": 57130496, "k_deposit": 160490240,
-             "k_trace<deposit> (trace-all)": 163207296},
+    "digest": "42f04be4894994e6",
+    "villa": {"k_refit_wide": 4962560, "k_verify_box": 367853184, "k_cont_trace<deposit>": 993006592,
+              "k_compact": 12016512, "k_trace (re-trace)": 204186112, "k_deposit": 644328704,
+              "k_trace<deposit> (trace-all)": 892434432},
+    "city": {"k_refit_wide": 819712, "k_verify_box": 88169344, "k_cont_trace<deposit>": 218521472,
+             "k_compact": 4012544, "k_trace (re-trace)": 57166336, "k_deposit": 160530944,
+             "k_trace<deposit> (trace-all)": 163926784},
 }
 TAUS = (0.0, 0.005, 0.01, 0.05)
 

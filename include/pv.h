@@ -62,7 +62,10 @@ enum {
 };
 enum {
   PV_BUILD_DYN_REBUILD = 1u,   /* rebuild dynamic BVHs every frame instead of refitting */
-  PV_BUILD_STATIC_LBVH = 2u    /* static tree from Morton codes (default: binned surface-area heuristic) */
+  PV_BUILD_STATIC_LBVH = 2u,   /* static tree from Morton codes (default: binned surface-area heuristic) */
+  PV_BUILD_REFIT_CLIMB = 4u    /* refit the dynamic wide nodes level by level, the last child to arrive
+                                  going on up (default: each node from the contiguous run of triangles
+                                  under it, no dependent levels); both give the same boxes */
 };
 
 #define PV_MAX_LIGHTS 4

@@ -27,6 +27,7 @@ PV_MODE_NAIVE_AABB, PV_MODE_NAIVE_EXACT, PV_MODE_ERROR = 0, 1, 2
 PV_FLAG_TEST_OLD_TRIS, PV_FLAG_ERROR_EXACT = 1, 2
 PV_BUILD_DYN_REBUILD = 1
 PV_BUILD_STATIC_LBVH = 2
+PV_BUILD_REFIT_CLIMB = 4
 PV_INFO_NSEG_SHIFT, PV_INFO_START_SHIFT = 22, 26
 PV_INFO_REPLACE, PV_INFO_REUSE_LIGHT = 1 << 30, 1 << 31
 

@@ -439,8 +439,8 @@ __global__ void k_wide_links(const WNode* wdyn, const uint32_t* n_wide, int w_of
   w_nch[w] = (uint8_t)m;
 }
 
-// Refit frames in one launch: the direct refit (refit_tri), then the last
-// block to finish runs the frame's pose bookkeeping, the top level and the
+// Refit frames in one launch: the direct refit, then the last block to
+// finish runs the frame's pose bookkeeping, the top level and the
 // moved-object groups (what k_frame_top does alone when nothing moved).
 struct TopArgs {
   uint32_t* done;              // blocks finished (reset by the last)
@@ -454,12 +454,9 @@ struct TopArgs {
   MovedGroups* groups;
 };
 
-__global__ void __launch_bounds__(256) k_refit_wide(XformParams P, RefitArgs R, TopArgs T) {
+// The end of a refit launch, called by every thread of every block.
+__device__ __forceinline__ void refit_finish(const XformParams& P, const RefitArgs& R, const TopArgs& T) {
   __shared__ bool s_last;
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t s = i < R.n ? R.tri_slot[i] : 0u;
-  const bool mv = i < R.n && ((P.moved >> s) & 1ull);
-  refit_tri(P.xf[mv ? s : 0], mv, s, R, i);
   __threadfence();                             // this block's triangles, boxes and object-box atomics
   __syncthreads();
   if (threadIdx.x == 0) s_last = atomicAdd(T.done, 1u) == gridDim.x - 1;
@@ -470,6 +467,40 @@ __global__ void __launch_bounds__(256) k_refit_wide(XformParams P, RefitArgs R, 
   pose_bookkeeping(P.xf, P.moved, P.n_dyn, T.objs, T.xf_old, T.xf_new, R.obox);
   build_top_and_groups(T.wnodes, T.tris, T.top_off, T.static_root, T.objs, (int)P.n_dyn, T.root_out, P.moved,
                        T.groups);
+}
+
+// Resident blocks per SM asked of k_refit_wide (the block count it launches
+// grows with the pairs).  6, and 8 (32 registers, 132 bytes of spills),
+// measured the same as 5 within 1 us on the city and the villa.
+#ifndef PV_REFIT_MIN_BLOCKS
+#define PV_REFIT_MIN_BLOCKS 5
+#endif
+
+// Blocks [0, blocks_tri): one thread per dynamic triangle (refit_leaf); the
+// blocks after them: one thread per pair of the pair table (refit_pair, the
+// slots of the wide nodes above the triangles).
+__global__ void __launch_bounds__(256, PV_REFIT_MIN_BLOCKS) k_refit_wide(XformParams P, RefitArgs R, PairArgs Q,
+                                                                          TopArgs T, uint32_t blocks_tri) {
+  if (blockIdx.x < blocks_tri) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t s = i < R.n ? R.tri_slot[i] : 0u;
+    const bool mv = i < R.n && ((P.moved >> s) & 1ull);
+    float3 blo, bhi;
+    refit_leaf(P.xf[mv ? s : 0], mv, s, R, i, blo, bhi);
+  } else {
+    refit_pair(P, R, Q, (blockIdx.x - blocks_tri) * blockDim.x + threadIdx.x);
+  }
+  refit_finish(P, R, T);
+}
+
+// The same with the climb of refit_tri, one thread per dynamic triangle (for
+// a scene built with PV_BUILD_REFIT_CLIMB, or without a pair table).
+__global__ void __launch_bounds__(256) k_refit_climb(XformParams P, RefitArgs R, TopArgs T) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t s = i < R.n ? R.tri_slot[i] : 0u;
+  const bool mv = i < R.n && ((P.moved >> s) & 1ull);
+  refit_tri(P.xf[mv ? s : 0], mv, s, R, i);
+  refit_finish(P, R, T);
 }
 
 // Pose bookkeeping of every slot, then (when objects moved) the top level
@@ -927,6 +958,80 @@ int build_bvh(pv_scene* s, const float* h_verts, const std::vector<uint32_t>& st
   return rc;
 }
 
+// After the first collapse: the pair table of k_refit_wide, from the parent
+// links.  Every non-root dynamic wide node contributes one pair per triangle
+// of its run, nodes in index order.  The runs are contiguous by construction
+// (the triangles are stored in leaf order and each wide node covers one
+// binary subtree); if one is not, no table is built and the refit climbs.
+// Synchronous.
+int build_refit_pairs(pv_scene* s, cudaStream_t st) {
+  const uint32_t n = s->n_dyn_tris;
+  s->pairs_ok = false;
+  if (n == 0 || (s->flags & (PV_BUILD_DYN_REBUILD | PV_BUILD_REFIT_CLIMB)) || kLeafMax != 1) return PV_OK;
+  int rc = PV_OK;
+  auto fail = [&](cudaError_t e) {
+    if (e != cudaSuccess && rc == PV_OK) rc = e == cudaErrorMemoryAllocation ? PV_ERR_OOM : PV_ERR_CUDA;
+  };
+  uint32_t nw = 0;
+  fail(cudaStreamSynchronize(st));
+  fail(cudaMemcpy(&nw, s->wcount + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if (rc != PV_OK) return rc;
+  if (nw > n) return PV_OK;
+  std::vector<uint32_t> tl(n), wl(std::max<uint32_t>(nw, 1u));
+  fail(cudaMemcpy(tl.data(), s->t_link, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if (nw) fail(cudaMemcpy(wl.data(), s->w_link, nw * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if (rc != PV_OK) return rc;
+  // each non-root wide node's run, by its parent slot
+  const size_t nl = 4 * (size_t)std::max<uint32_t>(nw, 1u);
+  std::vector<uint32_t> lo(nl, 0xFFFFFFFFu), hi(nl, 0u), cnt(nl, 0u);
+  for (uint32_t i = 0; i < n; ++i) {
+    uint32_t link = tl[i];
+    for (int guard = 0; guard < 64 && link != 0xFFFFFFFFu; ++guard) {
+      const uint32_t w = link >> 2;
+      if (w >= nw) return PV_OK;
+      const uint32_t up = wl[w];
+      if (up == 0xFFFFFFFFu) break;            // w is an object's root
+      if (up >= nl) return PV_OK;
+      lo[up] = std::min(lo[up], i);
+      hi[up] = std::max(hi[up], i);
+      ++cnt[up];
+      link = up;
+    }
+  }
+  std::vector<uint32_t> plink, ptri, warps(nl, 0u);
+  for (uint32_t w = 0; w < nw; ++w) {
+    const uint32_t up = wl[w];
+    if (up == 0xFFFFFFFFu || up >= nl) continue;
+    if (cnt[up] == 0 || hi[up] - lo[up] + 1u != cnt[up]) return PV_OK;
+    const size_t first = plink.size(), last = first + cnt[up] - 1;
+    warps[up] = (uint32_t)((last >> 5) - (first >> 5) + 1);
+    for (uint32_t i = lo[up]; i <= hi[up]; ++i) {
+      plink.push_back(up | (warps[up] == 1u ? kPairOne : 0u));
+      ptri.push_back(i);
+    }
+  }
+  const size_t np = plink.size();
+  std::vector<int> acc(6 * nl);
+  for (size_t k = 0; k < acc.size(); ++k) acc[k] = k % 6 < 3 ? INT_MAX : INT_MIN;
+  fail(cudaMalloc(&s->pair_link, std::max<size_t>(np, 1) * sizeof(uint32_t)));
+  fail(cudaMalloc(&s->pair_tri, std::max<size_t>(np, 1) * sizeof(uint32_t)));
+  fail(cudaMalloc(&s->pair_warps, nl * sizeof(uint32_t)));
+  fail(cudaMalloc(&s->pair_acc, acc.size() * sizeof(int)));
+  fail(cudaMalloc(&s->pair_count, nl * sizeof(uint32_t)));
+  if (rc != PV_OK) return rc;
+  if (np) {
+    fail(cudaMemcpy(s->pair_link, plink.data(), np * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    fail(cudaMemcpy(s->pair_tri, ptri.data(), np * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  }
+  fail(cudaMemcpy(s->pair_warps, warps.data(), nl * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  fail(cudaMemcpy(s->pair_acc, acc.data(), acc.size() * sizeof(int), cudaMemcpyHostToDevice));
+  fail(cudaMemcpy(s->pair_count, warps.data(), nl * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  if (rc != PV_OK) return rc;
+  s->n_pairs = (uint32_t)np;
+  s->pairs_ok = true;
+  return PV_OK;
+}
+
 // Per frame: previous pose kept, moved objects transformed; the dynamic tree
 // is refitted, or rebuilt from world-space Morton codes
 // (PV_BUILD_DYN_REBUILD); then the top level is rebuilt.
@@ -967,7 +1072,19 @@ void launch_update_dynamic(pv_scene* s, cudaStream_t st) {
         T.static_root = s->s_wroot;
         T.root_out = s->root;
         T.groups = s->groups;
-        k_refit_wide<<<blocks(n, 256), 256, 0, st>>>(P, R, T);
+        if (s->pairs_ok) {
+          PairArgs Q;
+          Q.link = s->pair_link;
+          Q.tri = s->pair_tri;
+          Q.warps = s->pair_warps;
+          Q.acc = s->pair_acc;
+          Q.count = s->pair_count;
+          Q.n_pairs = s->n_pairs;
+          const uint32_t bt = blocks(n, 256);
+          k_refit_wide<<<bt + blocks(s->n_pairs, 256), 256, 0, st>>>(P, R, Q, T, bt);
+        } else {
+          k_refit_climb<<<blocks(n, 256), 256, 0, st>>>(P, R, T);
+        }
         return;
       }
       k_frame_top<<<1, 32, 0, st>>>(P, s->objs, s->xf_old, s->xf_new, s->obox, s->wnodes, s->tris, (int)s->w_top_off,

@@ -47,6 +47,14 @@ struct pv_scene {
   uint32_t* w_arrive = nullptr;      // [n_dyn_tris] children refitted this frame (reset by the last), then the
                                      // refit's finished-block count
   uint32_t* t_link = nullptr;        // [n_dyn_tris] dynamic triangle -> parent wide node (local << 2 | slot)
+  // pair table of the refit without dependent levels (k_refit_wide, refit_pair)
+  uint32_t* pair_link = nullptr;     // [n_pairs] parent slot of the pair's wide node (| kPairOne)
+  uint32_t* pair_tri = nullptr;      // [n_pairs] local dynamic triangle under the node
+  uint32_t* pair_warps = nullptr;    // [4 x dynamic wide nodes] warps over each node's pairs, by parent slot
+  int* pair_acc = nullptr;           // [4 x dynamic wide nodes][6] box of a node over several warps
+  uint32_t* pair_count = nullptr;    // [4 x dynamic wide nodes] warps still to arrive
+  uint32_t n_pairs = 0;
+  bool pairs_ok = false;             // the table is built (else the refit climbs)
   int* obox = nullptr;               // [kMaxDyn][6] exact new boxes of the frame, order-preserving integers
   uint8_t* d_tri_slot = nullptr;     // [n_dyn_tris] slot per dynamic triangle
   pvk::DynObj* objs = nullptr;       // [n_dyn]
@@ -160,6 +168,7 @@ void radix_sort(uint64_t*& k0, uint32_t*& v0, uint64_t*& k1, uint32_t*& v1, uint
 uint32_t radix_tiles(uint32_t n);
 int build_bvh(pv_scene* s, const float* h_verts, const std::vector<uint32_t>& static_prims, cudaStream_t st);
 void launch_update_dynamic(pv_scene* s, cudaStream_t st);
+int build_refit_pairs(pv_scene* s, cudaStream_t st);
 
 // compact.cu
 void launch_compact(pv_scene* s, const uint32_t* info, uint32_t n, uint32_t* list, uint32_t* count,

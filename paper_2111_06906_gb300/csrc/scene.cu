@@ -50,7 +50,7 @@ void free_scene(pv_scene* s) {
   for (cudaEvent_t e : s->stage_ev)
     if (e) cudaEventDestroy(e);
   void* ptrs[] = {s->nodes, s->wnodes, s->wsrc, s->wcount, s->cq, s->tris, s->root, s->d_local, s->d_tri_prim, s->d_leaf_parent, s->d_node_parent,
-                  s->d_fit_flags, s->w_link, s->w_nch, s->w_arrive, s->t_link, s->obox, s->d_tri_slot, s->objs, s->groups, s->r_keys[0], s->r_keys[1], s->r_vals[0], s->r_vals[1],
+                  s->d_fit_flags, s->w_link, s->w_nch, s->w_arrive, s->t_link, s->pair_link, s->pair_tri, s->pair_warps, s->pair_acc, s->pair_count, s->obox, s->d_tri_slot, s->objs, s->groups, s->r_keys[0], s->r_keys[1], s->r_vals[0], s->r_vals[1],
                   s->r_hist, s->r_tris, s->r_local, s->r_prim, s->prim_slot, s->prim_dyn, s->prim_alb, s->prim_nrm,
                   s->xf_old, s->xf_new, s->ws_mask, s->ws_cont, s->ws_list, s->ws_touched, s->ws_tiles, s->ws_ctr, s->status, s->b_keys[0], s->b_keys[1],
                   s->b_vals[0], s->b_vals[1], s->b_hist, s->dm_c[0], s->dm_c[1], s->dm_c[2], s->dm_c[3],
@@ -274,6 +274,7 @@ extern "C" int pv_build_scene(const pv_scene_desc* d, void* stream, pv_scene** o
     fail(cudaGetLastError());
   }
   if (rc == PV_OK) fail(cudaStreamSynchronize(st));
+  if (rc == PV_OK) rc = pvh::build_refit_pairs(s, st);
   s->dyn_tris_of.clear();
   s->dyn_tris_of.shrink_to_fit();
   if (rc != PV_OK) {

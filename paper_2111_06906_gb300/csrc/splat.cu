@@ -56,16 +56,6 @@ __global__ void __launch_bounds__(256) k_gbuffer(SceneView sv, Cam c, GPixel* g)
   g[px] = o;
 }
 
-// Continuous pixel coordinates of q (pixel centres at integers); false behind the near plane.
-__device__ __forceinline__ bool project(const Cam& c, float3 q, float& pi, float& pj) {
-  const float3 v = q - c.pos;
-  const float z = dot(v, c.f);
-  if (!(z > c.znear)) return false;
-  pi = (dot(v, c.r) / (z * c.tx) + 1.0f) * 0.5f * (float)c.W - 0.5f;
-  pj = (1.0f - dot(v, c.u) / (z * c.ty)) * 0.5f * (float)c.H - 0.5f;
-  return true;
-}
-
 // A photon takes part when every corner of its kernel cube lies beyond the
 // near plane (its screen footprint is then bounded).
 __device__ __forceinline__ bool in_front(const Cam& c, float3 x, float radius) {

@@ -104,14 +104,16 @@ __device__ __forceinline__ Tri xform_tri(const float* m, const float* v, uint32_
   return T;
 }
 
-// Direct refit of the dynamic objects' wide nodes, one thread per dynamic
+// Direct refit of the dynamic objects' wide nodes.  One thread per dynamic
 // triangle: a moved object's triangle goes to the new pose, its exact box
 // joins the object's box (integer atomics), and its padded box is written
-// into its slot of the parent wide node; the last child to arrive at a node
-// takes the union of the node's children up to the parent, and so on to the
-// object's root.  The boxes are the same minima and maxima of the same
-// padded leaf boxes that the binary refit gathers, so the wide nodes come out
-// identical, in a third of the dependent levels.
+// into its slot of the parent wide node (refit_leaf).  The nodes above come
+// either from a climb, where the last child to arrive at a node takes the
+// union of the node's children up to the parent, and so on to the object's
+// root (refit_tri), or from the node's run of triangles, with no dependent
+// levels (refit_pair).  Either way the boxes are the same minima and maxima
+// of the same padded leaf boxes that the binary refit gathers, so the wide
+// nodes come out identical.
 struct RefitArgs {
   const float* local;
   const uint32_t* prim;
@@ -137,9 +139,14 @@ __device__ __forceinline__ uint32_t arrive(uint32_t* count) {
   return old;
 }
 
-__device__ __forceinline__ void refit_tri(const float* xf_slot, bool moved_lane, uint32_t s, const RefitArgs& R,
-                                          uint32_t i) {
+// The first half of a dynamic triangle's refit, called by every thread of
+// the block: a moved triangle goes to the new pose (stored), its exact box
+// joins the object's box, and its padded box (blo, bhi) is written into its
+// slot of the parent wide node.
+__device__ __forceinline__ void refit_leaf(const float* xf_slot, bool moved_lane, uint32_t s, const RefitArgs& R,
+                                           uint32_t i, float3& blo, float3& bhi) {
   const int lane = threadIdx.x & 31;
+  const uint32_t link = moved_lane ? R.t_link[i] : 0xFFFFFFFFu;
   float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
   Tri T;
   if (moved_lane) {
@@ -175,24 +182,36 @@ __device__ __forceinline__ void refit_tri(const float* xf_slot, bool moved_lane,
     }
   }
   if (!moved_lane) return;
-  float3 blo, bhi;
   tri_box(T, blo, bhi);
   pad_box(blo, bhi);
+  if (link == 0xFFFFFFFFu) return;             // a one-triangle object: the triangle is the root
+  WNode* nd = R.wdyn + (link >> 2);
+  const uint32_t c = link & 3u;
+  (&nd->lox.x)[c] = blo.x;
+  (&nd->hix.x)[c] = bhi.x;
+  (&nd->loy.x)[c] = blo.y;
+  (&nd->hiy.x)[c] = bhi.y;
+  (&nd->loz.x)[c] = blo.z;
+  (&nd->hiz.x)[c] = bhi.z;
+}
+
+// The refit by climbing: after refit_leaf, the last child to arrive at a wide
+// node takes the union of the node's children up to the parent, and so on to
+// the object's root.
+__device__ __forceinline__ void refit_tri(const float* xf_slot, bool moved_lane, uint32_t s, const RefitArgs& R,
+                                          uint32_t i) {
+  float3 blo, bhi;
+  refit_leaf(xf_slot, moved_lane, s, R, i, blo, bhi);
+  if (!moved_lane) return;
   uint32_t link = R.t_link[i];
   for (int guard = 0; guard < 64 && link != 0xFFFFFFFFu; ++guard) {
-    const uint32_t w = link >> 2, c = link & 3u;
-    WNode* nd = R.wdyn + w;
-    (&nd->lox.x)[c] = blo.x;
-    (&nd->hix.x)[c] = bhi.x;
-    (&nd->loy.x)[c] = blo.y;
-    (&nd->hiy.x)[c] = bhi.y;
-    (&nd->loz.x)[c] = blo.z;
-    (&nd->hiz.x)[c] = bhi.z;
+    const uint32_t w = link >> 2;
     const uint32_t m = R.w_nch[w];
     if (arrive(R.w_arrive + w) + 1u < m) return;
     R.w_arrive[w] = 0u;                        // every child of this frame has arrived
     blo = make_float3(3.0e38f, 3.0e38f, 3.0e38f);
     bhi = make_float3(-3.0e38f, -3.0e38f, -3.0e38f);
+    WNode* nd = R.wdyn + w;
     for (uint32_t q = 0; q < m; ++q) {
       blo.x = fminf(blo.x, __ldcg(&nd->lox.x + q));
       blo.y = fminf(blo.y, __ldcg(&nd->loy.x + q));
@@ -202,7 +221,105 @@ __device__ __forceinline__ void refit_tri(const float* xf_slot, bool moved_lane,
       bhi.z = fmaxf(bhi.z, __ldcg(&nd->hiz.x + q));
     }
     link = R.w_link[w];
+    if (link == 0xFFFFFFFFu) return;
+    WNode* up = R.wdyn + (link >> 2);
+    const uint32_t c = link & 3u;
+    (&up->lox.x)[c] = blo.x;
+    (&up->hix.x)[c] = bhi.x;
+    (&up->loy.x)[c] = blo.y;
+    (&up->hiy.x)[c] = bhi.y;
+    (&up->loz.x)[c] = blo.z;
+    (&up->hiz.x)[c] = bhi.z;
   }
+}
+
+// The refit without a climb.  The dynamic triangles are stored in the leaf
+// order of their tree, so the triangles under a wide node are a contiguous
+// run, and the box that the node's parent slot holds (the union of the padded
+// triangle boxes below it, which the climb builds level by level) is a
+// minimum and a maximum over that run.  The pairs (node, triangle of its run)
+// of every non-root dynamic wide node are listed node after node and cut into
+// warps of 32, one thread per pair: the thread transforms its triangle as
+// refit_leaf does, the lanes of one node reduce their boxes, and the node's
+// box is written into its parent slot.  A node whose pairs span several warps
+// is combined through integer atomics, and the last warp to arrive writes the
+// slot.  No warp waits on another level, and the minima and maxima are exact,
+// so the slots come out as the climb makes them.
+constexpr uint32_t kPairOne = 0x80000000u;    // flag of a node whose pairs lie inside one warp
+
+struct PairArgs {
+  const uint32_t* link;      // [n_pairs] parent slot (wide node << 2 | slot) of the pair's node, with kPairOne
+  const uint32_t* tri;       // [n_pairs] local dynamic triangle under the node
+  const uint32_t* warps;     // [by parent slot] warps that hold the node's pairs
+  int* acc;                  // [by parent slot][6] box over several warps (order-preserving integers; empty
+                             // between frames)
+  uint32_t* count;           // [by parent slot] warps still to arrive this frame (warps between frames)
+  uint32_t n_pairs;
+};
+
+// The wide-node box (order-preserving integers r) into parent slot ``link``.
+__device__ __forceinline__ void write_slot(const RefitArgs& R, uint32_t link, const int (&r)[6]) {
+  WNode* nd = R.wdyn + (link >> 2);
+  const uint32_t c = link & 3u;
+  (&nd->lox.x)[c] = of_ord(r[0]);
+  (&nd->loy.x)[c] = of_ord(r[1]);
+  (&nd->loz.x)[c] = of_ord(r[2]);
+  (&nd->hix.x)[c] = of_ord(r[3]);
+  (&nd->hiy.x)[c] = of_ord(r[4]);
+  (&nd->hiz.x)[c] = of_ord(r[5]);
+}
+
+// Pair q (every lane of the warp calls it).
+__device__ __forceinline__ void refit_pair(const XformParams& P, const RefitArgs& R, const PairArgs& Q, uint32_t q) {
+  const int lane = threadIdx.x & 31;
+  const bool in = q < Q.n_pairs;
+  const uint32_t e = in ? __ldg(Q.link + q) : 0u;
+  const uint32_t i = in ? __ldg(Q.tri + q) : 0u;
+  const uint32_t s = in ? R.tri_slot[i] : 0u;
+  const bool mv = in && ((P.moved >> s) & 1ull);
+  int b[6] = {0, 0, 0, 0, 0, 0};
+  if (mv) {
+    float lo[3] = {0.f, 0.f, 0.f}, hi[3] = {0.f, 0.f, 0.f};
+    const Tri T = xform_tri(P.xf[s], R.local + 9 * (size_t)i, 0u, lo, hi);
+    float3 blo, bhi;
+    tri_box(T, blo, bhi);
+    pad_box(blo, bhi);
+    b[0] = ord_of(blo.x);
+    b[1] = ord_of(blo.y);
+    b[2] = ord_of(blo.z);
+    b[3] = ord_of(bhi.x);
+    b[4] = ord_of(bhi.y);
+    b[5] = ord_of(bhi.z);
+  }
+  const uint32_t link = e & ~kPairOne;
+  // a node's pairs are consecutive, so the lanes of one node are one group
+  const unsigned grp = __match_any_sync(0xffffffffu, mv ? (int)link : -1);
+  if (!mv) return;
+  int r[6];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    r[j] = __reduce_min_sync(grp, b[j]);
+    r[3 + j] = __reduce_max_sync(grp, b[3 + j]);
+  }
+  if (lane != __ffs(grp) - 1) return;
+  if (!(e & kPairOne)) {
+    int* a = Q.acc + 6 * (size_t)link;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      atomicMin(a + j, r[j]);
+      atomicMax(a + 3 + j, r[3 + j]);
+    }
+    uint32_t left;                             // release: the box atomics above; acquire: the other warps'
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], -1;" : "=r"(left) : "l"(Q.count + link) : "memory");
+    if (left != 1u) return;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      r[j] = __ldcg(a + j);
+      a[j] = j < 3 ? INT_MAX : INT_MIN;
+    }
+    Q.count[link] = __ldg(Q.warps + link);
+  }
+  write_slot(R, link, r);
 }
 
 // Per-frame pose bookkeeping of every dynamic slot (what update_object does
