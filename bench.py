@@ -57,13 +57,13 @@ OPS_PER_NODE = 4 * OPS_PER_SLAB
 # only for the kernel sources they were captured on: the digest of csrc/ and include/ at capture time.  Any other
 # source digest reports no traffic.
 NCU_TRAFFIC = {
-    "digest": "42f04be4894994e6",
-    "villa": {"k_refit_wide": 4962560, "k_verify_box": 367853184, "k_cont_trace<deposit>": 993006592,
-              "k_compact": 12016512, "k_trace (re-trace)": 204186112, "k_deposit": 644328704,
-              "k_trace<deposit> (trace-all)": 892434432},
-    "city": {"k_refit_wide": 819712, "k_verify_box": 88169344, "k_cont_trace<deposit>": 218521472,
-             "k_compact": 4012544, "k_trace (re-trace)": 57166336, "k_deposit": 160530944,
-             "k_trace<deposit> (trace-all)": 163926784},
+    "digest": "eea445baffede396",
+    "villa": {"k_refit_wide": 4974592, "k_verify_box": 367724288, "k_cont_trace<deposit>": 991691136,
+              "k_compact": 12016384, "k_trace (re-trace)": 204486016, "k_deposit": 644327424,
+              "k_trace<deposit> (trace-all)": 892445952},
+    "city": {"k_refit_wide": 825088, "k_verify_box": 88076672, "k_cont_trace<deposit>": 218518272,
+             "k_compact": 4012288, "k_trace (re-trace)": 57209856, "k_deposit": 160499712,
+             "k_trace<deposit> (trace-all)": 164392320},
 }
 TAUS = (0.0, 0.005, 0.01, 0.05)
 

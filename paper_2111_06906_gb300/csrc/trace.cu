@@ -211,9 +211,10 @@ __device__ __forceinline__ void cont_flush(ContCounters& cc, uint32_t* s_cnt) {
 
 // kDep: 0 no deposit, 1 deposit into a cleared atlas, 2 carried atlas (delta).
 //
-// Launched as a programmatic dependent of k_verify: its blocks may be placed
-// on the SMs while k_verify's last blocks run, and wait here until k_verify
-// has finished and its writes are visible (a no-op for an ordinary launch).
+// Launched as a programmatic dependent of k_verify (PV_CONT_TRACE_PDL), its
+// blocks may be placed on the SMs while k_verify's last blocks run, and wait
+// below until k_verify has finished and its writes are visible; for the
+// default ordinary launch the wait returns at once.
 template <int kDep>
 __global__ void __launch_bounds__(pvh::kTraceThreads, PV_CONT_TRACE_MIN_BLOCKS)
     k_cont_trace(SceneView sv, FrameLights L, TraceArgs A, ContArgs C, DepositArgs D) {
@@ -396,8 +397,15 @@ void launch_trace(pv_scene* s, const pv_paths* p, const uint32_t* list, const ui
   }
 }
 
-// k_cont_trace as a programmatic dependent launch: it may start while the
-// kernel before it on the stream (k_verify) is finishing.
+// k_cont_trace right after k_verify.  With PV_CONT_TRACE_PDL it is a
+// programmatic dependent launch, which may start while k_verify is finishing.
+// That made back-to-back frames 3 % slower (villa 1.182 against 1.147 ms per
+// frame, city 0.440 against 0.427 ms) with the same time from a frame's first
+// launch to its last: the cost fell between frames.  So the launch is an
+// ordinary one by default.
+#ifndef PV_CONT_TRACE_PDL
+#define PV_CONT_TRACE_PDL 0
+#endif
 template <int kDep>
 void launch_cont_trace_pdl(int blocks, const SceneView& sv, const FrameLights& L, const TraceArgs& A,
                            const ContArgs& C, const DepositArgs& D, cudaStream_t st) {
@@ -408,7 +416,7 @@ void launch_cont_trace_pdl(int blocks, const SceneView& sv, const FrameLights& L
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
+  at[0].val.programmaticStreamSerializationAllowed = PV_CONT_TRACE_PDL;
   cfg.attrs = at;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, k_cont_trace<kDep>, sv, L, A, C, D);

@@ -36,8 +36,8 @@ namespace {
 constexpr bool kVerifyLoop = PV_VERIFY_FLAT && PV_VERIFY_PERSISTENT;
 
 // Flat segment mapping in error mode, else thread per path; with
-// kVerifyLoop a grid of resident blocks looping over tiles.  The dependent re-trace kernel may be scheduled
-// as soon as every block has started.
+// kVerifyLoop a grid of resident blocks looping over tiles.  A re-trace kernel launched as its
+// programmatic dependent (PV_CONT_TRACE_PDL) may be scheduled as soon as every block has started.
 template <bool kPointVis, bool kExact>
 __device__ __forceinline__ void verify_kernel(const SceneView& sv, const FrameLights& L, const VerifyArgs& A,
                                               VerifySmem& sm) {
